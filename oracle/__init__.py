@@ -1,0 +1,29 @@
+"""FP64 CPU oracle for PCV -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA library and
+its binding) never imports, links or calls it, and it imports nothing from
+the product.  The C source ``pcv_oracle.c`` is compiled by ``build()`` into
+``oracle/_build/liboracle.so``.
+
+Parity status of each function (pins live in ``tests/test_oracle_*.py``):
+
+* Philox4x32-10 -- pinned by the generator's published known-answer vectors.
+* normals / uniforms / init index -- pinned by moments and exact integer math.
+* log density, gradient, held-out log predictive -- pinned by conjugate
+  sufficient-statistic identities, central finite differences and brute
+  force sums.
+* leapfrog trajectory -- pinned by the closed-form linear map on a quadratic
+  potential, reversibility and O(eps^2) energy error.
+* online accumulators and estimators -- pinned against two-pass batch
+  formulas (eq. bmean / bmvar / rhat) on stored draws, against the AR(1)
+  closed-form ESS, and against the conjugate closed-form fold posteriors.
+* full-data warm-up (dual averaging, mass estimate) -- parity unpinned
+  beyond the conjugate-model checks: it is an adaptive heuristic with no
+  closed form; its outputs are only checked statistically.
+"""
+from .oracle import (  # noqa: F401
+    build, lib, Problem, problem_from_workload, philox, normals, uniform,
+    index, log_density, trajectory, accumulate_series, OraclePCV,
+    FOLD_FIELDS, TOTAL_FIELDS,
+)
