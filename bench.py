@@ -1,0 +1,302 @@
+#!/usr/bin/env python3
+"""PCV throughput benchmark: leapfrog gradient evaluations per second over
+all fold-chains (one step = one lock-step HMC iteration of every chain:
+momentum draw, L_f fused gradient+update launches, FP64 accept and the
+online accumulators).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--precision fp32|bf16|tf32]
+
+Multi-GPU (torchrun, one rank per GPU): each rank runs its own copy of the
+workload with its own sampler seed (folds are independent posteriors, so the
+path shards with no data-path collective; weak scaling).  Rank 0 prints one
+JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2310_07002_b300 import workloads as W  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP32 CUDA-core peak: 148 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.032 GHz
+FP32_SIMT_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+
+WORKLOADS = {
+    "logistic_loo": lambda: W.logistic_loo(),        # N=2000, p=20, K=2000, L=8
+    "logistic_large": lambda: W.logistic_large(),    # N=1e5, p=100, K=1000, L=16
+    "gauss_blocks": lambda: W.gauss_blocks(),
+    "hier_logo": lambda: W.hier_logo(),
+    "ar2_hvblock": lambda: W.ar2_hvblock(),
+}
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+def flops_per_grad_eval(w) -> float:
+    """Algorithmic flops of one masked log-density gradient for one chain:
+    2 N p for x'beta over all N rows and 2 N p for X'r (Appendix B masking
+    evaluates every row)."""
+    return 4.0 * w.N * w.p
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f:
+            parts = [t.strip() for t in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_rate(w, seconds: float, n_chains_target: int, threads: int):
+    """Oracle (as it stands) on a bounded sample of the workload: the first
+    folds' chains over all N rows, started at the data-generating parameters.
+    Returns (grad-evals/s, description, cores)."""
+    import oracle
+    L = w.chains_per_fold
+    n_folds = max(1, n_chains_target // L)
+    sub_fold = np.where((w.fold >= 0) & (w.fold < n_folds), w.fold, -1).astype(np.int32)
+    prob = oracle.oracle._ProblemHolder(w.kind, w.X, w.y, sub_fold, n_folds, w.hv_buffer, w.group,
+                                        w.n_groups, w.beta_prior_sd, w.sigma_known,
+                                        w.sigma_prior_sd, w.tau_prior_sd)
+    d = prob.dim
+    th = np.zeros((n_folds * L, d))
+    truth = w.truth.get("beta", w.truth.get("phi"))
+    if truth is not None:
+        th[:, :len(truth)] = truth
+    run = oracle.OraclePCV(prob, L, w.seed, w.leapfrog_steps, eps=1e-3, b=1,
+                           max_batches=1 << 16, n_threads=threads)
+    run.set_state(th, eps=1e-3)
+    iters = 0
+    t0 = time.perf_counter()
+    while True:
+        run.sample(1)
+        iters += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    evals = n_folds * L * w.leapfrog_steps * iters
+    desc = ("%d folds x %d chains x %d iterations (%d leapfrog steps each) over all %d rows"
+            % (n_folds, L, iters, w.leapfrog_steps, w.N))
+    return evals / el, desc, threads
+
+
+def run_reference(args, w):
+    """Reference arm: the FP64 oracle on the host cores, bounded samples."""
+    threads = os.cpu_count() or 1
+    per_step = max(0.5, min(5.0, 150.0 / max(1, args.steps + args.warmup)))
+    target = 64 if w.N * w.p < 1e6 else 16
+    oracle_rate(w, 0.2, target, threads)               # warm-up (page-in, threads)
+    rates = []
+    desc = ""
+    for _ in range(args.steps):
+        r, desc, _ = oracle_rate(w, per_step, target, threads)
+        rates.append(r)
+    value = float(np.mean(rates))
+    line = {
+        "impl": "reference", "metric": "leapfrog grad-evals/s over all fold-chains",
+        "value": value, "unit": "grad-evals/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "N": w.N, "p": w.p, "K": w.K, "L": w.chains_per_fold,
+                   "leapfrog_steps": w.leapfrog_steps},
+        "cpu_baseline": {"value": value, "unit": "grad-evals/s", "cores": threads,
+                         "kind": "oracle", "sample": "each step: " + desc},
+        "e2e": {"value": value, "unit": "grad-evals/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="logistic_loo", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    w = WORKLOADS[args.workload]()
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, w)
+        return
+
+    import torch
+    from paper_2310_07002_b300.build import build
+    from paper_2310_07002_b300 import pcv as P
+    build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    prec = P.PRECISIONS[args.precision]
+    K, Wu = args.steps, args.warmup
+    seed = w.seed + 7919 * rank
+    common = dict(seed=seed, batch_size=1, max_batches=K + 64, acov_max_lag=64,
+                  precision=prec, init_scale=0.1)
+    pc = P.PCV.from_workload(w, **common)
+    pc.warmup(100, Wu)                                   # untimed warm-up iterations
+    stream = pc.stream
+    C, Lf = pc.C, w.leapfrog_steps
+    # L2 flush buffer (larger than the 126 MB L2), written between timed steps
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier()
+    step_ms = []
+    for _ in range(K):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        pc.sample(1)                                     # CUDA events on the launch stream
+        step_ms.append(pc.last_sample_ms())
+    barrier()
+    clk = clocks.stop()
+    total_ms = float(np.sum(step_ms))
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    evals = float(C) * Lf * K * world
+    value = evals / (total_ms / 1e3)
+
+    # dominant kernel: the fused leapfrog gradient launch, timed live
+    k_ms = pc.time_leapfrog_kernel(20)
+    fl = flops_per_grad_eval(w) * C
+    pk, pk_kind = peaks()
+    if prec == P.FP32_SIMT:
+        roof = {"bound": "alu", "achieved": fl / (k_ms / 1e3) / 1e12,
+                "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "peak_source": "FP32 CUDA-core peak from unit counts and the 2032 MHz max clock"}
+    else:
+        ratio = 1.0 if prec == P.BF16 else 0.5
+        pkv = pk.get("bf16_tflops_sustained", 1400.0) * ratio
+        roof = {"bound": "tensor", "achieved": fl / (k_ms / 1e3) / 1e12, "peak": pkv,
+                "unit": "TFLOP/s", "peak_source": "%s sustained bf16 x %.1f" % (pk_kind, ratio)}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel_ms"] = k_ms
+    pc.close()
+
+    # end to end through the C ABI with host buffers: create (H2D of X, y,
+    # folds), set positions (H2D), K iterations, scores + diagnostics (D2H)
+    theta0 = np.zeros((C, w.dim))
+    truth = w.truth.get("beta", w.truth.get("phi"))
+    if truth is not None:
+        theta0[:, :len(truth)] = truth
+    barrier()
+    t0 = time.perf_counter()
+    pe = P.PCV.from_workload(w, **dict(common, batch_size=K // 2 if K % 2 == 0 else 1))
+    pe.set_positions(theta0, step_size=1e-3)
+    pe.sample(K)
+    sc = pe.scores()
+    dg = pe.diagnostics()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    pe.close()
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = 4 * w.N * w.p + 4 * w.N + 4 * w.N + 8 * C * w.dim
+    d2h = 8 * w.K * 2 + 8 * 3 + 8 * w.K * 5 + 8 * 2
+    _ = (sc, dg)
+
+    line = {
+        "metric": "leapfrog grad-evals/s over all fold-chains",
+        "value": value, "unit": "grad-evals/s", "n_gpus": world, "steps": K, "warmup": Wu,
+        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "tf32": "tf32", "bf16": "bf16"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": w.name, "N": w.N, "p": w.p, "K": w.K, "L": w.chains_per_fold,
+                   "chains": C, "leapfrog_steps": Lf, "precision": args.precision,
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": "replica per GPU (independent fold-chains)"},
+        "gpu_launches": K * (Lf + 2),
+        "roofline": roof,
+        "clocks": clk,
+        "e2e": {"value": evals / e2e_s,
+                "unit": "grad-evals/s", "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, desc, cores = oracle_rate(w, 12.0, 64 if w.N * w.p < 1e6 else 16, os.cpu_count() or 1)
+        line["cpu_baseline"] = {"value": r, "unit": "grad-evals/s", "cores": cores,
+                                "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,271 @@
+/*
+ * pcv.h -- C ABI of the B300 (sm_103a) parallel Bayesian cross-validation
+ * library (PCV; "Bayesian cross-validation by parallel Markov chain Monte
+ * Carlo", arXiv 2310.07002).
+ *
+ * One context holds one model, one data set, one CV design and K*L HMC
+ * chains (L chains for each of K folds) that advance in lock-step on one
+ * GPU (Section 3.3).  The workflow of Section 3 maps to the calls:
+ *
+ *   Step 1/2  pcv_warmup       full-data chains adapt step size and mass,
+ *                              fold chains start from full-data draws and
+ *                              run a short discarded warm-up (Section 3.1)
+ *   Step 3    pcv_sample       parallel sampling with online accumulators
+ *                              (Algorithm A2); callable repeatedly
+ *   Step 4    pcv_scores       per-fold elpd and MCSE (eq. cv-score, mc-var)
+ *             pcv_diagnostics  per-fold and max R-hat, ESS (Section 4)
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a pcv_status; nothing throws or aborts across the
+ *     ABI.  On failure the context (when there is one) keeps a message for
+ *     pcv_last_error.
+ *   - "host" pointers are ordinary CPU memory owned by the caller; "device"
+ *     pointers are CUDA global memory on the context's device, owned by the
+ *     caller.  The library never retains a caller pointer after a call
+ *     returns.
+ *   - Work is issued on the stream given in pcv_options.cuda_stream (NULL:
+ *     the legacy default stream).  Calls that return host results
+ *     synchronise that stream before returning; device-result calls are
+ *     asynchronous on it.
+ *   - Matrices are row-major.
+ */
+#ifndef PCV_H
+#define PCV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pcv_ctx pcv_ctx;
+
+typedef enum {
+    PCV_OK = 0,
+    PCV_E_INVALID_ARG = 1,  /* a size, pointer or option is out of range */
+    PCV_E_BAD_STATE = 2,    /* call out of order (see the state machine) */
+    PCV_E_CUDA = 3,         /* a CUDA runtime error; message has the reason */
+    PCV_E_OOM = 4,          /* device allocation failed */
+    PCV_E_NUMERIC = 5,      /* non-finite data, or a non-finite state */
+    PCV_E_TIMEOUT = 6,      /* a bounded device-side wait ran out */
+    PCV_E_UNSUPPORTED = 7   /* valid request this build does not implement */
+} pcv_status;
+
+/* Likelihood families (the Appendix B masks apply to all of them). */
+typedef enum {
+    PCV_GAUSS_LINEAR = 0,   /* y ~ N(x'beta, sigma^2); sigma known or sampled */
+    PCV_LOGISTIC = 1,       /* y ~ Bernoulli(sigmoid(x'beta)) */
+    PCV_HIER_GAUSS = 2,     /* y ~ N(x'beta + tau z_g(n), sigma^2), z ~ N(0,1) */
+    PCV_AR_GAUSS = 3        /* Gaussian on a lagged design, sigma sampled */
+} pcv_model_kind;
+
+/* Arithmetic of the leapfrog gradient (the accept test and the online
+ * accumulators are FP64 in every mode). */
+typedef enum {
+    PCV_FP32_SIMT = 0,      /* FP32 CUDA-core kernels */
+    PCV_TF32 = 1,           /* tcgen05 tensor cores, TF32 in, FP32 accumulate */
+    PCV_BF16 = 2            /* tcgen05 tensor cores, BF16 in, FP32 accumulate */
+} pcv_precision;
+
+/*
+ * Model.  Parameter vector theta (dimension pcv_dim()):
+ *   GAUSS_LINEAR, sigma_known > 0 : beta[p]
+ *   GAUSS_LINEAR, sigma_known <= 0: beta[p], log sigma
+ *   AR_GAUSS                      : phi[p] (coefficients of the lag columns), log sigma
+ *   LOGISTIC                      : beta[p]
+ *   HIER_GAUSS                    : beta[p], z[n_groups], log tau, log sigma
+ * Priors: beta ~ N(0, beta_prior_sd^2 I); sigma ~ half-N(0, sigma_prior_sd);
+ * tau ~ half-N(0, tau_prior_sd); scale parameters are sampled on the log
+ * scale with the log-Jacobian added.
+ */
+typedef struct {
+    int32_t kind;              /* pcv_model_kind */
+    double beta_prior_sd;      /* > 0 */
+    double sigma_known;        /* GAUSS_LINEAR: > 0 known noise sd, <= 0 sampled */
+    double sigma_prior_sd;     /* > 0 when sigma is sampled */
+    double tau_prior_sd;       /* > 0 (HIER_GAUSS) */
+    const int32_t *group;      /* host, N entries in [0, n_groups) (HIER_GAUSS), else NULL */
+    int32_t n_groups;          /* HIER_GAUSS only */
+} pcv_model;
+
+/* Optional device allocator (the Python binding passes the torch caching
+ * allocator).  NULL: cudaMalloc / cudaFree. */
+typedef void *(*pcv_alloc_fn)(size_t bytes, void *user);
+typedef void (*pcv_free_fn)(void *ptr, void *user);
+
+typedef struct {
+    uint64_t seed;             /* Philox4x32-10 key */
+    int32_t leapfrog_steps;    /* L_f >= 1 */
+    double step_size;          /* > 0 fixed; <= 0 adapted in the full-data warm-up */
+    const double *inv_mass_diag; /* host, pcv_dim() entries, or NULL (identity, or adapted
+                                    when step_size <= 0) */
+    int32_t batch_size;        /* b of eq. bmean, >= 1 (default 50) */
+    int32_t hv_buffer;         /* h rows excluded on each side of a test block (default 0) */
+    int32_t precision;         /* pcv_precision (default PCV_FP32_SIMT) */
+    void *cuda_stream;         /* cudaStream_t, NULL = legacy default stream */
+    int32_t store_draws;       /* > 0: also keep up to this many draws per chain of the
+                                  held-out log predictive (Algorithm 1 test mode) */
+    int32_t acov_max_lag;      /* M for the autocorrelation ESS (default 64, 0 = off) */
+    int32_t max_batches;       /* capacity of per-batch summaries (default 1024) */
+    int32_t n_fulldata_draws;  /* draws kept per full-data chain as the init pool (default 250) */
+    double init_scale;         /* full-data chains start at init_scale * N(0, I) (default 1) */
+    int32_t use_graphs;        /* 1: replay iterations as CUDA graphs (default 1) */
+    pcv_alloc_fn device_alloc; /* optional allocator (see above) */
+    pcv_free_fn device_free;
+    void *alloc_user;
+} pcv_options;
+
+/* Fill *opt with the defaults listed above (seed 0, L_f 16, adapted step). */
+void pcv_default_options(pcv_options *opt);
+
+/*
+ * Create a context (state: created).
+ *   X               host, N x p row-major, finite
+ *   y               host, N, finite (LOGISTIC: 0 or 1)
+ *   fold_assignment host, N; fold of each row in [0, K) or -1 for rows that are
+ *                   in no test set; every fold 0..K-1 must appear.  With
+ *                   hv_buffer > 0 each fold's test rows must be contiguous.
+ *   chains_per_fold L >= 2 (R-hat needs two chains)
+ * Rows are re-ordered internally so that each fold's test rows (and, for
+ * HIER_GAUSS, each group) are contiguous; results do not depend on the
+ * caller's row order except through hv_buffer.  X, y and the fold layout are
+ * copied to device memory owned by the context.  The fold masks are those
+ * of eq. mask-log-prob / mask-log-pred (Appendix B), the training mask being
+ * the complement of the test mask (minus the h(v)-block buffer).
+ * Errors: INVALID_ARG (N < 1, p < 1, L < 2, a fold with no test or no
+ * training rows, missing fold ids, bad option), NUMERIC (non-finite data),
+ * UNSUPPORTED (precision/model/size combination not built), OOM, CUDA.
+ */
+pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
+                      const int32_t *fold_assignment, int64_t N, int32_t p,
+                      int32_t chains_per_fold, const pcv_options *opt, pcv_ctx **out);
+
+/*
+ * Warm-up reuse (Section 3.1; Algorithm 1 before its sampling loop):
+ * 4 full-data chains run n_fulldata_warmup adaptation iterations (dual
+ * averaging of the step size toward acceptance 0.8 unless a step size was
+ * given; a diagonal inverse mass from iterations [n/4, n/2) unless one was
+ * given) and n_fulldata_draws kept iterations; each fold chain starts from a
+ * full-data draw chosen uniformly with replacement and runs n_fold_warmup
+ * discarded iterations.  State: created -> warmed.  May be called once.
+ */
+pcv_status pcv_warmup(pcv_ctx *ctx, int32_t n_fulldata_warmup, int32_t n_fold_warmup);
+
+/*
+ * Draw n_draws (a positive multiple of batch_size) HMC iterations for all
+ * K*L chains and feed each draw of s = log p(y_test_k | theta) into the
+ * online accumulators (Algorithm A2).  Repeatable: later calls continue the
+ * same chains and accumulators (progressive estimates).  State: warmed or
+ * sampled -> sampled.
+ */
+pcv_status pcv_sample(pcv_ctx *ctx, int32_t n_draws);
+
+/*
+ * Scores (host outputs, caller-owned; any pointer may be NULL):
+ *   elpd_k[K]   log of the Monte Carlo mean of p(y_test_k | theta)  (eq. cv-score term)
+ *   mcse_k[K]   its MCSE by batch means and the delta method     (eq. bmvar, mc-var)
+ *   elpd_total  sum of elpd_k; mcse_total = sqrt(sum mcse_k^2)
+ *   se_epistemic sqrt(K var_k(elpd_k))                          (eq. norm-approx)
+ * Needs at least 2 batches sampled (BAD_STATE otherwise).
+ */
+pcv_status pcv_scores(pcv_ctx *ctx, double *elpd_k, double *mcse_k, double *elpd_total,
+                      double *mcse_total, double *se_epistemic);
+
+/*
+ * Diagnostics on the s draws (host outputs, caller-owned; any may be NULL):
+ *   rhat_k[K]        eq. rhat (no splitting, no rank normalisation)
+ *   split_rhat_k[K]  eq. rhat over 2L half chains made of whole batches
+ *   ess_bm_k[K]      L n s^2 / sigma^2_bm of exp(s)              (Section 4.1)
+ *   ess_acov_k[K]    multi-chain autocorrelation ESS of s (Geyer initial
+ *                    monotone sequence, lags <= acov_max_lag)
+ *   divergences_k[K] divergent transitions while sampling
+ *   rhat_max         max_k rhat_k                                (eq. rhat-max)
+ *   ess_total        aggregate ESS over folds                    (Section 4.1)
+ */
+pcv_status pcv_diagnostics(pcv_ctx *ctx, double *rhat_k, double *split_rhat_k,
+                           double *ess_bm_k, double *ess_acov_k, int64_t *divergences_k,
+                           double *rhat_max, double *ess_total);
+
+int32_t pcv_num_folds(const pcv_ctx *ctx);    /* K, or -1 for NULL */
+int32_t pcv_num_chains(const pcv_ctx *ctx);   /* K * L */
+int32_t pcv_dim(const pcv_ctx *ctx);          /* dimension of theta */
+const char *pcv_last_error(const pcv_ctx *ctx);  /* never NULL; valid until the next call */
+void pcv_destroy(pcv_ctx *ctx);               /* frees all device memory; NULL is a no-op */
+
+/* ---------------- inspection and test entry points ---------------- */
+
+/*
+ * Set every fold chain's position (host, C x dim, chain c = k*L + l) and,
+ * optionally, the step size (> 0) and inverse mass (host, dim; NULL keeps
+ * it), instead of pcv_warmup.  Recomputes log densities and gradients.
+ * State: created/warmed -> warmed (accumulators untouched).
+ */
+pcv_status pcv_set_positions(pcv_ctx *ctx, const double *theta, double step_size,
+                             const double *inv_mass_diag);
+
+/* Current positions (host C x dim), log posterior and held-out log
+ * predictive at them (host C each); any pointer may be NULL. */
+pcv_status pcv_get_positions(pcv_ctx *ctx, double *theta, double *logp, double *shat);
+
+/* Step size and inverse mass (host, dim) in use. */
+pcv_status pcv_get_adaptation(pcv_ctx *ctx, double *step_size, double *inv_mass_diag);
+
+/*
+ * Evaluate, for n (position, fold) pairs, the fold-masked log posterior
+ * (eq. mask-log-prob + log prior), its gradient and the held-out log
+ * predictive (eq. mask-log-pred) with the kernels of the given precision.
+ *   theta   device, n x dim FP32
+ *   fold    device, n fold ids in [0, K]; K means the full data set
+ *   logp    device, n FP64 (out)      grad device, n x dim FP32 (out)
+ *   shat    device, n FP64 (out)
+ * Uses the context's workspace.  Asynchronous on the context stream.
+ */
+pcv_status pcv_log_density(pcv_ctx *ctx, const float *theta, const int32_t *fold, int32_t n,
+                           int32_t precision, double *logp, float *grad, double *shat);
+
+/*
+ * One leapfrog trajectory (L_f steps, Section 3.3) for every fold chain from
+ * the given start: theta0, r0 device C x dim FP32.  Outputs (device):
+ * theta1, r1 C x dim FP32; logp1, shat1 C FP64.  Uses the context's step
+ * size and inverse mass.  Does not change the chains.
+ */
+pcv_status pcv_trajectory(pcv_ctx *ctx, const float *theta0, const float *r0, int32_t precision,
+                          float *theta1, float *r1, double *logp1, double *shat1);
+
+/*
+ * Standard normals the sampler draws for (iteration, stream): device out,
+ * C x dim FP32, chain c in row c.  Streams: 0 fold momentum, 16 full data.
+ */
+pcv_status pcv_draw_normals(pcv_ctx *ctx, uint32_t iteration, uint32_t stream, float *out);
+
+/*
+ * Feed n given draws per chain (device, C x n FP64) to the online
+ * accumulators, as if sampled.  n must be a multiple of batch_size.
+ * State: warmed/sampled -> sampled.
+ */
+pcv_status pcv_accumulate(pcv_ctx *ctx, const double *shat, int32_t n);
+
+/* Stored draws (host, C x n_stored FP64) when store_draws > 0; *n_stored out. */
+pcv_status pcv_get_draws(pcv_ctx *ctx, double *shat, int32_t *n_stored);
+
+/* Mean acceptance rate per fold over sampling (host, K). */
+pcv_status pcv_accept_rate(pcv_ctx *ctx, double *accept_k);
+
+/* Device time in milliseconds of the most recent pcv_sample call (CUDA events
+ * on the context stream). */
+pcv_status pcv_last_sample_ms(pcv_ctx *ctx, double *ms);
+
+/*
+ * Time the fused leapfrog gradient kernel exactly as sampling launches it
+ * (one kick-drift step for all fold chains, Section 3.3): `reps` launches on
+ * the context stream between two CUDA events; *ms_per_launch receives the
+ * mean.  Only the proposal buffers change (the next iteration overwrites
+ * them); needs warmed positions.
+ */
+pcv_status pcv_time_leapfrog_kernel(pcv_ctx *ctx, int32_t reps, double *ms_per_launch);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PCV_H */

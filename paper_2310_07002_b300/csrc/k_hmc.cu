@@ -1,0 +1,518 @@
+// k_hmc.cu -- per-chain HMC kernels around the fused gradient step:
+//   k_begin     momentum draw (Philox4x32-10 + Box-Muller), H0, first
+//               half-kick and drift of the leapfrog (Section 3.3)
+//   k_accept    FP64 Hamiltonian difference and Metropolis accept, the
+//               divergence count, and the online accumulators of
+//               Algorithm A2 (Appendix A.1) updated in place
+//   k_fd_adapt  full-data dual averaging of the step size and the windowed
+//               diagonal mass estimate (warm-up reuse, Section 3.1)
+//   k_finalize  per-fold estimators: elpd, MCSE (eq. bmvar, mc-var), ESS
+//               (Section 4.1), R-hat / split R-hat (eq. rhat), Geyer ESS
+// All accept-test and accumulator arithmetic is FP64.
+#include "pcv_internal.cuh"
+
+namespace pcv {
+
+// ---------------------------------------------------------------------------
+// k_begin: one warp per chain
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_begin(BeginArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (c >= a.C) return;
+  const unsigned it = *a.iter;
+  const float eps = *a.eps;
+  const float *th = a.theta + (size_t)c * a.ld;
+  const float *g = a.grad + (size_t)c * a.ld;
+  double kin = 0.0;
+  for (int q = lane; 4 * q < a.d; q += 32) {
+    float z[4];
+    if (a.r_given) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) z[e] = 0.0f;
+    } else {
+      const uint4 w = philox_at(a.seed, (uint32_t)q, (uint32_t)c, it, a.stream);
+      const float2 p0 = box_muller(w.x, w.y), p1 = box_muller(w.z, w.w);
+      z[0] = p0.x; z[1] = p0.y; z[2] = p1.x; z[3] = p1.y;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int j = 4 * q + e;
+      if (j >= a.d) break;
+      const float mv = a.minv[j];
+      const float r0 = a.r_given ? a.r_given[(size_t)c * a.ld + j] : z[e] / sqrtf(mv);
+      kin += (double)mv * (double)r0 * (double)r0;
+      const float rh = r0 + 0.5f * eps * g[j];
+      const float tn = th[j] + eps * mv * rh;
+      a.r[(size_t)c * a.ld + j] = rh;
+      a.theta_p[(size_t)c * a.ld + j] = tn;
+      if (a.shadow_hi) {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(tn);
+        a.shadow_hi[(size_t)c * a.ld_shadow + j] = hi;
+        a.shadow_lo[(size_t)c * a.ld_shadow + j] = __float2bfloat16_rn(tn - __bfloat162float(hi));
+      }
+    }
+  }
+  kin = warp_sum_d(kin);
+  if (lane == 0) a.H0[c] = -a.logp[c] + 0.5 * kin;
+}
+
+// standard normals for (iteration, stream) into out[C x ld] (scaled)
+__global__ void __launch_bounds__(256) k_normals(int C, int d, int ld, unsigned long long seed,
+                                                 unsigned int iter, unsigned int stream,
+                                                 float scale, float *out) {
+  const int nq = (d + 3) / 4;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)C * nq) return;
+  const int c = (int)(t / nq), q = (int)(t - (long long)c * nq);
+  const uint4 w = philox_at(seed, (uint32_t)q, (uint32_t)c, iter, stream);
+  const float2 p0 = box_muller(w.x, w.y), p1 = box_muller(w.z, w.w);
+  const float z[4] = {p0.x, p0.y, p1.x, p1.y};
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int j = 4 * q + e;
+    if (j < d) out[(size_t)c * ld + j] = scale * z[e];
+  }
+}
+
+// fold chains start from full-data draws chosen uniformly with replacement:
+// index = floor(w0 * n_pool / 2^32) from Philox stream ST_INIT (Algorithm 1)
+__global__ void k_init_from_pool(int C, int d, int ld, unsigned long long seed, const float *pool,
+                                 int n_pool, float *theta) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)C * d) return;
+  const int c = (int)(t / d), j = (int)(t - (long long)c * d);
+  const uint4 w = philox_at(seed, 0u, (uint32_t)c, 0u, ST_INIT);
+  const unsigned idx = (unsigned)(((unsigned long long)w.x * (unsigned long long)n_pool) >> 32);
+  theta[(size_t)c * ld + j] = pool[(size_t)idx * ld + j];
+}
+
+__global__ void k_shadow(int C, int d, int ld, const float *theta, __nv_bfloat16 *hi,
+                         __nv_bfloat16 *lo, int ld_shadow) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)C * d) return;
+  const int c = (int)(t / d), j = (int)(t - (long long)c * d);
+  const float v = theta[(size_t)c * ld + j];
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  hi[(size_t)c * ld_shadow + j] = h;
+  lo[(size_t)c * ld_shadow + j] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+// ---------------------------------------------------------------------------
+// online accumulators (Algorithm A2 with the readings: log-shifted Welford
+// instead of centred log-space sums)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double log_add_exp(double a, double b) {
+  if (a == -INFINITY) return b;
+  if (b == -INFINITY) return a;
+  const double m = fmax(a, b);
+  return m + log1p(exp(-fabs(a - b)));
+}
+
+// running (shift, mean, M2) of exp(lv - shift) values; count_after >= 1
+__device__ __forceinline__ void lshift_push(double &shift, double &mean, double &M2,
+                                            long long count_after, double lv) {
+  if (lv > shift) {
+    if (shift != -INFINITY) {
+      const double sc = exp(shift - lv);
+      mean *= sc;
+      M2 *= sc * sc;
+    }
+    shift = lv;
+  }
+  const double v = exp(lv - shift);
+  const double delta = v - mean;
+  mean += delta / (double)count_after;
+  M2 += delta * (v - mean);
+}
+
+// push draw s of chain c; n_before draws already accumulated (same for all
+// chains).  Called by a full warp.
+__device__ void accum_push(const Accum &A, int c, double s, long long n_before, int lane) {
+  const long long n = n_before + 1;
+  const int b = A.b;
+  const int in_batch = (int)(n_before % b) + 1;
+  double x = 0.0;
+  if (lane == 0) {
+    A.Ux[c] = log_add_exp(A.Ux[c], s);
+    A.Ux2[c] = log_add_exp(A.Ux2[c], 2.0 * s);
+    A.Zx[c] = log_add_exp(in_batch == 1 ? -INFINITY : A.Zx[c], s);
+    double em = A.em[c], emean = A.emean[c], eM2 = A.eM2[c];
+    lshift_push(em, emean, eM2, n, s);
+    A.em[c] = em; A.emean[c] = emean; A.eM2[c] = eM2;
+    double wm = A.wmean[c], wM2 = A.wM2[c];
+    double dl = s - wm;
+    wm += dl / (double)n;
+    wM2 += dl * (s - wm);
+    A.wmean[c] = wm; A.wM2[c] = wM2;
+    double bm = in_batch == 1 ? 0.0 : A.bmean_cur[c], b2 = in_batch == 1 ? 0.0 : A.bM2_cur[c];
+    dl = s - bm;
+    bm += dl / (double)in_batch;
+    b2 += dl * (s - bm);
+    A.bmean_cur[c] = bm; A.bM2_cur[c] = b2;
+    if (n_before == 0) A.c0[c] = s;
+    x = s - A.c0[c];
+    A.xsum[c] += x;
+    if (in_batch == b) {                     // the batch closes (A2 batch loop end)
+      const long long na = n / b;
+      const double z = A.Zx[c] - log((double)b);   // log of the batch mean, eq. bmean
+      double vm = A.vm[c], vmean = A.vmean[c], vM2 = A.vM2[c];
+      lshift_push(vm, vmean, vM2, na, z);
+      A.vm[c] = vm; A.vmean[c] = vmean; A.vM2[c] = vM2;
+      if (na <= A.max_batches) {
+        A.bmean[(size_t)(na - 1) * A.C + c] = bm;
+        A.bM2[(size_t)(na - 1) * A.C + c] = b2;
+      }
+    }
+  }
+  if (A.M > 0) {
+    x = __shfl_sync(0xffffffffu, x, 0);
+    const long long t = n_before;                // 0-based time of this draw
+    double *lag = A.lagsum + (size_t)c * (A.M + 1);
+    double *ring = A.ring + (size_t)c * A.M;
+    for (int m = lane; m <= A.M; m += 32) {
+      if (m == 0) lag[0] += x * x;
+      else if (m <= t) lag[m] += x * ring[(t - m) % A.M];
+    }
+    __syncwarp();
+    if (lane == 0) {
+      ring[t % A.M] = x;
+      if (t < A.M) A.first[(size_t)c * A.M + t] = x;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_accept: one warp per chain; the last block advances the counters
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_accept(AcceptArgs a) {
+  __shared__ int is_last;
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const unsigned it = a.fd ? a.st->fd_iter : a.st->iter;
+  const long long n_before = a.st->n_draws;
+  if (c < a.C) {
+    double kin = 0.0;
+    for (int j = lane; j < a.d; j += 32) {
+      const double rj = a.r[(size_t)c * a.ld + j];
+      kin += (double)a.minv[j] * rj * rj;
+    }
+    kin = warp_sum_d(kin);
+    const double H1 = -a.logp_p[c] + 0.5 * kin;
+    const double dH = H1 - a.H0[c];
+    const uint4 w = philox_at(a.seed, 0u, (uint32_t)c, it, a.stream);
+    const double logu = log(unit_from_word(w.x));
+    const bool finite = isfinite(H1) && isfinite(dH);
+    const bool acc = finite && (logu < -dH);
+    const bool div = !finite || dH > 1000.0;
+    if (acc) {
+      for (int j = lane; j < a.d; j += 32) {
+        a.theta[(size_t)c * a.ld + j] = a.theta_p[(size_t)c * a.ld + j];
+        a.grad[(size_t)c * a.ld + j] = a.grad_p[(size_t)c * a.ld + j];
+      }
+    }
+    if (lane == 0) {
+      if (acc) {
+        a.logp[c] = a.logp_p[c];
+        a.shat[c] = a.shat_p[c];
+      }
+      if (a.accept_prob) a.accept_prob[c] = finite ? (dH <= 0.0 ? 1.0 : exp(-dH)) : 0.0;
+      if (a.accumulate) {
+        a.acc.div[c] += div ? 1 : 0;
+        a.acc.acc[c] += acc ? 1 : 0;
+      }
+    }
+    if (a.accumulate) {
+      const double s = acc ? a.shat_p[c] : a.shat[c];
+      accum_push(a.acc, c, s, n_before, lane);
+      if (lane == 0 && a.acc.draws && n_before < a.acc.draw_cap)
+        a.acc.draws[(size_t)c * a.acc.draw_cap + n_before] = s;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(&a.st->ticket, 1u);
+    is_last = prev == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (is_last && threadIdx.x == 0) {
+    __threadfence();
+    a.st->ticket = 0u;
+    if (a.fd) a.st->fd_iter += 1u;
+    else {
+      a.st->iter += 1u;
+      if (a.accumulate) a.st->n_draws += 1;
+    }
+  }
+}
+
+// push given draws (test entry): one warp per chain, draws[t] for t in [0, n)
+__global__ void __launch_bounds__(256) k_accumulate_given(Accum A, const double *s, int n,
+                                                           long long n0) {
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (c >= A.C) return;
+  for (int t = 0; t < n; ++t) {
+    const double v = s[(size_t)c * n + t];
+    accum_push(A, c, v, n0 + t, lane);
+    if (lane == 0 && A.draws && n0 + t < A.draw_cap) A.draws[(size_t)c * A.draw_cap + n0 + t] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// full-data adaptation (one block), run after each full-data iteration
+// ---------------------------------------------------------------------------
+
+__device__ void da_reset(IterState *st, double eps) {
+  st->da_mu = log(10.0 * eps);
+  st->da_hbar = 0.0;
+  st->da_logeps = log(eps);
+  st->da_logeps_bar = 0.0;
+  st->da_t = 0;
+}
+
+__global__ void k_fd_adapt(FdAdaptArgs a) {
+  const int i = (int)a.st->fd_iter - 1;          // iteration just completed
+  if (i < a.n_adapt) {
+    if (a.adapt_eps && threadIdx.x == 0) {
+      // Nesterov dual averaging (Hoffman & Gelman 2014): delta 0.8, gamma 0.05,
+      // t0 10, kappa 0.75
+      double asum = 0.0;
+      for (int c = 0; c < a.C; ++c) asum += a.accept_prob[c];
+      IterState *st = a.st;
+      st->da_t += 1;
+      const double t = (double)st->da_t;
+      const double wgt = 1.0 / (t + 10.0);
+      st->da_hbar = (1.0 - wgt) * st->da_hbar + wgt * (0.8 - asum / a.C);
+      st->da_logeps = st->da_mu - sqrt(t) / 0.05 * st->da_hbar;
+      const double eta = pow(t, -0.75);
+      st->da_logeps_bar = eta * st->da_logeps + (1.0 - eta) * st->da_logeps_bar;
+      st->eps = (float)exp(st->da_logeps);
+    }
+    __syncthreads();
+    if (a.adapt_mass && i >= a.w0 && i < a.w1) {
+      const double n0 = a.st->mass_n;
+      for (int j = threadIdx.x; j < a.d; j += blockDim.x) {
+        double m = a.wmean[j], M2 = a.wM2[j];
+        for (int c = 0; c < a.C; ++c) {
+          const double v = a.theta[(size_t)c * a.ld + j];
+          const double dl = v - m;
+          m += dl / (n0 + c + 1);
+          M2 += dl * (v - m);
+        }
+        a.wmean[j] = m;
+        a.wM2[j] = M2;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) a.st->mass_n = n0 + a.C;
+      __syncthreads();
+      const double wn = a.st->mass_n;
+      if (i == a.w1 - 1 && wn > 1.0) {
+        const double w = wn / (wn + 5.0);
+        for (int j = threadIdx.x; j < a.d; j += blockDim.x)
+          a.minv[j] = (float)(w * (a.wM2[j] / (wn - 1.0)) + 1e-3 * (1.0 - w));
+        if (threadIdx.x == 0) da_reset(a.st, (double)a.st->eps);
+      }
+    }
+  } else {
+    const int k = i - a.n_adapt;
+    if (k < a.n_keep) {
+      for (int t = threadIdx.x; t < a.C * a.d; t += blockDim.x) {
+        const int c = t / a.d, j = t - c * a.d;
+        a.pool[((size_t)k * a.C + c) * a.ld + j] = a.theta[(size_t)c * a.ld + j];
+      }
+    }
+  }
+}
+
+__global__ void k_fd_init_state(IterState *st, float eps0, int adapt) {
+  st->eps = eps0;
+  da_reset(st, (double)eps0);
+  st->mass_n = 0.0;
+  st->fd_iter = 0u;
+  (void)adapt;
+}
+
+__global__ void k_fd_final_eps(IterState *st) { st->eps = (float)exp(st->da_logeps_bar); }
+
+// ---------------------------------------------------------------------------
+// per-fold estimators
+// ---------------------------------------------------------------------------
+
+struct Welf { double n, mean, M2; };
+__device__ __forceinline__ void welf_merge(Welf &x, double n2, double m2, double M22) {
+  const double nt = x.n + n2;
+  if (nt == 0.0) return;
+  const double dl = m2 - x.mean;
+  x.mean += dl * n2 / nt;
+  x.M2 += M22 + dl * dl * x.n * n2 / nt;
+  x.n = nt;
+}
+
+// eq. rhat from sequence summaries: sqrt(((n-1)/n W + B/n) / W)
+__device__ double rhat_eq(int nseq, double n, const double *mean, const double *M2) {
+  double Wv = 0.0, gm = 0.0;
+  for (int l = 0; l < nseq; ++l) { Wv += M2[l] / (n - 1.0); gm += mean[l]; }
+  Wv /= nseq; gm /= nseq;
+  double B = 0.0;
+  for (int l = 0; l < nseq; ++l) B += (mean[l] - gm) * (mean[l] - gm);
+  B *= n / (nseq - 1.0);
+  return sqrt((((n - 1.0) / n) * Wv + B / n) / Wv);
+}
+
+// one thread per fold; scratch: per-thread arrays in a global buffer
+__global__ void k_finalize(Accum A, int K, int L, long long n, double *out, double *scratch) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  const int b = A.b;
+  const long long a = n / b;
+  const int c0 = k * L;
+  double *o = out + (size_t)k * F_NFIELDS;
+  double *mean = scratch + (size_t)k * (4 * L + 2 * (A.M + 2));
+  double *M2 = mean + 2 * L;
+  double *rho = M2 + 2 * L;
+  // f_k by log-sum-exp of the per-chain U_x (A2 final step)
+  double lse = -INFINITY;
+  for (int l = 0; l < L; ++l) lse = log_add_exp(lse, A.Ux[c0 + l]);
+  const double Ln = (double)L * (double)n;
+  o[F_ELPD] = lse - log(Ln);
+  // pooled log-shifted Welford of exp(s) (sample variance s^2)
+  double sh = -INFINITY;
+  for (int l = 0; l < L; ++l) sh = fmax(sh, A.em[c0 + l]);
+  Welf pe = {0.0, 0.0, 0.0};
+  for (int l = 0; l < L; ++l) {
+    const double sc = exp(A.em[c0 + l] - sh);
+    welf_merge(pe, (double)n, A.emean[c0 + l] * sc, A.eM2[c0 + l] * sc * sc);
+  }
+  const double s2_rel = (pe.M2 / (pe.n - 1.0)) / (pe.mean * pe.mean);
+  // pooled batch means (eq. bmvar), centred on the grand mean f_k
+  double vsh = -INFINITY;
+  for (int l = 0; l < L; ++l) vsh = fmax(vsh, A.vm[c0 + l]);
+  Welf pv = {0.0, 0.0, 0.0};
+  for (int l = 0; l < L; ++l) {
+    const double sc = exp(A.vm[c0 + l] - vsh);
+    welf_merge(pv, (double)a, A.vmean[c0 + l] * sc, A.vM2[c0 + l] * sc * sc);
+  }
+  const double sig2_rel = ((double)b * pv.M2 / ((double)L * (double)a - 1.0)) / (pv.mean * pv.mean);
+  o[F_SIG2BM] = sig2_rel;
+  o[F_S2] = s2_rel;
+  o[F_MCSE] = sqrt(sig2_rel / Ln);                 // delta method, eq. mc-var
+  o[F_ESSBM] = Ln * s2_rel / sig2_rel;
+  // R-hat on s (eq. rhat)
+  for (int l = 0; l < L; ++l) { mean[l] = A.wmean[c0 + l]; M2[l] = A.wM2[c0 + l]; }
+  o[F_RHAT] = rhat_eq(L, (double)n, mean, M2);
+  // split R-hat: halves of whole batches (middle batch dropped if a is odd)
+  const long long half = a / 2;
+  if (half >= 1 && a <= A.max_batches) {
+    for (int l = 0; l < L; ++l) {
+      for (int hh = 0; hh < 2; ++hh) {
+        Welf w = {0.0, 0.0, 0.0};
+        const long long h0 = hh == 0 ? 0 : a - half;
+        for (long long h = h0; h < h0 + half; ++h)
+          welf_merge(w, (double)b, A.bmean[(size_t)h * A.C + c0 + l], A.bM2[(size_t)h * A.C + c0 + l]);
+        mean[2 * l + hh] = w.mean;
+        M2[2 * l + hh] = w.M2;
+      }
+    }
+    o[F_SRHAT] = rhat_eq(2 * L, (double)(half * b), mean, M2);
+  } else {
+    o[F_SRHAT] = NAN;
+  }
+  // multi-chain autocorrelation ESS of s with Geyer's initial monotone sequence
+  int trunc = 0;
+  double ess = NAN;
+  if (A.M > 0) {
+    const int Mu = (int)(A.M < n - 1 ? A.M : n - 1);
+    double Wv = 0.0, gm = 0.0, B = 0.0;
+    for (int l = 0; l < L; ++l) { Wv += A.wM2[c0 + l] / (double)(n - 1); gm += A.wmean[c0 + l]; }
+    Wv /= L; gm /= L;
+    for (int l = 0; l < L; ++l) B += (A.wmean[c0 + l] - gm) * (A.wmean[c0 + l] - gm);
+    B *= (double)n / (L - 1.0);
+    const double varplus = ((double)(n - 1) / n) * Wv + B / n;
+    for (int m = 0; m <= Mu; ++m) rho[m] = 0.0;
+    for (int l = 0; l < L; ++l) {
+      const int c = c0 + l;
+      const double xbar = A.xsum[c] / (double)n;
+      double head = 0.0, tail = 0.0;
+      for (int m = 0; m <= Mu; ++m) {
+        if (m > 0) {
+          head += A.first[(size_t)c * A.M + (m - 1)];
+          tail += A.ring[(size_t)c * A.M + (int)((n - m) % A.M)];
+        }
+        const double P = A.xsum[c] - head, Q = A.xsum[c] - tail;
+        const double gam = A.lagsum[(size_t)c * (A.M + 1) + m] - xbar * (P + Q) +
+                           (double)(n - m) * xbar * xbar;
+        rho[m] += gam / (double)n;
+      }
+    }
+    for (int m = 0; m <= Mu; ++m) rho[m] = 1.0 - (Wv - rho[m] / L) / varplus;
+    rho[0] = 1.0;
+    double tau = -1.0, prev = INFINITY;
+    trunc = 1;
+    for (int kk = 0; 2 * kk + 1 <= Mu; ++kk) {
+      double P = rho[2 * kk] + rho[2 * kk + 1];
+      if (!(P > 0.0)) { trunc = 0; break; }
+      if (P > prev) P = prev;
+      prev = P;
+      tau += 2.0 * P;
+    }
+    if (tau < 1e-12) tau = 1e-12;
+    ess = Ln / tau;
+  }
+  o[F_ESSAC] = ess;
+  o[F_ACTRUNC] = trunc;
+  double dv = 0.0, ac = 0.0;
+  for (int l = 0; l < L; ++l) { dv += (double)A.div[c0 + l]; ac += (double)A.acc[c0 + l]; }
+  o[F_DIV] = dv;
+  o[F_ACCRATE] = ac / Ln;
+}
+
+// totals over folds (one block)
+__global__ void k_totals(const double *fo, int K, double Ln, double *tot) {
+  __shared__ double sh[7][256];
+  double e = 0, m2 = 0, rmax = -INFINITY, srmax = -INFINITY, s2 = 0, sg = 0, dv = 0;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const double *o = fo + (size_t)k * F_NFIELDS;
+    e += o[F_ELPD];
+    m2 += o[F_MCSE] * o[F_MCSE];
+    rmax = fmax(rmax, o[F_RHAT]);
+    srmax = fmax(srmax, o[F_SRHAT]);
+    s2 += o[F_S2];
+    sg += o[F_SIG2BM];
+    dv += o[F_DIV];
+  }
+  sh[0][threadIdx.x] = e; sh[1][threadIdx.x] = m2; sh[2][threadIdx.x] = rmax;
+  sh[3][threadIdx.x] = srmax; sh[4][threadIdx.x] = s2; sh[5][threadIdx.x] = sg;
+  sh[6][threadIdx.x] = dv;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      for (int f = 0; f < 7; ++f) {
+        if (f == 2 || f == 3) sh[f][threadIdx.x] = fmax(sh[f][threadIdx.x], sh[f][threadIdx.x + s]);
+        else sh[f][threadIdx.x] += sh[f][threadIdx.x + s];
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double mean = sh[0][0] / K;
+    double v = 0.0;
+    for (int k = 0; k < K; ++k) {
+      const double dd = fo[(size_t)k * F_NFIELDS + F_ELPD] - mean;
+      v += dd * dd;
+    }
+    v = K > 1 ? v / (K - 1) : 0.0;
+    tot[T_ELPD] = sh[0][0];
+    tot[T_MCSE] = sqrt(sh[1][0]);
+    tot[T_SEEPI] = sqrt(K * v);
+    tot[T_RHATMAX] = sh[2][0];
+    tot[T_ESSTOT] = Ln * sh[4][0] / sh[5][0];
+    tot[T_SRHATMAX] = sh[3][0];
+    tot[T_DIV] = sh[6][0];
+  }
+}
+
+}  // namespace pcv

@@ -1,0 +1,913 @@
+// pcv_api.cu -- host side of the PCV C ABI (include/pcv.h): validation, the
+// sorted row layout and fold ranges, device buffers, and the orchestration
+// of warm-up reuse (Section 3.1) and lock-step sampling (Section 3.3,
+// Algorithm A2).  Each HMC iteration is one momentum kernel, L_f fused
+// gradient+update kernels and one accept/accumulate kernel; iterations are
+// captured once as CUDA graphs and replayed, with all counters in device
+// memory.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/pcv.h"
+#include "pcv_internal.cuh"
+
+
+using namespace pcv;
+
+namespace {
+
+constexpr int kNumFdChains = 4;
+constexpr int kTargetCtas = 148 * 4;
+
+struct ChainBufs {
+  int C = 0, L = 1, fold_base = 0;
+  float *theta = nullptr, *grad = nullptr, *theta_p = nullptr, *r = nullptr, *grad_p = nullptr;
+  double *logp = nullptr, *shat = nullptr, *logp_p = nullptr, *shat_p = nullptr, *H0 = nullptr;
+  double *accept_prob = nullptr;
+};
+
+enum CtxState { ST_CREATED = 0, ST_WARMED = 1, ST_SAMPLED = 2 };
+
+}  // namespace
+
+struct pcv_ctx {
+  std::string err;
+  pcv_options opt;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev0 = nullptr, ev1 = nullptr;
+  int kind = 0, variant = 0, p = 0, p_pad = 0, d = 0, d_pad = 0, K = 0, L = 0, C = 0, G = 0;
+  int64_t N = 0;
+  int h = 0, Lf = 16, b = 50, M = 64, max_batches = 1024, n_fd_draws = 250;
+  Problem pb{};
+  std::vector<void *> allocs;
+  // device buffers
+  float *X = nullptr, *y = nullptr, *minv = nullptr, *pool = nullptr;
+  int *seg_off = nullptr, *seg_grp = nullptr, *grp_seg = nullptr;
+  FoldDesc *folds = nullptr;
+  IterState *st = nullptr;
+  ChainBufs fold_cb, fd_cb, traj_cb;
+  Accum acc{};
+  float *ws = nullptr;
+  size_t ws_floats = 0;
+  unsigned int *tickets = nullptr;
+  size_t n_tickets = 0;
+  double *wmean = nullptr, *wM2 = nullptr;
+  double *fold_out = nullptr, *tot_out = nullptr, *fin_scratch = nullptr;
+  // host
+  std::vector<int64_t> perm;
+  int state = ST_CREATED;
+  long long n_sampled = 0;
+  double last_ms = 0.0;
+  bool finalized = false;
+  std::vector<double> h_fold, h_tot;
+  // graphs
+  cudaGraphExec_t g_sample_b = nullptr, g_fold_1 = nullptr, g_fd_1 = nullptr;
+  int fd_n_adapt = 0;
+};
+
+namespace {
+
+pcv_status fail(pcv_ctx *x, pcv_status s, const std::string &msg) {
+  if (x) x->err = msg;
+  return s;
+}
+
+pcv_status fail_cuda(pcv_ctx *x, const char *what, cudaError_t e) {
+  std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return fail(x, e == cudaErrorMemoryAllocation ? PCV_E_OOM : PCV_E_CUDA, m);
+}
+
+#define CK(call)                                             \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return fail_cuda(x, #call, e_);   \
+  } while (0)
+
+void *dalloc(pcv_ctx *x, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~(size_t)255;
+  void *ptr = nullptr;
+  if (x->opt.device_alloc) {
+    ptr = x->opt.device_alloc(bytes, x->opt.alloc_user);
+  } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+    ptr = nullptr;
+  }
+  if (ptr) {
+    x->allocs.push_back(ptr);
+    cudaMemsetAsync(ptr, 0, bytes, x->stream);
+  }
+  return ptr;
+}
+
+template <class T>
+bool dalloc_n(pcv_ctx *x, T **out, size_t n) {
+  *out = static_cast<T *>(dalloc(x, n * sizeof(T)));
+  return *out != nullptr;
+}
+
+void free_all(pcv_ctx *x) {
+  if (x->stream) cudaStreamSynchronize(x->stream);
+  for (void *p : x->allocs) {
+    if (x->opt.device_free) x->opt.device_free(p, x->opt.alloc_user);
+    else cudaFree(p);
+  }
+  x->allocs.clear();
+}
+
+int splits_for(const pcv_ctx *x, int C) {
+  const int tiles = (C + 31) / 32;
+  int s = (kTargetCtas + tiles - 1) / tiles;
+  int cap;
+  if (x->variant == MV_HIER) cap = std::max(1, x->G / 4);
+  else cap = std::max(1, (int)(x->N / 256));
+  return std::max(1, std::min(s, cap));
+}
+
+pcv_status ensure_ws(pcv_ctx *x, int C, int splits) {
+  const int tiles = (C + 31) / 32;
+  const int PP = simt_flat_pp(x->p);
+  const int stride = std::max(x->d_pad, PP) + 4;
+  const size_t need = (size_t)tiles * splits * 32 * stride;
+  if (need > x->ws_floats) {
+    float *w;
+    if (!dalloc_n(x, &w, need)) return fail(x, PCV_E_OOM, "workspace allocation failed");
+    x->ws = w;
+    x->ws_floats = need;
+  }
+  if ((size_t)tiles > x->n_tickets) {
+    unsigned *t;
+    if (!dalloc_n(x, &t, (size_t)tiles)) return fail(x, PCV_E_OOM, "ticket allocation failed");
+    x->tickets = t;
+    x->n_tickets = tiles;
+  }
+  return PCV_OK;
+}
+
+GradArgs grad_args(pcv_ctx *x, const ChainBufs &cb, bool proposal) {
+  GradArgs a{};
+  a.C = cb.C;
+  a.L = cb.L;
+  a.fold_base = cb.fold_base;
+  a.fold_of = nullptr;
+  a.theta = proposal ? cb.theta_p : cb.theta;
+  a.ld_theta = x->d_pad;
+  a.grad = proposal ? cb.grad_p : cb.grad;
+  a.ld_grad = x->d_pad;
+  a.logp = proposal ? cb.logp_p : cb.logp;
+  a.shat = proposal ? cb.shat_p : cb.shat;
+  a.need_ll = 1;
+  a.mode = MODE_NONE;
+  a.r = cb.r;
+  a.eps = &x->st->eps;
+  a.minv = x->minv;
+  a.splits = splits_for(x, cb.C);
+  a.ws = x->ws;
+  a.ws_stride = std::max(x->d_pad, simt_flat_pp(x->p)) + 4;
+  a.tickets = x->tickets;
+  a.shadow_hi = a.shadow_lo = nullptr;
+  a.ld_shadow = 0;
+  return a;
+}
+
+pcv_status launch_grad(pcv_ctx *x, GradArgs a) {
+  pcv_status s = ensure_ws(x, a.C, a.splits);
+  if (s != PCV_OK) return s;
+  a.ws = x->ws;
+  a.tickets = x->tickets;
+  CK(launch_grad_simt(x->pb, a, x->stream));
+  return PCV_OK;
+}
+
+// evaluate gradient, logp and shat at the current positions of a chain set
+pcv_status refresh(pcv_ctx *x, ChainBufs &cb) {
+  GradArgs a = grad_args(x, cb, false);
+  return launch_grad(x, a);
+}
+
+// one HMC transition for every chain of a set (Section 3.3)
+pcv_status launch_iteration(pcv_ctx *x, ChainBufs &cb, bool fd, bool accumulate) {
+  BeginArgs ba{};
+  ba.C = cb.C; ba.d = x->d; ba.ld = x->d_pad;
+  ba.seed = x->opt.seed;
+  ba.stream = fd ? ST_FD_MOM : ST_MOM;
+  ba.iter = fd ? &x->st->fd_iter : &x->st->iter;
+  ba.theta = cb.theta; ba.grad = cb.grad; ba.logp = cb.logp;
+  ba.theta_p = cb.theta_p; ba.r = cb.r; ba.H0 = cb.H0;
+  ba.eps = &x->st->eps; ba.minv = x->minv;
+  ba.r_given = nullptr;
+  k_begin<<<(cb.C + 7) / 8, 256, 0, x->stream>>>(ba);
+  CK(cudaGetLastError());
+  GradArgs ga = grad_args(x, cb, true);
+  for (int s = 1; s <= x->Lf; ++s) {
+    ga.mode = s < x->Lf ? MODE_KICK_DRIFT : MODE_LAST_KICK;
+    ga.need_ll = s == x->Lf;
+    pcv_status st = launch_grad(x, ga);
+    if (st != PCV_OK) return st;
+  }
+  AcceptArgs aa{};
+  aa.C = cb.C; aa.d = x->d; aa.ld = x->d_pad;
+  aa.seed = x->opt.seed;
+  aa.stream = fd ? ST_FD_ACC : ST_ACC;
+  aa.st = x->st;
+  aa.fd = fd ? 1 : 0;
+  aa.theta = cb.theta; aa.grad = cb.grad; aa.logp = cb.logp; aa.shat = cb.shat;
+  aa.theta_p = cb.theta_p; aa.r = cb.r; aa.grad_p = cb.grad_p;
+  aa.logp_p = cb.logp_p; aa.shat_p = cb.shat_p; aa.H0 = cb.H0;
+  aa.minv = x->minv;
+  aa.accumulate = accumulate ? 1 : 0;
+  aa.acc = x->acc;
+  aa.accept_prob = cb.accept_prob;
+  k_accept<<<(cb.C + 7) / 8, 256, 0, x->stream>>>(aa);
+  CK(cudaGetLastError());
+  if (fd) {
+    FdAdaptArgs fa{};
+    fa.st = x->st;
+    fa.n_adapt = x->fd_n_adapt;
+    fa.w0 = x->fd_n_adapt / 4;
+    fa.w1 = x->fd_n_adapt / 2;
+    fa.adapt_eps = !(x->opt.step_size > 0);
+    fa.adapt_mass = fa.adapt_eps && x->opt.inv_mass_diag == nullptr;
+    fa.C = cb.C; fa.d = x->d; fa.ld = x->d_pad;
+    fa.theta = cb.theta;
+    fa.accept_prob = cb.accept_prob;
+    fa.minv = x->minv;
+    fa.wmean = x->wmean; fa.wM2 = x->wM2;
+    fa.pool = x->pool;
+    fa.n_keep = x->n_fd_draws;
+    k_fd_adapt<<<1, 128, 0, x->stream>>>(fa);
+    CK(cudaGetLastError());
+  }
+  return PCV_OK;
+}
+
+// run `count` iterations, through a captured graph of `per_graph` iterations
+pcv_status run_iterations(pcv_ctx *x, ChainBufs &cb, bool fd, bool accumulate, long long count,
+                          cudaGraphExec_t *cache, int per_graph) {
+  if (count <= 0) return PCV_OK;
+  if (!x->opt.use_graphs) {
+    for (long long i = 0; i < count; ++i) {
+      pcv_status s = launch_iteration(x, cb, fd, accumulate);
+      if (s != PCV_OK) return s;
+    }
+    return PCV_OK;
+  }
+  // make sure workspaces exist before capture (no allocation inside a capture)
+  pcv_status s0 = ensure_ws(x, cb.C, splits_for(x, cb.C));
+  if (s0 != PCV_OK) return s0;
+  if (!*cache) {
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(x->stream, cudaStreamCaptureModeThreadLocal));
+    pcv_status s = PCV_OK;
+    for (int i = 0; i < per_graph && s == PCV_OK; ++i) s = launch_iteration(x, cb, fd, accumulate);
+    cudaError_t e = cudaStreamEndCapture(x->stream, &g);
+    if (s != PCV_OK) return s;
+    if (e != cudaSuccess) return fail_cuda(x, "cudaStreamEndCapture", e);
+    e = cudaGraphInstantiate(cache, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail_cuda(x, "cudaGraphInstantiate", e);
+  }
+  long long full = count / per_graph, rest = count - full * per_graph;
+  for (long long i = 0; i < full; ++i) CK(cudaGraphLaunch(*cache, x->stream));
+  for (long long i = 0; i < rest; ++i) {
+    pcv_status s = launch_iteration(x, cb, fd, accumulate);
+    if (s != PCV_OK) return s;
+  }
+  return PCV_OK;
+}
+
+pcv_status alloc_chains(pcv_ctx *x, ChainBufs &cb, int C, int L, int fold_base) {
+  cb.C = C; cb.L = L; cb.fold_base = fold_base;
+  const size_t n = (size_t)C * x->d_pad;
+  bool ok = dalloc_n(x, &cb.theta, n) && dalloc_n(x, &cb.grad, n) && dalloc_n(x, &cb.theta_p, n) &&
+            dalloc_n(x, &cb.r, n) && dalloc_n(x, &cb.grad_p, n) && dalloc_n(x, &cb.logp, (size_t)C) &&
+            dalloc_n(x, &cb.shat, (size_t)C) && dalloc_n(x, &cb.logp_p, (size_t)C) &&
+            dalloc_n(x, &cb.shat_p, (size_t)C) && dalloc_n(x, &cb.H0, (size_t)C) &&
+            dalloc_n(x, &cb.accept_prob, (size_t)C);
+  return ok ? PCV_OK : fail(x, PCV_E_OOM, "chain state allocation failed");
+}
+
+pcv_status alloc_accum(pcv_ctx *x) {
+  Accum &A = x->acc;
+  const size_t C = (size_t)x->C;
+  A.C = x->C; A.M = x->M; A.max_batches = x->max_batches; A.b = x->b;
+  bool ok = true;
+  double **scal[] = {&A.Ux, &A.Ux2, &A.Zx, &A.em, &A.emean, &A.eM2, &A.vm, &A.vmean, &A.vM2,
+                     &A.wmean, &A.wM2, &A.bmean_cur, &A.bM2_cur, &A.c0, &A.xsum};
+  for (double **pp : scal) ok = ok && dalloc_n(x, pp, C);
+  ok = ok && dalloc_n(x, &A.bmean, C * x->max_batches) && dalloc_n(x, &A.bM2, C * x->max_batches);
+  ok = ok && dalloc_n(x, &A.lagsum, C * (x->M + 1)) && dalloc_n(x, &A.first, C * std::max(1, x->M)) &&
+       dalloc_n(x, &A.ring, C * std::max(1, x->M));
+  ok = ok && dalloc_n(x, &A.div, C) && dalloc_n(x, &A.acc, C);
+  A.draw_cap = x->opt.store_draws > 0 ? x->opt.store_draws : 0;
+  A.draws = nullptr;
+  if (A.draw_cap > 0) ok = ok && dalloc_n(x, &A.draws, C * A.draw_cap);
+  if (!ok) return fail(x, PCV_E_OOM, "accumulator allocation failed");
+  // -inf initialisation of the log-space fields (A2 "initial entries -inf")
+  std::vector<double> ninf(C, -INFINITY);
+  for (double *p : {A.Ux, A.Ux2, A.Zx, A.em, A.vm})
+    CK(cudaMemcpyAsync(p, ninf.data(), C * sizeof(double), cudaMemcpyHostToDevice, x->stream));
+  CK(cudaStreamSynchronize(x->stream));
+  return PCV_OK;
+}
+
+// order the legacy default stream and the private stream (NULL stream option)
+void enter(pcv_ctx *x) {
+  if (x->own_stream) {
+    cudaEventRecord(x->ev_in, cudaStreamLegacy);
+    cudaStreamWaitEvent(x->stream, x->ev_in, 0);
+  }
+}
+void leave(pcv_ctx *x) {
+  if (x->own_stream) {
+    cudaEventRecord(x->ev_out, x->stream);
+    cudaStreamWaitEvent(cudaStreamLegacy, x->ev_out, 0);
+  }
+}
+
+pcv_status finalize(pcv_ctx *x) {
+  if (x->finalized) return PCV_OK;
+  if (x->n_sampled < 2LL * x->b)
+    return fail(x, PCV_E_BAD_STATE, "need at least two batches of draws (pcv_sample)");
+  k_finalize<<<(x->K + 127) / 128, 128, 0, x->stream>>>(x->acc, x->K, x->L, x->n_sampled,
+                                                          x->fold_out, x->fin_scratch);
+  CK(cudaGetLastError());
+  k_totals<<<1, 256, 0, x->stream>>>(x->fold_out, x->K, (double)x->L * x->n_sampled, x->tot_out);
+  CK(cudaGetLastError());
+  x->h_fold.resize((size_t)x->K * F_NFIELDS);
+  x->h_tot.resize(T_NFIELDS);
+  CK(cudaMemcpyAsync(x->h_fold.data(), x->fold_out, x->h_fold.size() * sizeof(double),
+                     cudaMemcpyDeviceToHost, x->stream));
+  CK(cudaMemcpyAsync(x->h_tot.data(), x->tot_out, x->h_tot.size() * sizeof(double),
+                     cudaMemcpyDeviceToHost, x->stream));
+  CK(cudaStreamSynchronize(x->stream));
+  x->finalized = true;
+  return PCV_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void pcv_default_options(pcv_options *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->seed = 0;
+  o->leapfrog_steps = 16;
+  o->step_size = -1.0;
+  o->inv_mass_diag = nullptr;
+  o->batch_size = 50;
+  o->hv_buffer = 0;
+  o->precision = PCV_FP32_SIMT;
+  o->cuda_stream = nullptr;
+  o->store_draws = 0;
+  o->acov_max_lag = 64;
+  o->max_batches = 1024;
+  o->n_fulldata_draws = 250;
+  o->init_scale = 1.0;
+  o->use_graphs = 1;
+}
+
+pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
+                      const int32_t *fold_assignment, int64_t N, int32_t p, int32_t chains_per_fold,
+                      const pcv_options *opt, pcv_ctx **out) {
+  if (!out) return PCV_E_INVALID_ARG;
+  *out = nullptr;
+  if (!model || !X || !y || !fold_assignment || !opt) return PCV_E_INVALID_ARG;
+  if (N < 1 || p < 1 || chains_per_fold < 2 || N > (int64_t)1 << 30) return PCV_E_INVALID_ARG;
+  if (opt->leapfrog_steps < 1 || opt->batch_size < 1 || opt->hv_buffer < 0 ||
+      opt->acov_max_lag < 0 || opt->max_batches < 1 || opt->n_fulldata_draws < 1)
+    return PCV_E_INVALID_ARG;
+  if (model->kind < PCV_GAUSS_LINEAR || model->kind > PCV_AR_GAUSS) return PCV_E_INVALID_ARG;
+  if (!(model->beta_prior_sd > 0)) return PCV_E_INVALID_ARG;
+
+  pcv_ctx *x = new pcv_ctx();
+  x->opt = *opt;
+  x->kind = model->kind;
+  x->N = N; x->p = p; x->L = chains_per_fold;
+  x->h = opt->hv_buffer; x->Lf = opt->leapfrog_steps; x->b = opt->batch_size;
+  x->M = opt->acov_max_lag; x->max_batches = opt->max_batches; x->n_fd_draws = opt->n_fulldata_draws;
+  auto bail = [&](pcv_status s, const std::string &m) {
+    // creation failed: release everything; report through a static message
+    static thread_local std::string last;
+    last = m;
+    free_all(x);
+    if (x->own_stream && x->stream) cudaStreamDestroy(x->stream);
+    delete x;
+    std::fprintf(stderr, "pcv_create: %s\n", last.c_str());
+    return s;
+  };
+  if (opt->precision != PCV_FP32_SIMT)
+    return bail(PCV_E_UNSUPPORTED, "tensor-core precisions are not available for this model/size");
+  // model variant and dimension
+  if (x->kind == PCV_LOGISTIC) { x->variant = MV_LOGISTIC; x->d = p; }
+  else if (x->kind == PCV_HIER_GAUSS) {
+    if (!model->group || model->n_groups < 1) return bail(PCV_E_INVALID_ARG, "HIER_GAUSS needs groups");
+    if (x->h > 0) return bail(PCV_E_UNSUPPORTED, "hv_buffer with HIER_GAUSS");
+    x->variant = MV_HIER; x->G = model->n_groups; x->d = p + x->G + 2;
+  } else if (x->kind == PCV_GAUSS_LINEAR && model->sigma_known > 0) {
+    x->variant = MV_GAUSS_KNOWN; x->d = p;
+  } else {
+    x->variant = MV_GAUSS_LOGSIG; x->d = p + 1;
+  }
+  if ((x->variant == MV_GAUSS_LOGSIG || x->variant == MV_HIER) && !(model->sigma_prior_sd > 0))
+    return bail(PCV_E_INVALID_ARG, "sigma_prior_sd must be > 0");
+  if (x->variant == MV_HIER && !(model->tau_prior_sd > 0)) return bail(PCV_E_INVALID_ARG, "tau_prior_sd must be > 0");
+  const int PP = simt_flat_pp(p);
+  if (PP < 0) return bail(PCV_E_UNSUPPORTED, "p > 32 needs a tensor-core precision");
+  x->p_pad = PP;
+  x->d_pad = (x->d + 3) / 4 * 4;
+
+  // data checks
+  for (int64_t i = 0; i < N * p; ++i)
+    if (!std::isfinite(X[i])) return bail(PCV_E_NUMERIC, "non-finite X");
+  for (int64_t i = 0; i < N; ++i) {
+    if (!std::isfinite(y[i])) return bail(PCV_E_NUMERIC, "non-finite y");
+    if (x->kind == PCV_LOGISTIC && y[i] != 0.0f && y[i] != 1.0f)
+      return bail(PCV_E_INVALID_ARG, "LOGISTIC needs y in {0, 1}");
+  }
+  int K = 0;
+  for (int64_t i = 0; i < N; ++i) {
+    const int f = fold_assignment[i];
+    if (f < -1) return bail(PCV_E_INVALID_ARG, "fold ids must be >= -1");
+    K = std::max(K, f + 1);
+  }
+  if (K < 1) return bail(PCV_E_INVALID_ARG, "no folds");
+  x->K = K;
+  x->C = K * x->L;
+  if (x->variant == MV_HIER)
+    for (int64_t i = 0; i < N; ++i)
+      if (model->group[i] < 0 || model->group[i] >= x->G) return bail(PCV_E_INVALID_ARG, "group id out of range");
+
+  // row order: sort by (fold, group) unless an h(v) buffer needs time order
+  x->perm.resize(N);
+  std::iota(x->perm.begin(), x->perm.end(), 0);
+  auto fkey = [&](int64_t i) { return fold_assignment[i] < 0 ? K : fold_assignment[i]; };
+  if (x->h == 0) {
+    std::stable_sort(x->perm.begin(), x->perm.end(), [&](int64_t a, int64_t b) {
+      const int fa = fkey(a), fb = fkey(b);
+      if (fa != fb) return fa < fb;
+      if (x->variant == MV_HIER) return model->group[a] < model->group[b];
+      return false;
+    });
+  }
+  std::vector<FoldDesc> fds(K + 1, FoldDesc{0, 0, 0, 0});
+  std::vector<int64_t> cnt(K, 0), lo(K, -1), hi(K, -1);
+  for (int64_t r = 0; r < N; ++r) {
+    const int f = fold_assignment[x->perm[r]];
+    if (f < 0) continue;
+    cnt[f]++;
+    if (lo[f] < 0) lo[f] = r;
+    hi[f] = r + 1;
+  }
+  for (int k = 0; k < K; ++k) {
+    if (cnt[k] == 0) return bail(PCV_E_INVALID_ARG, "fold " + std::to_string(k) + " has no test rows");
+    if (hi[k] - lo[k] != cnt[k])
+      return bail(PCV_E_INVALID_ARG, "fold " + std::to_string(k) + " test rows are not contiguous");
+    const int64_t elo = std::max<int64_t>(0, lo[k] - x->h), ehi = std::min<int64_t>(N, hi[k] + x->h);
+    if (N - (ehi - elo) < 1) return bail(PCV_E_INVALID_ARG, "fold " + std::to_string(k) + " has no training rows");
+    fds[k] = FoldDesc{(int)lo[k], (int)hi[k], (int)elo, (int)ehi};
+  }
+  // hierarchical segments: one contiguous row run per group
+  std::vector<int> seg_off, seg_grp, grp_seg;
+  if (x->variant == MV_HIER) {
+    grp_seg.assign(x->G, -1);
+    for (int64_t r = 0; r < N; ++r) {
+      const int g = model->group[x->perm[r]];
+      if (r == 0 || g != model->group[x->perm[r - 1]]) {
+        if (grp_seg[g] >= 0) return bail(PCV_E_UNSUPPORTED, "a group spans several folds");
+        grp_seg[g] = (int)seg_grp.size();
+        seg_grp.push_back(g);
+        seg_off.push_back((int)r);
+      }
+    }
+    seg_off.push_back((int)N);
+    for (int g = 0; g < x->G; ++g)
+      if (grp_seg[g] < 0) return bail(PCV_E_INVALID_ARG, "every group needs at least one row");
+  }
+
+  // stream and events
+  if (opt->cuda_stream) {
+    x->stream = (cudaStream_t)opt->cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&x->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return bail(PCV_E_CUDA, "cudaStreamCreate failed");
+    x->own_stream = true;
+  }
+  cudaEventCreateWithFlags(&x->ev_in, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&x->ev_out, cudaEventDisableTiming);
+  cudaEventCreate(&x->ev0);
+  cudaEventCreate(&x->ev1);
+  enter(x);
+
+  // device data
+  std::vector<float> hX((size_t)N * x->p_pad, 0.0f), hy(N);
+  for (int64_t r = 0; r < N; ++r) {
+    const int64_t i = x->perm[r];
+    std::memcpy(&hX[(size_t)r * x->p_pad], X + i * p, sizeof(float) * p);
+    hy[r] = y[i];
+  }
+  if (!dalloc_n(x, &x->X, hX.size()) || !dalloc_n(x, &x->y, (size_t)N) ||
+      !dalloc_n(x, &x->folds, (size_t)K + 1) || !dalloc_n(x, &x->minv, (size_t)x->d_pad) ||
+      !dalloc_n(x, &x->st, 1) || !dalloc_n(x, &x->wmean, (size_t)x->d) || !dalloc_n(x, &x->wM2, (size_t)x->d) ||
+      !dalloc_n(x, &x->pool, (size_t)x->n_fd_draws * kNumFdChains * x->d_pad) ||
+      !dalloc_n(x, &x->fold_out, (size_t)K * F_NFIELDS) || !dalloc_n(x, &x->tot_out, (size_t)T_NFIELDS) ||
+      !dalloc_n(x, &x->fin_scratch, (size_t)K * (4 * x->L + 2 * (x->M + 2))))
+    return bail(PCV_E_OOM, "device allocation failed");
+  cudaMemcpyAsync(x->X, hX.data(), hX.size() * sizeof(float), cudaMemcpyHostToDevice, x->stream);
+  cudaMemcpyAsync(x->y, hy.data(), hy.size() * sizeof(float), cudaMemcpyHostToDevice, x->stream);
+  cudaMemcpyAsync(x->folds, fds.data(), fds.size() * sizeof(FoldDesc), cudaMemcpyHostToDevice, x->stream);
+  std::vector<float> hm(x->d_pad, 1.0f);
+  if (opt->inv_mass_diag)
+    for (int j = 0; j < x->d; ++j) {
+      if (!(opt->inv_mass_diag[j] > 0)) return bail(PCV_E_INVALID_ARG, "inverse mass must be > 0");
+      hm[j] = (float)opt->inv_mass_diag[j];
+    }
+  cudaMemcpyAsync(x->minv, hm.data(), hm.size() * sizeof(float), cudaMemcpyHostToDevice, x->stream);
+  if (x->variant == MV_HIER) {
+    if (!dalloc_n(x, &x->seg_off, seg_off.size()) || !dalloc_n(x, &x->seg_grp, seg_grp.size()) ||
+        !dalloc_n(x, &x->grp_seg, grp_seg.size()))
+      return bail(PCV_E_OOM, "device allocation failed");
+    cudaMemcpyAsync(x->seg_off, seg_off.data(), seg_off.size() * sizeof(int), cudaMemcpyHostToDevice, x->stream);
+    cudaMemcpyAsync(x->seg_grp, seg_grp.data(), seg_grp.size() * sizeof(int), cudaMemcpyHostToDevice, x->stream);
+    cudaMemcpyAsync(x->grp_seg, grp_seg.data(), grp_seg.size() * sizeof(int), cudaMemcpyHostToDevice, x->stream);
+  }
+  IterState hst{};
+  hst.eps = opt->step_size > 0 ? (float)opt->step_size : 0.1f;
+  cudaMemcpyAsync(x->st, &hst, sizeof(hst), cudaMemcpyHostToDevice, x->stream);
+
+  Problem &pb = x->pb;
+  pb.variant = x->variant; pb.N = (int)N; pb.p = p; pb.p_pad = x->p_pad; pb.d = x->d; pb.d_pad = x->d_pad;
+  pb.G = x->G; pb.K = K; pb.X = x->X; pb.y = x->y; pb.grp_off = x->seg_off; pb.folds = x->folds;
+  pb.seg_grp = x->seg_grp; pb.grp_seg = x->grp_seg;
+  pb.beta_prec = (float)(1.0 / (model->beta_prior_sd * model->beta_prior_sd));
+  pb.log_beta_sd = (float)std::log(model->beta_prior_sd);
+  pb.sigma_known = (float)(model->sigma_known > 0 ? model->sigma_known : 1.0);
+  const double ssd = model->sigma_prior_sd > 0 ? model->sigma_prior_sd : 1.0;
+  const double tsd = model->tau_prior_sd > 0 ? model->tau_prior_sd : 1.0;
+  pb.sigma_prec = (float)(1.0 / (ssd * ssd));
+  pb.log_sigma_sd = (float)std::log(ssd);
+  pb.tau_prec = (float)(1.0 / (tsd * tsd));
+  pb.log_tau_sd = (float)std::log(tsd);
+
+  pcv_status s;
+  if ((s = alloc_chains(x, x->fold_cb, x->C, x->L, 0)) != PCV_OK) return bail(s, x->err);
+  if ((s = alloc_chains(x, x->fd_cb, kNumFdChains, kNumFdChains, K)) != PCV_OK) return bail(s, x->err);
+  if ((s = alloc_accum(x)) != PCV_OK) return bail(s, x->err);
+  if ((s = ensure_ws(x, x->C, splits_for(x, x->C))) != PCV_OK) return bail(s, x->err);
+  if ((s = ensure_ws(x, kNumFdChains, splits_for(x, kNumFdChains))) != PCV_OK) return bail(s, x->err);
+  if (cudaStreamSynchronize(x->stream) != cudaSuccess) return bail(PCV_E_CUDA, "upload failed");
+  leave(x);
+  *out = x;
+  return PCV_OK;
+}
+
+pcv_status pcv_warmup(pcv_ctx *x, int32_t n_fd, int32_t n_wu) {
+  if (!x) return PCV_E_INVALID_ARG;
+  if (x->state != ST_CREATED) return fail(x, PCV_E_BAD_STATE, "pcv_warmup may be called once, before sampling");
+  if (n_fd < 0 || n_wu < 0) return fail(x, PCV_E_INVALID_ARG, "negative iteration count");
+  enter(x);
+  const bool adapt = !(x->opt.step_size > 0);
+  const float eps0 = adapt ? 0.1f : (float)x->opt.step_size;
+  x->fd_n_adapt = n_fd;
+  k_fd_init_state<<<1, 1, 0, x->stream>>>(x->st, eps0, adapt ? 1 : 0);
+  CK(cudaGetLastError());
+  CK(cudaMemsetAsync(x->wmean, 0, sizeof(double) * x->d, x->stream));
+  CK(cudaMemsetAsync(x->wM2, 0, sizeof(double) * x->d, x->stream));
+  // full-data chains: init_scale * N(0, I) from stream ST_FD_INIT
+  {
+    const int nq = (x->d + 3) / 4;
+    const long long T = (long long)kNumFdChains * nq;
+    k_normals<<<(unsigned)((T + 255) / 256), 256, 0, x->stream>>>(
+        kNumFdChains, x->d, x->d_pad, x->opt.seed, 0u, ST_FD_INIT, (float)x->opt.init_scale, x->fd_cb.theta);
+    CK(cudaGetLastError());
+  }
+  pcv_status s = refresh(x, x->fd_cb);
+  if (s != PCV_OK) return s;
+  s = run_iterations(x, x->fd_cb, true, false, n_fd, &x->g_fd_1, 1);
+  if (s != PCV_OK) return s;
+  if (adapt && n_fd > 0) {
+    k_fd_final_eps<<<1, 1, 0, x->stream>>>(x->st);
+    CK(cudaGetLastError());
+  }
+  s = run_iterations(x, x->fd_cb, true, false, x->n_fd_draws, &x->g_fd_1, 1);
+  if (s != PCV_OK) return s;
+  // fold chains start from full-data draws (Algorithm 1)
+  {
+    const long long T = (long long)x->C * x->d;
+    k_init_from_pool<<<(unsigned)((T + 255) / 256), 256, 0, x->stream>>>(
+        x->C, x->d, x->d_pad, x->opt.seed, x->pool, x->n_fd_draws * kNumFdChains, x->fold_cb.theta);
+    CK(cudaGetLastError());
+  }
+  s = refresh(x, x->fold_cb);
+  if (s != PCV_OK) return s;
+  s = run_iterations(x, x->fold_cb, false, false, n_wu, &x->g_fold_1, 1);
+  if (s != PCV_OK) return s;
+  CK(cudaStreamSynchronize(x->stream));
+  leave(x);
+  x->state = ST_WARMED;
+  return PCV_OK;
+}
+
+pcv_status pcv_sample(pcv_ctx *x, int32_t n_draws) {
+  if (!x) return PCV_E_INVALID_ARG;
+  if (x->state == ST_CREATED) return fail(x, PCV_E_BAD_STATE, "pcv_sample before pcv_warmup / pcv_set_positions");
+  if (n_draws <= 0 || n_draws % x->b != 0)
+    return fail(x, PCV_E_INVALID_ARG, "n_draws must be a positive multiple of batch_size");
+  if ((x->n_sampled + n_draws) / x->b > x->max_batches)
+    return fail(x, PCV_E_INVALID_ARG, "more batches than max_batches");
+  enter(x);
+  CK(cudaEventRecord(x->ev0, x->stream));
+  pcv_status s = run_iterations(x, x->fold_cb, false, true, n_draws, &x->g_sample_b, x->b);
+  if (s != PCV_OK) return s;
+  CK(cudaEventRecord(x->ev1, x->stream));
+  CK(cudaEventSynchronize(x->ev1));
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, x->ev0, x->ev1);
+  x->last_ms = ms;
+  x->n_sampled += n_draws;
+  x->finalized = false;
+  x->state = ST_SAMPLED;
+  leave(x);
+  return PCV_OK;
+}
+
+pcv_status pcv_scores(pcv_ctx *x, double *elpd_k, double *mcse_k, double *elpd_total, double *mcse_total,
+                      double *se_epistemic) {
+  if (!x) return PCV_E_INVALID_ARG;
+  if (x->state != ST_SAMPLED) return fail(x, PCV_E_BAD_STATE, "pcv_scores before pcv_sample");
+  pcv_status s = finalize(x);
+  if (s != PCV_OK) return s;
+  for (int k = 0; k < x->K; ++k) {
+    if (elpd_k) elpd_k[k] = x->h_fold[(size_t)k * F_NFIELDS + F_ELPD];
+    if (mcse_k) mcse_k[k] = x->h_fold[(size_t)k * F_NFIELDS + F_MCSE];
+  }
+  if (elpd_total) *elpd_total = x->h_tot[T_ELPD];
+  if (mcse_total) *mcse_total = x->h_tot[T_MCSE];
+  if (se_epistemic) *se_epistemic = x->h_tot[T_SEEPI];
+  return PCV_OK;
+}
+
+pcv_status pcv_diagnostics(pcv_ctx *x, double *rhat_k, double *split_rhat_k, double *ess_bm_k,
+                           double *ess_acov_k, int64_t *divergences_k, double *rhat_max, double *ess_total) {
+  if (!x) return PCV_E_INVALID_ARG;
+  if (x->state != ST_SAMPLED) return fail(x, PCV_E_BAD_STATE, "pcv_diagnostics before pcv_sample");
+  pcv_status s = finalize(x);
+  if (s != PCV_OK) return s;
+  for (int k = 0; k < x->K; ++k) {
+    const double *o = &x->h_fold[(size_t)k * F_NFIELDS];
+    if (rhat_k) rhat_k[k] = o[F_RHAT];
+    if (split_rhat_k) split_rhat_k[k] = o[F_SRHAT];
+    if (ess_bm_k) ess_bm_k[k] = o[F_ESSBM];
+    if (ess_acov_k) ess_acov_k[k] = o[F_ESSAC];
+    if (divergences_k) divergences_k[k] = (int64_t)o[F_DIV];
+  }
+  if (rhat_max) *rhat_max = x->h_tot[T_RHATMAX];
+  if (ess_total) *ess_total = x->h_tot[T_ESSTOT];
+  return PCV_OK;
+}
+
+int32_t pcv_num_folds(const pcv_ctx *x) { return x ? x->K : -1; }
+int32_t pcv_num_chains(const pcv_ctx *x) { return x ? x->C : -1; }
+int32_t pcv_dim(const pcv_ctx *x) { return x ? x->d : -1; }
+const char *pcv_last_error(const pcv_ctx *x) { return x ? x->err.c_str() : "null context"; }
+
+void pcv_destroy(pcv_ctx *x) {
+  if (!x) return;
+  free_all(x);
+  for (cudaGraphExec_t g : {x->g_sample_b, x->g_fold_1, x->g_fd_1})
+    if (g) cudaGraphExecDestroy(g);
+  for (cudaEvent_t e : {x->ev_in, x->ev_out, x->ev0, x->ev1})
+    if (e) cudaEventDestroy(e);
+  if (x->own_stream && x->stream) cudaStreamDestroy(x->stream);
+  delete x;
+}
+
+pcv_status pcv_set_positions(pcv_ctx *x, const double *theta, double step_size, const double *inv_mass) {
+  if (!x || !theta) return fail(x, PCV_E_INVALID_ARG, "null argument");
+  if (x->state == ST_SAMPLED) return fail(x, PCV_E_BAD_STATE, "positions cannot be reset after sampling");
+  enter(x);
+  std::vector<float> h((size_t)x->C * x->d_pad, 0.0f);
+  for (int c = 0; c < x->C; ++c)
+    for (int j = 0; j < x->d; ++j) {
+      const double v = theta[(size_t)c * x->d + j];
+      if (!std::isfinite(v)) return fail(x, PCV_E_NUMERIC, "non-finite position");
+      h[(size_t)c * x->d_pad + j] = (float)v;
+    }
+  CK(cudaMemcpyAsync(x->fold_cb.theta, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, x->stream));
+  if (step_size > 0) {
+    const float e = (float)step_size;
+    CK(cudaMemcpyAsync(&x->st->eps, &e, sizeof(float), cudaMemcpyHostToDevice, x->stream));
+  }
+  if (inv_mass) {
+    std::vector<float> hm(x->d_pad, 1.0f);
+    for (int j = 0; j < x->d; ++j) {
+      if (!(inv_mass[j] > 0)) return fail(x, PCV_E_INVALID_ARG, "inverse mass must be > 0");
+      hm[j] = (float)inv_mass[j];
+    }
+    CK(cudaMemcpyAsync(x->minv, hm.data(), hm.size() * sizeof(float), cudaMemcpyHostToDevice, x->stream));
+  }
+  pcv_status s = refresh(x, x->fold_cb);
+  if (s != PCV_OK) return s;
+  CK(cudaStreamSynchronize(x->stream));
+  leave(x);
+  x->state = ST_WARMED;
+  return PCV_OK;
+}
+
+pcv_status pcv_get_positions(pcv_ctx *x, double *theta, double *logp, double *shat) {
+  if (!x) return PCV_E_INVALID_ARG;
+  enter(x);
+  std::vector<float> h((size_t)x->C * x->d_pad);
+  std::vector<double> lp(x->C), sh(x->C);
+  CK(cudaMemcpyAsync(h.data(), x->fold_cb.theta, h.size() * sizeof(float), cudaMemcpyDeviceToHost, x->stream));
+  CK(cudaMemcpyAsync(lp.data(), x->fold_cb.logp, lp.size() * sizeof(double), cudaMemcpyDeviceToHost, x->stream));
+  CK(cudaMemcpyAsync(sh.data(), x->fold_cb.shat, sh.size() * sizeof(double), cudaMemcpyDeviceToHost, x->stream));
+  CK(cudaStreamSynchronize(x->stream));
+  leave(x);
+  for (int c = 0; c < x->C; ++c) {
+    if (theta)
+      for (int j = 0; j < x->d; ++j) theta[(size_t)c * x->d + j] = h[(size_t)c * x->d_pad + j];
+    if (logp) logp[c] = lp[c];
+    if (shat) shat[c] = sh[c];
+  }
+  return PCV_OK;
+}
+
+pcv_status pcv_get_adaptation(pcv_ctx *x, double *step_size, double *inv_mass) {
+  if (!x) return PCV_E_INVALID_ARG;
+  enter(x);
+  IterState hs;
+  std::vector<float> hm(x->d_pad);
+  CK(cudaMemcpyAsync(&hs, x->st, sizeof(hs), cudaMemcpyDeviceToHost, x->stream));
+  CK(cudaMemcpyAsync(hm.data(), x->minv, hm.size() * sizeof(float), cudaMemcpyDeviceToHost, x->stream));
+  CK(cudaStreamSynchronize(x->stream));
+  leave(x);
+  if (step_size) *step_size = hs.eps;
+  if (inv_mass)
+    for (int j = 0; j < x->d; ++j) inv_mass[j] = hm[j];
+  return PCV_OK;
+}
+
+pcv_status pcv_log_density(pcv_ctx *x, const float *theta, const int32_t *fold, int32_t n, int32_t precision,
+                           double *logp, float *grad, double *shat) {
+  if (!x) return PCV_E_INVALID_ARG;
+  if (!theta || !fold || !logp || !grad || !shat || n < 1) return fail(x, PCV_E_INVALID_ARG, "bad argument");
+  if (precision != PCV_FP32_SIMT) return fail(x, PCV_E_UNSUPPORTED, "precision not available for this context");
+  enter(x);
+  ChainBufs cb;
+  cb.C = n; cb.L = 1; cb.fold_base = 0;
+  GradArgs a = grad_args(x, cb, false);
+  a.fold_of = fold;
+  a.theta = theta; a.ld_theta = x->d;
+  a.grad = grad; a.ld_grad = x->d;
+  a.logp = logp; a.shat = shat;
+  a.need_ll = 1;
+  a.mode = MODE_NONE;
+  a.r = nullptr;
+  pcv_status s = launch_grad(x, a);
+  if (s != PCV_OK) return s;
+  leave(x);
+  return PCV_OK;
+}
+
+pcv_status pcv_trajectory(pcv_ctx *x, const float *theta0, const float *r0, int32_t precision, float *theta1,
+                          float *r1, double *logp1, double *shat1) {
+  if (!x) return PCV_E_INVALID_ARG;
+  if (!theta0 || !r0 || !theta1 || !r1 || !logp1 || !shat1) return fail(x, PCV_E_INVALID_ARG, "null argument");
+  if (precision != PCV_FP32_SIMT) return fail(x, PCV_E_UNSUPPORTED, "precision not available for this context");
+  enter(x);
+  if (!x->traj_cb.theta) {
+    pcv_status s = alloc_chains(x, x->traj_cb, x->C, x->L, 0);
+    if (s != PCV_OK) return s;
+  }
+  ChainBufs &cb = x->traj_cb;
+  float *rstart;
+  if (!dalloc_n(x, &rstart, (size_t)x->C * x->d_pad)) return fail(x, PCV_E_OOM, "allocation failed");
+  const size_t row = sizeof(float) * x->d, pitch = sizeof(float) * x->d_pad;
+  CK(cudaMemcpy2DAsync(cb.theta, pitch, theta0, row, row, x->C, cudaMemcpyDeviceToDevice, x->stream));
+  CK(cudaMemcpy2DAsync(rstart, pitch, r0, row, row, x->C, cudaMemcpyDeviceToDevice, x->stream));
+  pcv_status s = refresh(x, cb);
+  if (s != PCV_OK) return s;
+  BeginArgs ba{};
+  ba.C = cb.C; ba.d = x->d; ba.ld = x->d_pad;
+  ba.seed = x->opt.seed; ba.stream = ST_MOM; ba.iter = &x->st->iter;
+  ba.theta = cb.theta; ba.grad = cb.grad; ba.logp = cb.logp;
+  ba.theta_p = cb.theta_p; ba.r = cb.r; ba.H0 = cb.H0;
+  ba.eps = &x->st->eps; ba.minv = x->minv; ba.r_given = rstart;
+  k_begin<<<(cb.C + 7) / 8, 256, 0, x->stream>>>(ba);
+  CK(cudaGetLastError());
+  GradArgs ga = grad_args(x, cb, true);
+  for (int st = 1; st <= x->Lf; ++st) {
+    ga.mode = st < x->Lf ? MODE_KICK_DRIFT : MODE_LAST_KICK;
+    ga.need_ll = st == x->Lf;
+    s = launch_grad(x, ga);
+    if (s != PCV_OK) return s;
+  }
+  CK(cudaMemcpy2DAsync(theta1, row, cb.theta_p, pitch, row, x->C, cudaMemcpyDeviceToDevice, x->stream));
+  CK(cudaMemcpy2DAsync(r1, row, cb.r, pitch, row, x->C, cudaMemcpyDeviceToDevice, x->stream));
+  CK(cudaMemcpyAsync(logp1, cb.logp_p, sizeof(double) * x->C, cudaMemcpyDeviceToDevice, x->stream));
+  CK(cudaMemcpyAsync(shat1, cb.shat_p, sizeof(double) * x->C, cudaMemcpyDeviceToDevice, x->stream));
+  CK(cudaStreamSynchronize(x->stream));
+  leave(x);
+  return PCV_OK;
+}
+
+pcv_status pcv_draw_normals(pcv_ctx *x, uint32_t iteration, uint32_t stream, float *out) {
+  if (!x) return PCV_E_INVALID_ARG;
+  if (!out) return fail(x, PCV_E_INVALID_ARG, "null argument");
+  enter(x);
+  const int nq = (x->d + 3) / 4;
+  const long long T = (long long)x->C * nq;
+  k_normals<<<(unsigned)((T + 255) / 256), 256, 0, x->stream>>>(x->C, x->d, x->d, x->opt.seed, iteration,
+                                                                stream, 1.0f, out);
+  CK(cudaGetLastError());
+  leave(x);
+  return PCV_OK;
+}
+
+pcv_status pcv_accumulate(pcv_ctx *x, const double *shat, int32_t n) {
+  if (!x) return PCV_E_INVALID_ARG;
+  if (!shat || n <= 0 || n % x->b != 0) return fail(x, PCV_E_INVALID_ARG, "n must be a positive multiple of batch_size");
+  if (x->state == ST_CREATED) return fail(x, PCV_E_BAD_STATE, "accumulate before positions are set");
+  if ((x->n_sampled + n) / x->b > x->max_batches) return fail(x, PCV_E_INVALID_ARG, "more batches than max_batches");
+  enter(x);
+  k_accumulate_given<<<(x->C + 7) / 8, 256, 0, x->stream>>>(x->acc, shat, n, x->n_sampled);
+  CK(cudaGetLastError());
+  x->n_sampled += n;
+  const long long nd = x->n_sampled;
+  CK(cudaMemcpyAsync(&x->st->n_draws, &nd, sizeof(nd), cudaMemcpyHostToDevice, x->stream));
+  CK(cudaStreamSynchronize(x->stream));
+  leave(x);
+  x->finalized = false;
+  x->state = ST_SAMPLED;
+  return PCV_OK;
+}
+
+pcv_status pcv_get_draws(pcv_ctx *x, double *shat, int32_t *n_stored) {
+  if (!x) return PCV_E_INVALID_ARG;
+  if (!x->acc.draws) return fail(x, PCV_E_BAD_STATE, "store_draws was not enabled");
+  const int n = (int)std::min<long long>(x->n_sampled, x->acc.draw_cap);
+  if (n_stored) *n_stored = n;
+  if (!shat) return PCV_OK;
+  enter(x);
+  std::vector<double> h((size_t)x->C * x->acc.draw_cap);
+  CK(cudaMemcpyAsync(h.data(), x->acc.draws, h.size() * sizeof(double), cudaMemcpyDeviceToHost, x->stream));
+  CK(cudaStreamSynchronize(x->stream));
+  leave(x);
+  for (int c = 0; c < x->C; ++c)
+    std::memcpy(shat + (size_t)c * n, &h[(size_t)c * x->acc.draw_cap], sizeof(double) * n);
+  return PCV_OK;
+}
+
+pcv_status pcv_accept_rate(pcv_ctx *x, double *accept_k) {
+  if (!x || !accept_k) return fail(x, PCV_E_INVALID_ARG, "null argument");
+  if (x->state != ST_SAMPLED) return fail(x, PCV_E_BAD_STATE, "no draws yet");
+  pcv_status s = finalize(x);
+  if (s != PCV_OK) return s;
+  for (int k = 0; k < x->K; ++k) accept_k[k] = x->h_fold[(size_t)k * F_NFIELDS + F_ACCRATE];
+  return PCV_OK;
+}
+
+pcv_status pcv_time_leapfrog_kernel(pcv_ctx *x, int32_t reps, double *ms_per_launch) {
+  if (!x || !ms_per_launch || reps < 1) return fail(x, PCV_E_INVALID_ARG, "bad argument");
+  if (x->state == ST_CREATED) return fail(x, PCV_E_BAD_STATE, "positions not set");
+  enter(x);
+  ChainBufs &cb = x->fold_cb;
+  const size_t n = sizeof(float) * (size_t)cb.C * x->d_pad;
+  CK(cudaMemcpyAsync(cb.theta_p, cb.theta, n, cudaMemcpyDeviceToDevice, x->stream));
+  CK(cudaMemsetAsync(cb.r, 0, n, x->stream));
+  GradArgs ga = grad_args(x, cb, true);
+  ga.mode = MODE_KICK_DRIFT;
+  ga.need_ll = 0;
+  pcv_status s = launch_grad(x, ga);                      // warm-up launch
+  if (s != PCV_OK) return s;
+  CK(cudaEventRecord(x->ev0, x->stream));
+  for (int i = 0; i < reps; ++i) {
+    s = launch_grad(x, ga);
+    if (s != PCV_OK) return s;
+  }
+  CK(cudaEventRecord(x->ev1, x->stream));
+  CK(cudaEventSynchronize(x->ev1));
+  float ms = 0.0f;
+  CK(cudaEventElapsedTime(&ms, x->ev0, x->ev1));
+  *ms_per_launch = ms / reps;
+  leave(x);
+  return PCV_OK;
+}
+
+pcv_status pcv_last_sample_ms(pcv_ctx *x, double *ms) {
+  if (!x || !ms) return PCV_E_INVALID_ARG;
+  *ms = x->last_ms;
+  return PCV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,253 @@
+// pcv_internal.cuh -- device-side data layout and helpers shared by the PCV
+// kernels (sm_103a).  Product code: nothing here is shared with the oracle.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace pcv {
+
+// model variants the kernels are specialised on
+enum ModelVariant : int {
+  MV_GAUSS_KNOWN = 0,   // Gaussian, sigma known
+  MV_GAUSS_LOGSIG = 1,  // Gaussian (linear or AR design), log sigma sampled
+  MV_LOGISTIC = 2,
+  MV_HIER = 3           // varying intercept tau*z_g, log tau, log sigma
+};
+
+// Philox stream tags (the counter's last word)
+enum Stream : uint32_t {
+  ST_MOM = 0, ST_ACC = 1, ST_INIT = 2, ST_FD_MOM = 16, ST_FD_ACC = 17, ST_FD_INIT = 18
+};
+
+// Row ranges of one fold in the library's sorted row order (the Appendix B
+// masks restated as ranges): test rows [test_lo, test_hi); training rows are
+// the rows outside [excl_lo, excl_hi) (the test block widened by the h(v)-block
+// buffer).  The full-data pseudo-fold (id K) has empty ranges.
+struct FoldDesc {
+  int test_lo, test_hi, excl_lo, excl_hi;
+};
+
+// Device view of the data (rows sorted so that test blocks and groups are
+// contiguous).
+struct Problem {
+  int variant;            // ModelVariant
+  int N;                  // rows
+  int p;                  // regressors
+  int p_pad;              // row stride of X (multiple of 4)
+  int d;                  // dimension of theta
+  int d_pad;              // row stride of chain vectors (multiple of 4)
+  int G;                  // groups (HIER)
+  int K;                  // folds; fold id K is the full data set
+  const float *X;         // N x p_pad, zero padded columns
+  const float *y;         // N
+  const int *grp_off;     // G + 1 row offsets of the group segments (HIER)
+  const int *seg_grp;     // G: group id of each segment (HIER)
+  const int *grp_seg;     // G: segment of each group (HIER)
+  const FoldDesc *folds;  // K + 1
+  float beta_prec;        // 1 / beta_prior_sd^2
+  float log_beta_sd;
+  float sigma_known;      // GAUSS_KNOWN
+  float sigma_prec;       // 1 / sigma_prior_sd^2
+  float log_sigma_sd;
+  float tau_prec;         // 1 / tau_prior_sd^2
+  float log_tau_sd;
+};
+
+enum { MODE_NONE = 0, MODE_KICK_DRIFT = 1, MODE_LAST_KICK = 2 };
+
+// Arguments of one gradient evaluation (optionally fused with a leapfrog
+// update) for a batch of chain positions.
+struct GradArgs {
+  int C;                  // positions
+  int L;                  // chains per fold (fold = fold_base + c / L) if fold_of == nullptr
+  int fold_base;
+  const int *fold_of;     // optional explicit fold per position
+  const float *theta;     // C x ld_theta (read; updated in place by MODE_KICK_DRIFT)
+  int ld_theta;
+  float *grad;            // C x ld_grad (out)
+  int ld_grad;
+  double *logp;           // C (out) when need_ll
+  double *shat;           // C (out) when need_ll
+  int need_ll;
+  int mode;               // MODE_NONE, MODE_KICK_DRIFT, MODE_LAST_KICK
+  float *r;               // C x ld_theta momenta (updated by the modes)
+  const float *eps;       // device scalar step size
+  const float *minv;      // inverse mass diagonal (d_pad)
+  // split-N cross-CTA combine
+  int splits;             // row splits per chain tile
+  float *ws;              // workspace: tiles x splits x 32 x ws_stride floats
+  int ws_stride;
+  unsigned int *tickets;  // one per chain tile, zero between launches
+  // bf16 hi/lo shadow of theta for the tensor-core path (written by updates)
+  __nv_bfloat16 *shadow_hi, *shadow_lo;
+  int ld_shadow;
+};
+
+// Per-chain online accumulator state, structure of arrays, FP64.
+struct Accum {
+  int C;
+  int M;                  // autocovariance lag cap (0 = off)
+  int max_batches;
+  int b;                  // batch size
+  double *Ux, *Ux2, *Zx;  // log-sum-exp of s, of 2 s, and of s in the current batch
+  double *em, *emean, *eM2;   // log-shifted Welford of exp(s) over draws
+  double *vm, *vmean, *vM2;   // log-shifted Welford of batch means
+  double *wmean, *wM2;        // Welford of s over draws
+  double *bmean_cur, *bM2_cur;// Welford of s in the current batch
+  double *bmean, *bM2;        // per closed batch [max_batches x C]
+  double *c0, *xsum;          // acov centring constant (first draw), sum of x
+  double *lagsum;             // [(M+1) x C]
+  double *first;              // [M x C]
+  double *ring;               // [M x C]
+  long long *div, *acc;       // divergences, accepts (sampling only)
+  double *draws;              // optional stored draws [C x draw_cap]
+  int draw_cap;
+};
+
+// Iteration counters and adaptation state kept in device memory so that
+// CUDA graph replays need no parameter updates.
+struct IterState {
+  unsigned int iter;        // fold-chain Philox iteration counter
+  unsigned int fd_iter;     // full-data iteration counter
+  long long n_draws;        // draws accumulated so far
+  unsigned int ticket;      // last-block election in the accept kernel
+  unsigned int error;       // device error flags
+  float eps;                // step size used by the kernels
+  float pad0;
+  double da_mu, da_hbar, da_logeps, da_logeps_bar;
+  long long da_t;
+  double mass_n;            // Welford count of the mass window
+};
+
+// Philox4x32-10 (Salmon et al., SC 2011): 10 rounds of the 4x32 bijection,
+// key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    if (i) { k.x += 0x9E3779B9u; k.y += 0xBB67AE85u; }
+    const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+    uint32_t hi0 = __umulhi(m0, c.x), lo0 = m0 * c.x;
+    uint32_t hi1 = __umulhi(m1, c.z), lo1 = m1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint4 philox_at(unsigned long long seed, uint32_t block, uint32_t chain,
+                                           uint32_t iter, uint32_t stream) {
+  return philox4x32_10(make_uint4(block, chain, iter, stream),
+                       make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+__device__ __forceinline__ double unit_from_word(uint32_t a) {
+  return ((double)a + 0.5) * 2.3283064365386963e-10;
+}
+
+// Box-Muller on two words: (sqrt(-2 ln u1) cos 2 pi u2, sqrt(-2 ln u1) sin 2 pi u2),
+// u = (w + 1/2) 2^-32 in (0, 1).
+__device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b) {
+  const double u1 = unit_from_word(a);
+  const float u2 = (float)unit_from_word(b);
+  const float rad = (float)sqrt(-2.0 * log(u1));
+  float s, c;
+  sincospif(2.0f * u2, &s, &c);
+  return make_float2(rad * c, rad * s);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ int fold_of_chain(const GradArgs &a, int c) {
+  return a.fold_of ? a.fold_of[c] : a.fold_base + c / a.L;
+}
+
+// log(1 + e^x) without overflow
+__device__ __forceinline__ float softplusf(float x) {
+  return fmaxf(x, 0.0f) + log1pf(__expf(-fabsf(x)));
+}
+
+constexpr float kLog2Pi = 1.8378770664093453f;
+constexpr double kLog2PiD = 1.8378770664093454835606594728112;
+constexpr double kLog2D = 0.69314718055994530942;
+
+// launchers (k_grad_simt.cu)
+int simt_flat_pp(int p);
+size_t hier_smem_bytes(int PP, int G, int splits);
+cudaError_t launch_grad_simt(const Problem &pb, const GradArgs &a, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// per-chain HMC kernels (k_hmc.cu)
+// ---------------------------------------------------------------------------
+struct BeginArgs {
+  int C, d, ld;
+  unsigned long long seed;
+  unsigned int stream;
+  const unsigned int *iter;     // device iteration counter
+  const float *theta, *grad;    // current state
+  const double *logp;
+  float *theta_p, *r;           // proposal position and momentum (out)
+  double *H0;                   // out
+  const float *eps, *minv;
+  const float *r_given;         // optional start momenta instead of drawing (C x ld)
+  __nv_bfloat16 *shadow_hi, *shadow_lo;
+  int ld_shadow;
+};
+
+struct AcceptArgs {
+  int C, d, ld;
+  unsigned long long seed;
+  unsigned int stream;
+  IterState *st;
+  int fd;                          // 1: full-data chains (fd_iter counter)
+  float *theta, *grad;
+  double *logp, *shat;
+  const float *theta_p, *r, *grad_p;
+  const double *logp_p, *shat_p, *H0;
+  const float *minv;
+  int accumulate;                  // 1: sampling phase
+  Accum acc;
+  double *accept_prob;             // per chain, or null
+};
+
+struct FdAdaptArgs {
+  IterState *st;
+  int n_adapt, w0, w1;
+  int adapt_eps, adapt_mass;
+  int C, d, ld;
+  const float *theta;
+  const double *accept_prob;
+  float *minv;
+  double *wmean, *wM2;        // d each
+  float *pool;                // n_keep*C x ld
+  int n_keep;
+};
+
+enum { F_ELPD, F_MCSE, F_SIG2BM, F_S2, F_ESSBM, F_RHAT, F_SRHAT, F_ESSAC, F_DIV, F_ACTRUNC,
+       F_ACCRATE, F_NFIELDS };
+enum { T_ELPD, T_MCSE, T_SEEPI, T_RHATMAX, T_ESSTOT, T_SRHATMAX, T_DIV, T_NFIELDS };
+
+__global__ void k_begin(BeginArgs a);
+__global__ void k_normals(int C, int d, int ld, unsigned long long seed, unsigned int iter,
+                          unsigned int stream, float scale, float *out);
+__global__ void k_init_from_pool(int C, int d, int ld, unsigned long long seed, const float *pool,
+                                 int n_pool, float *theta);
+__global__ void k_shadow(int C, int d, int ld, const float *theta, __nv_bfloat16 *hi,
+                         __nv_bfloat16 *lo, int ld_shadow);
+__global__ void k_accept(AcceptArgs a);
+__global__ void k_accumulate_given(Accum A, const double *s, int n, long long n0);
+__global__ void k_fd_adapt(FdAdaptArgs a);
+__global__ void k_fd_init_state(IterState *st, float eps0, int adapt);
+__global__ void k_fd_final_eps(IterState *st);
+__global__ void k_finalize(Accum A, int K, int L, long long n, double *out, double *scratch);
+__global__ void k_totals(const double *fo, int K, double Ln, double *tot);
+
+}  // namespace pcv

@@ -98,6 +98,12 @@ def round_to_bf16(a: np.ndarray) -> np.ndarray:
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
+def _fp32(a: np.ndarray) -> np.ndarray:
+    """Values representable in float32 (the library stores X and y in FP32),
+    kept as float64 so the FP64 oracle reads exactly the GPU's inputs."""
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
 def _sigmoid(x):
     return 1.0 / (1.0 + np.exp(-x))
 
@@ -112,6 +118,7 @@ def gauss_blocks(N: int = 200, p: int = 5, K: int = 10, L: int = 4,
     beta = g.standard_normal(p)
     y = X @ beta + g.standard_normal(N)
     fold = (np.arange(N) * K // N).astype(np.int32)
+    X, y = _fp32(X), _fp32(y)
     return Workload("gauss_blocks", GAUSS_LINEAR, X, y, fold, K, L,
                     beta_prior_sd=10.0, sigma_known=1.0, leapfrog_steps=16,
                     step_size=0.05, n_fulldata_warmup=500, n_fold_warmup=500,
@@ -130,6 +137,7 @@ def logistic_loo(N: int = 2000, p: int = 20, L: int = 8, seed: int = 1002,
     K = N if K is None else K
     fold = np.full(N, -1, np.int32)
     fold[:K] = np.arange(K, dtype=np.int32)
+    X = _fp32(X)
     return Workload("logistic_loo", LOGISTIC, X, y, fold, K, L,
                     beta_prior_sd=2.5, n_fulldata_warmup=500, n_fold_warmup=500,
                     n_draws=1000, seed=2002, truth={"beta": beta})
@@ -150,6 +158,7 @@ def hier_logo(G: int = 100, p: int = 10, L: int = 16, mean_extra: float = 30.0,
     sigma = abs(g.standard_normal())
     z = g.standard_normal(G)
     y = X @ beta + tau * z[group] + sigma * g.standard_normal(N)
+    X, y = _fp32(X), _fp32(y)
     return Workload("hier_logo", HIER_GAUSS, X, y, group.copy(), G, L,
                     beta_prior_sd=1.0, sigma_prior_sd=1.0, tau_prior_sd=1.0,
                     group=group, n_groups=G, n_fulldata_warmup=500,
@@ -183,6 +192,7 @@ def ar2_hvblock(T: int = 5000, K: int = 250, v: int = 10, h: int = 10,
         hi = min(lo + v, N)
         if lo < N:
             fold[lo:hi] = k
+    X, y = _fp32(X), _fp32(y)
     return Workload("ar2_hvblock", AR_GAUSS, X, y, fold, K, L,
                     beta_prior_sd=1.0, sigma_known=-1.0, sigma_prior_sd=1.0,
                     hv_buffer=h, n_fulldata_warmup=500, n_fold_warmup=500,
