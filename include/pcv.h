@@ -265,6 +265,31 @@ pcv_status pcv_last_sample_ms(pcv_ctx *ctx, double *ms);
  */
 pcv_status pcv_time_leapfrog_kernel(pcv_ctx *ctx, int32_t reps, double *ms_per_launch);
 
+/*
+ * Allocation-free variant of pcv_log_density (the paper has no counterpart;
+ * it exists for callers that may not allocate device memory while they run:
+ * a process whose GPU memory belongs to another framework's pool, or a
+ * latency-bound loop where cudaMalloc could block or synchronise the device).
+ * Same arguments, layout and results as pcv_log_density, but the kernels'
+ * split-N partial sums and tickets use fixed device arrays compiled into the
+ * library (16 MiB of FP32 scratch and 8192 tickets; every GPU that loads the
+ * library holds them until the process exits) instead of the context's
+ * workspace, so the call itself allocates nothing.
+ *   - Limit: ceil(n / 32) <= 8192 and ceil(n / 32) * 32 * (dim rounded up to
+ *     a multiple of 4, at least the kernel width, plus 4) <= 4 Mi floats;
+ *     larger n returns PCV_E_INVALID_ARG with a message naming the limit.
+ *   - The first call on a device looks up the arrays' device addresses
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the arrays, which keep the previous call's contents
+ *     (the tickets are cleared at the start of each call): calls that can
+ *     overlap on the GPU, from any context or stream, race and must be
+ *     serialised by the caller.
+ */
+pcv_status pcv_log_density_noalloc(pcv_ctx *ctx, const float *theta, const int32_t *fold,
+                                   int32_t n, int32_t precision, double *logp, float *grad,
+                                   double *shat);
+
 #ifdef __cplusplus
 }
 #endif

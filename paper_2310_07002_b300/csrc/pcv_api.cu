@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -911,3 +912,94 @@ pcv_status pcv_last_sample_ms(pcv_ctx *x, double *ms) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free gradient evaluation.
+//
+// Some callers must not allocate device memory at call time: a process that
+// hands the GPU's memory to another framework's pool, or a latency-bound
+// serving loop where cudaMalloc could stall or synchronise the device at an
+// unpredictable moment.  For them the split-N workspace and tickets of the
+// gradient kernels live in fixed file-scope device arrays instead of the
+// context's (growable) workspace.  Every GPU that loads this library keeps
+// these arrays (kNoAllocScratchFloats floats = 16 MiB, plus kNoAllocTickets
+// counters) until the process exits.
+// ===========================================================================
+namespace {
+
+constexpr size_t kNoAllocScratchFloats = (size_t)4 << 20;   // 16 MiB of FP32 partials
+constexpr int kNoAllocTickets = 8192;                        // chain tiles of 32
+
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchFloats];
+static __device__ __align__(256) unsigned int g_noalloc_tickets[kNoAllocTickets];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+float *g_noalloc_ws[kMaxDevices] = {};
+unsigned int *g_noalloc_tk[kMaxDevices] = {};
+
+// Device addresses of the arrays on the current device, looked up once per
+// device (host code cannot use the symbols' names as device pointers).
+cudaError_t noalloc_addresses(float **ws, unsigned int **tk) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ws[dev]) {
+    void *p = nullptr, *q = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    e = cudaGetSymbolAddress(&q, g_noalloc_tickets);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ws[dev] = static_cast<float *>(p);
+    g_noalloc_tk[dev] = static_cast<unsigned int *>(q);
+  }
+  *ws = g_noalloc_ws[dev];
+  *tk = g_noalloc_tk[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" pcv_status pcv_log_density_noalloc(pcv_ctx *x, const float *theta, const int32_t *fold,
+                                              int32_t n, int32_t precision, double *logp,
+                                              float *grad, double *shat) {
+  if (!x) return PCV_E_INVALID_ARG;
+  if (!theta || !fold || !logp || !grad || !shat || n < 1) return fail(x, PCV_E_INVALID_ARG, "bad argument");
+  if (precision != PCV_FP32_SIMT) return fail(x, PCV_E_UNSUPPORTED, "precision not available for this context");
+  const int tiles = (n + 31) / 32;
+  const int stride = std::max(x->d_pad, simt_flat_pp(x->p)) + 4;
+  if (tiles > kNoAllocTickets || (size_t)tiles * 32 * stride > kNoAllocScratchFloats)
+    return fail(x, PCV_E_INVALID_ARG,
+                "pcv_log_density_noalloc: n = " + std::to_string(n) + " positions of dimension " +
+                    std::to_string(x->d) + " exceed the fixed scratch (" +
+                    std::to_string(kNoAllocScratchFloats) + " floats, " + std::to_string(kNoAllocTickets) +
+                    " tiles of 32); use pcv_log_density");
+  float *ws = nullptr;
+  unsigned int *tk = nullptr;
+  CK(noalloc_addresses(&ws, &tk));
+  // largest split count that fits the fixed scratch, at most the usual choice
+  ChainBufs cb;
+  cb.C = n; cb.L = 1; cb.fold_base = 0;
+  GradArgs a = grad_args(x, cb, false);
+  const size_t per_split = (size_t)tiles * 32 * stride;
+  a.splits = std::max(1, std::min(a.splits, (int)(kNoAllocScratchFloats / per_split)));
+  a.fold_of = fold;
+  a.theta = theta; a.ld_theta = x->d;
+  a.grad = grad; a.ld_grad = x->d;
+  a.logp = logp; a.shat = shat;
+  a.need_ll = 1;
+  a.mode = MODE_NONE;
+  a.r = nullptr;
+  a.ws = ws;
+  a.ws_stride = stride;
+  a.tickets = tk;
+  enter(x);
+  // tickets must start at zero: a previous call that failed part-way could
+  // have left some set (clearing is a memset, not an allocation)
+  CK(cudaMemsetAsync(tk, 0, sizeof(unsigned int) * (size_t)tiles, x->stream));
+  CK(launch_grad_simt(x->pb, a, x->stream));
+  leave(x);
+  return PCV_OK;
+}

@@ -98,6 +98,7 @@ def load():
         "pcv_accept_rate": (i32, [vp, vp]),
         "pcv_last_sample_ms": (i32, [vp, ct.POINTER(f64)]),
         "pcv_time_leapfrog_kernel": (i32, [vp, i32, ct.POINTER(f64)]),
+        "pcv_log_density_noalloc": (i32, [vp, vp, vp, i32, i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -114,7 +115,7 @@ def exported_symbols():
             "pcv_destroy", "pcv_set_positions", "pcv_get_positions", "pcv_get_adaptation",
             "pcv_log_density", "pcv_trajectory", "pcv_draw_normals", "pcv_accumulate",
             "pcv_get_draws", "pcv_accept_rate", "pcv_last_sample_ms",
-            "pcv_time_leapfrog_kernel"]
+            "pcv_time_leapfrog_kernel", "pcv_log_density_noalloc"]
 
 
 def _ptr(a: Optional[np.ndarray]):
