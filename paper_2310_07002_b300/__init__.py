@@ -7,7 +7,8 @@ synthetic inputs.
 from . import workloads  # noqa: F401
 
 
-def build(force: bool = False) -> str:
+def build_library(force: bool = False) -> str:
+    """Compile the CUDA library in-tree (see the ``build`` module)."""
     from .build import build as _b
     return _b(force=force)
 

@@ -19,7 +19,7 @@ def header_functions():
 
 @pytest.fixture(scope="module")
 def libpcv():
-    from paper_2310_07002_b300 import build
+    from paper_2310_07002_b300.build import build
     path = build()
     from paper_2310_07002_b300 import pcv
     return pcv.load(), path

@@ -21,7 +21,7 @@ def torch():
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    from paper_2310_07002_b300 import build
+    from paper_2310_07002_b300.build import build
     build()
     return torch
 
