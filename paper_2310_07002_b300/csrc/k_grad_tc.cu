@@ -1,0 +1,539 @@
+// k_grad_tc.cu -- tcgen05 / TMEM / TMA kernel for one fold-masked gradient
+// evaluation of the logistic model for all chains, fused with the leapfrog
+// update (Section 3.3; masks of eq. mask-log-prob / mask-log-pred, Appendix
+// B).  The two contractions of the masked likelihood gradient are tensor-core
+// GEMMs in BF16 with FP32 accumulation:
+//
+//   S = Theta_tile . X_chunk^T      (128 chains x 128 rows, K = p)   -> TMEM
+//   R = mask .* (y - sigmoid(2 S))  (epilogue, BF16)                 -> SMEM
+//   G += R . X_chunk                (128 chains x p, K = 128 rows)   -> TMEM
+//
+// Theta is stored scaled by 1/2 (exact in binary floating point), so S is
+// eta/2 and sigmoid(eta) = 1/2 + tanh(S)/2.  The same SMEM X tile is the
+// K-major B operand of the first GEMM and the MN-major B operand of the
+// second.  When log densities are needed (last leapfrog step, evaluations)
+// Theta is split into bf16 hi + lo parts and S accumulates both, giving an
+// FP32-accurate eta for the FP64 accept test.
+//
+// Work: persistent CTAs (one per SM) take equal contiguous ranges of the
+// flattened (chain tile, row chunk) units ("stream-K").  A CTA flushes its G
+// partial for each tile segment to a workspace; the last CTA of a tile
+// (atomic ticket, no spinning) sums the segments in order and applies priors
+// and the momentum / position update.
+//
+// Roles: warp 0 issues TMA loads, warp 1 allocates TMEM and issues the MMAs
+// (one thread), warps 2-5 run the epilogue (thread = TMEM lane = chain).
+// Every mbarrier wait is bounded: on time-out the kernel sets an error flag,
+// stops issuing work and exits after freeing TMEM.
+#include <cuda.h>
+
+#include "pcv_internal.cuh"
+
+namespace pcv {
+
+constexpr int kTN = 128;        // rows per chunk
+constexpr int kTM = 128;        // chains per tile
+constexpr int kTcThreads = 192; // 6 warps
+
+
+// ----------------------------- PTX helpers --------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait (2 s of wall time).  Returns false on time-out or abort.
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                       unsigned int *err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (global_ns() - t0 > 2000000000ull) {
+      atomicOr(err, 1u);
+      *abort_flag = 1;
+      return false;
+    }
+  }
+  return true;
+}
+// Bounded wait that ignores the abort flag (draining copies in flight).
+__device__ __noinline__ void mbar_wait_quiet(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > 2000000000ull) return;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *tm, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+#define PCV_TMEM_LD32(taddr, v)                                                                  \
+  asm volatile(                                                                                  \
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"  \
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"      \
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),    \
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), \
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),          \
+        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),          \
+        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])           \
+      : "r"(taddr))
+#define PCV_TMEM_LD16(taddr, v)                                                                  \
+  asm volatile(                                                                                  \
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"  \
+      "%14,%15}, [%16];"                                                                         \
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),    \
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), \
+        "=r"(v[14]), "=r"(v[15])                                                                 \
+      : "r"(taddr))
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor (tcgen05): start >> 4 at bits 0-13, leading
+// byte offset >> 4 at 16-29, stride byte offset >> 4 at 32-45, the fixed
+// version 0b001 at 46-48, 128-byte swizzle (value 2) at 61-63.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+// Instruction descriptor, kind::f16: D F32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9 = 1, 10-12 = 1), A K-major, B K-major or MN-major (bit 16),
+// N >> 3 at 17-22, M >> 4 at 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool b_mn_major) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((b_mn_major ? 1u : 0u) << 16) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t bf16x2_from(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+__device__ __forceinline__ uint32_t tanh_bf16x2(uint32_t x) {
+  uint32_t r;
+  asm("tanh.approx.bf16x2 %0, %1;" : "=r"(r) : "r"(x));
+  return r;
+}
+__device__ __forceinline__ uint32_t fma_bf16x2(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r;
+  asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+  return r;
+}
+
+// CTA owning flattened unit u when U units are split over n CTAs as
+// [floor(b U / n), floor((b+1) U / n)).
+__host__ __device__ inline int owner_cta(long long u, long long U, long long n) {
+  return (int)(((u + 1) * n + U - 1) / U - 1);
+}
+
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_grad_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_hi,
+              const __grid_constant__ CUtensorMap tm_lo, Problem pb, GradArgs a, TcArgs ta) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int KA = ta.KP / 64;                       // 128-byte K atoms
+  const uint32_t th_bytes = (uint32_t)KA * kTM * 128;
+  const uint32_t x_bytes = (uint32_t)KA * kTN * 128;
+  const uint32_t r_bytes = (kTN / 64) * kTM * 128;
+  const int NS = ta.NS;
+  uint8_t *th_hi = sm;
+  uint8_t *th_lo = th_hi + th_bytes;
+  uint8_t *xs = th_lo + (ta.need_lo ? th_bytes : 0);
+  uint8_t *rs = xs + (size_t)NS * x_bytes;
+  uint8_t *ys = rs + 2 * r_bytes;                  // NS x kTN bf16
+  uint64_t *bars = reinterpret_cast<uint64_t *>(ys + NS * kTN * 2 + 64);
+  // barrier slots
+  uint64_t *x_full = bars, *x_empty = bars + 4, *s_full = bars + 8, *s_empty = bars + 10;
+  uint64_t *r_full = bars + 12, *r_empty = bars + 14, *th_full = bars + 16, *th_empty = bars + 17;
+  uint64_t *g_full = bars + 18, *g_empty = bars + 19;
+  uint32_t *tmem_base_slot = reinterpret_cast<uint32_t *>(bars + 20);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 21);
+  int *last_flag = reinterpret_cast<int *>(bars + 22);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long U = (long long)ta.T * ta.J;
+  const long long u0 = (long long)blockIdx.x * U / ta.n_cta;
+  const long long u1 = (long long)(blockIdx.x + 1) * U / ta.n_cta;
+  const int nunits = (int)(u1 - u0);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) { mbar_init(smem_u32(&x_full[s]), 1); mbar_init(smem_u32(&x_empty[s]), 1); }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(smem_u32(&s_full[s]), 1); mbar_init(smem_u32(&s_empty[s]), 4);
+      mbar_init(smem_u32(&r_full[s]), 4); mbar_init(smem_u32(&r_empty[s]), 1);
+    }
+    mbar_init(smem_u32(th_full), 1); mbar_init(smem_u32(th_empty), 1);
+    mbar_init(smem_u32(g_full), 1); mbar_init(smem_u32(g_empty), 4);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {   // TMEM: 2 x 128 columns of S, then G
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_base_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_base_slot;
+  const uint32_t tmem_G = tmem + 256;
+
+  if (warp == 0) {
+    // ------------------------------ TMA producer ---------------------------
+    if (lane == 0) {
+      int seg = 0, th_issued = -1;
+      int last_round[4] = {-1, -1, -1, -1};
+      for (int i = 0; i < nunits; ++i) {
+        const long long u = u0 + i;
+        const int t = (int)(u / ta.J), j = (int)(u - (long long)t * ta.J);
+        if (i == 0 || j == 0) {
+          if (!mbar_wait(smem_u32(th_empty), (seg & 1) ^ 1, abort_flag, ta.err)) break;
+          mbar_expect_tx(smem_u32(th_full), th_bytes * (ta.need_lo ? 2 : 1));
+          for (int kb = 0; kb < KA; ++kb) {
+            tma_load_2d(smem_u32(th_hi + kb * kTM * 128), &tm_hi, kb * 64, t * kTM, smem_u32(th_full));
+            if (ta.need_lo)
+              tma_load_2d(smem_u32(th_lo + kb * kTM * 128), &tm_lo, kb * 64, t * kTM, smem_u32(th_full));
+          }
+          th_issued = seg;
+          ++seg;
+        }
+        const int st = i % NS, rnd = i / NS;
+        if (!mbar_wait(smem_u32(&x_empty[st]), (rnd & 1) ^ 1, abort_flag, ta.err)) break;
+        mbar_expect_tx(smem_u32(&x_full[st]), x_bytes + kTN * 2);
+        uint8_t *xb = xs + (size_t)st * x_bytes;
+        for (int kb = 0; kb < KA; ++kb)
+          tma_load_2d(smem_u32(xb + kb * kTN * 128), &tm_x, kb * 64, j * kTN, smem_u32(&x_full[st]));
+        bulk_load(smem_u32(ys + st * kTN * 2), ta.yc + (size_t)j * kTN, kTN * 2, smem_u32(&x_full[st]));
+        last_round[st] = rnd;
+      }
+      // on abort: let copies already issued land before the CTA exits
+      if (*abort_flag) {
+        for (int s = 0; s < NS; ++s)
+          if (last_round[s] >= 0) mbar_wait_quiet(smem_u32(&x_full[s]), last_round[s] & 1);
+        if (th_issued >= 0) mbar_wait_quiet(smem_u32(th_full), th_issued & 1);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------ MMA issuer -----------------------------
+    if (lane == 0) {
+      const uint32_t id1 = idesc_bf16(kTM, kTN, false);
+      const uint32_t id2 = idesc_bf16(kTM, ta.PN, true);
+      int seg1 = 0, seg2 = 0;
+      auto gemm2 = [&](int k) -> bool {
+        const long long u = u0 + k;
+        const int t = (int)(u / ta.J), j = (int)(u - (long long)t * ta.J);
+        const bool first = (k == 0 || j == 0);
+        const bool last = (k == nunits - 1 || j == ta.J - 1);
+        const int rb = k & 1;
+        if (!mbar_wait(smem_u32(&r_full[rb]), (k >> 1) & 1, abort_flag, ta.err)) return false;
+        if (first && !mbar_wait(smem_u32(g_empty), (seg2 & 1) ^ 1, abort_flag, ta.err)) return false;
+        tc_fence_after();
+        const int st = k % NS;
+        const uint32_t xb = smem_u32(xs + (size_t)st * x_bytes);
+        const uint32_t rbuf = smem_u32(rs + (size_t)rb * r_bytes);
+        for (int ks = 0; ks < kTN / 16; ++ks) {
+          const uint64_t ad = sdesc_sw128(rbuf + (ks >> 2) * kTM * 128 + (ks & 3) * 32, 16, 1024);
+          const uint64_t bd = sdesc_sw128(xb + ks * 2048, kTN * 128, 1024);
+          tc_mma_bf16(tmem_G, ad, bd, id2, (first && ks == 0) ? 0u : 1u);
+        }
+        tc_commit(smem_u32(&r_empty[rb]));
+        tc_commit(smem_u32(&x_empty[st]));
+        if (last) { tc_commit(smem_u32(g_full)); ++seg2; }
+        return true;
+      };
+      bool ok = true;
+      for (int i = 0; i < nunits && ok; ++i) {
+        const long long u = u0 + i;
+        const int t = (int)(u / ta.J), j = (int)(u - (long long)t * ta.J);
+        const bool first = (i == 0 || j == 0);
+        const bool last = (i == nunits - 1 || j == ta.J - 1);
+        (void)t;
+        if (first) {
+          if (!mbar_wait(smem_u32(th_full), seg1 & 1, abort_flag, ta.err)) { ok = false; break; }
+        }
+        const int st = i % NS;
+        if (!mbar_wait(smem_u32(&x_full[st]), (i / NS) & 1, abort_flag, ta.err)) { ok = false; break; }
+        const int sb = i & 1;
+        if (!mbar_wait(smem_u32(&s_empty[sb]), ((i >> 1) & 1) ^ 1, abort_flag, ta.err)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t xb = smem_u32(xs + (size_t)st * x_bytes);
+        const uint32_t thb = smem_u32(th_hi), tlb = smem_u32(th_lo);
+        const uint32_t dS = tmem + sb * 128;
+        for (int ks = 0; ks < ta.KS; ++ks) {
+          const uint32_t off = (ks >> 2) * kTM * 128 + (ks & 3) * 32;
+          const uint32_t offx = (ks >> 2) * kTN * 128 + (ks & 3) * 32;
+          tc_mma_bf16(dS, sdesc_sw128(thb + off, 16, 1024), sdesc_sw128(xb + offx, 16, 1024), id1,
+                      ks > 0 ? 1u : 0u);
+        }
+        if (ta.need_lo) {
+          for (int ks = 0; ks < ta.KS; ++ks) {
+            const uint32_t off = (ks >> 2) * kTM * 128 + (ks & 3) * 32;
+            const uint32_t offx = (ks >> 2) * kTN * 128 + (ks & 3) * 32;
+            tc_mma_bf16(dS, sdesc_sw128(tlb + off, 16, 1024), sdesc_sw128(xb + offx, 16, 1024), id1, 1u);
+          }
+        }
+        tc_commit(smem_u32(&s_full[sb]));
+        if (last) { tc_commit(smem_u32(th_empty)); ++seg1; }
+        if (i > 0 && !gemm2(i - 1)) { ok = false; break; }
+      }
+      if (ok && nunits > 0) gemm2(nunits - 1);
+    }
+  } else {
+    // ------------------------------ epilogue -------------------------------
+    const int q = warp & 3;                        // TMEM lane quarter of this warp
+    const int m = q * 32 + lane;                   // chain row within the tile
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    const bool accurate = ta.need_lo != 0;
+    const uint32_t neg_half2 = 0xBF00BF00u;        // (-0.5, -0.5) in bf16x2
+    int seg = 0;
+    int t_cur = -1, c = 0;
+    bool valid = false;
+    FoldDesc fd = {0, 0, 0, 0};
+    float ll_tr = 0.0f, ll_te = 0.0f;
+    for (int i = 0; i < nunits; ++i) {
+      const long long u = u0 + i;
+      const int t = (int)(u / ta.J), j = (int)(u - (long long)t * ta.J);
+      const bool last = (i == nunits - 1 || j == ta.J - 1);
+      if (t != t_cur) {
+        t_cur = t;
+        c = t * kTM + m;
+        valid = c < a.C;
+        if (valid) fd = pb.folds[fold_of_chain(a, c)];
+        ll_tr = ll_te = 0.0f;
+      }
+      const int sb = i & 1, rb = i & 1;
+      if (!mbar_wait(smem_u32(&s_full[sb]), (i >> 1) & 1, abort_flag, ta.err)) break;
+      tc_fence_after();
+      if (!mbar_wait(smem_u32(&r_empty[rb]), ((i >> 1) & 1) ^ 1, abort_flag, ta.err)) break;
+      const int n0 = j * kTN;
+      const bool overlap = valid && (n0 < fd.excl_hi) && (n0 + kTN > fd.excl_lo);
+      const uint32_t *yw = reinterpret_cast<const uint32_t *>(ys + (i % NS) * kTN * 2);
+      uint8_t *rbuf = rs + (size_t)rb * r_bytes;
+      for (int piece = 0; piece < kTN / 32; ++piece) {
+        uint32_t v[32];
+        PCV_TMEM_LD32(tmem + sb * 128 + piece * 32 + lane_off, v);
+        tmem_wait_ld();
+        uint32_t packed[16];
+        if (!accurate) {
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const float s0 = __uint_as_float(v[2 * k]), s1 = __uint_as_float(v[2 * k + 1]);
+            const uint32_t t2 = tanh_bf16x2(bf16x2_from(s0, s1));
+            const uint32_t y2 = yw[piece * 16 + k];
+            packed[k] = fma_bf16x2(t2, neg_half2, y2);       // (y - 1/2) - tanh(S)/2
+          }
+          if (overlap) {
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+              const int n = n0 + piece * 32 + k;
+              if (n >= fd.excl_lo && n < fd.excl_hi)
+                packed[k >> 1] &= (k & 1) ? 0x0000FFFFu : 0xFFFF0000u;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 32; k += 2) {
+            float rr[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int n = n0 + piece * 32 + k + h;
+              const float eta = 2.0f * __uint_as_float(v[k + h]);
+              const uint32_t y2 = yw[piece * 16 + (k >> 1)];
+              const float yv = __uint_as_float((h ? (y2 & 0xFFFF0000u) : (y2 << 16))) + 0.5f;
+              const float e = __expf(-fabsf(eta));
+              const float inv = __fdividef(1.0f, 1.0f + e);
+              const float sig = eta >= 0.0f ? inv : e * inv;
+              const bool in_rows = n < pb.N;
+              const bool tr = in_rows && (n < fd.excl_lo || n >= fd.excl_hi);
+              const bool te = in_rows && n >= fd.test_lo && n < fd.test_hi;
+              const float ll = yv * eta - (fmaxf(eta, 0.0f) + __logf(1.0f + e));
+              if (tr) ll_tr += ll;
+              if (te) ll_te += ll;
+              rr[h] = tr ? (yv - sig) : 0.0f;
+            }
+            packed[k >> 1] = bf16x2_from(rr[0], rr[1]);
+          }
+        }
+        // R tile: row m, K columns piece*32 .. +32 (64 bytes = four 16-byte
+        // chunks) of K atom piece / 2, 128-byte swizzle (chunk ^= m & 7)
+        uint8_t *row = rbuf + (piece >> 1) * kTM * 128 + m * 128;
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+          const int cidx = (piece & 1) * 4 + qq;
+          uint4 val = make_uint4(packed[4 * qq], packed[4 * qq + 1], packed[4 * qq + 2], packed[4 * qq + 3]);
+          *reinterpret_cast<uint4 *>(row + ((cidx ^ (m & 7)) << 4)) = val;
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&s_empty[sb]));
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&r_full[rb]));
+      if (last) {
+        // segment end: flush the G partial of this tile
+        if (!mbar_wait(smem_u32(g_full), seg & 1, abort_flag, ta.err)) break;
+        tc_fence_after();
+        const int b0 = owner_cta((long long)t * ta.J, U, ta.n_cta);
+        const int sidx = blockIdx.x - b0;
+        float *wsp = ta.ws + ((size_t)t * ta.max_seg + sidx) * (size_t)(ta.PN + 2) * kTM;
+        for (int cb = 0; cb < ta.PN; cb += 16) {
+          uint32_t gv[16];
+          PCV_TMEM_LD16(tmem_G + cb + lane_off, gv);
+          tmem_wait_ld();
+#pragma unroll
+          for (int k = 0; k < 16; ++k) wsp[(size_t)(cb + k) * kTM + m] = __uint_as_float(gv[k]);
+        }
+        wsp[(size_t)ta.PN * kTM + m] = ll_tr;
+        wsp[(size_t)(ta.PN + 1) * kTM + m] = ll_te;
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(g_empty));
+        ++seg;
+        ll_tr = ll_te = 0.0f;
+        __threadfence();
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        const int nseg = owner_cta((long long)t * ta.J + ta.J - 1, U, ta.n_cta) - b0 + 1;
+        if (m == 0) {
+          const unsigned prev = atomicAdd(ta.tickets + t, 1u);
+          *last_flag = (prev == (unsigned)nseg - 1);
+          if (prev == (unsigned)nseg - 1) ta.tickets[t] = 0u;
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (*last_flag && valid) {
+          __threadfence();
+          // sum the tile's segments in order, add the prior, update
+          const float *base = ta.ws + (size_t)t * ta.max_seg * (size_t)(ta.PN + 2) * kTM;
+          const size_t seg_stride = (size_t)(ta.PN + 2) * kTM;
+          float *th = const_cast<float *>(a.theta) + (size_t)c * a.ld_theta;
+          float *gr = a.grad + (size_t)c * a.ld_grad;
+          float *rr = a.r ? a.r + (size_t)c * a.ld_theta : nullptr;
+          const float eps = a.mode != MODE_NONE ? *a.eps : 0.0f;
+          const float kick = a.mode == MODE_LAST_KICK ? 0.5f * eps : eps;
+          double lp = 0.0;
+          for (int jj = 0; jj < pb.p; ++jj) {
+            float gs = 0.0f;
+            for (int s = 0; s < nseg; ++s) gs += __ldcg(base + s * seg_stride + (size_t)jj * kTM + m);
+            const float tv = th[jj];
+            const float g = gs - tv * pb.beta_prec;
+            gr[jj] = g;
+            if (a.need_ll)
+              lp += -0.5 * kLog2PiD - (double)pb.log_beta_sd - 0.5 * (double)tv * tv * pb.beta_prec;
+            if (a.mode != MODE_NONE) {
+              const float rj = rr[jj] + kick * g;
+              rr[jj] = rj;
+              if (a.mode == MODE_KICK_DRIFT) {
+                const float tn = tv + eps * a.minv[jj] * rj;
+                th[jj] = tn;
+                const float half = 0.5f * tn;       // shadows hold theta / 2
+                const __nv_bfloat16 hi = __float2bfloat16_rn(half);
+                a.shadow_hi[(size_t)c * a.ld_shadow + jj] = hi;
+                a.shadow_lo[(size_t)c * a.ld_shadow + jj] = __float2bfloat16_rn(half - __bfloat162float(hi));
+              }
+            }
+          }
+          if (a.need_ll) {
+            double s0 = 0.0, s1 = 0.0;
+            for (int s = 0; s < nseg; ++s) {
+              s0 += (double)__ldcg(base + s * seg_stride + (size_t)ta.PN * kTM + m);
+              s1 += (double)__ldcg(base + s * seg_stride + (size_t)(ta.PN + 1) * kTM + m);
+            }
+            a.logp[c] = s0 + lp;
+            a.shat[c] = s1;
+          }
+        }
+      }
+    }
+  }
+  // teardown: every role has left its loop (normally or by abort)
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+size_t tc_smem_bytes(int KP, int NS, int need_lo) {
+  const size_t KA = KP / 64;
+  size_t b = KA * kTM * 128 * (need_lo ? 2 : 1) + (size_t)NS * KA * kTN * 128 + 2 * (kTN / 64) * kTM * 128 +
+             (size_t)NS * kTN * 2 + 64 + 24 * 8;
+  return b + 1024;   // alignment slack
+}
+
+int tc_segments_per_tile(int T, int J, int n_cta) {
+  const long long U = (long long)T * J;
+  int mx = 1;
+  for (int t = 0; t < T; ++t) {
+    const int b0 = owner_cta((long long)t * J, U, n_cta);
+    const int b1 = owner_cta((long long)t * J + J - 1, U, n_cta);
+    mx = mx > b1 - b0 + 1 ? mx : b1 - b0 + 1;
+  }
+  return mx;
+}
+
+// once per context (outside any stream capture): allow the large dynamic SMEM
+cudaError_t tc_prepare() {
+  return cudaFuncSetAttribute(k_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
+cudaError_t launch_grad_tc(const CUtensorMap &tm_x, const CUtensorMap &tm_hi, const CUtensorMap &tm_lo,
+                           const Problem &pb, const GradArgs &a, const TcArgs &ta, cudaStream_t st) {
+  const size_t smem = tc_smem_bytes(ta.KP, ta.NS, ta.need_lo);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  k_grad_tc<<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta);
+  return cudaGetLastError();
+}
+
+}  // namespace pcv

@@ -47,10 +47,11 @@ __global__ void __launch_bounds__(256) k_begin(BeginArgs a) {
       const float tn = th[j] + eps * mv * rh;
       a.r[(size_t)c * a.ld + j] = rh;
       a.theta_p[(size_t)c * a.ld + j] = tn;
-      if (a.shadow_hi) {
-        const __nv_bfloat16 hi = __float2bfloat16_rn(tn);
+      if (a.shadow_hi) {                     // bf16 hi + lo of theta / 2 (tensor-core operand)
+        const float half = 0.5f * tn;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(half);
         a.shadow_hi[(size_t)c * a.ld_shadow + j] = hi;
-        a.shadow_lo[(size_t)c * a.ld_shadow + j] = __float2bfloat16_rn(tn - __bfloat162float(hi));
+        a.shadow_lo[(size_t)c * a.ld_shadow + j] = __float2bfloat16_rn(half - __bfloat162float(hi));
       }
     }
   }
@@ -93,7 +94,7 @@ __global__ void k_shadow(int C, int d, int ld, const float *theta, __nv_bfloat16
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)C * d) return;
   const int c = (int)(t / d), j = (int)(t - (long long)c * d);
-  const float v = theta[(size_t)c * ld + j];
+  const float v = 0.5f * theta[(size_t)c * ld + j];     // shadows hold theta / 2
   const __nv_bfloat16 h = __float2bfloat16_rn(v);
   hi[(size_t)c * ld_shadow + j] = h;
   lo[(size_t)c * ld_shadow + j] = __float2bfloat16_rn(v - __bfloat162float(h));

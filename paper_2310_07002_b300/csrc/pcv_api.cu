@@ -14,8 +14,19 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "../../include/pcv.h"
 #include "pcv_internal.cuh"
+
+namespace pcv {
+size_t tc_smem_bytes(int KP, int NS, int need_lo);
+int tc_segments_per_tile(int T, int J, int n_cta);
+cudaError_t tc_prepare();
+cudaError_t launch_grad_tc(const CUtensorMap &tm_x, const CUtensorMap &tm_hi, const CUtensorMap &tm_lo,
+                           const Problem &pb, const GradArgs &a, const TcArgs &ta, cudaStream_t st);
+}  // namespace pcv
 
 
 using namespace pcv;
@@ -30,6 +41,10 @@ struct ChainBufs {
   float *theta = nullptr, *grad = nullptr, *theta_p = nullptr, *r = nullptr, *grad_p = nullptr;
   double *logp = nullptr, *shat = nullptr, *logp_p = nullptr, *shat_p = nullptr, *H0 = nullptr;
   double *accept_prob = nullptr;
+  // tensor-core path: bf16 hi / lo of theta / 2 [C_pad x KP] and their TMA maps
+  int C_pad = 0;
+  __nv_bfloat16 *shadow_hi = nullptr, *shadow_lo = nullptr;
+  CUtensorMap tm_hi{}, tm_lo{};
 };
 
 enum CtxState { ST_CREATED = 0, ST_WARMED = 1, ST_SAMPLED = 2 };
@@ -70,6 +85,18 @@ struct pcv_ctx {
   // graphs
   cudaGraphExec_t g_sample_b = nullptr, g_fold_1 = nullptr, g_fd_1 = nullptr;
   int fd_n_adapt = 0;
+  // tensor-core path
+  bool tc = false;
+  int KP = 0, KS = 0, PN = 0, N_pad = 0, J = 0, n_sm = 148;
+  __nv_bfloat16 *X16 = nullptr, *yc16 = nullptr;
+  CUtensorMap tm_x{};
+  float *ws_tc = nullptr;
+  size_t ws_tc_floats = 0;
+  unsigned int *tickets_tc = nullptr;
+  size_t n_tickets_tc = 0;
+  ChainBufs ld_cb;          // positions of pcv_log_density calls (tensor-core path)
+  int ld_cap = 0;
+  float *rstart = nullptr;
 };
 
 namespace {
@@ -132,7 +159,7 @@ int splits_for(const pcv_ctx *x, int C) {
 
 pcv_status ensure_ws(pcv_ctx *x, int C, int splits) {
   const int tiles = (C + 31) / 32;
-  const int PP = simt_flat_pp(x->p);
+  const int PP = std::max(0, simt_flat_pp(x->p));
   const int stride = std::max(x->d_pad, PP) + 4;
   const size_t need = (size_t)tiles * splits * 32 * stride;
   if (need > x->ws_floats) {
@@ -146,6 +173,77 @@ pcv_status ensure_ws(pcv_ctx *x, int C, int splits) {
     if (!dalloc_n(x, &t, (size_t)tiles)) return fail(x, PCV_E_OOM, "ticket allocation failed");
     x->tickets = t;
     x->n_tickets = tiles;
+  }
+  return PCV_OK;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void *ptr = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  }
+  return fn;
+}
+
+// 2-D bf16 tensor [rows x cols] row-major, 128 x 64 boxes, 128-byte swizzle
+bool encode_bf16_map(CUtensorMap *m, const void *base, int rows, int cols) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  cuuint32_t box[2] = {64, 128};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+pcv_status alloc_shadows(pcv_ctx *x, ChainBufs &cb, int C) {
+  cb.C_pad = (C + 127) / 128 * 128;
+  if (!dalloc_n(x, &cb.shadow_hi, (size_t)cb.C_pad * x->KP) || !dalloc_n(x, &cb.shadow_lo, (size_t)cb.C_pad * x->KP))
+    return fail(x, PCV_E_OOM, "shadow allocation failed");
+  if (!encode_bf16_map(&cb.tm_hi, cb.shadow_hi, cb.C_pad, x->KP) ||
+      !encode_bf16_map(&cb.tm_lo, cb.shadow_lo, cb.C_pad, x->KP))
+    return fail(x, PCV_E_CUDA, "cuTensorMapEncodeTiled failed for the parameter shadows");
+  return PCV_OK;
+}
+
+TcArgs tc_args(pcv_ctx *x, int C, bool need_lo) {
+  TcArgs t{};
+  t.KP = x->KP; t.KS = x->KS; t.PN = x->PN; t.N_pad = x->N_pad; t.J = x->J;
+  t.T = (C + 127) / 128;
+  const long long U = (long long)t.T * t.J;
+  t.n_cta = (int)std::min<long long>(x->n_sm, U);
+  t.max_seg = tc_segments_per_tile(t.T, t.J, t.n_cta);
+  t.need_lo = need_lo ? 1 : 0;
+  t.NS = need_lo ? 2 : 3;
+  t.yc = x->yc16;
+  t.ws = x->ws_tc;
+  t.tickets = x->tickets_tc;
+  t.err = &x->st->error;
+  return t;
+}
+
+pcv_status ensure_ws_tc(pcv_ctx *x, int C) {
+  TcArgs t = tc_args(x, C, false);
+  const size_t need = (size_t)t.T * t.max_seg * (t.PN + 2) * 128;
+  if (need > x->ws_tc_floats) {
+    float *w;
+    if (!dalloc_n(x, &w, need)) return fail(x, PCV_E_OOM, "workspace allocation failed");
+    x->ws_tc = w;
+    x->ws_tc_floats = need;
+  }
+  if ((size_t)t.T > x->n_tickets_tc) {
+    unsigned *tk;
+    if (!dalloc_n(x, &tk, (size_t)t.T)) return fail(x, PCV_E_OOM, "ticket allocation failed");
+    x->tickets_tc = tk;
+    x->n_tickets_tc = t.T;
   }
   return PCV_OK;
 }
@@ -169,14 +267,23 @@ GradArgs grad_args(pcv_ctx *x, const ChainBufs &cb, bool proposal) {
   a.minv = x->minv;
   a.splits = splits_for(x, cb.C);
   a.ws = x->ws;
-  a.ws_stride = std::max(x->d_pad, simt_flat_pp(x->p)) + 4;
+  a.ws_stride = std::max(x->d_pad, std::max(0, simt_flat_pp(x->p))) + 4;
   a.tickets = x->tickets;
-  a.shadow_hi = a.shadow_lo = nullptr;
-  a.ld_shadow = 0;
+  a.shadow_hi = x->tc ? cb.shadow_hi : nullptr;
+  a.shadow_lo = x->tc ? cb.shadow_lo : nullptr;
+  a.ld_shadow = x->tc ? x->KP : 0;
   return a;
 }
 
-pcv_status launch_grad(pcv_ctx *x, GradArgs a) {
+pcv_status launch_grad(pcv_ctx *x, GradArgs a, const ChainBufs *cb = nullptr) {
+  if (x->tc) {
+    if (!cb) return fail(x, PCV_E_UNSUPPORTED, "internal: tensor-core launch without a chain set");
+    pcv_status s = ensure_ws_tc(x, a.C);
+    if (s != PCV_OK) return s;
+    TcArgs t = tc_args(x, a.C, a.need_ll != 0);
+    CK(launch_grad_tc(x->tm_x, cb->tm_hi, a.need_ll ? cb->tm_lo : cb->tm_hi, x->pb, a, t, x->stream));
+    return PCV_OK;
+  }
   pcv_status s = ensure_ws(x, a.C, a.splits);
   if (s != PCV_OK) return s;
   a.ws = x->ws;
@@ -185,10 +292,22 @@ pcv_status launch_grad(pcv_ctx *x, GradArgs a) {
   return PCV_OK;
 }
 
+// write the bf16 shadow of a chain set's current positions (tensor-core path)
+pcv_status write_shadow(pcv_ctx *x, ChainBufs &cb, const float *theta, int ld) {
+  if (!x->tc) return PCV_OK;
+  const long long T = (long long)cb.C * x->d;
+  k_shadow<<<(unsigned)((T + 255) / 256), 256, 0, x->stream>>>(cb.C, x->d, ld, theta, cb.shadow_hi, cb.shadow_lo,
+                                                              x->KP);
+  CK(cudaGetLastError());
+  return PCV_OK;
+}
+
 // evaluate gradient, logp and shat at the current positions of a chain set
 pcv_status refresh(pcv_ctx *x, ChainBufs &cb) {
+  pcv_status s = write_shadow(x, cb, cb.theta, x->d_pad);
+  if (s != PCV_OK) return s;
   GradArgs a = grad_args(x, cb, false);
-  return launch_grad(x, a);
+  return launch_grad(x, a, &cb);
 }
 
 // one HMC transition for every chain of a set (Section 3.3)
@@ -202,13 +321,16 @@ pcv_status launch_iteration(pcv_ctx *x, ChainBufs &cb, bool fd, bool accumulate)
   ba.theta_p = cb.theta_p; ba.r = cb.r; ba.H0 = cb.H0;
   ba.eps = &x->st->eps; ba.minv = x->minv;
   ba.r_given = nullptr;
+  ba.shadow_hi = x->tc ? cb.shadow_hi : nullptr;
+  ba.shadow_lo = x->tc ? cb.shadow_lo : nullptr;
+  ba.ld_shadow = x->KP;
   k_begin<<<(cb.C + 7) / 8, 256, 0, x->stream>>>(ba);
   CK(cudaGetLastError());
   GradArgs ga = grad_args(x, cb, true);
   for (int s = 1; s <= x->Lf; ++s) {
     ga.mode = s < x->Lf ? MODE_KICK_DRIFT : MODE_LAST_KICK;
     ga.need_ll = s == x->Lf;
-    pcv_status st = launch_grad(x, ga);
+    pcv_status st = launch_grad(x, ga, &cb);
     if (st != PCV_OK) return st;
   }
   AcceptArgs aa{};
@@ -259,7 +381,7 @@ pcv_status run_iterations(pcv_ctx *x, ChainBufs &cb, bool fd, bool accumulate, l
     return PCV_OK;
   }
   // make sure workspaces exist before capture (no allocation inside a capture)
-  pcv_status s0 = ensure_ws(x, cb.C, splits_for(x, cb.C));
+  pcv_status s0 = x->tc ? ensure_ws_tc(x, cb.C) : ensure_ws(x, cb.C, splits_for(x, cb.C));
   if (s0 != PCV_OK) return s0;
   if (!*cache) {
     cudaGraph_t g;
@@ -290,7 +412,8 @@ pcv_status alloc_chains(pcv_ctx *x, ChainBufs &cb, int C, int L, int fold_base) 
             dalloc_n(x, &cb.shat, (size_t)C) && dalloc_n(x, &cb.logp_p, (size_t)C) &&
             dalloc_n(x, &cb.shat_p, (size_t)C) && dalloc_n(x, &cb.H0, (size_t)C) &&
             dalloc_n(x, &cb.accept_prob, (size_t)C);
-  return ok ? PCV_OK : fail(x, PCV_E_OOM, "chain state allocation failed");
+  if (!ok) return fail(x, PCV_E_OOM, "chain state allocation failed");
+  return x->tc ? alloc_shadows(x, cb, C) : PCV_OK;
 }
 
 pcv_status alloc_accum(pcv_ctx *x) {
@@ -406,8 +529,11 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
     std::fprintf(stderr, "pcv_create: %s\n", last.c_str());
     return s;
   };
-  if (opt->precision != PCV_FP32_SIMT)
-    return bail(PCV_E_UNSUPPORTED, "tensor-core precisions are not available for this model/size");
+  if (opt->precision < PCV_FP32_SIMT || opt->precision > PCV_BF16) return bail(PCV_E_INVALID_ARG, "bad precision");
+  if (opt->precision == PCV_TF32) return bail(PCV_E_UNSUPPORTED, "TF32 is not built in this version");
+  x->tc = opt->precision == PCV_BF16;
+  if (x->tc && (model->kind != PCV_LOGISTIC || p > 128))
+    return bail(PCV_E_UNSUPPORTED, "the BF16 tensor-core path covers LOGISTIC with p <= 128");
   // model variant and dimension
   if (x->kind == PCV_LOGISTIC) { x->variant = MV_LOGISTIC; x->d = p; }
   else if (x->kind == PCV_HIER_GAUSS) {
@@ -423,8 +549,15 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
     return bail(PCV_E_INVALID_ARG, "sigma_prior_sd must be > 0");
   if (x->variant == MV_HIER && !(model->tau_prior_sd > 0)) return bail(PCV_E_INVALID_ARG, "tau_prior_sd must be > 0");
   const int PP = simt_flat_pp(p);
-  if (PP < 0) return bail(PCV_E_UNSUPPORTED, "p > 32 needs a tensor-core precision");
-  x->p_pad = PP;
+  if (PP < 0 && !x->tc) return bail(PCV_E_UNSUPPORTED, "p > 32 needs the BF16 tensor-core precision");
+  x->p_pad = PP > 0 ? PP : (p + 3) / 4 * 4;
+  if (x->tc) {
+    x->KP = (p + 63) / 64 * 64;
+    x->KS = (p + 15) / 16;
+    x->PN = 16 * x->KS;
+    x->N_pad = (int)((N + 127) / 128 * 128);
+    x->J = x->N_pad / 128;
+  }
   x->d_pad = (x->d + 3) / 4 * 4;
 
   // data checks
@@ -516,6 +649,26 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
     std::memcpy(&hX[(size_t)r * x->p_pad], X + i * p, sizeof(float) * p);
     hy[r] = y[i];
   }
+  if (x->tc) {
+    // bf16 design matrix [N_pad x KP] (round to nearest even) and y - 1/2
+    std::vector<__nv_bfloat16> hX16((size_t)x->N_pad * x->KP, __float2bfloat16_rn(0.0f));
+    std::vector<__nv_bfloat16> hyc((size_t)x->N_pad, __float2bfloat16_rn(0.0f));
+    for (int64_t r = 0; r < N; ++r) {
+      for (int j = 0; j < p; ++j) hX16[(size_t)r * x->KP + j] = __float2bfloat16_rn(hX[(size_t)r * x->p_pad + j]);
+      hyc[r] = __float2bfloat16_rn(hy[r] - 0.5f);
+    }
+    if (!dalloc_n(x, &x->X16, hX16.size()) || !dalloc_n(x, &x->yc16, hyc.size()))
+      return bail(PCV_E_OOM, "device allocation failed");
+    cudaMemcpyAsync(x->X16, hX16.data(), hX16.size() * 2, cudaMemcpyHostToDevice, x->stream);
+    cudaMemcpyAsync(x->yc16, hyc.data(), hyc.size() * 2, cudaMemcpyHostToDevice, x->stream);
+    if (cudaStreamSynchronize(x->stream) != cudaSuccess) return bail(PCV_E_CUDA, "upload failed");
+    if (!encode_bf16_map(&x->tm_x, x->X16, x->N_pad, x->KP))
+      return bail(PCV_E_CUDA, "cuTensorMapEncodeTiled failed for X");
+    if (tc_prepare() != cudaSuccess) return bail(PCV_E_CUDA, "cudaFuncSetAttribute failed");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&x->n_sm, cudaDevAttrMultiProcessorCount, dev);
+  }
   if (!dalloc_n(x, &x->X, hX.size()) || !dalloc_n(x, &x->y, (size_t)N) ||
       !dalloc_n(x, &x->folds, (size_t)K + 1) || !dalloc_n(x, &x->minv, (size_t)x->d_pad) ||
       !dalloc_n(x, &x->st, 1) || !dalloc_n(x, &x->wmean, (size_t)x->d) || !dalloc_n(x, &x->wM2, (size_t)x->d) ||
@@ -563,8 +716,12 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
   if ((s = alloc_chains(x, x->fold_cb, x->C, x->L, 0)) != PCV_OK) return bail(s, x->err);
   if ((s = alloc_chains(x, x->fd_cb, kNumFdChains, kNumFdChains, K)) != PCV_OK) return bail(s, x->err);
   if ((s = alloc_accum(x)) != PCV_OK) return bail(s, x->err);
-  if ((s = ensure_ws(x, x->C, splits_for(x, x->C))) != PCV_OK) return bail(s, x->err);
-  if ((s = ensure_ws(x, kNumFdChains, splits_for(x, kNumFdChains))) != PCV_OK) return bail(s, x->err);
+  if (x->tc) {
+    if ((s = ensure_ws_tc(x, x->C)) != PCV_OK) return bail(s, x->err);
+  } else {
+    if ((s = ensure_ws(x, x->C, splits_for(x, x->C))) != PCV_OK) return bail(s, x->err);
+    if ((s = ensure_ws(x, kNumFdChains, splits_for(x, kNumFdChains))) != PCV_OK) return bail(s, x->err);
+  }
   if (cudaStreamSynchronize(x->stream) != cudaSuccess) return bail(PCV_E_CUDA, "upload failed");
   leave(x);
   *out = x;
@@ -613,6 +770,11 @@ pcv_status pcv_warmup(pcv_ctx *x, int32_t n_fd, int32_t n_wu) {
   s = run_iterations(x, x->fold_cb, false, false, n_wu, &x->g_fold_1, 1);
   if (s != PCV_OK) return s;
   CK(cudaStreamSynchronize(x->stream));
+  {
+    unsigned int derr = 0;
+    CK(cudaMemcpy(&derr, &x->st->error, sizeof(derr), cudaMemcpyDeviceToHost));
+    if (derr) return fail(x, PCV_E_TIMEOUT, "a device-side wait timed out (error flags " + std::to_string(derr) + ")");
+  }
   leave(x);
   x->state = ST_WARMED;
   return PCV_OK;
@@ -634,6 +796,11 @@ pcv_status pcv_sample(pcv_ctx *x, int32_t n_draws) {
   float ms = 0.0f;
   cudaEventElapsedTime(&ms, x->ev0, x->ev1);
   x->last_ms = ms;
+  {
+    unsigned int derr = 0;
+    CK(cudaMemcpy(&derr, &x->st->error, sizeof(derr), cudaMemcpyDeviceToHost));
+    if (derr) return fail(x, PCV_E_TIMEOUT, "a device-side wait timed out (error flags " + std::to_string(derr) + ")");
+  }
   x->n_sampled += n_draws;
   x->finalized = false;
   x->state = ST_SAMPLED;
@@ -762,10 +929,22 @@ pcv_status pcv_log_density(pcv_ctx *x, const float *theta, const int32_t *fold, 
                            double *logp, float *grad, double *shat) {
   if (!x) return PCV_E_INVALID_ARG;
   if (!theta || !fold || !logp || !grad || !shat || n < 1) return fail(x, PCV_E_INVALID_ARG, "bad argument");
-  if (precision != PCV_FP32_SIMT) return fail(x, PCV_E_UNSUPPORTED, "precision not available for this context");
+  if (precision != (x->tc ? PCV_BF16 : PCV_FP32_SIMT))
+    return fail(x, PCV_E_UNSUPPORTED, "precision not available for this context");
   enter(x);
   ChainBufs cb;
   cb.C = n; cb.L = 1; cb.fold_base = 0;
+  if (x->tc) {
+    if (n > x->ld_cap) {                     // grow the shadow buffers of evaluated positions
+      pcv_status s0 = alloc_shadows(x, x->ld_cb, n);
+      if (s0 != PCV_OK) return s0;
+      x->ld_cap = x->ld_cb.C_pad;
+    }
+    cb.C_pad = x->ld_cb.C_pad; cb.shadow_hi = x->ld_cb.shadow_hi; cb.shadow_lo = x->ld_cb.shadow_lo;
+    cb.tm_hi = x->ld_cb.tm_hi; cb.tm_lo = x->ld_cb.tm_lo;
+    pcv_status s0 = write_shadow(x, cb, theta, x->d);
+    if (s0 != PCV_OK) return s0;
+  }
   GradArgs a = grad_args(x, cb, false);
   a.fold_of = fold;
   a.theta = theta; a.ld_theta = x->d;
@@ -774,7 +953,7 @@ pcv_status pcv_log_density(pcv_ctx *x, const float *theta, const int32_t *fold, 
   a.need_ll = 1;
   a.mode = MODE_NONE;
   a.r = nullptr;
-  pcv_status s = launch_grad(x, a);
+  pcv_status s = launch_grad(x, a, &cb);
   if (s != PCV_OK) return s;
   leave(x);
   return PCV_OK;
@@ -784,15 +963,16 @@ pcv_status pcv_trajectory(pcv_ctx *x, const float *theta0, const float *r0, int3
                           float *r1, double *logp1, double *shat1) {
   if (!x) return PCV_E_INVALID_ARG;
   if (!theta0 || !r0 || !theta1 || !r1 || !logp1 || !shat1) return fail(x, PCV_E_INVALID_ARG, "null argument");
-  if (precision != PCV_FP32_SIMT) return fail(x, PCV_E_UNSUPPORTED, "precision not available for this context");
+  if (precision != (x->tc ? PCV_BF16 : PCV_FP32_SIMT))
+    return fail(x, PCV_E_UNSUPPORTED, "precision not available for this context");
   enter(x);
   if (!x->traj_cb.theta) {
     pcv_status s = alloc_chains(x, x->traj_cb, x->C, x->L, 0);
     if (s != PCV_OK) return s;
+    if (!dalloc_n(x, &x->rstart, (size_t)x->C * x->d_pad)) return fail(x, PCV_E_OOM, "allocation failed");
   }
   ChainBufs &cb = x->traj_cb;
-  float *rstart;
-  if (!dalloc_n(x, &rstart, (size_t)x->C * x->d_pad)) return fail(x, PCV_E_OOM, "allocation failed");
+  float *rstart = x->rstart;
   const size_t row = sizeof(float) * x->d, pitch = sizeof(float) * x->d_pad;
   CK(cudaMemcpy2DAsync(cb.theta, pitch, theta0, row, row, x->C, cudaMemcpyDeviceToDevice, x->stream));
   CK(cudaMemcpy2DAsync(rstart, pitch, r0, row, row, x->C, cudaMemcpyDeviceToDevice, x->stream));
@@ -804,13 +984,16 @@ pcv_status pcv_trajectory(pcv_ctx *x, const float *theta0, const float *r0, int3
   ba.theta = cb.theta; ba.grad = cb.grad; ba.logp = cb.logp;
   ba.theta_p = cb.theta_p; ba.r = cb.r; ba.H0 = cb.H0;
   ba.eps = &x->st->eps; ba.minv = x->minv; ba.r_given = rstart;
+  ba.shadow_hi = x->tc ? cb.shadow_hi : nullptr;
+  ba.shadow_lo = x->tc ? cb.shadow_lo : nullptr;
+  ba.ld_shadow = x->KP;
   k_begin<<<(cb.C + 7) / 8, 256, 0, x->stream>>>(ba);
   CK(cudaGetLastError());
   GradArgs ga = grad_args(x, cb, true);
   for (int st = 1; st <= x->Lf; ++st) {
     ga.mode = st < x->Lf ? MODE_KICK_DRIFT : MODE_LAST_KICK;
     ga.need_ll = st == x->Lf;
-    s = launch_grad(x, ga);
+    s = launch_grad(x, ga, &cb);
     if (s != PCV_OK) return s;
   }
   CK(cudaMemcpy2DAsync(theta1, row, cb.theta_p, pitch, row, x->C, cudaMemcpyDeviceToDevice, x->stream));
@@ -886,14 +1069,16 @@ pcv_status pcv_time_leapfrog_kernel(pcv_ctx *x, int32_t reps, double *ms_per_lau
   const size_t n = sizeof(float) * (size_t)cb.C * x->d_pad;
   CK(cudaMemcpyAsync(cb.theta_p, cb.theta, n, cudaMemcpyDeviceToDevice, x->stream));
   CK(cudaMemsetAsync(cb.r, 0, n, x->stream));
+  pcv_status s = write_shadow(x, cb, cb.theta_p, x->d_pad);
+  if (s != PCV_OK) return s;
   GradArgs ga = grad_args(x, cb, true);
   ga.mode = MODE_KICK_DRIFT;
   ga.need_ll = 0;
-  pcv_status s = launch_grad(x, ga);                      // warm-up launch
+  s = launch_grad(x, ga, &cb);                            // warm-up launch
   if (s != PCV_OK) return s;
   CK(cudaEventRecord(x->ev0, x->stream));
   for (int i = 0; i < reps; ++i) {
-    s = launch_grad(x, ga);
+    s = launch_grad(x, ga, &cb);
     if (s != PCV_OK) return s;
   }
   CK(cudaEventRecord(x->ev1, x->stream));

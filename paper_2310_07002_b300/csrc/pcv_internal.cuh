@@ -179,6 +179,24 @@ constexpr float kLog2Pi = 1.8378770664093453f;
 constexpr double kLog2PiD = 1.8378770664093454835606594728112;
 constexpr double kLog2D = 0.69314718055994530942;
 
+// tensor-core path (k_grad_tc.cu)
+struct TcArgs {
+  int KP;                 // padded p in SMEM / global (64 or 128)
+  int KS;                 // GEMM1 K steps of 16 (ceil(p / 16))
+  int PN;                 // GEMM2 N (16 * ceil(p / 16))
+  int N_pad;              // rows padded to a multiple of the 128-row chunk
+  int J;                  // chunks per tile
+  int T;                  // chain tiles of 128
+  int n_cta;              // grid size
+  int max_seg;            // workspace segments per tile
+  int NS;                 // X pipeline stages
+  int need_lo;            // accumulate the theta lo part too (accurate eta)
+  const __nv_bfloat16 *yc;// N_pad: y - 1/2 (zero for padded rows)
+  float *ws;              // T x max_seg x (PN + 2) x 128
+  unsigned int *tickets;  // T
+  unsigned int *err;      // error flags (bit 0: wait time-out)
+};
+
 // launchers (k_grad_simt.cu)
 int simt_flat_pp(int p);
 size_t hier_smem_bytes(int PP, int G, int splits);

@@ -126,12 +126,14 @@ def gauss_blocks(N: int = 200, p: int = 5, K: int = 10, L: int = 4,
 
 
 def logistic_loo(N: int = 2000, p: int = 20, L: int = 8, seed: int = 1002,
-                 K: Optional[int] = None) -> Workload:
+                 K: Optional[int] = None, bf16: bool = False) -> Workload:
     """Logistic regression, leave-one-out (K = N folds, or the first K rows
     held out one at a time when K < N).  beta_true ~ N(0, 0.5^2),
-    prior beta ~ N(0, 2.5^2 I)."""
+    prior beta ~ N(0, 2.5^2 I).  bf16=True rounds X to bfloat16 values."""
     g = _rng(seed)
     X = g.standard_normal((N, p))
+    if bf16:
+        X = round_to_bf16(X)
     beta = 0.5 * g.standard_normal(p)
     y = (g.random(N) < _sigmoid(X @ beta)).astype(np.float64)
     K = N if K is None else K

@@ -1,0 +1,120 @@
+"""GPU parity of the BF16 tensor-core (tcgen05) path against the FP64
+oracle, through the C ABI.
+
+Inputs use a bfloat16-valued design matrix, so both sides see identical data
+and the error measures arithmetic only.  Tolerances (BF16 path):
+  log density, held-out log predictive: |d| / max(|ref|, 1) <= 1e-2 (stated
+    target; the hi/lo split of theta makes it far smaller in practice, and
+    the tighter bound 1e-4 is asserted too)
+  gradient: ||d||_2 / ||ref||_2 <= 1e-2
+  one L_f-step trajectory: ||d||_2 / ||ref||_2 <= 2e-2
+"""
+import numpy as np
+import pytest
+
+from paper_2310_07002_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_07002_b300.build import build
+    build()
+    return torch
+
+
+def rel_scalar(a, b):
+    return np.abs(a - b) / np.maximum(np.abs(b), 1.0)
+
+
+def rel_vec(a, b):
+    return np.linalg.norm(a - b, axis=-1) / np.maximum(np.linalg.norm(b, axis=-1), 1e-30)
+
+
+def bf16_workload(p):
+    # 9 row chunks with a ragged tail (1037 rows); positions span 3 chain tiles
+    if p <= 32:
+        return W.logistic_loo(N=1037, p=p, K=40, L=4, bf16=True)
+    w = W.logistic_large(N=1037, p=p, K=10, block=50, L=4)
+    return w
+
+
+@pytest.mark.parametrize("p", [20, 100])
+def test_bf16_log_density_and_gradient(torch, orc, p):
+    from paper_2310_07002_b300.pcv import PCV, BF16
+    w = bf16_workload(p)
+    pc = PCV.from_workload(w, precision=BF16)
+    prob = orc.problem_from_workload(w)
+    n = 300                                       # 128 + 128 + 44 positions
+    scale = 0.3 if p <= 32 else 0.1
+    tt = torch.tensor(W.random_theta(w.dim, n, scale=scale, seed=19), dtype=torch.float32, device="cuda")
+    folds = np.arange(n) % (w.K + 1)
+    fo = torch.tensor(folds, dtype=torch.int32, device="cuda")
+    lp, g, sh = pc.log_density(tt, fo, BF16)
+    torch.cuda.synchronize()
+    lp, g, sh = lp.cpu().numpy(), g.cpu().double().numpy(), sh.cpu().numpy()
+    th = tt.cpu().double().numpy()
+    lr = np.empty(n); sr = np.empty(n); gr = np.empty((n, w.dim))
+    for i in range(n):
+        k = int(folds[i])
+        lr[i], gr[i], sr[i] = orc.log_density(prob, -1 if k == w.K else k, th[i])
+    e_lp, e_sh, e_g = rel_scalar(lp, lr).max(), rel_scalar(sh, sr).max(), rel_vec(g, gr).max()
+    print("bf16 p=%d: logp %.2e shat %.2e grad %.2e" % (p, e_lp, e_sh, e_g))
+    assert e_lp <= 1e-4 and e_sh <= 1e-4
+    assert e_g <= 1e-2
+    pc.close()
+
+
+@pytest.mark.parametrize("p", [20, 100])
+def test_bf16_trajectory(torch, orc, p):
+    from paper_2310_07002_b300.pcv import PCV, BF16
+    w = bf16_workload(p)
+    eps = 0.01 if p <= 32 else 0.004
+    minv = np.ones(w.dim)
+    pc = PCV.from_workload(w, precision=BF16, step_size=eps, inv_mass_diag=minv)
+    prob = orc.problem_from_workload(w)
+    g = np.random.Generator(np.random.Philox(6))
+    th0 = (0.2 if p <= 32 else 0.05) * g.standard_normal((w.n_chains, w.dim))
+    r0 = g.standard_normal((w.n_chains, w.dim))
+    t0 = torch.tensor(th0, dtype=torch.float32, device="cuda")
+    rr0 = torch.tensor(r0, dtype=torch.float32, device="cuda")
+    th1, r1, lp1, _ = pc.trajectory(t0, rr0, BF16)
+    th1, r1, lp1 = th1.cpu().double().numpy(), r1.cpu().double().numpy(), lp1.cpu().numpy()
+    a0, b0 = t0.cpu().double().numpy(), rr0.cpu().double().numpy()
+    ref_th = np.empty_like(th1); ref_r = np.empty_like(r1); ref_lp = np.empty(w.n_chains)
+    for c in range(w.n_chains):
+        k = c // w.chains_per_fold
+        _, g0, _ = orc.log_density(prob, k, a0[c])
+        ref_th[c], ref_r[c], _, ref_lp[c], _ = orc.trajectory(prob, k, np.float32(eps), w.leapfrog_steps,
+                                                             minv, a0[c], b0[c], g0)
+    e_th = rel_vec(th1, ref_th).max()
+    e_r = rel_vec(r1, ref_r).max()
+    print("bf16 trajectory p=%d: theta %.2e r %.2e" % (p, e_th, e_r))
+    assert e_th <= 2e-2 and e_r <= 2e-2
+    pc.close()
+
+
+def test_bf16_and_fp32_runs_agree_within_mcse(torch):
+    # the same logistic CV problem sampled with the BF16 tensor-core path and
+    # the FP32 SIMT path: fold elpd within 4 combined MCSE
+    from paper_2310_07002_b300.pcv import PCV, BF16, FP32_SIMT
+    w = W.logistic_loo(N=600, p=12, K=24, L=8, bf16=True)
+    out = {}
+    for prec in (FP32_SIMT, BF16):
+        pc = PCV.from_workload(w, precision=prec)
+        pc.warmup(300, 300)
+        pc.sample(1000)
+        out[prec] = (pc.scores(), pc.diagnostics(), pc.accept_rate())
+        pc.close()
+    s32, d32, a32 = out[FP32_SIMT]
+    s16, d16, a16 = out[BF16]
+    comb = np.sqrt(s32["mcse"] ** 2 + s16["mcse"] ** 2)
+    z = np.abs(s32["elpd"] - s16["elpd"]) / comb
+    print("max z %.2f, rhat_max fp32 %.4f bf16 %.4f, accept %.3f %.3f" %
+          (z.max(), d32["rhat_max"], d16["rhat_max"], a32.mean(), a16.mean()))
+    assert z.max() < 4.5
+    assert d16["rhat_max"] < 1.1 and a16.mean() > 0.5
