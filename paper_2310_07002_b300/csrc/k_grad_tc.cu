@@ -79,6 +79,17 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile i
   }
   return true;
 }
+// Warp-uniform bounded wait: lane 0 waits, the outcome is broadcast, and
+// __syncwarp orders the other lanes after lane 0's acquire.  Keeps the
+// warp converged for the .sync.aligned tcgen05 instructions that follow.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                          unsigned int *err) {
+  int ok = 0;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag, err) ? 1 : 0;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __syncwarp();
+  return ok != 0;
+}
 // Bounded wait that ignores the abort flag (draining copies in flight).
 __device__ __noinline__ void mbar_wait_quiet(uint32_t bar, uint32_t parity) {
   const uint64_t t0 = global_ns();
@@ -350,9 +361,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         ll_tr = ll_te = 0.0f;
       }
       const int sb = i & 1, rb = i & 1;
-      if (!mbar_wait(smem_u32(&s_full[sb]), (i >> 1) & 1, abort_flag, ta.err)) break;
+      if (!warp_wait(smem_u32(&s_full[sb]), (i >> 1) & 1, abort_flag, ta.err)) break;
       tc_fence_after();
-      if (!mbar_wait(smem_u32(&r_empty[rb]), ((i >> 1) & 1) ^ 1, abort_flag, ta.err)) break;
+      // the X stage of this unit is still resident (its release needs this
+      // epilogue's R); waiting on its barrier makes the TMA-written y visible
+      if (!warp_wait(smem_u32(&x_full[i % NS]), (i / NS) & 1, abort_flag, ta.err)) break;
+      if (!warp_wait(smem_u32(&r_empty[rb]), ((i >> 1) & 1) ^ 1, abort_flag, ta.err)) break;
       const int n0 = j * kTN;
       const bool overlap = valid && (n0 < fd.excl_hi) && (n0 + kTN > fd.excl_lo);
       const uint32_t *yw = reinterpret_cast<const uint32_t *>(ys + (i % NS) * kTN * 2);
@@ -420,7 +434,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (lane == 0) mbar_arrive(smem_u32(&r_full[rb]));
       if (last) {
         // segment end: flush the G partial of this tile
-        if (!mbar_wait(smem_u32(g_full), seg & 1, abort_flag, ta.err)) break;
+        if (!warp_wait(smem_u32(g_full), seg & 1, abort_flag, ta.err)) break;
         tc_fence_after();
         const int b0 = owner_cta((long long)t * ta.J, U, ta.n_cta);
         const int sidx = blockIdx.x - b0;
