@@ -206,7 +206,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint64_t *g_full = bars + 18, *g_empty = bars + 19;
   uint32_t *tmem_base_slot = reinterpret_cast<uint32_t *>(bars + 20);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 21);
-  int *last_flag = reinterpret_cast<int *>(bars + 22);
+  volatile int *last_flag = reinterpret_cast<volatile int *>(bars + 22);
+  uint64_t *flush_bar = bars + 23, *decide_bar = bars + 24;   // epilogue-internal sync
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long U = (long long)ta.T * ta.J;
@@ -222,6 +223,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     mbar_init(smem_u32(th_full), 1); mbar_init(smem_u32(th_empty), 1);
     mbar_init(smem_u32(g_full), 1); mbar_init(smem_u32(g_empty), 4);
+    mbar_init(smem_u32(flush_bar), 4); mbar_init(smem_u32(decide_bar), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -451,17 +453,23 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(g_empty));
+        const int fl = seg;                       // flush count of this CTA (barrier phase)
         ++seg;
         ll_tr = ll_te = 0.0f;
+        // all four warps' partials are written and fenced before the ticket
         __threadfence();
-        asm volatile("bar.sync 1, 128;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(flush_bar));
+        if (!warp_wait(smem_u32(flush_bar), fl & 1, abort_flag, ta.err)) break;
         const int nseg = owner_cta((long long)t * ta.J + ta.J - 1, U, ta.n_cta) - b0 + 1;
         if (m == 0) {
+          __threadfence();
           const unsigned prev = atomicAdd(ta.tickets + t, 1u);
           *last_flag = (prev == (unsigned)nseg - 1);
           if (prev == (unsigned)nseg - 1) ta.tickets[t] = 0u;
+          mbar_arrive(smem_u32(decide_bar));
         }
-        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (!warp_wait(smem_u32(decide_bar), fl & 1, abort_flag, ta.err)) break;
         if (*last_flag && valid) {
           __threadfence();
           // sum the tile's segments in order, add the prior, update
@@ -522,7 +530,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 size_t tc_smem_bytes(int KP, int NS, int need_lo) {
   const size_t KA = KP / 64;
   size_t b = KA * kTM * 128 * (need_lo ? 2 : 1) + (size_t)NS * KA * kTN * 128 + 2 * (kTN / 64) * kTM * 128 +
-             (size_t)NS * kTN * 2 + 64 + 24 * 8;
+             (size_t)NS * kTN * 2 + 64 + 32 * 8;
   return b + 1024;   // alignment slack
 }
 
