@@ -37,6 +37,8 @@ FP32_SIMT_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 WORKLOADS = {
     "logistic_loo": lambda: W.logistic_loo(),        # N=2000, p=20, K=2000, L=8
     "logistic_large": lambda: W.logistic_large(),    # N=1e5, p=100, K=1000, L=16
+    # a quarter-size case of the same kernel for multi-pass profiler captures
+    "logistic_large_q": lambda: W.logistic_large(N=25_000, K=250),
     "gauss_blocks": lambda: W.gauss_blocks(),
     "hier_logo": lambda: W.hier_logo(),
     "ar2_hvblock": lambda: W.ar2_hvblock(),

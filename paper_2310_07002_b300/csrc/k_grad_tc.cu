@@ -11,9 +11,12 @@
 // Theta is stored scaled by 1/2 (exact in binary floating point), so S is
 // eta/2 and sigmoid(eta) = 1/2 + tanh(S)/2.  The same SMEM X tile is the
 // K-major B operand of the first GEMM and the MN-major B operand of the
-// second.  When log densities are needed (last leapfrog step, evaluations)
-// Theta is split into bf16 hi + lo parts and S accumulates both, giving an
-// FP32-accurate eta for the FP64 accept test.
+// second.  Theta is split into bf16 hi + lo parts and S accumulates both,
+// giving an FP32-accurate eta: with the hi part alone the gradient is a
+// piecewise-constant function of theta whose error (a few percent of a
+// posterior standard deviation) leaves HMC exact but slows its mixing.
+// Where log densities are needed (last leapfrog step, evaluations) the
+// epilogue runs in FP32 and also sums the masked log likelihoods.
 //
 // Work: persistent CTAs (one per SM) take equal contiguous ranges of the
 // flattened (chain tile, row chunk) units ("stream-K").  A CTA flushes its G
@@ -344,7 +347,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int q = warp & 3;                        // TMEM lane quarter of this warp
     const int m = q * 32 + lane;                   // chain row within the tile
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-    const bool accurate = ta.need_lo != 0;
+    const bool accurate = ta.accurate != 0;
     const uint32_t neg_half2 = 0xBF00BF00u;        // (-0.5, -0.5) in bf16x2
     int seg = 0;
     int t_cur = -1, c = 0;

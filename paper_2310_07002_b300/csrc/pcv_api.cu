@@ -221,8 +221,11 @@ TcArgs tc_args(pcv_ctx *x, int C, bool need_lo) {
   const long long U = (long long)t.T * t.J;
   t.n_cta = (int)std::min<long long>(x->n_sm, U);
   t.max_seg = tc_segments_per_tile(t.T, t.J, t.n_cta);
-  t.need_lo = need_lo ? 1 : 0;
-  t.NS = need_lo ? 2 : 3;
+  // theta hi + lo on every step (see k_grad_tc.cu); FP32 epilogue when
+  // log densities are needed
+  t.need_lo = 1;
+  t.accurate = need_lo ? 1 : 0;
+  t.NS = tc_smem_bytes(t.KP, 3, 1) <= 227 * 1024 ? 3 : 2;
   t.yc = x->yc16;
   t.ws = x->ws_tc;
   t.tickets = x->tickets_tc;
@@ -281,7 +284,7 @@ pcv_status launch_grad(pcv_ctx *x, GradArgs a, const ChainBufs *cb = nullptr) {
     pcv_status s = ensure_ws_tc(x, a.C);
     if (s != PCV_OK) return s;
     TcArgs t = tc_args(x, a.C, a.need_ll != 0);
-    CK(launch_grad_tc(x->tm_x, cb->tm_hi, a.need_ll ? cb->tm_lo : cb->tm_hi, x->pb, a, t, x->stream));
+    CK(launch_grad_tc(x->tm_x, cb->tm_hi, cb->tm_lo, x->pb, a, t, x->stream));
     return PCV_OK;
   }
   pcv_status s = ensure_ws(x, a.C, a.splits);

@@ -190,7 +190,8 @@ struct TcArgs {
   int n_cta;              // grid size
   int max_seg;            // workspace segments per tile
   int NS;                 // X pipeline stages
-  int need_lo;            // accumulate the theta lo part too (accurate eta)
+  int need_lo;            // accumulate the theta lo part too (FP32-accurate eta)
+  int accurate;           // FP32 epilogue with log densities (else the bf16x2 fast path)
   const __nv_bfloat16 *yc;// N_pad: y - 1/2 (zero for padded rows)
   float *ws;              // T x max_seg x (PN + 2) x 128
   unsigned int *tickets;  // T
