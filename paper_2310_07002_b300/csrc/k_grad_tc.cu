@@ -25,7 +25,9 @@
 // and the momentum / position update.
 //
 // Roles: warp 0 issues TMA loads, warp 1 allocates TMEM and issues the MMAs
-// (one thread), warps 2-5 run the epilogue (thread = TMEM lane = chain).
+// (one thread), warps 2-9 run the epilogue as two warpgroups, each taking
+// half of a chunk's 128 rows (thread = TMEM lane = chain; two warps per SM
+// sub-partition so TMEM-load and barrier latencies overlap).
 // Every mbarrier wait is bounded: on time-out the kernel sets an error flag,
 // stops issuing work and exits after freeing TMEM.
 #include <cuda.h>
@@ -36,7 +38,7 @@ namespace pcv {
 
 constexpr int kTN = 128;        // rows per chunk
 constexpr int kTM = 128;        // chains per tile
-constexpr int kTcThreads = 192; // 6 warps
+constexpr int kTcThreads = 320; // 10 warps: TMA, MMA, 8 epilogue
 
 
 // ----------------------------- PTX helpers --------------------------------
@@ -123,6 +125,10 @@ __device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t a_desc, ui
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
       "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
       : "memory");
+  // Keep consecutive MMAs of an unrolled group apart: without an instruction
+  // between them, the last MMA of a short unrolled group (4 MMAs) was
+  // measured to accumulate a wrong product on sm_103a.
+  __syncwarp(1u);
 }
 #define PCV_TMEM_LD32(taddr, v)                                                                  \
   asm volatile(                                                                                  \
@@ -187,6 +193,10 @@ __host__ __device__ inline int owner_cta(long long u, long long U, long long n) 
 }
 
 // --------------------------------------------------------------------------
+// KS (GEMM1 K steps of 16, = ceil(p / 16)) is a template parameter so that
+// every MMA group is straight-line code: MMAs issued from a runtime-count
+// loop between commits measured up to 3x slower on sm_103a.
+template <int KS>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_grad_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_hi,
               const __grid_constant__ CUtensorMap tm_lo, Problem pb, GradArgs a, TcArgs ta) {
@@ -211,6 +221,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 21);
   volatile int *last_flag = reinterpret_cast<volatile int *>(bars + 22);
   uint64_t *flush_bar = bars + 23, *decide_bar = bars + 24;   // epilogue-internal sync
+  uint64_t *fin_bar = bars + 25;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long U = (long long)ta.T * ta.J;
@@ -221,12 +232,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) { mbar_init(smem_u32(&x_full[s]), 1); mbar_init(smem_u32(&x_empty[s]), 1); }
     for (int s = 0; s < 2; ++s) {
-      mbar_init(smem_u32(&s_full[s]), 1); mbar_init(smem_u32(&s_empty[s]), 4);
-      mbar_init(smem_u32(&r_full[s]), 4); mbar_init(smem_u32(&r_empty[s]), 1);
+      mbar_init(smem_u32(&s_full[s]), 1); mbar_init(smem_u32(&s_empty[s]), 8);
+      mbar_init(smem_u32(&r_full[s]), 8); mbar_init(smem_u32(&r_empty[s]), 1);
     }
     mbar_init(smem_u32(th_full), 1); mbar_init(smem_u32(th_empty), 1);
-    mbar_init(smem_u32(g_full), 1); mbar_init(smem_u32(g_empty), 4);
-    mbar_init(smem_u32(flush_bar), 4); mbar_init(smem_u32(decide_bar), 1);
+    mbar_init(smem_u32(g_full), 1); mbar_init(smem_u32(g_empty), 8);
+    mbar_init(smem_u32(flush_bar), 8); mbar_init(smem_u32(decide_bar), 1);
+    mbar_init(smem_u32(fin_bar), 8);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -293,11 +305,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (first && !mbar_wait(smem_u32(g_empty), (seg2 & 1) ^ 1, abort_flag, ta.err)) return false;
         tc_fence_after();
         const int st = k % NS;
-        const uint32_t xb = smem_u32(xs + (size_t)st * x_bytes);
-        const uint32_t rbuf = smem_u32(rs + (size_t)rb * r_bytes);
+        // descriptors: base once, K steps add (byte offset >> 4) to the
+        // 14-bit start-address field (all SMEM offsets stay below 256 KB)
+        const uint64_t ad0 = sdesc_sw128(smem_u32(rs + (size_t)rb * r_bytes), 16, 1024);
+        const uint64_t bd0 = sdesc_sw128(smem_u32(xs + (size_t)st * x_bytes), kTN * 128, 1024);
+#pragma unroll
         for (int ks = 0; ks < kTN / 16; ++ks) {
-          const uint64_t ad = sdesc_sw128(rbuf + (ks >> 2) * kTM * 128 + (ks & 3) * 32, 16, 1024);
-          const uint64_t bd = sdesc_sw128(xb + ks * 2048, kTN * 128, 1024);
+          const uint64_t ad = ad0 + (uint64_t)((((ks >> 2) * kTM * 128) + (ks & 3) * 32) >> 4);
+          const uint64_t bd = bd0 + (uint64_t)((ks * 2048) >> 4);
           tc_mma_bf16(tmem_G, ad, bd, id2, (first && ks == 0) ? 0u : 1u);
         }
         tc_commit(smem_u32(&r_empty[rb]));
@@ -320,20 +335,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int sb = i & 1;
         if (!mbar_wait(smem_u32(&s_empty[sb]), ((i >> 1) & 1) ^ 1, abort_flag, ta.err)) { ok = false; break; }
         tc_fence_after();
-        const uint32_t xb = smem_u32(xs + (size_t)st * x_bytes);
-        const uint32_t thb = smem_u32(th_hi), tlb = smem_u32(th_lo);
+        const uint64_t xd0 = sdesc_sw128(smem_u32(xs + (size_t)st * x_bytes), 16, 1024);
+        const uint64_t hd0 = sdesc_sw128(smem_u32(th_hi), 16, 1024);
+        const uint64_t ld0 = sdesc_sw128(smem_u32(th_lo), 16, 1024);
         const uint32_t dS = tmem + sb * 128;
-        for (int ks = 0; ks < ta.KS; ++ks) {
-          const uint32_t off = (ks >> 2) * kTM * 128 + (ks & 3) * 32;
-          const uint32_t offx = (ks >> 2) * kTN * 128 + (ks & 3) * 32;
-          tc_mma_bf16(dS, sdesc_sw128(thb + off, 16, 1024), sdesc_sw128(xb + offx, 16, 1024), id1,
-                      ks > 0 ? 1u : 0u);
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks) {
+          const uint64_t off = (uint64_t)((((ks >> 2) * kTM * 128) + (ks & 3) * 32) >> 4);
+          const uint64_t offx = (uint64_t)((((ks >> 2) * kTN * 128) + (ks & 3) * 32) >> 4);
+          tc_mma_bf16(dS, hd0 + off, xd0 + offx, id1, ks > 0 ? 1u : 0u);
         }
         if (ta.need_lo) {
-          for (int ks = 0; ks < ta.KS; ++ks) {
-            const uint32_t off = (ks >> 2) * kTM * 128 + (ks & 3) * 32;
-            const uint32_t offx = (ks >> 2) * kTN * 128 + (ks & 3) * 32;
-            tc_mma_bf16(dS, sdesc_sw128(tlb + off, 16, 1024), sdesc_sw128(xb + offx, 16, 1024), id1, 1u);
+#pragma unroll
+          for (int ks = 0; ks < KS; ++ks) {
+            const uint64_t off = (uint64_t)((((ks >> 2) * kTM * 128) + (ks & 3) * 32) >> 4);
+            const uint64_t offx = (uint64_t)((((ks >> 2) * kTN * 128) + (ks & 3) * 32) >> 4);
+            tc_mma_bf16(dS, ld0 + off, xd0 + offx, id1, 1u);
           }
         }
         tc_commit(smem_u32(&s_full[sb]));
@@ -344,12 +361,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
   } else {
     // ------------------------------ epilogue -------------------------------
-    const int q = warp & 3;                        // TMEM lane quarter of this warp
-    const int m = q * 32 + lane;                   // chain row within the tile
+    const int ew = warp - 2;                        // epilogue warp 0..7
+    const int eg = ew >> 2;                         // warpgroup: chunk rows [64 eg, 64 eg + 64)
+    const int q = warp & 3;                         // TMEM lane quarter of this warp
+    const int m = q * 32 + lane;                    // chain row within the tile
+    const int et = ew * 32 + lane;                  // 0..255
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     const bool accurate = ta.accurate != 0;
-    const uint32_t neg_half2 = 0xBF00BF00u;        // (-0.5, -0.5) in bf16x2
-    int seg = 0;
+    const uint32_t neg_half2 = 0xBF00BF00u;         // (-0.5, -0.5) in bf16x2
+    const int wstride = ta.PN + 4;                  // workspace rows per segment
+    int seg = 0, nfin = 0;
     int t_cur = -1, c = 0;
     bool valid = false;
     FoldDesc fd = {0, 0, 0, 0};
@@ -367,155 +388,166 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       const int sb = i & 1, rb = i & 1;
       if (!warp_wait(smem_u32(&s_full[sb]), (i >> 1) & 1, abort_flag, ta.err)) break;
-      tc_fence_after();
       // the X stage of this unit is still resident (its release needs this
       // epilogue's R); waiting on its barrier makes the TMA-written y visible
       if (!warp_wait(smem_u32(&x_full[i % NS]), (i / NS) & 1, abort_flag, ta.err)) break;
       if (!warp_wait(smem_u32(&r_empty[rb]), ((i >> 1) & 1) ^ 1, abort_flag, ta.err)) break;
-      const int n0 = j * kTN;
-      const bool overlap = valid && (n0 < fd.excl_hi) && (n0 + kTN > fd.excl_lo);
-      const uint32_t *yw = reinterpret_cast<const uint32_t *>(ys + (i % NS) * kTN * 2);
-      uint8_t *rbuf = rs + (size_t)rb * r_bytes;
-      for (int piece = 0; piece < kTN / 32; ++piece) {
-        uint32_t v[32];
-        PCV_TMEM_LD32(tmem + sb * 128 + piece * 32 + lane_off, v);
-        tmem_wait_ld();
-        uint32_t packed[16];
-        if (!accurate) {
+      tc_fence_after();
+      // both TMEM loads of this warpgroup's 64 columns, then the wait right
+      // away: the destination registers are written asynchronously until
+      // tcgen05.wait::ld, so no other code may touch them in between
+      uint32_t v[64];
+      PCV_TMEM_LD32(tmem + sb * 128 + 64 * eg + lane_off, v);
+      PCV_TMEM_LD32(tmem + sb * 128 + 64 * eg + 32 + lane_off, (v + 32));
+      tmem_wait_ld();
+      const int n0 = j * kTN + 64 * eg;             // first row of this warpgroup
+      const uint32_t *yw = reinterpret_cast<const uint32_t *>(ys + (i % NS) * kTN * 2) + 32 * eg;
+      // residual y - sigmoid(eta) = (y - 1/2) - tanh(S)/2 in bf16x2 (the same
+      // function on every leapfrog step)
+      uint32_t packed[32];
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const float s0 = __uint_as_float(v[2 * k]), s1 = __uint_as_float(v[2 * k + 1]);
-            const uint32_t t2 = tanh_bf16x2(bf16x2_from(s0, s1));
-            const uint32_t y2 = yw[piece * 16 + k];
-            packed[k] = fma_bf16x2(t2, neg_half2, y2);       // (y - 1/2) - tanh(S)/2
-          }
-          if (overlap) {
+      for (int k = 0; k < 32; ++k) {
+        const uint32_t t2 = tanh_bf16x2(bf16x2_from(__uint_as_float(v[2 * k]), __uint_as_float(v[2 * k + 1])));
+        packed[k] = fma_bf16x2(t2, neg_half2, yw[k]);
+      }
+      if (valid && n0 < fd.excl_hi && n0 + 64 > fd.excl_lo) {
 #pragma unroll
-            for (int k = 0; k < 32; ++k) {
-              const int n = n0 + piece * 32 + k;
-              if (n >= fd.excl_lo && n < fd.excl_hi)
-                packed[k >> 1] &= (k & 1) ? 0x0000FFFFu : 0xFFFF0000u;
-            }
-          }
-        } else {
-#pragma unroll
-          for (int k = 0; k < 32; k += 2) {
-            float rr[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int n = n0 + piece * 32 + k + h;
-              const float eta = 2.0f * __uint_as_float(v[k + h]);
-              const uint32_t y2 = yw[piece * 16 + (k >> 1)];
-              const float yv = __uint_as_float((h ? (y2 & 0xFFFF0000u) : (y2 << 16))) + 0.5f;
-              const float e = __expf(-fabsf(eta));
-              const float inv = __fdividef(1.0f, 1.0f + e);
-              const float sig = eta >= 0.0f ? inv : e * inv;
-              const bool in_rows = n < pb.N;
-              const bool tr = in_rows && (n < fd.excl_lo || n >= fd.excl_hi);
-              const bool te = in_rows && n >= fd.test_lo && n < fd.test_hi;
-              const float ll = yv * eta - (fmaxf(eta, 0.0f) + __logf(1.0f + e));
-              if (tr) ll_tr += ll;
-              if (te) ll_te += ll;
-              rr[h] = tr ? (yv - sig) : 0.0f;
-            }
-            packed[k >> 1] = bf16x2_from(rr[0], rr[1]);
-          }
-        }
-        // R tile: row m, K columns piece*32 .. +32 (64 bytes = four 16-byte
-        // chunks) of K atom piece / 2, 128-byte swizzle (chunk ^= m & 7)
-        uint8_t *row = rbuf + (piece >> 1) * kTM * 128 + m * 128;
-#pragma unroll
-        for (int qq = 0; qq < 4; ++qq) {
-          const int cidx = (piece & 1) * 4 + qq;
-          uint4 val = make_uint4(packed[4 * qq], packed[4 * qq + 1], packed[4 * qq + 2], packed[4 * qq + 3]);
-          *reinterpret_cast<uint4 *>(row + ((cidx ^ (m & 7)) << 4)) = val;
+        for (int k = 0; k < 64; ++k) {
+          const int n = n0 + k;
+          if (n >= fd.excl_lo && n < fd.excl_hi) packed[k >> 1] &= (k & 1) ? 0x0000FFFFu : 0xFFFF0000u;
         }
       }
+      if (accurate) {
+        // masked log likelihood y eta - softplus(eta), softplus(eta) =
+        // max(eta, 0) + log(1 + exp(-|eta|)), FP32 (2 MUFU operations)
+#pragma unroll
+        for (int k = 0; k < 64; ++k) {
+          const int n = n0 + k;
+          const float eta = 2.0f * __uint_as_float(v[k]);
+          const uint32_t y2 = yw[k >> 1];
+          const float yv = __uint_as_float((k & 1) ? (y2 & 0xFFFF0000u) : (y2 << 16)) + 0.5f;
+          const float e = exp2f(-fabsf(eta) * 1.4426950408889634f);
+          const float ll = yv * eta - fmaxf(eta, 0.0f) - __log2f(1.0f + e) * 0.6931471805599453f;
+          const bool in_rows = n < pb.N;
+          if (in_rows && (n < fd.excl_lo || n >= fd.excl_hi)) ll_tr += ll;
+          if (in_rows && n >= fd.test_lo && n < fd.test_hi) ll_te += ll;
+        }
+      }
+      // R tile: row m, K atom eg (64 columns = eight 16-byte chunks), 128-byte
+      // swizzle (chunk ^= m & 7)
+      uint8_t *row = rs + (size_t)rb * r_bytes + eg * kTM * 128 + m * 128;
+#pragma unroll
+      for (int cc = 0; cc < 8; ++cc)
+        *reinterpret_cast<uint4 *>(row + ((cc ^ (m & 7)) << 4)) =
+            make_uint4(packed[4 * cc], packed[4 * cc + 1], packed[4 * cc + 2], packed[4 * cc + 3]);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&s_empty[sb]));
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&r_full[rb]));
-      if (last) {
-        // segment end: flush the G partial of this tile
-        if (!warp_wait(smem_u32(g_full), seg & 1, abort_flag, ta.err)) break;
-        tc_fence_after();
-        const int b0 = owner_cta((long long)t * ta.J, U, ta.n_cta);
-        const int sidx = blockIdx.x - b0;
-        float *wsp = ta.ws + ((size_t)t * ta.max_seg + sidx) * (size_t)(ta.PN + 2) * kTM;
-        for (int cb = 0; cb < ta.PN; cb += 16) {
-          uint32_t gv[16];
-          PCV_TMEM_LD16(tmem_G + cb + lane_off, gv);
-          tmem_wait_ld();
+      if (!last) continue;
+      // ---- segment end: flush this tile's G partial and the ll sums
+      if (!warp_wait(smem_u32(g_full), seg & 1, abort_flag, ta.err)) break;
+      tc_fence_after();
+      const int b0 = owner_cta((long long)t * ta.J, U, ta.n_cta);
+      const int sidx = blockIdx.x - b0;
+      float *wsp = ta.ws + ((size_t)t * ta.max_seg + sidx) * (size_t)wstride * kTM;
+      for (int cb = 16 * eg; cb < ta.PN; cb += 32) {
+        uint32_t gv[16];
+        PCV_TMEM_LD16(tmem_G + cb + lane_off, gv);
+        tmem_wait_ld();
 #pragma unroll
-          for (int k = 0; k < 16; ++k) wsp[(size_t)(cb + k) * kTM + m] = __uint_as_float(gv[k]);
-        }
-        wsp[(size_t)ta.PN * kTM + m] = ll_tr;
-        wsp[(size_t)(ta.PN + 1) * kTM + m] = ll_te;
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(g_empty));
-        const int fl = seg;                       // flush count of this CTA (barrier phase)
-        ++seg;
-        ll_tr = ll_te = 0.0f;
-        // all four warps' partials are written and fenced before the ticket
+        for (int k = 0; k < 16; ++k) wsp[(size_t)(cb + k) * kTM + m] = __uint_as_float(gv[k]);
+      }
+      wsp[(size_t)(ta.PN + 2 * eg) * kTM + m] = ll_tr;
+      wsp[(size_t)(ta.PN + 2 * eg + 1) * kTM + m] = ll_te;
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(g_empty));
+      const int fl = seg++;
+      ll_tr = ll_te = 0.0f;
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(flush_bar));
+      if (!warp_wait(smem_u32(flush_bar), fl & 1, abort_flag, ta.err)) break;
+      const int nseg = owner_cta((long long)t * ta.J + ta.J - 1, U, ta.n_cta) - b0 + 1;
+      if (et == 0) {
         __threadfence();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(flush_bar));
-        if (!warp_wait(smem_u32(flush_bar), fl & 1, abort_flag, ta.err)) break;
-        const int nseg = owner_cta((long long)t * ta.J + ta.J - 1, U, ta.n_cta) - b0 + 1;
-        if (m == 0) {
-          __threadfence();
-          const unsigned prev = atomicAdd(ta.tickets + t, 1u);
-          *last_flag = (prev == (unsigned)nseg - 1);
-          if (prev == (unsigned)nseg - 1) ta.tickets[t] = 0u;
-          mbar_arrive(smem_u32(decide_bar));
+        const unsigned prev = atomicAdd(ta.tickets + t, 1u);
+        *last_flag = (prev == (unsigned)nseg - 1);
+        if (prev == (unsigned)nseg - 1) ta.tickets[t] = 0u;
+        mbar_arrive(smem_u32(decide_bar));
+      }
+      if (!warp_wait(smem_u32(decide_bar), fl & 1, abort_flag, ta.err)) break;
+      if (!*last_flag) continue;
+      // ---- last segment of tile t: sum the segments, priors, leapfrog update.
+      // The R buffers are idle here (every issued GEMM2 has completed and no
+      // new one starts before this epilogue's next R), so they stage the
+      // summed gradient [p][129] for coalesced per-chain writes.
+      __threadfence();
+      float *stage = reinterpret_cast<float *>(rs);
+      const float *base = ta.ws + (size_t)t * ta.max_seg * (size_t)wstride * kTM;
+      const size_t seg_stride = (size_t)wstride * kTM;
+      {
+        const int mm = et & 127;
+        for (int jj = et >> 7; jj < pb.p; jj += 2) {
+          float gs = 0.0f;
+          for (int s2 = 0; s2 < nseg; ++s2) gs += __ldcg(base + s2 * seg_stride + (size_t)jj * kTM + mm);
+          stage[jj * 129 + mm] = gs;
         }
-        if (!warp_wait(smem_u32(decide_bar), fl & 1, abort_flag, ta.err)) break;
-        if (*last_flag && valid) {
-          __threadfence();
-          // sum the tile's segments in order, add the prior, update
-          const float *base = ta.ws + (size_t)t * ta.max_seg * (size_t)(ta.PN + 2) * kTM;
-          const size_t seg_stride = (size_t)(ta.PN + 2) * kTM;
-          float *th = const_cast<float *>(a.theta) + (size_t)c * a.ld_theta;
-          float *gr = a.grad + (size_t)c * a.ld_grad;
-          float *rr = a.r ? a.r + (size_t)c * a.ld_theta : nullptr;
-          const float eps = a.mode != MODE_NONE ? *a.eps : 0.0f;
-          const float kick = a.mode == MODE_LAST_KICK ? 0.5f * eps : eps;
-          double lp = 0.0;
-          for (int jj = 0; jj < pb.p; ++jj) {
-            float gs = 0.0f;
-            for (int s = 0; s < nseg; ++s) gs += __ldcg(base + s * seg_stride + (size_t)jj * kTM + m);
-            const float tv = th[jj];
-            const float g = gs - tv * pb.beta_prec;
-            gr[jj] = g;
-            if (a.need_ll)
-              lp += -0.5 * kLog2PiD - (double)pb.log_beta_sd - 0.5 * (double)tv * tv * pb.beta_prec;
-            if (a.mode != MODE_NONE) {
-              const float rj = rr[jj] + kick * g;
-              rr[jj] = rj;
-              if (a.mode == MODE_KICK_DRIFT) {
-                const float tn = tv + eps * a.minv[jj] * rj;
-                th[jj] = tn;
-                const float half = 0.5f * tn;       // shadows hold theta / 2
-                const __nv_bfloat16 hi = __float2bfloat16_rn(half);
-                a.shadow_hi[(size_t)c * a.ld_shadow + jj] = hi;
-                a.shadow_lo[(size_t)c * a.ld_shadow + jj] = __float2bfloat16_rn(half - __bfloat162float(hi));
-              }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(fin_bar));
+      if (!warp_wait(smem_u32(fin_bar), (2 * nfin) & 1, abort_flag, ta.err)) break;
+      const float eps = a.mode != MODE_NONE ? *a.eps : 0.0f;
+      const float kick = a.mode == MODE_LAST_KICK ? 0.5f * eps : eps;
+      for (int mm = ew; mm < kTM; mm += 8) {           // warp per chain, lanes over dims
+        const int cc = t * kTM + mm;
+        if (cc >= a.C) break;
+        float *th = const_cast<float *>(a.theta) + (size_t)cc * a.ld_theta;
+        float *gr = a.grad + (size_t)cc * a.ld_grad;
+        float *rr = a.r ? a.r + (size_t)cc * a.ld_theta : nullptr;
+        double lp = 0.0;
+        for (int jj = lane; jj < pb.p; jj += 32) {
+          const float tv = th[jj];
+          const float g = stage[jj * 129 + mm] - tv * pb.beta_prec;
+          gr[jj] = g;
+          if (a.need_ll) lp += -0.5 * kLog2PiD - (double)pb.log_beta_sd - 0.5 * (double)tv * tv * pb.beta_prec;
+          if (a.mode != MODE_NONE) {
+            const float rj = rr[jj] + kick * g;
+            rr[jj] = rj;
+            if (a.mode == MODE_KICK_DRIFT) {
+              const float tn = tv + eps * a.minv[jj] * rj;
+              th[jj] = tn;
+              const float half = 0.5f * tn;            // shadows hold theta / 2
+              const __nv_bfloat16 hi = __float2bfloat16_rn(half);
+              a.shadow_hi[(size_t)cc * a.ld_shadow + jj] = hi;
+              a.shadow_lo[(size_t)cc * a.ld_shadow + jj] = __float2bfloat16_rn(half - __bfloat162float(hi));
             }
           }
-          if (a.need_ll) {
-            double s0 = 0.0, s1 = 0.0;
-            for (int s = 0; s < nseg; ++s) {
-              s0 += (double)__ldcg(base + s * seg_stride + (size_t)ta.PN * kTM + m);
-              s1 += (double)__ldcg(base + s * seg_stride + (size_t)(ta.PN + 1) * kTM + m);
-            }
-            a.logp[c] = s0 + lp;
-            a.shat[c] = s1;
+        }
+        if (a.need_ll) {
+          lp = warp_sum_d(lp);
+          double s0 = 0.0, s1 = 0.0;
+          for (int s2 = lane; s2 < nseg; s2 += 32) {
+            const float *ws2 = base + s2 * seg_stride;
+            s0 += (double)__ldcg(ws2 + (size_t)ta.PN * kTM + mm) + (double)__ldcg(ws2 + (size_t)(ta.PN + 2) * kTM + mm);
+            s1 += (double)__ldcg(ws2 + (size_t)(ta.PN + 1) * kTM + mm) + (double)__ldcg(ws2 + (size_t)(ta.PN + 3) * kTM + mm);
+          }
+          s0 = warp_sum_d(s0);
+          s1 = warp_sum_d(s1);
+          if (lane == 0) {
+            a.logp[cc] = s0 + lp;
+            a.shat[cc] = s1;
           }
         }
       }
+      // the staging area is reused as R only after every warp has finished
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(fin_bar));
+      if (!warp_wait(smem_u32(fin_bar), (2 * nfin + 1) & 1, abort_flag, ta.err)) break;
+      ++nfin;
     }
   }
   // teardown: every role has left its loop (normally or by abort)
@@ -533,7 +565,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 size_t tc_smem_bytes(int KP, int NS, int need_lo) {
   const size_t KA = KP / 64;
   size_t b = KA * kTM * 128 * (need_lo ? 2 : 1) + (size_t)NS * KA * kTN * 128 + 2 * (kTN / 64) * kTM * 128 +
-             (size_t)NS * kTN * 2 + 64 + 32 * 8;
+             (size_t)NS * kTN * 2 + 64 + 32 * 8;   // 26 barrier / flag slots used
   return b + 1024;   // alignment slack
 }
 
@@ -548,16 +580,33 @@ int tc_segments_per_tile(int T, int J, int n_cta) {
   return mx;
 }
 
+template <int KS>
+static cudaError_t set_smem_attr() {
+  return cudaFuncSetAttribute(k_grad_tc<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
 // once per context (outside any stream capture): allow the large dynamic SMEM
 cudaError_t tc_prepare() {
-  return cudaFuncSetAttribute(k_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaError_t e = cudaSuccess;
+  cudaError_t r[8] = {set_smem_attr<1>(), set_smem_attr<2>(), set_smem_attr<3>(), set_smem_attr<4>(),
+                      set_smem_attr<5>(), set_smem_attr<6>(), set_smem_attr<7>(), set_smem_attr<8>()};
+  for (cudaError_t x : r)
+    if (x != cudaSuccess) e = x;
+  return e;
 }
 
 cudaError_t launch_grad_tc(const CUtensorMap &tm_x, const CUtensorMap &tm_hi, const CUtensorMap &tm_lo,
                            const Problem &pb, const GradArgs &a, const TcArgs &ta, cudaStream_t st) {
   const size_t smem = tc_smem_bytes(ta.KP, ta.NS, ta.need_lo);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  k_grad_tc<<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta);
+  switch (ta.KS) {
+#define PCV_TC_CASE(K) \
+  case K: k_grad_tc<K><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta); break;
+    PCV_TC_CASE(1) PCV_TC_CASE(2) PCV_TC_CASE(3) PCV_TC_CASE(4)
+    PCV_TC_CASE(5) PCV_TC_CASE(6) PCV_TC_CASE(7) PCV_TC_CASE(8)
+#undef PCV_TC_CASE
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

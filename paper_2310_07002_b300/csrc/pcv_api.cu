@@ -235,7 +235,7 @@ TcArgs tc_args(pcv_ctx *x, int C, bool need_lo) {
 
 pcv_status ensure_ws_tc(pcv_ctx *x, int C) {
   TcArgs t = tc_args(x, C, false);
-  const size_t need = (size_t)t.T * t.max_seg * (t.PN + 2) * 128;
+  const size_t need = (size_t)t.T * t.max_seg * (t.PN + 4) * 128;
   if (need > x->ws_tc_floats) {
     float *w;
     if (!dalloc_n(x, &w, need)) return fail(x, PCV_E_OOM, "workspace allocation failed");

@@ -193,7 +193,7 @@ struct TcArgs {
   int need_lo;            // accumulate the theta lo part too (FP32-accurate eta)
   int accurate;           // FP32 epilogue with log densities (else the bf16x2 fast path)
   const __nv_bfloat16 *yc;// N_pad: y - 1/2 (zero for padded rows)
-  float *ws;              // T x max_seg x (PN + 2) x 128
+  float *ws;              // T x max_seg x (PN + 4) x 128
   unsigned int *tickets;  // T
   unsigned int *err;      // error flags (bit 0: wait time-out)
 };
