@@ -5,8 +5,12 @@
 // GEMMs in BF16 with FP32 accumulation:
 //
 //   S = Theta_tile . X_chunk^T      (128 chains x 128 rows, K = p)   -> TMEM
-//   R = mask .* (y - sigmoid(2 S))  (epilogue, BF16)                 -> SMEM
+//   R = mask .* (y - sigmoid(2 S))  (epilogue, BF16)                 -> TMEM
 //   G += R . X_chunk                (128 chains x p, K = 128 rows)   -> TMEM
+//
+// R is the A operand of the second GEMM straight from TMEM, so shared memory
+// carries only Theta, X and y: with both operands of both GEMMs in SMEM the
+// MMAs alone saturate its bandwidth.
 //
 // Theta is stored scaled by 1/2 (exact in binary floating point), so S is
 // eta/2 and sigmoid(eta) = 1/2 + tanh(S)/2.  The same SMEM X tile is the
@@ -24,8 +28,10 @@
 // (atomic ticket, no spinning) sums the segments in order and applies priors
 // and the momentum / position update.
 //
-// Roles: warp 0 issues TMA loads, warp 1 allocates TMEM and issues the MMAs
-// (one thread), warps 2-9 run the epilogue as two warpgroups, each taking
+// Roles: warp 0 issues TMA loads, warp 1 allocates TMEM and issues the
+// first GEMM (one thread), warp 10 issues the second GEMM (one thread, so
+// that waiting for the epilogue never delays the first GEMM of later
+// chunks), warps 2-9 run the epilogue as two warpgroups, each taking
 // half of a chunk's 128 rows (thread = TMEM lane = chain; two warps per SM
 // sub-partition so TMEM-load and barrier latencies overlap).
 // Every mbarrier wait is bounded: on time-out the kernel sets an error flag,
@@ -38,7 +44,7 @@ namespace pcv {
 
 constexpr int kTN = 128;        // rows per chunk
 constexpr int kTM = 128;        // chains per tile
-constexpr int kTcThreads = 320; // 10 warps: TMA, MMA, 8 epilogue
+constexpr int kTcThreads = 352; // 11 warps: TMA, GEMM1 MMA, 8 epilogue, GEMM2 MMA
 
 
 // ----------------------------- PTX helpers --------------------------------
@@ -84,13 +90,29 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile i
   }
   return true;
 }
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Non-blocking check first (cheap when the phase has completed), then the
+// bounded blocking wait.
+__device__ __forceinline__ bool mbar_wait_fast(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                               unsigned int *err) {
+  return mbar_test(bar, parity) || mbar_wait(bar, parity, abort_flag, err);
+}
 // Warp-uniform bounded wait: lane 0 waits, the outcome is broadcast, and
 // __syncwarp orders the other lanes after lane 0's acquire.  Keeps the
 // warp converged for the .sync.aligned tcgen05 instructions that follow.
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
                                           unsigned int *err) {
   int ok = 0;
-  if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag, err) ? 1 : 0;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait_fast(bar, parity, abort_flag, err) ? 1 : 0;
   ok = __shfl_sync(0xffffffffu, ok, 0);
   __syncwarp();
   return ok != 0;
@@ -130,6 +152,26 @@ __device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t a_desc, ui
   // measured to accumulate a wrong product on sm_103a.
   __syncwarp(1u);
 }
+__device__ __forceinline__ void tc_mma_bf16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                               uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+  __syncwarp(1u);   // see tc_mma_bf16
+}
+#define PCV_TMEM_ST32(taddr, v)                                                                  \
+  asm volatile(                                                                                  \
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13," \
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"            \
+      ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), \
+        "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]),         \
+        "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]),       \
+        "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),       \
+        "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])                                            \
+      : "memory")
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 #define PCV_TMEM_LD32(taddr, v)                                                                  \
   asm volatile(                                                                                  \
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"  \
@@ -205,13 +247,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int KA = ta.KP / 64;                       // 128-byte K atoms
   const uint32_t th_bytes = (uint32_t)KA * kTM * 128;
   const uint32_t x_bytes = (uint32_t)KA * kTN * 128;
-  const uint32_t r_bytes = (kTN / 64) * kTM * 128;
+  const uint32_t stage_bytes = (uint32_t)pb.p * 129 * 4;   // finish staging [p][129] floats
   const int NS = ta.NS;
   uint8_t *th_hi = sm;
   uint8_t *th_lo = th_hi + th_bytes;
   uint8_t *xs = th_lo + (ta.need_lo ? th_bytes : 0);
-  uint8_t *rs = xs + (size_t)NS * x_bytes;
-  uint8_t *ys = rs + 2 * r_bytes;                  // NS x kTN bf16
+  uint8_t *stg = xs + (size_t)NS * x_bytes;       // finish staging area
+  uint8_t *ys = stg + ((stage_bytes + 1023) & ~1023u);   // NS x kTN bf16
   uint64_t *bars = reinterpret_cast<uint64_t *>(ys + NS * kTN * 2 + 64);
   // barrier slots
   uint64_t *x_full = bars, *x_empty = bars + 4, *s_full = bars + 8, *s_empty = bars + 10;
@@ -232,17 +274,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) { mbar_init(smem_u32(&x_full[s]), 1); mbar_init(smem_u32(&x_empty[s]), 1); }
     for (int s = 0; s < 2; ++s) {
-      mbar_init(smem_u32(&s_full[s]), 1); mbar_init(smem_u32(&s_empty[s]), 8);
-      mbar_init(smem_u32(&r_full[s]), 8); mbar_init(smem_u32(&r_empty[s]), 1);
+      mbar_init(smem_u32(&s_full[s]), 1); mbar_init(smem_u32(&s_empty[s]), 4);
+      mbar_init(smem_u32(&r_full[s]), 4); mbar_init(smem_u32(&r_empty[s]), 1);
     }
     mbar_init(smem_u32(th_full), 1); mbar_init(smem_u32(th_empty), 1);
-    mbar_init(smem_u32(g_full), 1); mbar_init(smem_u32(g_empty), 8);
+    mbar_init(smem_u32(g_full), 1); mbar_init(smem_u32(g_empty), 4);
     mbar_init(smem_u32(flush_bar), 8); mbar_init(smem_u32(decide_bar), 1);
     mbar_init(smem_u32(fin_bar), 8);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) {   // TMEM: 2 x 128 columns of S, then G
+  if (warp == 1) {   // TMEM: S[0] 0-127, S[1] 128-255, G 256-383, R[0] 384-447, R[1] 448-511
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_base_slot)),
                  "r"(512)
                  : "memory");
@@ -253,6 +295,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_base_slot;
   const uint32_t tmem_G = tmem + 256;
+  const uint32_t tmem_R = tmem + 384;              // R[b] at tmem_R + 64 b (bf16x2 per column)
 
   if (warp == 0) {
     // ------------------------------ TMA producer ---------------------------
@@ -263,7 +306,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const long long u = u0 + i;
         const int t = (int)(u / ta.J), j = (int)(u - (long long)t * ta.J);
         if (i == 0 || j == 0) {
-          if (!mbar_wait(smem_u32(th_empty), (seg & 1) ^ 1, abort_flag, ta.err)) break;
+          if (!mbar_wait_fast(smem_u32(th_empty), (seg & 1) ^ 1, abort_flag, ta.err)) break;
           mbar_expect_tx(smem_u32(th_full), th_bytes * (ta.need_lo ? 2 : 1));
           for (int kb = 0; kb < KA; ++kb) {
             tma_load_2d(smem_u32(th_hi + kb * kTM * 128), &tm_hi, kb * 64, t * kTM, smem_u32(th_full));
@@ -274,7 +317,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           ++seg;
         }
         const int st = i % NS, rnd = i / NS;
-        if (!mbar_wait(smem_u32(&x_empty[st]), (rnd & 1) ^ 1, abort_flag, ta.err)) break;
+        if (!mbar_wait_fast(smem_u32(&x_empty[st]), (rnd & 1) ^ 1, abort_flag, ta.err)) break;
         mbar_expect_tx(smem_u32(&x_full[st]), x_bytes + kTN * 2);
         uint8_t *xb = xs + (size_t)st * x_bytes;
         for (int kb = 0; kb < KA; ++kb)
@@ -290,54 +333,26 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
     }
   } else if (warp == 1) {
-    // ------------------------------ MMA issuer -----------------------------
+    // ------------------------------ GEMM1 issuer ---------------------------
+    // Per unit i: S[i & 1] = Theta . X_chunk^T (hi + lo).  (tile, chunk), stage
+    // and parities are tracked incrementally.
     if (lane == 0) {
       const uint32_t id1 = idesc_bf16(kTM, kTN, false);
-      const uint32_t id2 = idesc_bf16(kTM, ta.PN, true);
-      int seg1 = 0, seg2 = 0;
-      auto gemm2 = [&](int k) -> bool {
-        const long long u = u0 + k;
-        const int t = (int)(u / ta.J), j = (int)(u - (long long)t * ta.J);
-        const bool first = (k == 0 || j == 0);
-        const bool last = (k == nunits - 1 || j == ta.J - 1);
-        const int rb = k & 1;
-        if (!mbar_wait(smem_u32(&r_full[rb]), (k >> 1) & 1, abort_flag, ta.err)) return false;
-        if (first && !mbar_wait(smem_u32(g_empty), (seg2 & 1) ^ 1, abort_flag, ta.err)) return false;
-        tc_fence_after();
-        const int st = k % NS;
-        // descriptors: base once, K steps add (byte offset >> 4) to the
-        // 14-bit start-address field (all SMEM offsets stay below 256 KB)
-        const uint64_t ad0 = sdesc_sw128(smem_u32(rs + (size_t)rb * r_bytes), 16, 1024);
-        const uint64_t bd0 = sdesc_sw128(smem_u32(xs + (size_t)st * x_bytes), kTN * 128, 1024);
-#pragma unroll
-        for (int ks = 0; ks < kTN / 16; ++ks) {
-          const uint64_t ad = ad0 + (uint64_t)((((ks >> 2) * kTM * 128) + (ks & 3) * 32) >> 4);
-          const uint64_t bd = bd0 + (uint64_t)((ks * 2048) >> 4);
-          tc_mma_bf16(tmem_G, ad, bd, id2, (first && ks == 0) ? 0u : 1u);
-        }
-        tc_commit(smem_u32(&r_empty[rb]));
-        tc_commit(smem_u32(&x_empty[st]));
-        if (last) { tc_commit(smem_u32(g_full)); ++seg2; }
-        return true;
-      };
-      bool ok = true;
-      for (int i = 0; i < nunits && ok; ++i) {
-        const long long u = u0 + i;
-        const int t = (int)(u / ta.J), j = (int)(u - (long long)t * ta.J);
+      const uint64_t hd0 = sdesc_sw128(smem_u32(th_hi), 16, 1024);
+      const uint64_t ld0 = sdesc_sw128(smem_u32(th_lo), 16, 1024);
+      const uint64_t xd_k = sdesc_sw128(smem_u32(xs), 16, 1024);   // K-major view, stage 0
+      const uint64_t x_step = (uint64_t)(x_bytes >> 4);
+      int j = (int)(u0 % ta.J);
+      int seg1 = 0, st = 0, xph = 0;
+      for (int i = 0; i < nunits; ++i) {
         const bool first = (i == 0 || j == 0);
         const bool last = (i == nunits - 1 || j == ta.J - 1);
-        (void)t;
-        if (first) {
-          if (!mbar_wait(smem_u32(th_full), seg1 & 1, abort_flag, ta.err)) { ok = false; break; }
-        }
-        const int st = i % NS;
-        if (!mbar_wait(smem_u32(&x_full[st]), (i / NS) & 1, abort_flag, ta.err)) { ok = false; break; }
+        if (first && !mbar_wait_fast(smem_u32(th_full), seg1 & 1, abort_flag, ta.err)) break;
+        if (!mbar_wait_fast(smem_u32(&x_full[st]), xph, abort_flag, ta.err)) break;
         const int sb = i & 1;
-        if (!mbar_wait(smem_u32(&s_empty[sb]), ((i >> 1) & 1) ^ 1, abort_flag, ta.err)) { ok = false; break; }
+        if (!mbar_wait_fast(smem_u32(&s_empty[sb]), ((i >> 1) & 1) ^ 1, abort_flag, ta.err)) break;
         tc_fence_after();
-        const uint64_t xd0 = sdesc_sw128(smem_u32(xs + (size_t)st * x_bytes), 16, 1024);
-        const uint64_t hd0 = sdesc_sw128(smem_u32(th_hi), 16, 1024);
-        const uint64_t ld0 = sdesc_sw128(smem_u32(th_lo), 16, 1024);
+        const uint64_t xd0 = xd_k + (uint64_t)st * x_step;
         const uint32_t dS = tmem + sb * 128;
 #pragma unroll
         for (int ks = 0; ks < KS; ++ks) {
@@ -355,14 +370,43 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         tc_commit(smem_u32(&s_full[sb]));
         if (last) { tc_commit(smem_u32(th_empty)); ++seg1; }
-        if (i > 0 && !gemm2(i - 1)) { ok = false; break; }
+        if (++j == ta.J) j = 0;
+        if (++st == NS) { st = 0; xph ^= 1; }
       }
-      if (ok && nunits > 0) gemm2(nunits - 1);
+    }
+  } else if (warp == 10) {
+    // ------------------------------ GEMM2 issuer ---------------------------
+    // Per unit i: G += R[i & 1] . X_chunk, after the epilogue produced R.
+    if (lane == 0) {
+      const uint32_t id2 = idesc_bf16(kTM, ta.PN, true);
+      const uint64_t xd_mn = sdesc_sw128(smem_u32(xs), kTN * 128, 1024);  // MN-major view, stage 0
+      const uint64_t x_step = (uint64_t)(x_bytes >> 4);
+      int j = (int)(u0 % ta.J);
+      int seg2 = 0, st = 0;
+      for (int i = 0; i < nunits; ++i) {
+        const bool first = (i == 0 || j == 0);
+        const bool last = (i == nunits - 1 || j == ta.J - 1);
+        const int rb = i & 1;
+        if (!mbar_wait_fast(smem_u32(&r_full[rb]), (i >> 1) & 1, abort_flag, ta.err)) break;
+        if (first && !mbar_wait_fast(smem_u32(g_empty), (seg2 & 1) ^ 1, abort_flag, ta.err)) break;
+        tc_fence_after();
+        const uint32_t a0 = tmem_R + 64 * rb;       // K step ks: 8 columns (16 bf16) at a0 + 8 ks
+        const uint64_t bd0 = xd_mn + (uint64_t)st * x_step;
+#pragma unroll
+        for (int ks = 0; ks < kTN / 16; ++ks)
+          tc_mma_bf16_ta(tmem_G, a0 + 8 * ks, bd0 + (uint64_t)((ks * 2048) >> 4), id2,
+                         (first && ks == 0) ? 0u : 1u);
+        tc_commit(smem_u32(&r_empty[rb]));
+        tc_commit(smem_u32(&x_empty[st]));
+        if (last) { tc_commit(smem_u32(g_full)); ++seg2; }
+        if (++j == ta.J) j = 0;
+        if (++st == NS) st = 0;
+      }
     }
   } else {
     // ------------------------------ epilogue -------------------------------
     const int ew = warp - 2;                        // epilogue warp 0..7
-    const int eg = ew >> 2;                         // warpgroup: chunk rows [64 eg, 64 eg + 64)
+    const int eg = ew >> 2;                         // warpgroup: units with (i & 1) == eg
     const int q = warp & 3;                         // TMEM lane quarter of this warp
     const int m = q * 32 + lane;                    // chain row within the tile
     const int et = ew * 32 + lane;                  // 0..255
@@ -370,103 +414,104 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const bool accurate = ta.accurate != 0;
     const uint32_t neg_half2 = 0xBF00BF00u;         // (-0.5, -0.5) in bf16x2
     const int wstride = ta.PN + 4;                  // workspace rows per segment
-    int seg = 0, nfin = 0;
-    int t_cur = -1, c = 0;
-    bool valid = false;
-    FoldDesc fd = {0, 0, 0, 0};
-    float ll_tr = 0.0f, ll_te = 0.0f;
-    for (int i = 0; i < nunits; ++i) {
-      const long long u = u0 + i;
-      const int t = (int)(u / ta.J), j = (int)(u - (long long)t * ta.J);
-      const bool last = (i == nunits - 1 || j == ta.J - 1);
-      if (t != t_cur) {
-        t_cur = t;
-        c = t * kTM + m;
-        valid = c < a.C;
-        if (valid) fd = pb.folds[fold_of_chain(a, c)];
-        ll_tr = ll_te = 0.0f;
-      }
-      const int sb = i & 1, rb = i & 1;
-      if (!warp_wait(smem_u32(&s_full[sb]), (i >> 1) & 1, abort_flag, ta.err)) break;
-      // the X stage of this unit is still resident (its release needs this
-      // epilogue's R); waiting on its barrier makes the TMA-written y visible
-      if (!warp_wait(smem_u32(&x_full[i % NS]), (i / NS) & 1, abort_flag, ta.err)) break;
-      if (!warp_wait(smem_u32(&r_empty[rb]), ((i >> 1) & 1) ^ 1, abort_flag, ta.err)) break;
-      tc_fence_after();
-      // both TMEM loads of this warpgroup's 64 columns, then the wait right
-      // away: the destination registers are written asynchronously until
-      // tcgen05.wait::ld, so no other code may touch them in between
-      uint32_t v[64];
-      PCV_TMEM_LD32(tmem + sb * 128 + 64 * eg + lane_off, v);
-      PCV_TMEM_LD32(tmem + sb * 128 + 64 * eg + 32 + lane_off, (v + 32));
-      tmem_wait_ld();
-      const int n0 = j * kTN + 64 * eg;             // first row of this warpgroup
-      const uint32_t *yw = reinterpret_cast<const uint32_t *>(ys + (i % NS) * kTN * 2) + 32 * eg;
-      // residual y - sigmoid(eta) = (y - 1/2) - tanh(S)/2 in bf16x2 (the same
-      // function on every leapfrog step)
-      uint32_t packed[32];
+    const int sb = eg, rb = eg;                     // this group's S and R buffers
+    int nseg_done = 0, nfin = 0;
+    bool aborted = false;
+    // walk the CTA's segments (maximal runs of units in one tile)
+    int t = (int)(u0 / ta.J), j0 = (int)(u0 - (long long)t * ta.J);
+    for (int ib = 0; ib < nunits && !aborted; ) {
+      const int ie = min(nunits, ib + (ta.J - j0));   // segment [ib, ie)
+      const int c = t * kTM + m;
+      const bool valid = c < a.C;
+      FoldDesc fd = {0, 0, 0, 0};
+      if (valid) fd = pb.folds[fold_of_chain(a, c)];
+      float ll_tr = 0.0f, ll_te = 0.0f;
+      for (int i = ib + ((ib & 1) != eg ? 1 : 0); i < ie; i += 2) {
+        const int j = j0 + (i - ib);
+        if (!warp_wait(smem_u32(&s_full[sb]), (i >> 1) & 1, abort_flag, ta.err)) { aborted = true; break; }
+        // the X stage of this unit is still resident (its release needs R);
+        // waiting on its barrier makes the TMA-written y visible
+        if (!warp_wait(smem_u32(&x_full[i % NS]), (i / NS) & 1, abort_flag, ta.err)) { aborted = true; break; }
+        if (!warp_wait(smem_u32(&r_empty[rb]), ((i >> 1) & 1) ^ 1, abort_flag, ta.err)) { aborted = true; break; }
+        tc_fence_after();
+        const uint32_t *ywu = reinterpret_cast<const uint32_t *>(ys + (i % NS) * kTN * 2);
+        for (int h = 0; h < 2; ++h) {               // two halves of 64 rows
+          // TMEM loads, then the wait right away: the destination registers
+          // are written asynchronously until tcgen05.wait::ld
+          uint32_t v[64];
+          PCV_TMEM_LD32(tmem + sb * 128 + 64 * h + lane_off, v);
+          PCV_TMEM_LD32(tmem + sb * 128 + 64 * h + 32 + lane_off, (v + 32));
+          tmem_wait_ld();
+          if (h == 1) {                             // S fully in registers: release it
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&s_empty[sb]));
+          }
+          const int n0 = j * kTN + 64 * h;
+          const uint32_t *yw = ywu + 32 * h;
+          // residual y - sigmoid(eta) = (y - 1/2) - tanh(S)/2 in bf16x2 (the
+          // same function on every leapfrog step)
+          uint32_t packed[32];
 #pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        const uint32_t t2 = tanh_bf16x2(bf16x2_from(__uint_as_float(v[2 * k]), __uint_as_float(v[2 * k + 1])));
-        packed[k] = fma_bf16x2(t2, neg_half2, yw[k]);
-      }
-      if (valid && n0 < fd.excl_hi && n0 + 64 > fd.excl_lo) {
+          for (int k = 0; k < 32; ++k) {
+            const uint32_t t2 = tanh_bf16x2(bf16x2_from(__uint_as_float(v[2 * k]), __uint_as_float(v[2 * k + 1])));
+            packed[k] = fma_bf16x2(t2, neg_half2, yw[k]);
+          }
+          if (valid && n0 < fd.excl_hi && n0 + 64 > fd.excl_lo) {
 #pragma unroll
-        for (int k = 0; k < 64; ++k) {
-          const int n = n0 + k;
-          if (n >= fd.excl_lo && n < fd.excl_hi) packed[k >> 1] &= (k & 1) ? 0x0000FFFFu : 0xFFFF0000u;
+            for (int k = 0; k < 64; ++k) {
+              const int n = n0 + k;
+              if (n >= fd.excl_lo && n < fd.excl_hi) packed[k >> 1] &= (k & 1) ? 0x0000FFFFu : 0xFFFF0000u;
+            }
+          }
+          if (accurate) {
+            // masked log likelihood y eta - softplus(eta), softplus(eta) =
+            // max(eta, 0) + log(1 + exp(-|eta|)), FP32 (2 MUFU operations)
+#pragma unroll
+            for (int k = 0; k < 64; ++k) {
+              const int n = n0 + k;
+              const float eta = 2.0f * __uint_as_float(v[k]);
+              const uint32_t y2 = yw[k >> 1];
+              const float yv = __uint_as_float((k & 1) ? (y2 & 0xFFFF0000u) : (y2 << 16)) + 0.5f;
+              const float e = exp2f(-fabsf(eta) * 1.4426950408889634f);
+              const float ll = yv * eta - fmaxf(eta, 0.0f) - __log2f(1.0f + e) * 0.6931471805599453f;
+              const bool in_rows = n < pb.N;
+              if (in_rows && (n < fd.excl_lo || n >= fd.excl_hi)) ll_tr += ll;
+              if (in_rows && n >= fd.test_lo && n < fd.test_hi) ll_te += ll;
+            }
+          }
+          // R row m (TMEM lane m): chunk rows 64 h .. 64 h + 63 as 32 bf16x2 columns
+          PCV_TMEM_ST32(tmem_R + 64 * rb + 32 * h + lane_off, packed);
         }
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&r_full[rb]));
       }
-      if (accurate) {
-        // masked log likelihood y eta - softplus(eta), softplus(eta) =
-        // max(eta, 0) + log(1 + exp(-|eta|)), FP32 (2 MUFU operations)
-#pragma unroll
-        for (int k = 0; k < 64; ++k) {
-          const int n = n0 + k;
-          const float eta = 2.0f * __uint_as_float(v[k]);
-          const uint32_t y2 = yw[k >> 1];
-          const float yv = __uint_as_float((k & 1) ? (y2 & 0xFFFF0000u) : (y2 << 16)) + 0.5f;
-          const float e = exp2f(-fabsf(eta) * 1.4426950408889634f);
-          const float ll = yv * eta - fmaxf(eta, 0.0f) - __log2f(1.0f + e) * 0.6931471805599453f;
-          const bool in_rows = n < pb.N;
-          if (in_rows && (n < fd.excl_lo || n >= fd.excl_hi)) ll_tr += ll;
-          if (in_rows && n >= fd.test_lo && n < fd.test_hi) ll_te += ll;
-        }
-      }
-      // R tile: row m, K atom eg (64 columns = eight 16-byte chunks), 128-byte
-      // swizzle (chunk ^= m & 7)
-      uint8_t *row = rs + (size_t)rb * r_bytes + eg * kTM * 128 + m * 128;
-#pragma unroll
-      for (int cc = 0; cc < 8; ++cc)
-        *reinterpret_cast<uint4 *>(row + ((cc ^ (m & 7)) << 4)) =
-            make_uint4(packed[4 * cc], packed[4 * cc + 1], packed[4 * cc + 2], packed[4 * cc + 3]);
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&s_empty[sb]));
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&r_full[rb]));
-      if (!last) continue;
-      // ---- segment end: flush this tile's G partial and the ll sums
-      if (!warp_wait(smem_u32(g_full), seg & 1, abort_flag, ta.err)) break;
-      tc_fence_after();
+      if (aborted) break;
+      // ---- segment end (both groups): the group that owns the segment's
+      // last unit flushes this tile's G partial; both write their ll sums
+      const int owner = (ie - 1) & 1;
+      const int fl = nseg_done++;
       const int b0 = owner_cta((long long)t * ta.J, U, ta.n_cta);
       const int sidx = blockIdx.x - b0;
       float *wsp = ta.ws + ((size_t)t * ta.max_seg + sidx) * (size_t)wstride * kTM;
-      for (int cb = 16 * eg; cb < ta.PN; cb += 32) {
-        uint32_t gv[16];
-        PCV_TMEM_LD16(tmem_G + cb + lane_off, gv);
-        tmem_wait_ld();
+      if (eg == owner) {
+        if (!warp_wait(smem_u32(g_full), fl & 1, abort_flag, ta.err)) break;
+        tc_fence_after();
+        for (int cb = 0; cb < ta.PN; cb += 16) {
+          uint32_t gv[16];
+          PCV_TMEM_LD16(tmem_G + cb + lane_off, gv);
+          tmem_wait_ld();
 #pragma unroll
-        for (int k = 0; k < 16; ++k) wsp[(size_t)(cb + k) * kTM + m] = __uint_as_float(gv[k]);
+          for (int k = 0; k < 16; ++k) wsp[(size_t)(cb + k) * kTM + m] = __uint_as_float(gv[k]);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(g_empty));
       }
       wsp[(size_t)(ta.PN + 2 * eg) * kTM + m] = ll_tr;
       wsp[(size_t)(ta.PN + 2 * eg + 1) * kTM + m] = ll_te;
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(g_empty));
-      const int fl = seg++;
-      ll_tr = ll_te = 0.0f;
       __threadfence();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(flush_bar));
@@ -480,74 +525,78 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         mbar_arrive(smem_u32(decide_bar));
       }
       if (!warp_wait(smem_u32(decide_bar), fl & 1, abort_flag, ta.err)) break;
-      if (!*last_flag) continue;
-      // ---- last segment of tile t: sum the segments, priors, leapfrog update.
-      // The R buffers are idle here (every issued GEMM2 has completed and no
-      // new one starts before this epilogue's next R), so they stage the
-      // summed gradient [p][129] for coalesced per-chain writes.
-      __threadfence();
-      float *stage = reinterpret_cast<float *>(rs);
-      const float *base = ta.ws + (size_t)t * ta.max_seg * (size_t)wstride * kTM;
-      const size_t seg_stride = (size_t)wstride * kTM;
-      {
-        const int mm = et & 127;
-        for (int jj = et >> 7; jj < pb.p; jj += 2) {
-          float gs = 0.0f;
-          for (int s2 = 0; s2 < nseg; ++s2) gs += __ldcg(base + s2 * seg_stride + (size_t)jj * kTM + mm);
-          stage[jj * 129 + mm] = gs;
+      if (*last_flag) {
+        // ---- last segment of tile t: sum the segments, priors, leapfrog
+        // update; the summed gradient is staged [p][129] in shared memory so
+        // that the per-chain writes are coalesced.
+        __threadfence();
+        float *stage = reinterpret_cast<float *>(stg);
+        const float *base = ta.ws + (size_t)t * ta.max_seg * (size_t)wstride * kTM;
+        const size_t seg_stride = (size_t)wstride * kTM;
+        {
+          const int mm = et & 127;
+          for (int jj = et >> 7; jj < pb.p; jj += 2) {
+            float gs = 0.0f;
+            for (int s2 = 0; s2 < nseg; ++s2) gs += __ldcg(base + s2 * seg_stride + (size_t)jj * kTM + mm);
+            stage[jj * 129 + mm] = gs;
+          }
         }
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(fin_bar));
-      if (!warp_wait(smem_u32(fin_bar), (2 * nfin) & 1, abort_flag, ta.err)) break;
-      const float eps = a.mode != MODE_NONE ? *a.eps : 0.0f;
-      const float kick = a.mode == MODE_LAST_KICK ? 0.5f * eps : eps;
-      for (int mm = ew; mm < kTM; mm += 8) {           // warp per chain, lanes over dims
-        const int cc = t * kTM + mm;
-        if (cc >= a.C) break;
-        float *th = const_cast<float *>(a.theta) + (size_t)cc * a.ld_theta;
-        float *gr = a.grad + (size_t)cc * a.ld_grad;
-        float *rr = a.r ? a.r + (size_t)cc * a.ld_theta : nullptr;
-        double lp = 0.0;
-        for (int jj = lane; jj < pb.p; jj += 32) {
-          const float tv = th[jj];
-          const float g = stage[jj * 129 + mm] - tv * pb.beta_prec;
-          gr[jj] = g;
-          if (a.need_ll) lp += -0.5 * kLog2PiD - (double)pb.log_beta_sd - 0.5 * (double)tv * tv * pb.beta_prec;
-          if (a.mode != MODE_NONE) {
-            const float rj = rr[jj] + kick * g;
-            rr[jj] = rj;
-            if (a.mode == MODE_KICK_DRIFT) {
-              const float tn = tv + eps * a.minv[jj] * rj;
-              th[jj] = tn;
-              const float half = 0.5f * tn;            // shadows hold theta / 2
-              const __nv_bfloat16 hi = __float2bfloat16_rn(half);
-              a.shadow_hi[(size_t)cc * a.ld_shadow + jj] = hi;
-              a.shadow_lo[(size_t)cc * a.ld_shadow + jj] = __float2bfloat16_rn(half - __bfloat162float(hi));
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(fin_bar));
+        if (!warp_wait(smem_u32(fin_bar), (2 * nfin) & 1, abort_flag, ta.err)) break;
+        const float eps = a.mode != MODE_NONE ? *a.eps : 0.0f;
+        const float kick = a.mode == MODE_LAST_KICK ? 0.5f * eps : eps;
+        for (int mm = ew; mm < kTM; mm += 8) {         // warp per chain, lanes over dims
+          const int cc = t * kTM + mm;
+          if (cc >= a.C) break;
+          float *th = const_cast<float *>(a.theta) + (size_t)cc * a.ld_theta;
+          float *gr = a.grad + (size_t)cc * a.ld_grad;
+          float *rr = a.r ? a.r + (size_t)cc * a.ld_theta : nullptr;
+          double lp = 0.0;
+          for (int jj = lane; jj < pb.p; jj += 32) {
+            const float tv = th[jj];
+            const float g = stage[jj * 129 + mm] - tv * pb.beta_prec;
+            gr[jj] = g;
+            if (a.need_ll) lp += -0.5 * kLog2PiD - (double)pb.log_beta_sd - 0.5 * (double)tv * tv * pb.beta_prec;
+            if (a.mode != MODE_NONE) {
+              const float rj = rr[jj] + kick * g;
+              rr[jj] = rj;
+              if (a.mode == MODE_KICK_DRIFT) {
+                const float tn = tv + eps * a.minv[jj] * rj;
+                th[jj] = tn;
+                const float half = 0.5f * tn;          // shadows hold theta / 2
+                const __nv_bfloat16 hi = __float2bfloat16_rn(half);
+                a.shadow_hi[(size_t)cc * a.ld_shadow + jj] = hi;
+                a.shadow_lo[(size_t)cc * a.ld_shadow + jj] = __float2bfloat16_rn(half - __bfloat162float(hi));
+              }
+            }
+          }
+          if (a.need_ll) {
+            lp = warp_sum_d(lp);
+            double s0 = 0.0, s1 = 0.0;
+            for (int s2 = lane; s2 < nseg; s2 += 32) {
+              const float *ws2 = base + s2 * seg_stride;
+              s0 += (double)__ldcg(ws2 + (size_t)ta.PN * kTM + mm) + (double)__ldcg(ws2 + (size_t)(ta.PN + 2) * kTM + mm);
+              s1 += (double)__ldcg(ws2 + (size_t)(ta.PN + 1) * kTM + mm) + (double)__ldcg(ws2 + (size_t)(ta.PN + 3) * kTM + mm);
+            }
+            s0 = warp_sum_d(s0);
+            s1 = warp_sum_d(s1);
+            if (lane == 0) {
+              a.logp[cc] = s0 + lp;
+              a.shat[cc] = s1;
             }
           }
         }
-        if (a.need_ll) {
-          lp = warp_sum_d(lp);
-          double s0 = 0.0, s1 = 0.0;
-          for (int s2 = lane; s2 < nseg; s2 += 32) {
-            const float *ws2 = base + s2 * seg_stride;
-            s0 += (double)__ldcg(ws2 + (size_t)ta.PN * kTM + mm) + (double)__ldcg(ws2 + (size_t)(ta.PN + 2) * kTM + mm);
-            s1 += (double)__ldcg(ws2 + (size_t)(ta.PN + 1) * kTM + mm) + (double)__ldcg(ws2 + (size_t)(ta.PN + 3) * kTM + mm);
-          }
-          s0 = warp_sum_d(s0);
-          s1 = warp_sum_d(s1);
-          if (lane == 0) {
-            a.logp[cc] = s0 + lp;
-            a.shat[cc] = s1;
-          }
-        }
+        // the staging area is reused only after every warp has finished
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(fin_bar));
+        if (!warp_wait(smem_u32(fin_bar), (2 * nfin + 1) & 1, abort_flag, ta.err)) break;
+        ++nfin;
       }
-      // the staging area is reused as R only after every warp has finished
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(fin_bar));
-      if (!warp_wait(smem_u32(fin_bar), (2 * nfin + 1) & 1, abort_flag, ta.err)) break;
-      ++nfin;
+      // next segment starts at chunk 0 of the next tile
+      ib = ie;
+      ++t;
+      j0 = 0;
     }
   }
   // teardown: every role has left its loop (normally or by abort)
@@ -562,9 +611,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-size_t tc_smem_bytes(int KP, int NS, int need_lo) {
+size_t tc_smem_bytes(int KP, int NS, int need_lo, int p) {
   const size_t KA = KP / 64;
-  size_t b = KA * kTM * 128 * (need_lo ? 2 : 1) + (size_t)NS * KA * kTN * 128 + 2 * (kTN / 64) * kTM * 128 +
+  const size_t stage = ((size_t)p * 129 * 4 + 1023) & ~(size_t)1023;
+  size_t b = KA * kTM * 128 * (need_lo ? 2 : 1) + (size_t)NS * KA * kTN * 128 + stage +
              (size_t)NS * kTN * 2 + 64 + 32 * 8;   // 26 barrier / flag slots used
   return b + 1024;   // alignment slack
 }
@@ -597,7 +647,7 @@ cudaError_t tc_prepare() {
 
 cudaError_t launch_grad_tc(const CUtensorMap &tm_x, const CUtensorMap &tm_hi, const CUtensorMap &tm_lo,
                            const Problem &pb, const GradArgs &a, const TcArgs &ta, cudaStream_t st) {
-  const size_t smem = tc_smem_bytes(ta.KP, ta.NS, ta.need_lo);
+  const size_t smem = tc_smem_bytes(ta.KP, ta.NS, ta.need_lo, pb.p);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   switch (ta.KS) {
 #define PCV_TC_CASE(K) \

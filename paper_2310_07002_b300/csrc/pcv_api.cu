@@ -21,7 +21,7 @@
 #include "pcv_internal.cuh"
 
 namespace pcv {
-size_t tc_smem_bytes(int KP, int NS, int need_lo);
+size_t tc_smem_bytes(int KP, int NS, int need_lo, int p);
 int tc_segments_per_tile(int T, int J, int n_cta);
 cudaError_t tc_prepare();
 cudaError_t launch_grad_tc(const CUtensorMap &tm_x, const CUtensorMap &tm_hi, const CUtensorMap &tm_lo,
@@ -225,7 +225,7 @@ TcArgs tc_args(pcv_ctx *x, int C, bool need_lo) {
   // log densities are needed
   t.need_lo = 1;
   t.accurate = need_lo ? 1 : 0;
-  t.NS = tc_smem_bytes(t.KP, 3, 1) <= 227 * 1024 ? 3 : 2;
+  t.NS = tc_smem_bytes(t.KP, 4, 1, x->p) <= 227 * 1024 ? 4 : (tc_smem_bytes(t.KP, 3, 1, x->p) <= 227 * 1024 ? 3 : 2);
   t.yc = x->yc16;
   t.ws = x->ws_tc;
   t.tickets = x->tickets_tc;
