@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint8_t *th_lo = th_hi + th_bytes;
   uint8_t *xs = th_lo + (ta.need_lo ? th_bytes : 0);
   uint8_t *stg = xs + (size_t)NS * x_bytes;       // finish staging area
-  uint8_t *ys = stg + ((stage_bytes + 1023) & ~1023u);   // NS x kTN bf16
+  uint8_t *ys = stg + ((stage_bytes + 8 + kTM * 8 + 1023) & ~1023u);   // NS x kTN bf16
   uint64_t *bars = reinterpret_cast<uint64_t *>(ys + NS * kTN * 2 + 64);
   // barrier slots
   uint64_t *x_full = bars, *x_empty = bars + 4, *s_full = bars + 8, *s_empty = bars + 10;
@@ -531,8 +531,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // that the per-chain writes are coalesced.
         __threadfence();
         float *stage = reinterpret_cast<float *>(stg);
+        double *lp_acc = reinterpret_cast<double *>(stg + ((stage_bytes + 7) & ~7u));   // 128 doubles
         const float *base = ta.ws + (size_t)t * ta.max_seg * (size_t)wstride * kTM;
         const size_t seg_stride = (size_t)wstride * kTM;
+        if (et < kTM) lp_acc[et] = 0.0;
         {
           const int mm = et & 127;
           for (int jj = et >> 7; jj < pb.p; jj += 2) {
@@ -543,54 +545,55 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(fin_bar));
-        if (!warp_wait(smem_u32(fin_bar), (2 * nfin) & 1, abort_flag, ta.err)) break;
+        if (!warp_wait(smem_u32(fin_bar), (3 * nfin) & 1, abort_flag, ta.err)) break;
         const float eps = a.mode != MODE_NONE ? *a.eps : 0.0f;
         const float kick = a.mode == MODE_LAST_KICK ? 0.5f * eps : eps;
-        for (int mm = ew; mm < kTM; mm += 8) {         // warp per chain, lanes over dims
+        // (chain, dimension) items spread over all 256 epilogue threads so
+        // that many independent loads are in flight; consecutive items are
+        // consecutive dimensions of one chain (coalesced)
+        const int p_ = pb.p;
+        for (int it = et; it < kTM * p_; it += 256) {
+          const int mm = it / p_, jj = it - mm * p_;
           const int cc = t * kTM + mm;
           if (cc >= a.C) break;
           float *th = const_cast<float *>(a.theta) + (size_t)cc * a.ld_theta;
-          float *gr = a.grad + (size_t)cc * a.ld_grad;
-          float *rr = a.r ? a.r + (size_t)cc * a.ld_theta : nullptr;
-          double lp = 0.0;
-          for (int jj = lane; jj < pb.p; jj += 32) {
-            const float tv = th[jj];
-            const float g = stage[jj * 129 + mm] - tv * pb.beta_prec;
-            gr[jj] = g;
-            if (a.need_ll) lp += -0.5 * kLog2PiD - (double)pb.log_beta_sd - 0.5 * (double)tv * tv * pb.beta_prec;
-            if (a.mode != MODE_NONE) {
-              const float rj = rr[jj] + kick * g;
-              rr[jj] = rj;
-              if (a.mode == MODE_KICK_DRIFT) {
-                const float tn = tv + eps * a.minv[jj] * rj;
-                th[jj] = tn;
-                const float half = 0.5f * tn;          // shadows hold theta / 2
-                const __nv_bfloat16 hi = __float2bfloat16_rn(half);
-                a.shadow_hi[(size_t)cc * a.ld_shadow + jj] = hi;
-                a.shadow_lo[(size_t)cc * a.ld_shadow + jj] = __float2bfloat16_rn(half - __bfloat162float(hi));
-              }
+          const float tv = th[jj];
+          const float g = stage[jj * 129 + mm] - tv * pb.beta_prec;
+          a.grad[(size_t)cc * a.ld_grad + jj] = g;
+          if (a.need_ll)
+            atomicAdd(&lp_acc[mm], -0.5 * kLog2PiD - (double)pb.log_beta_sd - 0.5 * (double)tv * tv * pb.beta_prec);
+          if (a.mode != MODE_NONE) {
+            float *rr = a.r + (size_t)cc * a.ld_theta;
+            const float rj = rr[jj] + kick * g;
+            rr[jj] = rj;
+            if (a.mode == MODE_KICK_DRIFT) {
+              const float tn = tv + eps * a.minv[jj] * rj;
+              th[jj] = tn;
+              const float half = 0.5f * tn;            // shadows hold theta / 2
+              const __nv_bfloat16 hi = __float2bfloat16_rn(half);
+              a.shadow_hi[(size_t)cc * a.ld_shadow + jj] = hi;
+              a.shadow_lo[(size_t)cc * a.ld_shadow + jj] = __float2bfloat16_rn(half - __bfloat162float(hi));
             }
           }
-          if (a.need_ll) {
-            lp = warp_sum_d(lp);
-            double s0 = 0.0, s1 = 0.0;
-            for (int s2 = lane; s2 < nseg; s2 += 32) {
-              const float *ws2 = base + s2 * seg_stride;
-              s0 += (double)__ldcg(ws2 + (size_t)ta.PN * kTM + mm) + (double)__ldcg(ws2 + (size_t)(ta.PN + 2) * kTM + mm);
-              s1 += (double)__ldcg(ws2 + (size_t)(ta.PN + 1) * kTM + mm) + (double)__ldcg(ws2 + (size_t)(ta.PN + 3) * kTM + mm);
-            }
-            s0 = warp_sum_d(s0);
-            s1 = warp_sum_d(s1);
-            if (lane == 0) {
-              a.logp[cc] = s0 + lp;
-              a.shat[cc] = s1;
-            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(fin_bar));
+        if (!warp_wait(smem_u32(fin_bar), (3 * nfin + 1) & 1, abort_flag, ta.err)) break;
+        if (a.need_ll && et < kTM && t * kTM + et < a.C) {
+          const int cc = t * kTM + et;
+          double s0 = 0.0, s1 = 0.0;
+          for (int s2 = 0; s2 < nseg; ++s2) {
+            const float *ws2 = base + s2 * seg_stride;
+            s0 += (double)__ldcg(ws2 + (size_t)ta.PN * kTM + et) + (double)__ldcg(ws2 + (size_t)(ta.PN + 2) * kTM + et);
+            s1 += (double)__ldcg(ws2 + (size_t)(ta.PN + 1) * kTM + et) + (double)__ldcg(ws2 + (size_t)(ta.PN + 3) * kTM + et);
           }
+          a.logp[cc] = s0 + lp_acc[et];
+          a.shat[cc] = s1;
         }
         // the staging area is reused only after every warp has finished
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(fin_bar));
-        if (!warp_wait(smem_u32(fin_bar), (2 * nfin + 1) & 1, abort_flag, ta.err)) break;
+        if (!warp_wait(smem_u32(fin_bar), (3 * nfin + 2) & 1, abort_flag, ta.err)) break;
         ++nfin;
       }
       // next segment starts at chunk 0 of the next tile
@@ -613,7 +616,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // ---------------------------------------------------------------------------
 size_t tc_smem_bytes(int KP, int NS, int need_lo, int p) {
   const size_t KA = KP / 64;
-  const size_t stage = ((size_t)p * 129 * 4 + 1023) & ~(size_t)1023;
+  const size_t stage = ((size_t)p * 129 * 4 + 8 + kTM * 8 + 1023) & ~(size_t)1023;
   size_t b = KA * kTM * 128 * (need_lo ? 2 : 1) + (size_t)NS * KA * kTN * 128 + stage +
              (size_t)NS * kTN * 2 + 64 + 32 * 8;   // 26 barrier / flag slots used
   return b + 1024;   // alignment slack
