@@ -353,6 +353,207 @@ __global__ void __launch_bounds__(kWarps * 32) k_grad_hier(Problem pb, GradArgs 
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Large p (33..128), flat models, FP32 CUDA cores.  A CTA owns a tile of 64
+// chains and one of `splits` row ranges; per 32-row chunk it computes
+//   S = Theta_tile . X_chunk^T   (2 x 4 register micro-tiles per thread),
+//   R = mask .* dlogp/deta       (shared memory),
+//   G += R . X_chunk             (4 x 8 register micro-tiles, kept for the range)
+// then combines split-N partials like the kernels above.
+// ---------------------------------------------------------------------------
+constexpr int kBigTileC = 64, kBigRows = 32;
+
+template <int MV>
+__global__ void __launch_bounds__(256) k_grad_bigp(Problem pb, GradArgs a, int pp) {
+  extern __shared__ float sm_big[];
+  const int ldt = pp + 1;                           // odd strides: conflict-free
+  float *th_s = sm_big;                             // [64][pp + 1]
+  float *xs = th_s + kBigTileC * ldt;               // [32][pp + 1]
+  float *rs = xs + kBigRows * ldt;                  // [64][33]
+  float *ys = rs + kBigTileC * 33;                  // [32]
+  float *lls = ys + kBigRows;                       // [2][64] ll partials, [64] dlogsig
+  __shared__ int is_last;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int tile = blockIdx.x / a.splits, split = blockIdx.x - tile * a.splits;
+  const int c0 = tile * kBigTileC;
+  const int p = pb.p;
+  for (int q = t; q < kBigTileC * pp; q += 256) {
+    const int cl = q / pp, j = q - cl * pp;
+    const int c = c0 + cl;
+    th_s[cl * ldt + j] = (c < a.C && j < p) ? a.theta[(size_t)c * a.ld_theta + j] : 0.0f;
+  }
+  for (int q = t; q < 3 * kBigTileC; q += 256) lls[q] = 0.0f;
+  // per-thread chain constants for the residual phase (chains cA, cA + 1)
+  const int cA = (t >> 3) * 2, rA = (t & 7) * 4;
+  float logsig[2] = {0.0f, 0.0f}, inv_s2[2] = {1.0f, 1.0f};
+  FoldDesc fd[2];
+  bool valid[2];
+  for (int u = 0; u < 2; ++u) {
+    const int c = c0 + cA + u;
+    valid[u] = c < a.C;
+    fd[u] = valid[u] ? pb.folds[fold_of_chain(a, c)] : FoldDesc{0, 0, 0, 0};
+    if (MV == MV_GAUSS_KNOWN) {
+      logsig[u] = logf(pb.sigma_known);
+      inv_s2[u] = 1.0f / (pb.sigma_known * pb.sigma_known);
+    } else if (MV == MV_GAUSS_LOGSIG) {
+      logsig[u] = valid[u] ? a.theta[(size_t)c * a.ld_theta + p] : 0.0f;
+      inv_s2[u] = expf(-2.0f * logsig[u]);
+    }
+  }
+  // GEMM2 accumulators: chains cg..cg+3, dims dg + 16 k
+  const int cg = (t >> 4) * 4, dg = t & 15;
+  float acc[4][8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[i][k] = 0.0f;
+  float ll_tr[2] = {0.0f, 0.0f}, ll_te[2] = {0.0f, 0.0f}, dls[2] = {0.0f, 0.0f};
+  const int r0 = (int)((long long)pb.N * split / a.splits);
+  const int r1 = (int)((long long)pb.N * (split + 1) / a.splits);
+  __syncthreads();
+  for (int n0 = r0; n0 < r1; n0 += kBigRows) {
+    const int nr = min(kBigRows, r1 - n0);
+    for (int q = t; q < kBigRows * pp; q += 256) {
+      const int rr = q / pp, j = q - rr * pp;
+      xs[rr * ldt + j] = rr < nr ? pb.X[(size_t)(n0 + rr) * pb.p_pad + j] : 0.0f;
+    }
+    if (t < kBigRows) ys[t] = t < nr ? pb.y[n0 + t] : 0.0f;
+    __syncthreads();
+    // GEMM1 micro-tile: chains cA, cA+1 x rows rA..rA+3
+    float sv[2][4];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) sv[u][v] = 0.0f;
+    for (int j = 0; j < p; ++j) {
+      const float t0 = th_s[cA * ldt + j], t1 = th_s[(cA + 1) * ldt + j];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const float xv = xs[(rA + v) * ldt + j];
+        sv[0][v] = fmaf(t0, xv, sv[0][v]);
+        sv[1][v] = fmaf(t1, xv, sv[1][v]);
+      }
+    }
+    // masked residual dlogp/deta (and log likelihoods on evaluation steps)
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int rr = rA + v, n = n0 + rr;
+        const float eta = sv[u][v], yv = ys[rr];
+        const bool in_rows = rr < nr;
+        const float tr = (in_rows && (n < fd[u].excl_lo || n >= fd[u].excl_hi)) ? 1.0f : 0.0f;
+        float dll, ll = 0.0f;
+        if (MV == MV_LOGISTIC) {
+          dll = yv - 1.0f / (1.0f + __expf(-eta));
+          if (a.need_ll) ll = yv * eta - softplusf(eta);
+        } else {
+          const float e = yv - eta;
+          dll = e * inv_s2[u];
+          if (a.need_ll) ll = -0.5f * kLog2Pi - logsig[u] - 0.5f * e * e * inv_s2[u];
+          if (MV == MV_GAUSS_LOGSIG) dls[u] = fmaf(tr, e * e * inv_s2[u] - 1.0f, dls[u]);
+        }
+        rs[(cA + u) * 33 + rr] = dll * tr;
+        if (a.need_ll) {
+          const float te = (in_rows && n >= fd[u].test_lo && n < fd[u].test_hi) ? 1.0f : 0.0f;
+          ll_tr[u] = fmaf(tr, ll, ll_tr[u]);
+          ll_te[u] = fmaf(te, ll, ll_te[u]);
+        }
+      }
+    }
+    __syncthreads();
+    // GEMM2: G[cg..cg+3][dg + 16 k] += R[c][rr] X[rr][d]
+    for (int rr = 0; rr < nr; ++rr) {
+      float rv[4], xv[8];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) rv[i] = rs[(cg + i) * 33 + rr];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) xv[k] = (dg + 16 * k < pp) ? xs[rr * ldt + dg + 16 * k] : 0.0f;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[i][k] = fmaf(rv[i], xv[k], acc[i][k]);
+    }
+    __syncthreads();
+  }
+  // per-chain likelihood sums: threads sharing cA (8 of them) add into smem
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    atomicAdd(&lls[cA + u], ll_tr[u]);
+    atomicAdd(&lls[kBigTileC + cA + u], ll_te[u]);
+    if (MV == MV_GAUSS_LOGSIG) atomicAdd(&lls[2 * kBigTileC + cA + u], dls[u]);
+  }
+  __syncthreads();
+  // partial of this CTA: [64 chains][ws_stride]: grads, slot pp dlogsig,
+  // pp+1 ll_tr, pp+2 ll_te
+  float *mine = a.ws + ((size_t)tile * a.splits + split) * kBigTileC * a.ws_stride;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (dg + 16 * k < pp) mine[(cg + i) * a.ws_stride + dg + 16 * k] = acc[i][k];
+  if (t < kBigTileC) {
+    mine[t * a.ws_stride + pp] = lls[2 * kBigTileC + t];
+    mine[t * a.ws_stride + pp + 1] = lls[t];
+    mine[t * a.ws_stride + pp + 2] = lls[kBigTileC + t];
+  }
+  __threadfence();
+  __syncthreads();
+  if (a.splits > 1) {
+    if (t == 0) {
+      const unsigned prev = atomicAdd(a.tickets + tile, 1u);
+      is_last = (prev == (unsigned)a.splits - 1);
+      if (is_last) a.tickets[tile] = 0u;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+  }
+  // sum the splits' partials in split order; likelihood sums in FP64
+  __shared__ double lld[2][kBigTileC];
+  float *tot = xs;                                  // [64][pp + 4], reuses the tile buffers
+  const int ts = pp + 4;
+  const float *base = a.ws + (size_t)tile * a.splits * kBigTileC * a.ws_stride;
+  for (int q = t; q < kBigTileC * (pp + 3); q += 256) {
+    const int cl = q / (pp + 3), j = q - cl * (pp + 3);
+    if (j > pp) {
+      double sacc = 0.0;
+      for (int s2 = 0; s2 < a.splits; ++s2)
+        sacc += (double)__ldcg(base + ((size_t)s2 * kBigTileC + cl) * a.ws_stride + j);
+      lld[j - pp - 1][cl] = sacc;
+    } else {
+      float sacc = 0.0f;
+      for (int s2 = 0; s2 < a.splits; ++s2) sacc += __ldcg(base + ((size_t)s2 * kBigTileC + cl) * a.ws_stride + j);
+      tot[cl * ts + j] = sacc;
+    }
+  }
+  __syncthreads();
+  for (int cl = warp; cl < kBigTileC; cl += 8) {
+    const int c = c0 + cl;
+    if (c >= a.C) continue;
+    float *row = tot + cl * ts;
+    if (MV == MV_GAUSS_LOGSIG) {
+      const float d = row[pp];
+      __syncwarp();
+      if (lane == 0) row[p] = d;                    // d/dlog sigma at index p
+      __syncwarp();
+    }
+    finish_chain<MV>(pb, a, c, row, lld[0][cl], lld[1][cl], lane);
+  }
+}
+
+int simt_chain_tile(int p) { return simt_flat_pp(p) > 0 ? 32 : kBigTileC; }
+
+size_t bigp_smem_bytes(int pp) {
+  const int ldt = pp + 1;
+  size_t f = (size_t)kBigTileC * ldt + (size_t)kBigRows * ldt + kBigTileC * 33 + kBigRows + 3 * kBigTileC;
+  const size_t tot = (size_t)kBigTileC * (pp + 4);
+  const size_t avail = (size_t)kBigRows * ldt + kBigTileC * 33 + kBigRows + 3 * kBigTileC;
+  if (tot > avail) f += tot - avail;
+  return f * sizeof(float);
+}
+
 // ---------------------------------------------------------------------------
 // host-side launchers
 // ---------------------------------------------------------------------------
@@ -386,9 +587,28 @@ size_t hier_smem_bytes(int PP, int, int) {
   return (size_t)kWarps * 32 * (PP + 4) * sizeof(float);
 }
 
+template <int MV>
+static cudaError_t launch_bigp_mv(const Problem &pb, const GradArgs &a, cudaStream_t st) {
+  const int pp = (pb.p + 3) / 4 * 4;
+  const int tiles = (a.C + kBigTileC - 1) / kBigTileC;
+  const size_t sm = bigp_smem_bytes(pp);
+  cudaError_t e = cudaFuncSetAttribute(k_grad_bigp<MV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_grad_bigp<MV><<<tiles * a.splits, 256, sm, st>>>(pb, a, pp);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_grad_simt(const Problem &pb, const GradArgs &a, cudaStream_t st) {
   const int PP = simt_flat_pp(pb.p);
-  if (PP < 0) return cudaErrorInvalidValue;
+  if (PP < 0) {
+    if (pb.p > 128) return cudaErrorInvalidValue;
+    switch (pb.variant) {
+      case MV_GAUSS_KNOWN: return launch_bigp_mv<MV_GAUSS_KNOWN>(pb, a, st);
+      case MV_GAUSS_LOGSIG: return launch_bigp_mv<MV_GAUSS_LOGSIG>(pb, a, st);
+      case MV_LOGISTIC: return launch_bigp_mv<MV_LOGISTIC>(pb, a, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (pb.variant) {
     case MV_GAUSS_KNOWN: return launch_flat_mv<MV_GAUSS_KNOWN>(pb, a, PP, st);
     case MV_GAUSS_LOGSIG: return launch_flat_mv<MV_GAUSS_LOGSIG>(pb, a, PP, st);

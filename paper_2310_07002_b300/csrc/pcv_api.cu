@@ -149,7 +149,8 @@ void free_all(pcv_ctx *x) {
 }
 
 int splits_for(const pcv_ctx *x, int C) {
-  const int tiles = (C + 31) / 32;
+  const int tw = x->tc ? 32 : simt_chain_tile(x->p);
+  const int tiles = (C + tw - 1) / tw;
   int s = (kTargetCtas + tiles - 1) / tiles;
   int cap;
   if (x->variant == MV_HIER) cap = std::max(1, x->G / 4);
@@ -158,10 +159,11 @@ int splits_for(const pcv_ctx *x, int C) {
 }
 
 pcv_status ensure_ws(pcv_ctx *x, int C, int splits) {
-  const int tiles = (C + 31) / 32;
+  const int tw = simt_chain_tile(x->p);
+  const int tiles = (C + tw - 1) / tw;
   const int PP = std::max(0, simt_flat_pp(x->p));
   const int stride = std::max(x->d_pad, PP) + 4;
-  const size_t need = (size_t)tiles * splits * 32 * stride;
+  const size_t need = (size_t)tiles * splits * tw * stride;
   if (need > x->ws_floats) {
     float *w;
     if (!dalloc_n(x, &w, need)) return fail(x, PCV_E_OOM, "workspace allocation failed");
@@ -552,7 +554,8 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
     return bail(PCV_E_INVALID_ARG, "sigma_prior_sd must be > 0");
   if (x->variant == MV_HIER && !(model->tau_prior_sd > 0)) return bail(PCV_E_INVALID_ARG, "tau_prior_sd must be > 0");
   const int PP = simt_flat_pp(p);
-  if (PP < 0 && !x->tc) return bail(PCV_E_UNSUPPORTED, "p > 32 needs the BF16 tensor-core precision");
+  if (!x->tc && (p > 128 || (PP < 0 && x->variant == MV_HIER)))
+    return bail(PCV_E_UNSUPPORTED, "FP32 path: p <= 128 (flat models) or p <= 32 (hierarchical)");
   x->p_pad = PP > 0 ? PP : (p + 3) / 4 * 4;
   if (x->tc) {
     x->KP = (p + 63) / 64 * 64;
@@ -1156,14 +1159,15 @@ extern "C" pcv_status pcv_log_density_noalloc(pcv_ctx *x, const float *theta, co
   if (!x) return PCV_E_INVALID_ARG;
   if (!theta || !fold || !logp || !grad || !shat || n < 1) return fail(x, PCV_E_INVALID_ARG, "bad argument");
   if (precision != PCV_FP32_SIMT) return fail(x, PCV_E_UNSUPPORTED, "precision not available for this context");
-  const int tiles = (n + 31) / 32;
+  const int tw = simt_chain_tile(x->p);
+  const int tiles = (n + tw - 1) / tw;
   const int stride = std::max(x->d_pad, simt_flat_pp(x->p)) + 4;
-  if (tiles > kNoAllocTickets || (size_t)tiles * 32 * stride > kNoAllocScratchFloats)
+  if (tiles > kNoAllocTickets || (size_t)tiles * tw * stride > kNoAllocScratchFloats)
     return fail(x, PCV_E_INVALID_ARG,
                 "pcv_log_density_noalloc: n = " + std::to_string(n) + " positions of dimension " +
                     std::to_string(x->d) + " exceed the fixed scratch (" +
                     std::to_string(kNoAllocScratchFloats) + " floats, " + std::to_string(kNoAllocTickets) +
-                    " tiles of 32); use pcv_log_density");
+                    " tiles of " + std::to_string(tw) + " chains); use pcv_log_density");
   float *ws = nullptr;
   unsigned int *tk = nullptr;
   CK(noalloc_addresses(&ws, &tk));
@@ -1171,7 +1175,7 @@ extern "C" pcv_status pcv_log_density_noalloc(pcv_ctx *x, const float *theta, co
   ChainBufs cb;
   cb.C = n; cb.L = 1; cb.fold_base = 0;
   GradArgs a = grad_args(x, cb, false);
-  const size_t per_split = (size_t)tiles * 32 * stride;
+  const size_t per_split = (size_t)tiles * tw * stride;
   a.splits = std::max(1, std::min(a.splits, (int)(kNoAllocScratchFloats / per_split)));
   a.fold_of = fold;
   a.theta = theta; a.ld_theta = x->d;

@@ -200,6 +200,8 @@ struct TcArgs {
 
 // launchers (k_grad_simt.cu)
 int simt_flat_pp(int p);
+size_t bigp_smem_bytes(int pp);
+int simt_chain_tile(int p);   // chains per CTA tile of the FP32 gradient kernels
 size_t hier_smem_bytes(int PP, int G, int splits);
 cudaError_t launch_grad_simt(const Problem &pb, const GradArgs &a, cudaStream_t st);
 

@@ -8,6 +8,8 @@ Tolerances (stated for FP32 kernels):
   normals: |d| <= 2e-6 (FP32 Box-Muller vs FP64)
   accumulators / estimators (FP64 on both sides): rtol 1e-9
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -33,6 +35,12 @@ def small_workloads():
         "logistic": W.logistic_loo(N=1037, p=20, K=25, L=3),
         "ar2": W.ar2_hvblock(T=1302, K=40, L=2),
         "hier": W.hier_logo(G=23, p=10, L=3, mean_extra=12.0),
+        # p > 32 takes the shared-memory-tiled FP32 kernel (64-chain tiles):
+        # 78 chains = 64 + 14, 1037 rows = 32 chunks of 32 + 13
+        "logistic_p100": W.logistic_loo(N=1037, p=100, K=25, L=3),
+        # Gaussian with sampled log sigma at p = 40 (gradient slot after beta)
+        "gauss_p40": dataclasses.replace(W.gauss_blocks(N=203, p=40, K=15, L=5),
+                                         sigma_known=-1.0, sigma_prior_sd=1.0),
     }
 
 
@@ -49,7 +57,7 @@ def rel_vec(a, b):
     return np.linalg.norm(a - b, axis=-1) / np.maximum(np.linalg.norm(b, axis=-1), 1e-30)
 
 
-@pytest.mark.parametrize("name", ["gauss", "logistic", "ar2", "hier"])
+@pytest.mark.parametrize("name", ["gauss", "logistic", "ar2", "hier", "logistic_p100", "gauss_p40"])
 def test_log_density_and_gradient(torch, orc, name):
     w = small_workloads()[name]
     pc = make_pcv(w)
@@ -84,10 +92,11 @@ def test_normals_match_oracle(torch, orc):
     pc.close()
 
 
-@pytest.mark.parametrize("name", ["gauss", "logistic", "ar2", "hier"])
+@pytest.mark.parametrize("name", ["gauss", "logistic", "ar2", "hier", "logistic_p100", "gauss_p40"])
 def test_single_trajectory(torch, orc, name):
     w = small_workloads()[name]
-    eps = {"gauss": 0.01, "logistic": 0.01, "ar2": 0.005, "hier": 0.01}[name]
+    eps = {"gauss": 0.01, "logistic": 0.01, "ar2": 0.005, "hier": 0.01, "logistic_p100": 0.004,
+           "gauss_p40": 0.002}[name]
     minv = np.linspace(0.5, 1.5, w.dim)
     pc = make_pcv(w, step_size=eps, inv_mass_diag=minv)
     prob = orc.problem_from_workload(w)
