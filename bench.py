@@ -5,7 +5,11 @@ momentum draw, L_f fused gradient+update launches, FP64 accept and the
 online accumulators).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload NAME] [--precision fp32|bf16|tf32]
+                  [--workload NAME] [--precision fp32|bf16|tf32] [--no-fp32-form]
+
+Default: the large random-block logistic workload (N=1e5, p=100, K=1000
+folds x 16 chains) in BF16 on the tensor cores, with the plain FP32 form
+timed beside it on the same GPU (`fp32_form`).
 
 Multi-GPU (torchrun, one rank per GPU): each rank runs its own copy of the
 workload with its own sampler seed (folds are independent posteriors, so the
@@ -43,6 +47,12 @@ WORKLOADS = {
     "hier_logo": lambda: W.hier_logo(),
     "ar2_hvblock": lambda: W.ar2_hvblock(),
 }
+
+
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
+# capture of that kernel (the profile summaries name the command); None when
+# the kernel changed after the capture.
+TRAFFIC = {}
 
 
 def peaks():
@@ -164,15 +174,50 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+def time_steps(P, w, prec, K, Wu, seed, barrier, flush, nvtx=True):
+    """Create a context for workload w at precision prec, run Wu untimed
+    warm-up iterations, then time K sampling iterations (one step each) with
+    CUDA events on the library's launch stream, L2 flushed before each step.
+    Returns (total_ms, chains, kernel_ms of the fused leapfrog launch)."""
+    import torch
+    common = dict(seed=seed, batch_size=1, max_batches=K + 64, acov_max_lag=64,
+                  precision=prec, init_scale=0.1)
+    pc = P.PCV.from_workload(w, **common)
+    pc.warmup(100, Wu)                                   # untimed warm-up iterations
+    stream = pc.stream
+    barrier()
+    step_ms = []
+    if nvtx:
+        torch.cuda.nvtx.range_push("pcv_timed")         # lets a profiler select these launches
+    for _ in range(K):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        pc.sample(1)                                     # CUDA events on the launch stream
+        step_ms.append(pc.last_sample_ms())
+    if nvtx:
+        torch.cuda.nvtx.range_pop()
+    barrier()
+    k_ms = pc.time_leapfrog_kernel(20)
+    C = pc.C
+    pc.close()
+    return float(np.sum(step_ms)), C, k_ms
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="logistic_loo", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"])
+    ap.add_argument("--workload", default="logistic_large", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "tf32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32-form", action="store_true",
+                    help="skip timing the plain FP32 form beside a BF16/TF32 run")
+    ap.add_argument("--profile-launches", action="store_true",
+                    help="for profiler captures: create the context, set positions "
+                         "(one gradient launch with log densities), then three "
+                         "kick-drift gradient launches; prints no JSON line")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -197,14 +242,21 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     prec = P.PRECISIONS[args.precision]
+    if args.profile_launches:
+        pc = P.PCV.from_workload(w, precision=prec)
+        theta0 = np.zeros((pc.C, w.dim))
+        truth = w.truth.get("beta", w.truth.get("phi"))
+        if truth is not None:
+            theta0[:, :len(truth)] = truth
+        pc.set_positions(theta0, step_size=1e-3)
+        ms = pc.time_leapfrog_kernel(2)
+        torch.cuda.synchronize()
+        pc.close()
+        print("profile launches done: %.3f ms per kick-drift launch" % ms, flush=True)
+        return
     K, Wu = args.steps, args.warmup
     seed = w.seed + 7919 * rank
-    common = dict(seed=seed, batch_size=1, max_batches=K + 64, acov_max_lag=64,
-                  precision=prec, init_scale=0.1)
-    pc = P.PCV.from_workload(w, **common)
-    pc.warmup(100, Wu)                                   # untimed warm-up iterations
-    stream = pc.stream
-    C, Lf = pc.C, w.leapfrog_steps
+    Lf = w.leapfrog_steps
     # L2 flush buffer (larger than the 126 MB L2), written between timed steps
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
@@ -215,18 +267,8 @@ def main():
         torch.cuda.synchronize()
 
     clocks = ClockSampler(local)
-    barrier()
-    step_ms = []
-    torch.cuda.nvtx.range_push("pcv_timed")             # lets a profiler select these launches
-    for _ in range(K):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-        pc.sample(1)                                     # CUDA events on the launch stream
-        step_ms.append(pc.last_sample_ms())
-    torch.cuda.nvtx.range_pop()
-    barrier()
+    total_ms, C, k_ms = time_steps(P, w, prec, K, Wu, seed, barrier, flush)
     clk = clocks.stop()
-    total_ms = float(np.sum(step_ms))
     if dist is not None:
         t = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -235,7 +277,6 @@ def main():
     value = evals / (total_ms / 1e3)
 
     # dominant kernel: the fused leapfrog gradient launch, timed live
-    k_ms = pc.time_leapfrog_kernel(20)
     fl = flops_per_grad_eval(w) * C
     pk, pk_kind = peaks()
     if prec == P.FP32_SIMT:
@@ -248,9 +289,18 @@ def main():
         roof = {"bound": "tensor", "achieved": fl / (k_ms / 1e3) / 1e12, "peak": pkv,
                 "unit": "TFLOP/s", "peak_source": "%s sustained bf16 x %.1f" % (pk_kind, ratio)}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = TRAFFIC.get((w.name, args.precision))
     roof["kernel_ms"] = k_ms
-    pc.close()
+    roof["flops_per_launch"] = fl
+
+    # the plain FP32 form on the same GPU, same workload (a few steps)
+    fp32_form = None
+    if prec != P.FP32_SIMT and not args.no_fp32_form:
+        K32 = max(1, min(K, 3))
+        ms32, _, k32 = time_steps(P, w, P.FP32_SIMT, K32, 3, seed, barrier, flush, nvtx=False)
+        v32 = float(C) * Lf * K32 * world / (ms32 / 1e3)
+        fp32_form = {"value": v32, "unit": "grad-evals/s", "steps": K32, "ms_per_step": ms32 / K32,
+                     "kernel_ms": k32, "speedup_of_this_run": value / v32}
 
     # end to end through the C ABI with host buffers: create (H2D of X, y,
     # folds), set positions (H2D), K iterations, scores + diagnostics (D2H)
@@ -260,7 +310,8 @@ def main():
         theta0[:, :len(truth)] = truth
     barrier()
     t0 = time.perf_counter()
-    pe = P.PCV.from_workload(w, **dict(common, batch_size=K // 2 if K % 2 == 0 else 1))
+    pe = P.PCV.from_workload(w, seed=seed, batch_size=K // 2 if K % 2 == 0 else 1,
+                             max_batches=K + 64, acov_max_lag=64, precision=prec, init_scale=0.1)
     pe.set_positions(theta0, step_size=1e-3)
     pe.sample(K)
     sc = pe.scores()
@@ -292,6 +343,8 @@ def main():
         "e2e": {"value": evals / e2e_s,
                 "unit": "grad-evals/s", "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K},
     }
+    if fp32_form is not None:
+        line["fp32_form"] = fp32_form
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, desc, cores = oracle_rate(w, 12.0, 64 if w.N * w.p < 1e6 else 16, os.cpu_count() or 1)
         line["cpu_baseline"] = {"value": r, "unit": "grad-evals/s", "cores": cores,

@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(256) k_grad_bigp(Problem pb, GradArgs a, int p
   float *xs = th_s + kBigTileC * ldt;               // [32][pp + 1]
   float *rs = xs + kBigRows * ldt;                  // [64][33]
   float *ys = rs + kBigTileC * 33;                  // [32]
-  float *lls = ys + kBigRows;                       // [2][64] ll partials, [64] dlogsig
+  float *lls = ys + kBigRows;                       // [3][64][8]: ll_tr, ll_te, dlogsig partials
   __shared__ int is_last;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int tile = blockIdx.x / a.splits, split = blockIdx.x - tile * a.splits;
@@ -383,7 +383,6 @@ __global__ void __launch_bounds__(256) k_grad_bigp(Problem pb, GradArgs a, int p
     const int c = c0 + cl;
     th_s[cl * ldt + j] = (c < a.C && j < p) ? a.theta[(size_t)c * a.ld_theta + j] : 0.0f;
   }
-  for (int q = t; q < 3 * kBigTileC; q += 256) lls[q] = 0.0f;
   // per-thread chain constants for the residual phase (chains cA, cA + 1)
   const int cA = (t >> 3) * 2, rA = (t & 7) * 4;
   float logsig[2] = {0.0f, 0.0f}, inv_s2[2] = {1.0f, 1.0f};
@@ -477,14 +476,22 @@ __global__ void __launch_bounds__(256) k_grad_bigp(Problem pb, GradArgs a, int p
     }
     __syncthreads();
   }
-  // per-chain likelihood sums: threads sharing cA (8 of them) add into smem
+  // per-chain likelihood sums: the 8 threads sharing cA leave their partials
+  // in shared memory; one thread per chain adds them in a fixed order
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
-    atomicAdd(&lls[cA + u], ll_tr[u]);
-    atomicAdd(&lls[kBigTileC + cA + u], ll_te[u]);
-    if (MV == MV_GAUSS_LOGSIG) atomicAdd(&lls[2 * kBigTileC + cA + u], dls[u]);
+    lls[(0 * kBigTileC + cA + u) * 8 + (t & 7)] = ll_tr[u];
+    lls[(1 * kBigTileC + cA + u) * 8 + (t & 7)] = ll_te[u];
+    lls[(2 * kBigTileC + cA + u) * 8 + (t & 7)] = dls[u];
   }
   __syncthreads();
+  float sums[3] = {0.0f, 0.0f, 0.0f};
+  if (t < kBigTileC) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+      for (int v = 0; v < 8; ++v) sums[q] += lls[(q * kBigTileC + t) * 8 + v];
+  }
   // partial of this CTA: [64 chains][ws_stride]: grads, slot pp dlogsig,
   // pp+1 ll_tr, pp+2 ll_te
   float *mine = a.ws + ((size_t)tile * a.splits + split) * kBigTileC * a.ws_stride;
@@ -494,9 +501,9 @@ __global__ void __launch_bounds__(256) k_grad_bigp(Problem pb, GradArgs a, int p
     for (int k = 0; k < 8; ++k)
       if (dg + 16 * k < pp) mine[(cg + i) * a.ws_stride + dg + 16 * k] = acc[i][k];
   if (t < kBigTileC) {
-    mine[t * a.ws_stride + pp] = lls[2 * kBigTileC + t];
-    mine[t * a.ws_stride + pp + 1] = lls[t];
-    mine[t * a.ws_stride + pp + 2] = lls[kBigTileC + t];
+    mine[t * a.ws_stride + pp] = sums[2];
+    mine[t * a.ws_stride + pp + 1] = sums[0];
+    mine[t * a.ws_stride + pp + 2] = sums[1];
   }
   __threadfence();
   __syncthreads();
@@ -547,9 +554,9 @@ int simt_chain_tile(int p) { return simt_flat_pp(p) > 0 ? 32 : kBigTileC; }
 
 size_t bigp_smem_bytes(int pp) {
   const int ldt = pp + 1;
-  size_t f = (size_t)kBigTileC * ldt + (size_t)kBigRows * ldt + kBigTileC * 33 + kBigRows + 3 * kBigTileC;
+  size_t f = (size_t)kBigTileC * ldt + (size_t)kBigRows * ldt + kBigTileC * 33 + kBigRows + 3 * kBigTileC * 8;
   const size_t tot = (size_t)kBigTileC * (pp + 4);
-  const size_t avail = (size_t)kBigRows * ldt + kBigTileC * 33 + kBigRows + 3 * kBigTileC;
+  const size_t avail = (size_t)kBigRows * ldt + kBigTileC * 33 + kBigRows + 3 * kBigTileC * 8;
   if (tot > avail) f += tot - avail;
   return f * sizeof(float);
 }

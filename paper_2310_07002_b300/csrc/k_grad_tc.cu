@@ -531,10 +531,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // that the per-chain writes are coalesced.
         __threadfence();
         float *stage = reinterpret_cast<float *>(stg);
-        double *lp_acc = reinterpret_cast<double *>(stg + ((stage_bytes + 7) & ~7u));   // 128 doubles
         const float *base = ta.ws + (size_t)t * ta.max_seg * (size_t)wstride * kTM;
         const size_t seg_stride = (size_t)wstride * kTM;
-        if (et < kTM) lp_acc[et] = 0.0;
         {
           const int mm = et & 127;
           for (int jj = et >> 7; jj < pb.p; jj += 2) {
@@ -560,8 +558,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           const float tv = th[jj];
           const float g = stage[jj * 129 + mm] - tv * pb.beta_prec;
           a.grad[(size_t)cc * a.ld_grad + jj] = g;
-          if (a.need_ll)
-            atomicAdd(&lp_acc[mm], -0.5 * kLog2PiD - (double)pb.log_beta_sd - 0.5 * (double)tv * tv * pb.beta_prec);
           if (a.mode != MODE_NONE) {
             float *rr = a.r + (size_t)cc * a.ld_theta;
             const float rj = rr[jj] + kick * g;
@@ -587,7 +583,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             s0 += (double)__ldcg(ws2 + (size_t)ta.PN * kTM + et) + (double)__ldcg(ws2 + (size_t)(ta.PN + 2) * kTM + et);
             s1 += (double)__ldcg(ws2 + (size_t)(ta.PN + 1) * kTM + et) + (double)__ldcg(ws2 + (size_t)(ta.PN + 3) * kTM + et);
           }
-          a.logp[cc] = s0 + lp_acc[et];
+          // log prior, summed in a fixed order (theta is not moved on the
+          // steps that need log densities, so it is the evaluation point)
+          const float *th = a.theta + (size_t)cc * a.ld_theta;
+          double q = 0.0;
+          for (int jj = 0; jj < pb.p; ++jj) {
+            const double tv = (double)th[jj];
+            q = fma(tv, tv, q);
+          }
+          const double lprior = (double)pb.p * (-0.5 * kLog2PiD - (double)pb.log_beta_sd) - 0.5 * pb.beta_prec * q;
+          a.logp[cc] = s0 + lprior;
           a.shat[cc] = s1;
         }
         // the staging area is reused only after every warp has finished

@@ -264,3 +264,24 @@ def test_error_codes(torch):
     with pytest.raises(PCVError) as e:
         PCV(3, w.X, w.y, f, 2, hv_buffer=2)
     assert e.value.status == E_INVALID_ARG
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_graph_replay_equals_plain_launches(torch, precision):
+    # The iteration replayed from a captured CUDA graph (counters in device
+    # memory) must produce bit-identical states and estimators to the same
+    # launches issued one by one.
+    from paper_2310_07002_b300.pcv import PRECISIONS
+    w = W.logistic_loo(N=517, p=20, K=30, L=4)
+    out = []
+    for graphs in (True, False):
+        pc = make_pcv(w, precision=PRECISIONS[precision], use_graphs=graphs, batch_size=10)
+        pc.warmup(40, 20)
+        pc.sample(60)
+        th, lp, sh = pc.positions()
+        sc = pc.scores()
+        dg = pc.diagnostics()
+        out.append((th, lp, sh, sc["elpd"], dg["rhat"], dg["ess_acov"]))
+        pc.close()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
