@@ -77,6 +77,8 @@ def _declare(L):
                                  ct.c_int32, ct.c_int32, ct.c_double]
     L.orc_pcv_create.restype = ct.c_void_p
     L.orc_pcv_destroy.argtypes = [ct.c_void_p]
+    L.orc_pcv_set_tuning.argtypes = [ct.c_void_p, ct.c_double, ct.c_double]
+    L.orc_pcv_set_tuning.restype = ct.c_int
     L.orc_pcv_fulldata.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_double]
     L.orc_pcv_fulldata.restype = ct.c_int
     L.orc_pcv_fold_warmup.argtypes = [ct.c_void_p, ct.c_int32]
@@ -198,7 +200,8 @@ class OraclePCV:
     def __init__(self, prob: _ProblemHolder, L: int, seed: int, Lf: int,
                  eps: float = -1.0, minv: Optional[np.ndarray] = None, b: int = 50,
                  M: int = 64, max_batches: int = 4096, store_draws: bool = False,
-                 n_threads: int = 0, init_scale: float = 1.0):
+                 n_threads: int = 0, init_scale: float = 1.0, traj_len: float = -1.0,
+                 jitter: float = -1.0):
         self.prob = prob
         self.L = L
         self.K = prob.s.K
@@ -208,6 +211,8 @@ class OraclePCV:
         nt = n_threads if n_threads > 0 else (os.cpu_count() or 1)
         self.h = lib().orc_pcv_create(ct.byref(prob.s), L, seed, Lf, eps, _dp(self._minv),
                                       b, M, max_batches, int(store_draws), nt, init_scale)
+        # trajectory-length cap and step-size jitter (< 0: the defaults)
+        lib().orc_pcv_set_tuning(self.h, traj_len, jitter)
 
     def __del__(self):
         if getattr(self, "h", None):

@@ -37,7 +37,8 @@
  *   counter = (block, chain, iteration, stream)
  *   block   = element index / 4 (each Philox call yields 4 words)
  *   streams: 0 fold-chain momentum, 1 fold-chain accept uniform,
- *            2 fold-chain init index, 16 full-data momentum,
+ *            2 fold-chain init index, 3 step-size jitter (chain 0: one
+ *            value per iteration, shared by all chains), 16 full-data momentum,
  *            17 full-data accept uniform, 18 full-data init position.
  *
  * Parity pins: see tests/test_oracle_*.py.  Every function here is pinned
@@ -55,7 +56,7 @@
 #define ORC_LOG_2PI 1.8378770664093454835606594728112
 
 enum { ORC_GAUSS = 0, ORC_LOGISTIC = 1, ORC_HIER = 2, ORC_AR = 3 };
-enum { ST_MOM = 0, ST_ACC = 1, ST_INIT = 2, ST_FD_MOM = 16, ST_FD_ACC = 17, ST_FD_INIT = 18 };
+enum { ST_MOM = 0, ST_ACC = 1, ST_INIT = 2, ST_JIT = 3, ST_FD_MOM = 16, ST_FD_ACC = 17, ST_FD_INIT = 18 };
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10                                                             */
@@ -196,11 +197,51 @@ static double lhalfnorm_logscale(double u, double s)
 }
 
 /*
+ * log N(e | 0, s2 I + t2 1 1') for a vector e of length m: the density of a
+ * group's rows after its intercept tau z ~ N(0, tau^2) is integrated out.
+ * Written out with a dense m x m Cholesky factor (plain on purpose).
+ */
+static double lmvn_compound(const double *e, int64_t m, double s2, double t2)
+{
+    double *A = (double *)malloc(sizeof(double) * (size_t)(m * m));
+    double *w = (double *)malloc(sizeof(double) * (size_t)m);
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t j = 0; j < m; ++j) A[i * m + j] = t2 + (i == j ? s2 : 0.0);
+    double logdet = 0.0;
+    for (int64_t j = 0; j < m; ++j) {              /* A = L L', L stored in the lower half */
+        double v = A[j * m + j];
+        for (int64_t q = 0; q < j; ++q) v -= A[j * m + q] * A[j * m + q];
+        const double ljj = sqrt(v);
+        A[j * m + j] = ljj;
+        logdet += 2.0 * log(ljj);
+        for (int64_t i = j + 1; i < m; ++i) {
+            double u = A[i * m + j];
+            for (int64_t q = 0; q < j; ++q) u -= A[i * m + q] * A[j * m + q];
+            A[i * m + j] = u / ljj;
+        }
+    }
+    double quad = 0.0;                             /* solve L w = e, quad = w'w */
+    for (int64_t i = 0; i < m; ++i) {
+        double u = e[i];
+        for (int64_t q = 0; q < i; ++q) u -= A[i * m + q] * w[q];
+        w[i] = u / A[i * m + i];
+        quad += w[i] * w[i];
+    }
+    free(A); free(w);
+    return -0.5 * (double)m * ORC_LOG_2PI - 0.5 * logdet - 0.5 * quad;
+}
+
+/*
  * Evaluate, for fold k and parameters theta (dimension orc_dim):
  *   logp = sum over training rows of log p(y_n | theta) + log prior(theta)
  *          (+ log-Jacobians of the log-scale parameters)      eq. mask-log-prob
  *   shat = sum over test rows of log p(y_n | theta)            eq. mask-log-pred
  *   grad = d logp / d theta
+ * Hierarchical model: a group none of whose rows trains in fold k is a new
+ * group for that fold, and its test rows are scored by the group-level
+ * predictive of eq. group-marg, the intercept tau z integrated over
+ * z ~ N(0, 1): log N(y_g | X_g beta, sigma^2 I + tau^2 1 1').  Test rows of
+ * a group that also has training rows use the sampled z.
  * Masks are built per call from the fold array (slow on purpose).
  */
 int orc_log_density(const orc_problem *P, int32_t k, const double *theta,
@@ -248,7 +289,7 @@ int orc_log_density(const orc_problem *P, int32_t k, const double *theta,
             dll_deta = e * inv_s2;
             if (train[n]) d_logsigma += -1.0 + e * e * inv_s2;
         }
-        if (test[n]) shat += ll;
+        if (test[n] && P->kind != ORC_HIER) shat += ll;
         if (train[n]) {
             logp += ll;
             for (int32_t j = 0; j < p; ++j) grad[j] += dll_deta * x[j];
@@ -257,6 +298,31 @@ int orc_log_density(const orc_problem *P, int32_t k, const double *theta,
                 d_logtau += dll_deta * tau * z[g];
             }
         }
+    }
+    if (P->kind == ORC_HIER) {
+        double *e = (double *)malloc(sizeof(double) * (size_t)N);
+        for (int32_t g = 0; g < P->G; ++g) {
+            int64_t m = 0, n_train = 0;
+            for (int64_t n = 0; n < N; ++n) {
+                if (P->group[n] != g) continue;
+                if (train[n]) ++n_train;
+                if (test[n]) {
+                    double eta = 0.0;
+                    for (int32_t j = 0; j < p; ++j) eta += P->X[n * p + j] * beta[j];
+                    e[m++] = P->y[n] - eta;
+                }
+            }
+            if (m == 0) continue;
+            if (n_train == 0) {
+                shat += lmvn_compound(e, m, sigma * sigma, tau * tau);
+            } else {
+                for (int64_t i = 0; i < m; ++i) {
+                    const double ei = e[i] - tau * z[g];
+                    shat += -0.5 * ORC_LOG_2PI - log_sigma - 0.5 * ei * ei * inv_s2;
+                }
+            }
+        }
+        free(e);
     }
     /* priors */
     for (int32_t j = 0; j < p; ++j) {
@@ -698,6 +764,8 @@ typedef struct {
     uint64_t seed;
     double eps;
     int adapt_eps;
+    double traj_len;          /* < 0: pi/2 when eps is adapted; 0: no cap */
+    double jitter;            /* < 0: 0.5 when eps is adapted, else 0 */
     double *minv;             /* d */
     int user_minv;
     double init_scale;
@@ -728,6 +796,7 @@ orc_pcv *orc_pcv_create(const orc_problem *P, int32_t L, uint64_t seed, int32_t 
     S->store_draws = store_draws; S->n_threads = n_threads > 0 ? n_threads : 1;
     S->seed = seed;
     S->eps = eps; S->adapt_eps = !(eps > 0);
+    S->traj_len = -1.0; S->jitter = -1.0;
     S->init_scale = init_scale > 0 ? init_scale : 1.0;
     S->minv = (double *)malloc(sizeof(double) * (size_t)S->d);
     S->user_minv = minv != NULL;
@@ -763,6 +832,28 @@ static void chain_refresh(const orc_problem *P, int32_t k, orc_chain *c)
     orc_log_density(P, k, c->theta, &c->logp, c->grad, &c->shat);
 }
 
+/* Trajectory length and step-size jitter (Section 3.1 reuses the full-data
+ * step size and trajectory length for every fold).  With L_f fixed, the
+ * adapted step size is capped at traj_len / L_f (traj_len in units of the
+ * adapted inverse mass, default pi/2), and the fold chains draw, once per
+ * iteration, eps_i = eps (1 + j (2u - 1)) with u from stream 3 (Neal 2011:
+ * a randomised step size breaks the periodicity of a fixed trajectory). */
+int orc_pcv_set_tuning(orc_pcv *S, double traj_len, double jitter)
+{
+    S->traj_len = traj_len;
+    S->jitter = jitter;
+    return 0;
+}
+static double eff_traj_len(const orc_pcv *S) { return S->traj_len < 0 ? 1.5707963267948966 : S->traj_len; }
+static double eff_jitter(const orc_pcv *S) { return S->jitter < 0 ? (S->adapt_eps ? 0.5 : 0.0) : S->jitter; }
+static double iter_eps(const orc_pcv *S, uint32_t iter)
+{
+    const double j = eff_jitter(S);
+    if (!(j > 0)) return S->eps;
+    const double u = orc_uniform(S->seed, 0, iter, ST_JIT);
+    return S->eps * (1.0 + j * (2.0 * u - 1.0));
+}
+
 /* Nesterov dual averaging of the log step size (Hoffman & Gelman 2014,
  * Section 3.2.1), target acceptance delta = 0.8, gamma = 0.05, t0 = 10,
  * kappa = 0.75. */
@@ -787,13 +878,15 @@ static void da_update(dual_avg *D, double accept_stat)
  * Full-data step (Step 1 of the workflow, as far as PCV needs it):
  * NFD = 4 full-data chains start from init_scale * N(0,1) (stream 18).
  * n_adapt iterations adapt eps by dual averaging (if no step size was given);
- * when no inverse mass was given, draws in iterations [n_adapt/4, n_adapt/2)
- * estimate a diagonal inverse mass, regularised as
- *   minv = w var + 1e-3 (1 - w), w = n / (n + 5),
- * after which dual averaging restarts from the current step size.  The final
- * step size is the dual-averaged exp(logeps_bar).  Then n_keep iterations at
- * fixed settings give the pool of 4 n_keep full-data draws (Algorithm 1,
- * "draw from {theta^(fd)}").
+ * when no inverse mass was given, the draws of two windows, iterations
+ * [n/4, n/2) and then [n/2, 7n/8) (n = n_adapt), each estimate a diagonal
+ * inverse mass, regularised as
+ *   minv = w var + 1e-3 (1 - w), w = m / (m + 5)   (m draws in the window),
+ * after which dual averaging restarts from the current step size (the second
+ * window sees chains that have settled and a sampler tuned to the first).
+ * The final step size is the dual-averaged exp(logeps_bar), capped at
+ * traj_len / L_f.  Then n_keep iterations at fixed settings give the pool of
+ * 4 n_keep full-data draws (Algorithm 1, "draw from {theta^(fd)}").
  */
 #define NFD 4
 int orc_pcv_fulldata(orc_pcv *S, int32_t n_adapt, int32_t n_keep, double eps0)
@@ -814,7 +907,7 @@ int orc_pcv_fulldata(orc_pcv *S, int32_t n_adapt, int32_t n_keep, double eps0)
     da_reset(&D, S->eps > 0 ? S->eps : 0.1);
     if (S->adapt_eps) { S->eps = eps0 > 0 ? eps0 : 0.1; da_reset(&D, S->eps); }
     int adapt_mass = S->adapt_eps && !S->user_minv;
-    int32_t w0 = n_adapt / 4, w1 = n_adapt / 2;
+    int32_t w0 = n_adapt / 4, w1 = n_adapt / 2, w2 = (7 * n_adapt) / 8;
     double wn = 0, *wmean = (double *)calloc((size_t)d, sizeof(double));
     double *wM2 = (double *)calloc((size_t)d, sizeof(double));
     uint32_t it = 0;
@@ -829,7 +922,7 @@ int orc_pcv_fulldata(orc_pcv *S, int32_t n_adapt, int32_t n_keep, double eps0)
             da_update(&D, asum / NFD);
             S->eps = exp(D.logeps);
         }
-        if (adapt_mass && i >= w0 && i < w1) {
+        if (adapt_mass && i >= w0 && i < w2) {
             for (int32_t c = 0; c < NFD; ++c) {
                 wn += 1.0;
                 for (int32_t j = 0; j < d; ++j) {
@@ -839,14 +932,20 @@ int orc_pcv_fulldata(orc_pcv *S, int32_t n_adapt, int32_t n_keep, double eps0)
                 }
             }
         }
-        if (adapt_mass && i == w1 - 1 && wn > 1) {
+        if (adapt_mass && (i == w1 - 1 || i == w2 - 1) && wn > 1) {
             double w = wn / (wn + 5.0);
             for (int32_t j = 0; j < d; ++j) S->minv[j] = w * (wM2[j] / (wn - 1.0)) + 1e-3 * (1.0 - w);
             for (int32_t c = 0; c < NFD; ++c) chain_refresh(P, -1, &ch[c]);
             da_reset(&D, S->eps);
+            wn = 0.0;                              /* the next window starts afresh */
+            for (int32_t j = 0; j < d; ++j) { wmean[j] = 0.0; wM2[j] = 0.0; }
         }
     }
-    if (S->adapt_eps && n_adapt > 0) S->eps = exp(D.logeps_bar);
+    if (S->adapt_eps && n_adapt > 0) {
+        S->eps = exp(D.logeps_bar);
+        const double T = eff_traj_len(S);
+        if (T > 0 && S->eps > T / S->Lf) S->eps = T / S->Lf;
+    }
     free(S->pool);
     S->n_pool = NFD * n_keep;
     S->pool = (double *)malloc(sizeof(double) * (size_t)S->n_pool * d);
@@ -880,7 +979,8 @@ int orc_pcv_fold_warmup(orc_pcv *S, int32_t n_wu)
         chain_refresh(P, k, &S->chains[c]);
         for (int32_t i = 0; i < n_wu; ++i) {
             int acc, div;
-            hmc_transition(P, k, S->seed, (uint32_t)c, S->iter + (uint32_t)i, ST_MOM, ST_ACC, S->eps,
+            const uint32_t it = S->iter + (uint32_t)i;
+            hmc_transition(P, k, S->seed, (uint32_t)c, it, ST_MOM, ST_ACC, iter_eps(S, it),
                            S->Lf, S->minv, &S->chains[c], work, &acc, &div);
         }
         free(work);
@@ -927,7 +1027,8 @@ int orc_pcv_sample(orc_pcv *S, int32_t n_draws)
         double *work = (double *)malloc(sizeof(double) * 3 * (size_t)d);
         for (int32_t i = 0; i < n_draws; ++i) {
             int acc, div;
-            hmc_transition(P, k, S->seed, (uint32_t)c, S->iter + (uint32_t)i, ST_MOM, ST_ACC, S->eps,
+            const uint32_t it = S->iter + (uint32_t)i;
+            hmc_transition(P, k, S->seed, (uint32_t)c, it, ST_MOM, ST_ACC, iter_eps(S, it),
                            S->Lf, S->minv, &S->chains[c], work, &acc, &div);
             S->acc[c].divergences += div;
             S->acc[c].accepts += acc;

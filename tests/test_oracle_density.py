@@ -112,9 +112,40 @@ def test_hier_against_scipy_and_fd(orc):
                      + stats.halfnorm.logpdf(tau, scale=1.0) + lt
                      + stats.halfnorm.logpdf(sig, scale=1.0) + ls)
             assert abs(lp - (ll[train].sum() + prior)) < 1e-9 * abs(lp)
-            assert abs(sh - ll[test].sum()) < 1e-9 * max(1, abs(sh))
+            # LOGO: the held-out group is a new group; its rows are scored by
+            # the group-level predictive (eq. group-marg) with the intercept
+            # tau z integrated over z ~ N(0, 1): a multivariate normal with
+            # covariance sigma^2 I + tau^2 11'
+            ref = 0.0
+            for grp in np.unique(w.group[test]):
+                rows = test & (w.group == grp)
+                m = int(rows.sum())
+                cov = sig ** 2 * np.eye(m) + tau ** 2 * np.ones((m, m))
+                ref += stats.multivariate_normal.logpdf(w.y[rows], w.X[rows] @ beta, cov)
+            assert abs(sh - ref) < 1e-9 * max(1, abs(sh))
             gfd = fd_grad(lambda t: orc.log_density(prob, k, t)[0], th)
             assert np.allclose(g, gfd, rtol=1e-6, atol=1e-5)
+
+
+def test_hier_heldout_group_is_integrated_over_its_intercept(orc):
+    # the same quantity by numerical integration of the definition:
+    # log int prod_n N(y_n | x_n beta + tau z, sigma^2) N(z | 0, 1) dz
+    from scipy import integrate
+    w = W.hier_logo(G=6, p=2, L=2, mean_extra=3.0)
+    prob = orc.problem_from_workload(w)
+    th = W.random_theta(w.dim, 1, scale=0.4, seed=5)[0]
+    beta, lt, ls = th[:2], th[2 + 6], th[3 + 6]
+    tau, sig = np.exp(lt), np.exp(ls)
+    k = 3
+    _, _, sh = orc.log_density(prob, k, th)
+    rows = w.fold == k
+    e = w.y[rows] - w.X[rows] @ beta
+    c = np.max(stats.norm.logpdf(e, 0.0, sig).sum() + 0.0)   # scale for the integrand
+
+    def integrand(z):
+        return np.exp(stats.norm.logpdf(e, tau * z, sig).sum() - c) * stats.norm.pdf(z)
+    val, _ = integrate.quad(integrand, -12, 12, epsabs=0, epsrel=1e-12, limit=400)
+    assert abs(sh - (np.log(val) + c)) < 1e-8 * max(1.0, abs(sh))
 
 
 def test_rows_in_no_test_set_always_train(orc):
