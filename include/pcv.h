@@ -114,6 +114,18 @@ typedef struct {
     pcv_alloc_fn device_alloc; /* optional allocator (see above) */
     pcv_free_fn device_free;
     void *alloc_user;
+    /* Trajectory length and step-size jitter. The paper reuses the full-data
+     * step size and trajectory length for every fold (Section 3.1); with
+     * leapfrog_steps fixed, an adapted step size is capped at
+     * trajectory_length / leapfrog_steps (trajectory_length in units of the
+     * adapted inverse mass; < 0: pi/2 when the step size is adapted, 0: no
+     * cap). Fold chains then draw one step size per iteration, shared by all
+     * chains, eps (1 + step_jitter (2u - 1)) with u from Philox stream 3,
+     * which breaks the periodicity of a fixed trajectory (Neal 2011).
+     * step_jitter < 0: 0.5 when the step size is adapted, else 0; must be
+     * < 1. */
+    double trajectory_length;
+    double step_jitter;
 } pcv_options;
 
 /* Fill *opt with the defaults listed above (seed 0, L_f 16, adapted step). */

@@ -223,6 +223,17 @@ __global__ void __launch_bounds__(kWarps * 32) k_grad_flat(Problem pb, GradArgs 
 // written only for the groups the CTA owns.  The finishing CTA sums the
 // shared slots over splits and takes each z slot from its owner split.
 // ---------------------------------------------------------------------------
+// log N(e | 0, s^2 I + t^2 1 1') of a group of m rows with residuals e
+// (intercept integrated out), from S1 = sum e and S2 = sum e^2:
+//   det = s^(2(m-1)) (s^2 + m t^2),
+//   e' inv e = (S2 - t^2 S1^2 / (s^2 + m t^2)) / s^2
+__device__ __forceinline__ double new_group_log_pred(float S1, float S2, int m, float logsig, float logtau) {
+  const double s2 = exp(2.0 * (double)logsig), t2 = exp(2.0 * (double)logtau);
+  const double den = s2 + (double)m * t2;
+  const double q = ((double)S2 - t2 * (double)S1 * (double)S1 / den) / s2;
+  return -0.5 * (double)m * kLog2PiD - 0.5 * ((double)(m - 1) * log(s2) + log(den)) - 0.5 * q;
+}
+
 template <int PP>
 __global__ void __launch_bounds__(kWarps * 32) k_grad_hier(Problem pb, GradArgs a) {
   constexpr int S = PP + 4;        // beta grads, dlogtau, dlogsig, ll_tr, ll_te
@@ -259,6 +270,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_grad_hier(Problem pb, GradArgs 
     const float z = valid ? tp[p + gid] : 0.0f;
     const float off = tau * z;
     const int n0 = __ldg(pb.grp_off + gg), n1 = __ldg(pb.grp_off + gg + 1);
+    // a group held out by this chain's fold has no training rows there: it
+    // is a new group, scored by the group-level predictive (eq. group-marg)
+    // from the sums of e0 = y - x beta over its rows
+    const bool test_seg = a.need_ll && valid && n1 > n0 && n0 >= fd.test_lo && n1 <= fd.test_hi;
+    float s1 = 0.0f, s2 = 0.0f;
     float seg = 0.0f;
     for (int n = n0; n < n1; ++n) {
       float x[PP];
@@ -280,11 +296,15 @@ __global__ void __launch_bounds__(kWarps * 32) k_grad_hier(Problem pb, GradArgs 
       dls = fmaf(tr, e * e * inv_s2 - 1.0f, dls);
       if (a.need_ll) {
         const float ll = -0.5f * kLog2Pi - logsig - 0.5f * e * e * inv_s2;
-        const float te = (n >= fd.test_lo && n < fd.test_hi) ? 1.0f : 0.0f;
         ll_tr = fmaf(tr, ll, ll_tr);
-        ll_te = fmaf(te, ll, ll_te);
+        if (test_seg) {
+          const float e0 = e + off;
+          s1 += e0;
+          s2 = fmaf(e0, e0, s2);
+        }
       }
     }
+    if (test_seg) ll_te += (float)new_group_log_pred(s1, s2, n1 - n0, logsig, logtau);
     mine[lane * a.ws_stride + p + gid] = tau * seg;  // d/dz_g of the likelihood
     dlt = fmaf(seg, off, dlt);                        // d/dlog tau: sum_g seg_g tau z_g
   }

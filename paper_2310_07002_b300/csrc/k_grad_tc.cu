@@ -47,6 +47,14 @@ constexpr int kTM = 128;        // chains per tile
 constexpr int kTcThreads = 352; // 11 warps: TMA, GEMM1 MMA, 8 epilogue, GEMM2 MMA
 
 
+// softplus(eta) for eta = 2 s (the first GEMM yields s = eta / 2):
+// max(eta, 0) + ln 2 * log2(1 + 2^(-|eta| log2 e)), two MUFU operations
+__device__ __forceinline__ float softplus_half(float s) {
+  const float e = exp2f(fabsf(s) * -2.8853900817779268f);   // 2^(-2|s| log2 e) = e^-|eta|
+  const float m = fmaxf(s, 0.0f);
+  return fmaf(__log2f(1.0f + e), 0.6931471805599453f, m + m);
+}
+
 // ----------------------------- PTX helpers --------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -413,7 +421,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     const bool accurate = ta.accurate != 0;
     const uint32_t neg_half2 = 0xBF00BF00u;         // (-0.5, -0.5) in bf16x2
-    const int wstride = ta.PN + 4;                  // workspace rows per segment
+    const int wstride = ta.PN + kTcSlots;           // workspace rows per segment
     const int sb = eg, rb = eg;                     // this group's S and R buffers
     int nseg_done = 0, nfin = 0;
     bool aborted = false;
@@ -425,7 +433,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const bool valid = c < a.C;
       FoldDesc fd = {0, 0, 0, 0};
       if (valid) fd = pb.folds[fold_of_chain(a, c)];
-      float ll_tr = 0.0f, ll_te = 0.0f;
+      double sp_tr = 0.0, sp_te = 0.0;              // softplus sums (train, test rows)
       for (int i = ib + ((ib & 1) != eg ? 1 : 0); i < ie; i += 2) {
         const int j = j0 + (i - ib);
         if (!warp_wait(smem_u32(&s_full[sb]), (i >> 1) & 1, abort_flag, ta.err)) { aborted = true; break; }
@@ -465,19 +473,28 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
           }
           if (accurate) {
-            // masked log likelihood y eta - softplus(eta), softplus(eta) =
-            // max(eta, 0) + log(1 + exp(-|eta|)), FP32 (2 MUFU operations)
+            // log likelihood y eta - softplus(eta): the linear part is
+            // theta . sum(y x) per fold (added in the finish), so only
+            // softplus(eta) = max(eta, 0) + log(1 + exp(-|eta|)) is summed
+            // here, in FP32 per half chunk and FP64 across chunks.
+            // Half chunks clear of the fold's excluded rows and of the
+            // padding need no per-row mask.
+            if (n0 + 64 <= pb.N && (n0 + 64 <= fd.excl_lo || n0 >= fd.excl_hi)) {
+              float acc4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-            for (int k = 0; k < 64; ++k) {
-              const int n = n0 + k;
-              const float eta = 2.0f * __uint_as_float(v[k]);
-              const uint32_t y2 = yw[k >> 1];
-              const float yv = __uint_as_float((k & 1) ? (y2 & 0xFFFF0000u) : (y2 << 16)) + 0.5f;
-              const float e = exp2f(-fabsf(eta) * 1.4426950408889634f);
-              const float ll = yv * eta - fmaxf(eta, 0.0f) - __log2f(1.0f + e) * 0.6931471805599453f;
-              const bool in_rows = n < pb.N;
-              if (in_rows && (n < fd.excl_lo || n >= fd.excl_hi)) ll_tr += ll;
-              if (in_rows && n >= fd.test_lo && n < fd.test_hi) ll_te += ll;
+              for (int k = 0; k < 64; ++k) acc4[k & 3] += softplus_half(__uint_as_float(v[k]));
+              sp_tr += (double)((acc4[0] + acc4[1]) + (acc4[2] + acc4[3]));
+            } else {
+              float tr = 0.0f, te = 0.0f;
+#pragma unroll
+              for (int k = 0; k < 64; ++k) {
+                const int n = n0 + k;
+                const float sp = softplus_half(__uint_as_float(v[k]));
+                if (n < pb.N && (n < fd.excl_lo || n >= fd.excl_hi)) tr += sp;
+                if (n >= fd.test_lo && n < fd.test_hi) te += sp;
+              }
+              sp_tr += (double)tr;
+              sp_te += (double)te;
             }
           }
           // R row m (TMEM lane m): chunk rows 64 h .. 64 h + 63 as 32 bf16x2 columns
@@ -510,8 +527,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(g_empty));
       }
-      wsp[(size_t)(ta.PN + 2 * eg) * kTM + m] = ll_tr;
-      wsp[(size_t)(ta.PN + 2 * eg + 1) * kTM + m] = ll_te;
+      {
+        const float h0 = (float)sp_tr, h1 = (float)sp_te;
+        wsp[(size_t)(ta.PN + 4 * eg + 0) * kTM + m] = h0;
+        wsp[(size_t)(ta.PN + 4 * eg + 1) * kTM + m] = (float)(sp_tr - (double)h0);
+        wsp[(size_t)(ta.PN + 4 * eg + 2) * kTM + m] = h1;
+        wsp[(size_t)(ta.PN + 4 * eg + 3) * kTM + m] = (float)(sp_te - (double)h1);
+      }
       __threadfence();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(flush_bar));
@@ -577,23 +599,30 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (!warp_wait(smem_u32(fin_bar), (3 * nfin + 1) & 1, abort_flag, ta.err)) break;
         if (a.need_ll && et < kTM && t * kTM + et < a.C) {
           const int cc = t * kTM + et;
-          double s0 = 0.0, s1 = 0.0;
+          double s0 = 0.0, s1 = 0.0;                // softplus sums over train / test rows
           for (int s2 = 0; s2 < nseg; ++s2) {
-            const float *ws2 = base + s2 * seg_stride;
-            s0 += (double)__ldcg(ws2 + (size_t)ta.PN * kTM + et) + (double)__ldcg(ws2 + (size_t)(ta.PN + 2) * kTM + et);
-            s1 += (double)__ldcg(ws2 + (size_t)(ta.PN + 1) * kTM + et) + (double)__ldcg(ws2 + (size_t)(ta.PN + 3) * kTM + et);
+            const float *ws2 = base + s2 * seg_stride + (size_t)ta.PN * kTM + et;
+#pragma unroll
+            for (int g2 = 0; g2 < 2; ++g2) {
+              s0 += (double)__ldcg(ws2 + (4 * g2 + 0) * kTM) + (double)__ldcg(ws2 + (4 * g2 + 1) * kTM);
+              s1 += (double)__ldcg(ws2 + (4 * g2 + 2) * kTM) + (double)__ldcg(ws2 + (4 * g2 + 3) * kTM);
+            }
           }
-          // log prior, summed in a fixed order (theta is not moved on the
-          // steps that need log densities, so it is the evaluation point)
+          // linear part theta . sum(y x) and the log prior, in a fixed order
+          // (theta is not moved on the steps that need log densities, so it
+          // is the evaluation point)
           const float *th = a.theta + (size_t)cc * a.ld_theta;
-          double q = 0.0;
+          const double *yl = ta.ylin + (size_t)fold_of_chain(a, cc) * 2 * pb.p;
+          double q = 0.0, lin_tr = 0.0, lin_te = 0.0;
           for (int jj = 0; jj < pb.p; ++jj) {
             const double tv = (double)th[jj];
             q = fma(tv, tv, q);
+            lin_tr = fma(tv, yl[jj], lin_tr);
+            lin_te = fma(tv, yl[pb.p + jj], lin_te);
           }
           const double lprior = (double)pb.p * (-0.5 * kLog2PiD - (double)pb.log_beta_sd) - 0.5 * pb.beta_prec * q;
-          a.logp[cc] = s0 + lprior;
-          a.shat[cc] = s1;
+          a.logp[cc] = (lin_tr - s0) + lprior;
+          a.shat[cc] = lin_te - s1;
         }
         // the staging area is reused only after every warp has finished
         __syncwarp();

@@ -22,7 +22,14 @@ __global__ void __launch_bounds__(256) k_begin(BeginArgs a) {
   const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (c >= a.C) return;
   const unsigned it = *a.iter;
-  const float eps = *a.eps;
+  // this iteration's step size: the nominal one, or (fold chains) jittered
+  // by one uniform per iteration shared by every chain (stream ST_JIT)
+  float eps = *a.eps;
+  if (a.jitter > 0.0f) {
+    const uint4 w = philox_at(a.seed, 0u, 0u, it, ST_JIT);
+    eps = (float)((double)eps * (1.0 + (double)a.jitter * (2.0 * unit_from_word(w.x) - 1.0)));
+  }
+  if (a.eps_iter && c == 0 && lane == 0) *a.eps_iter = eps;
   const float *th = a.theta + (size_t)c * a.ld;
   const float *g = a.grad + (size_t)c * a.ld;
   double kin = 0.0;
@@ -294,7 +301,7 @@ __global__ void k_fd_adapt(FdAdaptArgs a) {
       st->eps = (float)exp(st->da_logeps);
     }
     __syncthreads();
-    if (a.adapt_mass && i >= a.w0 && i < a.w1) {
+    if (a.adapt_mass && i >= a.w0 && i < a.w2) {
       const double n0 = a.st->mass_n;
       for (int j = threadIdx.x; j < a.d; j += blockDim.x) {
         double m = a.wmean[j], M2 = a.wM2[j];
@@ -311,11 +318,20 @@ __global__ void k_fd_adapt(FdAdaptArgs a) {
       if (threadIdx.x == 0) a.st->mass_n = n0 + a.C;
       __syncthreads();
       const double wn = a.st->mass_n;
-      if (i == a.w1 - 1 && wn > 1.0) {
+      if ((i == a.w1 - 1 || i == a.w2 - 1) && wn > 1.0) {
+        // end of a mass window: regularised variance, restart dual
+        // averaging, and start the next window's Welford sums afresh
         const double w = wn / (wn + 5.0);
-        for (int j = threadIdx.x; j < a.d; j += blockDim.x)
+        for (int j = threadIdx.x; j < a.d; j += blockDim.x) {
           a.minv[j] = (float)(w * (a.wM2[j] / (wn - 1.0)) + 1e-3 * (1.0 - w));
-        if (threadIdx.x == 0) da_reset(a.st, (double)a.st->eps);
+          a.wmean[j] = 0.0;
+          a.wM2[j] = 0.0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          da_reset(a.st, (double)a.st->eps);
+          a.st->mass_n = 0.0;
+        }
       }
     }
   } else {
@@ -331,13 +347,23 @@ __global__ void k_fd_adapt(FdAdaptArgs a) {
 
 __global__ void k_fd_init_state(IterState *st, float eps0, int adapt) {
   st->eps = eps0;
+  st->eps_iter = eps0;
   da_reset(st, (double)eps0);
   st->mass_n = 0.0;
   st->fd_iter = 0u;
   (void)adapt;
 }
 
-__global__ void k_fd_final_eps(IterState *st) { st->eps = (float)exp(st->da_logeps_bar); }
+// the dual-averaged step size, capped so that L_f steps span at most the
+// trajectory length (eps_cap = trajectory length / L_f; <= 0: no cap)
+__global__ void k_fd_final_eps(IterState *st, float eps_cap) {
+  float e = (float)exp(st->da_logeps_bar);
+  if (eps_cap > 0.0f && e > eps_cap) e = eps_cap;
+  st->eps = e;
+  st->eps_iter = e;
+}
+
+__global__ void k_copy_eps(IterState *st) { st->eps_iter = st->eps; }
 
 // ---------------------------------------------------------------------------
 // per-fold estimators

@@ -60,6 +60,8 @@ struct pcv_ctx {
   int kind = 0, variant = 0, p = 0, p_pad = 0, d = 0, d_pad = 0, K = 0, L = 0, C = 0, G = 0;
   int64_t N = 0;
   int h = 0, Lf = 16, b = 50, M = 64, max_batches = 1024, n_fd_draws = 250;
+  double traj_len = 0.0;          // effective trajectory length (0: no cap)
+  float jitter = 0.0f;            // effective step-size jitter of the fold chains
   Problem pb{};
   std::vector<void *> allocs;
   // device buffers
@@ -91,6 +93,7 @@ struct pcv_ctx {
   __nv_bfloat16 *X16 = nullptr, *yc16 = nullptr;
   CUtensorMap tm_x{};
   float *ws_tc = nullptr;
+  double *ylin = nullptr;         // tensor-core path: per-fold sums of y x (see TcArgs)
   size_t ws_tc_floats = 0;
   unsigned int *tickets_tc = nullptr;
   size_t n_tickets_tc = 0;
@@ -230,6 +233,7 @@ TcArgs tc_args(pcv_ctx *x, int C, bool need_lo) {
   t.NS = tc_smem_bytes(t.KP, 4, 1, x->p) <= 227 * 1024 ? 4 : (tc_smem_bytes(t.KP, 3, 1, x->p) <= 227 * 1024 ? 3 : 2);
   t.yc = x->yc16;
   t.ws = x->ws_tc;
+  t.ylin = x->ylin;
   t.tickets = x->tickets_tc;
   t.err = &x->st->error;
   return t;
@@ -237,7 +241,7 @@ TcArgs tc_args(pcv_ctx *x, int C, bool need_lo) {
 
 pcv_status ensure_ws_tc(pcv_ctx *x, int C) {
   TcArgs t = tc_args(x, C, false);
-  const size_t need = (size_t)t.T * t.max_seg * (t.PN + 4) * 128;
+  const size_t need = (size_t)t.T * t.max_seg * (t.PN + kTcSlots) * 128;
   if (need > x->ws_tc_floats) {
     float *w;
     if (!dalloc_n(x, &w, need)) return fail(x, PCV_E_OOM, "workspace allocation failed");
@@ -268,7 +272,7 @@ GradArgs grad_args(pcv_ctx *x, const ChainBufs &cb, bool proposal) {
   a.need_ll = 1;
   a.mode = MODE_NONE;
   a.r = cb.r;
-  a.eps = &x->st->eps;
+  a.eps = &x->st->eps_iter;
   a.minv = x->minv;
   a.splits = splits_for(x, cb.C);
   a.ws = x->ws;
@@ -325,6 +329,8 @@ pcv_status launch_iteration(pcv_ctx *x, ChainBufs &cb, bool fd, bool accumulate)
   ba.theta = cb.theta; ba.grad = cb.grad; ba.logp = cb.logp;
   ba.theta_p = cb.theta_p; ba.r = cb.r; ba.H0 = cb.H0;
   ba.eps = &x->st->eps; ba.minv = x->minv;
+  ba.jitter = fd ? 0.0f : x->jitter;
+  ba.eps_iter = &x->st->eps_iter;
   ba.r_given = nullptr;
   ba.shadow_hi = x->tc ? cb.shadow_hi : nullptr;
   ba.shadow_lo = x->tc ? cb.shadow_lo : nullptr;
@@ -359,6 +365,7 @@ pcv_status launch_iteration(pcv_ctx *x, ChainBufs &cb, bool fd, bool accumulate)
     fa.n_adapt = x->fd_n_adapt;
     fa.w0 = x->fd_n_adapt / 4;
     fa.w1 = x->fd_n_adapt / 2;
+    fa.w2 = (7 * x->fd_n_adapt) / 8;
     fa.adapt_eps = !(x->opt.step_size > 0);
     fa.adapt_mass = fa.adapt_eps && x->opt.inv_mass_diag == nullptr;
     fa.C = cb.C; fa.d = x->d; fa.ld = x->d_pad;
@@ -503,6 +510,8 @@ void pcv_default_options(pcv_options *o) {
   o->n_fulldata_draws = 250;
   o->init_scale = 1.0;
   o->use_graphs = 1;
+  o->trajectory_length = -1.0;
+  o->step_jitter = -1.0;
 }
 
 pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
@@ -513,7 +522,8 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
   if (!model || !X || !y || !fold_assignment || !opt) return PCV_E_INVALID_ARG;
   if (N < 1 || p < 1 || chains_per_fold < 2 || N > (int64_t)1 << 30) return PCV_E_INVALID_ARG;
   if (opt->leapfrog_steps < 1 || opt->batch_size < 1 || opt->hv_buffer < 0 ||
-      opt->acov_max_lag < 0 || opt->max_batches < 1 || opt->n_fulldata_draws < 1)
+      opt->acov_max_lag < 0 || opt->max_batches < 1 || opt->n_fulldata_draws < 1 ||
+      !(opt->step_jitter < 1.0) || !std::isfinite(opt->trajectory_length))
     return PCV_E_INVALID_ARG;
   if (model->kind < PCV_GAUSS_LINEAR || model->kind > PCV_AR_GAUSS) return PCV_E_INVALID_ARG;
   if (!(model->beta_prior_sd > 0)) return PCV_E_INVALID_ARG;
@@ -524,6 +534,13 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
   x->N = N; x->p = p; x->L = chains_per_fold;
   x->h = opt->hv_buffer; x->Lf = opt->leapfrog_steps; x->b = opt->batch_size;
   x->M = opt->acov_max_lag; x->max_batches = opt->max_batches; x->n_fd_draws = opt->n_fulldata_draws;
+  {
+    // trajectory length (cap of the adapted step size) and step-size jitter:
+    // < 0 selects the defaults, which apply when the step size is adapted
+    const bool adapted = !(opt->step_size > 0);
+    x->traj_len = opt->trajectory_length < 0 ? (adapted ? 1.5707963267948966 : 0.0) : opt->trajectory_length;
+    x->jitter = (float)(opt->step_jitter < 0 ? (adapted ? 0.5 : 0.0) : opt->step_jitter);
+  }
   auto bail = [&](pcv_status s, const std::string &m) {
     // creation failed: release everything; report through a static message
     static thread_local std::string last;
@@ -663,8 +680,29 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
       for (int j = 0; j < p; ++j) hX16[(size_t)r * x->KP + j] = __float2bfloat16_rn(hX[(size_t)r * x->p_pad + j]);
       hyc[r] = __float2bfloat16_rn(hy[r] - 0.5f);
     }
-    if (!dalloc_n(x, &x->X16, hX16.size()) || !dalloc_n(x, &x->yc16, hyc.size()))
+    // per fold: sum over training rows and over test rows of y_n x_n, with
+    // the bf16 X the tensor cores see (the linear part of the logistic log
+    // likelihood is theta . these sums); fold K is the full data
+    std::vector<double> hyl((size_t)(K + 1) * 2 * p, 0.0), all(p, 0.0);
+    auto add_rows = [&](double *dst, int64_t r0, int64_t r1) {
+      for (int64_t r = r0; r < r1; ++r) {
+        if (hy[r] == 0.0f) continue;
+        for (int j = 0; j < p; ++j) dst[j] += (double)__bfloat162float(hX16[(size_t)r * x->KP + j]);
+      }
+    };
+    add_rows(all.data(), 0, N);
+    std::vector<double> ex(p);
+    for (int k = 0; k <= K; ++k) {
+      double *tr = &hyl[(size_t)k * 2 * p], *te = tr + p;
+      std::fill(ex.begin(), ex.end(), 0.0);
+      add_rows(ex.data(), fds[k].excl_lo, fds[k].excl_hi);
+      add_rows(te, fds[k].test_lo, fds[k].test_hi);
+      for (int j = 0; j < p; ++j) tr[j] = all[j] - ex[j];
+    }
+    if (!dalloc_n(x, &x->X16, hX16.size()) || !dalloc_n(x, &x->yc16, hyc.size()) ||
+        !dalloc_n(x, &x->ylin, hyl.size()))
       return bail(PCV_E_OOM, "device allocation failed");
+    cudaMemcpyAsync(x->ylin, hyl.data(), hyl.size() * sizeof(double), cudaMemcpyHostToDevice, x->stream);
     cudaMemcpyAsync(x->X16, hX16.data(), hX16.size() * 2, cudaMemcpyHostToDevice, x->stream);
     cudaMemcpyAsync(x->yc16, hyc.data(), hyc.size() * 2, cudaMemcpyHostToDevice, x->stream);
     if (cudaStreamSynchronize(x->stream) != cudaSuccess) return bail(PCV_E_CUDA, "upload failed");
@@ -702,6 +740,7 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
   }
   IterState hst{};
   hst.eps = opt->step_size > 0 ? (float)opt->step_size : 0.1f;
+  hst.eps_iter = hst.eps;
   cudaMemcpyAsync(x->st, &hst, sizeof(hst), cudaMemcpyHostToDevice, x->stream);
 
   Problem &pb = x->pb;
@@ -759,7 +798,7 @@ pcv_status pcv_warmup(pcv_ctx *x, int32_t n_fd, int32_t n_wu) {
   s = run_iterations(x, x->fd_cb, true, false, n_fd, &x->g_fd_1, 1);
   if (s != PCV_OK) return s;
   if (adapt && n_fd > 0) {
-    k_fd_final_eps<<<1, 1, 0, x->stream>>>(x->st);
+    k_fd_final_eps<<<1, 1, 0, x->stream>>>(x->st, x->traj_len > 0 ? (float)(x->traj_len / x->Lf) : 0.0f);
     CK(cudaGetLastError());
   }
   s = run_iterations(x, x->fd_cb, true, false, x->n_fd_draws, &x->g_fd_1, 1);
@@ -878,8 +917,9 @@ pcv_status pcv_set_positions(pcv_ctx *x, const double *theta, double step_size, 
     }
   CK(cudaMemcpyAsync(x->fold_cb.theta, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, x->stream));
   if (step_size > 0) {
-    const float e = (float)step_size;
-    CK(cudaMemcpyAsync(&x->st->eps, &e, sizeof(float), cudaMemcpyHostToDevice, x->stream));
+    const float e[2] = {(float)step_size, (float)step_size};   // eps, eps_iter
+    static_assert(offsetof(IterState, eps_iter) == offsetof(IterState, eps) + sizeof(float), "layout");
+    CK(cudaMemcpyAsync(&x->st->eps, e, sizeof(e), cudaMemcpyHostToDevice, x->stream));
   }
   if (inv_mass) {
     std::vector<float> hm(x->d_pad, 1.0f);
@@ -990,6 +1030,7 @@ pcv_status pcv_trajectory(pcv_ctx *x, const float *theta0, const float *r0, int3
   ba.theta = cb.theta; ba.grad = cb.grad; ba.logp = cb.logp;
   ba.theta_p = cb.theta_p; ba.r = cb.r; ba.H0 = cb.H0;
   ba.eps = &x->st->eps; ba.minv = x->minv; ba.r_given = rstart;
+  ba.jitter = 0.0f; ba.eps_iter = &x->st->eps_iter;
   ba.shadow_hi = x->tc ? cb.shadow_hi : nullptr;
   ba.shadow_lo = x->tc ? cb.shadow_lo : nullptr;
   ba.ld_shadow = x->KP;

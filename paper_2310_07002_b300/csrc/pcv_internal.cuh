@@ -17,7 +17,7 @@ enum ModelVariant : int {
 
 // Philox stream tags (the counter's last word)
 enum Stream : uint32_t {
-  ST_MOM = 0, ST_ACC = 1, ST_INIT = 2, ST_FD_MOM = 16, ST_FD_ACC = 17, ST_FD_INIT = 18
+  ST_MOM = 0, ST_ACC = 1, ST_INIT = 2, ST_JIT = 3, ST_FD_MOM = 16, ST_FD_ACC = 17, ST_FD_INIT = 18
 };
 
 // Row ranges of one fold in the library's sorted row order (the Appendix B
@@ -113,8 +113,8 @@ struct IterState {
   long long n_draws;        // draws accumulated so far
   unsigned int ticket;      // last-block election in the accept kernel
   unsigned int error;       // device error flags
-  float eps;                // step size used by the kernels
-  float pad0;
+  float eps;                // nominal step size (adapted in the full-data warm-up)
+  float eps_iter;           // this iteration's step size (eps, jittered for fold chains)
   double da_mu, da_hbar, da_logeps, da_logeps_bar;
   long long da_t;
   double mass_n;            // Welford count of the mass window
@@ -180,6 +180,10 @@ constexpr double kLog2PiD = 1.8378770664093454835606594728112;
 constexpr double kLog2D = 0.69314718055994530942;
 
 // tensor-core path (k_grad_tc.cu)
+// workspace rows per tile segment beyond the PN gradient rows: per
+// warpgroup the training and test softplus sums, each as an FP32 hi + lo pair
+constexpr int kTcSlots = 8;
+
 struct TcArgs {
   int KP;                 // padded p in SMEM / global (64 or 128)
   int KS;                 // GEMM1 K steps of 16 (ceil(p / 16))
@@ -193,7 +197,9 @@ struct TcArgs {
   int need_lo;            // accumulate the theta lo part too (FP32-accurate eta)
   int accurate;           // FP32 epilogue with log densities (else the bf16x2 fast path)
   const __nv_bfloat16 *yc;// N_pad: y - 1/2 (zero for padded rows)
-  float *ws;              // T x max_seg x (PN + 4) x 128
+  const double *ylin;     // (K + 1) x 2 x p: sums over the training / test rows of
+                          // fold k of y_n x_n (bf16 X); k = K is the full data
+  float *ws;              // T x max_seg x (PN + kTcSlots) x 128
   unsigned int *tickets;  // T
   unsigned int *err;      // error flags (bit 0: wait time-out)
 };
@@ -217,7 +223,9 @@ struct BeginArgs {
   const double *logp;
   float *theta_p, *r;           // proposal position and momentum (out)
   double *H0;                   // out
-  const float *eps, *minv;
+  const float *eps, *minv;      // nominal step size, inverse mass
+  float jitter;                 // eps_iter = eps (1 + jitter (2u - 1)), u from stream ST_JIT
+  float *eps_iter;              // out (written by block 0): the step size of this iteration
   const float *r_given;         // optional start momenta instead of drawing (C x ld)
   __nv_bfloat16 *shadow_hi, *shadow_lo;
   int ld_shadow;
@@ -241,7 +249,8 @@ struct AcceptArgs {
 
 struct FdAdaptArgs {
   IterState *st;
-  int n_adapt, w0, w1;
+  int n_adapt, w0, w1, w2;     // mass windows [w0, w1) and [w1, w2)
+  float eps_cap;              // final step size cap (trajectory length / L_f); <= 0: none
   int adapt_eps, adapt_mass;
   int C, d, ld;
   const float *theta;
@@ -267,7 +276,8 @@ __global__ void k_accept(AcceptArgs a);
 __global__ void k_accumulate_given(Accum A, const double *s, int n, long long n0);
 __global__ void k_fd_adapt(FdAdaptArgs a);
 __global__ void k_fd_init_state(IterState *st, float eps0, int adapt);
-__global__ void k_fd_final_eps(IterState *st);
+__global__ void k_fd_final_eps(IterState *st, float eps_cap);
+__global__ void k_copy_eps(IterState *st);
 __global__ void k_finalize(Accum A, int K, int L, long long n, double *out, double *scratch);
 __global__ void k_totals(const double *fo, int K, double Ln, double *tot);
 

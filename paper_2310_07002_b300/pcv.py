@@ -53,7 +53,8 @@ class Options(ct.Structure):
                 ("max_batches", ct.c_int32), ("n_fulldata_draws", ct.c_int32),
                 ("init_scale", ct.c_double), ("use_graphs", ct.c_int32),
                 ("device_alloc", ALLOC_FN), ("device_free", FREE_FN),
-                ("alloc_user", ct.c_void_p)]
+                ("alloc_user", ct.c_void_p), ("trajectory_length", ct.c_double),
+                ("step_jitter", ct.c_double)]
 
 
 _lib = None
@@ -166,7 +167,8 @@ class PCV:
                  precision: int = FP32_SIMT, stream=None, store_draws: int = 0,
                  acov_max_lag: int = 64, max_batches: int = 1024,
                  n_fulldata_draws: int = 250, init_scale: float = 1.0,
-                 use_graphs: bool = True, torch_allocator: bool = True):
+                 use_graphs: bool = True, torch_allocator: bool = True,
+                 trajectory_length: float = -1.0, step_jitter: float = -1.0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("PCV needs a CUDA device (sm_103a); none is available")
@@ -200,6 +202,8 @@ class PCV:
         o.n_fulldata_draws = n_fulldata_draws
         o.init_scale = init_scale
         o.use_graphs = 1 if use_graphs else 0
+        o.trajectory_length = trajectory_length
+        o.step_jitter = step_jitter
         self._alloc = None
         if torch_allocator:
             self._alloc = _TorchAllocator(torch.cuda.current_device())

@@ -1,0 +1,112 @@
+"""Run a whole parallel cross-validation on one of the synthetic workloads and
+print one JSON line with the scores, the diagnostics and the wall clock of
+each phase.
+
+    python -m paper_2310_07002_b300.run_pcv --workload logistic_large \
+        [--precision bf16] [--draws N] [--fd-warmup N] [--fold-warmup N] \
+        [--compare fp32]
+
+The phases are those of the PCV workflow (Section 3): create (data to the
+device), warm-up (full-data adaptation, then the fold chains' discarded
+warm-up; Section 3.1), sampling with the online accumulators (Algorithm A2)
+and the estimators (Section 3.2, Section 4). `--compare` runs the same
+workload again at a second precision with another sampler seed and reports,
+per fold, z = (elpd_a - elpd_b) / sqrt(MCSE_a^2 + MCSE_b^2).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import workloads as W
+
+WORKLOADS = {
+    "gauss_blocks": lambda: W.gauss_blocks(),
+    "logistic_loo": lambda: W.logistic_loo(),
+    "hier_logo": lambda: W.hier_logo(),
+    "ar2_hvblock": lambda: W.ar2_hvblock(),
+    "logistic_large": lambda: W.logistic_large(),
+}
+
+
+def run(w, precision: str, draws: int, fd_warmup: int, fold_warmup: int, seed: int):
+    import torch
+    from . import pcv as P
+    t = {}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pc = P.PCV.from_workload(w, precision=P.PRECISIONS[precision], seed=seed)
+    torch.cuda.synchronize()
+    t["create_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    pc.warmup(fd_warmup, fold_warmup)
+    torch.cuda.synchronize()
+    t["warmup_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    pc.sample(draws)
+    torch.cuda.synchronize()
+    t["sample_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    sc = pc.scores()
+    dg = pc.diagnostics()
+    t["finalize_s"] = time.perf_counter() - t0
+    eps, _ = pc.adaptation()
+    acc = pc.accept_rate()
+    C = pc.C
+    pc.close()
+    t["total_s"] = sum(t.values())
+    evals = float(C) * w.leapfrog_steps * (fold_warmup + draws)
+    out = {
+        "precision": precision, "seed": seed, "chains": C,
+        "elpd": float(sc["elpd_total"]), "mcse": float(sc["mcse_total"]),
+        "se_epistemic": float(sc["se_epistemic"]),
+        "rhat_max": float(dg["rhat_max"]),
+        "split_rhat_max": float(np.max(dg["split_rhat"])),
+        "folds_rhat_ge_1.01": int(np.sum(dg["rhat"] >= 1.01)),
+        "ess_total": float(dg["ess_total"]),
+        "ess_bm_min": float(np.min(dg["ess_bm"])), "ess_acov_min": float(np.min(dg["ess_acov"])),
+        "divergences": int(np.sum(dg["divergences"])),
+        "accept_mean": float(np.mean(acc)), "step_size": float(eps),
+        "fold_grad_evals_per_s": evals / (t["warmup_s"] + t["sample_s"]),
+        "wall": t,
+    }
+    return out, sc, dg
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="logistic_large", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
+    ap.add_argument("--draws", type=int, default=None)
+    ap.add_argument("--fd-warmup", type=int, default=None)
+    ap.add_argument("--fold-warmup", type=int, default=None)
+    ap.add_argument("--compare", default=None, choices=["fp32", "bf16"])
+    ap.add_argument("--seed", type=int, default=None)
+    args = ap.parse_args()
+    from .build import build
+    build()
+    w = WORKLOADS[args.workload]()
+    draws = args.draws or w.n_draws
+    fdw = args.fd_warmup or w.n_fulldata_warmup
+    fow = args.fold_warmup or w.n_fold_warmup
+    seed = w.seed if args.seed is None else args.seed
+    a, sca, _ = run(w, args.precision, draws, fdw, fow, seed)
+    line = {"workload": w.name, "N": w.N, "p": w.p, "K": w.K, "L": w.chains_per_fold,
+            "leapfrog_steps": w.leapfrog_steps, "draws": draws, "fd_warmup": fdw,
+            "fold_warmup": fow, "batch_size": w.batch_size, "run": a}
+    if args.compare:
+        b, scb, _ = run(w, args.compare, draws, fdw, fow, seed + 1)
+        z = (sca["elpd"] - scb["elpd"]) / np.sqrt(sca["mcse"] ** 2 + scb["mcse"] ** 2)
+        zt = (a["elpd"] - b["elpd"]) / np.hypot(a["mcse"], b["mcse"])
+        line["compare"] = {"run": b, "z_total": float(zt), "z_abs_max": float(np.max(np.abs(z))),
+                           "z_abs_mean": float(np.mean(np.abs(z))),
+                           "folds_abs_z_gt_3": int(np.sum(np.abs(z) > 3)),
+                           "speedup_sampling": b["wall"]["sample_s"] / a["wall"]["sample_s"]}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

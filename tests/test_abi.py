@@ -56,6 +56,7 @@ def test_default_options_host_only(libpcv):
     L.pcv_default_options(ct.byref(o))
     assert o.leapfrog_steps == 16 and o.batch_size == 50 and o.step_size < 0
     assert o.acov_max_lag == 64 and o.use_graphs == 1 and o.max_batches == 1024
+    assert o.trajectory_length == -1.0 and o.step_jitter == -1.0     # defaults: auto
 
 
 def test_create_rejects_bad_arguments_before_any_cuda_call(libpcv):
@@ -75,8 +76,12 @@ def test_create_rejects_bad_arguments_before_any_cuda_call(libpcv):
     for N, p, Lc in [(10, 2, 1), (10, 0, 4), (0, 2, 4)]:
         assert L.pcv_create(ct.byref(m), X.ctypes.data, y.ctypes.data, f.ctypes.data, N, p, Lc,
                             ct.byref(o), ct.byref(h)) == E_INVALID_ARG
-    # bad option
+    # bad options
     o.batch_size = 0
+    assert L.pcv_create(ct.byref(m), X.ctypes.data, y.ctypes.data, f.ctypes.data, 10, 2, 4,
+                        ct.byref(o), ct.byref(h)) == E_INVALID_ARG
+    L.pcv_default_options(ct.byref(o))
+    o.step_jitter = 1.0                      # a step size of zero would be possible
     assert L.pcv_create(ct.byref(m), X.ctypes.data, y.ctypes.data, f.ctypes.data, 10, 2, 4,
                         ct.byref(o), ct.byref(h)) == E_INVALID_ARG
     assert not h.value

@@ -23,11 +23,17 @@ def closed_form(w, k):
     return mu, S, elpd
 
 
-def test_conjugate_fold_posteriors_and_elpd(orc):
+import pytest
+
+
+@pytest.mark.parametrize("eps, jitter", [(0.05, -1.0),   # the config: fixed step, no jitter
+                                         (0.05, 0.5),    # jittered step size
+                                         (-1.0, -1.0)])  # adapted: mass windows, cap, jitter
+def test_conjugate_fold_posteriors_and_elpd(orc, eps, jitter):
     w = W.gauss_blocks()
     prob = orc.problem_from_workload(w)
     L, b = w.chains_per_fold, w.batch_size
-    run = orc.OraclePCV(prob, L, w.seed, w.leapfrog_steps, eps=w.step_size, b=b)
+    run = orc.OraclePCV(prob, L, w.seed, w.leapfrog_steps, eps=eps, b=b, jitter=jitter)
     run.fulldata(200, 250)
     run.fold_warmup(w.n_fold_warmup)
     run.sample(w.n_draws)
