@@ -26,6 +26,9 @@ from . import workloads as W
 WORKLOADS = {
     "gauss_blocks": lambda: W.gauss_blocks(),
     "logistic_loo": lambda: W.logistic_loo(),
+    # X rounded to bf16 values: both precisions then see the same data, so a
+    # comparison measures arithmetic only
+    "logistic_loo_bf16x": lambda: W.logistic_loo(bf16=True),
     "hier_logo": lambda: W.hier_logo(),
     "ar2_hvblock": lambda: W.ar2_hvblock(),
     "logistic_large": lambda: W.logistic_large(),
@@ -84,6 +87,9 @@ def main():
     ap.add_argument("--fd-warmup", type=int, default=None)
     ap.add_argument("--fold-warmup", type=int, default=None)
     ap.add_argument("--compare", default=None, choices=["fp32", "bf16"])
+    ap.add_argument("--compare-draws", type=int, default=None,
+                    help="draws of the comparison run (default: the same)")
+    ap.add_argument("--compare-fold-warmup", type=int, default=None)
     ap.add_argument("--seed", type=int, default=None)
     args = ap.parse_args()
     from .build import build
@@ -93,18 +99,25 @@ def main():
     fdw = args.fd_warmup or w.n_fulldata_warmup
     fow = args.fold_warmup or w.n_fold_warmup
     seed = w.seed if args.seed is None else args.seed
-    a, sca, _ = run(w, args.precision, draws, fdw, fow, seed)
+    a, sca, dga = run(w, args.precision, draws, fdw, fow, seed)
     line = {"workload": w.name, "N": w.N, "p": w.p, "K": w.K, "L": w.chains_per_fold,
             "leapfrog_steps": w.leapfrog_steps, "draws": draws, "fd_warmup": fdw,
             "fold_warmup": fow, "batch_size": w.batch_size, "run": a}
     if args.compare:
-        b, scb, _ = run(w, args.compare, draws, fdw, fow, seed + 1)
+        b, scb, dgb = run(w, args.compare, args.compare_draws or draws, fdw,
+                          args.compare_fold_warmup or fow, seed + 1)
         z = (sca["elpd"] - scb["elpd"]) / np.sqrt(sca["mcse"] ** 2 + scb["mcse"] ** 2)
+
+        def infl(sc, dg):   # batch-means MCSE inflated where ESS_bm exceeds ESS_acov
+            return sc["mcse"] * np.sqrt(np.maximum(1.0, dg["ess_bm"] / dg["ess_acov"]))
+        zi = (sca["elpd"] - scb["elpd"]) / np.hypot(infl(sca, dga), infl(scb, dgb))
         zt = (a["elpd"] - b["elpd"]) / np.hypot(a["mcse"], b["mcse"])
         line["compare"] = {"run": b, "z_total": float(zt), "z_abs_max": float(np.max(np.abs(z))),
                            "z_abs_mean": float(np.mean(np.abs(z))),
                            "folds_abs_z_gt_3": int(np.sum(np.abs(z) > 3)),
-                           "speedup_sampling": b["wall"]["sample_s"] / a["wall"]["sample_s"]}
+                           "z_acov_abs_max": float(np.max(np.abs(zi))),
+                           "folds_abs_z_acov_gt_3": int(np.sum(np.abs(zi) > 3)),
+                           "speedup_grad_evals": a["fold_grad_evals_per_s"] / b["fold_grad_evals_per_s"]}
     print(json.dumps(line), flush=True)
 
 
