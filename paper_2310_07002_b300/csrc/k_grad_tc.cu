@@ -12,13 +12,18 @@
 // carries only Theta, X and y: with both operands of both GEMMs in SMEM the
 // MMAs alone saturate its bandwidth.
 //
-// Theta is stored scaled by 1/2 (exact in binary floating point), so S is
-// eta/2 and sigmoid(eta) = 1/2 + tanh(S)/2.  The same SMEM X tile is the
+// The tensor cores see theta centred on a reference theta_ref (the mean of
+// the full-data draws, or of the positions a caller sets) and scaled by 1/2:
+// the shadows hold (theta - theta_ref) / 2 in bf16 hi + lo parts, the
+// epilogue adds eta_ref / 2 = x . theta_ref / 2 (FP32, per row), so S is
+// eta / 2 and sigmoid(eta) = 1/2 + tanh(S)/2.  The same SMEM X tile is the
 // K-major B operand of the first GEMM and the MN-major B operand of the
-// second.  Theta is split into bf16 hi + lo parts and S accumulates both,
-// giving an FP32-accurate eta: with the hi part alone the gradient is a
-// piecewise-constant function of theta whose error (a few percent of a
-// posterior standard deviation) leaves HMC exact but slows its mixing.
+// second.  Launches that need log densities accumulate hi + lo (an
+// FP32-accurate eta for the Metropolis test); the kick-drift launches use
+// the hi part only once a reference is set.  Centred, the bf16 rounding of
+// theta - theta_ref is ~0.4 % of a posterior standard deviation (of theta
+// itself it was a few percent, enough to slow mixing); HMC stays exact
+// because the accept test uses the accurate log density.
 // Where log densities are needed (last leapfrog step, evaluations) the
 // epilogue also sums softplus(eta) over the fold's training and test rows;
 // the linear part y eta of the log likelihood is theta . sum(y x), from
@@ -47,6 +52,7 @@ namespace pcv {
 constexpr int kTN = 128;        // rows per chunk
 constexpr int kTM = 128;        // chains per tile
 constexpr int kTcThreads = 352; // 11 warps: TMA, GEMM1 MMA, 8 epilogue, GEMM2 MMA
+constexpr int kTcMaxStages = 8; // X pipeline stages (as many as fit in shared memory)
 
 
 // softplus(eta) for eta = 2 s (the first GEMM yields s = eta / 2):
@@ -243,7 +249,7 @@ __host__ __device__ inline int owner_cta(long long u, long long U, long long n) 
 // KS (GEMM1 K steps of 16, = ceil(p / 16)) is a template parameter so that
 // every MMA group is straight-line code: MMAs issued from a runtime-count
 // loop between commits measured up to 3x slower on sm_103a.
-template <int KS>
+template <int KS, bool ACC>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_grad_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_hi,
               const __grid_constant__ CUtensorMap tm_lo, Problem pb, GradArgs a, TcArgs ta) {
@@ -252,23 +258,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int KA = ta.KP / 64;                       // 128-byte K atoms
   const uint32_t th_bytes = (uint32_t)KA * kTM * 128;
   const uint32_t x_bytes = (uint32_t)KA * kTN * 128;
-  const uint32_t stage_bytes = (uint32_t)pb.p * 129 * 4;   // finish staging [p][129] floats
   const int NS = ta.NS;
   uint8_t *th_hi = sm;
   uint8_t *th_lo = th_hi + th_bytes;
   uint8_t *xs = th_lo + (ta.need_lo ? th_bytes : 0);
-  uint8_t *stg = xs + (size_t)NS * x_bytes;       // finish staging area
-  uint8_t *ys = stg + ((stage_bytes + 8 + kTM * 8 + 1023) & ~1023u);   // NS x kTN bf16
-  uint64_t *bars = reinterpret_cast<uint64_t *>(ys + NS * kTN * 2 + 64);
-  // barrier slots
-  uint64_t *x_full = bars, *x_empty = bars + 4, *s_full = bars + 8, *s_empty = bars + 10;
-  uint64_t *r_full = bars + 12, *r_empty = bars + 14, *th_full = bars + 16, *th_empty = bars + 17;
-  uint64_t *g_full = bars + 18, *g_empty = bars + 19;
-  uint32_t *tmem_base_slot = reinterpret_cast<uint32_t *>(bars + 20);
-  volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 21);
-  volatile int *last_flag = reinterpret_cast<volatile int *>(bars + 22);
-  uint64_t *flush_bar = bars + 23, *decide_bar = bars + 24;   // epilogue-internal sync
-  uint64_t *fin_bar = bars + 25;
+  uint8_t *ys = xs + (size_t)NS * x_bytes;        // NS x kTN bf16 (y - 1/2)
+  float *ehs = reinterpret_cast<float *>(ys + NS * kTN * 2);   // NS x kTN: eta_ref / 2
+  uint64_t *bars = reinterpret_cast<uint64_t *>(ys + NS * kTN * 6 + 64);
+  // barrier slots (up to kTcMaxStages X stages)
+  uint64_t *x_full = bars, *x_empty = bars + kTcMaxStages;
+  uint64_t *s_full = bars + 2 * kTcMaxStages, *s_empty = s_full + 2;
+  uint64_t *r_full = s_full + 4, *r_empty = s_full + 6, *th_full = s_full + 8, *th_empty = s_full + 9;
+  uint64_t *g_full = s_full + 10, *g_empty = s_full + 11;
+  uint32_t *tmem_base_slot = reinterpret_cast<uint32_t *>(s_full + 12);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(s_full + 13);
+  volatile int *last_flag = reinterpret_cast<volatile int *>(s_full + 14);
+  uint64_t *flush_bar = s_full + 15, *decide_bar = s_full + 16;   // epilogue-internal sync
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long U = (long long)ta.T * ta.J;
@@ -285,7 +290,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     mbar_init(smem_u32(th_full), 1); mbar_init(smem_u32(th_empty), 1);
     mbar_init(smem_u32(g_full), 1); mbar_init(smem_u32(g_empty), 4);
     mbar_init(smem_u32(flush_bar), 8); mbar_init(smem_u32(decide_bar), 1);
-    mbar_init(smem_u32(fin_bar), 8);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -306,7 +310,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // ------------------------------ TMA producer ---------------------------
     if (lane == 0) {
       int seg = 0, th_issued = -1;
-      int last_round[4] = {-1, -1, -1, -1};
+      int last_round[kTcMaxStages];
+#pragma unroll
+      for (int s2 = 0; s2 < kTcMaxStages; ++s2) last_round[s2] = -1;
       for (int i = 0; i < nunits; ++i) {
         const long long u = u0 + i;
         const int t = (int)(u / ta.J), j = (int)(u - (long long)t * ta.J);
@@ -323,11 +329,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         const int st = i % NS, rnd = i / NS;
         if (!mbar_wait_fast(smem_u32(&x_empty[st]), (rnd & 1) ^ 1, abort_flag, ta.err)) break;
-        mbar_expect_tx(smem_u32(&x_full[st]), x_bytes + kTN * 2);
+        mbar_expect_tx(smem_u32(&x_full[st]), x_bytes + kTN * 6);
         uint8_t *xb = xs + (size_t)st * x_bytes;
         for (int kb = 0; kb < KA; ++kb)
           tma_load_2d(smem_u32(xb + kb * kTN * 128), &tm_x, kb * 64, j * kTN, smem_u32(&x_full[st]));
         bulk_load(smem_u32(ys + st * kTN * 2), ta.yc + (size_t)j * kTN, kTN * 2, smem_u32(&x_full[st]));
+        bulk_load(smem_u32(ehs + st * kTN), ta.eta_half + (size_t)j * kTN, kTN * 4, smem_u32(&x_full[st]));
         last_round[st] = rnd;
       }
       // on abort: let copies already issued land before the CTA exits
@@ -416,10 +423,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int m = q * 32 + lane;                    // chain row within the tile
     const int et = ew * 32 + lane;                  // 0..255
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-    const bool accurate = ta.accurate != 0;
+    constexpr bool accurate = ACC;                  // log densities (a separate instantiation)
     const int wstride = ta.PN + kTcSlots;           // workspace rows per segment
     const int sb = eg, rb = eg;                     // this group's S and R buffers
-    int nseg_done = 0, nfin = 0;
+    int nseg_done = 0;
     bool aborted = false;
     // walk the CTA's segments (maximal runs of units in one tile)
     int t = (int)(u0 / ta.J), j0 = (int)(u0 - (long long)t * ta.J);
@@ -436,46 +443,40 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // the X stage of this unit is still resident (its release needs R);
         // waiting on its barrier makes the TMA-written y visible
         if (!warp_wait(smem_u32(&x_full[i % NS]), (i / NS) & 1, abort_flag, ta.err)) { aborted = true; break; }
-        if (!warp_wait(smem_u32(&r_empty[rb]), ((i >> 1) & 1) ^ 1, abort_flag, ta.err)) { aborted = true; break; }
         tc_fence_after();
         const uint32_t *ywu = reinterpret_cast<const uint32_t *>(ys + (i % NS) * kTN * 2);
-        for (int h = 0; h < 2; ++h) {               // two halves of 64 rows
-          // TMEM loads, then the wait right away: the destination registers
-          // are written asynchronously until tcgen05.wait::ld
-          uint32_t v[64];
-          PCV_TMEM_LD32(tmem + sb * 128 + 64 * h + lane_off, v);
-          PCV_TMEM_LD32(tmem + sb * 128 + 64 * h + 32 + lane_off, (v + 32));
-          tmem_wait_ld();
-          if (h == 1) {                             // S fully in registers: release it
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&s_empty[sb]));
-          }
+        const float4 *ehu = reinterpret_cast<const float4 *>(ehs + (i % NS) * kTN);
+        // residual of half h (64 rows) of the chunk from v = S into pk
+        // (32 bf16x2), plus the log-likelihood sums when ACC
+        auto half_residual = [&](const int h, const uint32_t (&v)[64], uint32_t (&pk)[32]) {
           const int n0 = j * kTN + 64 * h;
           const uint32_t *yw = ywu + 32 * h;
+          // S holds (eta - eta_ref) / 2: the row's eta_ref / 2 is added
+          // where S is used
+          const float2 *eh2 = reinterpret_cast<const float2 *>(ehu) + 32 * h;
           // residual y - sigmoid(eta) = (y - 1/2) - tanh(S)/2 in FP32, rounded
           // to bf16 for the second GEMM (the same function on every leapfrog
           // step). A bf16x2 tanh here would bias the gradient: its error is
           // a smooth function of eta, so it adds up over rows instead of
           // averaging out (a force error of ~6 % of the posterior scale per
           // dimension at N = 1e5, which shrinks the adapted step size).
-          uint32_t packed[32];
 #pragma unroll
           for (int k = 0; k < 32; ++k) {
             const uint32_t y2 = yw[k];
-            const float ta = tanh_f32(__uint_as_float(v[2 * k]));
-            const float tb = tanh_f32(__uint_as_float(v[2 * k + 1]));
-            packed[k] = bf16x2_from(fmaf(-0.5f, ta, __uint_as_float(y2 << 16)),
-                                    fmaf(-0.5f, tb, __uint_as_float(y2 & 0xFFFF0000u)));
+            const float2 e2 = eh2[k];
+            const float ta = tanh_f32(__uint_as_float(v[2 * k]) + e2.x);
+            const float tb = tanh_f32(__uint_as_float(v[2 * k + 1]) + e2.y);
+            pk[k] = bf16x2_from(fmaf(-0.5f, ta, __uint_as_float(y2 << 16)),
+                                fmaf(-0.5f, tb, __uint_as_float(y2 & 0xFFFF0000u)));
           }
           if (valid && n0 < fd.excl_hi && n0 + 64 > fd.excl_lo) {
 #pragma unroll
             for (int k = 0; k < 64; ++k) {
               const int n = n0 + k;
-              if (n >= fd.excl_lo && n < fd.excl_hi) packed[k >> 1] &= (k & 1) ? 0x0000FFFFu : 0xFFFF0000u;
+              if (n >= fd.excl_lo && n < fd.excl_hi) pk[k >> 1] &= (k & 1) ? 0x0000FFFFu : 0xFFFF0000u;
             }
           }
-          if (accurate) {
+          if constexpr (accurate) {
             // log likelihood y eta - softplus(eta): the linear part is
             // theta . sum(y x) per fold (added in the finish), so only
             // softplus(eta) = max(eta, 0) + log(1 + exp(-|eta|)) is summed
@@ -485,14 +486,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (n0 + 64 <= pb.N && (n0 + 64 <= fd.excl_lo || n0 >= fd.excl_hi)) {
               float acc4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-              for (int k = 0; k < 64; ++k) acc4[k & 3] += softplus_half(__uint_as_float(v[k]));
+              for (int k = 0; k < 64; ++k)
+                acc4[k & 3] += softplus_half(__uint_as_float(v[k]) + (k & 1 ? eh2[k >> 1].y : eh2[k >> 1].x));
               sp_tr += (double)((acc4[0] + acc4[1]) + (acc4[2] + acc4[3]));
             } else {
               float tr = 0.0f, te = 0.0f;
 #pragma unroll
               for (int k = 0; k < 64; ++k) {
                 const int n = n0 + k;
-                const float sp = softplus_half(__uint_as_float(v[k]));
+                const float sp = softplus_half(__uint_as_float(v[k]) + (k & 1 ? eh2[k >> 1].y : eh2[k >> 1].x));
                 if (n < pb.N && (n < fd.excl_lo || n >= fd.excl_hi)) tr += sp;
                 if (n >= fd.test_lo && n < fd.test_hi) te += sp;
               }
@@ -500,9 +502,30 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               sp_te += (double)te;
             }
           }
-          // R row m (TMEM lane m): chunk rows 64 h .. 64 h + 63 as 32 bf16x2 columns
-          PCV_TMEM_ST32(tmem_R + 64 * rb + 32 * h + lane_off, packed);
-        }
+        };
+        // S is read and released before the wait for the R buffer, so that
+        // the first GEMM of unit i + 2 is not held up by the second GEMM of
+        // unit i - 2.  TMEM loads are followed by their wait right away (the
+        // destination registers are written asynchronously until then), and
+        // each store by its wait before its source registers are reused.
+        uint32_t v[64], pk[32];
+        PCV_TMEM_LD32(tmem + sb * 128 + lane_off, v);
+        PCV_TMEM_LD32(tmem + sb * 128 + 32 + lane_off, (v + 32));
+        tmem_wait_ld();
+        half_residual(0, v, pk);
+        PCV_TMEM_LD32(tmem + sb * 128 + 64 + lane_off, v);
+        PCV_TMEM_LD32(tmem + sb * 128 + 96 + lane_off, (v + 32));
+        tmem_wait_ld();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&s_empty[sb]));   // S fully read: release it
+        if (!warp_wait(smem_u32(&r_empty[rb]), ((i >> 1) & 1) ^ 1, abort_flag, ta.err)) { aborted = true; break; }
+        tc_fence_after();
+        // R row m (TMEM lane m): chunk rows 64 h .. 64 h + 63 as 32 bf16x2 columns
+        PCV_TMEM_ST32(tmem_R + 64 * rb + lane_off, pk);
+        tmem_wait_st();
+        half_residual(1, v, pk);
+        PCV_TMEM_ST32(tmem_R + 64 * rb + 32 + lane_off, pk);
         tmem_wait_st();
         tc_fence_before();
         __syncwarp();
@@ -515,7 +538,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int fl = nseg_done++;
       const int b0 = owner_cta((long long)t * ta.J, U, ta.n_cta);
       const int sidx = blockIdx.x - b0;
+      // workspace rows are chain-major ([chain][PN + slots]) so that the
+      // finish reads them in the layout of theta / grad (coalesced)
       float *wsp = ta.ws + ((size_t)t * ta.max_seg + sidx) * (size_t)wstride * kTM;
+      float *wrow = wsp + (size_t)m * wstride;
       if (eg == owner) {
         if (!warp_wait(smem_u32(g_full), fl & 1, abort_flag, ta.err)) break;
         tc_fence_after();
@@ -524,7 +550,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           PCV_TMEM_LD16(tmem_G + cb + lane_off, gv);
           tmem_wait_ld();
 #pragma unroll
-          for (int k = 0; k < 16; ++k) wsp[(size_t)(cb + k) * kTM + m] = __uint_as_float(gv[k]);
+          for (int k = 0; k < 16; k += 4)
+            __stcg(reinterpret_cast<float4 *>(wrow + cb + k),
+                   make_float4(__uint_as_float(gv[k]), __uint_as_float(gv[k + 1]),
+                               __uint_as_float(gv[k + 2]), __uint_as_float(gv[k + 3])));
         }
         tc_fence_before();
         __syncwarp();
@@ -532,10 +561,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       {
         const float h0 = (float)sp_tr, h1 = (float)sp_te;
-        wsp[(size_t)(ta.PN + 4 * eg + 0) * kTM + m] = h0;
-        wsp[(size_t)(ta.PN + 4 * eg + 1) * kTM + m] = (float)(sp_tr - (double)h0);
-        wsp[(size_t)(ta.PN + 4 * eg + 2) * kTM + m] = h1;
-        wsp[(size_t)(ta.PN + 4 * eg + 3) * kTM + m] = (float)(sp_te - (double)h1);
+        __stcg(reinterpret_cast<float4 *>(wrow + ta.PN + 4 * eg),
+               make_float4(h0, (float)(sp_tr - (double)h0), h1, (float)(sp_te - (double)h1)));
       }
       __threadfence();
       __syncwarp();
@@ -551,24 +578,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       if (!warp_wait(smem_u32(decide_bar), fl & 1, abort_flag, ta.err)) break;
       if (*last_flag) {
-        // ---- last segment of tile t: sum the segments, priors, leapfrog
-        // update; the summed gradient is staged [p][129] in shared memory so
-        // that the per-chain writes are coalesced.
+        // ---- last segment of tile t: sum the segments in order, priors,
+        // leapfrog update.  No shared memory is involved, so the epilogue
+        // warps need no barrier inside the finish.
         __threadfence();
-        float *stage = reinterpret_cast<float *>(stg);
         const float *base = ta.ws + (size_t)t * ta.max_seg * (size_t)wstride * kTM;
         const size_t seg_stride = (size_t)wstride * kTM;
-        {
-          const int mm = et & 127;
-          for (int jj = et >> 7; jj < pb.p; jj += 2) {
-            float gs = 0.0f;
-            for (int s2 = 0; s2 < nseg; ++s2) gs += __ldcg(base + s2 * seg_stride + (size_t)jj * kTM + mm);
-            stage[jj * 129 + mm] = gs;
-          }
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(fin_bar));
-        if (!warp_wait(smem_u32(fin_bar), (3 * nfin) & 1, abort_flag, ta.err)) break;
         const float eps = a.mode != MODE_NONE ? *a.eps : 0.0f;
         const float kick = a.mode == MODE_LAST_KICK ? 0.5f * eps : eps;
         // (chain, dimension) items spread over all 256 epilogue threads so
@@ -581,7 +596,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           if (cc >= a.C) break;
           float *th = const_cast<float *>(a.theta) + (size_t)cc * a.ld_theta;
           const float tv = th[jj];
-          const float g = stage[jj * 129 + mm] - tv * pb.beta_prec;
+          float gs = 0.0f;
+          for (int s2 = 0; s2 < nseg; ++s2) gs += __ldcg(base + s2 * seg_stride + (size_t)mm * wstride + jj);
+          const float g = gs - tv * pb.beta_prec;
           a.grad[(size_t)cc * a.ld_grad + jj] = g;
           if (a.mode != MODE_NONE) {
             float *rr = a.r + (size_t)cc * a.ld_theta;
@@ -590,25 +607,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (a.mode == MODE_KICK_DRIFT) {
               const float tn = tv + eps * a.minv[jj] * rj;
               th[jj] = tn;
-              const float half = 0.5f * tn;            // shadows hold theta / 2
+              const float half = 0.5f * (tn - ta.theta_ref[jj]);   // shadows hold (theta - ref) / 2
               const __nv_bfloat16 hi = __float2bfloat16_rn(half);
               a.shadow_hi[(size_t)cc * a.ld_shadow + jj] = hi;
               a.shadow_lo[(size_t)cc * a.ld_shadow + jj] = __float2bfloat16_rn(half - __bfloat162float(hi));
             }
           }
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(fin_bar));
-        if (!warp_wait(smem_u32(fin_bar), (3 * nfin + 1) & 1, abort_flag, ta.err)) break;
         if (a.need_ll && et < kTM && t * kTM + et < a.C) {
           const int cc = t * kTM + et;
           double s0 = 0.0, s1 = 0.0;                // softplus sums over train / test rows
           for (int s2 = 0; s2 < nseg; ++s2) {
-            const float *ws2 = base + s2 * seg_stride + (size_t)ta.PN * kTM + et;
+            const float *ws2 = base + s2 * seg_stride + (size_t)et * wstride + ta.PN;
 #pragma unroll
             for (int g2 = 0; g2 < 2; ++g2) {
-              s0 += (double)__ldcg(ws2 + (4 * g2 + 0) * kTM) + (double)__ldcg(ws2 + (4 * g2 + 1) * kTM);
-              s1 += (double)__ldcg(ws2 + (4 * g2 + 2) * kTM) + (double)__ldcg(ws2 + (4 * g2 + 3) * kTM);
+              s0 += (double)__ldcg(ws2 + 4 * g2 + 0) + (double)__ldcg(ws2 + 4 * g2 + 1);
+              s1 += (double)__ldcg(ws2 + 4 * g2 + 2) + (double)__ldcg(ws2 + 4 * g2 + 3);
             }
           }
           // linear part theta . sum(y x) and the log prior, in a fixed order
@@ -627,11 +641,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           a.logp[cc] = (lin_tr - s0) + lprior;
           a.shat[cc] = lin_te - s1;
         }
-        // the staging area is reused only after every warp has finished
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(fin_bar));
-        if (!warp_wait(smem_u32(fin_bar), (3 * nfin + 2) & 1, abort_flag, ta.err)) break;
-        ++nfin;
       }
       // next segment starts at chunk 0 of the next tile
       ib = ie;
@@ -652,12 +661,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // host side
 // ---------------------------------------------------------------------------
 size_t tc_smem_bytes(int KP, int NS, int need_lo, int p) {
+  (void)p;
   const size_t KA = KP / 64;
-  const size_t stage = ((size_t)p * 129 * 4 + 8 + kTM * 8 + 1023) & ~(size_t)1023;
-  size_t b = KA * kTM * 128 * (need_lo ? 2 : 1) + (size_t)NS * KA * kTN * 128 + stage +
-             (size_t)NS * kTN * 2 + 64 + 32 * 8;   // 26 barrier / flag slots used
+  size_t b = KA * kTM * 128 * (need_lo ? 2 : 1) + (size_t)NS * KA * kTN * 128 +
+             (size_t)NS * kTN * 6 + 64 + (2 * kTcMaxStages + 17) * 8;   // y, eta_ref/2; barrier / flag slots
   return b + 1024;   // alignment slack
 }
+
+int tc_max_stages() { return kTcMaxStages; }
 
 int tc_segments_per_tile(int T, int J, int n_cta) {
   const long long U = (long long)T * J;
@@ -672,7 +683,9 @@ int tc_segments_per_tile(int T, int J, int n_cta) {
 
 template <int KS>
 static cudaError_t set_smem_attr() {
-  return cudaFuncSetAttribute(k_grad_tc<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_grad_tc<KS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaError_t e2 = cudaFuncSetAttribute(k_grad_tc<KS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  return e != cudaSuccess ? e : e2;
 }
 
 // once per context (outside any stream capture): allow the large dynamic SMEM
@@ -690,8 +703,11 @@ cudaError_t launch_grad_tc(const CUtensorMap &tm_x, const CUtensorMap &tm_hi, co
   const size_t smem = tc_smem_bytes(ta.KP, ta.NS, ta.need_lo, pb.p);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   switch (ta.KS) {
-#define PCV_TC_CASE(K) \
-  case K: k_grad_tc<K><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta); break;
+#define PCV_TC_CASE(K)                                                                          \
+  case K:                                                                                       \
+    if (ta.accurate) k_grad_tc<K, true><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta); \
+    else k_grad_tc<K, false><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta);            \
+    break;
     PCV_TC_CASE(1) PCV_TC_CASE(2) PCV_TC_CASE(3) PCV_TC_CASE(4)
     PCV_TC_CASE(5) PCV_TC_CASE(6) PCV_TC_CASE(7) PCV_TC_CASE(8)
 #undef PCV_TC_CASE

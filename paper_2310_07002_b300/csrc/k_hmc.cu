@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(256) k_begin(BeginArgs a) {
       a.r[(size_t)c * a.ld + j] = rh;
       a.theta_p[(size_t)c * a.ld + j] = tn;
       if (a.shadow_hi) {                     // bf16 hi + lo of theta / 2 (tensor-core operand)
-        const float half = 0.5f * tn;
+        const float half = 0.5f * (tn - a.theta_ref[j]);
         const __nv_bfloat16 hi = __float2bfloat16_rn(half);
         a.shadow_hi[(size_t)c * a.ld_shadow + j] = hi;
         a.shadow_lo[(size_t)c * a.ld_shadow + j] = __float2bfloat16_rn(half - __bfloat162float(hi));
@@ -96,12 +96,12 @@ __global__ void k_init_from_pool(int C, int d, int ld, unsigned long long seed, 
   theta[(size_t)c * ld + j] = pool[(size_t)idx * ld + j];
 }
 
-__global__ void k_shadow(int C, int d, int ld, const float *theta, __nv_bfloat16 *hi,
-                         __nv_bfloat16 *lo, int ld_shadow) {
+__global__ void k_shadow(int C, int d, int ld, const float *theta, const float *theta_ref,
+                         __nv_bfloat16 *hi, __nv_bfloat16 *lo, int ld_shadow) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)C * d) return;
   const int c = (int)(t / d), j = (int)(t - (long long)c * d);
-  const float v = 0.5f * theta[(size_t)c * ld + j];     // shadows hold theta / 2
+  const float v = 0.5f * (theta[(size_t)c * ld + j] - theta_ref[j]);   // shadows hold (theta - ref) / 2
   const __nv_bfloat16 h = __float2bfloat16_rn(v);
   hi[(size_t)c * ld_shadow + j] = h;
   lo[(size_t)c * ld_shadow + j] = __float2bfloat16_rn(v - __bfloat162float(h));
@@ -542,4 +542,26 @@ __global__ void k_totals(const double *fo, int K, double Ln, double *tot) {
   }
 }
 
+}  // namespace pcv
+
+namespace pcv {
+// centring reference for the tensor-core path: theta_ref = mean of n rows
+// of src (ld floats apart), then eta_half[n] = x16_n . theta_ref / 2 for
+// every row (bf16 X as the tensor cores see it, FP64 sums, 0 on padding)
+__global__ void k_theta_ref(int n, int d, int ld, const float *src, float *theta_ref) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d; j += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += (double)src[(size_t)i * ld + j];
+    theta_ref[j] = (float)(s / n);
+  }
+}
+__global__ void k_eta_ref(int N, int N_pad, int p, int KP, const __nv_bfloat16 *X16, const float *theta_ref,
+                          float *eta_half) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N_pad) return;
+  double s = 0.0;
+  if (n < N)
+    for (int j = 0; j < p; ++j) s += (double)__bfloat162float(X16[(size_t)n * KP + j]) * (double)theta_ref[j];
+  eta_half[n] = (float)(0.5 * s);
+}
 }  // namespace pcv

@@ -22,6 +22,7 @@
 
 namespace pcv {
 size_t tc_smem_bytes(int KP, int NS, int need_lo, int p);
+int tc_max_stages();
 int tc_segments_per_tile(int T, int J, int n_cta);
 cudaError_t tc_prepare();
 cudaError_t launch_grad_tc(const CUtensorMap &tm_x, const CUtensorMap &tm_hi, const CUtensorMap &tm_lo,
@@ -94,6 +95,9 @@ struct pcv_ctx {
   CUtensorMap tm_x{};
   float *ws_tc = nullptr;
   double *ylin = nullptr;         // tensor-core path: per-fold sums of y x (see TcArgs)
+  float *theta_ref = nullptr;     // tensor-core path: centring reference (d_pad)
+  float *eta_half = nullptr;      // tensor-core path: x . theta_ref / 2 per row (N_pad)
+  bool centered = false;          // a reference has been set
   size_t ws_tc_floats = 0;
   unsigned int *tickets_tc = nullptr;
   size_t n_tickets_tc = 0;
@@ -219,19 +223,24 @@ pcv_status alloc_shadows(pcv_ctx *x, ChainBufs &cb, int C) {
   return PCV_OK;
 }
 
-TcArgs tc_args(pcv_ctx *x, int C, bool need_lo) {
+TcArgs tc_args(pcv_ctx *x, int C, bool need_ll) {
   TcArgs t{};
   t.KP = x->KP; t.KS = x->KS; t.PN = x->PN; t.N_pad = x->N_pad; t.J = x->J;
   t.T = (C + 127) / 128;
   const long long U = (long long)t.T * t.J;
   t.n_cta = (int)std::min<long long>(x->n_sm, U);
   t.max_seg = tc_segments_per_tile(t.T, t.J, t.n_cta);
-  // theta hi + lo on every step (see k_grad_tc.cu); FP32 epilogue when
-  // log densities are needed
-  t.need_lo = 1;
-  t.accurate = need_lo ? 1 : 0;
-  t.NS = tc_smem_bytes(t.KP, 4, 1, x->p) <= 227 * 1024 ? 4 : (tc_smem_bytes(t.KP, 3, 1, x->p) <= 227 * 1024 ? 3 : 2);
+  // theta hi + lo where log densities are needed or no centring reference
+  // is set yet; the kick-drift launches of centred chains use hi only
+  t.need_lo = (need_ll || !x->centered) ? 1 : 0;
+  t.accurate = need_ll ? 1 : 0;
+  // the deepest X pipeline that fits in shared memory
+  t.NS = 2;
+  for (int ns = tc_max_stages(); ns > 2; --ns)
+    if (tc_smem_bytes(t.KP, ns, 1, x->p) <= 227 * 1024) { t.NS = ns; break; }
   t.yc = x->yc16;
+  t.eta_half = x->eta_half;
+  t.theta_ref = x->theta_ref;
   t.ws = x->ws_tc;
   t.ylin = x->ylin;
   t.tickets = x->tickets_tc;
@@ -305,9 +314,21 @@ pcv_status launch_grad(pcv_ctx *x, GradArgs a, const ChainBufs *cb = nullptr) {
 pcv_status write_shadow(pcv_ctx *x, ChainBufs &cb, const float *theta, int ld) {
   if (!x->tc) return PCV_OK;
   const long long T = (long long)cb.C * x->d;
-  k_shadow<<<(unsigned)((T + 255) / 256), 256, 0, x->stream>>>(cb.C, x->d, ld, theta, cb.shadow_hi, cb.shadow_lo,
-                                                              x->KP);
+  k_shadow<<<(unsigned)((T + 255) / 256), 256, 0, x->stream>>>(cb.C, x->d, ld, theta, x->theta_ref, cb.shadow_hi,
+                                                              cb.shadow_lo, x->KP);
   CK(cudaGetLastError());
+  return PCV_OK;
+}
+
+// tensor-core path: centre on the mean of n parameter vectors (ld apart)
+pcv_status set_reference(pcv_ctx *x, const float *src, int n, int ld) {
+  if (!x->tc) return PCV_OK;
+  k_theta_ref<<<(x->d + 127) / 128, 128, 0, x->stream>>>(n, x->d, ld, src, x->theta_ref);
+  CK(cudaGetLastError());
+  k_eta_ref<<<(x->N_pad + 255) / 256, 256, 0, x->stream>>>((int)x->N, x->N_pad, x->p, x->KP, x->X16, x->theta_ref,
+                                                          x->eta_half);
+  CK(cudaGetLastError());
+  x->centered = true;
   return PCV_OK;
 }
 
@@ -335,6 +356,7 @@ pcv_status launch_iteration(pcv_ctx *x, ChainBufs &cb, bool fd, bool accumulate)
   ba.shadow_hi = x->tc ? cb.shadow_hi : nullptr;
   ba.shadow_lo = x->tc ? cb.shadow_lo : nullptr;
   ba.ld_shadow = x->KP;
+  ba.theta_ref = x->theta_ref;
   k_begin<<<(cb.C + 7) / 8, 256, 0, x->stream>>>(ba);
   CK(cudaGetLastError());
   GradArgs ga = grad_args(x, cb, true);
@@ -700,7 +722,8 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
       for (int j = 0; j < p; ++j) tr[j] = all[j] - ex[j];
     }
     if (!dalloc_n(x, &x->X16, hX16.size()) || !dalloc_n(x, &x->yc16, hyc.size()) ||
-        !dalloc_n(x, &x->ylin, hyl.size()))
+        !dalloc_n(x, &x->ylin, hyl.size()) || !dalloc_n(x, &x->theta_ref, (size_t)x->d_pad) ||
+        !dalloc_n(x, &x->eta_half, (size_t)x->N_pad))
       return bail(PCV_E_OOM, "device allocation failed");
     cudaMemcpyAsync(x->ylin, hyl.data(), hyl.size() * sizeof(double), cudaMemcpyHostToDevice, x->stream);
     cudaMemcpyAsync(x->X16, hX16.data(), hX16.size() * 2, cudaMemcpyHostToDevice, x->stream);
@@ -802,6 +825,9 @@ pcv_status pcv_warmup(pcv_ctx *x, int32_t n_fd, int32_t n_wu) {
     CK(cudaGetLastError());
   }
   s = run_iterations(x, x->fd_cb, true, false, x->n_fd_draws, &x->g_fd_1, 1);
+  if (s != PCV_OK) return s;
+  // tensor-core path: centre on the mean of the full-data draws
+  s = set_reference(x, x->pool, x->n_fd_draws * kNumFdChains, x->d_pad);
   if (s != PCV_OK) return s;
   // fold chains start from full-data draws (Algorithm 1)
   {
@@ -916,6 +942,11 @@ pcv_status pcv_set_positions(pcv_ctx *x, const double *theta, double step_size, 
       h[(size_t)c * x->d_pad + j] = (float)v;
     }
   CK(cudaMemcpyAsync(x->fold_cb.theta, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, x->stream));
+  {
+    // tensor-core path: centre on the mean of the given positions
+    pcv_status sr = set_reference(x, x->fold_cb.theta, x->C, x->d_pad);
+    if (sr != PCV_OK) return sr;
+  }
   if (step_size > 0) {
     const float e[2] = {(float)step_size, (float)step_size};   // eps, eps_iter
     static_assert(offsetof(IterState, eps_iter) == offsetof(IterState, eps) + sizeof(float), "layout");
@@ -1034,6 +1065,7 @@ pcv_status pcv_trajectory(pcv_ctx *x, const float *theta0, const float *r0, int3
   ba.shadow_hi = x->tc ? cb.shadow_hi : nullptr;
   ba.shadow_lo = x->tc ? cb.shadow_lo : nullptr;
   ba.ld_shadow = x->KP;
+  ba.theta_ref = x->theta_ref;
   k_begin<<<(cb.C + 7) / 8, 256, 0, x->stream>>>(ba);
   CK(cudaGetLastError());
   GradArgs ga = grad_args(x, cb, true);

@@ -197,6 +197,8 @@ struct TcArgs {
   int need_lo;            // accumulate the theta lo part too (FP32-accurate eta)
   int accurate;           // FP32 epilogue with log densities (else the bf16x2 fast path)
   const __nv_bfloat16 *yc;// N_pad: y - 1/2 (zero for padded rows)
+  const float *eta_half;  // N_pad: eta_ref / 2 = x_n . theta_ref / 2 (0 for padded rows)
+  const float *theta_ref; // d: the shadows hold (theta - theta_ref) / 2
   const double *ylin;     // (K + 1) x 2 x p: sums over the training / test rows of
                           // fold k of y_n x_n (bf16 X); k = K is the full data
   float *ws;              // T x max_seg x (PN + kTcSlots) x 128
@@ -229,6 +231,7 @@ struct BeginArgs {
   const float *r_given;         // optional start momenta instead of drawing (C x ld)
   __nv_bfloat16 *shadow_hi, *shadow_lo;
   int ld_shadow;
+  const float *theta_ref;       // shadows hold (theta_p - theta_ref) / 2
 };
 
 struct AcceptArgs {
@@ -270,8 +273,11 @@ __global__ void k_normals(int C, int d, int ld, unsigned long long seed, unsigne
                           unsigned int stream, float scale, float *out);
 __global__ void k_init_from_pool(int C, int d, int ld, unsigned long long seed, const float *pool,
                                  int n_pool, float *theta);
-__global__ void k_shadow(int C, int d, int ld, const float *theta, __nv_bfloat16 *hi,
-                         __nv_bfloat16 *lo, int ld_shadow);
+__global__ void k_shadow(int C, int d, int ld, const float *theta, const float *theta_ref,
+                         __nv_bfloat16 *hi, __nv_bfloat16 *lo, int ld_shadow);
+__global__ void k_theta_ref(int n, int d, int ld, const float *src, float *theta_ref);
+__global__ void k_eta_ref(int N, int N_pad, int p, int KP, const __nv_bfloat16 *X16, const float *theta_ref,
+                          float *eta_half);
 __global__ void k_accept(AcceptArgs a);
 __global__ void k_accumulate_given(Accum A, const double *s, int n, long long n0);
 __global__ void k_fd_adapt(FdAdaptArgs a);
