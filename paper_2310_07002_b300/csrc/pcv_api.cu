@@ -234,10 +234,11 @@ TcArgs tc_args(pcv_ctx *x, int C, bool need_ll) {
   // is set yet; the kick-drift launches of centred chains use hi only
   t.need_lo = (need_ll || !x->centered) ? 1 : 0;
   t.accurate = need_ll ? 1 : 0;
-  // the deepest X pipeline that fits in shared memory
+  // the deepest X pipeline that fits in shared memory (without the theta
+  // lo buffer, hi-only launches have room for one or two more stages)
   t.NS = 2;
   for (int ns = tc_max_stages(); ns > 2; --ns)
-    if (tc_smem_bytes(t.KP, ns, 1, x->p) <= 227 * 1024) { t.NS = ns; break; }
+    if (tc_smem_bytes(t.KP, ns, t.need_lo, x->p) <= 227 * 1024) { t.NS = ns; break; }
   t.yc = x->yc16;
   t.eta_half = x->eta_half;
   t.theta_ref = x->theta_ref;
