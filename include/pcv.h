@@ -126,6 +126,13 @@ typedef struct {
      * < 1. */
     double trajectory_length;
     double step_jitter;
+    /* 1 (default): before the first iterations of a chain set, time the
+     * gradient launch under a few launch configurations (split-N count of
+     * the FP32 kernels, X pipeline depth of the tensor-core kernel) and keep
+     * the fastest for that chain count. The split count changes the order of
+     * the FP32 partial sums, so results are bit-reproducible only with the
+     * same choice; 0 keeps the fixed rule. */
+    int32_t autotune;
 } pcv_options;
 
 /* Fill *opt with the defaults listed above (seed 0, L_f 16, adapted step). */
@@ -263,6 +270,13 @@ pcv_status pcv_get_draws(pcv_ctx *ctx, double *shat, int32_t *n_stored);
 
 /* Mean acceptance rate per fold over sampling (host, K). */
 pcv_status pcv_accept_rate(pcv_ctx *ctx, double *accept_k);
+
+/* The launch configurations the autotuner chose (pcv_options.autotune), one
+ * line per chain set: the candidates with their measured time per launch
+ * and the choice. Writes a NUL-terminated string of at most len bytes
+ * (truncated if longer) into buf, a host buffer the caller owns. No
+ * counterpart in the paper. */
+pcv_status pcv_tuning_info(const pcv_ctx *ctx, char *buf, int32_t len);
 
 /* Device time in milliseconds of the most recent pcv_sample call (CUDA events
  * on the context stream). */

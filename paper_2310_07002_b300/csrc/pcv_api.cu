@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <numeric>
 #include <string>
@@ -98,6 +99,12 @@ struct pcv_ctx {
   float *theta_ref = nullptr;     // tensor-core path: centring reference (d_pad)
   float *eta_half = nullptr;      // tensor-core path: x . theta_ref / 2 per row (N_pad)
   bool centered = false;          // a reference has been set
+  // autotuned launch configurations: split-N count of the FP32 gradient
+  // kernels per chain count; X stages of the tensor-core kernel per
+  // (chain count, theta lo used)
+  std::map<int, int> tuned_splits;
+  std::map<std::pair<int, int>, int> tuned_ns;
+  std::vector<std::string> tune_log;
   size_t ws_tc_floats = 0;
   unsigned int *tickets_tc = nullptr;
   size_t n_tickets_tc = 0;
@@ -155,14 +162,21 @@ void free_all(pcv_ctx *x) {
   x->allocs.clear();
 }
 
-int splits_for(const pcv_ctx *x, int C) {
+int splits_cap(const pcv_ctx *x) {
+  return x->variant == MV_HIER ? std::max(1, x->G / 4) : std::max(1, (int)(x->N / 256));
+}
+
+// fixed rule: enough CTAs to fill 4 per SM, at most the cap
+int splits_rule(const pcv_ctx *x, int C) {
   const int tw = x->tc ? 32 : simt_chain_tile(x->p);
   const int tiles = (C + tw - 1) / tw;
-  int s = (kTargetCtas + tiles - 1) / tiles;
-  int cap;
-  if (x->variant == MV_HIER) cap = std::max(1, x->G / 4);
-  else cap = std::max(1, (int)(x->N / 256));
-  return std::max(1, std::min(s, cap));
+  const int s = (kTargetCtas + tiles - 1) / tiles;
+  return std::max(1, std::min(s, splits_cap(x)));
+}
+
+int splits_for(const pcv_ctx *x, int C) {
+  auto it = x->tuned_splits.find(C);
+  return it != x->tuned_splits.end() ? it->second : splits_rule(x, C);
 }
 
 pcv_status ensure_ws(pcv_ctx *x, int C, int splits) {
@@ -223,6 +237,12 @@ pcv_status alloc_shadows(pcv_ctx *x, ChainBufs &cb, int C) {
   return PCV_OK;
 }
 
+int tc_max_fit_stages(const pcv_ctx *x, int need_lo) {
+  for (int ns = tc_max_stages(); ns > 2; --ns)
+    if (tc_smem_bytes(x->KP, ns, need_lo, x->p) <= 227 * 1024) return ns;
+  return 2;
+}
+
 TcArgs tc_args(pcv_ctx *x, int C, bool need_ll) {
   TcArgs t{};
   t.KP = x->KP; t.KS = x->KS; t.PN = x->PN; t.N_pad = x->N_pad; t.J = x->J;
@@ -235,10 +255,11 @@ TcArgs tc_args(pcv_ctx *x, int C, bool need_ll) {
   t.need_lo = (need_ll || !x->centered) ? 1 : 0;
   t.accurate = need_ll ? 1 : 0;
   // the deepest X pipeline that fits in shared memory (without the theta
-  // lo buffer, hi-only launches have room for one or two more stages)
-  t.NS = 2;
-  for (int ns = tc_max_stages(); ns > 2; --ns)
-    if (tc_smem_bytes(t.KP, ns, t.need_lo, x->p) <= 227 * 1024) { t.NS = ns; break; }
+  // lo buffer, hi-only launches have room for one or two more stages),
+  // unless the autotuner chose another depth for this chain count
+  t.NS = tc_max_fit_stages(x, t.need_lo);
+  auto it = x->tuned_ns.find(std::make_pair(C, t.need_lo));
+  if (it != x->tuned_ns.end()) t.NS = it->second;
   t.yc = x->yc16;
   t.eta_half = x->eta_half;
   t.theta_ref = x->theta_ref;
@@ -308,6 +329,60 @@ pcv_status launch_grad(pcv_ctx *x, GradArgs a, const ChainBufs *cb = nullptr) {
   a.ws = x->ws;
   a.tickets = x->tickets;
   CK(launch_grad_simt(x->pb, a, x->stream));
+  return PCV_OK;
+}
+
+// Autotuner: time the gradient launch of a chain set (no leapfrog update;
+// the proposal buffers are scratch between iterations) under a few launch
+// configurations and keep the fastest for this chain count.
+pcv_status tune(pcv_ctx *x, ChainBufs &cb) {
+  if (!x->opt.autotune || cb.C < 1) return PCV_OK;
+  const int C = cb.C;
+  const int need_lo = x->centered ? 0 : 1;
+  if (x->tc ? x->tuned_ns.count(std::make_pair(C, need_lo)) > 0 : x->tuned_splits.count(C) > 0) return PCV_OK;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  auto time_launch = [&](float *ms) -> pcv_status {
+    GradArgs a = grad_args(x, cb, true);
+    a.mode = MODE_NONE;
+    a.need_ll = 0;
+    pcv_status s = launch_grad(x, a, &cb);                       // warm-up
+    if (s != PCV_OK) return s;
+    CK(cudaEventRecord(e0, x->stream));
+    for (int r = 0; r < 3 && s == PCV_OK; ++r) s = launch_grad(x, a, &cb);
+    if (s != PCV_OK) return s;
+    CK(cudaEventRecord(e1, x->stream));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(ms, e0, e1));
+    return PCV_OK;
+  };
+  std::vector<int> cand;
+  if (x->tc) {
+    for (int ns = 2; ns <= tc_max_fit_stages(x, need_lo); ++ns) cand.push_back(ns);
+  } else {
+    const int s0 = splits_rule(x, C), cap = splits_cap(x);
+    for (int v : {s0 / 4, s0 / 2, s0, 2 * s0})
+      if (v >= 1 && v <= cap && std::find(cand.begin(), cand.end(), v) == cand.end()) cand.push_back(v);
+  }
+  int best = cand.back();
+  float best_ms = 1e30f;
+  std::string log = std::string(x->tc ? "tensor-core X stages" : "FP32 split-N count") + " for " +
+                    std::to_string(C) + " chains:";
+  for (int v : cand) {
+    if (x->tc) x->tuned_ns[std::make_pair(C, need_lo)] = v;
+    else x->tuned_splits[C] = v;
+    float ms = 0.0f;
+    pcv_status s = time_launch(&ms);
+    if (s != PCV_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
+    log += " " + std::to_string(v) + "=" + std::to_string(ms / 3.0f) + "ms";
+    if (ms < best_ms) { best_ms = ms; best = v; }
+  }
+  if (x->tc) x->tuned_ns[std::make_pair(C, need_lo)] = best;
+  else x->tuned_splits[C] = best;
+  x->tune_log.push_back(log + " -> " + std::to_string(best));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   return PCV_OK;
 }
 
@@ -535,6 +610,7 @@ void pcv_default_options(pcv_options *o) {
   o->use_graphs = 1;
   o->trajectory_length = -1.0;
   o->step_jitter = -1.0;
+  o->autotune = 1;
 }
 
 pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
@@ -819,6 +895,7 @@ pcv_status pcv_warmup(pcv_ctx *x, int32_t n_fd, int32_t n_wu) {
   }
   pcv_status s = refresh(x, x->fd_cb);
   if (s != PCV_OK) return s;
+  if ((s = tune(x, x->fd_cb)) != PCV_OK) return s;
   s = run_iterations(x, x->fd_cb, true, false, n_fd, &x->g_fd_1, 1);
   if (s != PCV_OK) return s;
   if (adapt && n_fd > 0) {
@@ -839,6 +916,7 @@ pcv_status pcv_warmup(pcv_ctx *x, int32_t n_fd, int32_t n_wu) {
   }
   s = refresh(x, x->fold_cb);
   if (s != PCV_OK) return s;
+  if ((s = tune(x, x->fold_cb)) != PCV_OK) return s;
   s = run_iterations(x, x->fold_cb, false, false, n_wu, &x->g_fold_1, 1);
   if (s != PCV_OK) return s;
   CK(cudaStreamSynchronize(x->stream));
@@ -860,8 +938,10 @@ pcv_status pcv_sample(pcv_ctx *x, int32_t n_draws) {
   if ((x->n_sampled + n_draws) / x->b > x->max_batches)
     return fail(x, PCV_E_INVALID_ARG, "more batches than max_batches");
   enter(x);
+  pcv_status s = tune(x, x->fold_cb);               // outside the timed region
+  if (s != PCV_OK) return s;
   CK(cudaEventRecord(x->ev0, x->stream));
-  pcv_status s = run_iterations(x, x->fold_cb, false, true, n_draws, &x->g_sample_b, x->b);
+  s = run_iterations(x, x->fold_cb, false, true, n_draws, &x->g_sample_b, x->b);
   if (s != PCV_OK) return s;
   CK(cudaEventRecord(x->ev1, x->stream));
   CK(cudaEventSynchronize(x->ev1));
@@ -1146,6 +1226,10 @@ pcv_status pcv_time_leapfrog_kernel(pcv_ctx *x, int32_t reps, double *ms_per_lau
   if (x->state == ST_CREATED) return fail(x, PCV_E_BAD_STATE, "positions not set");
   enter(x);
   ChainBufs &cb = x->fold_cb;
+  {
+    pcv_status st = tune(x, cb);
+    if (st != PCV_OK) return st;
+  }
   const size_t n = sizeof(float) * (size_t)cb.C * x->d_pad;
   CK(cudaMemcpyAsync(cb.theta_p, cb.theta, n, cudaMemcpyDeviceToDevice, x->stream));
   CK(cudaMemsetAsync(cb.r, 0, n, x->stream));
@@ -1167,6 +1251,14 @@ pcv_status pcv_time_leapfrog_kernel(pcv_ctx *x, int32_t reps, double *ms_per_lau
   CK(cudaEventElapsedTime(&ms, x->ev0, x->ev1));
   *ms_per_launch = ms / reps;
   leave(x);
+  return PCV_OK;
+}
+
+pcv_status pcv_tuning_info(const pcv_ctx *x, char *buf, int32_t len) {
+  if (!x || !buf || len < 1) return PCV_E_INVALID_ARG;
+  std::string s;
+  for (const std::string &l : x->tune_log) s += l + "\n";
+  std::snprintf(buf, (size_t)len, "%s", s.c_str());
   return PCV_OK;
 }
 

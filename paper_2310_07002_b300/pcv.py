@@ -54,7 +54,7 @@ class Options(ct.Structure):
                 ("init_scale", ct.c_double), ("use_graphs", ct.c_int32),
                 ("device_alloc", ALLOC_FN), ("device_free", FREE_FN),
                 ("alloc_user", ct.c_void_p), ("trajectory_length", ct.c_double),
-                ("step_jitter", ct.c_double)]
+                ("step_jitter", ct.c_double), ("autotune", ct.c_int32)]
 
 
 _lib = None
@@ -87,6 +87,7 @@ def load():
         "pcv_num_chains": (i32, [vp]),
         "pcv_dim": (i32, [vp]),
         "pcv_last_error": (ct.c_char_p, [vp]),
+        "pcv_tuning_info": (i32, [vp, ct.c_char_p, i32]),
         "pcv_destroy": (None, [vp]),
         "pcv_set_positions": (i32, [vp, vp, f64, vp]),
         "pcv_get_positions": (i32, [vp, vp, vp, vp]),
@@ -116,7 +117,7 @@ def exported_symbols():
             "pcv_destroy", "pcv_set_positions", "pcv_get_positions", "pcv_get_adaptation",
             "pcv_log_density", "pcv_trajectory", "pcv_draw_normals", "pcv_accumulate",
             "pcv_get_draws", "pcv_accept_rate", "pcv_last_sample_ms",
-            "pcv_time_leapfrog_kernel", "pcv_log_density_noalloc"]
+            "pcv_time_leapfrog_kernel", "pcv_log_density_noalloc", "pcv_tuning_info"]
 
 
 def _ptr(a: Optional[np.ndarray]):
@@ -168,7 +169,8 @@ class PCV:
                  acov_max_lag: int = 64, max_batches: int = 1024,
                  n_fulldata_draws: int = 250, init_scale: float = 1.0,
                  use_graphs: bool = True, torch_allocator: bool = True,
-                 trajectory_length: float = -1.0, step_jitter: float = -1.0):
+                 trajectory_length: float = -1.0, step_jitter: float = -1.0,
+                 autotune: bool = True):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("PCV needs a CUDA device (sm_103a); none is available")
@@ -204,6 +206,7 @@ class PCV:
         o.use_graphs = 1 if use_graphs else 0
         o.trajectory_length = trajectory_length
         o.step_jitter = step_jitter
+        o.autotune = 1 if autotune else 0
         self._alloc = None
         if torch_allocator:
             self._alloc = _TorchAllocator(torch.cuda.current_device())
@@ -305,6 +308,11 @@ class PCV:
         self._check(self._L.pcv_get_positions(self.h, _ptr(th), _ptr(lp), _ptr(sh)),
                     "pcv_get_positions")
         return th, lp, sh
+
+    def tuning_info(self) -> str:
+        buf = ct.create_string_buffer(4096)
+        self._check(self._L.pcv_tuning_info(self.h, buf, len(buf)), "pcv_tuning_info")
+        return buf.value.decode()
 
     def adaptation(self):
         e = ct.c_double()

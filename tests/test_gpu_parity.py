@@ -303,7 +303,10 @@ def test_graph_replay_equals_plain_launches(torch, precision):
     w = W.logistic_loo(N=517, p=20, K=30, L=4)
     out = []
     for graphs in (True, False):
-        pc = make_pcv(w, precision=PRECISIONS[precision], use_graphs=graphs, batch_size=10)
+        # a fixed launch configuration: the autotuner's choice of split count
+        # could differ between the two contexts and change rounding
+        pc = make_pcv(w, precision=PRECISIONS[precision], use_graphs=graphs, batch_size=10,
+                      autotune=False)
         pc.warmup(40, 20)
         pc.sample(60)
         th, lp, sh = pc.positions()
@@ -313,3 +316,24 @@ def test_graph_replay_equals_plain_launches(torch, precision):
         pc.close()
     for a, b in zip(*out):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_autotuner_records_its_choice_and_results_hold(torch, orc, precision):
+    from paper_2310_07002_b300.pcv import PRECISIONS
+    w = W.logistic_loo(N=517, p=20, K=30, L=4)
+    pc = make_pcv(w, precision=PRECISIONS[precision], batch_size=10)
+    pc.warmup(40, 20)
+    info = pc.tuning_info()
+    assert "->" in info and "chains" in info, info
+    # the tuned launch still computes the oracle's gradient
+    prob = orc.problem_from_workload(w)
+    th = W.random_theta(w.dim, pc.C, scale=0.3, seed=3)
+    tt = torch.tensor(th, dtype=torch.float32, device="cuda")
+    fo = torch.tensor(np.arange(pc.C) // w.chains_per_fold, dtype=torch.int32, device="cuda")
+    lp, g, _ = pc.log_density(tt, fo, precision=PRECISIONS[precision])
+    th32 = tt.cpu().double().numpy()
+    ref = np.stack([orc.log_density(prob, int(k), th32[i])[1] for i, k in enumerate(fo.cpu().numpy())])
+    tol = 1e-5 if precision == "fp32" else 1e-2
+    assert rel_vec(g.cpu().double().numpy(), ref).max() <= tol
+    pc.close()
