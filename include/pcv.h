@@ -271,6 +271,25 @@ pcv_status pcv_get_draws(pcv_ctx *ctx, double *shat, int32_t *n_stored);
 /* Mean acceptance rate per fold over sampling (host, K). */
 pcv_status pcv_accept_rate(pcv_ctx *ctx, double *accept_k);
 
+/*
+ * Checkpoint / resume (progressive reporting, Section 1: a run can be
+ * stopped, reported and continued). A checkpoint holds everything the next
+ * iterations read: iteration counters and adaptation state, step size and
+ * inverse mass, fold-chain positions, gradients and log densities, the
+ * centring reference (tensor-core path), every online accumulator, stored
+ * draws, and the autotuner's choices, behind a header that identifies the
+ * problem and the options. Loading it into a context created with the same
+ * model, data and options (and no warm-up) continues the run bit for bit.
+ *   pcv_checkpoint_size: *bytes = the buffer size the save needs.
+ *   pcv_checkpoint_save: host buffer buf (caller-owned, >= that size);
+ *     PCV_E_BAD_STATE before warm-up or pcv_set_positions.
+ *   pcv_checkpoint_load: PCV_E_INVALID_ARG if the buffer is not a
+ *     checkpoint, is truncated, or belongs to another problem or options.
+ */
+pcv_status pcv_checkpoint_size(pcv_ctx *ctx, int64_t *bytes);
+pcv_status pcv_checkpoint_save(pcv_ctx *ctx, void *buf, int64_t bytes);
+pcv_status pcv_checkpoint_load(pcv_ctx *ctx, const void *buf, int64_t bytes);
+
 /* The launch configurations the autotuner chose (pcv_options.autotune), one
  * line per chain set: the candidates with their measured time per launch
  * and the choice. Writes a NUL-terminated string of at most len bytes

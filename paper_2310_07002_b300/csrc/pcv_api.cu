@@ -1254,6 +1254,142 @@ pcv_status pcv_time_leapfrog_kernel(pcv_ctx *x, int32_t reps, double *ms_per_lau
   return PCV_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Checkpoint / resume: the O(C) state that the next iterations read, in a
+// fixed order behind a header that identifies the problem and the options.
+// ---------------------------------------------------------------------------
+namespace {
+struct CkptHeader {
+  char magic[8];
+  int32_t version;
+  int32_t precision, variant, p, d, d_pad, K, L, C, M, max_batches, b, draw_cap, Lf, N_pad;
+  int64_t N;
+  uint64_t seed;
+  int64_t n_sampled;
+  int32_t state, centered;
+  int32_t tuned_splits, tuned_ns0, tuned_ns1;
+  float jitter;
+  double traj_len;
+  int64_t payload;
+};
+constexpr char kCkptMagic[8] = {'P', 'C', 'V', 'C', 'K', 'P', 'T', '1'};
+
+struct Seg { void *dev; size_t bytes; };
+
+std::vector<Seg> ckpt_segments(pcv_ctx *x) {
+  const size_t C = (size_t)x->C;
+  std::vector<Seg> v;
+  Accum &A = x->acc;
+  v.push_back({x->st, sizeof(IterState)});
+  v.push_back({x->minv, sizeof(float) * x->d_pad});
+  v.push_back({x->fold_cb.theta, sizeof(float) * C * x->d_pad});
+  v.push_back({x->fold_cb.grad, sizeof(float) * C * x->d_pad});
+  v.push_back({x->fold_cb.logp, sizeof(double) * C});
+  v.push_back({x->fold_cb.shat, sizeof(double) * C});
+  if (x->tc) {
+    v.push_back({x->theta_ref, sizeof(float) * x->d_pad});
+    v.push_back({x->eta_half, sizeof(float) * x->N_pad});
+  }
+  for (double *p : {A.Ux, A.Ux2, A.Zx, A.em, A.emean, A.eM2, A.vm, A.vmean, A.vM2, A.wmean, A.wM2,
+                    A.bmean_cur, A.bM2_cur, A.c0, A.xsum})
+    v.push_back({p, sizeof(double) * C});
+  v.push_back({A.bmean, sizeof(double) * C * x->max_batches});
+  v.push_back({A.bM2, sizeof(double) * C * x->max_batches});
+  v.push_back({A.lagsum, sizeof(double) * C * (x->M + 1)});
+  v.push_back({A.first, sizeof(double) * C * std::max(1, x->M)});
+  v.push_back({A.ring, sizeof(double) * C * std::max(1, x->M)});
+  v.push_back({A.div, sizeof(long long) * C});
+  v.push_back({A.acc, sizeof(long long) * C});
+  if (A.draw_cap > 0) v.push_back({A.draws, sizeof(double) * C * A.draw_cap});
+  return v;
+}
+
+CkptHeader ckpt_header(pcv_ctx *x) {
+  CkptHeader h{};
+  std::memcpy(h.magic, kCkptMagic, 8);
+  h.version = 1;
+  h.precision = x->opt.precision; h.variant = x->variant; h.p = x->p; h.d = x->d; h.d_pad = x->d_pad;
+  h.K = x->K; h.L = x->L; h.C = x->C; h.M = x->M; h.max_batches = x->max_batches; h.b = x->b;
+  h.draw_cap = x->acc.draw_cap; h.Lf = x->Lf; h.N_pad = x->N_pad; h.N = x->N; h.seed = x->opt.seed;
+  h.jitter = x->jitter; h.traj_len = x->traj_len;
+  size_t payload = 0;
+  for (const Seg &g : ckpt_segments(x)) payload += g.bytes;
+  h.payload = (int64_t)payload;
+  return h;
+}
+}  // namespace
+
+pcv_status pcv_checkpoint_size(pcv_ctx *x, int64_t *bytes) {
+  if (!x) return PCV_E_INVALID_ARG;
+  if (!bytes) return fail(x, PCV_E_INVALID_ARG, "null argument");
+  *bytes = (int64_t)sizeof(CkptHeader) + ckpt_header(x).payload;
+  return PCV_OK;
+}
+
+pcv_status pcv_checkpoint_save(pcv_ctx *x, void *buf, int64_t bytes) {
+  if (!x) return PCV_E_INVALID_ARG;
+  if (!buf) return fail(x, PCV_E_INVALID_ARG, "null buffer");
+  if (x->state == ST_CREATED) return fail(x, PCV_E_BAD_STATE, "nothing to checkpoint before warm-up");
+  CkptHeader h = ckpt_header(x);
+  if (bytes < (int64_t)sizeof(h) + h.payload) return fail(x, PCV_E_INVALID_ARG, "checkpoint buffer too small");
+  h.n_sampled = x->n_sampled;
+  h.state = x->state;
+  h.centered = x->centered ? 1 : 0;
+  auto ts = x->tuned_splits.find(x->C);
+  h.tuned_splits = ts != x->tuned_splits.end() ? ts->second : -1;
+  auto n0 = x->tuned_ns.find(std::make_pair(x->C, 0)), n1 = x->tuned_ns.find(std::make_pair(x->C, 1));
+  h.tuned_ns0 = n0 != x->tuned_ns.end() ? n0->second : -1;
+  h.tuned_ns1 = n1 != x->tuned_ns.end() ? n1->second : -1;
+  enter(x);
+  uint8_t *out = static_cast<uint8_t *>(buf);
+  std::memcpy(out, &h, sizeof(h));
+  size_t off = sizeof(h);
+  for (const Seg &g : ckpt_segments(x)) {
+    CK(cudaMemcpyAsync(out + off, g.dev, g.bytes, cudaMemcpyDeviceToHost, x->stream));
+    off += g.bytes;
+  }
+  CK(cudaStreamSynchronize(x->stream));
+  leave(x);
+  return PCV_OK;
+}
+
+pcv_status pcv_checkpoint_load(pcv_ctx *x, const void *buf, int64_t bytes) {
+  if (!x) return PCV_E_INVALID_ARG;
+  if (!buf || bytes < (int64_t)sizeof(CkptHeader)) return fail(x, PCV_E_INVALID_ARG, "no checkpoint");
+  CkptHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  const CkptHeader mine = ckpt_header(x);
+  if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1)
+    return fail(x, PCV_E_INVALID_ARG, "not a PCV checkpoint");
+  if (h.precision != mine.precision || h.variant != mine.variant || h.p != mine.p || h.d != mine.d ||
+      h.K != mine.K || h.L != mine.L || h.C != mine.C || h.M != mine.M || h.max_batches != mine.max_batches ||
+      h.b != mine.b || h.draw_cap != mine.draw_cap || h.Lf != mine.Lf || h.N != mine.N || h.seed != mine.seed ||
+      h.jitter != mine.jitter || h.traj_len != mine.traj_len || h.payload != mine.payload)
+    return fail(x, PCV_E_INVALID_ARG, "the checkpoint belongs to another problem or other options");
+  if (bytes < (int64_t)sizeof(h) + h.payload) return fail(x, PCV_E_INVALID_ARG, "truncated checkpoint");
+  if (h.state != ST_WARMED && h.state != ST_SAMPLED) return fail(x, PCV_E_INVALID_ARG, "bad checkpoint state");
+  enter(x);
+  const uint8_t *in = static_cast<const uint8_t *>(buf);
+  size_t off = sizeof(h);
+  for (const Seg &g : ckpt_segments(x)) {
+    CK(cudaMemcpyAsync(g.dev, in + off, g.bytes, cudaMemcpyHostToDevice, x->stream));
+    off += g.bytes;
+  }
+  x->n_sampled = h.n_sampled;
+  x->state = h.state;
+  x->finalized = false;
+  x->centered = h.centered != 0;
+  if (h.tuned_splits > 0) x->tuned_splits[x->C] = h.tuned_splits;
+  if (h.tuned_ns0 > 0) x->tuned_ns[std::make_pair(x->C, 0)] = h.tuned_ns0;
+  if (h.tuned_ns1 > 0) x->tuned_ns[std::make_pair(x->C, 1)] = h.tuned_ns1;
+  // the bf16 shadows follow from the restored positions and reference
+  pcv_status s = write_shadow(x, x->fold_cb, x->fold_cb.theta, x->d_pad);
+  if (s != PCV_OK) return s;
+  CK(cudaStreamSynchronize(x->stream));
+  leave(x);
+  return PCV_OK;
+}
+
 pcv_status pcv_tuning_info(const pcv_ctx *x, char *buf, int32_t len) {
   if (!x || !buf || len < 1) return PCV_E_INVALID_ARG;
   std::string s;

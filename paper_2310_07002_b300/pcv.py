@@ -88,6 +88,9 @@ def load():
         "pcv_dim": (i32, [vp]),
         "pcv_last_error": (ct.c_char_p, [vp]),
         "pcv_tuning_info": (i32, [vp, ct.c_char_p, i32]),
+        "pcv_checkpoint_size": (i32, [vp, ct.POINTER(i64)]),
+        "pcv_checkpoint_save": (i32, [vp, vp, i64]),
+        "pcv_checkpoint_load": (i32, [vp, vp, i64]),
         "pcv_destroy": (None, [vp]),
         "pcv_set_positions": (i32, [vp, vp, f64, vp]),
         "pcv_get_positions": (i32, [vp, vp, vp, vp]),
@@ -117,7 +120,8 @@ def exported_symbols():
             "pcv_destroy", "pcv_set_positions", "pcv_get_positions", "pcv_get_adaptation",
             "pcv_log_density", "pcv_trajectory", "pcv_draw_normals", "pcv_accumulate",
             "pcv_get_draws", "pcv_accept_rate", "pcv_last_sample_ms",
-            "pcv_time_leapfrog_kernel", "pcv_log_density_noalloc", "pcv_tuning_info"]
+            "pcv_time_leapfrog_kernel", "pcv_log_density_noalloc", "pcv_tuning_info",
+            "pcv_checkpoint_size", "pcv_checkpoint_save", "pcv_checkpoint_load"]
 
 
 def _ptr(a: Optional[np.ndarray]):
@@ -308,6 +312,19 @@ class PCV:
         self._check(self._L.pcv_get_positions(self.h, _ptr(th), _ptr(lp), _ptr(sh)),
                     "pcv_get_positions")
         return th, lp, sh
+
+    def checkpoint(self) -> bytes:
+        """The run's state as bytes (see pcv_checkpoint_save)."""
+        n = ct.c_int64()
+        self._check(self._L.pcv_checkpoint_size(self.h, ct.byref(n)), "pcv_checkpoint_size")
+        buf = ct.create_string_buffer(n.value)
+        self._check(self._L.pcv_checkpoint_save(self.h, buf, n.value), "pcv_checkpoint_save")
+        return buf.raw
+
+    def restore(self, blob: bytes):
+        """Continue a run from checkpoint() bytes (same model, data and options)."""
+        buf = ct.create_string_buffer(blob, len(blob))
+        self._check(self._L.pcv_checkpoint_load(self.h, buf, len(blob)), "pcv_checkpoint_load")
 
     def tuning_info(self) -> str:
         buf = ct.create_string_buffer(4096)
