@@ -18,12 +18,16 @@ Parity status of each function (pins live in ``tests/test_oracle_*.py``):
 * online accumulators and estimators -- pinned against two-pass batch
   formulas (eq. bmean / bmvar / rhat) on stored draws, against the AR(1)
   closed-form ESS, and against the conjugate closed-form fold posteriors.
+* R-hat_max shuffle benchmark -- pinned by the identity picks (the fold's
+  R-hat from stored draws), by brute-force enumeration of every pick pattern
+  on a tiny case, by the uniformity of the picks, and by the paper's
+  pathological chains (a shifted chain lies outside the benchmark).
 * full-data warm-up (dual averaging, mass estimate) -- parity unpinned
   beyond the conjugate-model checks: it is an adaptive heuristic with no
   closed form; its outputs are only checked statistically.
 """
 from .oracle import (  # noqa: F401
     build, lib, Problem, problem_from_workload, philox, normals, uniform,
-    index, log_density, trajectory, accumulate_series, OraclePCV,
+    index, log_density, trajectory, accumulate_series, shuffle_series, rhat_from_picks, OraclePCV,
     FOLD_FIELDS, TOTAL_FIELDS,
 )

@@ -77,6 +77,14 @@ def _declare(L):
                                  ct.c_int32, ct.c_int32, ct.c_double]
     L.orc_pcv_create.restype = ct.c_void_p
     L.orc_pcv_destroy.argtypes = [ct.c_void_p]
+    _I = ct.POINTER(ct.c_int32)
+    L.orc_shuffle_series.argtypes = [ct.c_int32, ct.c_int32, ct.c_int32, _D, ct.c_int32, ct.c_int32,
+                                     ct.c_int32, ct.c_int32, ct.c_uint64, _D, _D]
+    L.orc_shuffle_series.restype = ct.c_int
+    L.orc_rhat_from_picks_series.argtypes = [ct.c_int32, ct.c_int32, _D, ct.c_int32, ct.c_int32, _I, _D]
+    L.orc_rhat_from_picks_series.restype = ct.c_int
+    L.orc_pcv_rhat_shuffle.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _D]
+    L.orc_pcv_rhat_shuffle.restype = ct.c_int
     L.orc_pcv_set_tuning.argtypes = [ct.c_void_p, ct.c_double, ct.c_double]
     L.orc_pcv_set_tuning.restype = ct.c_int
     L.orc_pcv_fulldata.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_double]
@@ -194,6 +202,32 @@ def accumulate_series(s: np.ndarray, L: int, b: int, M: int = 64,
             {f: to[i] for i, f in enumerate(TOTAL_FIELDS)})
 
 
+def shuffle_series(s: np.ndarray, L: int, b: int, D: int, R: int, seed: int,
+                   max_batches: int = 4096):
+    """R-hat_max benchmark (Section 4.2) on a given draw sequence s[C, n]:
+    returns (R-hat_max of each replicate [R], per-fold values [R, K])."""
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    C, n = s.shape
+    out = np.empty(R)
+    allv = np.empty((R, C // L))
+    rc = lib().orc_shuffle_series(C, L, n, _dp(s), b, max_batches, D, R, seed, _dp(out), _dp(allv))
+    assert rc == 0
+    return out, allv
+
+
+def rhat_from_picks(s: np.ndarray, b: int, D: int, picks) -> float:
+    """R-hat of L chains rebuilt from blocks: block d of slot l comes from
+    chain picks[l][d] (s[L, n])."""
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    L, n = s.shape
+    pk = np.ascontiguousarray(np.asarray(picks, dtype=np.int32).reshape(L * D))
+    out = np.empty(1)
+    rc = lib().orc_rhat_from_picks_series(L, n, _dp(s), b, D,
+                                          pk.ctypes.data_as(ct.POINTER(ct.c_int32)), _dp(out))
+    assert rc == 0
+    return float(out[0])
+
+
 class OraclePCV:
     """A whole PCV run in the oracle: warm-up reuse, sampling, estimators."""
 
@@ -240,6 +274,11 @@ class OraclePCV:
         assert lib().orc_pcv_results(self.h, _dp(fo), _dp(to)) == 0
         return ({f: fo[:, i] for i, f in enumerate(FOLD_FIELDS)},
                 {f: to[i] for i, f in enumerate(TOTAL_FIELDS)})
+
+    def rhat_shuffle(self, D: int, R: int):
+        out = np.empty(R)
+        assert lib().orc_pcv_rhat_shuffle(self.h, D, R, _dp(out)) == 0
+        return out
 
     def draws(self, n: int):
         out = np.empty((self.C, n))

@@ -756,6 +756,98 @@ int orc_accumulate_series(int32_t C, int32_t L, int32_t n, const double *s, int3
 }
 
 /* ------------------------------------------------------------------------ */
+/* R-hat_max benchmark by block shuffling (Section 4.2; the shuffle loop of  */
+/* Algorithm A2)                                                              */
+/* ------------------------------------------------------------------------ */
+/*
+ * Each chain's draws are cut into D contiguous blocks of whole batches
+ * (block d holds batches [d a / D, (d+1) a / D)).  A replicate rebuilds, for
+ * every chain slot l of a fold, a sequence whose block d is block d of chain
+ * picks[l * D + d]; its R-hat (eq. rhat) is computed from the Welford states
+ * of those blocks.  With picks[l * D + d] = l the result is the fold's R-hat.
+ */
+double orc_rhat_from_picks_accum(const orc_accum *Ac, int32_t L, int32_t D, const int32_t *picks)
+{
+    const int64_t a = Ac[0].a;
+    double *cnt = (double *)calloc(3 * (size_t)L, sizeof(double));
+    double *mean = cnt + L, *M2 = cnt + 2 * L;
+    for (int32_t l = 0; l < L; ++l) {
+        for (int32_t d = 0; d < D; ++d) {
+            const orc_accum *src = &Ac[picks[l * D + d]];
+            int64_t h0 = (int64_t)d * a / D, h1 = (int64_t)(d + 1) * a / D;
+            for (int64_t h = h0; h < h1; ++h)
+                welford_merge(&cnt[l], &mean[l], &M2[l], (double)(src->n / a), src->bmean[h], src->bM2[h]);
+        }
+    }
+    double r = rhat_from(L, cnt, mean, M2);
+    free(cnt);
+    return r;
+}
+
+/* The chain picks of replicate r for fold k: pick t = l D + d uses word t % 4
+ * of Philox (block t / 4, chain k, iteration r, stream 4) and l' = floor(w L
+ * / 2^32), a chain drawn uniformly with replacement. */
+#define ST_SHUF 4u
+static void shuffle_picks(uint64_t seed, int32_t k, int32_t r, int32_t L, int32_t D, int32_t *picks)
+{
+    for (int32_t t = 0; t < L * D; ++t) {
+        uint32_t w[4];
+        philox_at(seed, (uint32_t)(t / 4), (uint32_t)k, (uint32_t)r, ST_SHUF, w);
+        picks[t] = (int32_t)(((uint64_t)w[t % 4] * (uint64_t)L) >> 32);
+    }
+}
+
+/* R replicates of R-hat_max: out_max[r] = max over folds of the replicate's
+ * R-hat; out_all[r * K + k] (optional) the per-fold values. */
+static int rhat_shuffle_accums(const orc_accum *A, int32_t K, int32_t L, int32_t D, int32_t R, uint64_t seed,
+                               double *out_max, double *out_all)
+{
+    if (D < 1 || R < 1 || A[0].a < D || A[0].a > A[0].max_batches) return -1;
+    int32_t *picks = (int32_t *)malloc(sizeof(int32_t) * (size_t)L * D);
+    for (int32_t r = 0; r < R; ++r) {
+        double mx = -INFINITY;
+        for (int32_t k = 0; k < K; ++k) {
+            shuffle_picks(seed, k, r, L, D, picks);
+            double v = orc_rhat_from_picks_accum(A + (size_t)k * L, L, D, picks);
+            if (out_all) out_all[(size_t)r * K + k] = v;
+            if (v > mx) mx = v;
+        }
+        out_max[r] = mx;
+    }
+    free(picks);
+    return 0;
+}
+
+/* Drivers on a given series s[C x n] of held-out log predictive draws. */
+int orc_shuffle_series(int32_t C, int32_t L, int32_t n, const double *s, int32_t b, int32_t max_batches,
+                       int32_t D, int32_t R, uint64_t seed, double *out_max, double *out_all)
+{
+    if (C % L != 0 || n < 2 || b < 1) return -1;
+    orc_accum *A = (orc_accum *)calloc((size_t)C, sizeof(orc_accum));
+    for (int32_t c = 0; c < C; ++c) {
+        accum_init(&A[c], 0, max_batches);
+        for (int32_t t = 0; t < n; ++t) accum_push(&A[c], s[(size_t)c * n + t], b);
+    }
+    int rc = rhat_shuffle_accums(A, C / L, L, D, R, seed, out_max, out_all);
+    for (int32_t c = 0; c < C; ++c) accum_free(&A[c]);
+    free(A);
+    return rc;
+}
+int orc_rhat_from_picks_series(int32_t L, int32_t n, const double *s, int32_t b, int32_t D, const int32_t *picks,
+                               double *out)
+{
+    orc_accum *A = (orc_accum *)calloc((size_t)L, sizeof(orc_accum));
+    for (int32_t c = 0; c < L; ++c) {
+        accum_init(&A[c], 0, n / b + 1);
+        for (int32_t t = 0; t < n; ++t) accum_push(&A[c], s[(size_t)c * n + t], b);
+    }
+    *out = orc_rhat_from_picks_accum(A, L, D, picks);
+    for (int32_t c = 0; c < L; ++c) accum_free(&A[c]);
+    free(A);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* The PCV run: warm-up reuse (Section 3.1) and sampling (Algorithm A2)      */
 /* ------------------------------------------------------------------------ */
 typedef struct {
@@ -1065,6 +1157,11 @@ int orc_pcv_results(orc_pcv *S, double *fold_out, double *tot)
     totals(fold_out, S->P.K, (double)S->L * S->n_sampled, tot);
     free(rho);
     return 0;
+}
+
+int orc_pcv_rhat_shuffle(orc_pcv *S, int32_t D, int32_t R, double *out_max)
+{
+    return rhat_shuffle_accums(S->acc, S->P.K, S->L, D, R, S->seed, out_max, NULL);
 }
 
 int orc_pcv_get_draws(orc_pcv *S, double *out)
