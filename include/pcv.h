@@ -272,6 +272,23 @@ pcv_status pcv_get_draws(pcv_ctx *ctx, double *shat, int32_t *n_stored);
 pcv_status pcv_accept_rate(pcv_ctx *ctx, double *accept_k);
 
 /*
+ * R-hat_max benchmark (Section 4.2; the block-shuffle loop of Algorithm A2):
+ * each chain's draws so far are cut into n_blocks contiguous blocks of whole
+ * batches (block d holds batches [d a / D, (d+1) a / D), a batches); each of
+ * n_reps replicates rebuilds every chain of every fold from blocks of that
+ * fold's chains drawn uniformly with replacement (Philox stream 4; pick
+ * t = l D + d of replicate r in fold k is word t % 4 of counter
+ * (t / 4, k, r, 4), chain floor(w L / 2^32)) and takes the R-hat (eq. rhat)
+ * of the rebuilt chains. rhat_max_rep (host, n_reps) receives the maximum
+ * over folds of each replicate: the histogram against which R-hat_max is
+ * read; rhat_fold_rep (host, n_reps x K, or NULL) the per-fold values.
+ * Needs pcv_sample first (PCV_E_BAD_STATE) and n_blocks <= batches <=
+ * max_batches (PCV_E_INVALID_ARG).
+ */
+pcv_status pcv_rhat_shuffle(pcv_ctx *ctx, int32_t n_blocks, int32_t n_reps, double *rhat_max_rep,
+                            double *rhat_fold_rep);
+
+/*
  * Checkpoint / resume (progressive reporting, Section 1: a run can be
  * stopped, reported and continued). A checkpoint holds everything the next
  * iterations read: iteration counters and adaptation state, step size and

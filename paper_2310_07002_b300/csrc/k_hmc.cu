@@ -565,3 +565,57 @@ __global__ void k_eta_ref(int N, int N_pad, int p, int KP, const __nv_bfloat16 *
   eta_half[n] = (float)(0.5 * s);
 }
 }  // namespace pcv
+
+namespace pcv {
+// ---------------------------------------------------------------------------
+// R-hat_max benchmark by block shuffling (Section 4.2; the shuffle loop of
+// Algorithm A2).  Chains are cut into D contiguous blocks of whole batches
+// (block d holds batches [d a / D, (d+1) a / D)); replicate r rebuilds
+// every chain slot of every fold from blocks of chains drawn uniformly with
+// replacement and takes the R-hat (eq. rhat) of the rebuilt chains.
+// ---------------------------------------------------------------------------
+// Welford state (count, mean, M2) of each (chain, block): [C x D] x 3
+__global__ void k_block_stats(Accum A, int a, int D, double *blk) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)A.C * D) return;
+  const int c = (int)(t / D), d = (int)(t - (long long)c * D);
+  Welf w{0.0, 0.0, 0.0};
+  const int h0 = (int)((long long)d * a / D), h1 = (int)((long long)(d + 1) * a / D);
+  for (int h = h0; h < h1; ++h) welf_merge(w, (double)A.b, A.bmean[(size_t)h * A.C + c], A.bM2[(size_t)h * A.C + c]);
+  blk[3 * t] = w.n;
+  blk[3 * t + 1] = w.mean;
+  blk[3 * t + 2] = w.M2;
+}
+
+// one thread per (replicate r, fold k): the picks are word t % 4 of Philox
+// (block t / 4, chain k, iteration r, stream ST_SHUF) for t = l D + d,
+// l' = floor(w L / 2^32); out_max[r] = max over folds (bit pattern of a
+// non-negative double, so an integer max orders it), out_all[r K + k]
+__global__ void k_rhat_shuffle(const double *blk, int K, int L, int D, int R, unsigned long long seed,
+                               unsigned long long *out_max, double *out_all) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)R * K) return;
+  const int r = (int)(t / K), k = (int)(t - (long long)r * K);
+  double wsum = 0.0, nn = 0.0;
+  Welf means{0.0, 0.0, 0.0};                      // Welford of the slot means
+  for (int l = 0; l < L; ++l) {
+    Welf w{0.0, 0.0, 0.0};
+    for (int d = 0; d < D; ++d) {
+      const int q = l * D + d;
+      const uint4 wd = philox_at(seed, (uint32_t)(q >> 2), (uint32_t)k, (uint32_t)r, ST_SHUF);
+      const uint32_t word = (q & 3) == 0 ? wd.x : (q & 3) == 1 ? wd.y : (q & 3) == 2 ? wd.z : wd.w;
+      const int src = (int)(((unsigned long long)word * (unsigned long long)L) >> 32);
+      const double *b3 = blk + 3 * ((size_t)(k * L + src) * D + d);
+      welf_merge(w, b3[0], b3[1], b3[2]);
+    }
+    nn = w.n;
+    wsum += w.M2 / (w.n - 1.0);
+    welf_merge(means, 1.0, w.mean, 0.0);
+  }
+  const double Wv = wsum / L;
+  const double B = nn * means.M2 / (L - 1.0);
+  const double rh = sqrt((((nn - 1.0) / nn) * Wv + B / nn) / Wv);
+  if (out_all) out_all[t] = rh;
+  atomicMax(out_max + r, (unsigned long long)__double_as_longlong(rh));
+}
+}  // namespace pcv

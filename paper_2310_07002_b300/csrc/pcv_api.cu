@@ -105,6 +105,10 @@ struct pcv_ctx {
   std::map<int, int> tuned_splits;
   std::map<std::pair<int, int>, int> tuned_ns;
   std::vector<std::string> tune_log;
+  // R-hat_max benchmark scratch
+  double *shuf_blk = nullptr, *shuf_all = nullptr;
+  unsigned long long *shuf_max = nullptr;
+  size_t shuf_blk_n = 0, shuf_all_n = 0, shuf_max_n = 0;
   size_t ws_tc_floats = 0;
   unsigned int *tickets_tc = nullptr;
   size_t n_tickets_tc = 0;
@@ -1386,6 +1390,46 @@ pcv_status pcv_checkpoint_load(pcv_ctx *x, const void *buf, int64_t bytes) {
   pcv_status s = write_shadow(x, x->fold_cb, x->fold_cb.theta, x->d_pad);
   if (s != PCV_OK) return s;
   CK(cudaStreamSynchronize(x->stream));
+  leave(x);
+  return PCV_OK;
+}
+
+pcv_status pcv_rhat_shuffle(pcv_ctx *x, int32_t n_blocks, int32_t n_reps, double *rhat_max_rep,
+                            double *rhat_fold_rep) {
+  if (!x) return PCV_E_INVALID_ARG;
+  if (!rhat_max_rep || n_blocks < 1 || n_reps < 1) return fail(x, PCV_E_INVALID_ARG, "bad argument");
+  if (x->state != ST_SAMPLED) return fail(x, PCV_E_BAD_STATE, "pcv_rhat_shuffle before pcv_sample");
+  const long long a = x->n_sampled / x->b;
+  if (a < n_blocks) return fail(x, PCV_E_INVALID_ARG, "fewer batches than blocks");
+  if (a > x->max_batches) return fail(x, PCV_E_INVALID_ARG, "more batches than max_batches were stored");
+  const size_t nb = (size_t)x->C * n_blocks * 3, na = (size_t)n_reps * x->K;
+  if (nb > x->shuf_blk_n) {
+    if (!dalloc_n(x, &x->shuf_blk, nb)) return fail(x, PCV_E_OOM, "allocation failed");
+    x->shuf_blk_n = nb;
+  }
+  if (rhat_fold_rep && na > x->shuf_all_n) {
+    if (!dalloc_n(x, &x->shuf_all, na)) return fail(x, PCV_E_OOM, "allocation failed");
+    x->shuf_all_n = na;
+  }
+  if ((size_t)n_reps > x->shuf_max_n) {
+    if (!dalloc_n(x, &x->shuf_max, (size_t)n_reps)) return fail(x, PCV_E_OOM, "allocation failed");
+    x->shuf_max_n = (size_t)n_reps;
+  }
+  enter(x);
+  const long long T1 = (long long)x->C * n_blocks;
+  k_block_stats<<<(unsigned)((T1 + 255) / 256), 256, 0, x->stream>>>(x->acc, (int)a, n_blocks, x->shuf_blk);
+  CK(cudaGetLastError());
+  CK(cudaMemsetAsync(x->shuf_max, 0, sizeof(unsigned long long) * n_reps, x->stream));
+  const long long T2 = (long long)n_reps * x->K;
+  k_rhat_shuffle<<<(unsigned)((T2 + 255) / 256), 256, 0, x->stream>>>(
+      x->shuf_blk, x->K, x->L, n_blocks, n_reps, x->opt.seed, x->shuf_max, rhat_fold_rep ? x->shuf_all : nullptr);
+  CK(cudaGetLastError());
+  std::vector<unsigned long long> hm(n_reps);
+  CK(cudaMemcpyAsync(hm.data(), x->shuf_max, sizeof(unsigned long long) * n_reps, cudaMemcpyDeviceToHost, x->stream));
+  if (rhat_fold_rep)
+    CK(cudaMemcpyAsync(rhat_fold_rep, x->shuf_all, sizeof(double) * na, cudaMemcpyDeviceToHost, x->stream));
+  CK(cudaStreamSynchronize(x->stream));
+  for (int r = 0; r < n_reps; ++r) std::memcpy(&rhat_max_rep[r], &hm[r], sizeof(double));
   leave(x);
   return PCV_OK;
 }

@@ -17,7 +17,7 @@ enum ModelVariant : int {
 
 // Philox stream tags (the counter's last word)
 enum Stream : uint32_t {
-  ST_MOM = 0, ST_ACC = 1, ST_INIT = 2, ST_JIT = 3, ST_FD_MOM = 16, ST_FD_ACC = 17, ST_FD_INIT = 18
+  ST_MOM = 0, ST_ACC = 1, ST_INIT = 2, ST_JIT = 3, ST_SHUF = 4, ST_FD_MOM = 16, ST_FD_ACC = 17, ST_FD_INIT = 18
 };
 
 // Row ranges of one fold in the library's sorted row order (the Appendix B
@@ -275,6 +275,9 @@ __global__ void k_init_from_pool(int C, int d, int ld, unsigned long long seed, 
                                  int n_pool, float *theta);
 __global__ void k_shadow(int C, int d, int ld, const float *theta, const float *theta_ref,
                          __nv_bfloat16 *hi, __nv_bfloat16 *lo, int ld_shadow);
+__global__ void k_block_stats(Accum A, int a, int D, double *blk);
+__global__ void k_rhat_shuffle(const double *blk, int K, int L, int D, int R, unsigned long long seed,
+                               unsigned long long *out_max, double *out_all);
 __global__ void k_theta_ref(int n, int d, int ld, const float *src, float *theta_ref);
 __global__ void k_eta_ref(int N, int N_pad, int p, int KP, const __nv_bfloat16 *X16, const float *theta_ref,
                           float *eta_half);

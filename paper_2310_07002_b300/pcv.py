@@ -88,6 +88,7 @@ def load():
         "pcv_dim": (i32, [vp]),
         "pcv_last_error": (ct.c_char_p, [vp]),
         "pcv_tuning_info": (i32, [vp, ct.c_char_p, i32]),
+        "pcv_rhat_shuffle": (i32, [vp, i32, i32, vp, vp]),
         "pcv_checkpoint_size": (i32, [vp, ct.POINTER(i64)]),
         "pcv_checkpoint_save": (i32, [vp, vp, i64]),
         "pcv_checkpoint_load": (i32, [vp, vp, i64]),
@@ -121,7 +122,8 @@ def exported_symbols():
             "pcv_log_density", "pcv_trajectory", "pcv_draw_normals", "pcv_accumulate",
             "pcv_get_draws", "pcv_accept_rate", "pcv_last_sample_ms",
             "pcv_time_leapfrog_kernel", "pcv_log_density_noalloc", "pcv_tuning_info",
-            "pcv_checkpoint_size", "pcv_checkpoint_save", "pcv_checkpoint_load"]
+            "pcv_checkpoint_size", "pcv_checkpoint_save", "pcv_checkpoint_load",
+            "pcv_rhat_shuffle"]
 
 
 def _ptr(a: Optional[np.ndarray]):
@@ -312,6 +314,15 @@ class PCV:
         self._check(self._L.pcv_get_positions(self.h, _ptr(th), _ptr(lp), _ptr(sh)),
                     "pcv_get_positions")
         return th, lp, sh
+
+    def rhat_shuffle(self, n_blocks: int = 5, n_reps: int = 500, per_fold: bool = False):
+        """R-hat_max benchmark replicates (Section 4.2): [n_reps] maxima over
+        folds, and [n_reps, K] per-fold values when per_fold."""
+        mx = np.empty(n_reps)
+        allv = np.empty((n_reps, self.K)) if per_fold else None
+        self._check(self._L.pcv_rhat_shuffle(self.h, n_blocks, n_reps, _ptr(mx), _ptr(allv)),
+                    "pcv_rhat_shuffle")
+        return (mx, allv) if per_fold else mx
 
     def checkpoint(self) -> bytes:
         """The run's state as bytes (see pcv_checkpoint_save)."""

@@ -56,6 +56,8 @@ def run(w, precision: str, draws: int, fd_warmup: int, fold_warmup: int, seed: i
     sc = pc.scores()
     dg = pc.diagnostics()
     t["finalize_s"] = time.perf_counter() - t0
+    # R-hat_max benchmark (Section 4.2): 500 block-shuffled replicates, 5 blocks
+    rep = pc.rhat_shuffle(5, 500) if draws // w.batch_size >= 5 else None
     eps, _ = pc.adaptation()
     acc = pc.accept_rate()
     C = pc.C
@@ -67,6 +69,9 @@ def run(w, precision: str, draws: int, fd_warmup: int, fold_warmup: int, seed: i
         "elpd": float(sc["elpd_total"]), "mcse": float(sc["mcse_total"]),
         "se_epistemic": float(sc["se_epistemic"]),
         "rhat_max": float(dg["rhat_max"]),
+        "rhat_max_shuffle_q": (None if rep is None else
+                               [float(q) for q in np.quantile(rep, [0.05, 0.5, 0.95])]),
+        "rhat_max_shuffle_rank": (None if rep is None else float(np.mean(rep < dg["rhat_max"]))),
         "split_rhat_max": float(np.max(dg["split_rhat"])),
         "folds_rhat_ge_1.01": int(np.sum(dg["rhat"] >= 1.01)),
         "ess_total": float(dg["ess_total"]),
