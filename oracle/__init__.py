@@ -22,12 +22,16 @@ Parity status of each function (pins live in ``tests/test_oracle_*.py``):
   R-hat from stored draws), by brute-force enumeration of every pick pattern
   on a tiny case, by the uniformity of the picks, and by the paper's
   pathological chains (a shifted chain lies outside the benchmark).
+* covariate-selection mask and pairwise comparison -- pinned by the
+  conjugate closed form of the sub-design model (its fold elpd within MCSE)
+  and of the difference of two models, and by scipy's normal cdf.
 * full-data warm-up (dual averaging, mass estimate) -- parity unpinned
   beyond the conjugate-model checks: it is an adaptive heuristic with no
   closed form; its outputs are only checked statistically.
 """
 from .oracle import (  # noqa: F401
     build, lib, Problem, problem_from_workload, philox, normals, uniform,
-    index, log_density, trajectory, accumulate_series, shuffle_series, rhat_from_picks, OraclePCV,
+    index, log_density, trajectory, accumulate_series, shuffle_series, rhat_from_picks, compare,
+    OraclePCV,
     FOLD_FIELDS, TOTAL_FIELDS,
 )

@@ -48,7 +48,7 @@ class Problem(ct.Structure):
                 ("K", ct.c_int32), ("h", ct.c_int32), ("group", ct.c_void_p),
                 ("G", ct.c_int32), ("beta_sd", ct.c_double),
                 ("sigma_known", ct.c_double), ("sigma_sd", ct.c_double),
-                ("tau_sd", ct.c_double)]
+                ("tau_sd", ct.c_double), ("active", ct.c_void_p)]
 
 
 _D = ct.POINTER(ct.c_double)
@@ -85,6 +85,8 @@ def _declare(L):
     L.orc_rhat_from_picks_series.restype = ct.c_int
     L.orc_pcv_rhat_shuffle.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _D]
     L.orc_pcv_rhat_shuffle.restype = ct.c_int
+    L.orc_compare.argtypes = [ct.c_int32, _D, _D, _D, _D, _D, _D, _D]
+    L.orc_compare.restype = ct.c_int
     L.orc_pcv_set_tuning.argtypes = [ct.c_void_p, ct.c_double, ct.c_double]
     L.orc_pcv_set_tuning.restype = ct.c_int
     L.orc_pcv_fulldata.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_double]
@@ -118,16 +120,18 @@ class _ProblemHolder:
     """Keeps the numpy arrays behind a Problem struct alive."""
 
     def __init__(self, kind, X, y, fold, K, h=0, group=None, G=0, beta_sd=1.0,
-                 sigma_known=-1.0, sigma_sd=1.0, tau_sd=1.0):
+                 sigma_known=-1.0, sigma_sd=1.0, tau_sd=1.0, active=None):
         self.X = np.ascontiguousarray(X, dtype=np.float64)
         self.y = np.ascontiguousarray(y, dtype=np.float64)
         self.fold = np.ascontiguousarray(fold, dtype=np.int32)
         self.group = None if group is None else np.ascontiguousarray(group, dtype=np.int32)
+        self.active = None if active is None else np.ascontiguousarray(active, dtype=np.int32)
         N, p = self.X.shape
         self.s = Problem(kind, p, N, self.X.ctypes.data, self.y.ctypes.data,
                          self.fold.ctypes.data, K, h,
                          None if self.group is None else self.group.ctypes.data,
-                         G, beta_sd, sigma_known, sigma_sd, tau_sd)
+                         G, beta_sd, sigma_known, sigma_sd, tau_sd,
+                         None if self.active is None else self.active.ctypes.data)
 
     @property
     def dim(self) -> int:
@@ -137,7 +141,19 @@ class _ProblemHolder:
 def problem_from_workload(w) -> _ProblemHolder:
     return _ProblemHolder(w.kind, w.X, w.y, w.fold, w.K, w.hv_buffer, w.group,
                           w.n_groups, w.beta_prior_sd, w.sigma_known,
-                          w.sigma_prior_sd, w.tau_prior_sd)
+                          w.sigma_prior_sd, w.tau_prior_sd, w.active)
+
+
+def compare(elpd_a, mcse_a, elpd_b, mcse_b):
+    """Pairwise model selection (eq. sel-cv, norm-approx, mc-var): returns a
+    dict with delta_k, mcse_k, delta, se, mcse, prob (Pr(A better than B))."""
+    ea, ma, eb, mb = (np.ascontiguousarray(v, dtype=np.float64) for v in (elpd_a, mcse_a, elpd_b, mcse_b))
+    K = ea.size
+    dk = np.empty(K)
+    mk = np.empty(K)
+    out = np.empty(4)
+    assert lib().orc_compare(K, _dp(ea), _dp(ma), _dp(eb), _dp(mb), _dp(dk), _dp(mk), _dp(out)) == 0
+    return {"delta_k": dk, "mcse_k": mk, "delta": out[0], "se": out[1], "mcse": out[2], "prob": out[3]}
 
 
 def philox(ctr, key):

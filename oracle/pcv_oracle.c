@@ -143,6 +143,10 @@ typedef struct {
     double sigma_known;     /* > 0: known noise sd */
     double sigma_sd;        /* half-normal prior scale of sigma */
     double tau_sd;          /* half-normal prior scale of tau */
+    const int32_t *active;  /* p flags, 1 = covariate in the model (NULL: all);
+                             * Appendix B's selection mask M_j: an inactive
+                             * coefficient is held at 0 (inverse mass 0), so it
+                             * drops out of the likelihood and the predictive */
 } orc_problem;
 
 int32_t orc_dim(const orc_problem *P)
@@ -398,7 +402,7 @@ static double hmc_transition(const orc_problem *P, int32_t k, uint64_t seed, uin
     const int32_t d = orc_dim(P);
     double *r = work, *th = work + d, *gr = work + 2 * d;
     orc_normals(seed, chain, iter, st_mom, d, r);
-    for (int32_t j = 0; j < d; ++j) r[j] /= sqrt(minv[j]);
+    for (int32_t j = 0; j < d; ++j) r[j] = minv[j] > 0 ? r[j] / sqrt(minv[j]) : 0.0;   /* held coordinates: r = 0 */
     double H0 = -c->logp + kinetic(d, minv, r);
     memcpy(th, c->theta, sizeof(double) * (size_t)d);
     memcpy(gr, c->grad, sizeof(double) * (size_t)d);
@@ -756,6 +760,40 @@ int orc_accumulate_series(int32_t C, int32_t L, int32_t n, const double *s, int3
 }
 
 /* ------------------------------------------------------------------------ */
+/* Pairwise model selection (eq. sel-cv, eq. norm-approx, eq. mc-var)        */
+/* ------------------------------------------------------------------------ */
+/*
+ * From the per-fold elpd and MCSE of models A and B on the same folds:
+ *   delta_k = elpd_A,k - elpd_B,k,  delta = sum_k delta_k          eq. sel-cv
+ *   sigma2  = 1/(K-1) sum_k (delta_k - delta/K)^2
+ *   se      = sqrt(K sigma2),  Pr(A > B) = Phi(delta / se)     eq. norm-approx
+ *   mcse_k  = sqrt(MCSE_A,k^2 + MCSE_B,k^2), mcse = sqrt(sum_k mcse_k^2)
+ *                                     (MC variance summed over models, eq. mc-var)
+ * out = {delta, se, mcse, prob}; delta_k, mcse_k per fold.
+ */
+int orc_compare(int32_t K, const double *elpd_a, const double *mcse_a, const double *elpd_b,
+                const double *mcse_b, double *delta_k, double *mcse_k, double *out)
+{
+    if (K < 2) return -1;
+    double sum = 0.0, mc2 = 0.0;
+    for (int32_t k = 0; k < K; ++k) {
+        delta_k[k] = elpd_a[k] - elpd_b[k];
+        mcse_k[k] = sqrt(mcse_a[k] * mcse_a[k] + mcse_b[k] * mcse_b[k]);
+        sum += delta_k[k];
+        mc2 += mcse_k[k] * mcse_k[k];
+    }
+    double var = 0.0;
+    for (int32_t k = 0; k < K; ++k) var += (delta_k[k] - sum / K) * (delta_k[k] - sum / K);
+    var /= (K - 1.0);
+    const double se = sqrt(K * var);
+    out[0] = sum;
+    out[1] = se;
+    out[2] = sqrt(mc2);
+    out[3] = 0.5 * erfc(-(sum / se) / sqrt(2.0));   /* Phi(delta / se) */
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* R-hat_max benchmark by block shuffling (Section 4.2; the shuffle loop of  */
 /* Algorithm A2)                                                              */
 /* ------------------------------------------------------------------------ */
@@ -893,6 +931,8 @@ orc_pcv *orc_pcv_create(const orc_problem *P, int32_t L, uint64_t seed, int32_t 
     S->minv = (double *)malloc(sizeof(double) * (size_t)S->d);
     S->user_minv = minv != NULL;
     for (int32_t j = 0; j < S->d; ++j) S->minv[j] = minv ? minv[j] : 1.0;
+    if (P->active)
+        for (int32_t j = 0; j < P->p; ++j) if (!P->active[j]) S->minv[j] = 0.0;
     S->chains = (orc_chain *)calloc((size_t)S->C, sizeof(orc_chain));
     S->thbuf = (double *)calloc((size_t)S->C * S->d, sizeof(double));
     S->grbuf = (double *)calloc((size_t)S->C * S->d, sizeof(double));
@@ -993,6 +1033,8 @@ int orc_pcv_fulldata(orc_pcv *S, int32_t n_adapt, int32_t n_keep, double eps0)
         ch[c].grad = ch[c].theta + d;
         orc_normals(S->seed, (uint32_t)c, 0, ST_FD_INIT, d, ch[c].theta);
         for (int32_t j = 0; j < d; ++j) ch[c].theta[j] *= S->init_scale;
+        if (P->active)
+            for (int32_t j = 0; j < P->p; ++j) if (!P->active[j]) ch[c].theta[j] = 0.0;
         chain_refresh(P, -1, &ch[c]);
     }
     dual_avg D;
@@ -1027,6 +1069,8 @@ int orc_pcv_fulldata(orc_pcv *S, int32_t n_adapt, int32_t n_keep, double eps0)
         if (adapt_mass && (i == w1 - 1 || i == w2 - 1) && wn > 1) {
             double w = wn / (wn + 5.0);
             for (int32_t j = 0; j < d; ++j) S->minv[j] = w * (wM2[j] / (wn - 1.0)) + 1e-3 * (1.0 - w);
+            if (P->active)
+                for (int32_t j = 0; j < P->p; ++j) if (!P->active[j]) S->minv[j] = 0.0;
             for (int32_t c = 0; c < NFD; ++c) chain_refresh(P, -1, &ch[c]);
             da_reset(&D, S->eps);
             wn = 0.0;                              /* the next window starts afresh */

@@ -61,6 +61,7 @@ class Workload:
     batch_size: int = 50
     seed: int = 0                    # sampler seed
     truth: dict = field(default_factory=dict)
+    active: Optional[np.ndarray] = None   # int32 [p] covariate-selection mask (None: all)
 
     @property
     def N(self) -> int:
