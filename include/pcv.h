@@ -87,6 +87,12 @@ typedef struct {
     double tau_prior_sd;       /* > 0 (HIER_GAUSS) */
     const int32_t *group;      /* host, N entries in [0, n_groups) (HIER_GAUSS), else NULL */
     int32_t n_groups;          /* HIER_GAUSS only */
+    /* host, p flags (1 = covariate in the model), or NULL for all: the
+     * covariate-selection mask M_j of Appendix B. An inactive coefficient is
+     * held at zero (inverse mass 0), so it leaves the likelihood and the
+     * predictive; two contexts that differ only in this mask are the models
+     * compared by pcv_compare. */
+    const int32_t *active_covariates;
 } pcv_model;
 
 /* Optional device allocator (the Python binding passes the torch caching
@@ -270,6 +276,19 @@ pcv_status pcv_get_draws(pcv_ctx *ctx, double *shat, int32_t *n_stored);
 
 /* Mean acceptance rate per fold over sampling (host, K). */
 pcv_status pcv_accept_rate(pcv_ctx *ctx, double *accept_k);
+
+/*
+ * Pairwise model selection (eq. sel-cv, eq. norm-approx, eq. mc-var) between
+ * model A (ctx_a) and model B (ctx_b), two contexts sampled on the same data
+ * and folds (typically the same model with different covariate masks):
+ *   delta_k = elpd_A,k - elpd_B,k (host, K), mcse_k = sqrt(MCSE_A,k^2 +
+ *   MCSE_B,k^2) (host, K), and out[4] = {delta = sum_k delta_k,
+ *   se = sqrt(K var_k(delta_k)), MCSE of delta = sqrt(sum_k mcse_k^2),
+ *   Pr(A better than B) = Phi(delta / se)}.
+ * Both contexts need pcv_sample first (PCV_E_BAD_STATE); different N or K
+ * give PCV_E_INVALID_ARG.
+ */
+pcv_status pcv_compare(pcv_ctx *ctx_a, pcv_ctx *ctx_b, double *delta_k, double *mcse_k, double *out);
 
 /*
  * R-hat_max benchmark (Section 4.2; the block-shuffle loop of Algorithm A2):

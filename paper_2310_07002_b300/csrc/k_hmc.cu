@@ -48,7 +48,8 @@ __global__ void __launch_bounds__(256) k_begin(BeginArgs a) {
       const int j = 4 * q + e;
       if (j >= a.d) break;
       const float mv = a.minv[j];
-      const float r0 = a.r_given ? a.r_given[(size_t)c * a.ld + j] : z[e] / sqrtf(mv);
+      // a coordinate with inverse mass 0 (masked covariate) is held: r = 0
+      const float r0 = a.r_given ? a.r_given[(size_t)c * a.ld + j] : (mv > 0.0f ? z[e] / sqrtf(mv) : 0.0f);
       kin += (double)mv * (double)r0 * (double)r0;
       const float rh = r0 + 0.5f * eps * g[j];
       const float tn = th[j] + eps * mv * rh;
@@ -324,6 +325,7 @@ __global__ void k_fd_adapt(FdAdaptArgs a) {
         const double w = wn / (wn + 5.0);
         for (int j = threadIdx.x; j < a.d; j += blockDim.x) {
           a.minv[j] = (float)(w * (a.wM2[j] / (wn - 1.0)) + 1e-3 * (1.0 - w));
+          if (a.active) a.minv[j] *= a.active[j];          // masked covariates stay held
           a.wmean[j] = 0.0;
           a.wM2[j] = 0.0;
         }
@@ -617,5 +619,52 @@ __global__ void k_rhat_shuffle(const double *blk, int K, int L, int D, int R, un
   const double rh = sqrt((((nn - 1.0) / nn) * Wv + B / nn) / Wv);
   if (out_all) out_all[t] = rh;
   atomicMax(out_max + r, (unsigned long long)__double_as_longlong(rh));
+}
+}  // namespace pcv
+
+namespace pcv {
+// zero the masked coordinates of C positions
+__global__ void k_mask_positions(int C, int d, int ld, const float *active, float *theta) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)C * d) return;
+  const int c = (int)(t / d), j = (int)(t - (long long)c * d);
+  theta[(size_t)c * ld + j] *= active[j];
+}
+
+// pairwise model selection from two contexts' fold results (eq. sel-cv,
+// eq. norm-approx, eq. mc-var): out = [delta_k (K) | mcse_k (K) | delta, se,
+// mcse, Pr(A better than B)]; one block, fixed reduction order
+__global__ void k_compare(const double *fo_a, const double *fo_b, int K, double *out) {
+  __shared__ double sh[2][256];
+  double s = 0.0, m2 = 0.0;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const double dk = fo_a[(size_t)k * F_NFIELDS + F_ELPD] - fo_b[(size_t)k * F_NFIELDS + F_ELPD];
+    const double ma = fo_a[(size_t)k * F_NFIELDS + F_MCSE], mb = fo_b[(size_t)k * F_NFIELDS + F_MCSE];
+    const double mk2 = ma * ma + mb * mb;
+    out[k] = dk;
+    out[K + k] = sqrt(mk2);
+    s += dk;
+    m2 += mk2;
+  }
+  sh[0][threadIdx.x] = s;
+  sh[1][threadIdx.x] = m2;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double sum = sh[0][0], mean = sum / K;
+    double v = 0.0;
+    for (int k = 0; k < K; ++k) v += (out[k] - mean) * (out[k] - mean);
+    const double se = sqrt(K * (v / (K - 1.0)));
+    out[2 * K] = sum;
+    out[2 * K + 1] = se;
+    out[2 * K + 2] = sqrt(sh[1][0]);
+    out[2 * K + 3] = 0.5 * erfc(-(sum / se) * 0.70710678118654752440);
+  }
 }
 }  // namespace pcv

@@ -105,6 +105,11 @@ struct pcv_ctx {
   std::map<int, int> tuned_splits;
   std::map<std::pair<int, int>, int> tuned_ns;
   std::vector<std::string> tune_log;
+  // covariate-selection mask (d_pad floats 1 / 0; nullptr: every covariate)
+  float *active_d = nullptr;
+  std::vector<float> active_h;
+  double *cmp_out = nullptr;
+  size_t cmp_n = 0;
   // R-hat_max benchmark scratch
   double *shuf_blk = nullptr, *shuf_all = nullptr;
   unsigned long long *shuf_max = nullptr;
@@ -476,6 +481,7 @@ pcv_status launch_iteration(pcv_ctx *x, ChainBufs &cb, bool fd, bool accumulate)
     fa.minv = x->minv;
     fa.wmean = x->wmean; fa.wM2 = x->wM2;
     fa.pool = x->pool;
+    fa.active = x->active_d;
     fa.n_keep = x->n_fd_draws;
     k_fd_adapt<<<1, 128, 0, x->stream>>>(fa);
     CK(cudaGetLastError());
@@ -833,6 +839,18 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
       if (!(opt->inv_mass_diag[j] > 0)) return bail(PCV_E_INVALID_ARG, "inverse mass must be > 0");
       hm[j] = (float)opt->inv_mass_diag[j];
     }
+  if (model->active_covariates) {
+    // covariate-selection mask: inactive coefficients are held at zero
+    x->active_h.assign(x->d_pad, 1.0f);
+    for (int j = 0; j < p; ++j) {
+      const int32_t a = model->active_covariates[j];
+      if (a != 0 && a != 1) return bail(PCV_E_INVALID_ARG, "active_covariates must hold 0 or 1");
+      x->active_h[j] = (float)a;
+      if (!a) hm[j] = 0.0f;
+    }
+    if (!dalloc_n(x, &x->active_d, (size_t)x->d_pad)) return bail(PCV_E_OOM, "device allocation failed");
+    cudaMemcpyAsync(x->active_d, x->active_h.data(), sizeof(float) * x->d_pad, cudaMemcpyHostToDevice, x->stream);
+  }
   cudaMemcpyAsync(x->minv, hm.data(), hm.size() * sizeof(float), cudaMemcpyHostToDevice, x->stream);
   if (x->variant == MV_HIER) {
     if (!dalloc_n(x, &x->seg_off, seg_off.size()) || !dalloc_n(x, &x->seg_grp, seg_grp.size()) ||
@@ -896,6 +914,12 @@ pcv_status pcv_warmup(pcv_ctx *x, int32_t n_fd, int32_t n_wu) {
     k_normals<<<(unsigned)((T + 255) / 256), 256, 0, x->stream>>>(
         kNumFdChains, x->d, x->d_pad, x->opt.seed, 0u, ST_FD_INIT, (float)x->opt.init_scale, x->fd_cb.theta);
     CK(cudaGetLastError());
+    if (x->active_d) {
+      const long long Tm = (long long)kNumFdChains * x->d;
+      k_mask_positions<<<(unsigned)((Tm + 255) / 256), 256, 0, x->stream>>>(kNumFdChains, x->d, x->d_pad,
+                                                                          x->active_d, x->fd_cb.theta);
+      CK(cudaGetLastError());
+    }
   }
   pcv_status s = refresh(x, x->fd_cb);
   if (s != PCV_OK) return s;
@@ -1024,7 +1048,7 @@ pcv_status pcv_set_positions(pcv_ctx *x, const double *theta, double step_size, 
     for (int j = 0; j < x->d; ++j) {
       const double v = theta[(size_t)c * x->d + j];
       if (!std::isfinite(v)) return fail(x, PCV_E_NUMERIC, "non-finite position");
-      h[(size_t)c * x->d_pad + j] = (float)v;
+      h[(size_t)c * x->d_pad + j] = x->active_d ? (float)v * x->active_h[j] : (float)v;   // masked: held at 0
     }
   CK(cudaMemcpyAsync(x->fold_cb.theta, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, x->stream));
   {
@@ -1041,7 +1065,7 @@ pcv_status pcv_set_positions(pcv_ctx *x, const double *theta, double step_size, 
     std::vector<float> hm(x->d_pad, 1.0f);
     for (int j = 0; j < x->d; ++j) {
       if (!(inv_mass[j] > 0)) return fail(x, PCV_E_INVALID_ARG, "inverse mass must be > 0");
-      hm[j] = (float)inv_mass[j];
+      hm[j] = (float)inv_mass[j] * (x->active_d ? x->active_h[j] : 1.0f);
     }
     CK(cudaMemcpyAsync(x->minv, hm.data(), hm.size() * sizeof(float), cudaMemcpyHostToDevice, x->stream));
   }
@@ -1391,6 +1415,33 @@ pcv_status pcv_checkpoint_load(pcv_ctx *x, const void *buf, int64_t bytes) {
   if (s != PCV_OK) return s;
   CK(cudaStreamSynchronize(x->stream));
   leave(x);
+  return PCV_OK;
+}
+
+pcv_status pcv_compare(pcv_ctx *a, pcv_ctx *b, double *delta_k, double *mcse_k, double *out) {
+  if (!a || !b) return PCV_E_INVALID_ARG;
+  pcv_ctx *x = a;   // the context that reports errors (CK)
+  if (!delta_k || !mcse_k || !out) return fail(a, PCV_E_INVALID_ARG, "null argument");
+  if (a->N != b->N || a->K != b->K) return fail(a, PCV_E_INVALID_ARG, "the two contexts have different data or folds");
+  if (a->state != ST_SAMPLED || b->state != ST_SAMPLED) return fail(a, PCV_E_BAD_STATE, "pcv_compare before pcv_sample");
+  pcv_status s = finalize(b);
+  if (s != PCV_OK) return fail(a, s, std::string("model B: ") + b->err);
+  enter(a);
+  if ((s = finalize(a)) != PCV_OK) return s;
+  const int K = a->K;
+  if ((size_t)(2 * K + 4) > a->cmp_n) {
+    if (!dalloc_n(a, &a->cmp_out, (size_t)(2 * K + 4))) return fail(a, PCV_E_OOM, "allocation failed");
+    a->cmp_n = (size_t)(2 * K + 4);
+  }
+  k_compare<<<1, 256, 0, a->stream>>>(a->fold_out, b->fold_out, K, a->cmp_out);
+  CK(cudaGetLastError());
+  std::vector<double> h((size_t)(2 * K + 4));
+  CK(cudaMemcpyAsync(h.data(), a->cmp_out, h.size() * sizeof(double), cudaMemcpyDeviceToHost, a->stream));
+  CK(cudaStreamSynchronize(a->stream));
+  std::memcpy(delta_k, h.data(), sizeof(double) * K);
+  std::memcpy(mcse_k, h.data() + K, sizeof(double) * K);
+  std::memcpy(out, h.data() + 2 * K, sizeof(double) * 4);
+  leave(a);
   return PCV_OK;
 }
 

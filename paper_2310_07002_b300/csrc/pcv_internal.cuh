@@ -254,6 +254,7 @@ struct FdAdaptArgs {
   IterState *st;
   int n_adapt, w0, w1, w2;     // mass windows [w0, w1) and [w1, w2)
   float eps_cap;              // final step size cap (trajectory length / L_f); <= 0: none
+  const float *active;        // d: 1 / 0 covariate-selection mask (nullptr: all active)
   int adapt_eps, adapt_mass;
   int C, d, ld;
   const float *theta;
@@ -276,6 +277,8 @@ __global__ void k_init_from_pool(int C, int d, int ld, unsigned long long seed, 
 __global__ void k_shadow(int C, int d, int ld, const float *theta, const float *theta_ref,
                          __nv_bfloat16 *hi, __nv_bfloat16 *lo, int ld_shadow);
 __global__ void k_block_stats(Accum A, int a, int D, double *blk);
+__global__ void k_mask_positions(int C, int d, int ld, const float *active, float *theta);
+__global__ void k_compare(const double *fo_a, const double *fo_b, int K, double *out);
 __global__ void k_rhat_shuffle(const double *blk, int K, int L, int D, int R, unsigned long long seed,
                                unsigned long long *out_max, double *out_all);
 __global__ void k_theta_ref(int n, int d, int ld, const float *src, float *theta_ref);

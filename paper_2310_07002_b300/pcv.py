@@ -37,7 +37,7 @@ class Model(ct.Structure):
     _fields_ = [("kind", ct.c_int32), ("beta_prior_sd", ct.c_double),
                 ("sigma_known", ct.c_double), ("sigma_prior_sd", ct.c_double),
                 ("tau_prior_sd", ct.c_double), ("group", ct.c_void_p),
-                ("n_groups", ct.c_int32)]
+                ("n_groups", ct.c_int32), ("active_covariates", ct.c_void_p)]
 
 
 ALLOC_FN = ct.CFUNCTYPE(ct.c_void_p, ct.c_size_t, ct.c_void_p)
@@ -89,6 +89,7 @@ def load():
         "pcv_last_error": (ct.c_char_p, [vp]),
         "pcv_tuning_info": (i32, [vp, ct.c_char_p, i32]),
         "pcv_rhat_shuffle": (i32, [vp, i32, i32, vp, vp]),
+        "pcv_compare": (i32, [vp, vp, vp, vp, vp]),
         "pcv_checkpoint_size": (i32, [vp, ct.POINTER(i64)]),
         "pcv_checkpoint_save": (i32, [vp, vp, i64]),
         "pcv_checkpoint_load": (i32, [vp, vp, i64]),
@@ -123,7 +124,7 @@ def exported_symbols():
             "pcv_get_draws", "pcv_accept_rate", "pcv_last_sample_ms",
             "pcv_time_leapfrog_kernel", "pcv_log_density_noalloc", "pcv_tuning_info",
             "pcv_checkpoint_size", "pcv_checkpoint_save", "pcv_checkpoint_load",
-            "pcv_rhat_shuffle"]
+            "pcv_rhat_shuffle", "pcv_compare"]
 
 
 def _ptr(a: Optional[np.ndarray]):
@@ -176,7 +177,7 @@ class PCV:
                  n_fulldata_draws: int = 250, init_scale: float = 1.0,
                  use_graphs: bool = True, torch_allocator: bool = True,
                  trajectory_length: float = -1.0, step_jitter: float = -1.0,
-                 autotune: bool = True):
+                 autotune: bool = True, active=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("PCV needs a CUDA device (sm_103a); none is available")
@@ -188,8 +189,9 @@ class PCV:
         self._group = None if group is None else np.ascontiguousarray(group, dtype=np.int32)
         N, p = X.shape
         self.N, self.p, self.L = N, p, chains_per_fold
+        self._active = None if active is None else np.ascontiguousarray(active, dtype=np.int32)
         m = Model(kind, beta_prior_sd, sigma_known, sigma_prior_sd, tau_prior_sd,
-                  _ptr(self._group), n_groups)
+                  _ptr(self._group), n_groups, _ptr(self._active))
         o = Options()
         L.pcv_default_options(ct.byref(o))
         o.seed = seed
@@ -233,7 +235,7 @@ class PCV:
     def from_workload(cls, w, **kw):
         args = dict(beta_prior_sd=w.beta_prior_sd, sigma_known=w.sigma_known,
                     sigma_prior_sd=w.sigma_prior_sd, tau_prior_sd=w.tau_prior_sd,
-                    group=w.group, n_groups=w.n_groups, seed=w.seed,
+                    group=w.group, n_groups=w.n_groups, seed=w.seed, active=w.active,
                     leapfrog_steps=w.leapfrog_steps, step_size=w.step_size,
                     batch_size=w.batch_size, hv_buffer=w.hv_buffer)
         args.update(kw)
@@ -314,6 +316,16 @@ class PCV:
         self._check(self._L.pcv_get_positions(self.h, _ptr(th), _ptr(lp), _ptr(sh)),
                     "pcv_get_positions")
         return th, lp, sh
+
+    def compare(self, other: "PCV"):
+        """This model (A) against `other` (B) on the same folds (eq. sel-cv,
+        norm-approx, mc-var)."""
+        dk = np.empty(self.K)
+        mk = np.empty(self.K)
+        out = np.empty(4)
+        self._check(self._L.pcv_compare(self.h, other.h, _ptr(dk), _ptr(mk), _ptr(out)), "pcv_compare")
+        return {"delta_k": dk, "mcse_k": mk, "delta": out[0], "se": out[1], "mcse": out[2],
+                "prob": out[3]}
 
     def rhat_shuffle(self, n_blocks: int = 5, n_reps: int = 500, per_fold: bool = False):
         """R-hat_max benchmark replicates (Section 4.2): [n_reps] maxima over

@@ -35,7 +35,7 @@ WORKLOADS = {
 }
 
 
-def run(w, precision: str, draws: int, fd_warmup: int, fold_warmup: int, seed: int):
+def run(w, precision: str, draws: int, fd_warmup: int, fold_warmup: int, seed: int, keep=False):
     import torch
     from . import pcv as P
     t = {}
@@ -61,7 +61,8 @@ def run(w, precision: str, draws: int, fd_warmup: int, fold_warmup: int, seed: i
     eps, _ = pc.adaptation()
     acc = pc.accept_rate()
     C = pc.C
-    pc.close()
+    if not keep:
+        pc.close()
     t["total_s"] = sum(t.values())
     evals = float(C) * w.leapfrog_steps * (fold_warmup + draws)
     out = {
@@ -81,6 +82,8 @@ def run(w, precision: str, draws: int, fd_warmup: int, fold_warmup: int, seed: i
         "fold_grad_evals_per_s": evals / (t["warmup_s"] + t["sample_s"]),
         "wall": t,
     }
+    if keep:
+        return out, sc, dg, pc
     return out, sc, dg
 
 
@@ -96,6 +99,9 @@ def main():
                     help="draws of the comparison run (default: the same)")
     ap.add_argument("--compare-fold-warmup", type=int, default=None)
     ap.add_argument("--seed", type=int, default=None)
+    ap.add_argument("--drop-covariates", default=None,
+                    help="comma-separated covariate indices: also run model B without them "
+                         "(Appendix B's selection mask) and report the pairwise comparison")
     args = ap.parse_args()
     from .build import build
     build()
@@ -104,7 +110,11 @@ def main():
     fdw = args.fd_warmup or w.n_fulldata_warmup
     fow = args.fold_warmup or w.n_fold_warmup
     seed = w.seed if args.seed is None else args.seed
-    a, sca, dga = run(w, args.precision, draws, fdw, fow, seed)
+    sel = args.drop_covariates is not None
+    if sel:
+        a, sca, dga, pa = run(w, args.precision, draws, fdw, fow, seed, keep=True)
+    else:
+        a, sca, dga = run(w, args.precision, draws, fdw, fow, seed)
     line = {"workload": w.name, "N": w.N, "p": w.p, "K": w.K, "L": w.chains_per_fold,
             "leapfrog_steps": w.leapfrog_steps, "draws": draws, "fd_warmup": fdw,
             "fold_warmup": fow, "batch_size": w.batch_size, "run": a}
@@ -123,6 +133,17 @@ def main():
                            "z_acov_abs_max": float(np.max(np.abs(zi))),
                            "folds_abs_z_acov_gt_3": int(np.sum(np.abs(zi) > 3)),
                            "speedup_grad_evals": a["fold_grad_evals_per_s"] / b["fold_grad_evals_per_s"]}
+    if sel:
+        import dataclasses
+        act = np.ones(w.p, np.int32)
+        act[[int(v) for v in args.drop_covariates.split(",")]] = 0
+        b_run, _, _, pb = run(dataclasses.replace(w, active=act), args.precision, draws, fdw, fow, seed, keep=True)
+        c = pa.compare(pb)
+        line["selection"] = {"dropped": args.drop_covariates, "model_b": b_run,
+                             "delta": c["delta"], "se": c["se"], "mcse": c["mcse"],
+                             "prob_a_better": c["prob"]}
+        pa.close()
+        pb.close()
     print(json.dumps(line), flush=True)
 
 
