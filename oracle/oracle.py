@@ -85,6 +85,10 @@ def _declare(L):
     L.orc_rhat_from_picks_series.restype = ct.c_int
     L.orc_pcv_rhat_shuffle.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _D]
     L.orc_pcv_rhat_shuffle.restype = ct.c_int
+    L.orc_pcv_enable_extra.argtypes = [ct.c_void_p, ct.c_int32]
+    L.orc_pcv_enable_extra.restype = ct.c_int
+    L.orc_pcv_extra_results.argtypes = [ct.c_void_p, _D, _D]
+    L.orc_pcv_extra_results.restype = ct.c_int
     L.orc_compare.argtypes = [ct.c_int32, _D, _D, _D, _D, _D, _D, _D]
     L.orc_compare.restype = ct.c_int
     L.orc_pcv_set_tuning.argtypes = [ct.c_void_p, ct.c_double, ct.c_double]
@@ -290,6 +294,16 @@ class OraclePCV:
         assert lib().orc_pcv_results(self.h, _dp(fo), _dp(to)) == 0
         return ({f: fo[:, i] for i, f in enumerate(FOLD_FIELDS)},
                 {f: to[i] for i, f in enumerate(TOTAL_FIELDS)})
+
+    def enable_extra_scores(self, flags: int = 3):
+        """Accumulate the Hyvarinen (1) and Dawid-Sebastiani (2) scores."""
+        assert lib().orc_pcv_enable_extra(self.h, flags) == 0
+
+    def extra_scores(self):
+        hs = np.empty(self.K)
+        dss = np.empty(self.K)
+        assert lib().orc_pcv_extra_results(self.h, _dp(hs), _dp(dss)) == 0
+        return hs, dss
 
     def rhat_shuffle(self, D: int, R: int):
         out = np.empty(R)

@@ -913,6 +913,13 @@ typedef struct {
      * current-batch sum, and a Welford of the batch means, C x d each */
     double *th_sum, *th_bsum, *th_bmean, *th_bM2;
     int64_t th_a;
+    /* Hyvarinen and Dawid-Sebastiani scores (Algorithms A3, A4), Gaussian
+     * models with conditionally independent rows: per chain, sums over draws
+     * of xi1 = sum_i [d2 log p / dy_i^2 + (d log p / dy_i)^2] and of
+     * xi2_i = d log p / dy_i (test row i), and of a predictive draw ytil and
+     * its outer product (plain sums: the oracle favours the obvious form) */
+    int32_t extra, T;         /* extra: 1 HS, 2 DSS; T: largest test set */
+    double *hs1, *hs2, *dsum, *douter;   /* C, C x T, C x T, C x T x T */
 } orc_pcv;
 
 orc_pcv *orc_pcv_create(const orc_problem *P, int32_t L, uint64_t seed, int32_t Lf, double eps,
@@ -956,7 +963,139 @@ void orc_pcv_destroy(orc_pcv *S)
     free(S->acc); free(S->chains); free(S->thbuf); free(S->grbuf);
     free(S->minv); free(S->draws); free(S->pool);
     free(S->th_sum); free(S->th_bsum); free(S->th_bmean); free(S->th_bM2);
+    free(S->hs1); free(S->hs2); free(S->dsum); free(S->douter);
     free(S);
+}
+
+/* test rows of fold k in the problem's row order */
+static int64_t fold_test_rows(const orc_problem *P, int32_t k, int64_t *rows)
+{
+    int64_t m = 0;
+    for (int64_t n = 0; n < P->N; ++n) if (P->fold[n] == k) rows[m++] = n;
+    return m;
+}
+
+int orc_pcv_enable_extra(orc_pcv *S, int32_t flags)
+{
+    const orc_problem *P = &S->P;
+    if (P->kind != ORC_GAUSS && P->kind != ORC_AR) return -1;
+    int64_t *rows = (int64_t *)malloc(sizeof(int64_t) * (size_t)P->N);
+    int32_t T = 0;
+    for (int32_t k = 0; k < P->K; ++k) {
+        int64_t m = fold_test_rows(P, k, rows);
+        if (m > T) T = (int32_t)m;
+    }
+    free(rows);
+    S->extra = flags;
+    S->T = T;
+    S->hs1 = (double *)calloc((size_t)S->C, sizeof(double));
+    S->hs2 = (double *)calloc((size_t)S->C * T, sizeof(double));
+    S->dsum = (double *)calloc((size_t)S->C * T, sizeof(double));
+    S->douter = (double *)calloc((size_t)S->C * T * T, sizeof(double));
+    return 0;
+}
+
+/* one sampling draw of chain c (fold k) at iteration it */
+static void extra_push(orc_pcv *S, int32_t c, int32_t k, uint32_t it, const double *theta, int64_t *rows,
+                       double *ytil)
+{
+    const orc_problem *P = &S->P;
+    const int64_t m = fold_test_rows(P, k, rows);
+    const double sigma = (P->kind == ORC_GAUSS && P->sigma_known > 0) ? P->sigma_known : exp(theta[P->p]);
+    const double s2 = sigma * sigma;
+    orc_normals(S->seed, (uint32_t)c, it, 5u, (int32_t)m, ytil);     /* stream 5: predictive draws */
+    double xi1 = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+        const int64_t n = rows[i];
+        double mu = 0.0;
+        for (int32_t j = 0; j < P->p; ++j) mu += P->X[n * P->p + j] * theta[j];
+        const double d1 = -(P->y[n] - mu) / s2;        /* d log N(y | mu, s2) / dy */
+        const double d2 = -1.0 / s2;                     /* d2 log N / dy2 */
+        xi1 += d2 + d1 * d1;
+        S->hs2[(size_t)c * S->T + i] += d1;
+        ytil[i] = mu + sigma * ytil[i];                  /* a draw from p(y_i | theta) */
+    }
+    S->hs1[c] += xi1;
+    for (int64_t i = 0; i < m; ++i) {
+        S->dsum[(size_t)c * S->T + i] += ytil[i];
+        for (int64_t j2 = 0; j2 < m; ++j2)
+            S->douter[((size_t)c * S->T + i) * S->T + j2] += ytil[i] * ytil[j2];
+    }
+}
+
+/* log det and quadratic form (y - mu)' A^{-1} (y - mu) of an m x m SPD matrix
+ * by a dense Cholesky factorisation (A is overwritten) */
+static void chol_logdet_quad(double *A, int64_t m, const double *r, double *logdet, double *quad)
+{
+    double *w = (double *)malloc(sizeof(double) * (size_t)m);
+    *logdet = 0.0;
+    for (int64_t j = 0; j < m; ++j) {
+        double v = A[j * m + j];
+        for (int64_t q = 0; q < j; ++q) v -= A[j * m + q] * A[j * m + q];
+        const double ljj = sqrt(v);
+        A[j * m + j] = ljj;
+        *logdet += 2.0 * log(ljj);
+        for (int64_t i = j + 1; i < m; ++i) {
+            double u = A[i * m + j];
+            for (int64_t q = 0; q < j; ++q) u -= A[i * m + q] * A[j * m + q];
+            A[i * m + j] = u / ljj;
+        }
+    }
+    *quad = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+        double u = r[i];
+        for (int64_t q = 0; q < i; ++q) u -= A[i * m + q] * w[q];
+        w[i] = u / A[i * m + i];
+        *quad += w[i] * w[i];
+    }
+    free(w);
+}
+
+/*
+ * Per fold, from the L chains' sums over n draws each:
+ *   HS_k  = sum_i [ -2 E(d2_i + d1_i^2) + (E d1_i)^2 ]   (Algorithm A3, per
+ *           test observation; positively oriented as in the score table)
+ *   DSS_k = -log|S| - (y - m)' S^{-1} (y - m), m and S the sample mean and
+ *           covariance (LN - 1 dof) of the predictive draws (Algorithm A4)
+ */
+int orc_pcv_extra_results(orc_pcv *S, double *hs, double *dss)
+{
+    if (!S->extra || S->n_sampled < 2) return -1;
+    const orc_problem *P = &S->P;
+    const int32_t L = S->L, T = S->T;
+    const double n = (double)S->n_sampled * L;
+    int64_t *rows = (int64_t *)malloc(sizeof(int64_t) * (size_t)P->N);
+    double *mu = (double *)malloc(sizeof(double) * (size_t)T), *A = (double *)malloc(sizeof(double) * (size_t)T * T);
+    double *r = (double *)malloc(sizeof(double) * (size_t)T);
+    for (int32_t k = 0; k < P->K; ++k) {
+        const int64_t m = fold_test_rows(P, k, rows);
+        double e1 = 0.0;
+        for (int32_t l = 0; l < L; ++l) e1 += S->hs1[k * L + l];
+        double h = -2.0 * e1 / n;
+        for (int64_t i = 0; i < m; ++i) {
+            double e2 = 0.0;
+            for (int32_t l = 0; l < L; ++l) e2 += S->hs2[(size_t)(k * L + l) * T + i];
+            h += (e2 / n) * (e2 / n);
+        }
+        hs[k] = h;
+        for (int64_t i = 0; i < m; ++i) {
+            double sm = 0.0;
+            for (int32_t l = 0; l < L; ++l) sm += S->dsum[(size_t)(k * L + l) * T + i];
+            mu[i] = sm / n;
+        }
+        for (int64_t i = 0; i < m; ++i)
+            for (int64_t j2 = 0; j2 < m; ++j2) {
+                double so = 0.0;
+                for (int32_t l = 0; l < L; ++l) so += S->douter[((size_t)(k * L + l) * T + i) * T + j2];
+                A[i * m + j2] = (so - n * mu[i] * mu[j2]) / (n - 1.0);
+            }
+        for (int64_t i = 0; i < m; ++i) r[i] = P->y[rows[i]] - mu[i];
+        double ld, q;
+        chol_logdet_quad(A, m, r, &ld, &q);
+        dss[k] = -ld - q;
+    }
+    free(rows); free(mu); free(A); free(r);
+    return 0;
 }
 
 static void chain_refresh(const orc_problem *P, int32_t k, orc_chain *c)
@@ -1161,6 +1300,8 @@ int orc_pcv_sample(orc_pcv *S, int32_t n_draws)
     for (int32_t c = 0; c < S->C; ++c) {
         int32_t k = c / S->L;
         double *work = (double *)malloc(sizeof(double) * 3 * (size_t)d);
+        int64_t *xrows = S->extra ? (int64_t *)malloc(sizeof(int64_t) * (size_t)P->N) : NULL;
+        double *xy = S->extra ? (double *)malloc(sizeof(double) * ((size_t)S->T + 4)) : NULL;
         for (int32_t i = 0; i < n_draws; ++i) {
             int acc, div;
             const uint32_t it = S->iter + (uint32_t)i;
@@ -1169,6 +1310,7 @@ int orc_pcv_sample(orc_pcv *S, int32_t n_draws)
             S->acc[c].divergences += div;
             S->acc[c].accepts += acc;
             accum_push(&S->acc[c], S->chains[c].shat, S->b);
+            if (S->extra) extra_push(S, c, k, S->iter + (uint32_t)i, S->chains[c].theta, xrows, xy);
             {
                 double *ts = S->th_sum + (size_t)c * d, *tb = S->th_bsum + (size_t)c * d;
                 for (int32_t j = 0; j < d; ++j) { ts[j] += S->chains[c].theta[j]; tb[j] += S->chains[c].theta[j]; }
@@ -1185,7 +1327,7 @@ int orc_pcv_sample(orc_pcv *S, int32_t n_draws)
             }
             if (S->store_draws) S->draws[(size_t)c * S->draw_cap + S->n_sampled + i] = S->chains[c].shat;
         }
-        free(work);
+        free(work); free(xrows); free(xy);
     }
     S->iter += (uint32_t)n_draws;
     S->n_sampled += n_draws;
