@@ -139,6 +139,11 @@ typedef struct {
      * the FP32 partial sums, so results are bit-reproducible only with the
      * same choice; 0 keeps the fixed rule. */
     int32_t autotune;
+    /* bit 0: accumulate the Hyvarinen score (Algorithm A3), bit 1: the
+     * Dawid-Sebastiani score (Algorithm A4), read with pcv_scores_extra.
+     * Gaussian linear and AR models only (rows conditionally independent
+     * given theta); the DSS needs test sets of at most 64 rows. Default 0. */
+    int32_t extra_scores;
 } pcv_options;
 
 /* Fill *opt with the defaults listed above (seed 0, L_f 16, adapted step). */
@@ -276,6 +281,21 @@ pcv_status pcv_get_draws(pcv_ctx *ctx, double *shat, int32_t *n_stored);
 
 /* Mean acceptance rate per fold over sampling (host, K). */
 pcv_status pcv_accept_rate(pcv_ctx *ctx, double *accept_k);
+
+/*
+ * Hyvarinen and Dawid-Sebastiani scores per fold and in total (positively
+ * oriented), from the accumulators enabled by pcv_options.extra_scores:
+ *   HS_k  = sum_i [-2 E(d2 log p/dy_i^2 + (d log p/dy_i)^2) + (E d log p/dy_i)^2]
+ *           over the fold's test rows i, expectations over every fold-chain
+ *           draw (Algorithm A3, per test observation);
+ *   DSS_k = -log|S_k| - (y - m_k)' S_k^{-1} (y - m_k), m_k and S_k the mean and
+ *           covariance of one predictive draw per chain and iteration
+ *           (Algorithm A4; draws from Philox stream 5).
+ * Host outputs: hs_k, dss_k (K each, or NULL for a score not enabled),
+ * hs_total, dss_total. PCV_E_UNSUPPORTED if neither score was enabled,
+ * PCV_E_BAD_STATE before pcv_sample.
+ */
+pcv_status pcv_scores_extra(pcv_ctx *ctx, double *hs_k, double *dss_k, double *hs_total, double *dss_total);
 
 /*
  * Pairwise model selection (eq. sel-cv, eq. norm-approx, eq. mc-var) between

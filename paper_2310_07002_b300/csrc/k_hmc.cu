@@ -668,3 +668,115 @@ __global__ void k_compare(const double *fo_a, const double *fo_b, int K, double 
   }
 }
 }  // namespace pcv
+
+namespace pcv {
+// ---------------------------------------------------------------------------
+// Hyvarinen (Algorithm A3) and Dawid-Sebastiani (Algorithm A4) scores for
+// the Gaussian models with conditionally independent rows.  One warp per
+// chain after the accept of a sampling iteration: for the fold's test rows,
+// mu_i = x_i . beta, d1_i = -(y_i - mu_i) / sigma^2, d2 = -1 / sigma^2 and a
+// predictive draw ytil_i = mu_i + sigma z_i (z: Philox stream ST_PRED,
+// element i of (chain, iteration) as for the momenta).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_extra_push(Problem pb, GradArgs a, Extra E, const unsigned int *iter,
+                                                    unsigned long long seed) {
+  extern __shared__ double ysh[];                    // [8 warps][T]
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int c = blockIdx.x * 8 + wib;
+  if (c >= a.C) return;
+  const unsigned it = *iter - 1u;                     // the iteration just accepted
+  const FoldDesc fd = pb.folds[fold_of_chain(a, c)];
+  const int m = fd.test_hi - fd.test_lo;
+  const float *th = a.theta + (size_t)c * a.ld_theta;
+  const double sigma = pb.variant == MV_GAUSS_KNOWN ? (double)pb.sigma_known : exp((double)th[pb.p]);
+  const double s2 = sigma * sigma;
+  double *yt = ysh + (size_t)wib * E.T;
+  double xi1 = 0.0;
+  for (int i = lane; i < m; i += 32) {
+    const int n = fd.test_lo + i;
+    double mu = 0.0;
+    for (int j = 0; j < pb.p; ++j) mu += (double)pb.X[(size_t)n * pb.p_pad + j] * (double)th[j];
+    const double d1 = -((double)pb.y[n] - mu) / s2;
+    xi1 += -1.0 / s2 + d1 * d1;
+    if (E.flags & 1) E.hs2[(size_t)c * E.T + i] += d1;
+    // element i of the standard normals of (chain, iteration): Philox block
+    // i / 4, Box-Muller pair (words 0, 1) or (2, 3)
+    const uint4 w = philox_at(seed, (uint32_t)(i >> 2), (uint32_t)c, it, ST_PRED);
+    const float2 z2 = (i & 2) ? box_muller(w.z, w.w) : box_muller(w.x, w.y);
+    const double z = (i & 1) ? (double)z2.y : (double)z2.x;
+    yt[i] = mu + sigma * z;
+  }
+  xi1 = warp_sum_d(xi1);
+  if ((E.flags & 1) && lane == 0) E.hs1[c] += xi1;
+  __syncwarp();
+  if (E.flags & 2) {
+    for (int i = lane; i < m; i += 32) E.dsum[(size_t)c * E.T + i] += yt[i];
+    for (int q = lane; q < m * m; q += 32) {
+      const int i = q / m, j = q - i * m;
+      E.douter[((size_t)c * E.T + i) * E.T + j] += yt[i] * yt[j];
+    }
+  }
+}
+
+// per fold (one block each): HS_k = sum_i [-2 E(d2 + d1^2)... as the pooled
+// means over L chains x n draws; DSS_k = -log|S| - (y - m)' S^-1 (y - m) by
+// a Cholesky factorisation of the pooled predictive covariance (thread 0)
+__global__ void k_extra_finalize(Problem pb, Extra E, int K, int L, double n, double *hs, double *dss) {
+  extern __shared__ double sm[];                     // A [T x T], mu [T], w [T]
+  const int k = blockIdx.x;
+  if (k >= K) return;
+  const FoldDesc fd = pb.folds[k];
+  const int m = fd.test_hi - fd.test_lo, T = E.T;
+  double *A = sm, *mu = sm + (size_t)T * T, *w = mu + T;
+  if (E.flags & 2) {
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      double sum = 0.0;
+      for (int l = 0; l < L; ++l) sum += E.dsum[(size_t)(k * L + l) * T + i];
+      mu[i] = sum / n;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < m * m; q += blockDim.x) {
+      const int i = q / m, j = q - i * m;
+      double so = 0.0;
+      for (int l = 0; l < L; ++l) so += E.douter[((size_t)(k * L + l) * T + i) * T + j];
+      A[i * m + j] = (so - n * mu[i] * mu[j]) / (n - 1.0);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  if (E.flags & 1) {
+    double e1 = 0.0;
+    for (int l = 0; l < L; ++l) e1 += E.hs1[k * L + l];
+    double h = -2.0 * e1 / n;
+    for (int i = 0; i < m; ++i) {
+      double e2 = 0.0;
+      for (int l = 0; l < L; ++l) e2 += E.hs2[(size_t)(k * L + l) * T + i];
+      h += (e2 / n) * (e2 / n);
+    }
+    hs[k] = h;
+  }
+  if (E.flags & 2) {
+    double ld = 0.0;
+    for (int j = 0; j < m; ++j) {
+      double v = A[j * m + j];
+      for (int q = 0; q < j; ++q) v -= A[j * m + q] * A[j * m + q];
+      const double ljj = sqrt(v);
+      A[j * m + j] = ljj;
+      ld += 2.0 * log(ljj);
+      for (int i = j + 1; i < m; ++i) {
+        double u = A[i * m + j];
+        for (int q = 0; q < j; ++q) u -= A[i * m + q] * A[j * m + q];
+        A[i * m + j] = u / ljj;
+      }
+    }
+    double quad = 0.0;
+    for (int i = 0; i < m; ++i) {
+      double u = (double)pb.y[fd.test_lo + i] - mu[i];
+      for (int q = 0; q < i; ++q) u -= A[i * m + q] * w[q];
+      w[i] = u / A[i * m + i];
+      quad += w[i] * w[i];
+    }
+    dss[k] = -ld - quad;
+  }
+}
+}  // namespace pcv

@@ -105,6 +105,9 @@ struct pcv_ctx {
   std::map<int, int> tuned_splits;
   std::map<std::pair<int, int>, int> tuned_ns;
   std::vector<std::string> tune_log;
+  // Hyvarinen / Dawid-Sebastiani accumulators
+  Extra extra{};
+  double *extra_out = nullptr;
   // covariate-selection mask (d_pad floats 1 / 0; nullptr: every covariate)
   float *active_d = nullptr;
   std::vector<float> active_h;
@@ -466,6 +469,11 @@ pcv_status launch_iteration(pcv_ctx *x, ChainBufs &cb, bool fd, bool accumulate)
   aa.accept_prob = cb.accept_prob;
   k_accept<<<(cb.C + 7) / 8, 256, 0, x->stream>>>(aa);
   CK(cudaGetLastError());
+  if (accumulate && x->extra.flags) {
+    k_extra_push<<<(cb.C + 7) / 8, 256, sizeof(double) * 8 * x->extra.T, x->stream>>>(
+        x->pb, grad_args(x, cb, false), x->extra, &x->st->iter, x->opt.seed);
+    CK(cudaGetLastError());
+  }
   if (fd) {
     FdAdaptArgs fa{};
     fa.st = x->st;
@@ -621,6 +629,7 @@ void pcv_default_options(pcv_options *o) {
   o->trajectory_length = -1.0;
   o->step_jitter = -1.0;
   o->autotune = 1;
+  o->extra_scores = 0;
 }
 
 pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
@@ -883,6 +892,23 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
   if ((s = alloc_chains(x, x->fold_cb, x->C, x->L, 0)) != PCV_OK) return bail(s, x->err);
   if ((s = alloc_chains(x, x->fd_cb, kNumFdChains, kNumFdChains, K)) != PCV_OK) return bail(s, x->err);
   if ((s = alloc_accum(x)) != PCV_OK) return bail(s, x->err);
+  if (opt->extra_scores) {
+    // Hyvarinen / Dawid-Sebastiani accumulators (Gaussian models whose rows
+    // are conditionally independent given theta)
+    if (opt->extra_scores & ~3) return bail(PCV_E_INVALID_ARG, "extra_scores: bits 0 (HS) and 1 (DSS) only");
+    if (x->variant != MV_GAUSS_KNOWN && x->variant != MV_GAUSS_LOGSIG)
+      return bail(PCV_E_UNSUPPORTED, "HS / DSS need a Gaussian linear or AR model");
+    int T = 0;
+    for (int k = 0; k < K; ++k) T = std::max(T, fds[k].test_hi - fds[k].test_lo);
+    if ((opt->extra_scores & 2) && T > 64) return bail(PCV_E_UNSUPPORTED, "DSS needs test sets of at most 64 rows");
+    Extra &E = x->extra;
+    E.flags = opt->extra_scores;
+    E.T = T;
+    const size_t C = (size_t)x->C;
+    if (!dalloc_n(x, &E.hs1, C) || !dalloc_n(x, &E.hs2, C * T) || !dalloc_n(x, &E.dsum, C * T) ||
+        !dalloc_n(x, &E.douter, C * T * T))
+      return bail(PCV_E_OOM, "accumulator allocation failed");
+  }
   if (x->tc) {
     if ((s = ensure_ws_tc(x, x->C)) != PCV_OK) return bail(s, x->err);
   } else {
@@ -1329,6 +1355,13 @@ std::vector<Seg> ckpt_segments(pcv_ctx *x) {
   v.push_back({A.div, sizeof(long long) * C});
   v.push_back({A.acc, sizeof(long long) * C});
   if (A.draw_cap > 0) v.push_back({A.draws, sizeof(double) * C * A.draw_cap});
+  if (x->extra.flags) {
+    const size_t T = (size_t)x->extra.T;
+    v.push_back({x->extra.hs1, sizeof(double) * C});
+    v.push_back({x->extra.hs2, sizeof(double) * C * T});
+    v.push_back({x->extra.dsum, sizeof(double) * C * T});
+    v.push_back({x->extra.douter, sizeof(double) * C * T * T});
+  }
   return v;
 }
 
@@ -1415,6 +1448,31 @@ pcv_status pcv_checkpoint_load(pcv_ctx *x, const void *buf, int64_t bytes) {
   if (s != PCV_OK) return s;
   CK(cudaStreamSynchronize(x->stream));
   leave(x);
+  return PCV_OK;
+}
+
+pcv_status pcv_scores_extra(pcv_ctx *x, double *hs_k, double *dss_k, double *hs_total, double *dss_total) {
+  if (!x) return PCV_E_INVALID_ARG;
+  if (!x->extra.flags) return fail(x, PCV_E_UNSUPPORTED, "extra_scores was not enabled");
+  if (x->state != ST_SAMPLED || x->n_sampled < 2) return fail(x, PCV_E_BAD_STATE, "pcv_scores_extra before pcv_sample");
+  const int K = x->K, T = x->extra.T;
+  if (!x->extra_out && !dalloc_n(x, &x->extra_out, (size_t)2 * K)) return fail(x, PCV_E_OOM, "allocation failed");
+  enter(x);
+  const size_t smem = sizeof(double) * ((size_t)T * T + 2 * (size_t)T);
+  k_extra_finalize<<<K, 128, smem, x->stream>>>(x->pb, x->extra, K, x->L, (double)x->L * (double)x->n_sampled,
+                                              x->extra_out, x->extra_out + K);
+  CK(cudaGetLastError());
+  std::vector<double> h((size_t)2 * K);
+  CK(cudaMemcpyAsync(h.data(), x->extra_out, h.size() * sizeof(double), cudaMemcpyDeviceToHost, x->stream));
+  CK(cudaStreamSynchronize(x->stream));
+  leave(x);
+  double th = 0.0, td = 0.0;
+  for (int k = 0; k < K; ++k) { th += h[k]; td += h[K + k]; }
+  const bool has_hs = x->extra.flags & 1, has_dss = x->extra.flags & 2;
+  if (hs_k && has_hs) std::memcpy(hs_k, h.data(), sizeof(double) * K);
+  if (dss_k && has_dss) std::memcpy(dss_k, h.data() + K, sizeof(double) * K);
+  if (hs_total) *hs_total = has_hs ? th : NAN;
+  if (dss_total) *dss_total = has_dss ? td : NAN;
   return PCV_OK;
 }
 

@@ -17,7 +17,7 @@ enum ModelVariant : int {
 
 // Philox stream tags (the counter's last word)
 enum Stream : uint32_t {
-  ST_MOM = 0, ST_ACC = 1, ST_INIT = 2, ST_JIT = 3, ST_SHUF = 4, ST_FD_MOM = 16, ST_FD_ACC = 17, ST_FD_INIT = 18
+  ST_MOM = 0, ST_ACC = 1, ST_INIT = 2, ST_JIT = 3, ST_SHUF = 4, ST_PRED = 5, ST_FD_MOM = 16, ST_FD_ACC = 17, ST_FD_INIT = 18
 };
 
 // Row ranges of one fold in the library's sorted row order (the Appendix B
@@ -276,6 +276,16 @@ __global__ void k_init_from_pool(int C, int d, int ld, unsigned long long seed, 
                                  int n_pool, float *theta);
 __global__ void k_shadow(int C, int d, int ld, const float *theta, const float *theta_ref,
                          __nv_bfloat16 *hi, __nv_bfloat16 *lo, int ld_shadow);
+// Hyvarinen / Dawid-Sebastiani accumulators (Algorithms A3, A4): per chain
+// sums over draws of xi1 = sum_i [d2 + d1^2], of d1_i, of a predictive draw
+// ytil_i and of ytil ytil' (T = the largest test set)
+struct Extra {
+  int flags, T;
+  double *hs1, *hs2, *dsum, *douter;   // C, C x T, C x T, C x T x T
+};
+__global__ void k_extra_push(Problem pb, GradArgs a, Extra E, const unsigned int *iter,
+                             unsigned long long seed);
+__global__ void k_extra_finalize(Problem pb, Extra E, int K, int L, double n, double *hs, double *dss);
 __global__ void k_block_stats(Accum A, int a, int D, double *blk);
 __global__ void k_mask_positions(int C, int d, int ld, const float *active, float *theta);
 __global__ void k_compare(const double *fo_a, const double *fo_b, int K, double *out);

@@ -54,7 +54,8 @@ class Options(ct.Structure):
                 ("init_scale", ct.c_double), ("use_graphs", ct.c_int32),
                 ("device_alloc", ALLOC_FN), ("device_free", FREE_FN),
                 ("alloc_user", ct.c_void_p), ("trajectory_length", ct.c_double),
-                ("step_jitter", ct.c_double), ("autotune", ct.c_int32)]
+                ("step_jitter", ct.c_double), ("autotune", ct.c_int32),
+                ("extra_scores", ct.c_int32)]
 
 
 _lib = None
@@ -90,6 +91,7 @@ def load():
         "pcv_tuning_info": (i32, [vp, ct.c_char_p, i32]),
         "pcv_rhat_shuffle": (i32, [vp, i32, i32, vp, vp]),
         "pcv_compare": (i32, [vp, vp, vp, vp, vp]),
+        "pcv_scores_extra": (i32, [vp, vp, vp, vp, vp]),
         "pcv_checkpoint_size": (i32, [vp, ct.POINTER(i64)]),
         "pcv_checkpoint_save": (i32, [vp, vp, i64]),
         "pcv_checkpoint_load": (i32, [vp, vp, i64]),
@@ -124,7 +126,7 @@ def exported_symbols():
             "pcv_get_draws", "pcv_accept_rate", "pcv_last_sample_ms",
             "pcv_time_leapfrog_kernel", "pcv_log_density_noalloc", "pcv_tuning_info",
             "pcv_checkpoint_size", "pcv_checkpoint_save", "pcv_checkpoint_load",
-            "pcv_rhat_shuffle", "pcv_compare"]
+            "pcv_rhat_shuffle", "pcv_compare", "pcv_scores_extra"]
 
 
 def _ptr(a: Optional[np.ndarray]):
@@ -177,7 +179,7 @@ class PCV:
                  n_fulldata_draws: int = 250, init_scale: float = 1.0,
                  use_graphs: bool = True, torch_allocator: bool = True,
                  trajectory_length: float = -1.0, step_jitter: float = -1.0,
-                 autotune: bool = True, active=None):
+                 autotune: bool = True, active=None, extra_scores: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("PCV needs a CUDA device (sm_103a); none is available")
@@ -215,6 +217,7 @@ class PCV:
         o.trajectory_length = trajectory_length
         o.step_jitter = step_jitter
         o.autotune = 1 if autotune else 0
+        o.extra_scores = extra_scores
         self._alloc = None
         if torch_allocator:
             self._alloc = _TorchAllocator(torch.cuda.current_device())
@@ -316,6 +319,16 @@ class PCV:
         self._check(self._L.pcv_get_positions(self.h, _ptr(th), _ptr(lp), _ptr(sh)),
                     "pcv_get_positions")
         return th, lp, sh
+
+    def scores_extra(self):
+        """Hyvarinen and Dawid-Sebastiani scores (Algorithms A3, A4): per
+        fold arrays and totals (NaN for a score that was not enabled)."""
+        hs = np.full(self.K, np.nan)
+        dss = np.full(self.K, np.nan)
+        th, td = ct.c_double(), ct.c_double()
+        self._check(self._L.pcv_scores_extra(self.h, _ptr(hs), _ptr(dss), ct.addressof(th),
+                                             ct.addressof(td)), "pcv_scores_extra")
+        return {"hs": hs, "dss": dss, "hs_total": th.value, "dss_total": td.value}
 
     def compare(self, other: "PCV"):
         """This model (A) against `other` (B) on the same folds (eq. sel-cv,
