@@ -144,6 +144,12 @@ typedef struct {
      * Gaussian linear and AR models only (rows conditionally independent
      * given theta); the DSS needs test sets of at most 64 rows. Default 0. */
     int32_t extra_scores;
+    /* Global id of this context's fold 0 when the folds of one problem are
+     * split over several contexts (one per GPU): the Philox counters of fold
+     * chain c use chain id first_fold * L + c and the shuffle benchmark fold
+     * id first_fold + k, so every fold draws the same random numbers however
+     * the folds are split. Default 0. */
+    int32_t first_fold;
 } pcv_options;
 
 /* Fill *opt with the defaults listed above (seed 0, L_f 16, adapted step). */

@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(256) k_begin(BeginArgs a) {
 #pragma unroll
       for (int e = 0; e < 4; ++e) z[e] = 0.0f;
     } else {
-      const uint4 w = philox_at(a.seed, (uint32_t)q, (uint32_t)c, it, a.stream);
+      const uint4 w = philox_at(a.seed, (uint32_t)q, (uint32_t)(a.chain_base + c), it, a.stream);
       const float2 p0 = box_muller(w.x, w.y), p1 = box_muller(w.z, w.w);
       z[0] = p0.x; z[1] = p0.y; z[2] = p1.x; z[3] = p1.y;
     }
@@ -88,11 +88,11 @@ __global__ void __launch_bounds__(256) k_normals(int C, int d, int ld, unsigned 
 // fold chains start from full-data draws chosen uniformly with replacement:
 // index = floor(w0 * n_pool / 2^32) from Philox stream ST_INIT (Algorithm 1)
 __global__ void k_init_from_pool(int C, int d, int ld, unsigned long long seed, const float *pool,
-                                 int n_pool, float *theta) {
+                                 int n_pool, float *theta, int chain_base) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)C * d) return;
   const int c = (int)(t / d), j = (int)(t - (long long)c * d);
-  const uint4 w = philox_at(seed, 0u, (uint32_t)c, 0u, ST_INIT);
+  const uint4 w = philox_at(seed, 0u, (uint32_t)(chain_base + c), 0u, ST_INIT);
   const unsigned idx = (unsigned)(((unsigned long long)w.x * (unsigned long long)n_pool) >> 32);
   theta[(size_t)c * ld + j] = pool[(size_t)idx * ld + j];
 }
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(256) k_accept(AcceptArgs a) {
     kin = warp_sum_d(kin);
     const double H1 = -a.logp_p[c] + 0.5 * kin;
     const double dH = H1 - a.H0[c];
-    const uint4 w = philox_at(a.seed, 0u, (uint32_t)c, it, a.stream);
+    const uint4 w = philox_at(a.seed, 0u, (uint32_t)(a.chain_base + c), it, a.stream);
     const double logu = log(unit_from_word(w.x));
     const bool finite = isfinite(H1) && isfinite(dH);
     const bool acc = finite && (logu < -dH);
@@ -594,7 +594,7 @@ __global__ void k_block_stats(Accum A, int a, int D, double *blk) {
 // l' = floor(w L / 2^32); out_max[r] = max over folds (bit pattern of a
 // non-negative double, so an integer max orders it), out_all[r K + k]
 __global__ void k_rhat_shuffle(const double *blk, int K, int L, int D, int R, unsigned long long seed,
-                               unsigned long long *out_max, double *out_all) {
+                               unsigned long long *out_max, double *out_all, int first_fold) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)R * K) return;
   const int r = (int)(t / K), k = (int)(t - (long long)r * K);
@@ -604,7 +604,7 @@ __global__ void k_rhat_shuffle(const double *blk, int K, int L, int D, int R, un
     Welf w{0.0, 0.0, 0.0};
     for (int d = 0; d < D; ++d) {
       const int q = l * D + d;
-      const uint4 wd = philox_at(seed, (uint32_t)(q >> 2), (uint32_t)k, (uint32_t)r, ST_SHUF);
+      const uint4 wd = philox_at(seed, (uint32_t)(q >> 2), (uint32_t)(first_fold + k), (uint32_t)r, ST_SHUF);
       const uint32_t word = (q & 3) == 0 ? wd.x : (q & 3) == 1 ? wd.y : (q & 3) == 2 ? wd.z : wd.w;
       const int src = (int)(((unsigned long long)word * (unsigned long long)L) >> 32);
       const double *b3 = blk + 3 * ((size_t)(k * L + src) * D + d);
@@ -679,7 +679,7 @@ namespace pcv {
 // element i of (chain, iteration) as for the momenta).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_extra_push(Problem pb, GradArgs a, Extra E, const unsigned int *iter,
-                                                    unsigned long long seed) {
+                                                    unsigned long long seed, int chain_base) {
   extern __shared__ double ysh[];                    // [8 warps][T]
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int c = blockIdx.x * 8 + wib;
@@ -701,7 +701,7 @@ __global__ void __launch_bounds__(256) k_extra_push(Problem pb, GradArgs a, Extr
     if (E.flags & 1) E.hs2[(size_t)c * E.T + i] += d1;
     // element i of the standard normals of (chain, iteration): Philox block
     // i / 4, Box-Muller pair (words 0, 1) or (2, 3)
-    const uint4 w = philox_at(seed, (uint32_t)(i >> 2), (uint32_t)c, it, ST_PRED);
+    const uint4 w = philox_at(seed, (uint32_t)(i >> 2), (uint32_t)(chain_base + c), it, ST_PRED);
     const float2 z2 = (i & 2) ? box_muller(w.z, w.w) : box_muller(w.x, w.y);
     const double z = (i & 1) ? (double)z2.y : (double)z2.x;
     yt[i] = mu + sigma * z;

@@ -62,6 +62,7 @@ struct pcv_ctx {
   int kind = 0, variant = 0, p = 0, p_pad = 0, d = 0, d_pad = 0, K = 0, L = 0, C = 0, G = 0;
   int64_t N = 0;
   int h = 0, Lf = 16, b = 50, M = 64, max_batches = 1024, n_fd_draws = 250;
+  int chain_base = 0;             // Philox chain id of fold-chain 0 (first_fold * L)
   double traj_len = 0.0;          // effective trajectory length (0: no cap)
   float jitter = 0.0f;            // effective step-size jitter of the fold chains
   Problem pb{};
@@ -440,6 +441,7 @@ pcv_status launch_iteration(pcv_ctx *x, ChainBufs &cb, bool fd, bool accumulate)
   ba.eps = &x->st->eps; ba.minv = x->minv;
   ba.jitter = fd ? 0.0f : x->jitter;
   ba.eps_iter = &x->st->eps_iter;
+  ba.chain_base = fd ? 0 : x->chain_base;
   ba.r_given = nullptr;
   ba.shadow_hi = x->tc ? cb.shadow_hi : nullptr;
   ba.shadow_lo = x->tc ? cb.shadow_lo : nullptr;
@@ -458,6 +460,7 @@ pcv_status launch_iteration(pcv_ctx *x, ChainBufs &cb, bool fd, bool accumulate)
   aa.C = cb.C; aa.d = x->d; aa.ld = x->d_pad;
   aa.seed = x->opt.seed;
   aa.stream = fd ? ST_FD_ACC : ST_ACC;
+  aa.chain_base = fd ? 0 : x->chain_base;
   aa.st = x->st;
   aa.fd = fd ? 1 : 0;
   aa.theta = cb.theta; aa.grad = cb.grad; aa.logp = cb.logp; aa.shat = cb.shat;
@@ -471,7 +474,7 @@ pcv_status launch_iteration(pcv_ctx *x, ChainBufs &cb, bool fd, bool accumulate)
   CK(cudaGetLastError());
   if (accumulate && x->extra.flags) {
     k_extra_push<<<(cb.C + 7) / 8, 256, sizeof(double) * 8 * x->extra.T, x->stream>>>(
-        x->pb, grad_args(x, cb, false), x->extra, &x->st->iter, x->opt.seed);
+        x->pb, grad_args(x, cb, false), x->extra, &x->st->iter, x->opt.seed, x->chain_base);
     CK(cudaGetLastError());
   }
   if (fd) {
@@ -630,6 +633,7 @@ void pcv_default_options(pcv_options *o) {
   o->step_jitter = -1.0;
   o->autotune = 1;
   o->extra_scores = 0;
+  o->first_fold = 0;
 }
 
 pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
@@ -641,7 +645,7 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
   if (N < 1 || p < 1 || chains_per_fold < 2 || N > (int64_t)1 << 30) return PCV_E_INVALID_ARG;
   if (opt->leapfrog_steps < 1 || opt->batch_size < 1 || opt->hv_buffer < 0 ||
       opt->acov_max_lag < 0 || opt->max_batches < 1 || opt->n_fulldata_draws < 1 ||
-      !(opt->step_jitter < 1.0) || !std::isfinite(opt->trajectory_length))
+      !(opt->step_jitter < 1.0) || !std::isfinite(opt->trajectory_length) || opt->first_fold < 0)
     return PCV_E_INVALID_ARG;
   if (model->kind < PCV_GAUSS_LINEAR || model->kind > PCV_AR_GAUSS) return PCV_E_INVALID_ARG;
   if (!(model->beta_prior_sd > 0)) return PCV_E_INVALID_ARG;
@@ -718,6 +722,7 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
   if (K < 1) return bail(PCV_E_INVALID_ARG, "no folds");
   x->K = K;
   x->C = K * x->L;
+  x->chain_base = opt->first_fold * x->L;
   if (x->variant == MV_HIER)
     for (int64_t i = 0; i < N; ++i)
       if (model->group[i] < 0 || model->group[i] >= x->G) return bail(PCV_E_INVALID_ARG, "group id out of range");
@@ -965,7 +970,8 @@ pcv_status pcv_warmup(pcv_ctx *x, int32_t n_fd, int32_t n_wu) {
   {
     const long long T = (long long)x->C * x->d;
     k_init_from_pool<<<(unsigned)((T + 255) / 256), 256, 0, x->stream>>>(
-        x->C, x->d, x->d_pad, x->opt.seed, x->pool, x->n_fd_draws * kNumFdChains, x->fold_cb.theta);
+        x->C, x->d, x->d_pad, x->opt.seed, x->pool, x->n_fd_draws * kNumFdChains, x->fold_cb.theta,
+        x->chain_base);
     CK(cudaGetLastError());
   }
   s = refresh(x, x->fold_cb);
@@ -1196,7 +1202,7 @@ pcv_status pcv_trajectory(pcv_ctx *x, const float *theta0, const float *r0, int3
   ba.theta = cb.theta; ba.grad = cb.grad; ba.logp = cb.logp;
   ba.theta_p = cb.theta_p; ba.r = cb.r; ba.H0 = cb.H0;
   ba.eps = &x->st->eps; ba.minv = x->minv; ba.r_given = rstart;
-  ba.jitter = 0.0f; ba.eps_iter = &x->st->eps_iter;
+  ba.jitter = 0.0f; ba.eps_iter = &x->st->eps_iter; ba.chain_base = x->chain_base;
   ba.shadow_hi = x->tc ? cb.shadow_hi : nullptr;
   ba.shadow_lo = x->tc ? cb.shadow_lo : nullptr;
   ba.ld_shadow = x->KP;
@@ -1322,6 +1328,7 @@ struct CkptHeader {
   int64_t n_sampled;
   int32_t state, centered;
   int32_t tuned_splits, tuned_ns0, tuned_ns1;
+  int32_t first_fold;
   float jitter;
   double traj_len;
   int64_t payload;
@@ -1372,7 +1379,7 @@ CkptHeader ckpt_header(pcv_ctx *x) {
   h.precision = x->opt.precision; h.variant = x->variant; h.p = x->p; h.d = x->d; h.d_pad = x->d_pad;
   h.K = x->K; h.L = x->L; h.C = x->C; h.M = x->M; h.max_batches = x->max_batches; h.b = x->b;
   h.draw_cap = x->acc.draw_cap; h.Lf = x->Lf; h.N_pad = x->N_pad; h.N = x->N; h.seed = x->opt.seed;
-  h.jitter = x->jitter; h.traj_len = x->traj_len;
+  h.jitter = x->jitter; h.traj_len = x->traj_len; h.first_fold = x->opt.first_fold;
   size_t payload = 0;
   for (const Seg &g : ckpt_segments(x)) payload += g.bytes;
   h.payload = (int64_t)payload;
@@ -1425,7 +1432,8 @@ pcv_status pcv_checkpoint_load(pcv_ctx *x, const void *buf, int64_t bytes) {
   if (h.precision != mine.precision || h.variant != mine.variant || h.p != mine.p || h.d != mine.d ||
       h.K != mine.K || h.L != mine.L || h.C != mine.C || h.M != mine.M || h.max_batches != mine.max_batches ||
       h.b != mine.b || h.draw_cap != mine.draw_cap || h.Lf != mine.Lf || h.N != mine.N || h.seed != mine.seed ||
-      h.jitter != mine.jitter || h.traj_len != mine.traj_len || h.payload != mine.payload)
+      h.jitter != mine.jitter || h.traj_len != mine.traj_len || h.payload != mine.payload ||
+      h.first_fold != mine.first_fold)
     return fail(x, PCV_E_INVALID_ARG, "the checkpoint belongs to another problem or other options");
   if (bytes < (int64_t)sizeof(h) + h.payload) return fail(x, PCV_E_INVALID_ARG, "truncated checkpoint");
   if (h.state != ST_WARMED && h.state != ST_SAMPLED) return fail(x, PCV_E_INVALID_ARG, "bad checkpoint state");
@@ -1531,7 +1539,8 @@ pcv_status pcv_rhat_shuffle(pcv_ctx *x, int32_t n_blocks, int32_t n_reps, double
   CK(cudaMemsetAsync(x->shuf_max, 0, sizeof(unsigned long long) * n_reps, x->stream));
   const long long T2 = (long long)n_reps * x->K;
   k_rhat_shuffle<<<(unsigned)((T2 + 255) / 256), 256, 0, x->stream>>>(
-      x->shuf_blk, x->K, x->L, n_blocks, n_reps, x->opt.seed, x->shuf_max, rhat_fold_rep ? x->shuf_all : nullptr);
+      x->shuf_blk, x->K, x->L, n_blocks, n_reps, x->opt.seed, x->shuf_max, rhat_fold_rep ? x->shuf_all : nullptr,
+      x->opt.first_fold);
   CK(cudaGetLastError());
   std::vector<unsigned long long> hm(n_reps);
   CK(cudaMemcpyAsync(hm.data(), x->shuf_max, sizeof(unsigned long long) * n_reps, cudaMemcpyDeviceToHost, x->stream));

@@ -227,6 +227,7 @@ struct BeginArgs {
   double *H0;                   // out
   const float *eps, *minv;      // nominal step size, inverse mass
   float jitter;                 // eps_iter = eps (1 + jitter (2u - 1)), u from stream ST_JIT
+  int chain_base;               // Philox chain id = chain_base + c (global fold-chain id)
   float *eps_iter;              // out (written by block 0): the step size of this iteration
   const float *r_given;         // optional start momenta instead of drawing (C x ld)
   __nv_bfloat16 *shadow_hi, *shadow_lo;
@@ -236,6 +237,7 @@ struct BeginArgs {
 
 struct AcceptArgs {
   int C, d, ld;
+  int chain_base;               // Philox chain id = chain_base + c
   unsigned long long seed;
   unsigned int stream;
   IterState *st;
@@ -273,7 +275,7 @@ __global__ void k_begin(BeginArgs a);
 __global__ void k_normals(int C, int d, int ld, unsigned long long seed, unsigned int iter,
                           unsigned int stream, float scale, float *out);
 __global__ void k_init_from_pool(int C, int d, int ld, unsigned long long seed, const float *pool,
-                                 int n_pool, float *theta);
+                                 int n_pool, float *theta, int chain_base);
 __global__ void k_shadow(int C, int d, int ld, const float *theta, const float *theta_ref,
                          __nv_bfloat16 *hi, __nv_bfloat16 *lo, int ld_shadow);
 // Hyvarinen / Dawid-Sebastiani accumulators (Algorithms A3, A4): per chain
@@ -284,13 +286,13 @@ struct Extra {
   double *hs1, *hs2, *dsum, *douter;   // C, C x T, C x T, C x T x T
 };
 __global__ void k_extra_push(Problem pb, GradArgs a, Extra E, const unsigned int *iter,
-                             unsigned long long seed);
+                             unsigned long long seed, int chain_base);
 __global__ void k_extra_finalize(Problem pb, Extra E, int K, int L, double n, double *hs, double *dss);
 __global__ void k_block_stats(Accum A, int a, int D, double *blk);
 __global__ void k_mask_positions(int C, int d, int ld, const float *active, float *theta);
 __global__ void k_compare(const double *fo_a, const double *fo_b, int K, double *out);
 __global__ void k_rhat_shuffle(const double *blk, int K, int L, int D, int R, unsigned long long seed,
-                               unsigned long long *out_max, double *out_all);
+                               unsigned long long *out_max, double *out_all, int first_fold);
 __global__ void k_theta_ref(int n, int d, int ld, const float *src, float *theta_ref);
 __global__ void k_eta_ref(int N, int N_pad, int p, int KP, const __nv_bfloat16 *X16, const float *theta_ref,
                           float *eta_half);

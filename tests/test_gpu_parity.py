@@ -337,3 +337,29 @@ def test_autotuner_records_its_choice_and_results_hold(torch, orc, precision):
     tol = 1e-5 if precision == "fp32" else 1e-2
     assert rel_vec(g.cpu().double().numpy(), ref).max() <= tol
     pc.close()
+
+
+def test_fold_shards_draw_the_streams_of_their_global_folds(torch):
+    # a context that owns folds k0..K-1 of a problem (rows of other folds
+    # train only) with first_fold = k0 follows the single-context paths of
+    # those folds; with first_fold = 0 it draws other random numbers
+    from paper_2310_07002_b300 import shard
+    from paper_2310_07002_b300.pcv import PCV
+    w = W.gauss_blocks(N=203, p=5, K=15, L=5)
+    L, k0 = w.chains_per_fold, 8
+    th0 = W.random_theta(w.dim, w.n_chains, scale=0.5, seed=47).astype(np.float32).astype(np.float64)
+    full = make_pcv(w, step_size=0.05, batch_size=10, autotune=False)
+    full.set_positions(th0, step_size=0.05)
+    full.sample(10)
+    ref = full.positions()[0][k0 * L:]
+    full.close()
+    sub = dataclasses.replace(w, fold=shard.shard_folds(w.fold, k0, w.K), K=w.K - k0)
+    out = {}
+    for ff in (k0, 0):
+        pc = make_pcv(sub, step_size=0.05, batch_size=10, autotune=False, first_fold=ff)
+        pc.set_positions(th0[k0 * L:], step_size=0.05)
+        pc.sample(10)
+        out[ff] = rel_vec(pc.positions()[0], ref)
+        pc.close()
+    assert np.mean(out[k0] < 1e-4) >= 0.9, np.sort(out[k0])[-5:]
+    assert np.mean(out[0] < 1e-4) < 0.2
