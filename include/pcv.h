@@ -64,7 +64,8 @@ typedef enum {
  * accumulators are FP64 in every mode). */
 typedef enum {
     PCV_FP32_SIMT = 0,      /* FP32 CUDA-core kernels */
-    PCV_TF32 = 1,           /* tcgen05 tensor cores, TF32 in, FP32 accumulate */
+    PCV_TF32 = 1,           /* tensor cores (mma.sync m16n8k8), TF32 in, FP32 accumulate;
+                               flat models with p <= 112 */
     PCV_BF16 = 2            /* tcgen05 tensor cores, BF16 in, FP32 accumulate */
 } pcv_precision;
 

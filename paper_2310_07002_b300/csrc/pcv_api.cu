@@ -63,6 +63,7 @@ struct pcv_ctx {
   int64_t N = 0;
   int h = 0, Lf = 16, b = 50, M = 64, max_batches = 1024, n_fd_draws = 250;
   int chain_base = 0;             // Philox chain id of fold-chain 0 (first_fold * L)
+  bool tf32 = false;              // TF32 rung (mma.sync tensor cores)
   double traj_len = 0.0;          // effective trajectory length (0: no cap)
   float jitter = 0.0f;            // effective step-size jitter of the fold chains
   Problem pb{};
@@ -175,13 +176,22 @@ void free_all(pcv_ctx *x) {
   x->allocs.clear();
 }
 
+// chains per CTA tile and workspace row stride of the CUDA-core / TF32
+// gradient kernels (split-N partials)
+int chain_tile(const pcv_ctx *x) { return x->tf32 ? 64 : simt_chain_tile(x->p); }
+int ws_stride_of(const pcv_ctx *x) {
+  int s = std::max(x->d_pad, std::max(0, simt_flat_pp(x->p)));
+  if (x->tf32) s = std::max(s, tf32_k_round(x->p));
+  return s + 4;
+}
+
 int splits_cap(const pcv_ctx *x) {
   return x->variant == MV_HIER ? std::max(1, x->G / 4) : std::max(1, (int)(x->N / 256));
 }
 
 // fixed rule: enough CTAs to fill 4 per SM, at most the cap
 int splits_rule(const pcv_ctx *x, int C) {
-  const int tw = x->tc ? 32 : simt_chain_tile(x->p);
+  const int tw = x->tc ? 32 : chain_tile(x);
   const int tiles = (C + tw - 1) / tw;
   const int s = (kTargetCtas + tiles - 1) / tiles;
   return std::max(1, std::min(s, splits_cap(x)));
@@ -193,10 +203,9 @@ int splits_for(const pcv_ctx *x, int C) {
 }
 
 pcv_status ensure_ws(pcv_ctx *x, int C, int splits) {
-  const int tw = simt_chain_tile(x->p);
+  const int tw = chain_tile(x);
   const int tiles = (C + tw - 1) / tw;
-  const int PP = std::max(0, simt_flat_pp(x->p));
-  const int stride = std::max(x->d_pad, PP) + 4;
+  const int stride = ws_stride_of(x);
   const size_t need = (size_t)tiles * splits * tw * stride;
   if (need > x->ws_floats) {
     float *w;
@@ -320,7 +329,7 @@ GradArgs grad_args(pcv_ctx *x, const ChainBufs &cb, bool proposal) {
   a.minv = x->minv;
   a.splits = splits_for(x, cb.C);
   a.ws = x->ws;
-  a.ws_stride = std::max(x->d_pad, std::max(0, simt_flat_pp(x->p))) + 4;
+  a.ws_stride = ws_stride_of(x);
   a.tickets = x->tickets;
   a.shadow_hi = x->tc ? cb.shadow_hi : nullptr;
   a.shadow_lo = x->tc ? cb.shadow_lo : nullptr;
@@ -341,7 +350,8 @@ pcv_status launch_grad(pcv_ctx *x, GradArgs a, const ChainBufs *cb = nullptr) {
   if (s != PCV_OK) return s;
   a.ws = x->ws;
   a.tickets = x->tickets;
-  CK(launch_grad_simt(x->pb, a, x->stream));
+  if (x->tf32) CK(launch_grad_tf32(x->pb, a, x->stream));
+  else CK(launch_grad_simt(x->pb, a, x->stream));
   return PCV_OK;
 }
 
@@ -674,8 +684,10 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
     return s;
   };
   if (opt->precision < PCV_FP32_SIMT || opt->precision > PCV_BF16) return bail(PCV_E_INVALID_ARG, "bad precision");
-  if (opt->precision == PCV_TF32) return bail(PCV_E_UNSUPPORTED, "TF32 is not built in this version");
   x->tc = opt->precision == PCV_BF16;
+  x->tf32 = opt->precision == PCV_TF32;
+  if (x->tf32 && (model->kind == PCV_HIER_GAUSS || p > 112))
+    return bail(PCV_E_UNSUPPORTED, "the TF32 path covers the flat models with p <= 112");
   if (x->tc && (model->kind != PCV_LOGISTIC || p > 128))
     return bail(PCV_E_UNSUPPORTED, "the BF16 tensor-core path covers LOGISTIC with p <= 128");
   // model variant and dimension
@@ -1147,7 +1159,7 @@ pcv_status pcv_log_density(pcv_ctx *x, const float *theta, const int32_t *fold, 
                            double *logp, float *grad, double *shat) {
   if (!x) return PCV_E_INVALID_ARG;
   if (!theta || !fold || !logp || !grad || !shat || n < 1) return fail(x, PCV_E_INVALID_ARG, "bad argument");
-  if (precision != (x->tc ? PCV_BF16 : PCV_FP32_SIMT))
+  if (precision != (x->tc ? PCV_BF16 : x->tf32 ? PCV_TF32 : PCV_FP32_SIMT))
     return fail(x, PCV_E_UNSUPPORTED, "precision not available for this context");
   enter(x);
   ChainBufs cb;
@@ -1181,7 +1193,7 @@ pcv_status pcv_trajectory(pcv_ctx *x, const float *theta0, const float *r0, int3
                           float *r1, double *logp1, double *shat1) {
   if (!x) return PCV_E_INVALID_ARG;
   if (!theta0 || !r0 || !theta1 || !r1 || !logp1 || !shat1) return fail(x, PCV_E_INVALID_ARG, "null argument");
-  if (precision != (x->tc ? PCV_BF16 : PCV_FP32_SIMT))
+  if (precision != (x->tc ? PCV_BF16 : x->tf32 ? PCV_TF32 : PCV_FP32_SIMT))
     return fail(x, PCV_E_UNSUPPORTED, "precision not available for this context");
   enter(x);
   if (!x->traj_cb.theta) {
