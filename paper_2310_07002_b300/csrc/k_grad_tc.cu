@@ -56,11 +56,15 @@ constexpr int kTcMaxStages = 8; // X pipeline stages (as many as fit in shared m
 
 
 // softplus(eta) for eta = 2 s (the first GEMM yields s = eta / 2):
-// max(eta, 0) + ln 2 * log2(1 + 2^(-|eta| log2 e)), two MUFU operations
+// max(eta, 0) + ln 2 * log2(1 + 2^(-|eta| log2 e)): two MUFU instructions
+// (ex2, lg2) and three more; this epilogue is bound by instruction issue, so
+// the count matters more than which pipe runs them
 __device__ __forceinline__ float softplus_half(float s) {
-  const float e = exp2f(fabsf(s) * -2.8853900817779268f);   // 2^(-2|s| log2 e) = e^-|eta|
+  float e, l;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(fabsf(s) * -2.8853900817779268f));   // e^-|eta|
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(1.0f + e));
   const float m = fmaxf(s, 0.0f);
-  return fmaf(__log2f(1.0f + e), 0.6931471805599453f, m + m);
+  return fmaf(l, 0.6931471805599453f, m + m);
 }
 
 // ----------------------------- PTX helpers --------------------------------
