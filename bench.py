@@ -52,7 +52,10 @@ WORKLOADS = {
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
 # capture of that kernel (the profile summaries name the command); None when
 # the kernel changed after the capture.
-TRAFFIC = {}
+TRAFFIC = {
+    # k_grad_tc<7, false> kick-drift launch, profiles/k_grad_tc_logistic_large.md
+    ("logistic_large", "bf16"): 38.07e6,
+}
 
 
 def peaks():
