@@ -137,7 +137,13 @@ __device__ __forceinline__ void lshift_push(double &shift, double &mean, double 
 }
 
 // push draw s of chain c; n_before draws already accumulated (same for all
-// chains).  Called by a full warp.
+// chains).  Called by a full warp.  The recursions are independent, so each
+// runs on its own lane (the same operations in the same order as a serial
+// update): lane 0 U_x, lane 1 U_x2, lane 2 the batch LSE Z_x and, when the
+// batch closes, the log-shifted Welford of batch means, lane 3 the
+// log-shifted Welford of exp(s), lane 4 the Welford sums of s, the batch
+// Welford state and the autocovariance centring; then all lanes add their
+// lags.
 __device__ void accum_push(const Accum &A, int c, double s, long long n_before, int lane) {
   const long long n = n_before + 1;
   const int b = A.b;
@@ -145,11 +151,23 @@ __device__ void accum_push(const Accum &A, int c, double s, long long n_before, 
   double x = 0.0;
   if (lane == 0) {
     A.Ux[c] = log_add_exp(A.Ux[c], s);
+  } else if (lane == 1) {
     A.Ux2[c] = log_add_exp(A.Ux2[c], 2.0 * s);
-    A.Zx[c] = log_add_exp(in_batch == 1 ? -INFINITY : A.Zx[c], s);
+  } else if (lane == 2) {
+    const double zx = log_add_exp(in_batch == 1 ? -INFINITY : A.Zx[c], s);
+    A.Zx[c] = zx;
+    if (in_batch == b) {                     // the batch closes (A2 batch loop end)
+      const long long na = n / b;
+      const double z = zx - log((double)b);  // log of the batch mean, eq. bmean
+      double vm = A.vm[c], vmean = A.vmean[c], vM2 = A.vM2[c];
+      lshift_push(vm, vmean, vM2, na, z);
+      A.vm[c] = vm; A.vmean[c] = vmean; A.vM2[c] = vM2;
+    }
+  } else if (lane == 3) {
     double em = A.em[c], emean = A.emean[c], eM2 = A.eM2[c];
     lshift_push(em, emean, eM2, n, s);
     A.em[c] = em; A.emean[c] = emean; A.eM2[c] = eM2;
+  } else if (lane == 4) {
     double wm = A.wmean[c], wM2 = A.wM2[c];
     double dl = s - wm;
     wm += dl / (double)n;
@@ -163,12 +181,8 @@ __device__ void accum_push(const Accum &A, int c, double s, long long n_before, 
     if (n_before == 0) A.c0[c] = s;
     x = s - A.c0[c];
     A.xsum[c] += x;
-    if (in_batch == b) {                     // the batch closes (A2 batch loop end)
+    if (in_batch == b) {
       const long long na = n / b;
-      const double z = A.Zx[c] - log((double)b);   // log of the batch mean, eq. bmean
-      double vm = A.vm[c], vmean = A.vmean[c], vM2 = A.vM2[c];
-      lshift_push(vm, vmean, vM2, na, z);
-      A.vm[c] = vm; A.vmean[c] = vmean; A.vM2[c] = vM2;
       if (na <= A.max_batches) {
         A.bmean[(size_t)(na - 1) * A.C + c] = bm;
         A.bM2[(size_t)(na - 1) * A.C + c] = b2;
@@ -176,17 +190,22 @@ __device__ void accum_push(const Accum &A, int c, double s, long long n_before, 
     }
   }
   if (A.M > 0) {
-    x = __shfl_sync(0xffffffffu, x, 0);
+    x = __shfl_sync(0xffffffffu, x, 4);
     const long long t = n_before;                // 0-based time of this draw
+    const int tr = (int)(t % A.M);               // ring slot of this draw
     double *lag = A.lagsum + (size_t)c * (A.M + 1);
     double *ring = A.ring + (size_t)c * A.M;
     for (int m = lane; m <= A.M; m += 32) {
       if (m == 0) lag[0] += x * x;
-      else if (m <= t) lag[m] += x * ring[(t - m) % A.M];
+      else if (m <= t) {
+        int slot = tr - m;                       // (t - m) mod M, as 0 <= tr < M and m <= M
+        if (slot < 0) slot += A.M;
+        lag[m] += x * ring[slot];
+      }
     }
     __syncwarp();
     if (lane == 0) {
-      ring[t % A.M] = x;
+      ring[tr] = x;
       if (t < A.M) A.first[(size_t)c * A.M + t] = x;
     }
   }
