@@ -90,11 +90,11 @@ def run(w, precision: str, draws: int, fd_warmup: int, fold_warmup: int, seed: i
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="logistic_large", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "tf32", "bf16"])
     ap.add_argument("--draws", type=int, default=None)
     ap.add_argument("--fd-warmup", type=int, default=None)
     ap.add_argument("--fold-warmup", type=int, default=None)
-    ap.add_argument("--compare", default=None, choices=["fp32", "bf16"])
+    ap.add_argument("--compare", default=None, choices=["fp32", "tf32", "bf16"])
     ap.add_argument("--compare-draws", type=int, default=None,
                     help="draws of the comparison run (default: the same)")
     ap.add_argument("--compare-fold-warmup", type=int, default=None)
