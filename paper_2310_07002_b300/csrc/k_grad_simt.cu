@@ -376,133 +376,168 @@ __global__ void __launch_bounds__(kWarps * 32) k_grad_hier(Problem pb, GradArgs 
 
 // ---------------------------------------------------------------------------
 // Large p (33..128), flat models, FP32 CUDA cores.  A CTA owns a tile of 64
-// chains and one of `splits` row ranges; per 32-row chunk it computes
-//   S = Theta_tile . X_chunk^T   (2 x 4 register micro-tiles per thread),
-//   R = mask .* dlogp/deta       (shared memory),
-//   G += R . X_chunk             (4 x 8 register micro-tiles, kept for the range)
-// then combines split-N partials like the kernels above.
+// chains and one of `splits` row ranges; per 64-row chunk it computes
+//   S = Theta_tile . X_chunk^T   (4 chains x 4 rows per thread, float4 loads along K)
+//   R = mask .* dlogp/deta       (shared memory)
+//   G += R . X_chunk             (4 chains x 8 dims per thread, kept for the range)
+// then combines split-N partials like the kernels above.  Rows of the
+// shared tiles are 132 floats (528 B = 16 mod 128 B): the float4 loads of
+// 8 consecutive rows, or of 8 consecutive dim groups, hit distinct banks.
 // ---------------------------------------------------------------------------
-constexpr int kBigTileC = 64, kBigRows = 32;
+constexpr int kBigTileC = 64, kBigRows = 64, kBigLd = 132, kBigLdr = 68;
 
 template <int MV>
 __global__ void __launch_bounds__(256) k_grad_bigp(Problem pb, GradArgs a, int pp) {
-  extern __shared__ float sm_big[];
-  const int ldt = pp + 1;                           // odd strides: conflict-free
-  float *th_s = sm_big;                             // [64][pp + 1]
-  float *xs = th_s + kBigTileC * ldt;               // [32][pp + 1]
-  float *rs = xs + kBigRows * ldt;                  // [64][33]
-  float *ys = rs + kBigTileC * 33;                  // [32]
-  float *lls = ys + kBigRows;                       // [3][64][8]: ll_tr, ll_te, dlogsig partials
+  extern __shared__ __align__(16) float sm_big[];
+  float *th_s = sm_big;                             // [64][132] theta (0 beyond p)
+  float *xs = th_s + kBigTileC * kBigLd;            // [64][132] X chunk (0 beyond p and nr)
+  float *rs = xs + kBigRows * kBigLd;               // [64][68]  residual, chains x rows
+  float *ys = rs + kBigTileC * kBigLdr;             // [64]
+  float *lls = ys + kBigRows;                       // [3][64][16]: ll_tr, ll_te, dlogsig partials
   __shared__ int is_last;
+  __shared__ double lld[2][kBigTileC];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int tile = blockIdx.x / a.splits, split = blockIdx.x - tile * a.splits;
   const int c0 = tile * kBigTileC;
   const int p = pb.p;
-  for (int q = t; q < kBigTileC * pp; q += 256) {
-    const int cl = q / pp, j = q - cl * pp;
+  for (int q = t; q < kBigTileC * 32; q += 256) {
+    const int cl = q >> 5, j4 = (q & 31) * 4;
     const int c = c0 + cl;
-    th_s[cl * ldt + j] = (c < a.C && j < p) ? a.theta[(size_t)c * a.ld_theta + j] : 0.0f;
+    float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (c < a.C) {
+      const float *tp = a.theta + (size_t)c * a.ld_theta;
+      if (j4 < p) v.x = tp[j4];
+      if (j4 + 1 < p) v.y = tp[j4 + 1];
+      if (j4 + 2 < p) v.z = tp[j4 + 2];
+      if (j4 + 3 < p) v.w = tp[j4 + 3];
+    }
+    *reinterpret_cast<float4 *>(th_s + cl * kBigLd + j4) = v;
   }
-  // per-thread chain constants for the residual phase (chains cA, cA + 1)
-  const int cA = (t >> 3) * 2, rA = (t & 7) * 4;
-  float logsig[2] = {0.0f, 0.0f}, inv_s2[2] = {1.0f, 1.0f};
-  FoldDesc fd[2];
-  bool valid[2];
-  for (int u = 0; u < 2; ++u) {
-    const int c = c0 + cA + u;
-    valid[u] = c < a.C;
-    fd[u] = valid[u] ? pb.folds[fold_of_chain(a, c)] : FoldDesc{0, 0, 0, 0};
+  // thread roles: chains 4 cg .. 4 cg + 3 in both GEMMs; rows rg + 16 j
+  // (j < 4) in the first, dims 4 dg .. 4 dg + 3 and 64 + 4 dg .. in the second
+  const int cg = t >> 4, rg = t & 15, dg = t & 15;
+  float logsig[4], inv_s2[4];
+  FoldDesc fd[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int c = c0 + 4 * cg + i;
+    const bool valid = c < a.C;
+    fd[i] = valid ? pb.folds[fold_of_chain(a, c)] : FoldDesc{0, 0, 0, 0};
+    logsig[i] = 0.0f;
+    inv_s2[i] = 1.0f;
     if (MV == MV_GAUSS_KNOWN) {
-      logsig[u] = logf(pb.sigma_known);
-      inv_s2[u] = 1.0f / (pb.sigma_known * pb.sigma_known);
+      logsig[i] = logf(pb.sigma_known);
+      inv_s2[i] = 1.0f / (pb.sigma_known * pb.sigma_known);
     } else if (MV == MV_GAUSS_LOGSIG) {
-      logsig[u] = valid[u] ? a.theta[(size_t)c * a.ld_theta + p] : 0.0f;
-      inv_s2[u] = expf(-2.0f * logsig[u]);
+      logsig[i] = valid ? a.theta[(size_t)c * a.ld_theta + p] : 0.0f;
+      inv_s2[i] = expf(-2.0f * logsig[i]);
     }
   }
-  // GEMM2 accumulators: chains cg..cg+3, dims dg + 16 k
-  const int cg = (t >> 4) * 4, dg = t & 15;
   float acc[4][8];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc[i][k] = 0.0f;
-  float ll_tr[2] = {0.0f, 0.0f}, ll_te[2] = {0.0f, 0.0f}, dls[2] = {0.0f, 0.0f};
+  float ll_tr[4] = {0.0f, 0.0f, 0.0f, 0.0f}, ll_te[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  float dls[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   const int r0 = (int)((long long)pb.N * split / a.splits);
   const int r1 = (int)((long long)pb.N * (split + 1) / a.splits);
   __syncthreads();
   for (int n0 = r0; n0 < r1; n0 += kBigRows) {
     const int nr = min(kBigRows, r1 - n0);
-    for (int q = t; q < kBigRows * pp; q += 256) {
-      const int rr = q / pp, j = q - rr * pp;
-      xs[rr * ldt + j] = rr < nr ? pb.X[(size_t)(n0 + rr) * pb.p_pad + j] : 0.0f;
+    for (int q = t; q < kBigRows * 32; q += 256) {
+      const int rr = q >> 5, j4 = (q & 31) * 4;
+      float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if (rr < nr && j4 < pb.p_pad) v = *reinterpret_cast<const float4 *>(pb.X + (size_t)(n0 + rr) * pb.p_pad + j4);
+      *reinterpret_cast<float4 *>(xs + rr * kBigLd + j4) = v;
     }
     if (t < kBigRows) ys[t] = t < nr ? pb.y[n0 + t] : 0.0f;
     __syncthreads();
-    // GEMM1 micro-tile: chains cA, cA+1 x rows rA..rA+3
-    float sv[2][4];
+    // ---- S: chains 4 cg + i, rows rg + 16 j
+    float sv[4][4];
 #pragma unroll
-    for (int u = 0; u < 2; ++u)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) sv[u][v] = 0.0f;
-    for (int j = 0; j < p; ++j) {
-      const float t0 = th_s[cA * ldt + j], t1 = th_s[(cA + 1) * ldt + j];
+      for (int j = 0; j < 4; ++j) sv[i][j] = 0.0f;
+    for (int k = 0; k < pp; k += 4) {
+      float4 av[4], bv[4];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const float xv = xs[(rA + v) * ldt + j];
-        sv[0][v] = fmaf(t0, xv, sv[0][v]);
-        sv[1][v] = fmaf(t1, xv, sv[1][v]);
-      }
+      for (int i = 0; i < 4; ++i) av[i] = *reinterpret_cast<const float4 *>(th_s + (4 * cg + i) * kBigLd + k);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = *reinterpret_cast<const float4 *>(xs + (rg + 16 * j) * kBigLd + k);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          float v = sv[i][j];
+          v = fmaf(av[i].x, bv[j].x, v);
+          v = fmaf(av[i].y, bv[j].y, v);
+          v = fmaf(av[i].z, bv[j].z, v);
+          sv[i][j] = fmaf(av[i].w, bv[j].w, v);
+        }
     }
-    // masked residual dlogp/deta (and log likelihoods on evaluation steps)
+    // ---- masked residual dlogp/deta (and log likelihoods on evaluation steps)
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
+    for (int i = 0; i < 4; ++i) {
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const int rr = rA + v, n = n0 + rr;
-        const float eta = sv[u][v], yv = ys[rr];
+      for (int j = 0; j < 4; ++j) {
+        const int rr = rg + 16 * j, n = n0 + rr;
+        const float eta = sv[i][j], yv = ys[rr];
         const bool in_rows = rr < nr;
-        const float tr = (in_rows && (n < fd[u].excl_lo || n >= fd[u].excl_hi)) ? 1.0f : 0.0f;
+        const float tr = (in_rows && (n < fd[i].excl_lo || n >= fd[i].excl_hi)) ? 1.0f : 0.0f;
         float dll, ll = 0.0f;
         if (MV == MV_LOGISTIC) {
           dll = yv - 1.0f / (1.0f + __expf(-eta));
           if (a.need_ll) ll = yv * eta - softplusf(eta);
         } else {
           const float e = yv - eta;
-          dll = e * inv_s2[u];
-          if (a.need_ll) ll = -0.5f * kLog2Pi - logsig[u] - 0.5f * e * e * inv_s2[u];
-          if (MV == MV_GAUSS_LOGSIG) dls[u] = fmaf(tr, e * e * inv_s2[u] - 1.0f, dls[u]);
+          dll = e * inv_s2[i];
+          if (a.need_ll) ll = -0.5f * kLog2Pi - logsig[i] - 0.5f * e * e * inv_s2[i];
+          if (MV == MV_GAUSS_LOGSIG) dls[i] = fmaf(tr, e * e * inv_s2[i] - 1.0f, dls[i]);
         }
-        rs[(cA + u) * 33 + rr] = dll * tr;
+        rs[(4 * cg + i) * kBigLdr + rr] = dll * tr;
         if (a.need_ll) {
-          const float te = (in_rows && n >= fd[u].test_lo && n < fd[u].test_hi) ? 1.0f : 0.0f;
-          ll_tr[u] = fmaf(tr, ll, ll_tr[u]);
-          ll_te[u] = fmaf(te, ll, ll_te[u]);
+          const float te = (in_rows && n >= fd[i].test_lo && n < fd[i].test_hi) ? 1.0f : 0.0f;
+          ll_tr[i] = fmaf(tr, ll, ll_tr[i]);
+          ll_te[i] = fmaf(te, ll, ll_te[i]);
         }
       }
     }
     __syncthreads();
-    // GEMM2: G[cg..cg+3][dg + 16 k] += R[c][rr] X[rr][d]
-    for (int rr = 0; rr < nr; ++rr) {
-      float rv[4], xv[8];
+    // ---- G[4 cg + i][dims] += R[4 cg + i][row] X[row][dims] (rows beyond nr
+    // carry R = 0 and X = 0)
+    for (int row = 0; row < kBigRows; row += 4) {
+      float4 rv[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) rv[i] = rs[(cg + i) * 33 + rr];
+      for (int i = 0; i < 4; ++i) rv[i] = *reinterpret_cast<const float4 *>(rs + (4 * cg + i) * kBigLdr + row);
 #pragma unroll
-      for (int k = 0; k < 8; ++k) xv[k] = (dg + 16 * k < pp) ? xs[rr * ldt + dg + 16 * k] : 0.0f;
+      for (int u = 0; u < 4; ++u) {
+        const float4 x0 = *reinterpret_cast<const float4 *>(xs + (row + u) * kBigLd + 4 * dg);
+        const float4 x1 = *reinterpret_cast<const float4 *>(xs + (row + u) * kBigLd + 64 + 4 * dg);
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int k = 0; k < 8; ++k) acc[i][k] = fmaf(rv[i], xv[k], acc[i][k]);
+        for (int i = 0; i < 4; ++i) {
+          const float r = u == 0 ? rv[i].x : u == 1 ? rv[i].y : u == 2 ? rv[i].z : rv[i].w;
+          acc[i][0] = fmaf(r, x0.x, acc[i][0]);
+          acc[i][1] = fmaf(r, x0.y, acc[i][1]);
+          acc[i][2] = fmaf(r, x0.z, acc[i][2]);
+          acc[i][3] = fmaf(r, x0.w, acc[i][3]);
+          acc[i][4] = fmaf(r, x1.x, acc[i][4]);
+          acc[i][5] = fmaf(r, x1.y, acc[i][5]);
+          acc[i][6] = fmaf(r, x1.z, acc[i][6]);
+          acc[i][7] = fmaf(r, x1.w, acc[i][7]);
+        }
+      }
     }
     __syncthreads();
   }
-  // per-chain likelihood sums: the 8 threads sharing cA leave their partials
-  // in shared memory; one thread per chain adds them in a fixed order
+  // per-chain likelihood sums: the 16 threads of a chain group leave their
+  // partials in shared memory; one thread per chain adds them in order
 #pragma unroll
-  for (int u = 0; u < 2; ++u) {
-    lls[(0 * kBigTileC + cA + u) * 8 + (t & 7)] = ll_tr[u];
-    lls[(1 * kBigTileC + cA + u) * 8 + (t & 7)] = ll_te[u];
-    lls[(2 * kBigTileC + cA + u) * 8 + (t & 7)] = dls[u];
+  for (int i = 0; i < 4; ++i) {
+    const int cl = 4 * cg + i;
+    lls[(0 * kBigTileC + cl) * 16 + rg] = ll_tr[i];
+    lls[(1 * kBigTileC + cl) * 16 + rg] = ll_te[i];
+    lls[(2 * kBigTileC + cl) * 16 + rg] = dls[i];
   }
   __syncthreads();
   float sums[3] = {0.0f, 0.0f, 0.0f};
@@ -510,7 +545,7 @@ __global__ void __launch_bounds__(256) k_grad_bigp(Problem pb, GradArgs a, int p
 #pragma unroll
     for (int q = 0; q < 3; ++q)
 #pragma unroll
-      for (int v = 0; v < 8; ++v) sums[q] += lls[(q * kBigTileC + t) * 8 + v];
+      for (int v = 0; v < 16; ++v) sums[q] += lls[(q * kBigTileC + t) * 16 + v];
   }
   // partial of this CTA: [64 chains][ws_stride]: grads, slot pp dlogsig,
   // pp+1 ll_tr, pp+2 ll_te
@@ -518,8 +553,10 @@ __global__ void __launch_bounds__(256) k_grad_bigp(Problem pb, GradArgs a, int p
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
-      if (dg + 16 * k < pp) mine[(cg + i) * a.ws_stride + dg + 16 * k] = acc[i][k];
+    for (int k = 0; k < 8; ++k) {
+      const int dim = (k < 4 ? 4 * dg : 64 + 4 * dg) + (k & 3);
+      if (dim < pp) mine[(4 * cg + i) * a.ws_stride + dim] = acc[i][k];
+    }
   if (t < kBigTileC) {
     mine[t * a.ws_stride + pp] = sums[2];
     mine[t * a.ws_stride + pp + 1] = sums[0];
@@ -538,8 +575,7 @@ __global__ void __launch_bounds__(256) k_grad_bigp(Problem pb, GradArgs a, int p
     __threadfence();
   }
   // sum the splits' partials in split order; likelihood sums in FP64
-  __shared__ double lld[2][kBigTileC];
-  float *tot = xs;                                  // [64][pp + 4], reuses the tile buffers
+  float *tot = xs;                                  // [64][pp + 4], reuses the X tile
   const int ts = pp + 4;
   const float *base = a.ws + (size_t)tile * a.splits * kBigTileC * a.ws_stride;
   for (int q = t; q < kBigTileC * (pp + 3); q += 256) {
@@ -569,7 +605,6 @@ __global__ void __launch_bounds__(256) k_grad_bigp(Problem pb, GradArgs a, int p
     finish_chain<MV>(pb, a, c, row, lld[0][cl], lld[1][cl], lane);
   }
 }
-
 
 // ---------------------------------------------------------------------------
 // TF32 rung (flat models, p <= 128): the two contractions on the tensor
@@ -824,12 +859,9 @@ cudaError_t launch_grad_tf32(const Problem &pb, const GradArgs &a, cudaStream_t 
 int simt_chain_tile(int p) { return simt_flat_pp(p) > 0 ? 32 : kBigTileC; }
 
 size_t bigp_smem_bytes(int pp) {
-  const int ldt = pp + 1;
-  size_t f = (size_t)kBigTileC * ldt + (size_t)kBigRows * ldt + kBigTileC * 33 + kBigRows + 3 * kBigTileC * 8;
-  const size_t tot = (size_t)kBigTileC * (pp + 4);
-  const size_t avail = (size_t)kBigRows * ldt + kBigTileC * 33 + kBigRows + 3 * kBigTileC * 8;
-  if (tot > avail) f += tot - avail;
-  return f * sizeof(float);
+  (void)pp;
+  return sizeof(float) * ((size_t)kBigTileC * kBigLd + (size_t)kBigRows * kBigLd + (size_t)kBigTileC * kBigLdr +
+                          kBigRows + 3 * kBigTileC * 16);
 }
 
 // ---------------------------------------------------------------------------
