@@ -35,12 +35,14 @@
 // (atomic ticket, no spinning) sums the segments in order and applies priors
 // and the momentum / position update.
 //
-// Roles: warp 0 issues TMA loads, warp 1 allocates TMEM and issues the
-// first GEMM (one thread), warp 10 issues the second GEMM (one thread, so
-// that waiting for the epilogue never delays the first GEMM of later
-// chunks), warps 2-9 run the epilogue as two warpgroups, each taking
-// half of a chunk's 128 rows (thread = TMEM lane = chain; two warps per SM
-// sub-partition so TMEM-load and barrier latencies overlap).
+// Roles: warpgroup 0 holds the producers: warp 0 issues TMA loads, warp 1
+// allocates TMEM and issues the first GEMM (one thread), warp 2 issues the
+// second GEMM (one thread, so that waiting for the epilogue never delays the
+// first GEMM of later chunks).  Warpgroups 1 and 2 run the epilogue on
+// alternate chunks (thread = TMEM lane = chain; two warps per SM
+// sub-partition so TMEM-load and barrier latencies overlap); they take the
+// registers the producers give up (setmaxnreg) and read a chunk's S row
+// whole, releasing S before computing R.
 // Every mbarrier wait is bounded: on time-out the kernel sets an error flag,
 // stops issuing work and exits after freeing TMEM.
 #include <cuda.h>
@@ -51,7 +53,12 @@ namespace pcv {
 
 constexpr int kTN = 128;        // rows per chunk
 constexpr int kTM = 128;        // chains per tile
-constexpr int kTcThreads = 352; // 11 warps: TMA, GEMM1 MMA, 8 epilogue, GEMM2 MMA
+constexpr int kTcThreads = 384; // 12 warps: TMA, GEMM1 MMA, GEMM2 MMA, idle, 8 epilogue
+// Registers per thread after the split (setmaxnreg): the producer warpgroup
+// gives registers up so that the epilogue can hold a whole S row.  The
+// split must fit in what the CTA was launched with: checked on the host
+// against the compiled register count before any launch.
+constexpr int kTcRegsProducer = 64, kTcRegsEpilogue = 208;
 constexpr int kTcMaxStages = 8; // X pipeline stages (as many as fit in shared memory)
 
 
@@ -96,7 +103,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait (2 s of wall time).  Returns false on time-out or abort.
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
                                        unsigned int *err) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
@@ -138,7 +145,7 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatil
   return ok != 0;
 }
 // Bounded wait that ignores the abort flag (draining copies in flight).
-__device__ __noinline__ void mbar_wait_quiet(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ void mbar_wait_quiet(uint32_t bar, uint32_t parity) {
   const uint64_t t0 = global_ns();
   while (!mbar_try_wait(bar, parity))
     if (global_ns() - t0 > 2000000000ull) return;
@@ -211,6 +218,23 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
         "=r"(v[14]), "=r"(v[15])                                                                 \
       : "r"(taddr))
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+#define PCV_TMEM_ST16(taddr, v)                                                                  \
+  asm volatile(                                                                                  \
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13," \
+      "%14,%15,%16};" ::"r"(taddr),                                                              \
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),    \
+      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]) \
+      : "memory")
+// The compiler does not know that a TMEM load writes its registers until the
+// wait, nor that a TMEM store may read its sources until the wait: an empty
+// asm that "modifies" the registers, placed right after the wait, keeps
+// every use of loaded values after it and every source register alive (not
+// reused for temporaries) up to it.
+template <int Nr>
+__device__ __forceinline__ void tmem_fence_regs(uint32_t (&v)[Nr]) {
+#pragma unroll
+  for (int k = 0; k < Nr; ++k) asm volatile("" : "+r"(v[k]));
+}
 
 // Shared-memory matrix descriptor (tcgen05): start >> 4 at bits 0-13, leading
 // byte offset >> 4 at 16-29, stride byte offset >> 4 at 32-45, the fixed
@@ -258,7 +282,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     k_grad_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_hi,
               const __grid_constant__ CUtensorMap tm_lo, Problem pb, GradArgs a, TcArgs ta) {
   extern __shared__ uint8_t smem_raw[];
-  uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  // 1024-byte aligned base, by an offset into the shared array (so that the
+  // compiler keeps shared-memory loads for y and eta_ref)
+  uint8_t *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const int KA = ta.KP / 64;                       // 128-byte K atoms
   const uint32_t th_bytes = (uint32_t)KA * kTM * 128;
   const uint32_t x_bytes = (uint32_t)KA * kTN * 128;
@@ -307,9 +333,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_base_slot;
+
   const uint32_t tmem_G = tmem + 256;
   const uint32_t tmem_R = tmem + 384;              // R[b] at tmem_R + 64 b (bf16x2 per column)
 
+  if (warp < 4) {
+  // register split: warpgroup 0 (producers) gives registers up ...
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kTcRegsProducer));
   if (warp == 0) {
     // ------------------------------ TMA producer ---------------------------
     if (lane == 0) {
@@ -390,7 +420,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (++st == NS) { st = 0; xph ^= 1; }
       }
     }
-  } else if (warp == 10) {
+  } else if (warp == 2) {
     // ------------------------------ GEMM2 issuer ---------------------------
     // Per unit i: G += R[i & 1] . X_chunk, after the epilogue produced R.
     if (lane == 0) {
@@ -419,9 +449,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (++st == NS) st = 0;
       }
     }
+  }
   } else {
+    // ... and warpgroups 1-2 (epilogue) take them
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kTcRegsEpilogue));
     // ------------------------------ epilogue -------------------------------
-    const int ew = warp - 2;                        // epilogue warp 0..7
+    const int ew = warp - 4;                        // epilogue warp 0..7
     const int eg = ew >> 2;                         // warpgroup: units with (i & 1) == eg
     const int q = warp & 3;                         // TMEM lane quarter of this warp
     const int m = q * 32 + lane;                    // chain row within the tile
@@ -449,15 +482,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (!warp_wait(smem_u32(&x_full[i % NS]), (i / NS) & 1, abort_flag, ta.err)) { aborted = true; break; }
         tc_fence_after();
         const uint32_t *ywu = reinterpret_cast<const uint32_t *>(ys + (i % NS) * kTN * 2);
-        const float4 *ehu = reinterpret_cast<const float4 *>(ehs + (i % NS) * kTN);
-        // residual of half h (64 rows) of the chunk from v = S into pk
-        // (32 bf16x2), plus the log-likelihood sums when ACC
-        auto half_residual = [&](const int h, const uint32_t (&v)[64], uint32_t (&pk)[32]) {
-          const int n0 = j * kTN + 64 * h;
-          const uint32_t *yw = ywu + 32 * h;
+        const float2 *ehu = reinterpret_cast<const float2 *>(ehs + (i % NS) * kTN);
+        // residual of quarter qq (32 rows) of the chunk from v = S into pk
+        // (16 bf16x2), plus the log-likelihood sums when ACC
+        auto quarter = [&](const int qq, const uint32_t (&v)[32], uint32_t (&pk)[16]) {
+          const int n0 = j * kTN + 32 * qq;
+          const uint32_t *yw = ywu + 16 * qq;
           // S holds (eta - eta_ref) / 2: the row's eta_ref / 2 is added
           // where S is used
-          const float2 *eh2 = reinterpret_cast<const float2 *>(ehu) + 32 * h;
+          const float2 *eh2 = ehu + 16 * qq;
           // residual y - sigmoid(eta) = (y - 1/2) - tanh(S)/2 in FP32, rounded
           // to bf16 for the second GEMM (the same function on every leapfrog
           // step). A bf16x2 tanh here would bias the gradient: its error is
@@ -465,7 +498,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           // averaging out (a force error of ~6 % of the posterior scale per
           // dimension at N = 1e5, which shrinks the adapted step size).
 #pragma unroll
-          for (int k = 0; k < 32; ++k) {
+          for (int k = 0; k < 16; ++k) {
             const uint32_t y2 = yw[k];
             const float2 e2 = eh2[k];
             const float ta = tanh_f32(__uint_as_float(v[2 * k]) + e2.x);
@@ -473,9 +506,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             pk[k] = bf16x2_from(fmaf(-0.5f, ta, __uint_as_float(y2 << 16)),
                                 fmaf(-0.5f, tb, __uint_as_float(y2 & 0xFFFF0000u)));
           }
-          if (valid && n0 < fd.excl_hi && n0 + 64 > fd.excl_lo) {
+          if (valid && n0 < fd.excl_hi && n0 + 32 > fd.excl_lo) {
 #pragma unroll
-            for (int k = 0; k < 64; ++k) {
+            for (int k = 0; k < 32; ++k) {
               const int n = n0 + k;
               if (n >= fd.excl_lo && n < fd.excl_hi) pk[k >> 1] &= (k & 1) ? 0x0000FFFFu : 0xFFFF0000u;
             }
@@ -484,19 +517,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             // log likelihood y eta - softplus(eta): the linear part is
             // theta . sum(y x) per fold (added in the finish), so only
             // softplus(eta) = max(eta, 0) + log(1 + exp(-|eta|)) is summed
-            // here, in FP32 per half chunk and FP64 across chunks.
-            // Half chunks clear of the fold's excluded rows and of the
+            // here, in FP32 per quarter and FP64 across quarters.
+            // Quarters clear of the fold's excluded rows and of the
             // padding need no per-row mask.
-            if (n0 + 64 <= pb.N && (n0 + 64 <= fd.excl_lo || n0 >= fd.excl_hi)) {
+            if (n0 + 32 <= pb.N && (n0 + 32 <= fd.excl_lo || n0 >= fd.excl_hi)) {
               float acc4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-              for (int k = 0; k < 64; ++k)
+              for (int k = 0; k < 32; ++k)
                 acc4[k & 3] += softplus_half(__uint_as_float(v[k]) + (k & 1 ? eh2[k >> 1].y : eh2[k >> 1].x));
               sp_tr += (double)((acc4[0] + acc4[1]) + (acc4[2] + acc4[3]));
             } else {
               float tr = 0.0f, te = 0.0f;
 #pragma unroll
-              for (int k = 0; k < 64; ++k) {
+              for (int k = 0; k < 32; ++k) {
                 const int n = n0 + k;
                 const float sp = softplus_half(__uint_as_float(v[k]) + (k & 1 ? eh2[k >> 1].y : eh2[k >> 1].x));
                 if (n < pb.N && (n < fd.excl_lo || n >= fd.excl_hi)) tr += sp;
@@ -507,30 +540,43 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
           }
         };
-        // S is read and released before the wait for the R buffer, so that
-        // the first GEMM of unit i + 2 is not held up by the second GEMM of
-        // unit i - 2.  TMEM loads are followed by their wait right away (the
-        // destination registers are written asynchronously until then), and
-        // each store by its wait before its source registers are reused.
-        uint32_t v[64], pk[32];
-        PCV_TMEM_LD32(tmem + sb * 128 + lane_off, v);
-        PCV_TMEM_LD32(tmem + sb * 128 + 32 + lane_off, (v + 32));
+        // The whole S tile row (128 columns) comes into registers at once and
+        // S is released before any arithmetic, so the first GEMM of unit
+        // i + 2 waits only for the TMEM loads of unit i.  The four R quarters
+        // go out as 16-column stores with one wait at the end (TMEM round
+        // trips are several hundred cycles while the MMAs run).  Loaded
+        // registers are used only after the load wait, and store sources
+        // stay allocated until the store wait (tmem_fence_regs pins both).
+        uint32_t v0[32], v1[32], v2[32], v3[32], p0[16], p1[16], p2[16], p3[16];
+        PCV_TMEM_LD32(tmem + sb * 128 + lane_off, v0);
+        PCV_TMEM_LD32(tmem + sb * 128 + 32 + lane_off, v1);
+        PCV_TMEM_LD32(tmem + sb * 128 + 64 + lane_off, v2);
+        PCV_TMEM_LD32(tmem + sb * 128 + 96 + lane_off, v3);
         tmem_wait_ld();
-        half_residual(0, v, pk);
-        PCV_TMEM_LD32(tmem + sb * 128 + 64 + lane_off, v);
-        PCV_TMEM_LD32(tmem + sb * 128 + 96 + lane_off, (v + 32));
-        tmem_wait_ld();
+        tmem_fence_regs(v0);
+        tmem_fence_regs(v1);
+        tmem_fence_regs(v2);
+        tmem_fence_regs(v3);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&s_empty[sb]));   // S fully read: release it
+        quarter(0, v0, p0);
         if (!warp_wait(smem_u32(&r_empty[rb]), ((i >> 1) & 1) ^ 1, abort_flag, ta.err)) { aborted = true; break; }
         tc_fence_after();
-        // R row m (TMEM lane m): chunk rows 64 h .. 64 h + 63 as 32 bf16x2 columns
-        PCV_TMEM_ST32(tmem_R + 64 * rb + lane_off, pk);
+        // R row m (TMEM lane m): chunk rows 2c, 2c + 1 in bf16x2 column c
+        const uint32_t rbuf = tmem_R + 64 * rb + lane_off;
+        PCV_TMEM_ST16(rbuf, p0);
+        quarter(1, v1, p1);
+        PCV_TMEM_ST16(rbuf + 16, p1);
+        quarter(2, v2, p2);
+        PCV_TMEM_ST16(rbuf + 32, p2);
+        quarter(3, v3, p3);
+        PCV_TMEM_ST16(rbuf + 48, p3);
         tmem_wait_st();
-        half_residual(1, v, pk);
-        PCV_TMEM_ST32(tmem_R + 64 * rb + 32 + lane_off, pk);
-        tmem_wait_st();
+        tmem_fence_regs(p0);
+        tmem_fence_regs(p1);
+        tmem_fence_regs(p2);
+        tmem_fence_regs(p3);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&r_full[rb]));
@@ -651,7 +697,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       ++t;
       j0 = 0;
     }
+    // back to the producers' count, so that all warps meet the teardown alike
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kTcRegsProducer));
   }
+
   // teardown: every role has left its loop (normally or by abort)
   tc_fence_before();
   __syncthreads();
@@ -692,6 +741,20 @@ static cudaError_t set_smem_attr() {
   return e != cudaSuccess ? e : e2;
 }
 
+// setmaxnreg.inc waits until the CTA's register pool can grant the request:
+// the pool is what the CTA was launched with (threads x the compiled register
+// count), so a split larger than that would never be granted.  Every
+// instantiation is checked once; launches are refused if any fails.
+static bool g_tc_regs_ok = false;
+template <int KS>
+static bool regs_fit() {
+  const long need = 128L * kTcRegsProducer + 256L * kTcRegsEpilogue;
+  cudaFuncAttributes fa, fb;
+  if (cudaFuncGetAttributes(&fa, k_grad_tc<KS, false>) != cudaSuccess) return false;
+  if (cudaFuncGetAttributes(&fb, k_grad_tc<KS, true>) != cudaSuccess) return false;
+  return (long)fa.numRegs * kTcThreads >= need && (long)fb.numRegs * kTcThreads >= need;
+}
+
 // once per context (outside any stream capture): allow the large dynamic SMEM
 cudaError_t tc_prepare() {
   cudaError_t e = cudaSuccess;
@@ -699,6 +762,9 @@ cudaError_t tc_prepare() {
                       set_smem_attr<5>(), set_smem_attr<6>(), set_smem_attr<7>(), set_smem_attr<8>()};
   for (cudaError_t x : r)
     if (x != cudaSuccess) e = x;
+  g_tc_regs_ok = regs_fit<1>() && regs_fit<2>() && regs_fit<3>() && regs_fit<4>() && regs_fit<5>() &&
+                 regs_fit<6>() && regs_fit<7>() && regs_fit<8>();
+  if (e == cudaSuccess && !g_tc_regs_ok) e = cudaErrorInvalidConfiguration;
   return e;
 }
 
@@ -706,6 +772,7 @@ cudaError_t launch_grad_tc(const CUtensorMap &tm_x, const CUtensorMap &tm_hi, co
                            const Problem &pb, const GradArgs &a, const TcArgs &ta, cudaStream_t st) {
   const size_t smem = tc_smem_bytes(ta.KP, ta.NS, ta.need_lo, pb.p);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  if (!g_tc_regs_ok) return cudaErrorInvalidConfiguration;   // tc_prepare not run, or the split does not fit
   switch (ta.KS) {
 #define PCV_TC_CASE(K)                                                                          \
   case K:                                                                                       \
