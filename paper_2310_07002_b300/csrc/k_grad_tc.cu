@@ -14,9 +14,11 @@
 //
 // The tensor cores see theta centred on a reference theta_ref (the mean of
 // the full-data draws, or of the positions a caller sets) and scaled by 1/2:
-// the shadows hold (theta - theta_ref) / 2 in bf16 hi + lo parts, the
-// epilogue adds eta_ref / 2 = x . theta_ref / 2 (FP32, per row), so S is
-// eta / 2 and sigmoid(eta) = 1/2 + tanh(S)/2.  The same SMEM X tile is the
+// the shadows hold (theta - theta_ref) / 2 in bf16 hi + lo parts.  The
+// row's eta_ref / 2 = x . theta_ref / 2 enters the same GEMM: three more K
+// columns of X hold it as hi + mid + lo bf16 parts and the hi shadow holds 1
+// there, so S is eta / 2 straight from the tensor cores and
+// sigmoid(eta) = 1/2 + tanh(S)/2 needs no per-row addition.  The same SMEM X tile is the
 // K-major B operand of the first GEMM and the MN-major B operand of the
 // second.  Launches that need log densities accumulate hi + lo (an
 // FP32-accurate eta for the Metropolis test); the kick-drift launches use
@@ -283,7 +285,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               const __grid_constant__ CUtensorMap tm_lo, Problem pb, GradArgs a, TcArgs ta) {
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte aligned base, by an offset into the shared array (so that the
-  // compiler keeps shared-memory loads for y and eta_ref)
+  // compiler keeps shared-memory loads for y)
   uint8_t *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const int KA = ta.KP / 64;                       // 128-byte K atoms
   const uint32_t th_bytes = (uint32_t)KA * kTM * 128;
@@ -292,9 +294,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint8_t *th_hi = sm;
   uint8_t *th_lo = th_hi + th_bytes;
   uint8_t *xs = th_lo + (ta.need_lo ? th_bytes : 0);
-  uint8_t *ys = xs + (size_t)NS * x_bytes;        // NS x kTN bf16 (y - 1/2)
-  float *ehs = reinterpret_cast<float *>(ys + NS * kTN * 2);   // NS x kTN: eta_ref / 2
-  uint64_t *bars = reinterpret_cast<uint64_t *>(ys + NS * kTN * 6 + 64);
+  float *ys = reinterpret_cast<float *>(xs + (size_t)NS * x_bytes);   // NS x kTN: y - 1/2
+  uint64_t *bars = reinterpret_cast<uint64_t *>(ys + NS * kTN + 16);
   // barrier slots (up to kTcMaxStages X stages)
   uint64_t *x_full = bars, *x_empty = bars + kTcMaxStages;
   uint64_t *s_full = bars + 2 * kTcMaxStages, *s_empty = s_full + 2;
@@ -363,12 +364,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         const int st = i % NS, rnd = i / NS;
         if (!mbar_wait_fast(smem_u32(&x_empty[st]), (rnd & 1) ^ 1, abort_flag, ta.err)) break;
-        mbar_expect_tx(smem_u32(&x_full[st]), x_bytes + kTN * 6);
+        mbar_expect_tx(smem_u32(&x_full[st]), x_bytes + kTN * 4);
         uint8_t *xb = xs + (size_t)st * x_bytes;
         for (int kb = 0; kb < KA; ++kb)
           tma_load_2d(smem_u32(xb + kb * kTN * 128), &tm_x, kb * 64, j * kTN, smem_u32(&x_full[st]));
-        bulk_load(smem_u32(ys + st * kTN * 2), ta.yc + (size_t)j * kTN, kTN * 2, smem_u32(&x_full[st]));
-        bulk_load(smem_u32(ehs + st * kTN), ta.eta_half + (size_t)j * kTN, kTN * 4, smem_u32(&x_full[st]));
+        bulk_load(smem_u32(ys + st * kTN), ta.yc + (size_t)j * kTN, kTN * 4, smem_u32(&x_full[st]));
         last_round[st] = rnd;
       }
       // on abort: let copies already issued land before the CTA exits
@@ -481,16 +481,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // waiting on its barrier makes the TMA-written y visible
         if (!warp_wait(smem_u32(&x_full[i % NS]), (i / NS) & 1, abort_flag, ta.err)) { aborted = true; break; }
         tc_fence_after();
-        const uint32_t *ywu = reinterpret_cast<const uint32_t *>(ys + (i % NS) * kTN * 2);
-        const float2 *ehu = reinterpret_cast<const float2 *>(ehs + (i % NS) * kTN);
+        const float2 *ywu = reinterpret_cast<const float2 *>(ys + (i % NS) * kTN);
         // residual of quarter qq (32 rows) of the chunk from v = S into pk
         // (16 bf16x2), plus the log-likelihood sums when ACC
         auto quarter = [&](const int qq, const uint32_t (&v)[32], uint32_t (&pk)[16]) {
           const int n0 = j * kTN + 32 * qq;
-          const uint32_t *yw = ywu + 16 * qq;
-          // S holds (eta - eta_ref) / 2: the row's eta_ref / 2 is added
-          // where S is used
-          const float2 *eh2 = ehu + 16 * qq;
+          const float2 *yw = ywu + 16 * qq;     // y - 1/2 of rows 2k, 2k + 1
           // residual y - sigmoid(eta) = (y - 1/2) - tanh(S)/2 in FP32, rounded
           // to bf16 for the second GEMM (the same function on every leapfrog
           // step). A bf16x2 tanh here would bias the gradient: its error is
@@ -499,12 +495,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           // dimension at N = 1e5, which shrinks the adapted step size).
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
-            const uint32_t y2 = yw[k];
-            const float2 e2 = eh2[k];
-            const float ta = tanh_f32(__uint_as_float(v[2 * k]) + e2.x);
-            const float tb = tanh_f32(__uint_as_float(v[2 * k + 1]) + e2.y);
-            pk[k] = bf16x2_from(fmaf(-0.5f, ta, __uint_as_float(y2 << 16)),
-                                fmaf(-0.5f, tb, __uint_as_float(y2 & 0xFFFF0000u)));
+            const float2 y2 = yw[k];
+            const float ta = tanh_f32(__uint_as_float(v[2 * k]));
+            const float tb = tanh_f32(__uint_as_float(v[2 * k + 1]));
+            pk[k] = bf16x2_from(fmaf(-0.5f, ta, y2.x), fmaf(-0.5f, tb, y2.y));
           }
           if (valid && n0 < fd.excl_hi && n0 + 32 > fd.excl_lo) {
 #pragma unroll
@@ -524,14 +518,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               float acc4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
               for (int k = 0; k < 32; ++k)
-                acc4[k & 3] += softplus_half(__uint_as_float(v[k]) + (k & 1 ? eh2[k >> 1].y : eh2[k >> 1].x));
+                acc4[k & 3] += softplus_half(__uint_as_float(v[k]));
               sp_tr += (double)((acc4[0] + acc4[1]) + (acc4[2] + acc4[3]));
             } else {
               float tr = 0.0f, te = 0.0f;
 #pragma unroll
               for (int k = 0; k < 32; ++k) {
                 const int n = n0 + k;
-                const float sp = softplus_half(__uint_as_float(v[k]) + (k & 1 ? eh2[k >> 1].y : eh2[k >> 1].x));
+                const float sp = softplus_half(__uint_as_float(v[k]));
                 if (n < pb.N && (n < fd.excl_lo || n >= fd.excl_hi)) tr += sp;
                 if (n >= fd.test_lo && n < fd.test_hi) te += sp;
               }
@@ -717,7 +711,7 @@ size_t tc_smem_bytes(int KP, int NS, int need_lo, int p) {
   (void)p;
   const size_t KA = KP / 64;
   size_t b = KA * kTM * 128 * (need_lo ? 2 : 1) + (size_t)NS * KA * kTN * 128 +
-             (size_t)NS * kTN * 6 + 64 + (2 * kTcMaxStages + 17) * 8;   // y, eta_ref/2; barrier / flag slots
+             (size_t)NS * kTN * 4 + 64 + (2 * kTcMaxStages + 17) * 8;   // y - 1/2; barrier / flag slots
   return b + 1024;   // alignment slack
 }
 
@@ -758,12 +752,12 @@ static bool regs_fit() {
 // once per context (outside any stream capture): allow the large dynamic SMEM
 cudaError_t tc_prepare() {
   cudaError_t e = cudaSuccess;
-  cudaError_t r[8] = {set_smem_attr<1>(), set_smem_attr<2>(), set_smem_attr<3>(), set_smem_attr<4>(),
-                      set_smem_attr<5>(), set_smem_attr<6>(), set_smem_attr<7>(), set_smem_attr<8>()};
+  cudaError_t r[9] = {set_smem_attr<1>(), set_smem_attr<2>(), set_smem_attr<3>(), set_smem_attr<4>(), set_smem_attr<5>(),
+                      set_smem_attr<6>(), set_smem_attr<7>(), set_smem_attr<8>(), set_smem_attr<9>()};
   for (cudaError_t x : r)
     if (x != cudaSuccess) e = x;
   g_tc_regs_ok = regs_fit<1>() && regs_fit<2>() && regs_fit<3>() && regs_fit<4>() && regs_fit<5>() &&
-                 regs_fit<6>() && regs_fit<7>() && regs_fit<8>();
+                 regs_fit<6>() && regs_fit<7>() && regs_fit<8>() && regs_fit<9>();
   if (e == cudaSuccess && !g_tc_regs_ok) e = cudaErrorInvalidConfiguration;
   return e;
 }
@@ -780,7 +774,7 @@ cudaError_t launch_grad_tc(const CUtensorMap &tm_x, const CUtensorMap &tm_hi, co
     else k_grad_tc<K, false><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta);            \
     break;
     PCV_TC_CASE(1) PCV_TC_CASE(2) PCV_TC_CASE(3) PCV_TC_CASE(4)
-    PCV_TC_CASE(5) PCV_TC_CASE(6) PCV_TC_CASE(7) PCV_TC_CASE(8)
+    PCV_TC_CASE(5) PCV_TC_CASE(6) PCV_TC_CASE(7) PCV_TC_CASE(8) PCV_TC_CASE(9)
 #undef PCV_TC_CASE
     default: return cudaErrorInvalidValue;
   }

@@ -585,6 +585,28 @@ __global__ void k_eta_ref(int N, int N_pad, int p, int KP, const __nv_bfloat16 *
     for (int j = 0; j < p; ++j) s += (double)__bfloat162float(X16[(size_t)n * KP + j]) * (double)theta_ref[j];
   eta_half[n] = (float)(0.5 * s);
 }
+// eta_ref / 2 of every row into the operand columns p .. p + kEtaCols - 1 of
+// the bf16 design matrix, as a sum of kEtaCols bf16 parts (each part rounds
+// what the previous ones left: 24 significant bits, the precision of eta_half)
+__global__ void k_eta_fold(int N_pad, int p, int KP, const float *eta_half, __nv_bfloat16 *X16) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N_pad) return;
+  float rest = eta_half[n];
+#pragma unroll
+  for (int k = 0; k < kEtaCols; ++k) {
+    const __nv_bfloat16 part = __float2bfloat16_rn(rest);
+    X16[(size_t)n * KP + p + k] = part;
+    rest -= __bfloat162float(part);
+  }
+}
+// the constant 1 of the eta_ref columns in a chain set's hi shadow (the lo
+// shadow keeps 0 there, so launches that add hi and lo count it once)
+__global__ void k_shadow_ones(int C_pad, int p, int KP, __nv_bfloat16 *hi) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= C_pad * kEtaCols) return;
+  const int c = t / kEtaCols, k = t - c * kEtaCols;
+  hi[(size_t)c * KP + p + k] = __float2bfloat16_rn(1.0f);
+}
 }  // namespace pcv
 
 namespace pcv {

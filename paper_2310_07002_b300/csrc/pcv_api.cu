@@ -94,7 +94,8 @@ struct pcv_ctx {
   // tensor-core path
   bool tc = false;
   int KP = 0, KS = 0, PN = 0, N_pad = 0, J = 0, n_sm = 148;
-  __nv_bfloat16 *X16 = nullptr, *yc16 = nullptr;
+  __nv_bfloat16 *X16 = nullptr;
+  float *ycf = nullptr;           // tensor-core path: y - 1/2 per row (N_pad)
   CUtensorMap tm_x{};
   float *ws_tc = nullptr;
   double *ylin = nullptr;         // tensor-core path: per-fold sums of y x (see TcArgs)
@@ -256,6 +257,9 @@ pcv_status alloc_shadows(pcv_ctx *x, ChainBufs &cb, int C) {
   if (!encode_bf16_map(&cb.tm_hi, cb.shadow_hi, cb.C_pad, x->KP) ||
       !encode_bf16_map(&cb.tm_lo, cb.shadow_lo, cb.C_pad, x->KP))
     return fail(x, PCV_E_CUDA, "cuTensorMapEncodeTiled failed for the parameter shadows");
+  // the eta_ref / 2 columns: 1 in hi for every chain row (also the padding)
+  k_shadow_ones<<<(cb.C_pad * kEtaCols + 255) / 256, 256, 0, x->stream>>>(cb.C_pad, x->p, x->KP, cb.shadow_hi);
+  CK(cudaGetLastError());
   return PCV_OK;
 }
 
@@ -282,8 +286,7 @@ TcArgs tc_args(pcv_ctx *x, int C, bool need_ll) {
   t.NS = tc_max_fit_stages(x, t.need_lo);
   auto it = x->tuned_ns.find(std::make_pair(C, t.need_lo));
   if (it != x->tuned_ns.end()) t.NS = it->second;
-  t.yc = x->yc16;
-  t.eta_half = x->eta_half;
+  t.yc = x->ycf;
   t.theta_ref = x->theta_ref;
   t.ws = x->ws_tc;
   t.ylin = x->ylin;
@@ -419,6 +422,13 @@ pcv_status write_shadow(pcv_ctx *x, ChainBufs &cb, const float *theta, int ld) {
   return PCV_OK;
 }
 
+// eta_ref / 2 (eta_half) into the operand columns of the bf16 design matrix
+pcv_status fold_eta(pcv_ctx *x) {
+  k_eta_fold<<<(x->N_pad + 255) / 256, 256, 0, x->stream>>>(x->N_pad, x->p, x->KP, x->eta_half, x->X16);
+  CK(cudaGetLastError());
+  return PCV_OK;
+}
+
 // tensor-core path: centre on the mean of n parameter vectors (ld apart)
 pcv_status set_reference(pcv_ctx *x, const float *src, int n, int ld) {
   if (!x->tc) return PCV_OK;
@@ -427,8 +437,9 @@ pcv_status set_reference(pcv_ctx *x, const float *src, int n, int ld) {
   k_eta_ref<<<(x->N_pad + 255) / 256, 256, 0, x->stream>>>((int)x->N, x->N_pad, x->p, x->KP, x->X16, x->theta_ref,
                                                           x->eta_half);
   CK(cudaGetLastError());
-  x->centered = true;
-  return PCV_OK;
+  const pcv_status s = fold_eta(x);
+  if (s == PCV_OK) x->centered = true;
+  return s;
 }
 
 // evaluate gradient, logp and shat at the current positions of a chain set
@@ -709,9 +720,10 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
     return bail(PCV_E_UNSUPPORTED, "FP32 path: p <= 128 (flat models) or p <= 32 (hierarchical)");
   x->p_pad = PP > 0 ? PP : (p + 3) / 4 * 4;
   if (x->tc) {
-    x->KP = (p + 63) / 64 * 64;
-    x->KS = (p + 15) / 16;
-    x->PN = 16 * x->KS;
+    // the first GEMM's K covers the p covariates and the eta_ref / 2 columns
+    x->KS = (p + kEtaCols + 15) / 16;
+    x->KP = (16 * x->KS + 63) / 64 * 64;
+    x->PN = 16 * ((p + 15) / 16);
     x->N_pad = (int)((N + 127) / 128 * 128);
     x->J = x->N_pad / 128;
   }
@@ -810,10 +822,10 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
   if (x->tc) {
     // bf16 design matrix [N_pad x KP] (round to nearest even) and y - 1/2
     std::vector<__nv_bfloat16> hX16((size_t)x->N_pad * x->KP, __float2bfloat16_rn(0.0f));
-    std::vector<__nv_bfloat16> hyc((size_t)x->N_pad, __float2bfloat16_rn(0.0f));
+    std::vector<float> hyc((size_t)x->N_pad, 0.0f);
     for (int64_t r = 0; r < N; ++r) {
       for (int j = 0; j < p; ++j) hX16[(size_t)r * x->KP + j] = __float2bfloat16_rn(hX[(size_t)r * x->p_pad + j]);
-      hyc[r] = __float2bfloat16_rn(hy[r] - 0.5f);
+      hyc[r] = hy[r] - 0.5f;
     }
     // per fold: sum over training rows and over test rows of y_n x_n, with
     // the bf16 X the tensor cores see (the linear part of the logistic log
@@ -834,13 +846,13 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
       add_rows(te, fds[k].test_lo, fds[k].test_hi);
       for (int j = 0; j < p; ++j) tr[j] = all[j] - ex[j];
     }
-    if (!dalloc_n(x, &x->X16, hX16.size()) || !dalloc_n(x, &x->yc16, hyc.size()) ||
+    if (!dalloc_n(x, &x->X16, hX16.size()) || !dalloc_n(x, &x->ycf, hyc.size()) ||
         !dalloc_n(x, &x->ylin, hyl.size()) || !dalloc_n(x, &x->theta_ref, (size_t)x->d_pad) ||
         !dalloc_n(x, &x->eta_half, (size_t)x->N_pad))
       return bail(PCV_E_OOM, "device allocation failed");
     cudaMemcpyAsync(x->ylin, hyl.data(), hyl.size() * sizeof(double), cudaMemcpyHostToDevice, x->stream);
     cudaMemcpyAsync(x->X16, hX16.data(), hX16.size() * 2, cudaMemcpyHostToDevice, x->stream);
-    cudaMemcpyAsync(x->yc16, hyc.data(), hyc.size() * 2, cudaMemcpyHostToDevice, x->stream);
+    cudaMemcpyAsync(x->ycf, hyc.data(), hyc.size() * sizeof(float), cudaMemcpyHostToDevice, x->stream);
     if (cudaStreamSynchronize(x->stream) != cudaSuccess) return bail(PCV_E_CUDA, "upload failed");
     if (!encode_bf16_map(&x->tm_x, x->X16, x->N_pad, x->KP))
       return bail(PCV_E_CUDA, "cuTensorMapEncodeTiled failed for X");
@@ -1463,9 +1475,11 @@ pcv_status pcv_checkpoint_load(pcv_ctx *x, const void *buf, int64_t bytes) {
   if (h.tuned_splits > 0) x->tuned_splits[x->C] = h.tuned_splits;
   if (h.tuned_ns0 > 0) x->tuned_ns[std::make_pair(x->C, 0)] = h.tuned_ns0;
   if (h.tuned_ns1 > 0) x->tuned_ns[std::make_pair(x->C, 1)] = h.tuned_ns1;
-  // the bf16 shadows follow from the restored positions and reference
+  // the bf16 shadows and the eta_ref columns of X follow from the restored
+  // positions and reference
   pcv_status s = write_shadow(x, x->fold_cb, x->fold_cb.theta, x->d_pad);
   if (s != PCV_OK) return s;
+  if (x->tc && (s = fold_eta(x)) != PCV_OK) return s;
   CK(cudaStreamSynchronize(x->stream));
   leave(x);
   return PCV_OK;

@@ -183,10 +183,15 @@ constexpr double kLog2D = 0.69314718055994530942;
 // workspace rows per tile segment beyond the PN gradient rows: per
 // warpgroup the training and test softplus sums, each as an FP32 hi + lo pair
 constexpr int kTcSlots = 8;
+// Tensor-core operand columns p .. p + kEtaCols - 1: X holds eta_ref / 2 of
+// its row split into kEtaCols bf16 parts (hi, mid, lo), the theta shadows hold
+// 1 (hi) and 0 (lo) there, so the first GEMM yields eta / 2 itself.
+constexpr int kEtaCols = 3;
 
 struct TcArgs {
-  int KP;                 // padded p in SMEM / global (64 or 128)
-  int KS;                 // GEMM1 K steps of 16 (ceil(p / 16))
+  int KP;                 // padded K in SMEM / global (a multiple of 64, >= 16 KS)
+  int KS;                 // GEMM1 K steps of 16 (ceil((p + kEtaCols) / 16)): the p
+                          // covariates and the eta_ref / 2 columns
   int PN;                 // GEMM2 N (16 * ceil(p / 16))
   int N_pad;              // rows padded to a multiple of the 128-row chunk
   int J;                  // chunks per tile
@@ -196,8 +201,7 @@ struct TcArgs {
   int NS;                 // X pipeline stages
   int need_lo;            // accumulate the theta lo part too (FP32-accurate eta)
   int accurate;           // FP32 epilogue with log densities (else the bf16x2 fast path)
-  const __nv_bfloat16 *yc;// N_pad: y - 1/2 (zero for padded rows)
-  const float *eta_half;  // N_pad: eta_ref / 2 = x_n . theta_ref / 2 (0 for padded rows)
+  const float *yc;        // N_pad: y - 1/2 (zero for padded rows)
   const float *theta_ref; // d: the shadows hold (theta - theta_ref) / 2
   const double *ylin;     // (K + 1) x 2 x p: sums over the training / test rows of
                           // fold k of y_n x_n (bf16 X); k = K is the full data
@@ -299,6 +303,8 @@ __global__ void k_rhat_shuffle(const double *blk, int K, int L, int D, int R, un
 __global__ void k_theta_ref(int n, int d, int ld, const float *src, float *theta_ref);
 __global__ void k_eta_ref(int N, int N_pad, int p, int KP, const __nv_bfloat16 *X16, const float *theta_ref,
                           float *eta_half);
+__global__ void k_eta_fold(int N_pad, int p, int KP, const float *eta_half, __nv_bfloat16 *X16);
+__global__ void k_shadow_ones(int C_pad, int p, int KP, __nv_bfloat16 *hi);
 __global__ void k_accept(AcceptArgs a);
 __global__ void k_accumulate_given(Accum A, const double *s, int n, long long n0);
 __global__ void k_fd_adapt(FdAdaptArgs a);
