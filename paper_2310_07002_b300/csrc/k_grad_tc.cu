@@ -630,12 +630,75 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const size_t seg_stride = (size_t)wstride * kTM;
         const float eps = a.mode != MODE_NONE ? *a.eps : 0.0f;
         const float kick = a.mode == MODE_LAST_KICK ? 0.5f * eps : eps;
-        // (chain, dimension) items spread over all 256 epilogue threads so
-        // that many independent loads are in flight; consecutive items are
-        // consecutive dimensions of one chain (coalesced)
+        // (chain, 4 dimensions) items spread over all 256 epilogue threads,
+        // kFinU items per thread at a time with all their loads issued before
+        // any arithmetic: a serial item loop waited on every load in turn and
+        // took ~50 us per tile.  Consecutive items are consecutive
+        // dimensions of one chain (coalesced float4 accesses).
         const int p_ = pb.p;
-        for (int it = et; it < kTM * p_; it += 256) {
-          const int mm = it / p_, jj = it - mm * p_;
+        const bool vec = ((a.ld_theta | a.ld_grad) & 3) == 0 &&
+                         ((reinterpret_cast<uintptr_t>(a.theta) | reinterpret_cast<uintptr_t>(a.grad) |
+                           reinterpret_cast<uintptr_t>(a.r)) & 15) == 0;
+        const int nq = vec ? p_ >> 2 : 0;           // whole quads per chain
+        const bool kd = a.mode == MODE_KICK_DRIFT;
+        constexpr int kFinU = 4;
+        for (int i0 = et; i0 < kTM * nq; i0 += 256 * kFinU) {
+          float4 tv[kFinU], gs[kFinU], rv[kFinU], mv[kFinU], rf[kFinU];
+          int cc_[kFinU], jj_[kFinU];
+          bool ok[kFinU];
+#pragma unroll
+          for (int u = 0; u < kFinU; ++u) {
+            const int it = i0 + 256 * u;
+            const int mm = it / max(nq, 1);
+            jj_[u] = 4 * (it - mm * nq);
+            cc_[u] = t * kTM + mm;
+            ok[u] = it < kTM * nq && cc_[u] < a.C;
+            tv[u] = gs[u] = rv[u] = mv[u] = rf[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (ok[u]) {
+              tv[u] = *reinterpret_cast<const float4 *>(a.theta + (size_t)cc_[u] * a.ld_theta + jj_[u]);
+              for (int s2 = 0; s2 < nseg; ++s2) {
+                const float4 w = __ldcg(reinterpret_cast<const float4 *>(base + s2 * seg_stride +
+                                                                         (size_t)mm * wstride + jj_[u]));
+                gs[u].x += w.x; gs[u].y += w.y; gs[u].z += w.z; gs[u].w += w.w;
+              }
+              if (a.mode != MODE_NONE)
+                rv[u] = *reinterpret_cast<const float4 *>(a.r + (size_t)cc_[u] * a.ld_theta + jj_[u]);
+              if (kd) {
+                mv[u] = *reinterpret_cast<const float4 *>(a.minv + jj_[u]);
+                rf[u] = *reinterpret_cast<const float4 *>(ta.theta_ref + jj_[u]);
+              }
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kFinU; ++u) {
+            if (!ok[u]) continue;
+            const float4 g = make_float4(gs[u].x - tv[u].x * pb.beta_prec, gs[u].y - tv[u].y * pb.beta_prec,
+                                         gs[u].z - tv[u].z * pb.beta_prec, gs[u].w - tv[u].w * pb.beta_prec);
+            *reinterpret_cast<float4 *>(a.grad + (size_t)cc_[u] * a.ld_grad + jj_[u]) = g;
+            if (a.mode == MODE_NONE) continue;
+            const float4 r4 = make_float4(rv[u].x + kick * g.x, rv[u].y + kick * g.y, rv[u].z + kick * g.z,
+                                          rv[u].w + kick * g.w);
+            *reinterpret_cast<float4 *>(a.r + (size_t)cc_[u] * a.ld_theta + jj_[u]) = r4;
+            if (!kd) continue;
+            const float4 tn = make_float4(tv[u].x + eps * mv[u].x * r4.x, tv[u].y + eps * mv[u].y * r4.y,
+                                          tv[u].z + eps * mv[u].z * r4.z, tv[u].w + eps * mv[u].w * r4.w);
+            *reinterpret_cast<float4 *>(const_cast<float *>(a.theta) + (size_t)cc_[u] * a.ld_theta + jj_[u]) = tn;
+            // shadows hold (theta - ref) / 2 as bf16 hi + lo
+            const float h0 = 0.5f * (tn.x - rf[u].x), h1 = 0.5f * (tn.y - rf[u].y);
+            const float h2 = 0.5f * (tn.z - rf[u].z), h3 = 0.5f * (tn.w - rf[u].w);
+            const uint32_t hi01 = bf16x2_from(h0, h1), hi23 = bf16x2_from(h2, h3);
+            const float l0 = h0 - __uint_as_float(hi01 << 16), l1 = h1 - __uint_as_float(hi01 & 0xFFFF0000u);
+            const float l2 = h2 - __uint_as_float(hi23 << 16), l3 = h3 - __uint_as_float(hi23 & 0xFFFF0000u);
+            const size_t so = (size_t)cc_[u] * a.ld_shadow + jj_[u];
+            *reinterpret_cast<uint2 *>(a.shadow_hi + so) = make_uint2(hi01, hi23);
+            *reinterpret_cast<uint2 *>(a.shadow_lo + so) = make_uint2(bf16x2_from(l0, l1), bf16x2_from(l2, l3));
+          }
+        }
+        // the remaining dimensions (p mod 4 of every chain, or all of them
+        // when the caller's layout does not allow float4 access), one by one
+        const int j_s = 4 * nq, n_rem = p_ - j_s;
+        for (int it = et; it < kTM * n_rem; it += 256) {
+          const int mm = it / n_rem, jj = j_s + (it - mm * n_rem);
           const int cc = t * kTM + mm;
           if (cc >= a.C) break;
           float *th = const_cast<float *>(a.theta) + (size_t)cc * a.ld_theta;
@@ -648,7 +711,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             float *rr = a.r + (size_t)cc * a.ld_theta;
             const float rj = rr[jj] + kick * g;
             rr[jj] = rj;
-            if (a.mode == MODE_KICK_DRIFT) {
+            if (kd) {
               const float tn = tv + eps * a.minv[jj] * rj;
               th[jj] = tn;
               const float half = 0.5f * (tn - ta.theta_ref[jj]);   // shadows hold (theta - ref) / 2
@@ -675,6 +738,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           const float *th = a.theta + (size_t)cc * a.ld_theta;
           const double *yl = ta.ylin + (size_t)fold_of_chain(a, cc) * 2 * pb.p;
           double q = 0.0, lin_tr = 0.0, lin_te = 0.0;
+#pragma unroll 4
           for (int jj = 0; jj < pb.p; ++jj) {
             const double tv = (double)th[jj];
             q = fma(tv, tv, q);
