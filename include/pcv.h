@@ -66,7 +66,9 @@ typedef enum {
     PCV_FP32_SIMT = 0,      /* FP32 CUDA-core kernels */
     PCV_TF32 = 1,           /* tensor cores (mma.sync m16n8k8), TF32 in, FP32 accumulate;
                                flat models with p <= 112 */
-    PCV_BF16 = 2            /* tcgen05 tensor cores, BF16 in, FP32 accumulate */
+    PCV_BF16 = 2            /* tcgen05 tensor cores, BF16 X and parameter shadows in,
+                               FP32 accumulate; flat models (logistic, Gaussian linear,
+                               AR) with p <= 128 */
 } pcv_precision;
 
 /*

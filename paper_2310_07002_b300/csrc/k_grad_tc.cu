@@ -279,7 +279,7 @@ __host__ __device__ inline int owner_cta(long long u, long long U, long long n) 
 // KS (GEMM1 K steps of 16, = ceil(p / 16)) is a template parameter so that
 // every MMA group is straight-line code: MMAs issued from a runtime-count
 // loop between commits measured up to 3x slower on sm_103a.
-template <int KS, bool ACC>
+template <int KS, bool ACC, bool GAUSS>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_grad_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_hi,
               const __grid_constant__ CUtensorMap tm_lo, Problem pb, GradArgs a, TcArgs ta) {
@@ -473,7 +473,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const bool valid = c < a.C;
       FoldDesc fd = {0, 0, 0, 0};
       if (valid) fd = pb.folds[fold_of_chain(a, c)];
-      double sp_tr = 0.0, sp_te = 0.0;              // softplus sums (train, test rows)
+      // per-chain sums over the fold's training and test rows: softplus(eta)
+      // (logistic) or squared residuals (Gaussian models)
+      double sp_tr = 0.0, sp_te = 0.0;
+      // Gaussian models: 1 / sigma^2 of the chain (sigma known, or exp of the
+      // log sigma coordinate after beta; theta only moves in the finish)
+      float inv_s2 = 1.0f;
+      if constexpr (GAUSS) {
+        if (pb.variant == MV_GAUSS_LOGSIG)
+          inv_s2 = valid ? expf(-2.0f * a.theta[(size_t)c * a.ld_theta + pb.p]) : 1.0f;
+        else
+          inv_s2 = 1.0f / (pb.sigma_known * pb.sigma_known);
+      }
+      const bool need_e2 = GAUSS && (ACC || pb.variant == MV_GAUSS_LOGSIG);
       for (int i = ib + ((ib & 1) != eg ? 1 : 0); i < ie; i += 2) {
         const int j = j0 + (i - ib);
         if (!warp_wait(smem_u32(&s_full[sb]), (i >> 1) & 1, abort_flag, ta.err)) { aborted = true; break; }
@@ -486,51 +498,93 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // (16 bf16x2), plus the log-likelihood sums when ACC
         auto quarter = [&](const int qq, const uint32_t (&v)[32], uint32_t (&pk)[16]) {
           const int n0 = j * kTN + 32 * qq;
-          const float2 *yw = ywu + 16 * qq;     // y - 1/2 of rows 2k, 2k + 1
-          // residual y - sigmoid(eta) = (y - 1/2) - tanh(S)/2 in FP32, rounded
-          // to bf16 for the second GEMM (the same function on every leapfrog
-          // step). A bf16x2 tanh here would bias the gradient: its error is
-          // a smooth function of eta, so it adds up over rows instead of
-          // averaging out (a force error of ~6 % of the posterior scale per
-          // dimension at N = 1e5, which shrinks the adapted step size).
+          // staged response of rows 2k, 2k + 1: y - 1/2 (logistic) or y
+          const float2 *yw = ywu + 16 * qq;
+          if constexpr (!GAUSS) {
+            // residual y - sigmoid(eta) = (y - 1/2) - tanh(S)/2 in FP32, rounded
+            // to bf16 for the second GEMM (the same function on every leapfrog
+            // step). A bf16x2 tanh here would bias the gradient: its error is
+            // a smooth function of eta, so it adds up over rows instead of
+            // averaging out (a force error of ~6 % of the posterior scale per
+            // dimension at N = 1e5, which shrinks the adapted step size).
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const float2 y2 = yw[k];
-            const float ta = tanh_f32(__uint_as_float(v[2 * k]));
-            const float tb = tanh_f32(__uint_as_float(v[2 * k + 1]));
-            pk[k] = bf16x2_from(fmaf(-0.5f, ta, y2.x), fmaf(-0.5f, tb, y2.y));
-          }
-          if (valid && n0 < fd.excl_hi && n0 + 32 > fd.excl_lo) {
-#pragma unroll
-            for (int k = 0; k < 32; ++k) {
-              const int n = n0 + k;
-              if (n >= fd.excl_lo && n < fd.excl_hi) pk[k >> 1] &= (k & 1) ? 0x0000FFFFu : 0xFFFF0000u;
+            for (int k = 0; k < 16; ++k) {
+              const float2 y2 = yw[k];
+              const float ta = tanh_f32(__uint_as_float(v[2 * k]));
+              const float tb = tanh_f32(__uint_as_float(v[2 * k + 1]));
+              pk[k] = bf16x2_from(fmaf(-0.5f, ta, y2.x), fmaf(-0.5f, tb, y2.y));
             }
-          }
-          if constexpr (accurate) {
-            // log likelihood y eta - softplus(eta): the linear part is
-            // theta . sum(y x) per fold (added in the finish), so only
-            // softplus(eta) = max(eta, 0) + log(1 + exp(-|eta|)) is summed
-            // here, in FP32 per quarter and FP64 across quarters.
-            // Quarters clear of the fold's excluded rows and of the
-            // padding need no per-row mask.
-            if (n0 + 32 <= pb.N && (n0 + 32 <= fd.excl_lo || n0 >= fd.excl_hi)) {
-              float acc4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-              for (int k = 0; k < 32; ++k)
-                acc4[k & 3] += softplus_half(__uint_as_float(v[k]));
-              sp_tr += (double)((acc4[0] + acc4[1]) + (acc4[2] + acc4[3]));
-            } else {
-              float tr = 0.0f, te = 0.0f;
+            if (valid && n0 < fd.excl_hi && n0 + 32 > fd.excl_lo) {
 #pragma unroll
               for (int k = 0; k < 32; ++k) {
                 const int n = n0 + k;
-                const float sp = softplus_half(__uint_as_float(v[k]));
-                if (n < pb.N && (n < fd.excl_lo || n >= fd.excl_hi)) tr += sp;
-                if (n >= fd.test_lo && n < fd.test_hi) te += sp;
+                if (n >= fd.excl_lo && n < fd.excl_hi) pk[k >> 1] &= (k & 1) ? 0x0000FFFFu : 0xFFFF0000u;
               }
-              sp_tr += (double)tr;
-              sp_te += (double)te;
+            }
+            if constexpr (accurate) {
+              // log likelihood y eta - softplus(eta): the linear part is
+              // theta . sum(y x) per fold (added in the finish), so only
+              // softplus(eta) = max(eta, 0) + log(1 + exp(-|eta|)) is summed
+              // here, in FP32 per quarter and FP64 across quarters.
+              // Quarters clear of the fold's excluded rows and of the
+              // padding need no per-row mask.
+              if (n0 + 32 <= pb.N && (n0 + 32 <= fd.excl_lo || n0 >= fd.excl_hi)) {
+                float acc4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+                for (int k = 0; k < 32; ++k)
+                  acc4[k & 3] += softplus_half(__uint_as_float(v[k]));
+                sp_tr += (double)((acc4[0] + acc4[1]) + (acc4[2] + acc4[3]));
+              } else {
+                float tr = 0.0f, te = 0.0f;
+#pragma unroll
+                for (int k = 0; k < 32; ++k) {
+                  const int n = n0 + k;
+                  const float sp = softplus_half(__uint_as_float(v[k]));
+                  if (n < pb.N && (n < fd.excl_lo || n >= fd.excl_hi)) tr += sp;
+                  if (n >= fd.test_lo && n < fd.test_hi) te += sp;
+                }
+                sp_tr += (double)tr;
+                sp_te += (double)te;
+              }
+            }
+
+          } else {
+            // Gaussian: residual (y - eta) / sigma^2 with eta = 2 S, rounded
+            // to bf16; the squared residuals of the fold's training and test
+            // rows feed the log sigma gradient and the log densities
+            float e[32];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              const float2 y2 = yw[k];
+              e[2 * k] = fmaf(-2.0f, __uint_as_float(v[2 * k]), y2.x);
+              e[2 * k + 1] = fmaf(-2.0f, __uint_as_float(v[2 * k + 1]), y2.y);
+              pk[k] = bf16x2_from(e[2 * k] * inv_s2, e[2 * k + 1] * inv_s2);
+            }
+            if (valid && n0 < fd.excl_hi && n0 + 32 > fd.excl_lo) {
+#pragma unroll
+              for (int k = 0; k < 32; ++k) {
+                const int n = n0 + k;
+                if (n >= fd.excl_lo && n < fd.excl_hi) pk[k >> 1] &= (k & 1) ? 0x0000FFFFu : 0xFFFF0000u;
+              }
+            }
+            if (need_e2) {
+              if (n0 + 32 <= pb.N && (n0 + 32 <= fd.excl_lo || n0 >= fd.excl_hi)) {
+                float acc4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+                for (int k = 0; k < 32; ++k) acc4[k & 3] = fmaf(e[k], e[k], acc4[k & 3]);
+                sp_tr += (double)((acc4[0] + acc4[1]) + (acc4[2] + acc4[3]));
+              } else {
+                float tr = 0.0f, te = 0.0f;
+#pragma unroll
+                for (int k = 0; k < 32; ++k) {
+                  const int n = n0 + k;
+                  const float e2 = e[k] * e[k];
+                  if (n < pb.N && (n < fd.excl_lo || n >= fd.excl_hi)) tr += e2;
+                  if (n >= fd.test_lo && n < fd.test_hi) te += e2;
+                }
+                sp_tr += (double)tr;
+                sp_te += (double)te;
+              }
             }
           }
         };
@@ -721,9 +775,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
           }
         }
-        if (a.need_ll && et < kTM && t * kTM + et < a.C) {
-          const int cc = t * kTM + et;
-          double s0 = 0.0, s1 = 0.0;                // softplus sums over train / test rows
+        // per-chain row sums of the segments (softplus or squared residuals)
+        const bool need_sums = a.need_ll || (GAUSS && pb.variant == MV_GAUSS_LOGSIG);
+        double s0 = 0.0, s1 = 0.0;                  // over the training / test rows
+        const int cc = t * kTM + et;
+        if (need_sums && et < kTM && cc < a.C) {
           for (int s2 = 0; s2 < nseg; ++s2) {
             const float *ws2 = base + s2 * seg_stride + (size_t)et * wstride + ta.PN;
 #pragma unroll
@@ -732,22 +788,67 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               s1 += (double)__ldcg(ws2 + 4 * g2 + 2) + (double)__ldcg(ws2 + 4 * g2 + 3);
             }
           }
-          // linear part theta . sum(y x) and the log prior, in a fixed order
+        }
+        if constexpr (GAUSS) {
+          // log sigma (after beta), sigma ~ half-N(0, sd^2):
+          // d/dlog sigma = sum_train (e^2 / sigma^2 - 1) - sigma^2 / sd^2 + 1
+          if (pb.variant == MV_GAUSS_LOGSIG && et < kTM && cc < a.C) {
+            const FoldDesc f = pb.folds[fold_of_chain(a, cc)];
+            const double n_tr = (double)(pb.N - (f.excl_hi - f.excl_lo));
+            float *th = const_cast<float *>(a.theta) + (size_t)cc * a.ld_theta;
+            const float ls = th[pb.p];
+            const float s2v = expf(2.0f * ls), is2 = expf(-2.0f * ls);
+            const float g = (float)((double)is2 * s0 - n_tr) - s2v * pb.sigma_prec + 1.0f;
+            a.grad[(size_t)cc * a.ld_grad + pb.p] = g;
+            if (a.mode != MODE_NONE) {
+              float *rr = a.r + (size_t)cc * a.ld_theta;
+              const float rj = rr[pb.p] + kick * g;
+              rr[pb.p] = rj;
+              if (kd) th[pb.p] = ls + eps * a.minv[pb.p] * rj;
+            }
+          }
+        }
+        if (a.need_ll && et < kTM && cc < a.C) {
           // (theta is not moved on the steps that need log densities, so it
           // is the evaluation point)
           const float *th = a.theta + (size_t)cc * a.ld_theta;
-          const double *yl = ta.ylin + (size_t)fold_of_chain(a, cc) * 2 * pb.p;
-          double q = 0.0, lin_tr = 0.0, lin_te = 0.0;
+          if constexpr (!GAUSS) {
+            // linear part theta . sum(y x) and the log prior, in a fixed order
+            const double *yl = ta.ylin + (size_t)fold_of_chain(a, cc) * 2 * pb.p;
+            double q = 0.0, lin_tr = 0.0, lin_te = 0.0;
 #pragma unroll 4
-          for (int jj = 0; jj < pb.p; ++jj) {
-            const double tv = (double)th[jj];
-            q = fma(tv, tv, q);
-            lin_tr = fma(tv, yl[jj], lin_tr);
-            lin_te = fma(tv, yl[pb.p + jj], lin_te);
+            for (int jj = 0; jj < pb.p; ++jj) {
+              const double tv = (double)th[jj];
+              q = fma(tv, tv, q);
+              lin_tr = fma(tv, yl[jj], lin_tr);
+              lin_te = fma(tv, yl[pb.p + jj], lin_te);
+            }
+            const double lprior = (double)pb.p * (-0.5 * kLog2PiD - (double)pb.log_beta_sd) - 0.5 * pb.beta_prec * q;
+            a.logp[cc] = (lin_tr - s0) + lprior;
+            a.shat[cc] = lin_te - s1;
+          } else {
+            // sum of -log(2 pi)/2 - log sigma - e^2 / (2 sigma^2) over the
+            // fold's training / test rows, and the log priors
+            double q = 0.0;
+#pragma unroll 4
+            for (int jj = 0; jj < pb.p; ++jj) q = fma((double)th[jj], (double)th[jj], q);
+            double lprior = (double)pb.p * (-0.5 * kLog2PiD - (double)pb.log_beta_sd) - 0.5 * pb.beta_prec * q;
+            double ls, is2;
+            if (pb.variant == MV_GAUSS_LOGSIG) {
+              const float lsf = th[pb.p];
+              const float s2v = expf(2.0f * lsf);
+              ls = (double)lsf;
+              is2 = (double)expf(-2.0f * lsf);
+              lprior += kLog2D - 0.5 * kLog2PiD - pb.log_sigma_sd - 0.5 * (double)s2v * pb.sigma_prec + ls;
+            } else {
+              ls = (double)logf(pb.sigma_known);
+              is2 = (double)(1.0f / (pb.sigma_known * pb.sigma_known));
+            }
+            const FoldDesc f = pb.folds[fold_of_chain(a, cc)];
+            const double n_tr = (double)(pb.N - (f.excl_hi - f.excl_lo)), n_te = (double)(f.test_hi - f.test_lo);
+            a.logp[cc] = -0.5 * is2 * s0 - n_tr * (0.5 * kLog2PiD + ls) + lprior;
+            a.shat[cc] = -0.5 * is2 * s1 - n_te * (0.5 * kLog2PiD + ls);
           }
-          const double lprior = (double)pb.p * (-0.5 * kLog2PiD - (double)pb.log_beta_sd) - 0.5 * pb.beta_prec * q;
-          a.logp[cc] = (lin_tr - s0) + lprior;
-          a.shat[cc] = lin_te - s1;
         }
       }
       // next segment starts at chunk 0 of the next tile
@@ -794,9 +895,14 @@ int tc_segments_per_tile(int T, int J, int n_cta) {
 
 template <int KS>
 static cudaError_t set_smem_attr() {
-  cudaError_t e = cudaFuncSetAttribute(k_grad_tc<KS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  cudaError_t e2 = cudaFuncSetAttribute(k_grad_tc<KS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  return e != cudaSuccess ? e : e2;
+  const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t r[4] = {cudaFuncSetAttribute(k_grad_tc<KS, false, false>, at, 227 * 1024),
+                      cudaFuncSetAttribute(k_grad_tc<KS, true, false>, at, 227 * 1024),
+                      cudaFuncSetAttribute(k_grad_tc<KS, false, true>, at, 227 * 1024),
+                      cudaFuncSetAttribute(k_grad_tc<KS, true, true>, at, 227 * 1024)};
+  for (cudaError_t x : r)
+    if (x != cudaSuccess) return x;
+  return cudaSuccess;
 }
 
 // setmaxnreg.inc waits until the CTA's register pool can grant the request:
@@ -807,10 +913,15 @@ static bool g_tc_regs_ok = false;
 template <int KS>
 static bool regs_fit() {
   const long need = 128L * kTcRegsProducer + 256L * kTcRegsEpilogue;
-  cudaFuncAttributes fa, fb;
-  if (cudaFuncGetAttributes(&fa, k_grad_tc<KS, false>) != cudaSuccess) return false;
-  if (cudaFuncGetAttributes(&fb, k_grad_tc<KS, true>) != cudaSuccess) return false;
-  return (long)fa.numRegs * kTcThreads >= need && (long)fb.numRegs * kTcThreads >= need;
+  cudaFuncAttributes fa[4];
+  if (cudaFuncGetAttributes(&fa[0], k_grad_tc<KS, false, false>) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa[1], k_grad_tc<KS, true, false>) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa[2], k_grad_tc<KS, false, true>) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa[3], k_grad_tc<KS, true, true>) != cudaSuccess)
+    return false;
+  for (const cudaFuncAttributes &f : fa)
+    if ((long)f.numRegs * kTcThreads < need) return false;
+  return true;
 }
 
 // once per context (outside any stream capture): allow the large dynamic SMEM
@@ -831,11 +942,18 @@ cudaError_t launch_grad_tc(const CUtensorMap &tm_x, const CUtensorMap &tm_hi, co
   const size_t smem = tc_smem_bytes(ta.KP, ta.NS, ta.need_lo, pb.p);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   if (!g_tc_regs_ok) return cudaErrorInvalidConfiguration;   // tc_prepare not run, or the split does not fit
+  if (pb.variant == MV_HIER) return cudaErrorInvalidValue;
+  const bool gauss = pb.variant == MV_GAUSS_KNOWN || pb.variant == MV_GAUSS_LOGSIG;
   switch (ta.KS) {
 #define PCV_TC_CASE(K)                                                                          \
   case K:                                                                                       \
-    if (ta.accurate) k_grad_tc<K, true><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta); \
-    else k_grad_tc<K, false><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta);            \
+    if (gauss) {                                                                                \
+      if (ta.accurate) k_grad_tc<K, true, true><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta); \
+      else k_grad_tc<K, false, true><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta);           \
+    } else {                                                                                    \
+      if (ta.accurate) k_grad_tc<K, true, false><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta); \
+      else k_grad_tc<K, false, false><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta);           \
+    }                                                                                           \
     break;
     PCV_TC_CASE(1) PCV_TC_CASE(2) PCV_TC_CASE(3) PCV_TC_CASE(4)
     PCV_TC_CASE(5) PCV_TC_CASE(6) PCV_TC_CASE(7) PCV_TC_CASE(8) PCV_TC_CASE(9)

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(256) k_begin(BeginArgs a) {
       const float tn = th[j] + eps * mv * rh;
       a.r[(size_t)c * a.ld + j] = rh;
       a.theta_p[(size_t)c * a.ld + j] = tn;
-      if (a.shadow_hi) {                     // bf16 hi + lo of theta / 2 (tensor-core operand)
+      if (a.shadow_hi && j < a.shadow_d) {   // bf16 hi + lo of theta / 2 (tensor-core operand)
         const float half = 0.5f * (tn - a.theta_ref[j]);
         const __nv_bfloat16 hi = __float2bfloat16_rn(half);
         a.shadow_hi[(size_t)c * a.ld_shadow + j] = hi;

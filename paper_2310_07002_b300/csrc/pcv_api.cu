@@ -415,8 +415,9 @@ pcv_status tune(pcv_ctx *x, ChainBufs &cb) {
 // write the bf16 shadow of a chain set's current positions (tensor-core path)
 pcv_status write_shadow(pcv_ctx *x, ChainBufs &cb, const float *theta, int ld) {
   if (!x->tc) return PCV_OK;
-  const long long T = (long long)cb.C * x->d;
-  k_shadow<<<(unsigned)((T + 255) / 256), 256, 0, x->stream>>>(cb.C, x->d, ld, theta, x->theta_ref, cb.shadow_hi,
+  const long long T = (long long)cb.C * x->p;
+  // beta only: a log sigma coordinate has no tensor-core operand column
+  k_shadow<<<(unsigned)((T + 255) / 256), 256, 0, x->stream>>>(cb.C, x->p, ld, theta, x->theta_ref, cb.shadow_hi,
                                                               cb.shadow_lo, x->KP);
   CK(cudaGetLastError());
   return PCV_OK;
@@ -467,6 +468,7 @@ pcv_status launch_iteration(pcv_ctx *x, ChainBufs &cb, bool fd, bool accumulate)
   ba.shadow_hi = x->tc ? cb.shadow_hi : nullptr;
   ba.shadow_lo = x->tc ? cb.shadow_lo : nullptr;
   ba.ld_shadow = x->KP;
+  ba.shadow_d = x->p;
   ba.theta_ref = x->theta_ref;
   k_begin<<<(cb.C + 7) / 8, 256, 0, x->stream>>>(ba);
   CK(cudaGetLastError());
@@ -699,8 +701,9 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
   x->tf32 = opt->precision == PCV_TF32;
   if (x->tf32 && (model->kind == PCV_HIER_GAUSS || p > 112))
     return bail(PCV_E_UNSUPPORTED, "the TF32 path covers the flat models with p <= 112");
-  if (x->tc && (model->kind != PCV_LOGISTIC || p > 128))
-    return bail(PCV_E_UNSUPPORTED, "the BF16 tensor-core path covers LOGISTIC with p <= 128");
+  if (x->tc && (model->kind == PCV_HIER_GAUSS || p > 128))
+    return bail(PCV_E_UNSUPPORTED, "the BF16 tensor-core path covers the flat models (logistic, Gaussian linear, "
+                                   "AR) with p <= 128");
   // model variant and dimension
   if (x->kind == PCV_LOGISTIC) { x->variant = MV_LOGISTIC; x->d = p; }
   else if (x->kind == PCV_HIER_GAUSS) {
@@ -825,7 +828,7 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
     std::vector<float> hyc((size_t)x->N_pad, 0.0f);
     for (int64_t r = 0; r < N; ++r) {
       for (int j = 0; j < p; ++j) hX16[(size_t)r * x->KP + j] = __float2bfloat16_rn(hX[(size_t)r * x->p_pad + j]);
-      hyc[r] = hy[r] - 0.5f;
+      hyc[r] = x->kind == PCV_LOGISTIC ? hy[r] - 0.5f : hy[r];   // the staged response
     }
     // per fold: sum over training rows and over test rows of y_n x_n, with
     // the bf16 X the tensor cores see (the linear part of the logistic log
@@ -837,9 +840,9 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
         for (int j = 0; j < p; ++j) dst[j] += (double)__bfloat162float(hX16[(size_t)r * x->KP + j]);
       }
     };
-    add_rows(all.data(), 0, N);
     std::vector<double> ex(p);
-    for (int k = 0; k <= K; ++k) {
+    if (x->kind == PCV_LOGISTIC) add_rows(all.data(), 0, N);
+    for (int k = 0; k <= K && x->kind == PCV_LOGISTIC; ++k) {
       double *tr = &hyl[(size_t)k * 2 * p], *te = tr + p;
       std::fill(ex.begin(), ex.end(), 0.0);
       add_rows(ex.data(), fds[k].excl_lo, fds[k].excl_hi);
@@ -1230,6 +1233,7 @@ pcv_status pcv_trajectory(pcv_ctx *x, const float *theta0, const float *r0, int3
   ba.shadow_hi = x->tc ? cb.shadow_hi : nullptr;
   ba.shadow_lo = x->tc ? cb.shadow_lo : nullptr;
   ba.ld_shadow = x->KP;
+  ba.shadow_d = x->p;
   ba.theta_ref = x->theta_ref;
   k_begin<<<(cb.C + 7) / 8, 256, 0, x->stream>>>(ba);
   CK(cudaGetLastError());

@@ -239,6 +239,7 @@ struct BeginArgs {
   const float *r_given;         // optional start momenta instead of drawing (C x ld)
   __nv_bfloat16 *shadow_hi, *shadow_lo;
   int ld_shadow;
+  int shadow_d;                 // leading coordinates with a shadow (beta: p)
   const float *theta_ref;       // shadows hold (theta_p - theta_ref) / 2
 };
 

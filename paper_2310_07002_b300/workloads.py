@@ -110,12 +110,15 @@ def _sigmoid(x):
 
 
 def gauss_blocks(N: int = 200, p: int = 5, K: int = 10, L: int = 4,
-                 seed: int = 1001) -> Workload:
+                 seed: int = 1001, bf16: bool = False) -> Workload:
     """Conjugate Gaussian linear regression, sigma = 1 known, beta ~ N(0, 10^2 I),
     K contiguous blocks held out.  Sampler: eps = 0.05, 16 leapfrog steps,
-    identity mass, 500 warmup + 1000 draws."""
+    identity mass, 500 warmup + 1000 draws.  bf16=True rounds X to bfloat16
+    values (y is drawn from the rounded X)."""
     g = _rng(seed)
     X = g.standard_normal((N, p))
+    if bf16:
+        X = round_to_bf16(X)
     beta = g.standard_normal(p)
     y = X @ beta + g.standard_normal(N)
     fold = (np.arange(N) * K // N).astype(np.int32)

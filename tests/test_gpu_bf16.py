@@ -126,3 +126,98 @@ def test_bf16_and_fp32_runs_agree_within_mcse(torch):
     assert zt < 4.0
     assert z.max() < 5.0 and z.mean() < 1.3
     assert d16["rhat_max"] < 1.1 and a16.mean() > 0.5
+
+
+def gauss_bf16_workloads():
+    import dataclasses
+    return {
+        # sigma known, p = 5: 9 row chunks with a ragged tail, 75 chains
+        "gauss": W.gauss_blocks(N=1037, p=5, K=15, L=5, bf16=True),
+        # log sigma sampled (the coordinate after beta), p = 40
+        "gauss_logsig_p40": dataclasses.replace(W.gauss_blocks(N=1037, p=40, K=15, L=5, bf16=True),
+                                                sigma_known=-1.0, sigma_prior_sd=1.0),
+        # AR(2) on a bf16 lagged design, hv-blocks (training rows excluded on
+        # both sides of every test block), rows in time order
+        "ar2": W.ar2_hvblock(T=1302, K=40, L=2, bf16=True),
+    }
+
+
+@pytest.mark.parametrize("name", ["gauss", "gauss_logsig_p40", "ar2"])
+def test_bf16_gaussian_log_density_and_gradient(torch, orc, name):
+    from paper_2310_07002_b300.pcv import PCV, BF16
+    w = gauss_bf16_workloads()[name]
+    pc = PCV.from_workload(w, precision=BF16)
+    prob = orc.problem_from_workload(w)
+    n = 300                                       # 128 + 128 + 44 positions
+    tt = torch.tensor(W.random_theta(w.dim, n, scale=0.3, seed=23), dtype=torch.float32, device="cuda")
+    folds = np.arange(n) % (w.K + 1)
+    fo = torch.tensor(folds, dtype=torch.int32, device="cuda")
+    lp, g, sh = pc.log_density(tt, fo, BF16)
+    torch.cuda.synchronize()
+    lp, g, sh = lp.cpu().numpy(), g.cpu().double().numpy(), sh.cpu().numpy()
+    th = tt.cpu().double().numpy()
+    lr = np.empty(n); sr = np.empty(n); gr = np.empty((n, w.dim))
+    for i in range(n):
+        k = int(folds[i])
+        lr[i], gr[i], sr[i] = orc.log_density(prob, -1 if k == w.K else k, th[i])
+    e_lp, e_sh, e_g = rel_scalar(lp, lr).max(), rel_scalar(sh, sr).max(), rel_vec(g, gr).max()
+    print("bf16 %s: logp %.2e shat %.2e grad %.2e" % (name, e_lp, e_sh, e_g))
+    assert e_lp <= 1e-4 and e_sh <= 1e-4
+    assert e_g <= 1e-2
+    pc.close()
+
+
+@pytest.mark.parametrize("name", ["gauss", "gauss_logsig_p40", "ar2"])
+def test_bf16_gaussian_trajectory(torch, orc, name):
+    from paper_2310_07002_b300.pcv import PCV, BF16
+    w = gauss_bf16_workloads()[name]
+    eps = {"gauss": 0.01, "gauss_logsig_p40": 0.002, "ar2": 0.005}[name]
+    minv = np.ones(w.dim)
+    pc = PCV.from_workload(w, precision=BF16, step_size=eps, inv_mass_diag=minv)
+    prob = orc.problem_from_workload(w)
+    g = np.random.Generator(np.random.Philox(7))
+    th0 = 0.2 * g.standard_normal((w.n_chains, w.dim))
+    r0 = g.standard_normal((w.n_chains, w.dim))
+    t0 = torch.tensor(th0, dtype=torch.float32, device="cuda")
+    rr0 = torch.tensor(r0, dtype=torch.float32, device="cuda")
+    th1, r1, lp1, _ = pc.trajectory(t0, rr0, BF16)
+    th1, r1, lp1 = th1.cpu().double().numpy(), r1.cpu().double().numpy(), lp1.cpu().numpy()
+    a0, b0 = t0.cpu().double().numpy(), rr0.cpu().double().numpy()
+    ref_th = np.empty_like(th1); ref_r = np.empty_like(r1); ref_lp = np.empty(w.n_chains)
+    for c in range(w.n_chains):
+        k = c // w.chains_per_fold
+        _, g0, _ = orc.log_density(prob, k, a0[c])
+        ref_th[c], ref_r[c], _, ref_lp[c], _ = orc.trajectory(prob, k, np.float32(eps), w.leapfrog_steps,
+                                                             minv, a0[c], b0[c], g0)
+    e_th, e_r, e_lp = rel_vec(th1, ref_th).max(), rel_vec(r1, ref_r).max(), rel_scalar(lp1, ref_lp).max()
+    print("bf16 trajectory %s: theta %.2e r %.2e logp %.2e" % (name, e_th, e_r, e_lp))
+    assert e_th <= 2e-2 and e_r <= 2e-2
+    pc.close()
+
+
+def test_bf16_and_fp32_ar2_runs_agree_within_mcse(torch):
+    # AR(2) hv-block CV on a bf16 lagged design, sampled with the BF16
+    # tensor-core path and with the FP32 kernels (same data on both sides)
+    from paper_2310_07002_b300.pcv import PCV, BF16, FP32_SIMT
+    w = W.ar2_hvblock(T=1302, K=40, L=8, bf16=True)
+    out = {}
+    for prec in (FP32_SIMT, BF16):
+        pc = PCV.from_workload(w, precision=prec)
+        pc.warmup(300, 300)
+        pc.sample(2000)
+        out[prec] = (pc.scores(), pc.diagnostics(), pc.accept_rate())
+        pc.close()
+    s32, d32, a32 = out[FP32_SIMT]
+    s16, d16, a16 = out[BF16]
+
+    def mcse(s, d):
+        return s["mcse"] * np.sqrt(np.maximum(1.0, d["ess_bm"] / d["ess_acov"]))
+
+    comb = np.sqrt(mcse(s32, d32) ** 2 + mcse(s16, d16) ** 2)
+    z = np.abs(s32["elpd"] - s16["elpd"]) / comb
+    zt = abs(s32["elpd_total"] - s16["elpd_total"]) / np.sqrt(s32["mcse_total"] ** 2 + s16["mcse_total"] ** 2)
+    print("ar2 fold max z %.2f mean z %.2f, total z %.2f, rhat_max fp32 %.4f bf16 %.4f, accept %.3f %.3f" %
+          (z.max(), z.mean(), zt, d32["rhat_max"], d16["rhat_max"], a32.mean(), a16.mean()))
+    assert zt < 4.0
+    assert z.max() < 5.0 and z.mean() < 1.3
+    assert d16["rhat_max"] < 1.1 and a16.mean() > 0.5
