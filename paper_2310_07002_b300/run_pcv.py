@@ -31,6 +31,8 @@ WORKLOADS = {
     "logistic_loo_bf16x": lambda: W.logistic_loo(bf16=True),
     "hier_logo": lambda: W.hier_logo(),
     "ar2_hvblock": lambda: W.ar2_hvblock(),
+    # lagged design rounded to bf16 values for both precisions (arithmetic only)
+    "ar2_hvblock_bf16x": lambda: W.ar2_hvblock(bf16=True),
     "logistic_large": lambda: W.logistic_large(),
 }
 
