@@ -816,47 +816,68 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
   enter(x);
 
   // device data
-  std::vector<float> hX((size_t)N * x->p_pad, 0.0f), hy(N);
+  // y and the row permutation on the host; X goes to the device as the
+  // caller laid it out and is gathered into the fold-sorted layout there
+  // (as are its bf16 copy and the per-fold sums of the tensor-core path)
+  std::vector<float> hy(N);
+  std::vector<int> hperm(N);
   for (int64_t r = 0; r < N; ++r) {
     const int64_t i = x->perm[r];
-    std::memcpy(&hX[(size_t)r * x->p_pad], X + i * p, sizeof(float) * p);
     hy[r] = y[i];
+    hperm[r] = (int)i;
   }
+  if (!dalloc_n(x, &x->X, (size_t)N * x->p_pad) || !dalloc_n(x, &x->y, (size_t)N) ||
+      !dalloc_n(x, &x->folds, (size_t)K + 1) || !dalloc_n(x, &x->minv, (size_t)x->d_pad) ||
+      !dalloc_n(x, &x->st, 1) || !dalloc_n(x, &x->wmean, (size_t)x->d) || !dalloc_n(x, &x->wM2, (size_t)x->d) ||
+      !dalloc_n(x, &x->pool, (size_t)x->n_fd_draws * kNumFdChains * x->d_pad) ||
+      !dalloc_n(x, &x->fold_out, (size_t)K * F_NFIELDS) || !dalloc_n(x, &x->tot_out, (size_t)T_NFIELDS) ||
+      !dalloc_n(x, &x->fin_scratch, (size_t)K * (4 * x->L + 2 * (x->M + 2))))
+    return bail(PCV_E_OOM, "device allocation failed");
+  {
+    float *xraw = nullptr;
+    int *dperm = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void **>(&xraw), sizeof(float) * (size_t)N * p, x->stream) != cudaSuccess)
+      return bail(PCV_E_OOM, "staging allocation failed");
+    if (cudaMallocAsync(reinterpret_cast<void **>(&dperm), sizeof(int) * (size_t)N, x->stream) != cudaSuccess) {
+      cudaFreeAsync(xraw, x->stream);
+      return bail(PCV_E_OOM, "staging allocation failed");
+    }
+    cudaMemcpyAsync(xraw, X, sizeof(float) * (size_t)N * p, cudaMemcpyHostToDevice, x->stream);
+    cudaMemcpyAsync(dperm, hperm.data(), sizeof(int) * (size_t)N, cudaMemcpyHostToDevice, x->stream);
+    const long long items = (long long)N * p;
+    k_gather_rows<<<(unsigned)((items + 255) / 256), 256, 0, x->stream>>>(N, p, x->p_pad, dperm, xraw, x->X);
+    cudaFreeAsync(xraw, x->stream);
+    cudaFreeAsync(dperm, x->stream);
+    if (cudaGetLastError() != cudaSuccess) return bail(PCV_E_CUDA, "row gather failed");
+  }
+  cudaMemcpyAsync(x->y, hy.data(), hy.size() * sizeof(float), cudaMemcpyHostToDevice, x->stream);
+  cudaMemcpyAsync(x->folds, fds.data(), fds.size() * sizeof(FoldDesc), cudaMemcpyHostToDevice, x->stream);
   if (x->tc) {
-    // bf16 design matrix [N_pad x KP] (round to nearest even) and y - 1/2
-    std::vector<__nv_bfloat16> hX16((size_t)x->N_pad * x->KP, __float2bfloat16_rn(0.0f));
+    // bf16 design matrix [N_pad x KP] (round to nearest even; padding rows
+    // and columns stay 0) and the staged response
     std::vector<float> hyc((size_t)x->N_pad, 0.0f);
-    for (int64_t r = 0; r < N; ++r) {
-      for (int j = 0; j < p; ++j) hX16[(size_t)r * x->KP + j] = __float2bfloat16_rn(hX[(size_t)r * x->p_pad + j]);
-      hyc[r] = x->kind == PCV_LOGISTIC ? hy[r] - 0.5f : hy[r];   // the staged response
-    }
-    // per fold: sum over training rows and over test rows of y_n x_n, with
-    // the bf16 X the tensor cores see (the linear part of the logistic log
-    // likelihood is theta . these sums); fold K is the full data
-    std::vector<double> hyl((size_t)(K + 1) * 2 * p, 0.0), all(p, 0.0);
-    auto add_rows = [&](double *dst, int64_t r0, int64_t r1) {
-      for (int64_t r = r0; r < r1; ++r) {
-        if (hy[r] == 0.0f) continue;
-        for (int j = 0; j < p; ++j) dst[j] += (double)__bfloat162float(hX16[(size_t)r * x->KP + j]);
-      }
-    };
-    std::vector<double> ex(p);
-    if (x->kind == PCV_LOGISTIC) add_rows(all.data(), 0, N);
-    for (int k = 0; k <= K && x->kind == PCV_LOGISTIC; ++k) {
-      double *tr = &hyl[(size_t)k * 2 * p], *te = tr + p;
-      std::fill(ex.begin(), ex.end(), 0.0);
-      add_rows(ex.data(), fds[k].excl_lo, fds[k].excl_hi);
-      add_rows(te, fds[k].test_lo, fds[k].test_hi);
-      for (int j = 0; j < p; ++j) tr[j] = all[j] - ex[j];
-    }
-    if (!dalloc_n(x, &x->X16, hX16.size()) || !dalloc_n(x, &x->ycf, hyc.size()) ||
-        !dalloc_n(x, &x->ylin, hyl.size()) || !dalloc_n(x, &x->theta_ref, (size_t)x->d_pad) ||
+    for (int64_t r = 0; r < N; ++r) hyc[r] = x->kind == PCV_LOGISTIC ? hy[r] - 0.5f : hy[r];
+    if (!dalloc_n(x, &x->X16, (size_t)x->N_pad * x->KP) || !dalloc_n(x, &x->ycf, hyc.size()) ||
+        !dalloc_n(x, &x->ylin, (size_t)(K + 1) * 2 * p) || !dalloc_n(x, &x->theta_ref, (size_t)x->d_pad) ||
         !dalloc_n(x, &x->eta_half, (size_t)x->N_pad))
       return bail(PCV_E_OOM, "device allocation failed");
-    cudaMemcpyAsync(x->ylin, hyl.data(), hyl.size() * sizeof(double), cudaMemcpyHostToDevice, x->stream);
-    cudaMemcpyAsync(x->X16, hX16.data(), hX16.size() * 2, cudaMemcpyHostToDevice, x->stream);
+    const long long items = (long long)N * p;
+    k_x_bf16<<<(unsigned)((items + 255) / 256), 256, 0, x->stream>>>(N, p, x->p_pad, x->KP, x->X, x->X16);
     cudaMemcpyAsync(x->ycf, hyc.data(), hyc.size() * sizeof(float), cudaMemcpyHostToDevice, x->stream);
-    if (cudaStreamSynchronize(x->stream) != cudaSuccess) return bail(PCV_E_CUDA, "upload failed");
+    if (x->kind == PCV_LOGISTIC) {
+      // per fold: sum over training rows and over test rows of y_n x_n, with
+      // the bf16 X the tensor cores see (the linear part of the logistic log
+      // likelihood is theta . these sums); fold K is the full data
+      double *all = nullptr;
+      if (cudaMallocAsync(reinterpret_cast<void **>(&all), sizeof(double) * p, x->stream) != cudaSuccess)
+        return bail(PCV_E_OOM, "staging allocation failed");
+      k_ylin_all<<<p, 256, 0, x->stream>>>((int)N, x->KP, x->X16, x->y, all);
+      k_ylin_folds<<<((K + 1) * p + 255) / 256, 256, 0, x->stream>>>(K, p, x->KP, x->X16, x->y, x->folds, all,
+                                                                     x->ylin);
+      cudaFreeAsync(all, x->stream);
+    }
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(x->stream) != cudaSuccess)
+      return bail(PCV_E_CUDA, "upload failed");
     if (!encode_bf16_map(&x->tm_x, x->X16, x->N_pad, x->KP))
       return bail(PCV_E_CUDA, "cuTensorMapEncodeTiled failed for X");
     if (tc_prepare() != cudaSuccess) return bail(PCV_E_CUDA, "cudaFuncSetAttribute failed");
@@ -864,16 +885,6 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&x->n_sm, cudaDevAttrMultiProcessorCount, dev);
   }
-  if (!dalloc_n(x, &x->X, hX.size()) || !dalloc_n(x, &x->y, (size_t)N) ||
-      !dalloc_n(x, &x->folds, (size_t)K + 1) || !dalloc_n(x, &x->minv, (size_t)x->d_pad) ||
-      !dalloc_n(x, &x->st, 1) || !dalloc_n(x, &x->wmean, (size_t)x->d) || !dalloc_n(x, &x->wM2, (size_t)x->d) ||
-      !dalloc_n(x, &x->pool, (size_t)x->n_fd_draws * kNumFdChains * x->d_pad) ||
-      !dalloc_n(x, &x->fold_out, (size_t)K * F_NFIELDS) || !dalloc_n(x, &x->tot_out, (size_t)T_NFIELDS) ||
-      !dalloc_n(x, &x->fin_scratch, (size_t)K * (4 * x->L + 2 * (x->M + 2))))
-    return bail(PCV_E_OOM, "device allocation failed");
-  cudaMemcpyAsync(x->X, hX.data(), hX.size() * sizeof(float), cudaMemcpyHostToDevice, x->stream);
-  cudaMemcpyAsync(x->y, hy.data(), hy.size() * sizeof(float), cudaMemcpyHostToDevice, x->stream);
-  cudaMemcpyAsync(x->folds, fds.data(), fds.size() * sizeof(FoldDesc), cudaMemcpyHostToDevice, x->stream);
   std::vector<float> hm(x->d_pad, 1.0f);
   if (opt->inv_mass_diag)
     for (int j = 0; j < x->d; ++j) {

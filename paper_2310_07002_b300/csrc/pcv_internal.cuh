@@ -305,6 +305,11 @@ __global__ void k_theta_ref(int n, int d, int ld, const float *src, float *theta
 __global__ void k_eta_ref(int N, int N_pad, int p, int KP, const __nv_bfloat16 *X16, const float *theta_ref,
                           float *eta_half);
 __global__ void k_eta_fold(int N_pad, int p, int KP, const float *eta_half, __nv_bfloat16 *X16);
+__global__ void k_gather_rows(long long N, int p, int p_pad, const int *perm, const float *xraw, float *X);
+__global__ void k_x_bf16(long long N, int p, int p_pad, int KP, const float *X, __nv_bfloat16 *X16);
+__global__ void k_ylin_all(int N, int KP, const __nv_bfloat16 *X16, const float *y, double *all);
+__global__ void k_ylin_folds(int K, int p, int KP, const __nv_bfloat16 *X16, const float *y, const FoldDesc *folds,
+                             const double *all, double *ylin);
 __global__ void k_shadow_ones(int C_pad, int p, int KP, __nv_bfloat16 *hi);
 __global__ void k_accept(AcceptArgs a);
 __global__ void k_accumulate_given(Accum A, const double *s, int n, long long n0);
