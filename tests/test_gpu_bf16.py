@@ -43,7 +43,9 @@ def bf16_workload(p):
     return w
 
 
-@pytest.mark.parametrize("p", [20, 100])
+# p = 14: the three eta_ref columns spill into a second K step (KS = 2);
+# p = 128: KS = 9, K padded to 192 (three 64-column TMA atoms)
+@pytest.mark.parametrize("p", [14, 20, 100, 128])
 def test_bf16_log_density_and_gradient(torch, orc, p):
     from paper_2310_07002_b300.pcv import PCV, BF16
     w = bf16_workload(p)
@@ -69,7 +71,7 @@ def test_bf16_log_density_and_gradient(torch, orc, p):
     pc.close()
 
 
-@pytest.mark.parametrize("p", [20, 100])
+@pytest.mark.parametrize("p", [20, 100, 128])
 def test_bf16_trajectory(torch, orc, p):
     from paper_2310_07002_b300.pcv import PCV, BF16
     w = bf16_workload(p)
