@@ -328,13 +328,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint64_t *bars = reinterpret_cast<uint64_t *>(ys + NS * kTN + 16);
   // barrier slots (up to kTcMaxStages X stages)
   uint64_t *x_full = bars, *x_empty = bars + kTcMaxStages;
+  // r_part[4 b + qq]: quarter qq (32 rows) of R buffer b is in TMEM, so the
+  // second GEMM starts on a chunk while its epilogue is still computing
   uint64_t *s_full = bars + 2 * kTcMaxStages, *s_empty = s_full + 2;
-  uint64_t *r_full = s_full + 4, *r_empty = s_full + 6, *th_full = s_full + 8, *th_empty = s_full + 9;
-  uint64_t *g_full = s_full + 10, *g_empty = s_full + 11;
-  uint32_t *tmem_base_slot = reinterpret_cast<uint32_t *>(s_full + 12);
-  volatile int *abort_flag = reinterpret_cast<volatile int *>(s_full + 13);
-  volatile int *last_flag = reinterpret_cast<volatile int *>(s_full + 14);
-  uint64_t *flush_bar = s_full + 15, *decide_bar = s_full + 16;   // epilogue-internal sync
+  uint64_t *r_part = s_full + 4, *r_empty = s_full + 12, *th_full = s_full + 14, *th_empty = s_full + 15;
+  uint64_t *g_full = s_full + 16, *g_empty = s_full + 17;
+  uint32_t *tmem_base_slot = reinterpret_cast<uint32_t *>(s_full + 18);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(s_full + 19);
+  volatile int *last_flag = reinterpret_cast<volatile int *>(s_full + 20);
+  uint64_t *flush_bar = s_full + 21, *decide_bar = s_full + 22;   // epilogue-internal sync
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long U = (long long)ta.T * ta.J;
@@ -346,7 +348,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int s = 0; s < NS; ++s) { mbar_init(smem_u32(&x_full[s]), 1); mbar_init(smem_u32(&x_empty[s]), 1); }
     for (int s = 0; s < 2; ++s) {
       mbar_init(smem_u32(&s_full[s]), 1); mbar_init(smem_u32(&s_empty[s]), 4);
-      mbar_init(smem_u32(&r_full[s]), 4); mbar_init(smem_u32(&r_empty[s]), 1);
+      for (int qq = 0; qq < 4; ++qq) mbar_init(smem_u32(&r_part[4 * s + qq]), 4);
+      mbar_init(smem_u32(&r_empty[s]), 1);
     }
     mbar_init(smem_u32(th_full), 1); mbar_init(smem_u32(th_empty), 1);
     mbar_init(smem_u32(g_full), 1); mbar_init(smem_u32(g_empty), 4);
@@ -452,7 +455,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
   } else if (warp == 2) {
     // ------------------------------ GEMM2 issuer ---------------------------
-    // Per unit i: G += R[i & 1] . X_chunk, after the epilogue produced R.
+    // Per unit i: G += R[i & 1] . X_chunk, two K steps (32 rows) per quarter
+    // of R as the epilogue produces it.
     if (lane == 0) {
       const uint32_t id2 = idesc_bf16(kTM, ta.PN, true);
       const uint64_t xd_mn = sdesc_sw128(smem_u32(xs), kTN * 128, 1024);  // MN-major view, stage 0
@@ -463,15 +467,23 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const bool first = (i == 0 || j == 0);
         const bool last = (i == nunits - 1 || j == ta.J - 1);
         const int rb = i & 1;
-        if (!mbar_wait_fast(smem_u32(&r_full[rb]), (i >> 1) & 1, abort_flag, ta.err)) break;
-        if (first && !mbar_wait_fast(smem_u32(g_empty), (seg2 & 1) ^ 1, abort_flag, ta.err)) break;
-        tc_fence_after();
         const uint32_t a0 = tmem_R + 64 * rb;       // K step ks: 8 columns (16 bf16) at a0 + 8 ks
         const uint64_t bd0 = xd_mn + (uint64_t)st * x_step;
+        bool ok = true;
 #pragma unroll
-        for (int ks = 0; ks < kTN / 16; ++ks)
-          tc_mma_bf16_ta(tmem_G, a0 + 8 * ks, bd0 + (uint64_t)((ks * 2048) >> 4), id2,
-                         (first && ks == 0) ? 0u : 1u);
+        for (int qq = 0; qq < 4 && ok; ++qq) {
+          ok = mbar_wait_fast(smem_u32(&r_part[4 * rb + qq]), (i >> 1) & 1, abort_flag, ta.err);
+          if (ok && qq == 0 && first) ok = mbar_wait_fast(smem_u32(g_empty), (seg2 & 1) ^ 1, abort_flag, ta.err);
+          if (!ok) break;
+          tc_fence_after();
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk) {
+            const int ks = 2 * qq + kk;
+            tc_mma_bf16_ta(tmem_G, a0 + 8 * ks, bd0 + (uint64_t)((ks * 2048) >> 4), id2,
+                           (first && ks == 0) ? 0u : 1u);
+          }
+        }
+        if (!ok) break;
         tc_commit(smem_u32(&r_empty[rb]));
         tc_commit(smem_u32(&x_empty[st]));
         if (last) { tc_commit(smem_u32(g_full)); ++seg2; }
@@ -621,10 +633,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // The whole S tile row (128 columns) comes into registers at once and
         // S is released before any arithmetic, so the first GEMM of unit
         // i + 2 waits only for the TMEM loads of unit i.  The four R quarters
-        // go out as 16-column stores with one wait at the end (TMEM round
-        // trips are several hundred cycles while the MMAs run).  Loaded
-        // registers are used only after the load wait, and store sources
-        // stay allocated until the store wait (tmem_fence_regs pins both).
+        // go out as 16-column stores; each store's wait comes after the
+        // next quarter's arithmetic (TMEM round trips are several hundred
+        // cycles while the MMAs run), and each completed quarter is handed
+        // to the second GEMM at once.  Loaded registers are used only after
+        // the load wait, and store sources stay allocated until their store
+        // wait (tmem_fence_regs pins both).
         uint32_t sv[128], p0[16], p1[16], p2[16], p3[16];
         PCV_TMEM_LD128(tmem + sb * 128 + lane_off, sv);   // one load: ~2 % faster than four x32
         tmem_wait_ld();
@@ -642,21 +656,29 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         tc_fence_after();
         // R row m (TMEM lane m): chunk rows 2c, 2c + 1 in bf16x2 column c
         const uint32_t rbuf = tmem_R + 64 * rb + lane_off;
+        // each quarter's store completes while the next quarter is computed;
+        // then the second GEMM may take it
+        auto quarter_stored = [&](int qq) {
+          tmem_wait_st();
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&r_part[4 * rb + qq]));
+        };
         PCV_TMEM_ST16(rbuf, p0);
         quarter(1, v1, p1);
+        quarter_stored(0);
+        tmem_fence_regs(p0);
         PCV_TMEM_ST16(rbuf + 16, p1);
         quarter(2, v2, p2);
+        quarter_stored(1);
+        tmem_fence_regs(p1);
         PCV_TMEM_ST16(rbuf + 32, p2);
         quarter(3, v3, p3);
-        PCV_TMEM_ST16(rbuf + 48, p3);
-        tmem_wait_st();
-        tmem_fence_regs(p0);
-        tmem_fence_regs(p1);
+        quarter_stored(2);
         tmem_fence_regs(p2);
+        PCV_TMEM_ST16(rbuf + 48, p3);
+        quarter_stored(3);
         tmem_fence_regs(p3);
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&r_full[rb]));
       }
       if (aborted) break;
       // ---- segment end (both groups): the group that owns the segment's
@@ -905,7 +927,7 @@ size_t tc_smem_bytes(int KP, int NS, int need_lo, int p) {
   (void)p;
   const size_t KA = KP / 64;
   size_t b = KA * kTM * 128 * (need_lo ? 2 : 1) + (size_t)NS * KA * kTN * 128 +
-             (size_t)NS * kTN * 4 + 64 + (2 * kTcMaxStages + 17) * 8;   // y - 1/2; barrier / flag slots
+             (size_t)NS * kTN * 4 + 64 + (2 * kTcMaxStages + 23) * 8;   // y - 1/2; barrier / flag slots
   return b + 1024;   // alignment slack
 }
 
