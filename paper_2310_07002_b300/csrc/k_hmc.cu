@@ -144,83 +144,109 @@ __device__ __forceinline__ void lshift_push(double &shift, double &mean, double 
 // log-shifted Welford of exp(s), lane 4 the Welford sums of s, the batch
 // Welford state and the autocovariance centring; then all lanes add their
 // lags.
-__device__ void accum_push(const Accum &A, int c, double s, long long n_before, int lane) {
+// The accumulators of one draw are split by the shape of their work: the
+// scalar ones (log-sum-exp, log-shifted Welford, Welford, batch means) are
+// FP64 transcendental chains, run one thread per chain so that a warp
+// instruction serves 32 chains (B300's FP64 units are narrow); the lag sums
+// of the autocovariance are a warp per chain, lanes over lags.
+
+// x_t = s_t - c0 (c0: the chain's first draw), the autocovariance variable
+__device__ __forceinline__ double acov_x(const Accum &A, int c, double s, long long n_before) {
+  return n_before == 0 ? 0.0 : s - A.c0[c];
+}
+
+// scalar accumulators of draw s (0-based index n_before) of chain c; one thread
+__device__ void accum_scalar(const Accum &A, int c, double s, long long n_before) {
   const long long n = n_before + 1;
   const int b = A.b;
   const int in_batch = (int)(n_before % b) + 1;
-  double x = 0.0;
-  if (lane == 0) {
-    A.Ux[c] = log_add_exp(A.Ux[c], s);
-  } else if (lane == 1) {
-    A.Ux2[c] = log_add_exp(A.Ux2[c], 2.0 * s);
-  } else if (lane == 2) {
-    const double zx = log_add_exp(in_batch == 1 ? -INFINITY : A.Zx[c], s);
-    A.Zx[c] = zx;
-    if (in_batch == b) {                     // the batch closes (A2 batch loop end)
-      const long long na = n / b;
-      const double z = zx - log((double)b);  // log of the batch mean, eq. bmean
-      double vm = A.vm[c], vmean = A.vmean[c], vM2 = A.vM2[c];
-      lshift_push(vm, vmean, vM2, na, z);
-      A.vm[c] = vm; A.vmean[c] = vmean; A.vM2[c] = vM2;
-    }
-  } else if (lane == 3) {
+  A.Ux[c] = log_add_exp(A.Ux[c], s);
+  A.Ux2[c] = log_add_exp(A.Ux2[c], 2.0 * s);
+  const double zx = log_add_exp(in_batch == 1 ? -INFINITY : A.Zx[c], s);
+  A.Zx[c] = zx;
+  if (in_batch == b) {                       // the batch closes (A2 batch loop end)
+    const long long na = n / b;
+    const double z = zx - log((double)b);    // log of the batch mean, eq. bmean
+    double vm = A.vm[c], vmean = A.vmean[c], vM2 = A.vM2[c];
+    lshift_push(vm, vmean, vM2, na, z);
+    A.vm[c] = vm; A.vmean[c] = vmean; A.vM2[c] = vM2;
+  }
+  {
     double em = A.em[c], emean = A.emean[c], eM2 = A.eM2[c];
     lshift_push(em, emean, eM2, n, s);
     A.em[c] = em; A.emean[c] = emean; A.eM2[c] = eM2;
-  } else if (lane == 4) {
-    double wm = A.wmean[c], wM2 = A.wM2[c];
-    double dl = s - wm;
-    wm += dl / (double)n;
-    wM2 += dl * (s - wm);
-    A.wmean[c] = wm; A.wM2[c] = wM2;
-    double bm = in_batch == 1 ? 0.0 : A.bmean_cur[c], b2 = in_batch == 1 ? 0.0 : A.bM2_cur[c];
-    dl = s - bm;
-    bm += dl / (double)in_batch;
-    b2 += dl * (s - bm);
-    A.bmean_cur[c] = bm; A.bM2_cur[c] = b2;
-    if (n_before == 0) A.c0[c] = s;
-    x = s - A.c0[c];
-    A.xsum[c] += x;
-    if (in_batch == b) {
-      const long long na = n / b;
-      if (na <= A.max_batches) {
-        A.bmean[(size_t)(na - 1) * A.C + c] = bm;
-        A.bM2[(size_t)(na - 1) * A.C + c] = b2;
-      }
-    }
   }
-  if (A.M > 0) {
-    x = __shfl_sync(0xffffffffu, x, 4);
-    const long long t = n_before;                // 0-based time of this draw
-    const int tr = (int)(t % A.M);               // ring slot of this draw
-    double *lag = A.lagsum + (size_t)c * (A.M + 1);
-    double *ring = A.ring + (size_t)c * A.M;
-    for (int m = lane; m <= A.M; m += 32) {
-      if (m == 0) lag[0] += x * x;
-      else if (m <= t) {
-        int slot = tr - m;                       // (t - m) mod M, as 0 <= tr < M and m <= M
-        if (slot < 0) slot += A.M;
-        lag[m] += x * ring[slot];
-      }
-    }
-    __syncwarp();
-    if (lane == 0) {
-      ring[tr] = x;
-      if (t < A.M) A.first[(size_t)c * A.M + t] = x;
+  double wm = A.wmean[c], wM2 = A.wM2[c];
+  double dl = s - wm;
+  wm += dl / (double)n;
+  wM2 += dl * (s - wm);
+  A.wmean[c] = wm; A.wM2[c] = wM2;
+  double bm = in_batch == 1 ? 0.0 : A.bmean_cur[c], b2 = in_batch == 1 ? 0.0 : A.bM2_cur[c];
+  dl = s - bm;
+  bm += dl / (double)in_batch;
+  b2 += dl * (s - bm);
+  A.bmean_cur[c] = bm; A.bM2_cur[c] = b2;
+  if (n_before == 0) A.c0[c] = s;
+  A.xsum[c] += acov_x(A, c, s, n_before);
+  if (in_batch == b) {
+    const long long na = n / b;
+    if (na <= A.max_batches) {
+      A.bmean[(size_t)(na - 1) * A.C + c] = bm;
+      A.bM2[(size_t)(na - 1) * A.C + c] = b2;
     }
   }
 }
 
-// ---------------------------------------------------------------------------
-// k_accept: one warp per chain; the last block advances the counters
-// ---------------------------------------------------------------------------
+// lag sums sum_t x_t x_{t-m}, m = 0..M, and the ring of the last M values of
+// x; one warp per chain, lanes over lags (t = n_before)
+__device__ void accum_lags(const Accum &A, int c, double x, long long t, int lane) {
+  if (A.M == 0) return;
+  const int tr = (int)(t % A.M);             // ring slot of this draw
+  double *lag = A.lagsum + (size_t)c * (A.M + 1);
+  double *ring = A.ring + (size_t)c * A.M;
+  for (int m = lane; m <= A.M; m += 32) {
+    if (m == 0) lag[0] += x * x;
+    else if (m <= t) {
+      int slot = tr - m;                     // (t - m) mod M, as 0 <= tr < M and m <= M
+      if (slot < 0) slot += A.M;
+      lag[m] += x * ring[slot];
+    }
+  }
+  __syncwarp();
+  if (lane == 0) {
+    ring[tr] = x;
+    if (t < A.M) A.first[(size_t)c * A.M + t] = x;
+  }
+}
 
-__global__ void __launch_bounds__(256) k_accept(AcceptArgs a) {
+// ---------------------------------------------------------------------------
+// k_accept: 32 chains per block; per chain one warp for the vector work
+// (kinetic energy, the accept copies, the lag sums) and one lane of warp 0
+// for the scalar FP64 work (log u, the accumulators); the last block
+// advances the counters
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kAccChains * 32) k_accept(AcceptArgs a) {
+  __shared__ double logu_s[kAccChains], s_s[kAccChains], dH_s[kAccChains];
+  __shared__ int flag_s[kAccChains];         // bit 0 accepted, 1 divergent, 2 finite
   __shared__ int is_last;
-  const int lane = threadIdx.x & 31;
-  const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cb0 = blockIdx.x * kAccChains;
   const unsigned it = a.fd ? a.st->fd_iter : a.st->iter;
   const long long n_before = a.st->n_draws;
+  // 1) the accept uniforms, one lane per chain
+  if (warp == 0) {
+    const int c = cb0 + lane;
+    double lu = 0.0;
+    if (c < a.C) {
+      const uint4 w = philox_at(a.seed, 0u, (uint32_t)(a.chain_base + c), it, a.stream);
+      lu = log(unit_from_word(w.x));
+    }
+    logu_s[lane] = lu;
+  }
+  __syncthreads();
+  // 2) one warp per chain: FP64 Hamiltonian difference, Metropolis test,
+  // restore-or-keep, the held-out value of the draw and its lag sums
+  const int c = cb0 + warp;
   if (c < a.C) {
     double kin = 0.0;
     for (int j = lane; j < a.d; j += 32) {
@@ -230,10 +256,8 @@ __global__ void __launch_bounds__(256) k_accept(AcceptArgs a) {
     kin = warp_sum_d(kin);
     const double H1 = -a.logp_p[c] + 0.5 * kin;
     const double dH = H1 - a.H0[c];
-    const uint4 w = philox_at(a.seed, 0u, (uint32_t)(a.chain_base + c), it, a.stream);
-    const double logu = log(unit_from_word(w.x));
     const bool finite = isfinite(H1) && isfinite(dH);
-    const bool acc = finite && (logu < -dH);
+    const bool acc = finite && (logu_s[warp] < -dH);
     const bool div = !finite || dH > 1000.0;
     if (acc) {
       for (int j = lane; j < a.d; j += 32) {
@@ -241,22 +265,29 @@ __global__ void __launch_bounds__(256) k_accept(AcceptArgs a) {
         a.grad[(size_t)c * a.ld + j] = a.grad_p[(size_t)c * a.ld + j];
       }
     }
+    const double s = acc ? a.shat_p[c] : a.shat[c];
     if (lane == 0) {
       if (acc) {
         a.logp[c] = a.logp_p[c];
         a.shat[c] = a.shat_p[c];
       }
-      if (a.accept_prob) a.accept_prob[c] = finite ? (dH <= 0.0 ? 1.0 : exp(-dH)) : 0.0;
-      if (a.accumulate) {
-        a.acc.div[c] += div ? 1 : 0;
-        a.acc.acc[c] += acc ? 1 : 0;
-      }
+      flag_s[warp] = (acc ? 1 : 0) | (div ? 2 : 0) | (finite ? 4 : 0);
+      dH_s[warp] = dH;
+      s_s[warp] = s;
     }
+    if (a.accumulate) accum_lags(a.acc, c, acov_x(a.acc, c, s, n_before), n_before, lane);
+  }
+  __syncthreads();
+  // 3) one lane per chain: acceptance probability, counters, accumulators
+  if (warp == 0 && cb0 + lane < a.C) {
+    const int cc = cb0 + lane;
+    const int f = flag_s[lane];
+    if (a.accept_prob) a.accept_prob[cc] = (f & 4) ? (dH_s[lane] <= 0.0 ? 1.0 : exp(-dH_s[lane])) : 0.0;
     if (a.accumulate) {
-      const double s = acc ? a.shat_p[c] : a.shat[c];
-      accum_push(a.acc, c, s, n_before, lane);
-      if (lane == 0 && a.acc.draws && n_before < a.acc.draw_cap)
-        a.acc.draws[(size_t)c * a.acc.draw_cap + n_before] = s;
+      a.acc.div[cc] += (f & 2) ? 1 : 0;
+      a.acc.acc[cc] += (f & 1) ? 1 : 0;
+      accum_scalar(a.acc, cc, s_s[lane], n_before);
+      if (a.acc.draws && n_before < a.acc.draw_cap) a.acc.draws[(size_t)cc * a.acc.draw_cap + n_before] = s_s[lane];
     }
   }
   __threadfence();
@@ -277,16 +308,23 @@ __global__ void __launch_bounds__(256) k_accept(AcceptArgs a) {
   }
 }
 
-// push given draws (test entry): one warp per chain, draws[t] for t in [0, n)
-__global__ void __launch_bounds__(256) k_accumulate_given(Accum A, const double *s, int n,
-                                                           long long n0) {
-  const int lane = threadIdx.x & 31;
-  const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (c >= A.C) return;
+// push given draws (test entry), 32 chains per block: per draw the scalar
+// accumulators (one lane per chain), then the lag sums (one warp per chain)
+__global__ void __launch_bounds__(kAccChains * 32) k_accumulate_given(Accum A, const double *s, int n,
+                                                                     long long n0) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cb0 = blockIdx.x * kAccChains;
   for (int t = 0; t < n; ++t) {
-    const double v = s[(size_t)c * n + t];
-    accum_push(A, c, v, n0 + t, lane);
-    if (lane == 0 && A.draws && n0 + t < A.draw_cap) A.draws[(size_t)c * A.draw_cap + n0 + t] = v;
+    if (warp == 0 && cb0 + lane < A.C) {
+      const int cc = cb0 + lane;
+      const double v = s[(size_t)cc * n + t];
+      accum_scalar(A, cc, v, n0 + t);
+      if (A.draws && n0 + t < A.draw_cap) A.draws[(size_t)cc * A.draw_cap + n0 + t] = v;
+    }
+    __syncthreads();
+    const int c = cb0 + warp;
+    if (c < A.C) accum_lags(A, c, acov_x(A, c, s[(size_t)c * n + t], n0 + t), n0 + t, lane);
+    __syncthreads();
   }
 }
 

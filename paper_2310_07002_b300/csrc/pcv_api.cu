@@ -493,7 +493,7 @@ pcv_status launch_iteration(pcv_ctx *x, ChainBufs &cb, bool fd, bool accumulate)
   aa.accumulate = accumulate ? 1 : 0;
   aa.acc = x->acc;
   aa.accept_prob = cb.accept_prob;
-  k_accept<<<(cb.C + 7) / 8, 256, 0, x->stream>>>(aa);
+  k_accept<<<(cb.C + kAccChains - 1) / kAccChains, kAccChains * 32, 0, x->stream>>>(aa);
   CK(cudaGetLastError());
   if (accumulate && x->extra.flags) {
     k_extra_push<<<(cb.C + 7) / 8, 256, sizeof(double) * 8 * x->extra.T, x->stream>>>(
@@ -1283,7 +1283,8 @@ pcv_status pcv_accumulate(pcv_ctx *x, const double *shat, int32_t n) {
   if (x->state == ST_CREATED) return fail(x, PCV_E_BAD_STATE, "accumulate before positions are set");
   if ((x->n_sampled + n) / x->b > x->max_batches) return fail(x, PCV_E_INVALID_ARG, "more batches than max_batches");
   enter(x);
-  k_accumulate_given<<<(x->C + 7) / 8, 256, 0, x->stream>>>(x->acc, shat, n, x->n_sampled);
+  k_accumulate_given<<<(x->C + kAccChains - 1) / kAccChains, kAccChains * 32, 0, x->stream>>>(x->acc, shat, n,
+                                                                                              x->n_sampled);
   CK(cudaGetLastError());
   x->n_sampled += n;
   const long long nd = x->n_sampled;

@@ -97,9 +97,9 @@ struct Accum {
   double *bmean_cur, *bM2_cur;// Welford of s in the current batch
   double *bmean, *bM2;        // per closed batch [max_batches x C]
   double *c0, *xsum;          // acov centring constant (first draw), sum of x
-  double *lagsum;             // [(M+1) x C]
-  double *first;              // [M x C]
-  double *ring;               // [M x C]
+  double *lagsum;             // [C x (M+1)]
+  double *first;              // [C x M]
+  double *ring;               // [C x M]
   long long *div, *acc;       // divergences, accepts (sampling only)
   double *draws;              // optional stored draws [C x draw_cap]
   int draw_cap;
@@ -311,6 +311,7 @@ __global__ void k_ylin_all(int N, int KP, const __nv_bfloat16 *X16, const float 
 __global__ void k_ylin_folds(int K, int p, int KP, const __nv_bfloat16 *X16, const float *y, const FoldDesc *folds,
                              const double *all, double *ylin);
 __global__ void k_shadow_ones(int C_pad, int p, int KP, __nv_bfloat16 *hi);
+constexpr int kAccChains = 32;   // chains per block of the accept / accumulate kernels
 __global__ void k_accept(AcceptArgs a);
 __global__ void k_accumulate_given(Accum A, const double *s, int n, long long n0);
 __global__ void k_fd_adapt(FdAdaptArgs a);
