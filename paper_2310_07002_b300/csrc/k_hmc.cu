@@ -18,18 +18,25 @@ namespace pcv {
 // ---------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(256) k_begin(BeginArgs a) {
+  __shared__ float eps_s;
   const int lane = threadIdx.x & 31;
   const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (c >= a.C) return;
   const unsigned it = *a.iter;
   // this iteration's step size: the nominal one, or (fold chains) jittered
-  // by one uniform per iteration shared by every chain (stream ST_JIT)
-  float eps = *a.eps;
-  if (a.jitter > 0.0f) {
-    const uint4 w = philox_at(a.seed, 0u, 0u, it, ST_JIT);
-    eps = (float)((double)eps * (1.0 + (double)a.jitter * (2.0 * unit_from_word(w.x) - 1.0)));
+  // by one uniform per iteration shared by every chain (stream ST_JIT);
+  // formed once per block (FP64 work is slow on this part)
+  if (threadIdx.x == 0) {
+    float e = *a.eps;
+    if (a.jitter > 0.0f) {
+      const uint4 w = philox_at(a.seed, 0u, 0u, it, ST_JIT);
+      e = (float)((double)e * (1.0 + (double)a.jitter * (2.0 * unit_from_word(w.x) - 1.0)));
+    }
+    eps_s = e;
+    if (a.eps_iter && blockIdx.x == 0) *a.eps_iter = e;
   }
-  if (a.eps_iter && c == 0 && lane == 0) *a.eps_iter = eps;
+  __syncthreads();
+  if (c >= a.C) return;
+  const float eps = eps_s;
   const float *th = a.theta + (size_t)c * a.ld;
   const float *g = a.grad + (size_t)c * a.ld;
   double kin = 0.0;
