@@ -20,7 +20,8 @@ namespace pcv {
 __global__ void __launch_bounds__(256) k_begin(BeginArgs a) {
   __shared__ float eps_s;
   const int lane = threadIdx.x & 31;
-  const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int gsz = begin_lanes_per_chain(a.d), sl = lane & (gsz - 1);
+  const int c = (blockIdx.x * 8 + (threadIdx.x >> 5)) * (32 / gsz) + lane / gsz;
   const unsigned it = *a.iter;
   // this iteration's step size: the nominal one, or (fold chains) jittered
   // by one uniform per iteration shared by every chain (stream ST_JIT);
@@ -35,12 +36,12 @@ __global__ void __launch_bounds__(256) k_begin(BeginArgs a) {
     if (a.eps_iter && blockIdx.x == 0) *a.eps_iter = e;
   }
   __syncthreads();
-  if (c >= a.C) return;
+  const bool valid = c < a.C;
   const float eps = eps_s;
   const float *th = a.theta + (size_t)c * a.ld;
   const float *g = a.grad + (size_t)c * a.ld;
   double kin = 0.0;
-  for (int q = lane; 4 * q < a.d; q += 32) {
+  for (int q = sl; valid && 4 * q < a.d; q += gsz) {
     float z[4];
     if (a.r_given) {
 #pragma unroll
@@ -70,8 +71,10 @@ __global__ void __launch_bounds__(256) k_begin(BeginArgs a) {
       }
     }
   }
-  kin = warp_sum_d(kin);
-  if (lane == 0) a.H0[c] = -a.logp[c] + 0.5 * kin;
+  // sum over the chain's lanes: the xor tree of warp_sum_d restricted to
+  // the group (lanes outside it hold 0, so the sum is the same bit for bit)
+  for (int off = gsz >> 1; off > 0; off >>= 1) kin += __shfl_xor_sync(0xffffffffu, kin, off);
+  if (valid && sl == 0) a.H0[c] = -a.logp[c] + 0.5 * kin;
 }
 
 // standard normals for (iteration, stream) into out[C x ld] (scaled)

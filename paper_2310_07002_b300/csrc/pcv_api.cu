@@ -470,7 +470,7 @@ pcv_status launch_iteration(pcv_ctx *x, ChainBufs &cb, bool fd, bool accumulate)
   ba.ld_shadow = x->KP;
   ba.shadow_d = x->p;
   ba.theta_ref = x->theta_ref;
-  k_begin<<<(cb.C + 7) / 8, 256, 0, x->stream>>>(ba);
+  k_begin<<<begin_blocks(cb.C, x->d), 256, 0, x->stream>>>(ba);
   CK(cudaGetLastError());
   GradArgs ga = grad_args(x, cb, true);
   for (int s = 1; s <= x->Lf; ++s) {
@@ -1246,7 +1246,7 @@ pcv_status pcv_trajectory(pcv_ctx *x, const float *theta0, const float *r0, int3
   ba.ld_shadow = x->KP;
   ba.shadow_d = x->p;
   ba.theta_ref = x->theta_ref;
-  k_begin<<<(cb.C + 7) / 8, 256, 0, x->stream>>>(ba);
+  k_begin<<<begin_blocks(cb.C, x->d), 256, 0, x->stream>>>(ba);
   CK(cudaGetLastError());
   GradArgs ga = grad_args(x, cb, true);
   for (int st = 1; st <= x->Lf; ++st) {

@@ -311,6 +311,19 @@ __global__ void k_ylin_all(int N, int KP, const __nv_bfloat16 *X16, const float 
 __global__ void k_ylin_folds(int K, int p, int KP, const __nv_bfloat16 *X16, const float *y, const FoldDesc *folds,
                              const double *all, double *ylin);
 __global__ void k_shadow_ones(int C_pad, int p, int KP, __nv_bfloat16 *hi);
+// k_begin: a chain takes this many lanes (the power of two that covers its
+// ceil(d/4) coordinate quads, at most 32), so small models pack 32 / that
+// many chains per warp; 8 warps per block
+__host__ __device__ inline int begin_lanes_per_chain(int d) {
+  const int nq = (d + 3) / 4;
+  int g = 1;
+  while (g < nq && g < 32) g <<= 1;
+  return g;
+}
+inline int begin_blocks(int C, int d) {
+  const int per_block = 8 * (32 / begin_lanes_per_chain(d));
+  return (C + per_block - 1) / per_block;
+}
 constexpr int kAccChains = 32;   // chains per block of the accept / accumulate kernels
 __global__ void k_accept(AcceptArgs a);
 __global__ void k_accumulate_given(Accum A, const double *s, int n, long long n0);
