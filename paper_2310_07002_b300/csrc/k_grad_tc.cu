@@ -577,11 +577,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                   acc4[k & 3] += softplus_half(__uint_as_float(v[k]));
                 sp_tr += (double)((acc4[0] + acc4[1]) + (acc4[2] + acc4[3]));
               } else {
-                float tr = 0.0f, te = 0.0f;
+                // rare (the quarter meets the fold's excluded rows or the
+                // padding): a rolled loop over a local copy keeps this
+                // path's code small, which the instruction cache of the
+                // log-density launch needs
+                float sq[32];
 #pragma unroll
+                for (int k = 0; k < 32; ++k) sq[k] = __uint_as_float(v[k]);
+                float tr = 0.0f, te = 0.0f;
+#pragma unroll 1
                 for (int k = 0; k < 32; ++k) {
                   const int n = n0 + k;
-                  const float sp = softplus_half(__uint_as_float(v[k]));
+                  const float sp = softplus_half(sq[k]);
                   if (n < pb.N && (n < fd.excl_lo || n >= fd.excl_hi)) tr += sp;
                   if (n >= fd.test_lo && n < fd.test_hi) te += sp;
                 }
@@ -616,11 +623,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 for (int k = 0; k < 32; ++k) acc4[k & 3] = fmaf(e[k], e[k], acc4[k & 3]);
                 sp_tr += (double)((acc4[0] + acc4[1]) + (acc4[2] + acc4[3]));
               } else {
-                float tr = 0.0f, te = 0.0f;
+                float sq[32];                      // rolled, as for the softplus sums
 #pragma unroll
+                for (int k = 0; k < 32; ++k) sq[k] = e[k];
+                float tr = 0.0f, te = 0.0f;
+#pragma unroll 1
                 for (int k = 0; k < 32; ++k) {
                   const int n = n0 + k;
-                  const float e2 = e[k] * e[k];
+                  const float e2 = sq[k] * sq[k];
                   if (n < pb.N && (n < fd.excl_lo || n >= fd.excl_hi)) tr += e2;
                   if (n >= fd.test_lo && n < fd.test_hi) te += e2;
                 }
