@@ -1,12 +1,14 @@
 // k_grad_tc.cu -- tcgen05 / TMEM / TMA kernel for one fold-masked gradient
-// evaluation of the logistic model for all chains, fused with the leapfrog
-// update (Section 3.3; masks of eq. mask-log-prob / mask-log-pred, Appendix
-// B).  The two contractions of the masked likelihood gradient are tensor-core
+// evaluation of a flat model (logistic; Gaussian linear and AR with the
+// GAUSS instantiations) for all chains, fused with the leapfrog update
+// (Section 3.3; masks of eq. mask-log-prob / mask-log-pred, Appendix B).
+// The two contractions of the masked likelihood gradient are tensor-core
 // GEMMs in BF16 with FP32 accumulation:
 //
-//   S = Theta_tile . X_chunk^T      (128 chains x 128 rows, K = p)   -> TMEM
-//   R = mask .* (y - sigmoid(2 S))  (epilogue, FP32, rounded to BF16) -> TMEM
-//   G += R . X_chunk                (128 chains x p, K = 128 rows)   -> TMEM
+//   S = Theta_tile . X_chunk^T      (128 chains x 128 rows, K = p + 3)  -> TMEM
+//   R = mask .* (y - sigmoid(2 S))  (epilogue, FP32, rounded to BF16)   -> TMEM
+//       (Gaussian: mask .* (y - 2 S) / sigma^2)
+//   G += R . X_chunk                (128 chains x p, K = 128 rows)      -> TMEM
 //
 // R is the A operand of the second GEMM straight from TMEM, so shared memory
 // carries only Theta, X and y: with both operands of both GEMMs in SMEM the
@@ -44,7 +46,8 @@
 // alternate chunks (thread = TMEM lane = chain; two warps per SM
 // sub-partition so TMEM-load and barrier latencies overlap); they take the
 // registers the producers give up (setmaxnreg) and read a chunk's S row
-// whole, releasing S before computing R.
+// whole, releasing S before computing R; each 32-row quarter of R is handed
+// to the second GEMM as soon as its TMEM store has completed.
 // Every mbarrier wait is bounded: on time-out the kernel sets an error flag,
 // stops issuing work and exits after freeing TMEM.
 #include <cuda.h>
