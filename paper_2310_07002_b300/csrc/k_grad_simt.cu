@@ -626,6 +626,16 @@ __device__ __forceinline__ uint32_t to_tf32(float v) {
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
   return r;
 }
+// 16-byte global -> shared copy that does not wait (cp.async); src_bytes 0
+// fills the destination with zeros and reads nothing
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int Pending>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(Pending) : "memory"); }
+
 __device__ __forceinline__ void mma_tf32(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
                                          uint32_t b0, uint32_t b1) {
   asm volatile(
@@ -637,11 +647,11 @@ __device__ __forceinline__ void mma_tf32(float (&c)[4], uint32_t a0, uint32_t a1
 
 template <int MV>
 __global__ void __launch_bounds__(256) k_grad_tf32(Problem pb, GradArgs a, int pk) {
-  extern __shared__ uint32_t sm_t32[];
+  extern __shared__ __align__(16) uint32_t sm_t32[];
   const int ldk = pk + 4;                           // = 4 (mod 8): conflict-free A/B fragment loads
   uint32_t *th_s = sm_t32;                          // [64][ldk]  TF32
-  uint32_t *xs = th_s + kT32C * ldk;                // [64][ldk]  TF32
-  uint32_t *rs = xs + kT32R * ldk;                  // [64][68]   TF32 residual (chains x rows)
+  uint32_t *xs0 = th_s + kT32C * ldk;               // [2][64][ldk] X chunks: FP32 as copied, then TF32
+  uint32_t *rs = xs0 + 2 * kT32R * ldk;             // [64][68]   TF32 residual (chains x rows)
   float *ys = reinterpret_cast<float *>(rs + kT32C * kT32Ldr);   // [64]
   float *lls = ys + kT32R;                          // [3][64][8] partial sums
   __shared__ double lld[2][kT32C];
@@ -680,12 +690,37 @@ __global__ void __launch_bounds__(256) k_grad_tf32(Problem pb, GradArgs a, int p
   float ll_tr[2] = {0.0f, 0.0f}, ll_te[2] = {0.0f, 0.0f}, dls[2] = {0.0f, 0.0f};
   const int r0 = (int)((long long)pb.N * split / a.splits);
   const int r1 = (int)((long long)pb.N * (split + 1) / a.splits);
+  // X chunks are double-buffered: chunk c + 1 is copied (cp.async) while
+  // chunk c is computed; each thread rounds to TF32 the elements it copied
+  const int nq4 = pk / 4;                           // 16-byte groups per row
+  auto fetch_x = [&](int n0c, uint32_t *buf) {
+    const int nrc = min(kT32R, r1 - n0c);
+    for (int i = t; i < kT32R * nq4; i += 256) {
+      const int rr = i / nq4, j4 = 4 * (i - rr * nq4);
+      const bool ok = rr < nrc && j4 < pb.p_pad;    // beyond: zeros (rows, K padding)
+      cp_async16(buf + rr * ldk + j4, ok ? pb.X + (size_t)(n0c + rr) * pb.p_pad + j4 : pb.X, ok ? 16 : 0);
+    }
+    cp_async_commit();
+  };
+  if (r0 < r1) fetch_x(r0, xs0);
   __syncthreads();
-  for (int n0 = r0; n0 < r1; n0 += kT32R) {
+  int cidx = 0;
+  for (int n0 = r0; n0 < r1; n0 += kT32R, ++cidx) {
     const int nr = min(kT32R, r1 - n0);
-    for (int i = t; i < kT32R * pk; i += 256) {
-      const int rr = i / pk, j = i - rr * pk;
-      xs[rr * ldk + j] = to_tf32(rr < nr && j < p ? pb.X[(size_t)(n0 + rr) * pb.p_pad + j] : 0.0f);
+    uint32_t *xs = xs0 + (cidx & 1) * kT32R * ldk;
+    if (n0 + kT32R < r1) {
+      fetch_x(n0 + kT32R, xs0 + ((cidx + 1) & 1) * kT32R * ldk);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    for (int i = t; i < kT32R * nq4; i += 256) {
+      const int rr = i / nq4, j4 = 4 * (i - rr * nq4);
+      uint4 *q4 = reinterpret_cast<uint4 *>(xs + rr * ldk + j4);
+      uint4 v = *q4;
+      v.x = to_tf32(__uint_as_float(v.x)); v.y = to_tf32(__uint_as_float(v.y));
+      v.z = to_tf32(__uint_as_float(v.z)); v.w = to_tf32(__uint_as_float(v.w));
+      *q4 = v;
     }
     if (t < kT32R) ys[t] = t < nr ? pb.y[n0 + t] : 0.0f;
     __syncthreads();
@@ -798,7 +833,7 @@ __global__ void __launch_bounds__(256) k_grad_tf32(Problem pb, GradArgs a, int p
   }
   // sum the splits' partials in split order (likelihood sums in FP64), then
   // priors and the leapfrog update, one warp per chain
-  float *tot = reinterpret_cast<float *>(xs);       // [64][pk + 4], reuses the X tile
+  float *tot = reinterpret_cast<float *>(xs0);      // [64][pk + 4], reuses an X buffer
   const int ts = pk + 4;
   const float *base = a.ws + (size_t)tile * a.splits * kT32C * a.ws_stride;
   for (int i = t; i < kT32C * (pk + 3); i += 256) {
@@ -830,7 +865,7 @@ __global__ void __launch_bounds__(256) k_grad_tf32(Problem pb, GradArgs a, int p
 
 size_t tf32_smem_bytes(int pk) {
   const size_t ldk = (size_t)pk + 4;
-  return sizeof(uint32_t) * (2 * kT32C * ldk + (size_t)kT32C * kT32Ldr + kT32R + 3 * kT32C * 8);
+  return sizeof(uint32_t) * ((kT32C + 2 * kT32R) * ldk + (size_t)kT32C * kT32Ldr + kT32R + 3 * kT32C * 8);
 }
 
 int tf32_k_round(int p) { return (p + 7) / 8 * 8; }
