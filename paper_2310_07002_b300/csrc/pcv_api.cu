@@ -107,6 +107,7 @@ struct pcv_ctx {
   // (chain count, theta lo used)
   std::map<int, int> tuned_splits;
   std::map<std::pair<int, int>, int> tuned_ns;
+  std::map<int, int> tuned_ncta;          // tensor-core grid per chain count (one CTA per tile or one per SM)
   std::vector<std::string> tune_log;
   // Hyvarinen / Dawid-Sebastiani accumulators
   Extra extra{};
@@ -275,6 +276,10 @@ TcArgs tc_args(pcv_ctx *x, int C, bool need_ll) {
   t.T = (C + 127) / 128;
   const long long U = (long long)t.T * t.J;
   t.n_cta = (int)std::min<long long>(x->n_sm, U);
+  // the autotuner may choose one CTA per chain tile instead (no tile split
+  // across CTAs: better for short tiles, worse when tiles are long)
+  auto itn = x->tuned_ncta.find(C);
+  if (itn != x->tuned_ncta.end()) t.n_cta = (int)std::min<long long>(itn->second, U);
   t.max_seg = tc_segments_per_tile(t.T, t.J, t.n_cta);
   // theta hi + lo where log densities are needed or no centring reference
   // is set yet; the kick-drift launches of centred chains use hi only
@@ -297,7 +302,10 @@ TcArgs tc_args(pcv_ctx *x, int C, bool need_ll) {
 
 pcv_status ensure_ws_tc(pcv_ctx *x, int C) {
   TcArgs t = tc_args(x, C, false);
-  const size_t need = (size_t)t.T * t.max_seg * (t.PN + kTcSlots) * 128;
+  // sized for the larger of the default grid (one CTA per SM) and the tuned
+  // one, so that either can run without a reallocation
+  const int seg_default = tc_segments_per_tile(t.T, t.J, (int)std::min<long long>(x->n_sm, (long long)t.T * t.J));
+  const size_t need = (size_t)t.T * std::max(t.max_seg, seg_default) * (t.PN + kTcSlots) * 128;
   if (need > x->ws_tc_floats) {
     float *w;
     if (!dalloc_n(x, &w, need)) return fail(x, PCV_E_OOM, "workspace allocation failed");
@@ -407,6 +415,24 @@ pcv_status tune(pcv_ctx *x, ChainBufs &cb) {
   if (x->tc) x->tuned_ns[std::make_pair(C, need_lo)] = best;
   else x->tuned_splits[C] = best;
   x->tune_log.push_back(log + " -> " + std::to_string(best));
+  if (x->tc && x->tuned_ncta.count(C) == 0) {
+    // grid: one CTA per SM (tiles split across CTAs, stream-K) or, when
+    // there are fewer tiles than SMs, one CTA per tile
+    const int T = (C + 127) / 128;
+    if (T < x->n_sm) {
+      x->tuned_ncta[C] = T;
+      float ms = 0.0f;
+      pcv_status s = time_launch(&ms);
+      if (s != PCV_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
+      const bool per_tile = ms < best_ms;
+      x->tune_log.push_back("tensor-core grid for " + std::to_string(C) + " chains: " + std::to_string(x->n_sm) +
+                            " CTAs=" + std::to_string(best_ms / 3.0f) + "ms " + std::to_string(T) + " CTAs=" +
+                            std::to_string(ms / 3.0f) + "ms -> " + std::to_string(per_tile ? T : x->n_sm));
+      x->tuned_ncta[C] = per_tile ? T : x->n_sm;
+    } else {
+      x->tuned_ncta[C] = x->n_sm;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return PCV_OK;
@@ -1367,7 +1393,7 @@ struct CkptHeader {
   uint64_t seed;
   int64_t n_sampled;
   int32_t state, centered;
-  int32_t tuned_splits, tuned_ns0, tuned_ns1;
+  int32_t tuned_splits, tuned_ns0, tuned_ns1, tuned_ncta;
   int32_t first_fold;
   float jitter;
   double traj_len;
@@ -1448,6 +1474,8 @@ pcv_status pcv_checkpoint_save(pcv_ctx *x, void *buf, int64_t bytes) {
   auto n0 = x->tuned_ns.find(std::make_pair(x->C, 0)), n1 = x->tuned_ns.find(std::make_pair(x->C, 1));
   h.tuned_ns0 = n0 != x->tuned_ns.end() ? n0->second : -1;
   h.tuned_ns1 = n1 != x->tuned_ns.end() ? n1->second : -1;
+  auto nc = x->tuned_ncta.find(x->C);
+  h.tuned_ncta = nc != x->tuned_ncta.end() ? nc->second : -1;
   enter(x);
   uint8_t *out = static_cast<uint8_t *>(buf);
   std::memcpy(out, &h, sizeof(h));
@@ -1491,6 +1519,7 @@ pcv_status pcv_checkpoint_load(pcv_ctx *x, const void *buf, int64_t bytes) {
   if (h.tuned_splits > 0) x->tuned_splits[x->C] = h.tuned_splits;
   if (h.tuned_ns0 > 0) x->tuned_ns[std::make_pair(x->C, 0)] = h.tuned_ns0;
   if (h.tuned_ns1 > 0) x->tuned_ns[std::make_pair(x->C, 1)] = h.tuned_ns1;
+  if (h.tuned_ncta > 0) x->tuned_ncta[x->C] = h.tuned_ncta;
   // the bf16 shadows and the eta_ref columns of X follow from the restored
   // positions and reference
   pcv_status s = write_shadow(x, x->fold_cb, x->fold_cb.theta, x->d_pad);
