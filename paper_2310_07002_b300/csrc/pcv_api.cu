@@ -759,8 +759,16 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
   x->d_pad = (x->d + 3) / 4 * 4;
 
   // data checks
-  for (int64_t i = 0; i < N * p; ++i)
-    if (!std::isfinite(X[i])) return bail(PCV_E_NUMERIC, "non-finite X");
+  {
+    // exponent all ones = Inf or NaN; a branch-free pass the compiler vectorises
+    uint32_t bad = 0;
+    for (int64_t i = 0; i < N * p; ++i) {
+      uint32_t u;
+      std::memcpy(&u, X + i, sizeof(u));
+      bad |= (uint32_t)((u & 0x7f800000u) == 0x7f800000u);
+    }
+    if (bad) return bail(PCV_E_NUMERIC, "non-finite X");
+  }
   for (int64_t i = 0; i < N; ++i) {
     if (!std::isfinite(y[i])) return bail(PCV_E_NUMERIC, "non-finite y");
     if (x->kind == PCV_LOGISTIC && y[i] != 0.0f && y[i] != 1.0f)
@@ -785,12 +793,19 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
   std::iota(x->perm.begin(), x->perm.end(), 0);
   auto fkey = [&](int64_t i) { return fold_assignment[i] < 0 ? K : fold_assignment[i]; };
   if (x->h == 0) {
-    std::stable_sort(x->perm.begin(), x->perm.end(), [&](int64_t a, int64_t b) {
-      const int fa = fkey(a), fb = fkey(b);
-      if (fa != fb) return fa < fb;
-      if (x->variant == MV_HIER) return model->group[a] < model->group[b];
-      return false;
-    });
+    // stable counting sorts (the keys are small integers): by group first
+    // (hierarchical model), then by fold, so rows end up ordered by
+    // (fold, group) and by original index within equal keys
+    auto counting_pass = [&](int nkeys, auto key) {
+      std::vector<int64_t> start((size_t)nkeys + 1, 0);
+      for (int64_t r = 0; r < N; ++r) start[(size_t)key(x->perm[r]) + 1]++;
+      for (int k = 0; k < nkeys; ++k) start[(size_t)k + 1] += start[(size_t)k];
+      std::vector<int64_t> out((size_t)N);
+      for (int64_t r = 0; r < N; ++r) out[(size_t)start[(size_t)key(x->perm[r])]++] = x->perm[r];
+      x->perm.swap(out);
+    };
+    if (x->variant == MV_HIER) counting_pass(x->G, [&](int64_t i) { return model->group[i]; });
+    counting_pass(K + 1, fkey);
   }
   std::vector<FoldDesc> fds(K + 1, FoldDesc{0, 0, 0, 0});
   std::vector<int64_t> cnt(K, 0), lo(K, -1), hi(K, -1);
