@@ -362,6 +362,15 @@ pcv_status pcv_checkpoint_load(pcv_ctx *ctx, const void *buf, int64_t bytes);
  * counterpart in the paper. */
 pcv_status pcv_tuning_info(const pcv_ctx *ctx, char *buf, int32_t len);
 
+/* Host wall-clock milliseconds that the context has spent, so far, in the
+ * autotuner (*autotune_ms: timing candidate launch configurations, once per
+ * chain set) and in capturing and instantiating CUDA graphs
+ * (*graph_capture_ms: once per kind of iteration). Both are part of the
+ * pcv_warmup / pcv_sample wall clock; they are reported apart because they
+ * do not recur. Host pointers, caller-owned; PCV_E_INVALID_ARG if any is
+ * null. No counterpart in the paper. */
+pcv_status pcv_setup_ms(const pcv_ctx *ctx, double *autotune_ms, double *graph_capture_ms);
+
 /* Device time in milliseconds of the most recent pcv_sample call (CUDA events
  * on the context stream). */
 pcv_status pcv_last_sample_ms(pcv_ctx *ctx, double *ms);

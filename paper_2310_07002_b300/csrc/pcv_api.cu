@@ -6,6 +6,7 @@
 // captured once as CUDA graphs and replayed, with all counters in device
 // memory.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -109,6 +110,9 @@ struct pcv_ctx {
   std::map<std::pair<int, int>, int> tuned_ns;
   std::map<int, int> tuned_ncta;          // tensor-core grid per chain count (one CTA per tile or one per SM)
   std::vector<std::string> tune_log;
+  // host wall clock spent autotuning and capturing / instantiating graphs
+  // (both inside pcv_warmup / pcv_sample; reported apart from them)
+  double tune_ms = 0.0, capture_ms = 0.0;
   // Hyvarinen / Dawid-Sebastiani accumulators
   Extra extra{};
   double *extra_out = nullptr;
@@ -374,6 +378,12 @@ pcv_status tune(pcv_ctx *x, ChainBufs &cb) {
   const int C = cb.C;
   const int need_lo = x->centered ? 0 : 1;
   if (x->tc ? x->tuned_ns.count(std::make_pair(C, need_lo)) > 0 : x->tuned_splits.count(C) > 0) return PCV_OK;
+  const auto w0 = std::chrono::steady_clock::now();
+  struct AddWall {   // adds the wall time of this call on every return path
+    double *acc;
+    std::chrono::steady_clock::time_point t0;
+    ~AddWall() { *acc += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count(); }
+  } add_wall{&x->tune_ms, w0};
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -564,6 +574,7 @@ pcv_status run_iterations(pcv_ctx *x, ChainBufs &cb, bool fd, bool accumulate, l
   pcv_status s0 = x->tc ? ensure_ws_tc(x, cb.C) : ensure_ws(x, cb.C, splits_for(x, cb.C));
   if (s0 != PCV_OK) return s0;
   if (!*cache) {
+    const auto w0 = std::chrono::steady_clock::now();
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(x->stream, cudaStreamCaptureModeThreadLocal));
     pcv_status s = PCV_OK;
@@ -574,6 +585,7 @@ pcv_status run_iterations(pcv_ctx *x, ChainBufs &cb, bool fd, bool accumulate, l
     e = cudaGraphInstantiate(cache, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail_cuda(x, "cudaGraphInstantiate", e);
+    x->capture_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
   }
   long long full = count / per_graph, rest = count - full * per_graph;
   for (long long i = 0; i < full; ++i) CK(cudaGraphLaunch(*cache, x->stream));
@@ -1643,6 +1655,13 @@ pcv_status pcv_tuning_info(const pcv_ctx *x, char *buf, int32_t len) {
   std::string s;
   for (const std::string &l : x->tune_log) s += l + "\n";
   std::snprintf(buf, (size_t)len, "%s", s.c_str());
+  return PCV_OK;
+}
+
+pcv_status pcv_setup_ms(const pcv_ctx *x, double *autotune_ms, double *graph_capture_ms) {
+  if (!x || !autotune_ms || !graph_capture_ms) return PCV_E_INVALID_ARG;
+  *autotune_ms = x->tune_ms;
+  *graph_capture_ms = x->capture_ms;
   return PCV_OK;
 }
 

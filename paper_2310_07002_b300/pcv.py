@@ -106,6 +106,7 @@ def load():
         "pcv_get_draws": (i32, [vp, vp, ct.POINTER(i32)]),
         "pcv_accept_rate": (i32, [vp, vp]),
         "pcv_last_sample_ms": (i32, [vp, ct.POINTER(f64)]),
+        "pcv_setup_ms": (i32, [vp, ct.POINTER(f64), ct.POINTER(f64)]),
         "pcv_time_leapfrog_kernel": (i32, [vp, i32, ct.POINTER(f64)]),
         "pcv_log_density_noalloc": (i32, [vp, vp, vp, i32, i32, vp, vp, vp]),
     }
@@ -126,7 +127,7 @@ def exported_symbols():
             "pcv_get_draws", "pcv_accept_rate", "pcv_last_sample_ms",
             "pcv_time_leapfrog_kernel", "pcv_log_density_noalloc", "pcv_tuning_info",
             "pcv_checkpoint_size", "pcv_checkpoint_save", "pcv_checkpoint_load",
-            "pcv_rhat_shuffle", "pcv_compare", "pcv_scores_extra"]
+            "pcv_rhat_shuffle", "pcv_compare", "pcv_scores_extra", "pcv_setup_ms"]
 
 
 def _ptr(a: Optional[np.ndarray]):
@@ -368,6 +369,13 @@ class PCV:
         buf = ct.create_string_buffer(4096)
         self._check(self._L.pcv_tuning_info(self.h, buf, len(buf)), "pcv_tuning_info")
         return buf.value.decode()
+
+    def setup_ms(self):
+        """Host milliseconds spent so far in the autotuner and in CUDA-graph
+        capture (both inside warmup / sample, reported apart)."""
+        a, g = ct.c_double(), ct.c_double()
+        self._check(self._L.pcv_setup_ms(self.h, ct.byref(a), ct.byref(g)), "pcv_setup_ms")
+        return {"autotune_ms": a.value, "graph_capture_ms": g.value}
 
     def adaptation(self):
         e = ct.c_double()

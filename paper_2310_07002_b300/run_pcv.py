@@ -63,9 +63,14 @@ def run(w, precision: str, draws: int, fd_warmup: int, fold_warmup: int, seed: i
     eps, _ = pc.adaptation()
     acc = pc.accept_rate()
     C = pc.C
+    su = pc.setup_ms()
     if not keep:
         pc.close()
     t["total_s"] = sum(t.values())
+    # one-off costs inside warm-up and sampling, stated apart (not added to
+    # the total a second time)
+    t["of_which_autotune_s"] = su["autotune_ms"] / 1e3
+    t["of_which_graph_capture_s"] = su["graph_capture_ms"] / 1e3
     evals = float(C) * w.leapfrog_steps * (fold_warmup + draws)
     out = {
         "precision": precision, "seed": seed, "chains": C,

@@ -313,6 +313,8 @@ def test_graph_replay_equals_plain_launches(torch, precision):
         sc = pc.scores()
         dg = pc.diagnostics()
         out.append((th, lp, sh, sc["elpd"], dg["rhat"], dg["ess_acov"]))
+        su = pc.setup_ms()
+        assert su["autotune_ms"] == 0.0 and (su["graph_capture_ms"] > 0.0) == graphs, su
         pc.close()
     for a, b in zip(*out):
         assert np.array_equal(a, b)
@@ -326,6 +328,9 @@ def test_autotuner_records_its_choice_and_results_hold(torch, orc, precision):
     pc.warmup(40, 20)
     info = pc.tuning_info()
     assert "->" in info and "chains" in info, info
+    # its wall clock and the graph captures' are kept apart from the run's
+    su = pc.setup_ms()
+    assert su["autotune_ms"] > 0.0 and su["graph_capture_ms"] > 0.0, su
     # the tuned launch still computes the oracle's gradient
     prob = orc.problem_from_workload(w)
     th = W.random_theta(w.dim, pc.C, scale=0.3, seed=3)
