@@ -229,7 +229,9 @@ pcv_status pcv_diagnostics(pcv_ctx *ctx, double *rhat_k, double *split_rhat_k,
 int32_t pcv_num_folds(const pcv_ctx *ctx);    /* K, or -1 for NULL */
 int32_t pcv_num_chains(const pcv_ctx *ctx);   /* K * L */
 int32_t pcv_dim(const pcv_ctx *ctx);          /* dimension of theta */
-const char *pcv_last_error(const pcv_ctx *ctx);  /* never NULL; valid until the next call */
+/* Never NULL; valid until the next call. With ctx == NULL: the message of
+ * the calling thread's last failed pcv_create ("null context" if none). */
+const char *pcv_last_error(const pcv_ctx *ctx);
 void pcv_destroy(pcv_ctx *ctx);               /* frees all device memory; NULL is a no-op */
 
 /* ---------------- inspection and test entry points ---------------- */

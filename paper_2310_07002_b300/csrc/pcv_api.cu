@@ -666,6 +666,13 @@ pcv_status finalize(pcv_ctx *x) {
   return PCV_OK;
 }
 
+// message of the calling thread's last failed pcv_create (there is no
+// context to hold it)
+std::string &create_error() {
+  static thread_local std::string m = "null context";
+  return m;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -700,16 +707,21 @@ void pcv_default_options(pcv_options *o) {
 pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
                       const int32_t *fold_assignment, int64_t N, int32_t p, int32_t chains_per_fold,
                       const pcv_options *opt, pcv_ctx **out) {
-  if (!out) return PCV_E_INVALID_ARG;
+  auto invalid = [](const char *m) {
+    create_error() = m;
+    return PCV_E_INVALID_ARG;
+  };
+  if (!out) return invalid("out is NULL");
   *out = nullptr;
-  if (!model || !X || !y || !fold_assignment || !opt) return PCV_E_INVALID_ARG;
-  if (N < 1 || p < 1 || chains_per_fold < 2 || N > (int64_t)1 << 30) return PCV_E_INVALID_ARG;
+  if (!model || !X || !y || !fold_assignment || !opt) return invalid("a required pointer is NULL");
+  if (N < 1 || p < 1 || chains_per_fold < 2 || N > (int64_t)1 << 30)
+    return invalid("need 1 <= N <= 2^30, p >= 1 and chains_per_fold >= 2");
   if (opt->leapfrog_steps < 1 || opt->batch_size < 1 || opt->hv_buffer < 0 ||
       opt->acov_max_lag < 0 || opt->max_batches < 1 || opt->n_fulldata_draws < 1 ||
       !(opt->step_jitter < 1.0) || !std::isfinite(opt->trajectory_length) || opt->first_fold < 0)
-    return PCV_E_INVALID_ARG;
-  if (model->kind < PCV_GAUSS_LINEAR || model->kind > PCV_AR_GAUSS) return PCV_E_INVALID_ARG;
-  if (!(model->beta_prior_sd > 0)) return PCV_E_INVALID_ARG;
+    return invalid("an option is out of range");
+  if (model->kind < PCV_GAUSS_LINEAR || model->kind > PCV_AR_GAUSS) return invalid("unknown model kind");
+  if (!(model->beta_prior_sd > 0)) return invalid("beta_prior_sd must be > 0");
 
   pcv_ctx *x = new pcv_ctx();
   x->opt = *opt;
@@ -725,13 +737,12 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
     x->jitter = (float)(opt->step_jitter < 0 ? (adapted ? 0.5 : 0.0) : opt->step_jitter);
   }
   auto bail = [&](pcv_status s, const std::string &m) {
-    // creation failed: release everything; report through a static message
-    static thread_local std::string last;
-    last = m;
+    // creation failed: release everything; the message stays with the
+    // calling thread for pcv_last_error(NULL)
+    create_error() = m;
     free_all(x);
     if (x->own_stream && x->stream) cudaStreamDestroy(x->stream);
     delete x;
-    std::fprintf(stderr, "pcv_create: %s\n", last.c_str());
     return s;
   };
   if (opt->precision < PCV_FP32_SIMT || opt->precision > PCV_BF16) return bail(PCV_E_INVALID_ARG, "bad precision");
@@ -1149,7 +1160,7 @@ pcv_status pcv_diagnostics(pcv_ctx *x, double *rhat_k, double *split_rhat_k, dou
 int32_t pcv_num_folds(const pcv_ctx *x) { return x ? x->K : -1; }
 int32_t pcv_num_chains(const pcv_ctx *x) { return x ? x->C : -1; }
 int32_t pcv_dim(const pcv_ctx *x) { return x ? x->d : -1; }
-const char *pcv_last_error(const pcv_ctx *x) { return x ? x->err.c_str() : "null context"; }
+const char *pcv_last_error(const pcv_ctx *x) { return x ? x->err.c_str() : create_error().c_str(); }
 
 void pcv_destroy(pcv_ctx *x) {
   if (!x) return;

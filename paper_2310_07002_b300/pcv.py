@@ -231,7 +231,7 @@ class PCV:
         st = L.pcv_create(ct.byref(m), _ptr(X), _ptr(y), _ptr(fold), N, p, chains_per_fold,
                           ct.byref(o), ct.byref(h))
         if st != OK:
-            raise PCVError(st, "pcv_create failed (see stderr)")
+            raise PCVError(st, "pcv_create: %s" % L.pcv_last_error(None).decode())
         self.h = h
         self.K = L.pcv_num_folds(h)
         self.C = L.pcv_num_chains(h)

@@ -66,8 +66,9 @@ def test_create_rejects_bad_arguments_before_any_cuda_call(libpcv):
     L.pcv_default_options(ct.byref(o))
     m = Model(0, 10.0, 1.0, 1.0, 1.0, None, 0)
     h = ct.c_void_p()
-    # null data pointers
+    # null data pointers; the message stays with the thread for pcv_last_error(NULL)
     assert L.pcv_create(ct.byref(m), None, None, None, 10, 2, 4, ct.byref(o), ct.byref(h)) == E_INVALID_ARG
+    assert b"NULL" in L.pcv_last_error(None)
     import numpy as np
     X = np.zeros((10, 2), np.float32)
     y = np.zeros(10, np.float32)
@@ -76,15 +77,23 @@ def test_create_rejects_bad_arguments_before_any_cuda_call(libpcv):
     for N, p, Lc in [(10, 2, 1), (10, 0, 4), (0, 2, 4)]:
         assert L.pcv_create(ct.byref(m), X.ctypes.data, y.ctypes.data, f.ctypes.data, N, p, Lc,
                             ct.byref(o), ct.byref(h)) == E_INVALID_ARG
+        assert b"chains_per_fold" in L.pcv_last_error(None)
     # bad options
     o.batch_size = 0
     assert L.pcv_create(ct.byref(m), X.ctypes.data, y.ctypes.data, f.ctypes.data, 10, 2, 4,
                         ct.byref(o), ct.byref(h)) == E_INVALID_ARG
+    assert L.pcv_last_error(None) == b"an option is out of range"
     L.pcv_default_options(ct.byref(o))
     o.step_jitter = 1.0                      # a step size of zero would be possible
     assert L.pcv_create(ct.byref(m), X.ctypes.data, y.ctypes.data, f.ctypes.data, 10, 2, 4,
                         ct.byref(o), ct.byref(h)) == E_INVALID_ARG
     assert not h.value
     assert L.pcv_num_folds(None) == -1
-    assert L.pcv_last_error(None) == b"null context"
+    assert L.pcv_last_error(None) == b"an option is out of range"
+    # a model kind the library does not know
+    L.pcv_default_options(ct.byref(o))
+    m.kind = 99
+    assert L.pcv_create(ct.byref(m), X.ctypes.data, y.ctypes.data, f.ctypes.data, 10, 2, 4,
+                        ct.byref(o), ct.byref(h)) == E_INVALID_ARG
+    assert L.pcv_last_error(None) == b"unknown model kind"
     L.pcv_destroy(None)

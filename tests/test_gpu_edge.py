@@ -116,3 +116,4 @@ def test_fold_without_test_rows_is_rejected(torch, precision):
     with pytest.raises(PCVError) as e:
         PCV(LOGISTIC, w.X, w.y, fold, 2, precision=PRECISIONS[precision])
     assert e.value.status == E_INVALID_ARG
+    assert "fold 4 has no test rows" in str(e.value)
