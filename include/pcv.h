@@ -17,8 +17,9 @@
  *
  * Conventions shared by every call:
  *   - Every call returns a pcv_status; nothing throws or aborts across the
- *     ABI.  On failure the context (when there is one) keeps a message for
- *     pcv_last_error.
+ *     ABI.  On failure the context keeps a message for pcv_last_error; a
+ *     failed pcv_create leaves its message with the calling thread
+ *     (pcv_last_error(NULL)).
  *   - "host" pointers are ordinary CPU memory owned by the caller; "device"
  *     pointers are CUDA global memory on the context's device, owned by the
  *     caller.  The library never retains a caller pointer after a call
