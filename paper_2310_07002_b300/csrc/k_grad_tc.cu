@@ -6,9 +6,16 @@
 // GEMMs in BF16 with FP32 accumulation:
 //
 //   S = Theta_tile . X_chunk^T      (128 chains x 128 rows, K = p + 3)  -> TMEM
-//   R = mask .* (y - sigmoid(2 S))  (epilogue, FP32, rounded to BF16)   -> TMEM
+//   R = mask .* (1 - tanh(S))       (epilogue, FP32, rounded to BF16)   -> TMEM
 //       (Gaussian: mask .* (y - 2 S) / sigma^2)
 //   G += R . X_chunk                (128 chains x p, K = 128 rows)      -> TMEM
+//
+// Logistic model: row n of the stored design matrix is s_n x_n with
+// s_n = 2 y_n - 1, so S = s eta / 2 and, as y - sigmoid(eta) =
+// s (1 - tanh(s eta / 2)) / 2, the likelihood gradient is G / 2 with no
+// response in the epilogue; 1 - tanh keeps its relative precision for rows
+// the model already predicts well.  The log likelihood of a row is
+// -softplus(-s eta).
 //
 // R is the A operand of the second GEMM straight from TMEM, so shared memory
 // carries only Theta, X and y: with both operands of both GEMMs in SMEM the
@@ -20,7 +27,7 @@
 // row's eta_ref / 2 = x . theta_ref / 2 enters the same GEMM: three more K
 // columns of X hold it as hi + mid + lo bf16 parts and the hi shadow holds 1
 // there, so S is eta / 2 straight from the tensor cores and
-// sigmoid(eta) = 1/2 + tanh(S)/2 needs no per-row addition.  The same SMEM X tile is the
+// the epilogue needs no per-row addition.  The same SMEM X tile is the
 // K-major B operand of the first GEMM and the MN-major B operand of the
 // second.  Launches that need log densities accumulate hi + lo (an
 // FP32-accurate eta for the Metropolis test); the kick-drift launches use
@@ -29,9 +36,8 @@
 // itself it was a few percent, enough to slow mixing); HMC stays exact
 // because the accept test uses the accurate log density.
 // Where log densities are needed (last leapfrog step, evaluations) the
-// epilogue also sums softplus(eta) over the fold's training and test rows;
-// the linear part y eta of the log likelihood is theta . sum(y x), from
-// per-fold sums made once at create.
+// epilogue also sums softplus(-s eta) over the fold's training and test
+// rows.
 //
 // Work: persistent CTAs (one per SM) take equal contiguous ranges of the
 // flattened (chain tile, row chunk) units ("stream-K").  A CTA flushes its G
@@ -333,7 +339,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint8_t *th_hi = sm;
   uint8_t *th_lo = th_hi + th_bytes;
   uint8_t *xs = th_lo + (ta.need_lo ? th_bytes : 0);
-  float *ys = reinterpret_cast<float *>(xs + (size_t)NS * x_bytes);   // NS x kTN: y - 1/2
+  float *ys = reinterpret_cast<float *>(xs + (size_t)NS * x_bytes);   // NS x kTN: y (Gaussian models)
   uint64_t *bars = reinterpret_cast<uint64_t *>(ys + NS * kTN + 16);
   // barrier slots (up to kTcMaxStages X stages)
   uint64_t *x_full = bars, *x_empty = bars + kTcMaxStages;
@@ -406,11 +412,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         const int st = i % NS, rnd = i / NS;
         if (!mbar_wait_fast(smem_u32(&x_empty[st]), (rnd & 1) ^ 1, abort_flag, ta.err)) break;
-        mbar_expect_tx(smem_u32(&x_full[st]), x_bytes + kTN * 4);
+        mbar_expect_tx(smem_u32(&x_full[st]), x_bytes + (GAUSS ? kTN * 4 : 0));
         uint8_t *xb = xs + (size_t)st * x_bytes;
         for (int kb = 0; kb < KA; ++kb)
           tma_load_2d(smem_u32(xb + kb * kTN * 128), &tm_x, kb * 64, j * kTN, smem_u32(&x_full[st]));
-        bulk_load(smem_u32(ys + st * kTN), ta.yc + (size_t)j * kTN, kTN * 4, smem_u32(&x_full[st]));
+        if (GAUSS)   // the logistic epilogue reads no response (sign-folded rows)
+          bulk_load(smem_u32(ys + st * kTN), ta.yc + (size_t)j * kTN, kTN * 4, smem_u32(&x_full[st]));
         last_round[st] = rnd;
       }
       // on abort: let copies already issued land before the CTA exits
@@ -540,31 +547,27 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int i = ib + ((ib & 1) != eg ? 1 : 0); i < ie; i += 2) {
         const int j = j0 + (i - ib);
         if (!warp_wait(smem_u32(&s_full[sb]), (i >> 1) & 1, abort_flag, ta.err)) { aborted = true; break; }
-        // the X stage of this unit is still resident (its release needs R);
-        // waiting on its barrier makes the TMA-written y visible
-        if (!warp_wait(smem_u32(&x_full[i % NS]), (i / NS) & 1, abort_flag, ta.err)) { aborted = true; break; }
+        // Gaussian models read the staged y: the X stage of this unit is
+        // still resident (its release needs R), and waiting on its barrier
+        // makes the TMA-written y visible
+        if (GAUSS && !warp_wait(smem_u32(&x_full[i % NS]), (i / NS) & 1, abort_flag, ta.err)) { aborted = true; break; }
         tc_fence_after();
         const float2 *ywu = reinterpret_cast<const float2 *>(ys + (i % NS) * kTN);
         // residual of quarter qq (32 rows) of the chunk from v = S into pk
         // (16 bf16x2), plus the log-likelihood sums when ACC
         auto quarter = [&](const int qq, const uint32_t (&v)[32], uint32_t (&pk)[16]) {
           const int n0 = j * kTN + 32 * qq;
-          // staged response of rows 2k, 2k + 1: y - 1/2 (logistic) or y
-          const float2 *yw = ywu + 16 * qq;
           if constexpr (!GAUSS) {
-            // residual y - sigmoid(eta) = (y - 1/2) - tanh(S)/2 in FP32, rounded
-            // to bf16 for the second GEMM (the same function on every leapfrog
-            // step). A bf16x2 tanh here would bias the gradient: its error is
-            // a smooth function of eta, so it adds up over rows instead of
-            // averaging out (a force error of ~6 % of the posterior scale per
-            // dimension at N = 1e5, which shrinks the adapted step size).
+            // 1 - tanh(S) in FP32 (twice the residual along the sign-folded
+            // row), rounded to bf16 for the second GEMM.  A bf16x2 tanh here
+            // would bias the gradient: its error is a smooth function of eta,
+            // so it adds up over rows instead of averaging out (a force error
+            // of ~6 % of the posterior scale per dimension at N = 1e5, which
+            // shrinks the adapted step size).
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-              const float2 y2 = yw[k];
-              const float ta = tanh_f32(__uint_as_float(v[2 * k]));
-              const float tb = tanh_f32(__uint_as_float(v[2 * k + 1]));
-              pk[k] = bf16x2_from(fmaf(-0.5f, ta, y2.x), fmaf(-0.5f, tb, y2.y));
-            }
+            for (int k = 0; k < 16; ++k)
+              pk[k] = bf16x2_from(1.0f - tanh_f32(__uint_as_float(v[2 * k])),
+                                  1.0f - tanh_f32(__uint_as_float(v[2 * k + 1])));
             if (valid && n0 < fd.excl_hi && n0 + 32 > fd.excl_lo) {
 #pragma unroll
               for (int k = 0; k < 32; ++k) {
@@ -573,10 +576,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               }
             }
             if constexpr (accurate) {
-              // log likelihood y eta - softplus(eta): the linear part is
-              // theta . sum(y x) per fold (added in the finish), so only
-              // softplus(eta) = max(eta, 0) + log(1 + exp(-|eta|)) is summed
-              // here, in FP32 per quarter and FP64 across quarters.
+              // log likelihood y eta - softplus(eta) = -softplus(-2 S) with
+              // the sign-folded S: softplus(-2 S) = max(-2 S, 0) +
+              // log(1 + exp(-|2 S|)) is summed here, in FP32 per quarter and
+              // FP64 across quarters.
               // Quarters clear of the fold's excluded rows and of the
               // padding need no per-row mask; there the logs of eight rows
               // are taken at once, as the log of the product of their
@@ -592,7 +595,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 for (int k = 0; k < 32; ++k) {
                   const float s = __uint_as_float(v[k]);
                   pr[k & 3] = fmaf(pr[k & 3], exp_neg_abs_eta(s), pr[k & 3]);
-                  mx[k & 3] += fmaxf(s, 0.0f);
+                  mx[k & 3] += fmaxf(-s, 0.0f);
                 }
                 float lg[4];
 #pragma unroll
@@ -611,7 +614,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll 1
                 for (int k = 0; k < 32; ++k) {
                   const int n = n0 + k;
-                  const float sp = softplus_half(sq[k]);
+                  const float sp = softplus_half(-sq[k]);
                   if (n < pb.N && (n < fd.excl_lo || n >= fd.excl_hi)) tr += sp;
                   if (n >= fd.test_lo && n < fd.test_hi) te += sp;
                 }
@@ -621,6 +624,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
 
           } else {
+            const float2 *yw = ywu + 16 * qq;   // staged y of rows 2k, 2k + 1
             // Gaussian: residual (y - eta) / sigma^2 with eta = 2 S, rounded
             // to bf16; the squared residuals of the fold's training and test
             // rows feed the log sigma gradient and the log densities
@@ -810,8 +814,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
           for (int u = 0; u < kFinU; ++u) {
             if (!ok[u]) continue;
-            const float4 g = make_float4(gs[u].x - tv[u].x * pb.beta_prec, gs[u].y - tv[u].y * pb.beta_prec,
-                                         gs[u].z - tv[u].z * pb.beta_prec, gs[u].w - tv[u].w * pb.beta_prec);
+            const float gsc = GAUSS ? 1.0f : 0.5f;   // logistic: the likelihood gradient is G / 2
+            const float4 g = make_float4(fmaf(gsc, gs[u].x, -tv[u].x * pb.beta_prec),
+                                         fmaf(gsc, gs[u].y, -tv[u].y * pb.beta_prec),
+                                         fmaf(gsc, gs[u].z, -tv[u].z * pb.beta_prec),
+                                         fmaf(gsc, gs[u].w, -tv[u].w * pb.beta_prec));
             *reinterpret_cast<float4 *>(a.grad + (size_t)cc_[u] * a.ld_grad + jj_[u]) = g;
             if (a.mode == MODE_NONE) continue;
             const float4 r4 = make_float4(rv[u].x + kick * g.x, rv[u].y + kick * g.y, rv[u].z + kick * g.z,
@@ -843,7 +850,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           const float tv = th[jj];
           float gs = 0.0f;
           for (int s2 = 0; s2 < nseg; ++s2) gs += __ldcg(base + s2 * seg_stride + (size_t)mm * wstride + jj);
-          const float g = gs - tv * pb.beta_prec;
+          const float g = fmaf(GAUSS ? 1.0f : 0.5f, gs, -tv * pb.beta_prec);
           a.grad[(size_t)cc * a.ld_grad + jj] = g;
           if (a.mode != MODE_NONE) {
             float *rr = a.r + (size_t)cc * a.ld_theta;
@@ -897,19 +904,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           // is the evaluation point)
           const float *th = a.theta + (size_t)cc * a.ld_theta;
           if constexpr (!GAUSS) {
-            // linear part theta . sum(y x) and the log prior, in a fixed order
-            const double *yl = ta.ylin + (size_t)fold_of_chain(a, cc) * 2 * pb.p;
-            double q = 0.0, lin_tr = 0.0, lin_te = 0.0;
+            // the log prior, in a fixed order; the likelihood sums are -s0, -s1
+            double q = 0.0;
 #pragma unroll 4
-            for (int jj = 0; jj < pb.p; ++jj) {
-              const double tv = (double)th[jj];
-              q = fma(tv, tv, q);
-              lin_tr = fma(tv, yl[jj], lin_tr);
-              lin_te = fma(tv, yl[pb.p + jj], lin_te);
-            }
+            for (int jj = 0; jj < pb.p; ++jj) q = fma((double)th[jj], (double)th[jj], q);
             const double lprior = (double)pb.p * (-0.5 * kLog2PiD - (double)pb.log_beta_sd) - 0.5 * pb.beta_prec * q;
-            a.logp[cc] = (lin_tr - s0) + lprior;
-            a.shat[cc] = lin_te - s1;
+            a.logp[cc] = lprior - s0;
+            a.shat[cc] = -s1;
           } else {
             // sum of -log(2 pi)/2 - log sigma - e^2 / (2 sigma^2) over the
             // fold's training / test rows, and the log priors
@@ -960,7 +961,7 @@ size_t tc_smem_bytes(int KP, int NS, int need_lo, int p) {
   (void)p;
   const size_t KA = KP / 64;
   size_t b = KA * kTM * 128 * (need_lo ? 2 : 1) + (size_t)NS * KA * kTN * 128 +
-             (size_t)NS * kTN * 4 + 64 + (2 * kTcMaxStages + 23) * 8;   // y - 1/2; barrier / flag slots
+             (size_t)NS * kTN * 4 + 64 + (2 * kTcMaxStages + 23) * 8;   // staged y; barrier / flag slots
   return b + 1024;   // alignment slack
 }
 

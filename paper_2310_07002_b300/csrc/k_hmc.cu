@@ -645,45 +645,16 @@ __global__ void k_gather_rows(long long N, int p, int p_pad, const int *perm, co
   const int j = (int)(t - r * p);
   X[r * p_pad + j] = xraw[(long long)perm[r] * p + j];
 }
-__global__ void k_x_bf16(long long N, int p, int p_pad, int KP, const float *X, __nv_bfloat16 *X16) {
+// bf16 copy of X; with ysign (logistic model) row r is multiplied by
+// s_r = 2 y_r - 1 (exact in bf16), so that the first GEMM yields s eta / 2
+__global__ void k_x_bf16(long long N, int p, int p_pad, int KP, const float *X, const float *ysign,
+                         __nv_bfloat16 *X16) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= N * p) return;
   const long long r = t / p;
   const int j = (int)(t - r * p);
-  X16[r * KP + j] = __float2bfloat16_rn(X[r * p_pad + j]);
-}
-// all[j] = sum over every row with y = 1 of x16[r][j], FP64: per-thread
-// strided partial sums, then a fixed tree over the block (deterministic)
-__global__ void __launch_bounds__(256) k_ylin_all(int N, int KP, const __nv_bfloat16 *X16, const float *y,
-                                                  double *all) {
-  __shared__ double red[256];
-  const int j = blockIdx.x;
-  double s = 0.0;
-  for (int r = threadIdx.x; r < N; r += 256)
-    if (y[r] != 0.0f) s += (double)__bfloat162float(X16[(size_t)r * KP + j]);
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) all[j] = red[0];
-}
-// per fold k (K = the full data) and dimension j: training-row sum
-// all[j] - (sum over the fold's excluded rows) and the test-row sum
-__global__ void k_ylin_folds(int K, int p, int KP, const __nv_bfloat16 *X16, const float *y, const FoldDesc *folds,
-                             const double *all, double *ylin) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (K + 1) * p) return;
-  const int k = t / p, j = t - k * p;
-  const FoldDesc f = folds[k];
-  double ex = 0.0, te = 0.0;
-  for (int r = f.excl_lo; r < f.excl_hi; ++r)
-    if (y[r] != 0.0f) ex += (double)__bfloat162float(X16[(size_t)r * KP + j]);
-  for (int r = f.test_lo; r < f.test_hi; ++r)
-    if (y[r] != 0.0f) te += (double)__bfloat162float(X16[(size_t)r * KP + j]);
-  ylin[(size_t)k * 2 * p + j] = all[j] - ex;
-  ylin[(size_t)k * 2 * p + p + j] = te;
+  const float v = X[r * p_pad + j];
+  X16[r * KP + j] = __float2bfloat16_rn(ysign && ysign[r] == 0.0f ? -v : v);
 }
 
 // eta_ref / 2 of every row into the operand columns p .. p + kEtaCols - 1 of

@@ -96,10 +96,9 @@ struct pcv_ctx {
   bool tc = false;
   int KP = 0, KS = 0, PN = 0, N_pad = 0, J = 0, n_sm = 148;
   __nv_bfloat16 *X16 = nullptr;
-  float *ycf = nullptr;           // tensor-core path: y - 1/2 per row (N_pad)
+  float *ycf = nullptr;           // tensor-core path: y per row (N_pad; Gaussian models)
   CUtensorMap tm_x{};
   float *ws_tc = nullptr;
-  double *ylin = nullptr;         // tensor-core path: per-fold sums of y x (see TcArgs)
   float *theta_ref = nullptr;     // tensor-core path: centring reference (d_pad)
   float *eta_half = nullptr;      // tensor-core path: x . theta_ref / 2 per row (N_pad)
   bool centered = false;          // a reference has been set
@@ -298,7 +297,6 @@ TcArgs tc_args(pcv_ctx *x, int C, bool need_ll) {
   t.yc = x->ycf;
   t.theta_ref = x->theta_ref;
   t.ws = x->ws_tc;
-  t.ylin = x->ylin;
   t.tickets = x->tickets_tc;
   t.err = &x->st->error;
   return t;
@@ -920,26 +918,17 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
     // bf16 design matrix [N_pad x KP] (round to nearest even; padding rows
     // and columns stay 0) and the staged response
     std::vector<float> hyc((size_t)x->N_pad, 0.0f);
-    for (int64_t r = 0; r < N; ++r) hyc[r] = x->kind == PCV_LOGISTIC ? hy[r] - 0.5f : hy[r];
+    for (int64_t r = 0; r < N; ++r) hyc[r] = hy[r];
     if (!dalloc_n(x, &x->X16, (size_t)x->N_pad * x->KP) || !dalloc_n(x, &x->ycf, hyc.size()) ||
-        !dalloc_n(x, &x->ylin, (size_t)(K + 1) * 2 * p) || !dalloc_n(x, &x->theta_ref, (size_t)x->d_pad) ||
+        !dalloc_n(x, &x->theta_ref, (size_t)x->d_pad) ||
         !dalloc_n(x, &x->eta_half, (size_t)x->N_pad))
       return bail(PCV_E_OOM, "device allocation failed");
     const long long items = (long long)N * p;
-    k_x_bf16<<<(unsigned)((items + 255) / 256), 256, 0, x->stream>>>(N, p, x->p_pad, x->KP, x->X, x->X16);
+    // logistic model: rows signed by 2 y - 1 (the kernel's residual and log
+    // likelihood are written for that form)
+    k_x_bf16<<<(unsigned)((items + 255) / 256), 256, 0, x->stream>>>(
+        N, p, x->p_pad, x->KP, x->X, x->kind == PCV_LOGISTIC ? x->y : nullptr, x->X16);
     cudaMemcpyAsync(x->ycf, hyc.data(), hyc.size() * sizeof(float), cudaMemcpyHostToDevice, x->stream);
-    if (x->kind == PCV_LOGISTIC) {
-      // per fold: sum over training rows and over test rows of y_n x_n, with
-      // the bf16 X the tensor cores see (the linear part of the logistic log
-      // likelihood is theta . these sums); fold K is the full data
-      double *all = nullptr;
-      if (cudaMallocAsync(reinterpret_cast<void **>(&all), sizeof(double) * p, x->stream) != cudaSuccess)
-        return bail(PCV_E_OOM, "staging allocation failed");
-      k_ylin_all<<<p, 256, 0, x->stream>>>((int)N, x->KP, x->X16, x->y, all);
-      k_ylin_folds<<<((K + 1) * p + 255) / 256, 256, 0, x->stream>>>(K, p, x->KP, x->X16, x->y, x->folds, all,
-                                                                     x->ylin);
-      cudaFreeAsync(all, x->stream);
-    }
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(x->stream) != cudaSuccess)
       return bail(PCV_E_CUDA, "upload failed");
     if (!encode_bf16_map(&x->tm_x, x->X16, x->N_pad, x->KP))

@@ -201,10 +201,8 @@ struct TcArgs {
   int NS;                 // X pipeline stages
   int need_lo;            // accumulate the theta lo part too (FP32-accurate eta)
   int accurate;           // FP32 epilogue with log densities (else the bf16x2 fast path)
-  const float *yc;        // N_pad: y - 1/2 (zero for padded rows)
+  const float *yc;        // N_pad: y (zero for padded rows); read by the Gaussian models
   const float *theta_ref; // d: the shadows hold (theta - theta_ref) / 2
-  const double *ylin;     // (K + 1) x 2 x p: sums over the training / test rows of
-                          // fold k of y_n x_n (bf16 X); k = K is the full data
   float *ws;              // T x max_seg x (PN + kTcSlots) x 128
   unsigned int *tickets;  // T
   unsigned int *err;      // error flags (bit 0: wait time-out)
@@ -306,10 +304,8 @@ __global__ void k_eta_ref(int N, int N_pad, int p, int KP, const __nv_bfloat16 *
                           float *eta_half);
 __global__ void k_eta_fold(int N_pad, int p, int KP, const float *eta_half, __nv_bfloat16 *X16);
 __global__ void k_gather_rows(long long N, int p, int p_pad, const int *perm, const float *xraw, float *X);
-__global__ void k_x_bf16(long long N, int p, int p_pad, int KP, const float *X, __nv_bfloat16 *X16);
-__global__ void k_ylin_all(int N, int KP, const __nv_bfloat16 *X16, const float *y, double *all);
-__global__ void k_ylin_folds(int K, int p, int KP, const __nv_bfloat16 *X16, const float *y, const FoldDesc *folds,
-                             const double *all, double *ylin);
+__global__ void k_x_bf16(long long N, int p, int p_pad, int KP, const float *X, const float *ysign,
+                         __nv_bfloat16 *X16);
 __global__ void k_shadow_ones(int C_pad, int p, int KP, __nv_bfloat16 *hi);
 // k_begin: a chain takes this many lanes (the power of two that covers its
 // ceil(d/4) coordinate quads, at most 32), so small models pack 32 / that
