@@ -71,6 +71,37 @@ def test_bf16_log_density_and_gradient(torch, orc, p):
     pc.close()
 
 
+def test_bf16_gradient_where_the_model_predicts_well(torch, orc):
+    # separable data evaluated at 4x the separating direction: every residual
+    # y - sigmoid(eta) is ~1e-3 or smaller, so the likelihood gradient is a
+    # sum of small residuals that BF16 must keep to relative precision (a
+    # bf16 value of sigmoid or tanh itself would round them to 0 or 2e-3)
+    import dataclasses
+    from paper_2310_07002_b300.pcv import PCV, BF16
+    w0 = W.logistic_loo(N=1037, p=20, K=40, L=4, bf16=True)
+    beta = w0.truth["beta"]
+    w = dataclasses.replace(w0, y=(w0.X.astype(np.float64) @ beta > 0).astype(np.float64))
+    pc = PCV.from_workload(w, precision=BF16)
+    prob = orc.problem_from_workload(w)
+    n = 128
+    th = 4.0 * beta[None, :] + 0.05 * W.random_theta(w.dim, n, scale=1.0, seed=23)
+    tt = torch.tensor(th, dtype=torch.float32, device="cuda")
+    folds = np.arange(n) % (w.K + 1)
+    lp, g, _ = pc.log_density(tt, torch.tensor(folds, dtype=torch.int32, device="cuda"), BF16)
+    torch.cuda.synchronize()
+    th = tt.cpu().double().numpy()
+    ref = [orc.log_density(prob, -1 if k == w.K else int(k), th[i]) for i, k in enumerate(folds)]
+    lr = np.array([r[0] for r in ref]); gr = np.stack([r[1] for r in ref])
+    # the likelihood part of the gradient (prior removed) is what the residuals carry
+    prior = -th / w.beta_prior_sd ** 2
+    e_g = rel_vec(g.cpu().double().numpy() - prior, gr - prior).max()
+    e_lp = rel_scalar(lp.cpu().numpy(), lr).max()
+    print("bf16 separable: logp %.2e likelihood gradient %.2e" % (e_lp, e_g))
+    assert e_lp <= 1e-4
+    assert e_g <= 1e-2
+    pc.close()
+
+
 @pytest.mark.parametrize("p", [20, 100, 128])
 def test_bf16_trajectory(torch, orc, p):
     from paper_2310_07002_b300.pcv import PCV, BF16
