@@ -18,16 +18,16 @@
 // -softplus(-s eta).
 //
 // R is the A operand of the second GEMM straight from TMEM, so shared memory
-// carries only Theta, X and y: with both operands of both GEMMs in SMEM the
-// MMAs alone saturate its bandwidth.
+// carries only Theta, X and (Gaussian models) y: with both operands of both
+// GEMMs in SMEM the MMAs alone saturate its bandwidth.
 //
 // The tensor cores see theta centred on a reference theta_ref (the mean of
 // the full-data draws, or of the positions a caller sets) and scaled by 1/2:
 // the shadows hold (theta - theta_ref) / 2 in bf16 hi + lo parts.  The
 // row's eta_ref / 2 = x . theta_ref / 2 enters the same GEMM: three more K
 // columns of X hold it as hi + mid + lo bf16 parts and the hi shadow holds 1
-// there, so S is eta / 2 straight from the tensor cores and
-// the epilogue needs no per-row addition.  The same SMEM X tile is the
+// there, so S is eta / 2 (logistic: s eta / 2) straight from the tensor
+// cores and the epilogue needs no per-row addition.  The same SMEM X tile is the
 // K-major B operand of the first GEMM and the MN-major B operand of the
 // second.  Launches that need log densities accumulate hi + lo (an
 // FP32-accurate eta for the Metropolis test); the kick-drift launches use
