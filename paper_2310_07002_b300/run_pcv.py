@@ -59,7 +59,9 @@ def run(w, precision: str, draws: int, fd_warmup: int, fold_warmup: int, seed: i
     dg = pc.diagnostics()
     t["finalize_s"] = time.perf_counter() - t0
     # R-hat_max benchmark (Section 4.2): 500 block-shuffled replicates, 5 blocks
+    t0 = time.perf_counter()
     rep = pc.rhat_shuffle(5, 500) if draws // w.batch_size >= 5 else None
+    shuffle_s = time.perf_counter() - t0
     eps, _ = pc.adaptation()
     acc = pc.accept_rate()
     C = pc.C
@@ -71,6 +73,7 @@ def run(w, precision: str, draws: int, fd_warmup: int, fold_warmup: int, seed: i
     # the total a second time)
     t["of_which_autotune_s"] = su["autotune_ms"] / 1e3
     t["of_which_graph_capture_s"] = su["graph_capture_ms"] / 1e3
+    t["rhat_shuffle_benchmark_s"] = shuffle_s   # after the run, not in the total
     evals = float(C) * w.leapfrog_steps * (fold_warmup + draws)
     out = {
         "precision": precision, "seed": seed, "chains": C,
@@ -145,10 +148,12 @@ def main():
         act = np.ones(w.p, np.int32)
         act[[int(v) for v in args.drop_covariates.split(",")]] = 0
         b_run, _, _, pb = run(dataclasses.replace(w, active=act), args.precision, draws, fdw, fow, seed, keep=True)
+        t0 = time.perf_counter()
         c = pa.compare(pb)
+        compare_s = time.perf_counter() - t0
         line["selection"] = {"dropped": args.drop_covariates, "model_b": b_run,
                              "delta": c["delta"], "se": c["se"], "mcse": c["mcse"],
-                             "prob_a_better": c["prob"]}
+                             "prob_a_better": c["prob"], "compare_s": compare_s}
         pa.close()
         pb.close()
     print(json.dumps(line), flush=True)
