@@ -7,7 +7,7 @@
 //
 //   S = Theta_tile . X_chunk^T      (128 chains x 128 rows, K = p + 3)  -> TMEM
 //   R = mask .* (1 - tanh(S))       (epilogue, FP32, rounded to BF16)   -> TMEM
-//       (Gaussian: mask .* (y - 2 S) / sigma^2)
+//       (Gaussian: mask .* (-2 S) / sigma^2, S = (eta - y) / 2)
 //   G += R . X_chunk                (128 chains x p, K = 128 rows)      -> TMEM
 //
 // Logistic model: row n of the stored design matrix is s_n x_n with
@@ -17,9 +17,12 @@
 // the model already predicts well.  The log likelihood of a row is
 // -softplus(-s eta).
 //
+// Gaussian models: the folded columns hold (eta_ref - y) / 2, so S =
+// (eta - y) / 2 and the residual needs no response either.
+//
 // R is the A operand of the second GEMM straight from TMEM, so shared memory
-// carries only Theta, X and (Gaussian models) y: with both operands of both
-// GEMMs in SMEM the MMAs alone saturate its bandwidth.
+// carries only Theta and X: with both operands of both GEMMs in SMEM the
+// MMAs alone saturate its bandwidth.
 //
 // The tensor cores see theta centred on a reference theta_ref (the mean of
 // the full-data draws, or of the positions a caller sets) and scaled by 1/2:
@@ -339,8 +342,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint8_t *th_hi = sm;
   uint8_t *th_lo = th_hi + th_bytes;
   uint8_t *xs = th_lo + (ta.need_lo ? th_bytes : 0);
-  float *ys = reinterpret_cast<float *>(xs + (size_t)NS * x_bytes);   // NS x kTN: y (Gaussian models)
-  uint64_t *bars = reinterpret_cast<uint64_t *>(ys + NS * kTN + 16);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(xs + (size_t)NS * x_bytes + 64);
   // barrier slots (up to kTcMaxStages X stages)
   uint64_t *x_full = bars, *x_empty = bars + kTcMaxStages;
   // r_part[4 b + qq]: quarter qq (32 rows) of R buffer b is in TMEM, so the
@@ -412,12 +414,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         const int st = i % NS, rnd = i / NS;
         if (!mbar_wait_fast(smem_u32(&x_empty[st]), (rnd & 1) ^ 1, abort_flag, ta.err)) break;
-        mbar_expect_tx(smem_u32(&x_full[st]), x_bytes + (GAUSS ? kTN * 4 : 0));
+        mbar_expect_tx(smem_u32(&x_full[st]), x_bytes);
         uint8_t *xb = xs + (size_t)st * x_bytes;
         for (int kb = 0; kb < KA; ++kb)
           tma_load_2d(smem_u32(xb + kb * kTN * 128), &tm_x, kb * 64, j * kTN, smem_u32(&x_full[st]));
-        if (GAUSS)   // the logistic epilogue reads no response (sign-folded rows)
-          bulk_load(smem_u32(ys + st * kTN), ta.yc + (size_t)j * kTN, kTN * 4, smem_u32(&x_full[st]));
         last_round[st] = rnd;
       }
       // on abort: let copies already issued land before the CTA exits
@@ -547,12 +547,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int i = ib + ((ib & 1) != eg ? 1 : 0); i < ie; i += 2) {
         const int j = j0 + (i - ib);
         if (!warp_wait(smem_u32(&s_full[sb]), (i >> 1) & 1, abort_flag, ta.err)) { aborted = true; break; }
-        // Gaussian models read the staged y: the X stage of this unit is
-        // still resident (its release needs R), and waiting on its barrier
-        // makes the TMA-written y visible
-        if (GAUSS && !warp_wait(smem_u32(&x_full[i % NS]), (i / NS) & 1, abort_flag, ta.err)) { aborted = true; break; }
         tc_fence_after();
-        const float2 *ywu = reinterpret_cast<const float2 *>(ys + (i % NS) * kTN);
         // residual of quarter qq (32 rows) of the chunk from v = S into pk
         // (16 bf16x2), plus the log-likelihood sums when ACC
         auto quarter = [&](const int qq, const uint32_t (&v)[32], uint32_t (&pk)[16]) {
@@ -624,16 +619,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
 
           } else {
-            const float2 *yw = ywu + 16 * qq;   // staged y of rows 2k, 2k + 1
-            // Gaussian: residual (y - eta) / sigma^2 with eta = 2 S, rounded
+            // Gaussian: residual (y - eta) / sigma^2 = -2 S / sigma^2, rounded
             // to bf16; the squared residuals of the fold's training and test
             // rows feed the log sigma gradient and the log densities
             float e[32];
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
-              const float2 y2 = yw[k];
-              e[2 * k] = fmaf(-2.0f, __uint_as_float(v[2 * k]), y2.x);
-              e[2 * k + 1] = fmaf(-2.0f, __uint_as_float(v[2 * k + 1]), y2.y);
+              e[2 * k] = -2.0f * __uint_as_float(v[2 * k]);
+              e[2 * k + 1] = -2.0f * __uint_as_float(v[2 * k + 1]);
               pk[k] = bf16x2_from(e[2 * k] * inv_s2, e[2 * k + 1] * inv_s2);
             }
             if (valid && n0 < fd.excl_hi && n0 + 32 > fd.excl_lo) {
@@ -961,7 +954,7 @@ size_t tc_smem_bytes(int KP, int NS, int need_lo, int p) {
   (void)p;
   const size_t KA = KP / 64;
   size_t b = KA * kTM * 128 * (need_lo ? 2 : 1) + (size_t)NS * KA * kTN * 128 +
-             (size_t)NS * kTN * 4 + 64 + (2 * kTcMaxStages + 23) * 8;   // staged y; barrier / flag slots
+             64 + (2 * kTcMaxStages + 23) * 8;   // barrier / flag slots
   return b + 1024;   // alignment slack
 }
 

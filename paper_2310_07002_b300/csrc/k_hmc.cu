@@ -660,10 +660,13 @@ __global__ void k_x_bf16(long long N, int p, int p_pad, int KP, const float *X, 
 // eta_ref / 2 of every row into the operand columns p .. p + kEtaCols - 1 of
 // the bf16 design matrix, as a sum of kEtaCols bf16 parts (each part rounds
 // what the previous ones left: 24 significant bits, the precision of eta_half)
-__global__ void k_eta_fold(int N_pad, int p, int KP, const float *eta_half, __nv_bfloat16 *X16) {
+__global__ void k_eta_fold(int N_pad, int p, int KP, const float *eta_half, const float *y,
+                           __nv_bfloat16 *X16) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N_pad) return;
-  float rest = eta_half[n];
+  // Gaussian models (y given): (eta_ref - y) / 2, so that the first GEMM
+  // yields (eta - y) / 2 and the epilogue needs no response
+  float rest = y ? eta_half[n] - 0.5f * y[n] : eta_half[n];
 #pragma unroll
   for (int k = 0; k < kEtaCols; ++k) {
     const __nv_bfloat16 part = __float2bfloat16_rn(rest);

@@ -96,7 +96,7 @@ struct pcv_ctx {
   bool tc = false;
   int KP = 0, KS = 0, PN = 0, N_pad = 0, J = 0, n_sm = 148;
   __nv_bfloat16 *X16 = nullptr;
-  float *ycf = nullptr;           // tensor-core path: y per row (N_pad; Gaussian models)
+  float *ycf = nullptr;           // tensor-core path: y per row (N_pad; folded into X16 for Gaussian models)
   CUtensorMap tm_x{};
   float *ws_tc = nullptr;
   float *theta_ref = nullptr;     // tensor-core path: centring reference (d_pad)
@@ -294,7 +294,6 @@ TcArgs tc_args(pcv_ctx *x, int C, bool need_ll) {
   t.NS = tc_max_fit_stages(x, t.need_lo);
   auto it = x->tuned_ns.find(std::make_pair(C, t.need_lo));
   if (it != x->tuned_ns.end()) t.NS = it->second;
-  t.yc = x->ycf;
   t.theta_ref = x->theta_ref;
   t.ws = x->ws_tc;
   t.tickets = x->tickets_tc;
@@ -459,7 +458,9 @@ pcv_status write_shadow(pcv_ctx *x, ChainBufs &cb, const float *theta, int ld) {
 
 // eta_ref / 2 (eta_half) into the operand columns of the bf16 design matrix
 pcv_status fold_eta(pcv_ctx *x) {
-  k_eta_fold<<<(x->N_pad + 255) / 256, 256, 0, x->stream>>>(x->N_pad, x->p, x->KP, x->eta_half, x->X16);
+  // Gaussian models fold -y / 2 into the same columns (zero-padded y)
+  k_eta_fold<<<(x->N_pad + 255) / 256, 256, 0, x->stream>>>(x->N_pad, x->p, x->KP, x->eta_half,
+                                                           x->kind == PCV_LOGISTIC ? nullptr : x->ycf, x->X16);
   CK(cudaGetLastError());
   return PCV_OK;
 }
@@ -929,6 +930,10 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
     k_x_bf16<<<(unsigned)((items + 255) / 256), 256, 0, x->stream>>>(
         N, p, x->p_pad, x->KP, x->X, x->kind == PCV_LOGISTIC ? x->y : nullptr, x->X16);
     cudaMemcpyAsync(x->ycf, hyc.data(), hyc.size() * sizeof(float), cudaMemcpyHostToDevice, x->stream);
+    // no reference yet (eta_ref = 0): the folded columns hold -y / 2
+    // (Gaussian models) or 0
+    cudaMemsetAsync(x->eta_half, 0, sizeof(float) * x->N_pad, x->stream);
+    if (fold_eta(x) != PCV_OK) return bail(PCV_E_CUDA, "upload failed");
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(x->stream) != cudaSuccess)
       return bail(PCV_E_CUDA, "upload failed");
     if (!encode_bf16_map(&x->tm_x, x->X16, x->N_pad, x->KP))

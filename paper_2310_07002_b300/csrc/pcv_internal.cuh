@@ -201,7 +201,6 @@ struct TcArgs {
   int NS;                 // X pipeline stages
   int need_lo;            // accumulate the theta lo part too (FP32-accurate eta)
   int accurate;           // FP32 epilogue with log densities (else the bf16x2 fast path)
-  const float *yc;        // N_pad: y (zero for padded rows); read by the Gaussian models
   const float *theta_ref; // d: the shadows hold (theta - theta_ref) / 2
   float *ws;              // T x max_seg x (PN + kTcSlots) x 128
   unsigned int *tickets;  // T
@@ -302,7 +301,8 @@ __global__ void k_rhat_shuffle(const double *blk, int K, int L, int D, int R, un
 __global__ void k_theta_ref(int n, int d, int ld, const float *src, float *theta_ref);
 __global__ void k_eta_ref(int N, int N_pad, int p, int KP, const __nv_bfloat16 *X16, const float *theta_ref,
                           float *eta_half);
-__global__ void k_eta_fold(int N_pad, int p, int KP, const float *eta_half, __nv_bfloat16 *X16);
+__global__ void k_eta_fold(int N_pad, int p, int KP, const float *eta_half, const float *y,
+                           __nv_bfloat16 *X16);
 __global__ void k_gather_rows(long long N, int p, int p_pad, const int *perm, const float *xraw, float *X);
 __global__ void k_x_bf16(long long N, int p, int p_pad, int KP, const float *X, const float *ysign,
                          __nv_bfloat16 *X16);
