@@ -153,6 +153,16 @@ def oracle_rate(w, seconds: float, n_chains_target: int, threads: int):
     return evals / el, desc, threads
 
 
+def bench_config(w, args):
+    """The workload description both arms print (the reference arm times the
+    same workload, so its `config` is this arm's)."""
+    return {"workload": w.name, "N": w.N, "p": w.p, "K": w.K, "L": w.chains_per_fold,
+            "chains": w.K * w.chains_per_fold, "leapfrog_steps": w.leapfrog_steps,
+            "precision": args.precision,
+            "l2": "flushed (256 MB write) before every timed step",
+            "parallelism": "replica per GPU (independent fold-chains)"}
+
+
 def run_reference(args, w):
     """Reference arm: the FP64 oracle on the host cores, bounded samples."""
     threads = os.cpu_count() or 1
@@ -169,8 +179,7 @@ def run_reference(args, w):
         "impl": "reference", "metric": "leapfrog grad-evals/s over all fold-chains",
         "value": value, "unit": "grad-evals/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "N": w.N, "p": w.p, "K": w.K, "L": w.chains_per_fold,
-                   "leapfrog_steps": w.leapfrog_steps},
+        "config": bench_config(w, args),
         "cpu_baseline": {"value": value, "unit": "grad-evals/s", "cores": threads,
                          "kind": "oracle", "sample": "each step: " + desc},
         "e2e": {"value": value, "unit": "grad-evals/s", "h2d_bytes_per_step": 0,
@@ -338,10 +347,7 @@ def main():
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "tf32": "tf32", "bf16": "bf16"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": w.name, "N": w.N, "p": w.p, "K": w.K, "L": w.chains_per_fold,
-                   "chains": C, "leapfrog_steps": Lf, "precision": args.precision,
-                   "l2": "flushed (256 MB write) before every timed step",
-                   "parallelism": "replica per GPU (independent fold-chains)"},
+        "config": bench_config(w, args),
         "gpu_launches": K * (Lf + 2),
         "roofline": roof,
         "clocks": clk,
