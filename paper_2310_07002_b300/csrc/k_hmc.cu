@@ -635,8 +635,8 @@ __global__ void k_eta_ref(int N, int N_pad, int p, int KP, const __nv_bfloat16 *
 }
 // ---------------------------------------------------------------------------
 // data set-up on the device (pcv_create): the caller's X rows gathered into
-// the fold-sorted layout, its bf16 copy for the tensor cores, and the
-// per-fold sums of y_n x_n of the logistic log likelihood's linear part
+// the fold-sorted layout and its bf16 copy for the tensor cores (logistic
+// rows signed by 2 y - 1)
 // ---------------------------------------------------------------------------
 __global__ void k_gather_rows(long long N, int p, int p_pad, const int *perm, const float *xraw, float *X) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;

@@ -917,7 +917,8 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
   cudaMemcpyAsync(x->folds, fds.data(), fds.size() * sizeof(FoldDesc), cudaMemcpyHostToDevice, x->stream);
   if (x->tc) {
     // bf16 design matrix [N_pad x KP] (round to nearest even; padding rows
-    // and columns stay 0) and the staged response
+    // and columns stay 0) and y on the device (zero-padded), which the
+    // Gaussian models fold into the eta_ref columns
     std::vector<float> hyc((size_t)x->N_pad, 0.0f);
     for (int64_t r = 0; r < N; ++r) hyc[r] = hy[r];
     if (!dalloc_n(x, &x->X16, (size_t)x->N_pad * x->KP) || !dalloc_n(x, &x->ycf, hyc.size()) ||
