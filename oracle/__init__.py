@@ -25,13 +25,16 @@ Parity status of each function (pins live in ``tests/test_oracle_*.py``):
 * covariate-selection mask and pairwise comparison -- pinned by the
   conjugate closed form of the sub-design model (its fold elpd within MCSE)
   and of the difference of two models, and by scipy's normal cdf.
-* full-data warm-up (dual averaging, mass estimate) -- parity unpinned
-  beyond the conjugate-model checks: it is an adaptive heuristic with no
-  closed form; its outputs are only checked statistically.
+* full-data warm-up adaptation (dual averaging, mass windows) -- pinned by
+  Hoffman & Gelman's closed form of the dual-averaging iterate and of its
+  average, closed-loop convergence to the acceptance target on a known
+  acceptance curve, numpy's sample variance over exactly the two window
+  ranges of known draws (and the restart from the current step), and the
+  exact full-data posterior variances of the conjugate Gaussian model.
 """
 from .oracle import (  # noqa: F401
     build, lib, Problem, problem_from_workload, philox, normals, uniform,
-    index, log_density, trajectory, accumulate_series, shuffle_series, rhat_from_picks, compare,
+    index, log_density, trajectory, accumulate_series, adapt_trace, shuffle_series, rhat_from_picks, compare,
     OraclePCV,
     FOLD_FIELDS, TOTAL_FIELDS,
 )

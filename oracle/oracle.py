@@ -95,6 +95,11 @@ def _declare(L):
     L.orc_pcv_set_tuning.restype = ct.c_int
     L.orc_pcv_fulldata.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_double]
     L.orc_pcv_fulldata.restype = ct.c_int
+    L.orc_pcv_fulldata_accept.argtypes = [ct.c_void_p, _D, _D]
+    L.orc_pcv_fulldata_accept.restype = ct.c_int
+    L.orc_adapt_trace.argtypes = [ct.c_int32, ct.c_int32, ct.c_int32, _D, _D, ct.c_double, ct.c_int32,
+                                  ct.c_int32, _D, ct.POINTER(ct.c_int32), ct.c_int32, _D, _D, _D]
+    L.orc_adapt_trace.restype = ct.c_int
     L.orc_pcv_fold_warmup.argtypes = [ct.c_void_p, ct.c_int32]
     L.orc_pcv_fold_warmup.restype = ct.c_int
     L.orc_pcv_set_state.argtypes = [ct.c_void_p, _D, ct.c_double, _D]
@@ -158,6 +163,29 @@ def compare(elpd_a, mcse_a, elpd_b, mcse_b):
     out = np.empty(4)
     assert lib().orc_compare(K, _dp(ea), _dp(ma), _dp(eb), _dp(mb), _dp(dk), _dp(mk), _dp(out)) == 0
     return {"delta_k": dk, "mcse_k": mk, "delta": out[0], "se": out[1], "mcse": out[2], "prob": out[3]}
+
+
+def adapt_trace(accept, draws, eps0=0.1, adapt_eps=True, adapt_mass=True, minv0=None,
+                active=None):
+    """The full-data warm-up adaptation (Section 3.1) driven by given inputs:
+    accept[i] is the chains' mean acceptance statistic after iteration i and
+    draws[i, c, :] the position of chain c after it.  Returns (step size after
+    each iteration [n], inverse mass after each iteration [n, d], final step
+    size with no cap)."""
+    acc = np.ascontiguousarray(accept, dtype=np.float64)
+    dr = np.ascontiguousarray(draws, dtype=np.float64)
+    n, nc, d = dr.shape
+    assert acc.shape == (n,)
+    m0 = np.ones(d) if minv0 is None else np.ascontiguousarray(minv0, dtype=np.float64)
+    act = None if active is None else np.ascontiguousarray(active, dtype=np.int32)
+    eps = np.empty(n)
+    minv = np.empty((n, d))
+    fin = ct.c_double()
+    rc = lib().orc_adapt_trace(n, nc, d, _dp(acc), _dp(dr), eps0, int(adapt_eps), int(adapt_mass), _dp(m0),
+                               None if act is None else act.ctypes.data_as(ct.POINTER(ct.c_int32)),
+                               0 if act is None else act.size, _dp(eps), _dp(minv), ct.byref(fin))
+    assert rc == 0
+    return eps, minv, fin.value
 
 
 def philox(ctr, key):
@@ -275,6 +303,15 @@ class OraclePCV:
 
     def fulldata(self, n_adapt: int, n_keep: int, eps0: float = 0.1):
         assert lib().orc_pcv_fulldata(self.h, n_adapt, n_keep, eps0) == 0
+
+    def fulldata_accept(self):
+        """Mean acceptance statistics of the full-data chains: over the
+        adaptation iterations since dual averaging last (re)started, and over
+        the iterations kept in the pool (fixed settings)."""
+        t = ct.c_double()
+        k = ct.c_double()
+        assert lib().orc_pcv_fulldata_accept(self.h, ct.byref(t), ct.byref(k)) == 0
+        return t.value, k.value
 
     def fold_warmup(self, n_wu: int):
         assert lib().orc_pcv_fold_warmup(self.h, n_wu) == 0

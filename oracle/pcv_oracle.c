@@ -920,6 +920,8 @@ typedef struct {
      * its outer product (plain sums: the oracle favours the obvious form) */
     int32_t extra, T;         /* extra: 1 HS, 2 DSS; T: largest test set */
     double *hs1, *hs2, *dsum, *douter;   /* C, C x T, C x T, C x T x T */
+    double fd_tail_accept;    /* mean acceptance statistic since the last dual-averaging start */
+    double fd_keep_accept;    /* mean acceptance statistic of the pool draws */
 } orc_pcv;
 
 orc_pcv *orc_pcv_create(const orc_problem *P, int32_t L, uint64_t seed, int32_t Lf, double eps,
@@ -1146,18 +1148,118 @@ static void da_update(dual_avg *D, double accept_stat)
 }
 
 /*
+ * The full-data warm-up adaptation (warm-up reuse, Section 3.1), one call per
+ * completed adaptation iteration i = 0 .. n-1 (n = n_adapt):
+ *   - the step size follows dual averaging on the chains' mean acceptance
+ *     statistic (if it is adapted);
+ *   - when the inverse mass is adapted too, the positions of iterations
+ *     [n/4, n/2) form the first window and those of [n/2, 7n/8) the second;
+ *     at the end of each window the diagonal inverse mass becomes
+ *       minv_j = w var_j + 1e-3 (1 - w),  w = m / (m + 5)
+ *     (var_j the sample variance of coordinate j over the m = chains x
+ *     iterations draws of the window, m - 1 degrees of freedom), masked
+ *     covariates stay at 0, and dual averaging restarts from the current
+ *     step size.
+ */
+typedef struct {
+    int32_t d, p, adapt_eps, adapt_mass, w0, w1, w2;
+    const int32_t *active;    /* p flags or NULL */
+    dual_avg D;
+    double eps;               /* current step size */
+    double *minv;             /* d, caller-owned */
+    double wn, *wmean, *wM2;  /* Welford sums of the open window */
+} warm_adapt;
+
+static void wa_init(warm_adapt *A, int32_t n_adapt, int32_t d, int32_t p, const int32_t *active,
+                    int adapt_eps, int adapt_mass, double eps0, double *minv)
+{
+    A->d = d; A->p = p; A->active = active;
+    A->adapt_eps = adapt_eps; A->adapt_mass = adapt_eps && adapt_mass;
+    A->w0 = n_adapt / 4; A->w1 = n_adapt / 2; A->w2 = (7 * n_adapt) / 8;
+    A->eps = eps0;
+    da_reset(&A->D, eps0);
+    A->minv = minv;
+    A->wn = 0.0;
+    A->wmean = (double *)calloc((size_t)d, sizeof(double));
+    A->wM2 = (double *)calloc((size_t)d, sizeof(double));
+}
+static void wa_free(warm_adapt *A) { free(A->wmean); free(A->wM2); }
+
+/* after adaptation iteration i: mean acceptance statistic of the chains and
+ * their positions theta[c] (nc chains); returns 1 if minv changed */
+static int wa_step(warm_adapt *A, int32_t i, double mean_accept, int32_t nc, const double *const *theta)
+{
+    if (A->adapt_eps) {
+        da_update(&A->D, mean_accept);
+        A->eps = exp(A->D.logeps);
+    }
+    if (!A->adapt_mass || i < A->w0 || i >= A->w2) return 0;
+    for (int32_t c = 0; c < nc; ++c) {
+        A->wn += 1.0;
+        for (int32_t j = 0; j < A->d; ++j) {
+            double dl = theta[c][j] - A->wmean[j];
+            A->wmean[j] += dl / A->wn;
+            A->wM2[j] += dl * (theta[c][j] - A->wmean[j]);
+        }
+    }
+    if ((i != A->w1 - 1 && i != A->w2 - 1) || !(A->wn > 1)) return 0;
+    double w = A->wn / (A->wn + 5.0);
+    for (int32_t j = 0; j < A->d; ++j) A->minv[j] = w * (A->wM2[j] / (A->wn - 1.0)) + 1e-3 * (1.0 - w);
+    if (A->active)
+        for (int32_t j = 0; j < A->p; ++j) if (!A->active[j]) A->minv[j] = 0.0;
+    da_reset(&A->D, A->eps);
+    A->wn = 0.0;                                  /* the next window starts afresh */
+    for (int32_t j = 0; j < A->d; ++j) { A->wmean[j] = 0.0; A->wM2[j] = 0.0; }
+    return 1;
+}
+
+/* the step size after adaptation: the dual-averaged exp(logeps_bar), capped
+ * at cap (<= 0: no cap) */
+static double wa_final_eps(const warm_adapt *A, double cap)
+{
+    double e = exp(A->D.logeps_bar);
+    return (cap > 0 && e > cap) ? cap : e;
+}
+
+/*
+ * The adaptation driven by given inputs instead of HMC transitions (for the
+ * tests): accept[i] is the mean acceptance statistic after iteration i and
+ * draws[(i nc + c) d + j] the position of chain c after it.  Outputs: the
+ * step size after each iteration (eps_out, n_adapt), the inverse mass after
+ * each iteration (minv_out, n_adapt x d, starting from minv0) and the final
+ * step size with no cap.
+ */
+int orc_adapt_trace(int32_t n_adapt, int32_t nc, int32_t d, const double *accept, const double *draws,
+                    double eps0, int32_t adapt_eps, int32_t adapt_mass, const double *minv0,
+                    const int32_t *active, int32_t p, double *eps_out, double *minv_out, double *eps_final)
+{
+    warm_adapt A;
+    double *minv = (double *)malloc(sizeof(double) * (size_t)d);
+    const double **th = (const double **)malloc(sizeof(double *) * (size_t)nc);
+    for (int32_t j = 0; j < d; ++j) minv[j] = minv0[j];
+    wa_init(&A, n_adapt, d, p, active, adapt_eps, adapt_mass, eps0, minv);
+    for (int32_t i = 0; i < n_adapt; ++i) {
+        for (int32_t c = 0; c < nc; ++c) th[c] = draws + ((size_t)i * nc + c) * d;
+        wa_step(&A, i, accept[i], nc, th);
+        eps_out[i] = A.eps;
+        memcpy(minv_out + (size_t)i * d, minv, sizeof(double) * (size_t)d);
+    }
+    *eps_final = wa_final_eps(&A, 0.0);
+    wa_free(&A);
+    free(minv); free(th);
+    return 0;
+}
+
+/*
  * Full-data step (Step 1 of the workflow, as far as PCV needs it):
- * NFD = 4 full-data chains start from init_scale * N(0,1) (stream 18).
- * n_adapt iterations adapt eps by dual averaging (if no step size was given);
- * when no inverse mass was given, the draws of two windows, iterations
- * [n/4, n/2) and then [n/2, 7n/8) (n = n_adapt), each estimate a diagonal
- * inverse mass, regularised as
- *   minv = w var + 1e-3 (1 - w), w = m / (m + 5)   (m draws in the window),
- * after which dual averaging restarts from the current step size (the second
- * window sees chains that have settled and a sampler tuned to the first).
- * The final step size is the dual-averaged exp(logeps_bar), capped at
- * traj_len / L_f.  Then n_keep iterations at fixed settings give the pool of
- * 4 n_keep full-data draws (Algorithm 1, "draw from {theta^(fd)}").
+ * NFD = 4 full-data chains start from init_scale * N(0,1) (stream 18) and
+ * run n_adapt iterations under the adaptation above (the step size when none
+ * was given, from eps0; the inverse mass as well when neither was given).
+ * The final step size is the dual-averaged one, capped at traj_len / L_f.
+ * Then n_keep iterations at fixed settings give the pool of 4 n_keep
+ * full-data draws (Algorithm 1, "draw from {theta^(fd)}").  The mean
+ * acceptance statistics of the last dual-averaging phase and of the kept
+ * draws are recorded for the tests.
  */
 #define NFD 4
 int orc_pcv_fulldata(orc_pcv *S, int32_t n_adapt, int32_t n_keep, double eps0)
@@ -1165,25 +1267,25 @@ int orc_pcv_fulldata(orc_pcv *S, int32_t n_adapt, int32_t n_keep, double eps0)
     const orc_problem *P = &S->P;
     const int32_t d = S->d;
     orc_chain ch[NFD];
+    const double *th[NFD];
     double *buf = (double *)calloc((size_t)NFD * 2 * d, sizeof(double));
     double *work = (double *)malloc(sizeof(double) * 3 * (size_t)d);
     for (int32_t c = 0; c < NFD; ++c) {
         ch[c].theta = buf + (size_t)c * 2 * d;
         ch[c].grad = ch[c].theta + d;
+        th[c] = ch[c].theta;
         orc_normals(S->seed, (uint32_t)c, 0, ST_FD_INIT, d, ch[c].theta);
         for (int32_t j = 0; j < d; ++j) ch[c].theta[j] *= S->init_scale;
         if (P->active)
             for (int32_t j = 0; j < P->p; ++j) if (!P->active[j]) ch[c].theta[j] = 0.0;
         chain_refresh(P, -1, &ch[c]);
     }
-    dual_avg D;
-    da_reset(&D, S->eps > 0 ? S->eps : 0.1);
-    if (S->adapt_eps) { S->eps = eps0 > 0 ? eps0 : 0.1; da_reset(&D, S->eps); }
-    int adapt_mass = S->adapt_eps && !S->user_minv;
-    int32_t w0 = n_adapt / 4, w1 = n_adapt / 2, w2 = (7 * n_adapt) / 8;
-    double wn = 0, *wmean = (double *)calloc((size_t)d, sizeof(double));
-    double *wM2 = (double *)calloc((size_t)d, sizeof(double));
+    if (S->adapt_eps) S->eps = eps0 > 0 ? eps0 : 0.1;
+    warm_adapt A;
+    wa_init(&A, n_adapt, d, P->p, P->active, S->adapt_eps, !S->user_minv, S->eps, S->minv);
     uint32_t it = 0;
+    double tail_sum = 0.0;
+    int32_t tail_n = 0;
     for (int32_t i = 0; i < n_adapt; ++i, ++it) {
         double asum = 0.0;
         for (int32_t c = 0; c < NFD; ++c) {
@@ -1191,48 +1293,46 @@ int orc_pcv_fulldata(orc_pcv *S, int32_t n_adapt, int32_t n_keep, double eps0)
             asum += hmc_transition(P, -1, S->seed, (uint32_t)c, it, ST_FD_MOM, ST_FD_ACC, S->eps,
                                    S->Lf, S->minv, &ch[c], work, &acc, &div);
         }
-        if (S->adapt_eps) {
-            da_update(&D, asum / NFD);
-            S->eps = exp(D.logeps);
-        }
-        if (adapt_mass && i >= w0 && i < w2) {
-            for (int32_t c = 0; c < NFD; ++c) {
-                wn += 1.0;
-                for (int32_t j = 0; j < d; ++j) {
-                    double dl = ch[c].theta[j] - wmean[j];
-                    wmean[j] += dl / wn;
-                    wM2[j] += dl * (ch[c].theta[j] - wmean[j]);
-                }
-            }
-        }
-        if (adapt_mass && (i == w1 - 1 || i == w2 - 1) && wn > 1) {
-            double w = wn / (wn + 5.0);
-            for (int32_t j = 0; j < d; ++j) S->minv[j] = w * (wM2[j] / (wn - 1.0)) + 1e-3 * (1.0 - w);
-            if (P->active)
-                for (int32_t j = 0; j < P->p; ++j) if (!P->active[j]) S->minv[j] = 0.0;
+        if (wa_step(&A, i, asum / NFD, NFD, th)) {
             for (int32_t c = 0; c < NFD; ++c) chain_refresh(P, -1, &ch[c]);
-            da_reset(&D, S->eps);
-            wn = 0.0;                              /* the next window starts afresh */
-            for (int32_t j = 0; j < d; ++j) { wmean[j] = 0.0; wM2[j] = 0.0; }
+            tail_sum = 0.0;                       /* dual averaging restarted */
+            tail_n = 0;
+        } else {
+            tail_sum += asum / NFD;
+            tail_n += 1;
         }
+        S->eps = A.eps;
     }
+    S->fd_tail_accept = tail_n > 0 ? tail_sum / tail_n : 0.0;
     if (S->adapt_eps && n_adapt > 0) {
-        S->eps = exp(D.logeps_bar);
         const double T = eff_traj_len(S);
-        if (T > 0 && S->eps > T / S->Lf) S->eps = T / S->Lf;
+        S->eps = wa_final_eps(&A, T > 0 ? T / S->Lf : 0.0);
     }
+    wa_free(&A);
     free(S->pool);
     S->n_pool = NFD * n_keep;
     S->pool = (double *)malloc(sizeof(double) * (size_t)S->n_pool * d);
+    double keep_acc = 0.0;
     for (int32_t i = 0; i < n_keep; ++i, ++it) {
         for (int32_t c = 0; c < NFD; ++c) {
             int acc, div;
-            hmc_transition(P, -1, S->seed, (uint32_t)c, it, ST_FD_MOM, ST_FD_ACC, S->eps, S->Lf,
-                           S->minv, &ch[c], work, &acc, &div);
+            keep_acc += hmc_transition(P, -1, S->seed, (uint32_t)c, it, ST_FD_MOM, ST_FD_ACC, S->eps, S->Lf,
+                                       S->minv, &ch[c], work, &acc, &div);
             memcpy(S->pool + ((size_t)i * NFD + c) * d, ch[c].theta, sizeof(double) * (size_t)d);
         }
     }
-    free(buf); free(work); free(wmean); free(wM2);
+    S->fd_keep_accept = n_keep > 0 ? keep_acc / (NFD * (double)n_keep) : 0.0;
+    free(buf); free(work);
+    return 0;
+}
+
+/* mean acceptance statistics of the full-data chains: over the adaptation
+ * iterations since dual averaging last (re)started, and over the draws kept
+ * in the pool */
+int orc_pcv_fulldata_accept(const orc_pcv *S, double *tail, double *keep)
+{
+    *tail = S->fd_tail_accept;
+    *keep = S->fd_keep_accept;
     return 0;
 }
 
