@@ -388,18 +388,27 @@ pcv_status pcv_last_sample_ms(pcv_ctx *ctx, double *ms);
 pcv_status pcv_time_leapfrog_kernel(pcv_ctx *ctx, int32_t reps, double *ms_per_launch);
 
 /*
- * Allocation-free variant of pcv_log_density (the paper has no counterpart;
- * it exists for callers that may not allocate device memory while they run:
- * a process whose GPU memory belongs to another framework's pool, or a
- * latency-bound loop where cudaMalloc could block or synchronise the device).
- * Same arguments, layout and results as pcv_log_density, but the kernels'
- * split-N partial sums and tickets use fixed device arrays compiled into the
- * library (16 MiB of FP32 scratch and 8192 tickets; every GPU that loads the
- * library holds them until the process exits) instead of the context's
+ * Allocation-free gradient evaluation (the paper has no counterpart).  It is
+ * for callers that may not allocate device memory while they run: a process
+ * whose GPU memory belongs to another framework's pool, or a latency-bound
+ * loop where cudaMalloc could block or synchronise the device.  The kernels'
+ * split-N partial sums and tickets live in fixed device arrays compiled into
+ * the library (16 MiB of FP32 scratch and 8192 tickets; every GPU that loads
+ * the library holds them until the process exits) instead of the context's
  * workspace, so the call itself allocates nothing.
- *   - Limit: ceil(n / 32) <= 8192 and ceil(n / 32) * 32 * (dim rounded up to
- *     a multiple of 4, at least the kernel width, plus 4) <= 4 Mi floats;
- *     larger n returns PCV_E_INVALID_ARG with a message naming the limit.
+ *   - Arguments, layout and results as pcv_log_density, except the
+ *     precision: it must be PCV_FP32_SIMT, and the call runs the FP32
+ *     CUDA-core gradient kernel on a context of any precision (the context
+ *     keeps the FP32 design matrix on every path), so on a BF16 or TF32
+ *     context it returns FP32 results where pcv_log_density would return the
+ *     context's precision.
+ *   - Limits, with T chains per tile (T = 32 for p <= 32, T = 64 above) and
+ *     W = max(dim rounded up to 4, the kernel's register width for p <= 32)
+ *     + 4 partial sums per chain: ceil(n / T) <= 8192 tiles (one ticket each)
+ *     and ceil(n / T) * T * W <= 4 Mi floats for one split of the rows; the
+ *     split count is the one pcv_log_density would use, reduced if needed so
+ *     that all splits fit.  Larger n returns PCV_E_INVALID_ARG with a message
+ *     naming the limit.
  *   - The first call on a device looks up the arrays' device addresses
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.

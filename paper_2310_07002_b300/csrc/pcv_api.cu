@@ -1694,7 +1694,7 @@ pcv_status pcv_last_sample_ms(pcv_ctx *x, double *ms) {
 namespace {
 
 constexpr size_t kNoAllocScratchFloats = (size_t)4 << 20;   // 16 MiB of FP32 partials
-constexpr int kNoAllocTickets = 8192;                        // chain tiles of 32
+constexpr int kNoAllocTickets = 8192;                        // chain tiles (32 or 64 chains)
 
 static __device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchFloats];
 static __device__ __align__(256) unsigned int g_noalloc_tickets[kNoAllocTickets];
@@ -1737,12 +1737,18 @@ extern "C" pcv_status pcv_log_density_noalloc(pcv_ctx *x, const float *theta, co
   const int tw = simt_chain_tile(x->p);
   const int tiles = (n + tw - 1) / tw;
   const int stride = std::max(x->d_pad, simt_flat_pp(x->p)) + 4;
-  if (tiles > kNoAllocTickets || (size_t)tiles * tw * stride > kNoAllocScratchFloats)
+  const std::string what = "pcv_log_density_noalloc: n = " + std::to_string(n) + " positions of dimension " +
+                           std::to_string(x->d) + " need " + std::to_string(tiles) + " chain tiles of " +
+                           std::to_string(tw);
+  if (tiles > kNoAllocTickets)
     return fail(x, PCV_E_INVALID_ARG,
-                "pcv_log_density_noalloc: n = " + std::to_string(n) + " positions of dimension " +
-                    std::to_string(x->d) + " exceed the fixed scratch (" +
-                    std::to_string(kNoAllocScratchFloats) + " floats, " + std::to_string(kNoAllocTickets) +
-                    " tiles of " + std::to_string(tw) + " chains); use pcv_log_density");
+                what + ", more than the fixed ticket array's " + std::to_string(kNoAllocTickets) +
+                    " tiles; use pcv_log_density");
+  if ((size_t)tiles * tw * stride > kNoAllocScratchFloats)
+    return fail(x, PCV_E_INVALID_ARG,
+                what + " x " + std::to_string(stride) + " partial sums = " +
+                    std::to_string((size_t)tiles * tw * stride) + " floats, more than the fixed scratch's " +
+                    std::to_string(kNoAllocScratchFloats) + "; use pcv_log_density");
   float *ws = nullptr;
   unsigned int *tk = nullptr;
   CK(noalloc_addresses(&ws, &tk));
