@@ -388,6 +388,36 @@ pcv_status pcv_last_sample_ms(pcv_ctx *ctx, double *ms);
 pcv_status pcv_time_leapfrog_kernel(pcv_ctx *ctx, int32_t reps, double *ms_per_launch);
 
 /*
+ * The pool of full-data draws that fold chains start from (Algorithm 1,
+ * "draw from {theta^(fd)}"; warm-up reuse, Section 3.1), after pcv_warmup:
+ * *n_pool = 4 x n_fulldata_draws rows; when pool is not NULL it receives
+ * them as [n_pool x dim] doubles (row i x 4 + c = full-data chain c after
+ * kept iteration i), in caller-owned host memory.  Fold chain c starts from
+ * row floor(w0 n_pool / 2^32), w0 the first Philox word of (block 0, chain
+ * first_fold x L + c, iteration 0, stream 2).  PCV_E_BAD_STATE before the
+ * warm-up.
+ */
+pcv_status pcv_get_pool(pcv_ctx *ctx, double *pool, int32_t *n_pool);
+
+/*
+ * Test entry for the full-data adaptation arithmetic (warm-up reuse,
+ * Section 3.1: dual averaging of the step size, Hoffman & Gelman 2014, and
+ * the two diagonal-mass windows [n/4, n/2) and [n/2, 7n/8)): runs the
+ * adaptation kernel n_adapt times on given inputs instead of HMC
+ * transitions.  accept [n_adapt x 4] holds the acceptance statistic of each
+ * of the 4 full-data chains after iteration i, draws [n_adapt x 4 x dim]
+ * (FP32) their positions; the step size starts at eps0 > 0 and the inverse
+ * mass at the context's.  Outputs (caller-owned host memory): eps_out
+ * [n_adapt] and minv_out [n_adapt x dim], the step size and inverse mass
+ * after each iteration, and *eps_final, the dual-averaged step size with no
+ * cap.  Only before pcv_warmup (PCV_E_BAD_STATE otherwise); the context's
+ * inverse mass is restored afterwards and pcv_warmup starts afresh.
+ */
+pcv_status pcv_adapt_trace(pcv_ctx *ctx, int32_t n_adapt, const double *accept, const float *draws,
+                           double eps0, int32_t adapt_mass, double *eps_out, double *minv_out,
+                           double *eps_final);
+
+/*
  * Allocation-free gradient evaluation (the paper has no counterpart).  It is
  * for callers that may not allocate device memory while they run: a process
  * whose GPU memory belongs to another framework's pool, or a latency-bound

@@ -1240,6 +1240,83 @@ pcv_status pcv_get_adaptation(pcv_ctx *x, double *step_size, double *inv_mass) {
   return PCV_OK;
 }
 
+pcv_status pcv_get_pool(pcv_ctx *x, double *pool, int32_t *n_pool) {
+  if (!x || !n_pool) return fail(x, PCV_E_INVALID_ARG, "null argument");
+  if (x->state == ST_CREATED) return fail(x, PCV_E_BAD_STATE, "the pool is filled by pcv_warmup");
+  const int n = x->n_fd_draws * kNumFdChains;
+  *n_pool = n;
+  if (!pool) return PCV_OK;
+  enter(x);
+  std::vector<float> h((size_t)n * x->d_pad);
+  CK(cudaMemcpyAsync(h.data(), x->pool, h.size() * sizeof(float), cudaMemcpyDeviceToHost, x->stream));
+  CK(cudaStreamSynchronize(x->stream));
+  leave(x);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < x->d; ++j) pool[(size_t)i * x->d + j] = h[(size_t)i * x->d_pad + j];
+  return PCV_OK;
+}
+
+pcv_status pcv_adapt_trace(pcv_ctx *x, int32_t n_adapt, const double *accept, const float *draws, double eps0,
+                           int32_t adapt_mass, double *eps_out, double *minv_out, double *eps_final) {
+  if (!x) return PCV_E_INVALID_ARG;
+  if (!accept || !draws || !eps_out || !minv_out || !eps_final || n_adapt < 1 || !(eps0 > 0))
+    return fail(x, PCV_E_INVALID_ARG, "bad argument");
+  if (x->state != ST_CREATED) return fail(x, PCV_E_BAD_STATE, "pcv_adapt_trace runs before pcv_warmup");
+  enter(x);
+  const int nc = kNumFdChains, d = x->d, ld = x->d_pad;
+  ChainBufs &cb = x->fd_cb;
+  // the context's inverse mass is restored afterwards
+  std::vector<float> minv_keep(ld);
+  CK(cudaMemcpyAsync(minv_keep.data(), x->minv, sizeof(float) * ld, cudaMemcpyDeviceToHost, x->stream));
+  k_fd_init_state<<<1, 1, 0, x->stream>>>(x->st, (float)eps0, 1);
+  CK(cudaGetLastError());
+  CK(cudaMemsetAsync(x->wmean, 0, sizeof(double) * d, x->stream));
+  CK(cudaMemsetAsync(x->wM2, 0, sizeof(double) * d, x->stream));
+  FdAdaptArgs fa{};
+  fa.st = x->st;
+  fa.n_adapt = n_adapt;
+  fa.w0 = n_adapt / 4;
+  fa.w1 = n_adapt / 2;
+  fa.w2 = (7 * n_adapt) / 8;
+  fa.adapt_eps = 1;
+  fa.adapt_mass = adapt_mass ? 1 : 0;
+  fa.C = nc; fa.d = d; fa.ld = ld;
+  fa.theta = cb.theta;
+  fa.accept_prob = cb.accept_prob;
+  fa.minv = x->minv;
+  fa.wmean = x->wmean; fa.wM2 = x->wM2;
+  fa.pool = x->pool;
+  fa.active = x->active_d;
+  fa.n_keep = 0;
+  std::vector<float> th((size_t)nc * ld, 0.0f), hm(ld);
+  for (int i = 0; i < n_adapt; ++i) {
+    for (int c = 0; c < nc; ++c)
+      for (int j = 0; j < d; ++j) th[(size_t)c * ld + j] = draws[((size_t)i * nc + c) * d + j];
+    const unsigned it = (unsigned)i + 1;      // the adaptation reads "the iteration just completed"
+    CK(cudaMemcpyAsync(cb.theta, th.data(), th.size() * sizeof(float), cudaMemcpyHostToDevice, x->stream));
+    CK(cudaMemcpyAsync(cb.accept_prob, accept + (size_t)i * nc, sizeof(double) * nc, cudaMemcpyHostToDevice,
+                       x->stream));
+    CK(cudaMemcpyAsync(&x->st->fd_iter, &it, sizeof(it), cudaMemcpyHostToDevice, x->stream));
+    k_fd_adapt<<<1, 128, 0, x->stream>>>(fa);
+    CK(cudaGetLastError());
+    IterState hs;
+    CK(cudaMemcpyAsync(&hs, x->st, sizeof(hs), cudaMemcpyDeviceToHost, x->stream));
+    CK(cudaMemcpyAsync(hm.data(), x->minv, sizeof(float) * ld, cudaMemcpyDeviceToHost, x->stream));
+    CK(cudaStreamSynchronize(x->stream));
+    eps_out[i] = hs.eps;
+    for (int j = 0; j < d; ++j) minv_out[(size_t)i * d + j] = hm[j];
+  }
+  k_fd_final_eps<<<1, 1, 0, x->stream>>>(x->st, 0.0f);
+  CK(cudaGetLastError());
+  IterState hs;
+  CK(cudaMemcpyAsync(&hs, x->st, sizeof(hs), cudaMemcpyDeviceToHost, x->stream));
+  CK(cudaMemcpyAsync(x->minv, minv_keep.data(), sizeof(float) * ld, cudaMemcpyHostToDevice, x->stream));
+  CK(cudaStreamSynchronize(x->stream));
+  *eps_final = hs.eps;
+  leave(x);
+  return PCV_OK;
+}
+
 pcv_status pcv_log_density(pcv_ctx *x, const float *theta, const int32_t *fold, int32_t n, int32_t precision,
                            double *logp, float *grad, double *shat) {
   if (!x) return PCV_E_INVALID_ARG;

@@ -109,6 +109,8 @@ def load():
         "pcv_setup_ms": (i32, [vp, ct.POINTER(f64), ct.POINTER(f64)]),
         "pcv_time_leapfrog_kernel": (i32, [vp, i32, ct.POINTER(f64)]),
         "pcv_log_density_noalloc": (i32, [vp, vp, vp, i32, i32, vp, vp, vp]),
+        "pcv_get_pool": (i32, [vp, vp, ct.POINTER(i32)]),
+        "pcv_adapt_trace": (i32, [vp, i32, vp, vp, f64, i32, vp, vp, ct.POINTER(f64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -127,7 +129,8 @@ def exported_symbols():
             "pcv_get_draws", "pcv_accept_rate", "pcv_last_sample_ms",
             "pcv_time_leapfrog_kernel", "pcv_log_density_noalloc", "pcv_tuning_info",
             "pcv_checkpoint_size", "pcv_checkpoint_save", "pcv_checkpoint_load",
-            "pcv_rhat_shuffle", "pcv_compare", "pcv_scores_extra", "pcv_setup_ms"]
+            "pcv_rhat_shuffle", "pcv_compare", "pcv_scores_extra", "pcv_setup_ms",
+            "pcv_get_pool", "pcv_adapt_trace"]
 
 
 def _ptr(a: Optional[np.ndarray]):
@@ -383,6 +386,29 @@ class PCV:
         self._check(self._L.pcv_get_adaptation(self.h, ct.addressof(e), _ptr(mv)),
                     "pcv_get_adaptation")
         return e.value, mv
+
+    def pool(self):
+        """The full-data draws the fold chains start from, [4 n_keep, dim]."""
+        n = ct.c_int32()
+        self._check(self._L.pcv_get_pool(self.h, None, ct.byref(n)), "pcv_get_pool")
+        out = np.empty((n.value, self.dim))
+        self._check(self._L.pcv_get_pool(self.h, _ptr(out), ct.byref(n)), "pcv_get_pool")
+        return out
+
+    def adapt_trace(self, accept, draws, eps0: float = 0.1, adapt_mass: bool = True):
+        """The full-data adaptation on given inputs (accept [n, 4], draws
+        [n, 4, dim] as float32): step size and inverse mass after each
+        iteration, and the final dual-averaged step size (no cap)."""
+        acc = np.ascontiguousarray(accept, dtype=np.float64)
+        dr = np.ascontiguousarray(draws, dtype=np.float32)
+        n = acc.shape[0]
+        assert acc.shape == (n, 4) and dr.shape == (n, 4, self.dim)
+        eps = np.empty(n)
+        minv = np.empty((n, self.dim))
+        fin = ct.c_double()
+        self._check(self._L.pcv_adapt_trace(self.h, n, _ptr(acc), _ptr(dr), eps0, int(adapt_mass),
+                                            _ptr(eps), _ptr(minv), ct.byref(fin)), "pcv_adapt_trace")
+        return eps, minv, fin.value
 
     def log_density(self, theta, fold, precision: int = FP32_SIMT):
         """(logp [n] f64, grad [n, dim] f32, shat [n] f64) for CUDA tensors
