@@ -200,14 +200,14 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
-def time_steps(P, w, prec, K, Wu, seed, barrier, flush, nvtx=True):
+def time_steps(P, w, prec, K, Wu, seed, barrier, flush, nvtx=True, fused=-1):
     """Create a context for workload w at precision prec, run Wu untimed
     warm-up iterations, then time K sampling iterations (one step each) with
     CUDA events on the library's launch stream, L2 flushed before each step.
     Returns (total_ms, chains, kernel_ms of the fused leapfrog launch)."""
     import torch
     common = dict(seed=seed, batch_size=1, max_batches=K + 64, acov_max_lag=64,
-                  precision=prec, init_scale=0.1)
+                  precision=prec, init_scale=0.1, fused_trajectory=fused)
     pc = P.PCV.from_workload(w, **common)
     pc.warmup(100, Wu)                                   # untimed warm-up iterations
     stream = pc.stream
@@ -240,6 +240,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-form", action="store_true",
                     help="skip timing the plain FP32 form beside a BF16/TF32 run")
+    ap.add_argument("--fused-trajectory", type=int, default=-1, choices=[-1, 0, 1, 2, 4, 8],
+                    help="whole trajectories in one launch: -1 autotuned (default), 0 never, w > 0 always "
+                         "with w warps per chain where the problem allows (fixes the choice for profiler runs)")
     ap.add_argument("--profile-launches", action="store_true",
                     help="for profiler captures: create the context, set positions "
                          "(one gradient launch with log densities), then three "
@@ -293,7 +296,7 @@ def main():
         torch.cuda.synchronize()
 
     clocks = ClockSampler(local)
-    total_ms, C, k_ms = time_steps(P, w, prec, K, Wu, seed, barrier, flush)
+    total_ms, C, k_ms = time_steps(P, w, prec, K, Wu, seed, barrier, flush, fused=args.fused_trajectory)
     clk = clocks.stop()
     if dist is not None:
         t = torch.tensor([total_ms], device="cuda")

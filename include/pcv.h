@@ -154,6 +154,16 @@ typedef struct {
      * id first_fold + k, so every fold draws the same random numbers however
      * the folds are split. Default 0. */
     int32_t first_fold;
+    /* Whole leapfrog trajectories in one launch for small problems (flat
+     * models, p <= 32, FP32 or BF16 form; Section 3.3's lock-step HMC needs
+     * no synchronisation between chains, so a team of 1, 2, 4 or 8 warps
+     * carries one chain through the momentum draw and all L_f gradient
+     * steps, its rows split over the team): -1 (default) lets the autotuner
+     * time it, with each team size, against k_begin + L_f gradient launches
+     * per chain count (without the autotuner: rows x register width <= 32 Ki
+     * takes it, with teams that fill the GPU); 0 never; 1, 2, 4 or 8: always
+     * where the problem allows it, with that many warps per chain. */
+    int32_t fused_trajectory;
 } pcv_options;
 
 /* Fill *opt with the defaults listed above (seed 0, L_f 16, adapted step). */

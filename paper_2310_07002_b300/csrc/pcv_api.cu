@@ -130,6 +130,12 @@ struct pcv_ctx {
   ChainBufs ld_cb;          // positions of pcv_log_density calls (tensor-core path)
   int ld_cap = 0;
   float *rstart = nullptr;
+  // whole trajectories in one launch (k_traj_small) for small problems:
+  // possible at all, the choice per chain count, and the BF16 form's copy
+  // of X
+  bool traj_ok = false;
+  std::map<int, int> tuned_fused;
+  __nv_bfloat16 *X16c = nullptr;
 };
 
 namespace {
@@ -367,6 +373,121 @@ pcv_status launch_grad(pcv_ctx *x, GradArgs a, const ChainBufs *cb = nullptr) {
   return PCV_OK;
 }
 
+// Whole trajectories in one launch: warps per chain (1, 2, 4, 8), or 0 for
+// k_begin + L_f gradient launches.  Where the autotuner has not decided for
+// a chain count, small problems (rows x register width <= 32 Ki) take it.
+int fused_for(const pcv_ctx *x, int C) {
+  if (!x->traj_ok) return 0;
+  if (x->opt.fused_trajectory > 0) return x->opt.fused_trajectory;
+  auto it = x->tuned_fused.find(C);
+  if (it != x->tuned_fused.end()) return it->second;
+  return x->N * (int64_t)traj_small_row_width(x->p) <= 32768 ? traj_default_wpc(C) : 0;
+}
+
+TrajArgs traj_args(pcv_ctx *x, ChainBufs &cb, bool fd, const float *r_given, float jitter, int wpc) {
+  TrajArgs t{};
+  t.wpc = wpc;
+  t.C = cb.C; t.L = cb.L; t.fold_base = cb.fold_base; t.ld = x->d_pad;
+  t.seed = x->opt.seed;
+  t.stream = fd ? ST_FD_MOM : ST_MOM;
+  t.chain_base = fd ? 0 : x->chain_base;
+  t.iter = fd ? &x->st->fd_iter : &x->st->iter;
+  t.eps = &x->st->eps;
+  t.eps_iter = &x->st->eps_iter;
+  t.jitter = jitter;
+  t.minv = x->minv;
+  t.theta = cb.theta; t.grad = cb.grad; t.logp = cb.logp;
+  t.r_given = r_given;
+  t.theta_p = cb.theta_p; t.r = cb.r; t.grad_p = cb.grad_p;
+  t.logp_p = cb.logp_p; t.shat_p = cb.shat_p; t.H0 = cb.H0;
+  t.Lf = x->Lf;
+  t.X16 = x->X16c;
+  t.eval_only = 0;
+  return t;
+}
+
+// The proposal of one HMC transition for every chain of a set (Section
+// 3.3): momentum draw, half kick and drift, then L_f gradient evaluations
+// with their kicks and drifts; as one launch per trajectory where fused
+// (force: -1 the chain set's choice, 0 separate launches, w > 0 fused with w
+// warps per chain), else k_begin and L_f gradient launches.
+pcv_status launch_proposal(pcv_ctx *x, ChainBufs &cb, bool fd, const float *r_given, float jitter,
+                           int force = -1) {
+  const int wpc = force < 0 ? fused_for(x, cb.C) : force;
+  if (wpc > 0) {
+    CK(launch_traj_small(x->pb, traj_args(x, cb, fd, r_given, jitter, wpc), x->stream));
+    return PCV_OK;
+  }
+  BeginArgs ba{};
+  ba.C = cb.C; ba.d = x->d; ba.ld = x->d_pad;
+  ba.seed = x->opt.seed;
+  ba.stream = fd ? ST_FD_MOM : ST_MOM;
+  ba.iter = fd ? &x->st->fd_iter : &x->st->iter;
+  ba.theta = cb.theta; ba.grad = cb.grad; ba.logp = cb.logp;
+  ba.theta_p = cb.theta_p; ba.r = cb.r; ba.H0 = cb.H0;
+  ba.eps = &x->st->eps; ba.minv = x->minv;
+  ba.jitter = jitter;
+  ba.eps_iter = &x->st->eps_iter;
+  ba.chain_base = fd ? 0 : x->chain_base;
+  ba.r_given = r_given;
+  ba.shadow_hi = x->tc ? cb.shadow_hi : nullptr;
+  ba.shadow_lo = x->tc ? cb.shadow_lo : nullptr;
+  ba.ld_shadow = x->KP;
+  ba.shadow_d = x->p;
+  ba.theta_ref = x->theta_ref;
+  k_begin<<<begin_blocks(cb.C, x->d), 256, 0, x->stream>>>(ba);
+  CK(cudaGetLastError());
+  GradArgs ga = grad_args(x, cb, true);
+  for (int s = 1; s <= x->Lf; ++s) {
+    ga.mode = s < x->Lf ? MODE_KICK_DRIFT : MODE_LAST_KICK;
+    ga.need_ll = s == x->Lf;
+    pcv_status st = launch_grad(x, ga, &cb);
+    if (st != PCV_OK) return st;
+  }
+  return PCV_OK;
+}
+
+pcv_status refresh(pcv_ctx *x, ChainBufs &cb);
+
+// the fused-trajectory choice for a chain set: one launch per trajectory
+// with 1, 2, 4 or 8 warps per chain against k_begin + L_f gradient
+// launches, each timed (1 warm-up + 3) on the proposal buffers, which are
+// scratch between iterations
+pcv_status tune_fused(pcv_ctx *x, ChainBufs &cb) {
+  const int C = cb.C;
+  if (!x->traj_ok || !x->opt.autotune || x->opt.fused_trajectory > 0 || C < 1 || x->tuned_fused.count(C))
+    return PCV_OK;
+  const int before = fused_for(x, C);
+  const bool fd = &cb == &x->fd_cb;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int cand[5] = {0, 1, 2, 4, 8};
+  float best_ms = 1e30f;
+  int best = 0;
+  std::string log = "trajectory for " + std::to_string(C) + " chains:";
+  for (int f : cand) {
+    float ms = 0.0f;
+    pcv_status s = launch_proposal(x, cb, fd, nullptr, 0.0f, f);
+    if (s == PCV_OK) s = cudaEventRecord(e0, x->stream) == cudaSuccess ? PCV_OK : PCV_E_CUDA;
+    for (int r = 0; r < 3 && s == PCV_OK; ++r) s = launch_proposal(x, cb, fd, nullptr, 0.0f, f);
+    if (s == PCV_OK && (cudaEventRecord(e1, x->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      s = fail(x, PCV_E_CUDA, "autotuner timing failed");
+    if (s != PCV_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
+    log += (f == 0 ? std::string(" separate launches=") : " fused " + std::to_string(f) + " warps/chain=") +
+           std::to_string(ms / 3.0f) + "ms";
+    if (ms < best_ms) { best_ms = ms; best = f; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  x->tuned_fused[C] = best;
+  x->tune_log.push_back(log + " -> " + (best == 0 ? std::string("separate") : "fused " + std::to_string(best)));
+  // the cached gradients and log densities come from the chosen path
+  if ((best != 0) != (before != 0)) return refresh(x, cb);
+  return PCV_OK;
+}
+
 // Autotuner: time the gradient launch of a chain set (no leapfrog update;
 // the proposal buffers are scratch between iterations) under a few launch
 // configurations and keep the fastest for this chain count.
@@ -374,7 +495,8 @@ pcv_status tune(pcv_ctx *x, ChainBufs &cb) {
   if (!x->opt.autotune || cb.C < 1) return PCV_OK;
   const int C = cb.C;
   const int need_lo = x->centered ? 0 : 1;
-  if (x->tc ? x->tuned_ns.count(std::make_pair(C, need_lo)) > 0 : x->tuned_splits.count(C) > 0) return PCV_OK;
+  if (x->tc ? x->tuned_ns.count(std::make_pair(C, need_lo)) > 0 : x->tuned_splits.count(C) > 0)
+    return tune_fused(x, cb);
   const auto w0 = std::chrono::steady_clock::now();
   struct AddWall {   // adds the wall time of this call on every return path
     double *acc;
@@ -442,7 +564,7 @@ pcv_status tune(pcv_ctx *x, ChainBufs &cb) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  return PCV_OK;
+  return tune_fused(x, cb);
 }
 
 // write the bf16 shadow of a chain set's current positions (tensor-core path)
@@ -482,38 +604,42 @@ pcv_status set_reference(pcv_ctx *x, const float *src, int n, int ld) {
 pcv_status refresh(pcv_ctx *x, ChainBufs &cb) {
   pcv_status s = write_shadow(x, cb, cb.theta, x->d_pad);
   if (s != PCV_OK) return s;
+  if (const int wpc = fused_for(x, cb.C)) {
+    // the same gradient as the fused trajectories (no momentum, no update)
+    TrajArgs t = traj_args(x, cb, false, nullptr, 0.0f, wpc);
+    t.eval_only = 1;
+    t.eps_iter = nullptr;
+    t.grad_p = cb.grad; t.logp_p = cb.logp; t.shat_p = cb.shat;
+    CK(launch_traj_small(x->pb, t, x->stream));
+    return PCV_OK;
+  }
   GradArgs a = grad_args(x, cb, false);
   return launch_grad(x, a, &cb);
 }
 
+pcv_status launch_fd_adapt(pcv_ctx *x, ChainBufs &cb);
+
 // one HMC transition for every chain of a set (Section 3.3)
 pcv_status launch_iteration(pcv_ctx *x, ChainBufs &cb, bool fd, bool accumulate) {
-  BeginArgs ba{};
-  ba.C = cb.C; ba.d = x->d; ba.ld = x->d_pad;
-  ba.seed = x->opt.seed;
-  ba.stream = fd ? ST_FD_MOM : ST_MOM;
-  ba.iter = fd ? &x->st->fd_iter : &x->st->iter;
-  ba.theta = cb.theta; ba.grad = cb.grad; ba.logp = cb.logp;
-  ba.theta_p = cb.theta_p; ba.r = cb.r; ba.H0 = cb.H0;
-  ba.eps = &x->st->eps; ba.minv = x->minv;
-  ba.jitter = fd ? 0.0f : x->jitter;
-  ba.eps_iter = &x->st->eps_iter;
-  ba.chain_base = fd ? 0 : x->chain_base;
-  ba.r_given = nullptr;
-  ba.shadow_hi = x->tc ? cb.shadow_hi : nullptr;
-  ba.shadow_lo = x->tc ? cb.shadow_lo : nullptr;
-  ba.ld_shadow = x->KP;
-  ba.shadow_d = x->p;
-  ba.theta_ref = x->theta_ref;
-  k_begin<<<begin_blocks(cb.C, x->d), 256, 0, x->stream>>>(ba);
-  CK(cudaGetLastError());
-  GradArgs ga = grad_args(x, cb, true);
-  for (int s = 1; s <= x->Lf; ++s) {
-    ga.mode = s < x->Lf ? MODE_KICK_DRIFT : MODE_LAST_KICK;
-    ga.need_ll = s == x->Lf;
-    pcv_status st = launch_grad(x, ga, &cb);
-    if (st != PCV_OK) return st;
+  const int wpc = fused_for(x, cb.C);
+  const bool extra = accumulate && x->extra.flags;
+  if (wpc > 0 && !extra) {
+    // the whole iteration in one launch: trajectory, Metropolis test and
+    // the draw's accumulators (the proposal never leaves the registers)
+    TrajArgs t = traj_args(x, cb, fd, nullptr, fd ? 0.0f : x->jitter, wpc);
+    t.accept = 1;
+    t.acc_stream = fd ? ST_FD_ACC : ST_ACC;
+    t.st = x->st;
+    t.fd = fd ? 1 : 0;
+    t.accumulate = accumulate ? 1 : 0;
+    t.acc = x->acc;
+    t.accept_prob = cb.accept_prob;
+    t.theta_w = cb.theta; t.grad_w = cb.grad; t.logp_w = cb.logp; t.shat_w = cb.shat;
+    CK(launch_traj_small(x->pb, t, x->stream));
+    return fd ? launch_fd_adapt(x, cb) : PCV_OK;
   }
+  pcv_status sp = launch_proposal(x, cb, fd, nullptr, fd ? 0.0f : x->jitter);
+  if (sp != PCV_OK) return sp;
   AcceptArgs aa{};
   aa.C = cb.C; aa.d = x->d; aa.ld = x->d_pad;
   aa.seed = x->opt.seed;
@@ -535,7 +661,12 @@ pcv_status launch_iteration(pcv_ctx *x, ChainBufs &cb, bool fd, bool accumulate)
         x->pb, grad_args(x, cb, false), x->extra, &x->st->iter, x->opt.seed, x->chain_base);
     CK(cudaGetLastError());
   }
-  if (fd) {
+  return fd ? launch_fd_adapt(x, cb) : PCV_OK;
+}
+
+// the full-data adaptation after an iteration of the full-data chains
+pcv_status launch_fd_adapt(pcv_ctx *x, ChainBufs &cb) {
+  {
     FdAdaptArgs fa{};
     fa.st = x->st;
     fa.n_adapt = x->fd_n_adapt;
@@ -701,6 +832,7 @@ void pcv_default_options(pcv_options *o) {
   o->autotune = 1;
   o->extra_scores = 0;
   o->first_fold = 0;
+  o->fused_trajectory = -1;
 }
 
 pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
@@ -717,7 +849,9 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
     return invalid("need 1 <= N <= 2^30, p >= 1 and chains_per_fold >= 2");
   if (opt->leapfrog_steps < 1 || opt->batch_size < 1 || opt->hv_buffer < 0 ||
       opt->acov_max_lag < 0 || opt->max_batches < 1 || opt->n_fulldata_draws < 1 ||
-      !(opt->step_jitter < 1.0) || !std::isfinite(opt->trajectory_length) || opt->first_fold < 0)
+      !(opt->step_jitter < 1.0) || !std::isfinite(opt->trajectory_length) || opt->first_fold < 0 ||
+      (opt->fused_trajectory != -1 && opt->fused_trajectory != 0 && opt->fused_trajectory != 1 &&
+       opt->fused_trajectory != 2 && opt->fused_trajectory != 4 && opt->fused_trajectory != 8))
     return invalid("an option is out of range");
   if (model->kind < PCV_GAUSS_LINEAR || model->kind > PCV_AR_GAUSS) return invalid("unknown model kind");
   if (!(model->beta_prior_sd > 0)) return invalid("beta_prior_sd must be > 0");
@@ -990,6 +1124,18 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
   pb.tau_prec = (float)(1.0 / (tsd * tsd));
   pb.log_tau_sd = (float)std::log(tsd);
 
+  // whole trajectories in one launch for the flat models with p <= 32 (FP32
+  // and the BF16 form, which reads a bf16 copy of X)
+  x->traj_ok = opt->fused_trajectory != 0 && !x->tf32 && traj_small_supported(pb);
+  if (x->traj_ok && x->tc) {
+    const int PP = traj_small_row_width(p);
+    const size_t n16 = ((size_t)N * PP + 7) / 8 * 8;     // whole 16-byte units (the kernel copies by 16 bytes)
+    if (!dalloc_n(x, &x->X16c, n16)) return bail(PCV_E_OOM, "device allocation failed");
+    cudaMemsetAsync(x->X16c, 0, n16 * sizeof(__nv_bfloat16), x->stream);
+    const long long items = (long long)N * PP;
+    k_x_bf16_compact<<<(unsigned)((items + 255) / 256), 256, 0, x->stream>>>(N, PP, x->p_pad, x->X, x->X16c);
+    if (cudaGetLastError() != cudaSuccess) return bail(PCV_E_CUDA, "bf16 copy of X failed");
+  }
   pcv_status s;
   if ((s = alloc_chains(x, x->fold_cb, x->C, x->L, 0)) != PCV_OK) return bail(s, x->err);
   if ((s = alloc_chains(x, x->fd_cb, kNumFdChains, kNumFdChains, K)) != PCV_OK) return bail(s, x->err);
@@ -1370,27 +1516,8 @@ pcv_status pcv_trajectory(pcv_ctx *x, const float *theta0, const float *r0, int3
   CK(cudaMemcpy2DAsync(rstart, pitch, r0, row, row, x->C, cudaMemcpyDeviceToDevice, x->stream));
   pcv_status s = refresh(x, cb);
   if (s != PCV_OK) return s;
-  BeginArgs ba{};
-  ba.C = cb.C; ba.d = x->d; ba.ld = x->d_pad;
-  ba.seed = x->opt.seed; ba.stream = ST_MOM; ba.iter = &x->st->iter;
-  ba.theta = cb.theta; ba.grad = cb.grad; ba.logp = cb.logp;
-  ba.theta_p = cb.theta_p; ba.r = cb.r; ba.H0 = cb.H0;
-  ba.eps = &x->st->eps; ba.minv = x->minv; ba.r_given = rstart;
-  ba.jitter = 0.0f; ba.eps_iter = &x->st->eps_iter; ba.chain_base = x->chain_base;
-  ba.shadow_hi = x->tc ? cb.shadow_hi : nullptr;
-  ba.shadow_lo = x->tc ? cb.shadow_lo : nullptr;
-  ba.ld_shadow = x->KP;
-  ba.shadow_d = x->p;
-  ba.theta_ref = x->theta_ref;
-  k_begin<<<begin_blocks(cb.C, x->d), 256, 0, x->stream>>>(ba);
-  CK(cudaGetLastError());
-  GradArgs ga = grad_args(x, cb, true);
-  for (int st = 1; st <= x->Lf; ++st) {
-    ga.mode = st < x->Lf ? MODE_KICK_DRIFT : MODE_LAST_KICK;
-    ga.need_ll = st == x->Lf;
-    s = launch_grad(x, ga, &cb);
-    if (s != PCV_OK) return s;
-  }
+  s = launch_proposal(x, cb, false, rstart, 0.0f);
+  if (s != PCV_OK) return s;
   CK(cudaMemcpy2DAsync(theta1, row, cb.theta_p, pitch, row, x->C, cudaMemcpyDeviceToDevice, x->stream));
   CK(cudaMemcpy2DAsync(r1, row, cb.r, pitch, row, x->C, cudaMemcpyDeviceToDevice, x->stream));
   CK(cudaMemcpyAsync(logp1, cb.logp_p, sizeof(double) * x->C, cudaMemcpyDeviceToDevice, x->stream));
@@ -1503,7 +1630,7 @@ struct CkptHeader {
   uint64_t seed;
   int64_t n_sampled;
   int32_t state, centered;
-  int32_t tuned_splits, tuned_ns0, tuned_ns1, tuned_ncta;
+  int32_t tuned_splits, tuned_ns0, tuned_ns1, tuned_ncta, tuned_fused;
   int32_t first_fold;
   float jitter;
   double traj_len;
@@ -1551,7 +1678,7 @@ std::vector<Seg> ckpt_segments(pcv_ctx *x) {
 CkptHeader ckpt_header(pcv_ctx *x) {
   CkptHeader h{};
   std::memcpy(h.magic, kCkptMagic, 8);
-  h.version = 1;
+  h.version = 2;
   h.precision = x->opt.precision; h.variant = x->variant; h.p = x->p; h.d = x->d; h.d_pad = x->d_pad;
   h.K = x->K; h.L = x->L; h.C = x->C; h.M = x->M; h.max_batches = x->max_batches; h.b = x->b;
   h.draw_cap = x->acc.draw_cap; h.Lf = x->Lf; h.N_pad = x->N_pad; h.N = x->N; h.seed = x->opt.seed;
@@ -1586,6 +1713,8 @@ pcv_status pcv_checkpoint_save(pcv_ctx *x, void *buf, int64_t bytes) {
   h.tuned_ns1 = n1 != x->tuned_ns.end() ? n1->second : -1;
   auto nc = x->tuned_ncta.find(x->C);
   h.tuned_ncta = nc != x->tuned_ncta.end() ? nc->second : -1;
+  auto tf = x->tuned_fused.find(x->C);
+  h.tuned_fused = tf != x->tuned_fused.end() ? tf->second : -1;
   enter(x);
   uint8_t *out = static_cast<uint8_t *>(buf);
   std::memcpy(out, &h, sizeof(h));
@@ -1605,7 +1734,7 @@ pcv_status pcv_checkpoint_load(pcv_ctx *x, const void *buf, int64_t bytes) {
   CkptHeader h;
   std::memcpy(&h, buf, sizeof(h));
   const CkptHeader mine = ckpt_header(x);
-  if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1)
+  if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 2)
     return fail(x, PCV_E_INVALID_ARG, "not a PCV checkpoint");
   if (h.precision != mine.precision || h.variant != mine.variant || h.p != mine.p || h.d != mine.d ||
       h.K != mine.K || h.L != mine.L || h.C != mine.C || h.M != mine.M || h.max_batches != mine.max_batches ||
@@ -1630,6 +1759,7 @@ pcv_status pcv_checkpoint_load(pcv_ctx *x, const void *buf, int64_t bytes) {
   if (h.tuned_ns0 > 0) x->tuned_ns[std::make_pair(x->C, 0)] = h.tuned_ns0;
   if (h.tuned_ns1 > 0) x->tuned_ns[std::make_pair(x->C, 1)] = h.tuned_ns1;
   if (h.tuned_ncta > 0) x->tuned_ncta[x->C] = h.tuned_ncta;
+  if (h.tuned_fused >= 0) x->tuned_fused[x->C] = h.tuned_fused;
   // the bf16 shadows and the eta_ref columns of X follow from the restored
   // positions and reference
   pcv_status s = write_shadow(x, x->fold_cb, x->fold_cb.theta, x->d_pad);

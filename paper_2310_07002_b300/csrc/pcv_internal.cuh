@@ -145,13 +145,21 @@ __device__ __forceinline__ double unit_from_word(uint32_t a) {
 }
 
 // Box-Muller on two words: (sqrt(-2 ln u1) cos 2 pi u2, sqrt(-2 ln u1) sin 2 pi u2),
-// u = (w + 1/2) 2^-32 in (0, 1).
+// u = (w + 1/2) 2^-32 in (0, 1).  FP32 throughout (FP64 is slow on this
+// part), with the complements taken from the integer words so that they
+// keep their relative precision: ln u1 = log1p(-(1 - u1)) when u1 >= 1/2,
+// else log(u1); the angle 2 pi u2 as 2 pi (u2 - 1) when u2 >= 1/2 (the same
+// point of the circle).  The result is within ~1e-7 relative of the FP64
+// transform.
 __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b) {
-  const double u1 = unit_from_word(a);
-  const float u2 = (float)unit_from_word(b);
-  const float rad = (float)sqrt(-2.0 * log(u1));
+  const float k = 2.3283064365386963e-10f;            // 2^-32
+  const float l = a >= 0x80000000u ? log1pf(-(((float)(0xFFFFFFFFu - a) + 0.5f) * k))
+                                   : logf(((float)a + 0.5f) * k);
+  const float t = b >= 0x80000000u ? -2.0f * (((float)(0xFFFFFFFFu - b) + 0.5f) * k)
+                                   : 2.0f * (((float)b + 0.5f) * k);
+  const float rad = sqrtf(-2.0f * l);
   float s, c;
-  sincospif(2.0f * u2, &s, &c);
+  sincospif(t, &s, &c);
   return make_float2(rad * c, rad * s);
 }
 
@@ -239,6 +247,51 @@ struct BeginArgs {
   int shadow_d;                 // leading coordinates with a shadow (beta: p)
   const float *theta_ref;       // shadows hold (theta_p - theta_ref) / 2
 };
+
+// A whole leapfrog trajectory per chain in one launch (k_traj_small.cu):
+// the momentum draw and first half step of k_begin, then L_f gradient
+// evaluations with their kicks and drifts, writing the same proposal state
+// as k_begin + L_f gradient launches.
+struct TrajArgs {
+  int C, L, fold_base, ld;
+  unsigned long long seed;
+  unsigned int stream;
+  int chain_base;
+  const unsigned int *iter;     // device iteration counter
+  const float *eps;             // nominal step size
+  float *eps_iter;              // out (chain 0): this iteration's step size
+  float jitter;
+  const float *minv;
+  const float *theta, *grad;    // current state
+  const double *logp;
+  const float *r_given;         // optional start momenta (C x ld)
+  float *theta_p, *r, *grad_p;  // proposal (out)
+  double *logp_p, *shat_p, *H0; // out
+  int Lf;
+  const __nv_bfloat16 *X16;     // BF16 form: N x PP copy of X, zero-padded to a multiple of
+                                // 16 bytes (else nullptr: FP32 X)
+  int eval_only;                // 1: gradient and log densities at theta only, into
+                                // grad_p, logp_p, shat_p (no momentum, no update)
+  int smem_rows;                // set by the launcher: X (or X16) and y staged in shared memory
+  int part_offset;              // set by the launcher: byte offset of the team partial sums
+  int wpc;                      // warps per chain (1, 2, 4, 8): a chain's rows are split over them
+  // accept mode: the Metropolis test and the draw's accumulators follow in
+  // the same launch (as k_accept), the proposal stays in registers
+  int accept;
+  unsigned int acc_stream;      // Philox stream of the accept uniforms
+  IterState *st;
+  int fd;                       // full-data chains (fd_iter counter, no accumulators)
+  int accumulate;
+  Accum acc;
+  double *accept_prob;          // per chain, or null
+  float *theta_w, *grad_w;      // the chains' state, updated on acceptance
+  double *logp_w, *shat_w;
+};
+int traj_default_wpc(int C);
+bool traj_small_supported(const Problem &pb);
+int traj_small_row_width(int p);
+cudaError_t launch_traj_small(const Problem &pb, const TrajArgs &t, cudaStream_t st);
+__global__ void k_x_bf16_compact(long long N, int PP, int p_pad, const float *X, __nv_bfloat16 *X16);
 
 struct AcceptArgs {
   int C, d, ld;

@@ -108,7 +108,7 @@ def test_bf16_trajectory(torch, orc, p):
     w = bf16_workload(p)
     eps = 0.01 if p <= 32 else 0.004
     minv = np.ones(w.dim)
-    pc = PCV.from_workload(w, precision=BF16, step_size=eps, inv_mass_diag=minv)
+    pc = PCV.from_workload(w, precision=BF16, step_size=eps, inv_mass_diag=minv, fused_trajectory=0)
     prob = orc.problem_from_workload(w)
     g = np.random.Generator(np.random.Philox(6))
     th0 = (0.2 if p <= 32 else 0.05) * g.standard_normal((w.n_chains, w.dim))
@@ -206,7 +206,7 @@ def test_bf16_gaussian_trajectory(torch, orc, name):
     w = gauss_bf16_workloads()[name]
     eps = {"gauss": 0.01, "gauss_logsig_p40": 0.002, "ar2": 0.005}[name]
     minv = np.ones(w.dim)
-    pc = PCV.from_workload(w, precision=BF16, step_size=eps, inv_mass_diag=minv)
+    pc = PCV.from_workload(w, precision=BF16, step_size=eps, inv_mass_diag=minv, fused_trajectory=0)
     prob = orc.problem_from_workload(w)
     g = np.random.Generator(np.random.Philox(7))
     th0 = 0.2 * g.standard_normal((w.n_chains, w.dim))

@@ -294,8 +294,9 @@ def test_error_codes(torch):
     assert e.value.status == E_INVALID_ARG
 
 
+@pytest.mark.parametrize("fused", [0, 1])
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
-def test_graph_replay_equals_plain_launches(torch, precision):
+def test_graph_replay_equals_plain_launches(torch, precision, fused):
     # The iteration replayed from a captured CUDA graph (counters in device
     # memory) must produce bit-identical states and estimators to the same
     # launches issued one by one.
@@ -306,7 +307,7 @@ def test_graph_replay_equals_plain_launches(torch, precision):
         # a fixed launch configuration: the autotuner's choice of split count
         # could differ between the two contexts and change rounding
         pc = make_pcv(w, precision=PRECISIONS[precision], use_graphs=graphs, batch_size=10,
-                      autotune=False)
+                      autotune=False, fused_trajectory=fused)
         pc.warmup(40, 20)
         pc.sample(60)
         th, lp, sh = pc.positions()

@@ -63,7 +63,8 @@ def test_masked_coefficients_stay_zero_on_the_tensor_cores(torch):
     w = W.logistic_loo(N=517, p=20, K=30, L=4)
     active = np.ones(w.p, np.int32)
     active[[2, 5, 11]] = 0
-    pc = PCV.from_workload(dataclasses.replace(w, active=active), precision=BF16, batch_size=10)
+    pc = PCV.from_workload(dataclasses.replace(w, active=active), precision=BF16, batch_size=10,
+                          fused_trajectory=0)
     pc.warmup(60, 30)
     pc.sample(100)
     th, _, _ = pc.positions()

@@ -70,7 +70,7 @@ def test_every_mma_group_length(torch, orc, p):
     # hi only: a trajectory of centred chains
     eps = 0.01 if p <= 32 else 0.004
     minv = np.ones(w.dim)
-    pc = PCV.from_workload(w, precision=BF16, step_size=eps, inv_mass_diag=minv)
+    pc = PCV.from_workload(w, precision=BF16, step_size=eps, inv_mass_diag=minv, fused_trajectory=0)
     gen = np.random.Generator(np.random.Philox(p))
     th0 = w.truth["beta"][None, :] + (0.1 if p <= 32 else 0.03) * gen.standard_normal((w.n_chains, w.dim))
     pc.set_positions(th0, step_size=eps)                   # centring reference = mean position
