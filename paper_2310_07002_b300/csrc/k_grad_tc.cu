@@ -312,6 +312,14 @@ __device__ __forceinline__ uint32_t bf16x2_from(float lo, float hi) {
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
   return r;
 }
+// hi + lo += v with the rounding error of the sum kept in lo (Knuth's
+// TwoSum: exact for any magnitudes)
+__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float v) {
+  const float s = hi + v;
+  const float bp = s - hi;
+  lo += (hi - (s - bp)) + (v - bp);
+  hi = s;
+}
 __device__ __forceinline__ float tanh_f32(float x) {
   float r;
   asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -535,7 +543,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (valid) fd = pb.folds[fold_of_chain(a, c)];
       // per-chain sums over the fold's training and test rows: softplus(eta)
       // (logistic) or squared residuals (Gaussian models)
-      double sp_tr = 0.0, sp_te = 0.0;
+      // (each as an FP32 pair hi + lo kept exact by TwoSum: FP64 arithmetic
+      // is slow on this part, and a per-quarter FP64 add paced the
+      // log-density launch)
+      float tr_hi = 0.0f, tr_lo = 0.0f, te_hi = 0.0f, te_lo = 0.0f;
       // Gaussian models: 1 / sigma^2 of the chain (sigma known, or exp of the
       // log sigma coordinate after beta; theta only moves in the finish)
       float inv_s2 = 1.0f;
@@ -597,8 +608,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 float lg[4];
 #pragma unroll
                 for (int g = 0; g < 4; ++g) lg[g] = log2_approx(pr[g]);
-                sp_tr += (double)fmaf((lg[0] + lg[1]) + (lg[2] + lg[3]), 0.6931471805599453f,
-                                      2.0f * ((mx[0] + mx[1]) + (mx[2] + mx[3])));
+                two_sum_add(tr_hi, tr_lo, fmaf((lg[0] + lg[1]) + (lg[2] + lg[3]), 0.6931471805599453f,
+                                               2.0f * ((mx[0] + mx[1]) + (mx[2] + mx[3]))));
               } else {
                 // rare (the quarter meets the fold's excluded rows or the
                 // padding): a rolled loop over a local copy keeps this
@@ -615,8 +626,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                   if (n < pb.N && (n < fd.excl_lo || n >= fd.excl_hi)) tr += sp;
                   if (n >= fd.test_lo && n < fd.test_hi) te += sp;
                 }
-                sp_tr += (double)tr;
-                sp_te += (double)te;
+                two_sum_add(tr_hi, tr_lo, tr);
+                two_sum_add(te_hi, te_lo, te);
               }
             }
 
@@ -643,7 +654,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 float acc4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
                 for (int k = 0; k < 32; ++k) acc4[k & 3] = fmaf(e[k], e[k], acc4[k & 3]);
-                sp_tr += (double)((acc4[0] + acc4[1]) + (acc4[2] + acc4[3]));
+                two_sum_add(tr_hi, tr_lo, (acc4[0] + acc4[1]) + (acc4[2] + acc4[3]));
               } else {
                 float sq[32];                      // rolled, as for the softplus sums
 #pragma unroll
@@ -656,8 +667,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                   if (n < pb.N && (n < fd.excl_lo || n >= fd.excl_hi)) tr += e2;
                   if (n >= fd.test_lo && n < fd.test_hi) te += e2;
                 }
-                sp_tr += (double)tr;
-                sp_te += (double)te;
+                two_sum_add(tr_hi, tr_lo, tr);
+                two_sum_add(te_hi, te_lo, te);
               }
             }
           }
@@ -671,6 +682,44 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // to the second GEMM at once.  Loaded registers are used only after
         // the load wait, and store sources stay allocated until their store
         // wait (tmem_fence_regs pins both).
+        if constexpr (ACC) {
+          // log-density launch (one of L_f per iteration): a rolled loop
+          // over the quarters, each loaded from TMEM on its own, keeps this
+          // instantiation's code small (the unrolled form below, with the
+          // softplus sums, overflowed the instruction cache); S is released
+          // after the last quarter's load
+          const uint32_t rbuf = tmem_R + 64 * rb + lane_off;
+#pragma unroll 1
+          for (int qq = 0; qq < 4; ++qq) {
+            uint32_t v[32], pk[16];
+            PCV_TMEM_LD32(tmem + sb * 128 + lane_off + 32 * qq, v);
+            tmem_wait_ld();
+            tmem_fence_regs(v);
+            if (qq == 3) {
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(smem_u32(&s_empty[sb]));
+            }
+            quarter(qq, v, pk);
+            if (qq == 0) {
+              if (!warp_wait(smem_u32(&r_empty[rb]), ((i >> 1) & 1) ^ 1, abort_flag, ta.err)) {
+                aborted = true;
+                break;
+              }
+              tc_fence_after();
+            }
+            PCV_TMEM_ST16(rbuf + 16 * qq, pk);
+            tmem_wait_st();
+            tmem_fence_regs(pk);
+            if (qq & 1) {                                   // a 64-row half of R is in TMEM
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(smem_u32(&r_part[4 * rb + (qq >> 1)]));
+            }
+          }
+          if (aborted) break;
+          continue;
+        }
         uint32_t sv[128], p0[16], p1[16], p2[16], p3[16];
         PCV_TMEM_LD128(tmem + sb * 128 + lane_off, sv);   // one load: ~2 % faster than four x32
         tmem_wait_ld();
@@ -740,9 +789,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (lane == 0) mbar_arrive(smem_u32(g_empty));
       }
       {
-        const float h0 = (float)sp_tr, h1 = (float)sp_te;
-        __stcg(reinterpret_cast<float4 *>(wrow + ta.PN + 4 * eg),
-               make_float4(h0, (float)(sp_tr - (double)h0), h1, (float)(sp_te - (double)h1)));
+        __stcg(reinterpret_cast<float4 *>(wrow + ta.PN + 4 * eg), make_float4(tr_hi, tr_lo, te_hi, te_lo));
       }
       __threadfence();
       __syncwarp();
