@@ -980,7 +980,9 @@ static int64_t fold_test_rows(const orc_problem *P, int32_t k, int64_t *rows)
 int orc_pcv_enable_extra(orc_pcv *S, int32_t flags)
 {
     const orc_problem *P = &S->P;
-    if (P->kind != ORC_GAUSS && P->kind != ORC_AR) return -1;
+    /* HS needs a density in y (Gaussian rows); the DSS needs only predictive
+     * draws, which the logistic model has too (Bernoulli) */
+    if (P->kind != ORC_GAUSS && P->kind != ORC_AR && !(P->kind == ORC_LOGISTIC && flags == 2)) return -1;
     int64_t *rows = (int64_t *)malloc(sizeof(int64_t) * (size_t)P->N);
     int32_t T = 0;
     for (int32_t k = 0; k < P->K; ++k) {
@@ -1003,6 +1005,25 @@ static void extra_push(orc_pcv *S, int32_t c, int32_t k, uint32_t it, const doub
 {
     const orc_problem *P = &S->P;
     const int64_t m = fold_test_rows(P, k, rows);
+    if (P->kind == ORC_LOGISTIC) {
+        /* a predictive draw ytil_i ~ Bernoulli(sigmoid(x_i' theta)): ytil_i = 1
+         * iff u_i < sigmoid(eta_i), u_i from word i % 4 of Philox block i / 4
+         * of stream 5 */
+        for (int64_t i = 0; i < m; ++i) {
+            const int64_t n = rows[i];
+            double eta = 0.0;
+            for (int32_t j = 0; j < P->p; ++j) eta += P->X[n * P->p + j] * theta[j];
+            uint32_t w[4];
+            philox_at(S->seed, (uint32_t)(i / 4), (uint32_t)c, it, 5u, w);
+            ytil[i] = u32_to_unit(w[i % 4]) < sigmoid(eta) ? 1.0 : 0.0;
+        }
+        for (int64_t i = 0; i < m; ++i) {
+            S->dsum[(size_t)c * S->T + i] += ytil[i];
+            for (int64_t j2 = 0; j2 < m; ++j2)
+                S->douter[((size_t)c * S->T + i) * S->T + j2] += ytil[i] * ytil[j2];
+        }
+        return;
+    }
     const double sigma = (P->kind == ORC_GAUSS && P->sigma_known > 0) ? P->sigma_known : exp(theta[P->p]);
     const double s2 = sigma * sigma;
     orc_normals(S->seed, (uint32_t)c, it, 5u, (int32_t)m, ytil);     /* stream 5: predictive draws */
@@ -1079,7 +1100,7 @@ int orc_pcv_extra_results(orc_pcv *S, double *hs, double *dss)
             for (int32_t l = 0; l < L; ++l) e2 += S->hs2[(size_t)(k * L + l) * T + i];
             h += (e2 / n) * (e2 / n);
         }
-        hs[k] = h;
+        hs[k] = (S->extra & 1) ? h : NAN;               /* HS only where it was accumulated */
         for (int64_t i = 0; i < m; ++i) {
             double sm = 0.0;
             for (int32_t l = 0; l < L; ++l) sm += S->dsum[(size_t)(k * L + l) * T + i];

@@ -694,9 +694,23 @@ __global__ void __launch_bounds__(256) k_extra_push(Problem pb, GradArgs a, Extr
   const FoldDesc fd = pb.folds[fold_of_chain(a, c)];
   const int m = fd.test_hi - fd.test_lo;
   const float *th = a.theta + (size_t)c * a.ld_theta;
+  double *yt = ysh + (size_t)wib * E.T;
+  if (pb.variant == MV_LOGISTIC) {
+    // a predictive draw ytil_i ~ Bernoulli(sigmoid(eta_i)) (DSS only): 1
+    // iff u_i < sigmoid(eta_i), u_i from word i % 4 of Philox block i / 4;
+    // the comparison in FP64
+    for (int i = lane; i < m; i += 32) {
+      const int n = fd.test_lo + i;
+      double eta = 0.0;
+      for (int j = 0; j < pb.p; ++j) eta += (double)pb.X[(size_t)n * pb.p_pad + j] * (double)th[j];
+      const uint4 w = philox_at(seed, (uint32_t)(i >> 2), (uint32_t)(chain_base + c), it, ST_PRED);
+      const uint32_t word = (i & 3) == 0 ? w.x : (i & 3) == 1 ? w.y : (i & 3) == 2 ? w.z : w.w;
+      const double pr = eta >= 0.0 ? 1.0 / (1.0 + exp(-eta)) : exp(eta) / (1.0 + exp(eta));
+      yt[i] = unit_from_word(word) < pr ? 1.0 : 0.0;
+    }
+  } else {
   const double sigma = pb.variant == MV_GAUSS_KNOWN ? (double)pb.sigma_known : exp((double)th[pb.p]);
   const double s2 = sigma * sigma;
-  double *yt = ysh + (size_t)wib * E.T;
   double xi1 = 0.0;
   for (int i = lane; i < m; i += 32) {
     const int n = fd.test_lo + i;
@@ -714,6 +728,7 @@ __global__ void __launch_bounds__(256) k_extra_push(Problem pb, GradArgs a, Extr
   }
   xi1 = warp_sum_d(xi1);
   if ((E.flags & 1) && lane == 0) E.hs1[c] += xi1;
+  }
   __syncwarp();
   if (E.flags & 2) {
     for (int i = lane; i < m; i += 32) E.dsum[(size_t)c * E.T + i] += yt[i];

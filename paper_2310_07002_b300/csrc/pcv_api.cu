@@ -1144,8 +1144,9 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
     // Hyvarinen / Dawid-Sebastiani accumulators (Gaussian models whose rows
     // are conditionally independent given theta)
     if (opt->extra_scores & ~3) return bail(PCV_E_INVALID_ARG, "extra_scores: bits 0 (HS) and 1 (DSS) only");
-    if (x->variant != MV_GAUSS_KNOWN && x->variant != MV_GAUSS_LOGSIG)
-      return bail(PCV_E_UNSUPPORTED, "HS / DSS need a Gaussian linear or AR model");
+    if (x->variant != MV_GAUSS_KNOWN && x->variant != MV_GAUSS_LOGSIG &&
+        !(x->variant == MV_LOGISTIC && opt->extra_scores == 2))
+      return bail(PCV_E_UNSUPPORTED, "HS needs a Gaussian linear or AR model; DSS a Gaussian or logistic one");
     int T = 0;
     for (int k = 0; k < K; ++k) T = std::max(T, fds[k].test_hi - fds[k].test_lo);
     if ((opt->extra_scores & 2) && T > 64) return bail(PCV_E_UNSUPPORTED, "DSS needs test sets of at most 64 rows");

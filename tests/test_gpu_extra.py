@@ -68,3 +68,28 @@ def test_extra_scores_need_a_gaussian_row_model(torch):
         with pytest.raises(PCVError) as e:
             PCV.from_workload(w, extra_scores=1)
         assert e.value.status == E_UNSUPPORTED
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_logistic_dss_equals_oracle_at_a_fixed_position(torch, orc, precision):
+    # Algorithm A4 for the logistic model: predictive draws are Bernoulli
+    # with the Philox stream-5 uniforms; with the chains held at one position
+    # (a step far below FP32 resolution) the GPU draws the oracle's draws, so
+    # the DSS must agree to rounding, and no HS exists for a discrete y
+    from paper_2310_07002_b300.pcv import PCV, PRECISIONS
+    from tests.test_oracle_extra import blocks_of
+    w = blocks_of(W.logistic_loo(N=200, p=3, L=4), K=5, T=3)
+    th0 = np.tile(w.truth["beta"], (w.n_chains, 1)).astype(np.float32).astype(np.float64)
+    pc = PCV.from_workload(w, step_size=1e-12, extra_scores=2, precision=PRECISIONS[precision])
+    pc.set_positions(th0, step_size=1e-12)
+    pc.sample(200)
+    ex = pc.scores_extra()
+    assert np.array_equal(pc.positions()[0], th0)
+    run = orc.OraclePCV(orc.problem_from_workload(w), w.chains_per_fold, w.seed, w.leapfrog_steps, eps=1e-12, b=50)
+    run.enable_extra_scores(2)
+    run.set_state(th0, eps=1e-12)
+    run.sample(200)
+    hs, dss = run.extra_scores()
+    assert np.all(np.isnan(ex["hs"])) and np.all(np.isnan(hs))
+    np.testing.assert_allclose(ex["dss"], dss, rtol=1e-9)
+    pc.close()

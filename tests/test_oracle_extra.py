@@ -49,3 +49,84 @@ def test_hs_and_dss_match_the_closed_forms(orc):
         T = int((w.fold == k).sum())
         sd = np.sqrt(2.0 * q * q / n + 2.0 * T / n)
         assert abs(dss[k] - d_ref) < 4.0 * sd + T * (T + 1) / n, (k, dss[k], d_ref, sd)
+
+
+def blocks_of(w, K, T):
+    """The workload's first K * T rows as K folds of T consecutive rows."""
+    import dataclasses
+    fold = np.full(w.N, -1, np.int32)
+    fold[:K * T] = np.arange(K * T) // T
+    return dataclasses.replace(w, fold=fold, K=K)
+
+
+def test_logistic_dss_at_a_fixed_position(orc):
+    # Chains held at one position (a step size far below the positions'
+    # resolution): every draw's predictive is Bernoulli(p_i), p_i =
+    # sigmoid(x_i' theta), independent across the test rows, so the DSS
+    # (Algorithm A4, with the sample mean and covariance of the draws) tends
+    # to -sum log p_i (1 - p_i) - sum (y_i - p_i)^2 / (p_i (1 - p_i)).  The
+    # estimator's own spread at this draw count is measured by simulating it
+    # with numpy's generator (brute force).
+    w = blocks_of(W.logistic_loo(N=200, p=3, L=4), K=5, T=3)
+    prob = orc.problem_from_workload(w)
+    th0 = np.tile(w.truth["beta"], (w.n_chains, 1))
+    run = orc.OraclePCV(prob, w.chains_per_fold, w.seed, w.leapfrog_steps, eps=1e-12, b=50)
+    run.enable_extra_scores(2)
+    run.set_state(th0, eps=1e-12)
+    n_draws = 2000
+    run.sample(n_draws)
+    hs, dss = run.extra_scores()
+    assert np.all(np.isnan(hs))                          # no HS for a discrete response
+    assert np.allclose(run.state()["theta"], th0, rtol=0, atol=1e-6)
+    n = w.chains_per_fold * n_draws
+    rng = np.random.default_rng(3)
+    for k in range(w.K):
+        rows = np.where(w.fold == k)[0]
+        pk = 1.0 / (1.0 + np.exp(-(w.X[rows] @ w.truth["beta"])))
+        yk = w.y[rows]
+        exact = -np.sum(np.log(pk * (1 - pk))) - np.sum((yk - pk) ** 2 / (pk * (1 - pk)))
+
+        def estimate(d):
+            mu = d.mean(axis=0)
+            S = np.cov(d, rowvar=False, ddof=1)
+            r = yk - mu
+            return -np.linalg.slogdet(S)[1] - r @ np.linalg.solve(S, r)
+
+        sims = [estimate((rng.random((n, 3)) < pk).astype(float)) for _ in range(200)]
+        sd = np.std(sims)
+        assert abs(np.mean(sims) - exact) < 0.2 * sd + 0.05 * abs(exact)   # the simulation agrees with the limit
+        assert abs(dss[k] - exact) < 5 * sd + abs(np.mean(sims) - exact), (k, dss[k], exact, sd)
+
+
+def test_logistic_dss_equals_two_pass_on_the_same_draws(orc):
+    # The predictive draws are reproducible: with the chains held at theta,
+    # ytil_i = 1 iff u_i < sigmoid(x_i' theta), u_i from word i % 4 of the
+    # Philox block (i / 4, chain, iteration, stream 5) -- the generator is
+    # pinned by its known-answer vectors.  The DSS from the online sums must
+    # equal the two-pass sample mean and covariance (n - 1 dof) of those draws.
+    w = blocks_of(W.logistic_loo(N=200, p=3, L=4), K=5, T=3)
+    prob = orc.problem_from_workload(w)
+    th0 = np.tile(w.truth["beta"], (w.n_chains, 1))
+    run = orc.OraclePCV(prob, w.chains_per_fold, w.seed, w.leapfrog_steps, eps=1e-12, b=50)
+    run.enable_extra_scores(2)
+    run.set_state(th0, eps=1e-12)
+    n_draws = 50
+    run.sample(n_draws)
+    _, dss = run.extra_scores()
+    key = [w.seed & 0xFFFFFFFF, w.seed >> 32]
+    for k in range(w.K):
+        rows = np.where(w.fold == k)[0]
+        pk = 1.0 / (1.0 + np.exp(-(w.X[rows] @ w.truth["beta"])))
+        d = []
+        for l in range(w.chains_per_fold):
+            c = k * w.chains_per_fold + l
+            for it in range(n_draws):
+                words = orc.philox([0, c, it, 5], key)
+                u = (np.array(words[:3], dtype=np.float64) + 0.5) / 2.0 ** 32
+                d.append((u < pk).astype(float))
+        d = np.array(d)
+        mu = d.mean(axis=0)
+        S = np.cov(d, rowvar=False, ddof=1)
+        r = w.y[rows] - mu
+        ref = -np.linalg.slogdet(S)[1] - r @ np.linalg.solve(S, r)
+        assert abs(dss[k] - ref) <= 1e-9 * max(1.0, abs(ref)), (k, dss[k], ref)
