@@ -62,7 +62,10 @@
 // stops issuing work and exits after freeing TMEM.
 #include <cuda.h>
 
+#include <utility>
+
 #include "pcv_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace pcv {
 
@@ -77,276 +80,33 @@ constexpr int kTcRegsProducer = 64, kTcRegsEpilogue = 208;
 constexpr int kTcMaxStages = 8; // X pipeline stages (as many as fit in shared memory)
 
 
-// softplus(eta) for eta = 2 s (the first GEMM yields s = eta / 2):
-// max(eta, 0) + ln 2 * log2(1 + 2^(-|eta| log2 e)) with the PTX ex2 / lg2
-// approximations
-__device__ __forceinline__ float exp_neg_abs_eta(float s) {   // e^-|eta|, eta = 2 s
-  float e;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(fabsf(s) * -2.8853900817779268f));
-  return e;
-}
-__device__ __forceinline__ float log2_approx(float x) {
-  float l;
-  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(x));
-  return l;
-}
-__device__ __forceinline__ float softplus_half(float s) {
-  const float m = fmaxf(s, 0.0f);
-  return fmaf(log2_approx(1.0f + exp_neg_abs_eta(s)), 0.6931471805599453f, m + m);
-}
-
-// ----------------------------- PTX helpers --------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait (2 s of wall time).  Returns false on time-out or abort.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
-                                       unsigned int *err) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  while (!mbar_try_wait(bar, parity)) {
-    if (*abort_flag) return false;
-    if (global_ns() - t0 > 2000000000ull) {
-      atomicOr(err, 1u);
-      *abort_flag = 1;
-      return false;
-    }
-  }
-  return true;
-}
-__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Non-blocking check first (cheap when the phase has completed), then the
-// bounded blocking wait.
-__device__ __forceinline__ bool mbar_wait_fast(uint32_t bar, uint32_t parity, volatile int *abort_flag,
-                                               unsigned int *err) {
-  return mbar_test(bar, parity) || mbar_wait(bar, parity, abort_flag, err);
-}
-// Warp-uniform bounded wait: lane 0 waits, the outcome is broadcast, and
-// __syncwarp orders the other lanes after lane 0's acquire.  Keeps the
-// warp converged for the .sync.aligned tcgen05 instructions that follow.
-__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
-                                          unsigned int *err) {
-  int ok = 0;
-  if ((threadIdx.x & 31) == 0) ok = mbar_wait_fast(bar, parity, abort_flag, err) ? 1 : 0;
-  ok = __shfl_sync(0xffffffffu, ok, 0);
-  __syncwarp();
-  return ok != 0;
-}
-// Bounded wait that ignores the abort flag (draining copies in flight).
-__device__ __forceinline__ void mbar_wait_quiet(uint32_t bar, uint32_t parity) {
-  const uint64_t t0 = global_ns();
-  while (!mbar_try_wait(bar, parity))
-    if (global_ns() - t0 > 2000000000ull) return;
-}
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *tm, int x, int y,
-                                            uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
-                                            uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-      : "memory");
-  // Keep consecutive MMAs of an unrolled group apart: without an instruction
-  // between them, the last MMA of a short unrolled group (4 MMAs) was
-  // measured to accumulate a wrong product on sm_103a.
-  __syncwarp(1u);
-}
-__device__ __forceinline__ void tc_mma_bf16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
-                                               uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
-      : "memory");
-  __syncwarp(1u);   // see tc_mma_bf16
-}
-#define PCV_TMEM_ST32(taddr, v)                                                                  \
-  asm volatile(                                                                                  \
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13," \
-      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"            \
-      ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), \
-        "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]),         \
-        "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]),       \
-        "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),       \
-        "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])                                            \
-      : "memory")
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-#define PCV_TMEM_LD32(taddr, v)                                                                  \
-  asm volatile(                                                                                  \
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"  \
-      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"      \
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),    \
-        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), \
-        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),          \
-        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),          \
-        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])           \
-      : "r"(taddr))
-#define PCV_TMEM_LD16(taddr, v)                                                                  \
-  asm volatile(                                                                                  \
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"  \
-      "%14,%15}, [%16];"                                                                         \
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),    \
-        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), \
-        "=r"(v[14]), "=r"(v[15])                                                                 \
-      : "r"(taddr))
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-// one TMEM load of 128 consecutive columns (a whole S row of the thread's lane)
-#define PCV_TMEM_LD128(taddr, v)                                                     \
-  asm volatile(                                                                      \
-      "tcgen05.ld.sync.aligned.32x32b.x128.b32 {"                                    \
-      "%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15," \
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31," \
-      "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47," \
-      "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63," \
-      "%64,%65,%66,%67,%68,%69,%70,%71,%72,%73,%74,%75,%76,%77,%78,%79," \
-      "%80,%81,%82,%83,%84,%85,%86,%87,%88,%89,%90,%91,%92,%93,%94,%95," \
-      "%96,%97,%98,%99,%100,%101,%102,%103,%104,%105,%106,%107,%108,%109,%110,%111," \
-      "%112,%113,%114,%115,%116,%117,%118,%119,%120,%121,%122,%123,%124,%125,%126,%127" \
-      "}, [%128];"                                                                  \
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), \
-        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), \
-        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), \
-        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31]), \
-        "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]), "=r"(v[37]), "=r"(v[38]), "=r"(v[39]), \
-        "=r"(v[40]), "=r"(v[41]), "=r"(v[42]), "=r"(v[43]), "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]), \
-        "=r"(v[48]), "=r"(v[49]), "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]), \
-        "=r"(v[56]), "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]), "=r"(v[62]), "=r"(v[63]), \
-        "=r"(v[64]), "=r"(v[65]), "=r"(v[66]), "=r"(v[67]), "=r"(v[68]), "=r"(v[69]), "=r"(v[70]), "=r"(v[71]), \
-        "=r"(v[72]), "=r"(v[73]), "=r"(v[74]), "=r"(v[75]), "=r"(v[76]), "=r"(v[77]), "=r"(v[78]), "=r"(v[79]), \
-        "=r"(v[80]), "=r"(v[81]), "=r"(v[82]), "=r"(v[83]), "=r"(v[84]), "=r"(v[85]), "=r"(v[86]), "=r"(v[87]), \
-        "=r"(v[88]), "=r"(v[89]), "=r"(v[90]), "=r"(v[91]), "=r"(v[92]), "=r"(v[93]), "=r"(v[94]), "=r"(v[95]), \
-        "=r"(v[96]), "=r"(v[97]), "=r"(v[98]), "=r"(v[99]), "=r"(v[100]), "=r"(v[101]), "=r"(v[102]), "=r"(v[103]), \
-        "=r"(v[104]), "=r"(v[105]), "=r"(v[106]), "=r"(v[107]), "=r"(v[108]), "=r"(v[109]), "=r"(v[110]), "=r"(v[111]), \
-        "=r"(v[112]), "=r"(v[113]), "=r"(v[114]), "=r"(v[115]), "=r"(v[116]), "=r"(v[117]), "=r"(v[118]), "=r"(v[119]), \
-        "=r"(v[120]), "=r"(v[121]), "=r"(v[122]), "=r"(v[123]), "=r"(v[124]), "=r"(v[125]), "=r"(v[126]), "=r"(v[127]) \
-      : "r"(taddr))
-#define PCV_TMEM_ST16(taddr, v)                                                                  \
-  asm volatile(                                                                                  \
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13," \
-      "%14,%15,%16};" ::"r"(taddr),                                                              \
-      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),    \
-      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]) \
-      : "memory")
-// The compiler does not know that a TMEM load writes its registers until the
-// wait, nor that a TMEM store may read its sources until the wait: an empty
-// asm that "modifies" the registers, placed right after the wait, keeps
-// every use of loaded values after it and every source register alive (not
-// reused for temporaries) up to it.
-template <int Nr>
-__device__ __forceinline__ void tmem_fence_regs(uint32_t (&v)[Nr]) {
-#pragma unroll
-  for (int k = 0; k < Nr; ++k) asm volatile("" : "+r"(v[k]));
-}
-
-// Shared-memory matrix descriptor (tcgen05): start >> 4 at bits 0-13, leading
-// byte offset >> 4 at 16-29, stride byte offset >> 4 at 32-45, the fixed
-// version 0b001 at 46-48, 128-byte swizzle (value 2) at 61-63.
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-// Instruction descriptor, kind::f16: D F32 (bits 4-5 = 1), A and B BF16
-// (bits 7-9 = 1, 10-12 = 1), A K-major, B K-major or MN-major (bit 16),
-// N >> 3 at 17-22, M >> 4 at 24-28.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool b_mn_major) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((b_mn_major ? 1u : 0u) << 16) |
-         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ uint32_t bf16x2_from(float lo, float hi) {
-  uint32_t r;
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
-  return r;
-}
-// hi + lo += v with the rounding error of the sum kept in lo (Knuth's
-// TwoSum: exact for any magnitudes)
-__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float v) {
-  const float s = hi + v;
-  const float bp = s - hi;
-  lo += (hi - (s - bp)) + (v - bp);
-  hi = s;
-}
-__device__ __forceinline__ float tanh_f32(float x) {
-  float r;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-
-// CTA owning flattened unit u when U units are split over n CTAs as
-// [floor(b U / n), floor((b+1) U / n)).
-__host__ __device__ inline int owner_cta(long long u, long long U, long long n) {
-  return (int)(((u + 1) * n + U - 1) / U - 1);
-}
-
 // --------------------------------------------------------------------------
 // KS (GEMM1 K steps of 16, = ceil(p / 16)) is a template parameter so that
 // every MMA group is straight-line code: MMAs issued from a runtime-count
 // loop between commits measured up to 3x slower on sm_103a.
-template <int KS, bool ACC, bool GAUSS>
+//
+// TF (the TF32 operand form): kind::tf32 MMAs (K = 8 per instruction) on
+// FP32 shadows of theta and an FP32 copy of X, both rounded to TF32, hi part
+// only; chunks of 64 rows (so that the FP32 tiles fit in shared memory and
+// TMEM); the second GEMM reads X^T (a K-major copy, loaded with each chunk
+// through tm_lo, which the TF form does not otherwise use) so that both
+// GEMMs take K-major operands; the residual goes to TMEM as TF32, one
+// element per column.
+template <int KS, bool ACC, bool GAUSS, bool TF = false>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_grad_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_hi,
               const __grid_constant__ CUtensorMap tm_lo, Problem pb, GradArgs a, TcArgs ta) {
+  constexpr int TN = TF ? 64 : kTN;                // rows per chunk
+  constexpr int AE = TF ? 32 : 64;                 // operand elements per 128-byte K atom
+  constexpr int NQ = TN / 32;                      // 32-row quarters per chunk
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte aligned base, by an offset into the shared array (so that the
   // compiler keeps shared-memory loads for y)
   uint8_t *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  const int KA = ta.KP / 64;                       // 128-byte K atoms
+  const int KA = ta.KP / AE;                       // 128-byte K atoms
   const uint32_t th_bytes = (uint32_t)KA * kTM * 128;
-  const uint32_t x_bytes = (uint32_t)KA * kTN * 128;
+  const uint32_t xk_bytes = (uint32_t)KA * TN * 128;            // K-major X chunk
+  const uint32_t x_bytes = xk_bytes + (TF ? 2u * ta.PN * 128u : 0u);   // + X^T chunk (TF)
   const int NS = ta.NS;
   uint8_t *th_hi = sm;
   uint8_t *th_lo = th_hi + th_bytes;
@@ -395,8 +155,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_base_slot;
 
-  const uint32_t tmem_G = tmem + 256;
-  const uint32_t tmem_R = tmem + 384;              // R[b] at tmem_R + 64 b (bf16x2 per column)
+  // S[b] at tmem + TN b; G after them; R[b] (64 columns: 128 rows as
+  // bf16x2, or 64 rows as TF32) after G
+  const uint32_t tmem_G = tmem + 2 * TN;
+  const uint32_t tmem_R = tmem_G + 128;
 
   if (warp < 4) {
   // register split: warpgroup 0 (producers) gives registers up ...
@@ -415,9 +177,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           if (!mbar_wait_fast(smem_u32(th_empty), (seg & 1) ^ 1, abort_flag, ta.err)) break;
           mbar_expect_tx(smem_u32(th_full), th_bytes * (ta.need_lo ? 2 : 1));
           for (int kb = 0; kb < KA; ++kb) {
-            tma_load_2d(smem_u32(th_hi + kb * kTM * 128), &tm_hi, kb * 64, t * kTM, smem_u32(th_full));
-            if (ta.need_lo)
-              tma_load_2d(smem_u32(th_lo + kb * kTM * 128), &tm_lo, kb * 64, t * kTM, smem_u32(th_full));
+            tma_load_2d(smem_u32(th_hi + kb * kTM * 128), &tm_hi, kb * AE, t * kTM, smem_u32(th_full));
+            if (!TF && ta.need_lo)
+              tma_load_2d(smem_u32(th_lo + kb * kTM * 128), &tm_lo, kb * AE, t * kTM, smem_u32(th_full));
           }
           th_issued = seg;
           ++seg;
@@ -427,7 +189,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         mbar_expect_tx(smem_u32(&x_full[st]), x_bytes);
         uint8_t *xb = xs + (size_t)st * x_bytes;
         for (int kb = 0; kb < KA; ++kb)
-          tma_load_2d(smem_u32(xb + kb * kTN * 128), &tm_x, kb * 64, j * kTN, smem_u32(&x_full[st]));
+          tma_load_2d(smem_u32(xb + kb * TN * 128), &tm_x, kb * AE, j * TN, smem_u32(&x_full[st]));
+        if constexpr (TF) {
+          // X^T of the chunk: two 32-row column blocks of PN feature rows
+          for (int h = 0; h < 2; ++h)
+            tma_load_2d(smem_u32(xb + xk_bytes + h * ta.PN * 128), &tm_lo, j * TN + 32 * h, 0,
+                        smem_u32(&x_full[st]));
+        }
         last_round[st] = rnd;
       }
       // on abort: let copies already issued land before the CTA exits
@@ -442,7 +210,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // Per unit i: S[i & 1] = Theta . X_chunk^T (hi + lo).  (tile, chunk), stage
     // and parities are tracked incrementally.
     if (lane == 0) {
-      const uint32_t id1 = idesc_bf16(kTM, kTN, false);
+      const uint32_t id1 = TF ? idesc_tf32(kTM, TN) : idesc_bf16(kTM, kTN, false);
       const uint64_t hd0 = sdesc_sw128(smem_u32(th_hi), 16, 1024);
       const uint64_t ld0 = sdesc_sw128(smem_u32(th_lo), 16, 1024);
       const uint64_t xd_k = sdesc_sw128(smem_u32(xs), 16, 1024);   // K-major view, stage 0
@@ -458,14 +226,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (!mbar_wait_fast(smem_u32(&s_empty[sb]), ((i >> 1) & 1) ^ 1, abort_flag, ta.err)) break;
         tc_fence_after();
         const uint64_t xd0 = xd_k + (uint64_t)st * x_step;
-        const uint32_t dS = tmem + sb * 128;
+        const uint32_t dS = tmem + sb * TN;
 #pragma unroll
         for (int ks = 0; ks < KS; ++ks) {
+          // K step ks: 32 bytes into 128-byte atom ks / 4 (16 bf16 or 8 TF32)
           const uint64_t off = (uint64_t)((((ks >> 2) * kTM * 128) + (ks & 3) * 32) >> 4);
-          const uint64_t offx = (uint64_t)((((ks >> 2) * kTN * 128) + (ks & 3) * 32) >> 4);
-          tc_mma_bf16(dS, hd0 + off, xd0 + offx, id1, ks > 0 ? 1u : 0u);
+          const uint64_t offx = (uint64_t)((((ks >> 2) * TN * 128) + (ks & 3) * 32) >> 4);
+          if constexpr (TF) tc_mma_tf32(dS, hd0 + off, xd0 + offx, id1, ks > 0 ? 1u : 0u);
+          else tc_mma_bf16(dS, hd0 + off, xd0 + offx, id1, ks > 0 ? 1u : 0u);
         }
-        if (ta.need_lo) {
+        if (!TF && ta.need_lo) {
 #pragma unroll
           for (int ks = 0; ks < KS; ++ks) {
             const uint64_t off = (uint64_t)((((ks >> 2) * kTM * 128) + (ks & 3) * 32) >> 4);
@@ -484,8 +254,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // Per unit i: G += R[i & 1] . X_chunk, four K steps (64 rows) per half
     // of R as the epilogue produces it.
     if (lane == 0) {
-      const uint32_t id2 = idesc_bf16(kTM, ta.PN, true);
-      const uint64_t xd_mn = sdesc_sw128(smem_u32(xs), kTN * 128, 1024);  // MN-major view, stage 0
+      const uint32_t id2 = TF ? idesc_tf32(kTM, ta.PN) : idesc_bf16(kTM, ta.PN, true);
+      // bf16: X chunk as the MN-major B operand; TF: X^T chunk, K-major
+      const uint64_t xd_mn = TF ? sdesc_sw128(smem_u32(xs) + xk_bytes, 16, 1024)
+                                : sdesc_sw128(smem_u32(xs), kTN * 128, 1024);
       const uint64_t x_step = (uint64_t)(x_bytes >> 4);
       int j = (int)(u0 % ta.J);
       int seg2 = 0, st = 0;
@@ -505,8 +277,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
             const int ks = 4 * qq + kk;
-            tc_mma_bf16_ta(tmem_G, a0 + 8 * ks, bd0 + (uint64_t)((ks * 2048) >> 4), id2,
-                           (first && ks == 0) ? 0u : 1u);
+            if constexpr (TF)   // 8 rows per K step: 32 bytes into 128-byte atom ks / 4 of X^T
+              tc_mma_tf32_ta(tmem_G, a0 + 8 * ks,
+                             bd0 + (uint64_t)((((ks >> 2) * ta.PN * 128) + (ks & 3) * 32) >> 4), id2,
+                             (first && ks == 0) ? 0u : 1u);
+            else                // 16 rows per K step: 2048 bytes of the MN-major X chunk
+              tc_mma_bf16_ta(tmem_G, a0 + 8 * ks, bd0 + (uint64_t)((ks * 2048) >> 4), id2,
+                             (first && ks == 0) ? 0u : 1u);
           }
         }
         if (!ok) break;
@@ -561,33 +338,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int j = j0 + (i - ib);
         if (!warp_wait(smem_u32(&s_full[sb]), (i >> 1) & 1, abort_flag, ta.err)) { aborted = true; break; }
         tc_fence_after();
-        // residual of quarter qq (32 rows) of the chunk from v = S into pk
-        // (16 bf16x2), plus the log-likelihood sums when ACC
-        auto quarter = [&](const int qq, const uint32_t (&v)[32], uint32_t (&pk)[16]) {
-          const int n0 = j * kTN + 32 * qq;
+        // residuals r of quarter qq (32 rows) of the chunk from v = S (FP32,
+        // the fold's excluded rows not yet masked), plus the log-likelihood
+        // or squared-residual sums
+        auto quarter = [&](const int qq, const uint32_t (&v)[32], float (&r)[32]) {
+          const int n0 = j * TN + 32 * qq;
           if constexpr (!GAUSS) {
             // 1 - tanh(S) in FP32 (twice the residual along the sign-folded
-            // row), rounded to bf16 for the second GEMM.  A bf16x2 tanh here
-            // would bias the gradient: its error is a smooth function of eta,
-            // so it adds up over rows instead of averaging out (a force error
-            // of ~6 % of the posterior scale per dimension at N = 1e5, which
-            // shrinks the adapted step size).
+            // row), rounded to bf16 (or TF32) for the second GEMM.  A bf16x2
+            // tanh here would bias the gradient: its error is a smooth
+            // function of eta, so it adds up over rows instead of averaging
+            // out (a force error of ~6 % of the posterior scale per dimension
+            // at N = 1e5, which shrinks the adapted step size).
 #pragma unroll
-            for (int k = 0; k < 16; ++k)
-              pk[k] = bf16x2_from(1.0f - tanh_f32(__uint_as_float(v[2 * k])),
-                                  1.0f - tanh_f32(__uint_as_float(v[2 * k + 1])));
-            if (valid && n0 < fd.excl_hi && n0 + 32 > fd.excl_lo) {
-#pragma unroll
-              for (int k = 0; k < 32; ++k) {
-                const int n = n0 + k;
-                if (n >= fd.excl_lo && n < fd.excl_hi) pk[k >> 1] &= (k & 1) ? 0x0000FFFFu : 0xFFFF0000u;
-              }
-            }
+            for (int k = 0; k < 32; ++k) r[k] = 1.0f - tanh_f32(__uint_as_float(v[k]));
             if constexpr (accurate) {
               // log likelihood y eta - softplus(eta) = -softplus(-2 S) with
               // the sign-folded S: softplus(-2 S) = max(-2 S, 0) +
               // log(1 + exp(-|2 S|)) is summed here, in FP32 per quarter and
-              // FP64 across quarters.
+              // as an exact FP32 pair across quarters.
               // Quarters clear of the fold's excluded rows and of the
               // padding need no per-row mask; there the logs of eight rows
               // are taken at once, as the log of the product of their
@@ -630,24 +399,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 two_sum_add(te_hi, te_lo, te);
               }
             }
-
           } else {
-            // Gaussian: residual (y - eta) / sigma^2 = -2 S / sigma^2, rounded
-            // to bf16; the squared residuals of the fold's training and test
-            // rows feed the log sigma gradient and the log densities
+            // Gaussian: residual (y - eta) / sigma^2 = -2 S / sigma^2; the
+            // squared residuals of the fold's training and test rows feed the
+            // log sigma gradient and the log densities
             float e[32];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-              e[2 * k] = -2.0f * __uint_as_float(v[2 * k]);
-              e[2 * k + 1] = -2.0f * __uint_as_float(v[2 * k + 1]);
-              pk[k] = bf16x2_from(e[2 * k] * inv_s2, e[2 * k + 1] * inv_s2);
-            }
-            if (valid && n0 < fd.excl_hi && n0 + 32 > fd.excl_lo) {
-#pragma unroll
-              for (int k = 0; k < 32; ++k) {
-                const int n = n0 + k;
-                if (n >= fd.excl_lo && n < fd.excl_hi) pk[k >> 1] &= (k & 1) ? 0x0000FFFFu : 0xFFFF0000u;
-              }
+            for (int k = 0; k < 32; ++k) {
+              e[k] = -2.0f * __uint_as_float(v[k]);
+              r[k] = e[k] * inv_s2;
             }
             if (need_e2) {
               if (n0 + 32 <= pb.N && (n0 + 32 <= fd.excl_lo || n0 >= fd.excl_hi)) {
@@ -673,34 +433,51 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
           }
         };
-        // The whole S tile row (128 columns) comes into registers at once and
-        // S is released before any arithmetic, so the first GEMM of unit
-        // i + 2 waits only for the TMEM loads of unit i.  The four R quarters
-        // go out as 16-column stores; each store's wait comes after the
-        // next quarter's arithmetic (TMEM round trips are several hundred
-        // cycles while the MMAs run), and each completed quarter is handed
-        // to the second GEMM at once.  Loaded registers are used only after
-        // the load wait, and store sources stay allocated until their store
-        // wait (tmem_fence_regs pins both).
-        if constexpr (ACC) {
-          // log-density launch (one of L_f per iteration): a rolled loop
-          // over the quarters, each loaded from TMEM on its own, keeps this
-          // instantiation's code small (the unrolled form below, with the
-          // softplus sums, overflowed the instruction cache); S is released
-          // after the last quarter's load
+        // the bf16 form of quarter qq: 16 bf16x2 (rows 2c, 2c + 1 in column c),
+        // the fold's excluded rows zeroed
+        auto pack16 = [&](const int qq, const float (&r)[32], uint32_t (&pk)[16]) {
+#pragma unroll
+          for (int k = 0; k < 16; ++k) pk[k] = bf16x2_from(r[2 * k], r[2 * k + 1]);
+          const int n0 = j * TN + 32 * qq;
+          if (valid && n0 < fd.excl_hi && n0 + 32 > fd.excl_lo) {
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+              const int n = n0 + k;
+              if (n >= fd.excl_lo && n < fd.excl_hi) pk[k >> 1] &= (k & 1) ? 0x0000FFFFu : 0xFFFF0000u;
+            }
+          }
+        };
+        // the TF32 form: one element per column, the excluded rows zeroed
+        auto pack32 = [&](const int qq, const float (&r)[32], uint32_t (&pk)[32]) {
+          const int n0 = j * TN + 32 * qq;
+          const bool edge = valid && n0 < fd.excl_hi && n0 + 32 > fd.excl_lo;
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            const int n = n0 + k;
+            pk[k] = (edge && n >= fd.excl_lo && n < fd.excl_hi) ? 0u : tf32_bits(r[k]);
+          }
+        };
+        if constexpr (ACC || TF) {
+          // a rolled loop over the quarters, each loaded from TMEM on its own:
+          // the log-density launch (one of L_f per iteration: small code for
+          // the instruction cache) and the TF32 form (two quarters per
+          // chunk); S is released after the last quarter's load, and each
+          // stored half of R (TF32: each quarter) is handed to the second
+          // GEMM at once
           const uint32_t rbuf = tmem_R + 64 * rb + lane_off;
 #pragma unroll 1
-          for (int qq = 0; qq < 4; ++qq) {
-            uint32_t v[32], pk[16];
-            PCV_TMEM_LD32(tmem + sb * 128 + lane_off + 32 * qq, v);
+          for (int qq = 0; qq < NQ; ++qq) {
+            uint32_t v[32];
+            float r[32];
+            PCV_TMEM_LD32(tmem + sb * TN + lane_off + 32 * qq, v);
             tmem_wait_ld();
             tmem_fence_regs(v);
-            if (qq == 3) {
+            if (qq == NQ - 1) {
               tc_fence_before();
               __syncwarp();
               if (lane == 0) mbar_arrive(smem_u32(&s_empty[sb]));
             }
-            quarter(qq, v, pk);
+            quarter(qq, v, r);
             if (qq == 0) {
               if (!warp_wait(smem_u32(&r_empty[rb]), ((i >> 1) & 1) ^ 1, abort_flag, ta.err)) {
                 aborted = true;
@@ -708,20 +485,30 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               }
               tc_fence_after();
             }
-            PCV_TMEM_ST16(rbuf + 16 * qq, pk);
-            tmem_wait_st();
-            tmem_fence_regs(pk);
-            if (qq & 1) {                                   // a 64-row half of R is in TMEM
+            if constexpr (TF) {
+              uint32_t pk[32];
+              pack32(qq, r, pk);
+              PCV_TMEM_ST32(rbuf + 32 * qq, pk);
+              tmem_wait_st();
+              tmem_fence_regs(pk);
+            } else {
+              uint32_t pk[16];
+              pack16(qq, r, pk);
+              PCV_TMEM_ST16(rbuf + 16 * qq, pk);
+              tmem_wait_st();
+              tmem_fence_regs(pk);
+            }
+            if (TF || (qq & 1)) {
               tc_fence_before();
               __syncwarp();
-              if (lane == 0) mbar_arrive(smem_u32(&r_part[4 * rb + (qq >> 1)]));
+              if (lane == 0) mbar_arrive(smem_u32(&r_part[4 * rb + (TF ? qq : qq >> 1)]));
             }
           }
           if (aborted) break;
           continue;
         }
         uint32_t sv[128], p0[16], p1[16], p2[16], p3[16];
-        PCV_TMEM_LD128(tmem + sb * 128 + lane_off, sv);   // one load: ~2 % faster than four x32
+        PCV_TMEM_LD128(tmem + sb * TN + lane_off, sv);   // one load: ~2 % faster than four x32
         tmem_wait_ld();
         tmem_fence_regs(sv);
         // the four 32-row quarters of the row (constant indices: registers)
@@ -732,7 +519,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&s_empty[sb]));   // S fully read: release it
-        quarter(0, v0, p0);
+        {
+          float r[32];
+          quarter(0, v0, r);
+          pack16(0, r, p0);
+        }
         if (!warp_wait(smem_u32(&r_empty[rb]), ((i >> 1) & 1) ^ 1, abort_flag, ta.err)) { aborted = true; break; }
         tc_fence_after();
         // R row m (TMEM lane m): chunk rows 2c, 2c + 1 in bf16x2 column c
@@ -747,14 +538,26 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           if (lane == 0) mbar_arrive(smem_u32(&r_part[4 * rb + qq]));
         };
         PCV_TMEM_ST16(rbuf, p0);
-        quarter(1, v1, p1);
+        {
+          float r[32];
+          quarter(1, v1, r);
+          pack16(1, r, p1);
+        }
         PCV_TMEM_ST16(rbuf + 16, p1);
-        quarter(2, v2, p2);
+        {
+          float r[32];
+          quarter(2, v2, r);
+          pack16(2, r, p2);
+        }
         quarter_stored(0);
         tmem_fence_regs(p0);
         tmem_fence_regs(p1);
         PCV_TMEM_ST16(rbuf + 32, p2);
-        quarter(3, v3, p3);
+        {
+          float r[32];
+          quarter(3, v3, r);
+          pack16(3, r, p3);
+        }
         PCV_TMEM_ST16(rbuf + 48, p3);
         quarter_stored(1);
         tmem_fence_regs(p2);
@@ -869,9 +672,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const float4 tn = make_float4(tv[u].x + eps * mv[u].x * r4.x, tv[u].y + eps * mv[u].y * r4.y,
                                           tv[u].z + eps * mv[u].z * r4.z, tv[u].w + eps * mv[u].w * r4.w);
             *reinterpret_cast<float4 *>(const_cast<float *>(a.theta) + (size_t)cc_[u] * a.ld_theta + jj_[u]) = tn;
-            // shadows hold (theta - ref) / 2 as bf16 hi + lo
+            // shadows hold (theta - ref) / 2 as bf16 hi + lo (TF32: one part)
             const float h0 = 0.5f * (tn.x - rf[u].x), h1 = 0.5f * (tn.y - rf[u].y);
             const float h2 = 0.5f * (tn.z - rf[u].z), h3 = 0.5f * (tn.w - rf[u].w);
+            if constexpr (TF) {
+              *reinterpret_cast<uint4 *>(ta.shadow32 + (size_t)cc_[u] * a.ld_shadow + jj_[u]) =
+                  make_uint4(tf32_bits(h0), tf32_bits(h1), tf32_bits(h2), tf32_bits(h3));
+              continue;
+            }
             const uint32_t hi01 = bf16x2_from(h0, h1), hi23 = bf16x2_from(h2, h3);
             const float l0 = h0 - __uint_as_float(hi01 << 16), l1 = h1 - __uint_as_float(hi01 & 0xFFFF0000u);
             const float l2 = h2 - __uint_as_float(hi23 << 16), l3 = h3 - __uint_as_float(hi23 & 0xFFFF0000u);
@@ -901,6 +709,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               const float tn = tv + eps * a.minv[jj] * rj;
               th[jj] = tn;
               const float half = 0.5f * (tn - ta.theta_ref[jj]);   // shadows hold (theta - ref) / 2
+              if constexpr (TF) {
+                ta.shadow32[(size_t)cc * a.ld_shadow + jj] = __uint_as_float(tf32_bits(half));
+                continue;
+              }
               const __nv_bfloat16 hi = __float2bfloat16_rn(half);
               a.shadow_hi[(size_t)cc * a.ld_shadow + jj] = hi;
               a.shadow_lo[(size_t)cc * a.ld_shadow + jj] = __float2bfloat16_rn(half - __bfloat162float(hi));
@@ -998,12 +810,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-size_t tc_smem_bytes(int KP, int NS, int need_lo, int p) {
+size_t tc_smem_bytes(int KP, int NS, int need_lo, int p, int tf32, int PN) {
   (void)p;
-  const size_t KA = KP / 64;
-  size_t b = KA * kTM * 128 * (need_lo ? 2 : 1) + (size_t)NS * KA * kTN * 128 +
-             64 + (2 * kTcMaxStages + 23) * 8;   // barrier / flag slots
-  return b + 1024;   // alignment slack
+  size_t b;
+  if (tf32) {   // theta hi; per stage the 64-row X chunk and its X^T (2 x PN rows of 128 B)
+    const size_t KA = KP / 32;
+    b = KA * kTM * 128 + (size_t)NS * (KA * 64 * 128 + 2 * (size_t)PN * 128);
+  } else {
+    const size_t KA = KP / 64;
+    b = KA * kTM * 128 * (need_lo ? 2 : 1) + (size_t)NS * KA * kTN * 128;
+  }
+  b += 64 + (2 * kTcMaxStages + 23) * 8;   // barrier / flag slots
+  return b + 1024;                          // alignment slack
 }
 
 int tc_max_stages() { return kTcMaxStages; }
@@ -1019,13 +837,13 @@ int tc_segments_per_tile(int T, int J, int n_cta) {
   return mx;
 }
 
-template <int KS>
+template <int KS, bool TF>
 static cudaError_t set_smem_attr() {
   const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t r[4] = {cudaFuncSetAttribute(k_grad_tc<KS, false, false>, at, 227 * 1024),
-                      cudaFuncSetAttribute(k_grad_tc<KS, true, false>, at, 227 * 1024),
-                      cudaFuncSetAttribute(k_grad_tc<KS, false, true>, at, 227 * 1024),
-                      cudaFuncSetAttribute(k_grad_tc<KS, true, true>, at, 227 * 1024)};
+  cudaError_t r[4] = {cudaFuncSetAttribute(k_grad_tc<KS, false, false, TF>, at, 227 * 1024),
+                      cudaFuncSetAttribute(k_grad_tc<KS, true, false, TF>, at, 227 * 1024),
+                      cudaFuncSetAttribute(k_grad_tc<KS, false, true, TF>, at, 227 * 1024),
+                      cudaFuncSetAttribute(k_grad_tc<KS, true, true, TF>, at, 227 * 1024)};
   for (cudaError_t x : r)
     if (x != cudaSuccess) return x;
   return cudaSuccess;
@@ -1036,56 +854,77 @@ static cudaError_t set_smem_attr() {
 // count), so a split larger than that would never be granted.  Every
 // instantiation is checked once; launches are refused if any fails.
 static bool g_tc_regs_ok = false;
-template <int KS>
+template <int KS, bool TF>
 static bool regs_fit() {
   const long need = 128L * kTcRegsProducer + 256L * kTcRegsEpilogue;
   cudaFuncAttributes fa[4];
-  if (cudaFuncGetAttributes(&fa[0], k_grad_tc<KS, false, false>) != cudaSuccess ||
-      cudaFuncGetAttributes(&fa[1], k_grad_tc<KS, true, false>) != cudaSuccess ||
-      cudaFuncGetAttributes(&fa[2], k_grad_tc<KS, false, true>) != cudaSuccess ||
-      cudaFuncGetAttributes(&fa[3], k_grad_tc<KS, true, true>) != cudaSuccess)
+  if (cudaFuncGetAttributes(&fa[0], k_grad_tc<KS, false, false, TF>) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa[1], k_grad_tc<KS, true, false, TF>) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa[2], k_grad_tc<KS, false, true, TF>) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa[3], k_grad_tc<KS, true, true, TF>) != cudaSuccess)
     return false;
   for (const cudaFuncAttributes &f : fa)
     if ((long)f.numRegs * kTcThreads < need) return false;
   return true;
 }
 
+template <int... K>
+static bool all_prepared(std::integer_sequence<int, K...>) {
+  bool ok = true;
+  ((ok = ok && set_smem_attr<K + 1, false>() == cudaSuccess && regs_fit<K + 1, false>()), ...);
+  return ok;
+}
+template <int... K>
+static bool all_prepared_tf(std::integer_sequence<int, K...>) {
+  bool ok = true;
+  ((ok = ok && set_smem_attr<K + 1, true>() == cudaSuccess && regs_fit<K + 1, true>()), ...);
+  return ok;
+}
+
 // once per context (outside any stream capture): allow the large dynamic SMEM
+// (bf16 form: K steps 1 .. 9, p <= 128; TF32 form: 1 .. 15, p <= 112)
 cudaError_t tc_prepare() {
-  cudaError_t e = cudaSuccess;
-  cudaError_t r[9] = {set_smem_attr<1>(), set_smem_attr<2>(), set_smem_attr<3>(), set_smem_attr<4>(), set_smem_attr<5>(),
-                      set_smem_attr<6>(), set_smem_attr<7>(), set_smem_attr<8>(), set_smem_attr<9>()};
-  for (cudaError_t x : r)
-    if (x != cudaSuccess) e = x;
-  g_tc_regs_ok = regs_fit<1>() && regs_fit<2>() && regs_fit<3>() && regs_fit<4>() && regs_fit<5>() &&
-                 regs_fit<6>() && regs_fit<7>() && regs_fit<8>() && regs_fit<9>();
-  if (e == cudaSuccess && !g_tc_regs_ok) e = cudaErrorInvalidConfiguration;
-  return e;
+  g_tc_regs_ok = all_prepared(std::make_integer_sequence<int, 9>{}) &&
+                 all_prepared_tf(std::make_integer_sequence<int, 15>{});
+  return g_tc_regs_ok ? cudaSuccess : cudaErrorInvalidConfiguration;
+}
+
+template <int K, bool TF>
+static void launch_k(bool gauss, bool accurate, const CUtensorMap &tm_x, const CUtensorMap &tm_hi,
+                     const CUtensorMap &tm_lo, const Problem &pb, const GradArgs &a, const TcArgs &ta, size_t smem,
+                     cudaStream_t st) {
+  if (gauss) {
+    if (accurate) k_grad_tc<K, true, true, TF><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta);
+    else k_grad_tc<K, false, true, TF><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta);
+  } else {
+    if (accurate) k_grad_tc<K, true, false, TF><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta);
+    else k_grad_tc<K, false, false, TF><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta);
+  }
+}
+
+template <bool TF, int... K>
+static bool launch_ks(int ks, std::integer_sequence<int, K...>, bool gauss, bool accurate, const CUtensorMap &tm_x,
+                      const CUtensorMap &tm_hi, const CUtensorMap &tm_lo, const Problem &pb, const GradArgs &a,
+                      const TcArgs &ta, size_t smem, cudaStream_t st) {
+  bool done = false;
+  ((ks == K + 1 ? (launch_k<K + 1, TF>(gauss, accurate, tm_x, tm_hi, tm_lo, pb, a, ta, smem, st), done = true)
+                : false), ...);
+  return done;
 }
 
 cudaError_t launch_grad_tc(const CUtensorMap &tm_x, const CUtensorMap &tm_hi, const CUtensorMap &tm_lo,
                            const Problem &pb, const GradArgs &a, const TcArgs &ta, cudaStream_t st) {
-  const size_t smem = tc_smem_bytes(ta.KP, ta.NS, ta.need_lo, pb.p);
+  const size_t smem = tc_smem_bytes(ta.KP, ta.NS, ta.need_lo, pb.p, ta.tf32, ta.PN);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   if (!g_tc_regs_ok) return cudaErrorInvalidConfiguration;   // tc_prepare not run, or the split does not fit
   if (pb.variant == MV_HIER) return cudaErrorInvalidValue;
+  if (ta.tf32 && ta.need_lo) return cudaErrorInvalidValue;    // the TF32 form has no lo part
   const bool gauss = pb.variant == MV_GAUSS_KNOWN || pb.variant == MV_GAUSS_LOGSIG;
-  switch (ta.KS) {
-#define PCV_TC_CASE(K)                                                                          \
-  case K:                                                                                       \
-    if (gauss) {                                                                                \
-      if (ta.accurate) k_grad_tc<K, true, true><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta); \
-      else k_grad_tc<K, false, true><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta);           \
-    } else {                                                                                    \
-      if (ta.accurate) k_grad_tc<K, true, false><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta); \
-      else k_grad_tc<K, false, false><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta);           \
-    }                                                                                           \
-    break;
-    PCV_TC_CASE(1) PCV_TC_CASE(2) PCV_TC_CASE(3) PCV_TC_CASE(4)
-    PCV_TC_CASE(5) PCV_TC_CASE(6) PCV_TC_CASE(7) PCV_TC_CASE(8) PCV_TC_CASE(9)
-#undef PCV_TC_CASE
-    default: return cudaErrorInvalidValue;
-  }
+  const bool ok = ta.tf32 ? launch_ks<true>(ta.KS, std::make_integer_sequence<int, 15>{}, gauss, ta.accurate != 0,
+                                           tm_x, tm_hi, tm_lo, pb, a, ta, smem, st)
+                          : launch_ks<false>(ta.KS, std::make_integer_sequence<int, 9>{}, gauss, ta.accurate != 0,
+                                             tm_x, tm_hi, tm_lo, pb, a, ta, smem, st);
+  if (!ok) return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

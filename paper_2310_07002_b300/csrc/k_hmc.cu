@@ -14,6 +14,13 @@
 
 namespace pcv {
 
+// FP32 rounded to TF32 (nearest, ties away from zero)
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
 // ---------------------------------------------------------------------------
 // k_begin: one warp per chain
 // ---------------------------------------------------------------------------
@@ -64,6 +71,8 @@ __global__ void __launch_bounds__(256) k_begin(BeginArgs a) {
       const float tn = th[j] + eps * mv * rh;
       a.r[(size_t)c * a.ld + j] = rh;
       a.theta_p[(size_t)c * a.ld + j] = tn;
+      if (a.shadow32 && j < a.shadow_d)      // TF32 form of the tensor-core operand
+        a.shadow32[(size_t)c * a.ld_shadow + j] = to_tf32(0.5f * (tn - a.theta_ref[j]));
       if (a.shadow_hi && j < a.shadow_d) {   // bf16 hi + lo of theta / 2 (tensor-core operand)
         const float half = 0.5f * (tn - a.theta_ref[j]);
         const __nv_bfloat16 hi = __float2bfloat16_rn(half);
@@ -566,6 +575,54 @@ __global__ void k_eta_fold(int N_pad, int p, int KP, const float *eta_half, cons
 }
 // the constant 1 of the eta_ref columns in a chain set's hi shadow (the lo
 // shadow keeps 0 there, so launches that add hi and lo count it once)
+// ---- the TF32 operand form of the tensor-core path: FP32 arrays whose
+// values are rounded to TF32 (to_tf32), as the MMAs read them
+// X [N_pad x KP] (logistic: rows signed by 2 y - 1) and X^T [PN x N_pad]
+__global__ void k_x_tf32(long long N, int p, int p_pad, int KP, int N_pad, const float *X, const float *ysign,
+                         float *X32, float *XT32) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * p) return;
+  const long long r = t / p;
+  const int j = (int)(t - r * p);
+  const float v = X[r * p_pad + j];
+  const float x = to_tf32(ysign && ysign[r] == 0.0f ? -v : v);
+  X32[r * KP + j] = x;
+  XT32[(size_t)j * N_pad + r] = x;
+}
+__global__ void k_eta_ref32(int N, int N_pad, int p, int KP, const float *X32, const float *theta_ref,
+                            float *eta_half) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N_pad) return;
+  double s = 0.0;
+  if (n < N)
+    for (int j = 0; j < p; ++j) s += (double)X32[(size_t)n * KP + j] * (double)theta_ref[j];
+  eta_half[n] = (float)(0.5 * s);
+}
+// eta_ref / 2 (Gaussian: (eta_ref - y) / 2) as three TF32 parts
+__global__ void k_eta_fold32(int N_pad, int p, int KP, const float *eta_half, const float *y, float *X32) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N_pad) return;
+  float rest = y ? eta_half[n] - 0.5f * y[n] : eta_half[n];
+#pragma unroll
+  for (int k = 0; k < kEtaCols; ++k) {
+    const float part = to_tf32(rest);
+    X32[(size_t)n * KP + p + k] = part;
+    rest -= part;
+  }
+}
+__global__ void k_shadow32(int C, int d, int ld, const float *theta, const float *theta_ref, float *s32, int ld_s) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)C * d) return;
+  const int c = (int)(t / d), j = (int)(t - (long long)c * d);
+  s32[(size_t)c * ld_s + j] = to_tf32(0.5f * (theta[(size_t)c * ld + j] - theta_ref[j]));
+}
+__global__ void k_shadow_ones32(int C_pad, int p, int KP, float *hi) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= C_pad * kEtaCols) return;
+  const int c = t / kEtaCols, k = t - c * kEtaCols;
+  hi[(size_t)c * KP + p + k] = 1.0f;
+}
+
 __global__ void k_shadow_ones(int C_pad, int p, int KP, __nv_bfloat16 *hi) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= C_pad * kEtaCols) return;

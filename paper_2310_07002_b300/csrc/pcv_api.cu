@@ -23,7 +23,7 @@
 #include "pcv_internal.cuh"
 
 namespace pcv {
-size_t tc_smem_bytes(int KP, int NS, int need_lo, int p);
+size_t tc_smem_bytes(int KP, int NS, int need_lo, int p, int tf32, int PN);
 int tc_max_stages();
 int tc_segments_per_tile(int T, int J, int n_cta);
 cudaError_t tc_prepare();
@@ -48,6 +48,7 @@ struct ChainBufs {
   int C_pad = 0;
   __nv_bfloat16 *shadow_hi = nullptr, *shadow_lo = nullptr;
   CUtensorMap tm_hi{}, tm_lo{};
+  float *shadow32 = nullptr;        // TF32 form: one FP32 shadow (TF32 values), map in tm_hi
 };
 
 enum CtxState { ST_CREATED = 0, ST_WARMED = 1, ST_SAMPLED = 2 };
@@ -94,7 +95,11 @@ struct pcv_ctx {
   int fd_n_adapt = 0;
   // tensor-core path
   bool tc = false;
+  bool tc32 = false;              // the tensor-core path with TF32 operands (64-row chunks)
   int KP = 0, KS = 0, PN = 0, N_pad = 0, J = 0, n_sm = 148;
+  int TN = 128;                   // rows per chunk of the tensor-core path
+  float *X32 = nullptr, *XT32 = nullptr;   // TF32 form: X [N_pad x KP] and X^T [PN x N_pad]
+  CUtensorMap tm_xt{};
   __nv_bfloat16 *X16 = nullptr;
   float *ycf = nullptr;           // tensor-core path: y per row (N_pad; folded into X16 for Gaussian models)
   CUtensorMap tm_x{};
@@ -260,8 +265,33 @@ bool encode_bf16_map(CUtensorMap *m, const void *base, int rows, int cols) {
   return r == CUDA_SUCCESS;
 }
 
+// 2-D FP32 tensor [rows x cols] row-major, boxes of box_rows x 32 columns
+// (128 bytes), 128-byte swizzle
+bool encode_f32_map(CUtensorMap *m, const void *base, int rows, int cols, int box_rows) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * 4};
+  cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 pcv_status alloc_shadows(pcv_ctx *x, ChainBufs &cb, int C) {
   cb.C_pad = (C + 127) / 128 * 128;
+  if (x->tc32) {
+    // TF32 form: one FP32 shadow, 1 in the eta_ref / 2 columns
+    if (!dalloc_n(x, &cb.shadow32, (size_t)cb.C_pad * x->KP)) return fail(x, PCV_E_OOM, "shadow allocation failed");
+    CK(cudaMemsetAsync(cb.shadow32, 0, sizeof(float) * (size_t)cb.C_pad * x->KP, x->stream));
+    if (!encode_f32_map(&cb.tm_hi, cb.shadow32, cb.C_pad, x->KP, 128))
+      return fail(x, PCV_E_CUDA, "cuTensorMapEncodeTiled failed for the parameter shadow");
+    k_shadow_ones32<<<(cb.C_pad * kEtaCols + 255) / 256, 256, 0, x->stream>>>(cb.C_pad, x->p, x->KP, cb.shadow32);
+    CK(cudaGetLastError());
+    return PCV_OK;
+  }
   if (!dalloc_n(x, &cb.shadow_hi, (size_t)cb.C_pad * x->KP) || !dalloc_n(x, &cb.shadow_lo, (size_t)cb.C_pad * x->KP))
     return fail(x, PCV_E_OOM, "shadow allocation failed");
   if (!encode_bf16_map(&cb.tm_hi, cb.shadow_hi, cb.C_pad, x->KP) ||
@@ -275,14 +305,14 @@ pcv_status alloc_shadows(pcv_ctx *x, ChainBufs &cb, int C) {
 
 int tc_max_fit_stages(const pcv_ctx *x, int need_lo) {
   for (int ns = tc_max_stages(); ns > 2; --ns)
-    if (tc_smem_bytes(x->KP, ns, need_lo, x->p) <= 227 * 1024) return ns;
+    if (tc_smem_bytes(x->KP, ns, need_lo, x->p, x->tc32 ? 1 : 0, x->PN) <= 227 * 1024) return ns;
   return 2;
 }
 
 TcArgs tc_args(pcv_ctx *x, int C, bool need_ll) {
   TcArgs t{};
   t.KP = x->KP; t.KS = x->KS; t.PN = x->PN; t.N_pad = x->N_pad; t.J = x->J;
-  t.T = (C + 127) / 128;
+  t.T = (C + 127) / 128;   // (the chain tiles; J = N_pad / TN chunks of rows)
   const long long U = (long long)t.T * t.J;
   t.n_cta = (int)std::min<long long>(x->n_sm, U);
   // the autotuner may choose one CTA per chain tile instead (no tile split
@@ -304,6 +334,8 @@ TcArgs tc_args(pcv_ctx *x, int C, bool need_ll) {
   t.ws = x->ws_tc;
   t.tickets = x->tickets_tc;
   t.err = &x->st->error;
+  t.tf32 = x->tc32 ? 1 : 0;
+  if (x->tc32) t.need_lo = 0;       // one TF32 part (centred)
   return t;
 }
 
@@ -361,7 +393,9 @@ pcv_status launch_grad(pcv_ctx *x, GradArgs a, const ChainBufs *cb = nullptr) {
     pcv_status s = ensure_ws_tc(x, a.C);
     if (s != PCV_OK) return s;
     TcArgs t = tc_args(x, a.C, a.need_ll != 0);
-    CK(launch_grad_tc(x->tm_x, cb->tm_hi, cb->tm_lo, x->pb, a, t, x->stream));
+    t.shadow32 = cb->shadow32;
+    // TF32 form: the X^T map goes where the bf16 form's lo shadow map goes
+    CK(launch_grad_tc(x->tm_x, cb->tm_hi, x->tc32 ? x->tm_xt : cb->tm_lo, x->pb, a, t, x->stream));
     return PCV_OK;
   }
   pcv_status s = ensure_ws(x, a.C, a.splits);
@@ -430,8 +464,9 @@ pcv_status launch_proposal(pcv_ctx *x, ChainBufs &cb, bool fd, const float *r_gi
   ba.eps_iter = &x->st->eps_iter;
   ba.chain_base = fd ? 0 : x->chain_base;
   ba.r_given = r_given;
-  ba.shadow_hi = x->tc ? cb.shadow_hi : nullptr;
-  ba.shadow_lo = x->tc ? cb.shadow_lo : nullptr;
+  ba.shadow_hi = x->tc && !x->tc32 ? cb.shadow_hi : nullptr;
+  ba.shadow_lo = x->tc && !x->tc32 ? cb.shadow_lo : nullptr;
+  ba.shadow32 = x->tc32 ? cb.shadow32 : nullptr;
   ba.ld_shadow = x->KP;
   ba.shadow_d = x->p;
   ba.theta_ref = x->theta_ref;
@@ -572,6 +607,12 @@ pcv_status write_shadow(pcv_ctx *x, ChainBufs &cb, const float *theta, int ld) {
   if (!x->tc) return PCV_OK;
   const long long T = (long long)cb.C * x->p;
   // beta only: a log sigma coordinate has no tensor-core operand column
+  if (x->tc32) {
+    k_shadow32<<<(unsigned)((T + 255) / 256), 256, 0, x->stream>>>(cb.C, x->p, ld, theta, x->theta_ref, cb.shadow32,
+                                                                  x->KP);
+    CK(cudaGetLastError());
+    return PCV_OK;
+  }
   k_shadow<<<(unsigned)((T + 255) / 256), 256, 0, x->stream>>>(cb.C, x->p, ld, theta, x->theta_ref, cb.shadow_hi,
                                                               cb.shadow_lo, x->KP);
   CK(cudaGetLastError());
@@ -580,6 +621,12 @@ pcv_status write_shadow(pcv_ctx *x, ChainBufs &cb, const float *theta, int ld) {
 
 // eta_ref / 2 (eta_half) into the operand columns of the bf16 design matrix
 pcv_status fold_eta(pcv_ctx *x) {
+  if (x->tc32) {
+    k_eta_fold32<<<(x->N_pad + 255) / 256, 256, 0, x->stream>>>(x->N_pad, x->p, x->KP, x->eta_half,
+                                                               x->kind == PCV_LOGISTIC ? nullptr : x->ycf, x->X32);
+    CK(cudaGetLastError());
+    return PCV_OK;
+  }
   // Gaussian models fold -y / 2 into the same columns (zero-padded y)
   k_eta_fold<<<(x->N_pad + 255) / 256, 256, 0, x->stream>>>(x->N_pad, x->p, x->KP, x->eta_half,
                                                            x->kind == PCV_LOGISTIC ? nullptr : x->ycf, x->X16);
@@ -592,6 +639,10 @@ pcv_status set_reference(pcv_ctx *x, const float *src, int n, int ld) {
   if (!x->tc) return PCV_OK;
   k_theta_ref<<<(x->d + 127) / 128, 128, 0, x->stream>>>(n, x->d, ld, src, x->theta_ref);
   CK(cudaGetLastError());
+  if (x->tc32)
+    k_eta_ref32<<<(x->N_pad + 255) / 256, 256, 0, x->stream>>>((int)x->N, x->N_pad, x->p, x->KP, x->X32,
+                                                              x->theta_ref, x->eta_half);
+  else
   k_eta_ref<<<(x->N_pad + 255) / 256, 256, 0, x->stream>>>((int)x->N, x->N_pad, x->p, x->KP, x->X16, x->theta_ref,
                                                           x->eta_half);
   CK(cudaGetLastError());
@@ -879,10 +930,13 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
     return s;
   };
   if (opt->precision < PCV_FP32_SIMT || opt->precision > PCV_BF16) return bail(PCV_E_INVALID_ARG, "bad precision");
-  x->tc = opt->precision == PCV_BF16;
-  x->tf32 = opt->precision == PCV_TF32;
-  if (x->tf32 && (model->kind == PCV_HIER_GAUSS || p > 112))
-    return bail(PCV_E_UNSUPPORTED, "the TF32 path covers the flat models with p <= 112");
+  // BF16 and TF32 run on the tensor-core path (tcgen05), TF32 with 32-bit
+  // operands
+  x->tc = opt->precision == PCV_BF16 || opt->precision == PCV_TF32;
+  x->tc32 = opt->precision == PCV_TF32;
+  x->tf32 = false;
+  if (x->tc32 && (model->kind == PCV_HIER_GAUSS || p > 112))
+    return bail(PCV_E_UNSUPPORTED, "the TF32 path covers the flat models (logistic, Gaussian linear, AR) with p <= 112");
   if (x->tc && (model->kind == PCV_HIER_GAUSS || p > 128))
     return bail(PCV_E_UNSUPPORTED, "the BF16 tensor-core path covers the flat models (logistic, Gaussian linear, "
                                    "AR) with p <= 128");
@@ -906,11 +960,14 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
   x->p_pad = PP > 0 ? PP : (p + 3) / 4 * 4;
   if (x->tc) {
     // the first GEMM's K covers the p covariates and the eta_ref / 2 columns
-    x->KS = (p + kEtaCols + 15) / 16;
-    x->KP = (16 * x->KS + 63) / 64 * 64;
+    // (K steps of 16 bf16 or 8 TF32 values; 128-byte K atoms of 64 or 32)
+    const int kstep = x->tc32 ? 8 : 16, atom = x->tc32 ? 32 : 64;
+    x->TN = x->tc32 ? 64 : 128;
+    x->KS = (p + kEtaCols + kstep - 1) / kstep;
+    x->KP = (kstep * x->KS + atom - 1) / atom * atom;
     x->PN = 16 * ((p + 15) / 16);
-    x->N_pad = (int)((N + 127) / 128 * 128);
-    x->J = x->N_pad / 128;
+    x->N_pad = (int)((N + x->TN - 1) / x->TN * x->TN);
+    x->J = x->N_pad / x->TN;
   }
   x->d_pad = (x->d + 3) / 4 * 4;
 
@@ -1050,20 +1107,30 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
   cudaMemcpyAsync(x->y, hy.data(), hy.size() * sizeof(float), cudaMemcpyHostToDevice, x->stream);
   cudaMemcpyAsync(x->folds, fds.data(), fds.size() * sizeof(FoldDesc), cudaMemcpyHostToDevice, x->stream);
   if (x->tc) {
-    // bf16 design matrix [N_pad x KP] (round to nearest even; padding rows
-    // and columns stay 0) and y on the device (zero-padded), which the
-    // Gaussian models fold into the eta_ref columns
+    // the operand copy of the design matrix: bf16 [N_pad x KP] (round to
+    // nearest even), or for the TF32 form X [N_pad x KP] and X^T [PN x N_pad]
+    // rounded to TF32; padding rows and columns stay 0.  y on the device
+    // (zero-padded), which the Gaussian models fold into the eta_ref columns
     std::vector<float> hyc((size_t)x->N_pad, 0.0f);
     for (int64_t r = 0; r < N; ++r) hyc[r] = hy[r];
-    if (!dalloc_n(x, &x->X16, (size_t)x->N_pad * x->KP) || !dalloc_n(x, &x->ycf, hyc.size()) ||
-        !dalloc_n(x, &x->theta_ref, (size_t)x->d_pad) ||
+    if (!dalloc_n(x, &x->ycf, hyc.size()) || !dalloc_n(x, &x->theta_ref, (size_t)x->d_pad) ||
         !dalloc_n(x, &x->eta_half, (size_t)x->N_pad))
       return bail(PCV_E_OOM, "device allocation failed");
     const long long items = (long long)N * p;
     // logistic model: rows signed by 2 y - 1 (the kernel's residual and log
     // likelihood are written for that form)
-    k_x_bf16<<<(unsigned)((items + 255) / 256), 256, 0, x->stream>>>(
-        N, p, x->p_pad, x->KP, x->X, x->kind == PCV_LOGISTIC ? x->y : nullptr, x->X16);
+    const float *ysign = x->kind == PCV_LOGISTIC ? x->y : nullptr;
+    if (x->tc32) {
+      if (!dalloc_n(x, &x->X32, (size_t)x->N_pad * x->KP) || !dalloc_n(x, &x->XT32, (size_t)x->PN * x->N_pad))
+        return bail(PCV_E_OOM, "device allocation failed");
+      cudaMemsetAsync(x->X32, 0, sizeof(float) * (size_t)x->N_pad * x->KP, x->stream);
+      cudaMemsetAsync(x->XT32, 0, sizeof(float) * (size_t)x->PN * x->N_pad, x->stream);
+      k_x_tf32<<<(unsigned)((items + 255) / 256), 256, 0, x->stream>>>(N, p, x->p_pad, x->KP, x->N_pad, x->X, ysign,
+                                                                        x->X32, x->XT32);
+    } else {
+      if (!dalloc_n(x, &x->X16, (size_t)x->N_pad * x->KP)) return bail(PCV_E_OOM, "device allocation failed");
+      k_x_bf16<<<(unsigned)((items + 255) / 256), 256, 0, x->stream>>>(N, p, x->p_pad, x->KP, x->X, ysign, x->X16);
+    }
     cudaMemcpyAsync(x->ycf, hyc.data(), hyc.size() * sizeof(float), cudaMemcpyHostToDevice, x->stream);
     // no reference yet (eta_ref = 0): the folded columns hold -y / 2
     // (Gaussian models) or 0
@@ -1071,7 +1138,9 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
     if (fold_eta(x) != PCV_OK) return bail(PCV_E_CUDA, "upload failed");
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(x->stream) != cudaSuccess)
       return bail(PCV_E_CUDA, "upload failed");
-    if (!encode_bf16_map(&x->tm_x, x->X16, x->N_pad, x->KP))
+    if (x->tc32 ? !(encode_f32_map(&x->tm_x, x->X32, x->N_pad, x->KP, 64) &&
+                    encode_f32_map(&x->tm_xt, x->XT32, x->PN, x->N_pad, x->PN))
+                : !encode_bf16_map(&x->tm_x, x->X16, x->N_pad, x->KP))
       return bail(PCV_E_CUDA, "cuTensorMapEncodeTiled failed for X");
     if (tc_prepare() != cudaSuccess) return bail(PCV_E_CUDA, "cudaFuncSetAttribute failed");
     int dev = 0;
@@ -1126,8 +1195,8 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
 
   // whole trajectories in one launch for the flat models with p <= 32 (FP32
   // and the BF16 form, which reads a bf16 copy of X)
-  x->traj_ok = opt->fused_trajectory != 0 && !x->tf32 && traj_small_supported(pb);
-  if (x->traj_ok && x->tc) {
+  x->traj_ok = opt->fused_trajectory != 0 && !x->tc32 && traj_small_supported(pb);
+  if (x->traj_ok && x->tc) {   // (the BF16 form)
     const int PP = traj_small_row_width(p);
     const size_t n16 = ((size_t)N * PP + 7) / 8 * 8;     // whole 16-byte units (the kernel copies by 16 bytes)
     if (!dalloc_n(x, &x->X16c, n16)) return bail(PCV_E_OOM, "device allocation failed");
@@ -1468,7 +1537,7 @@ pcv_status pcv_log_density(pcv_ctx *x, const float *theta, const int32_t *fold, 
                            double *logp, float *grad, double *shat) {
   if (!x) return PCV_E_INVALID_ARG;
   if (!theta || !fold || !logp || !grad || !shat || n < 1) return fail(x, PCV_E_INVALID_ARG, "bad argument");
-  if (precision != (x->tc ? PCV_BF16 : x->tf32 ? PCV_TF32 : PCV_FP32_SIMT))
+  if (precision != x->opt.precision)
     return fail(x, PCV_E_UNSUPPORTED, "precision not available for this context");
   enter(x);
   ChainBufs cb;
@@ -1480,6 +1549,7 @@ pcv_status pcv_log_density(pcv_ctx *x, const float *theta, const int32_t *fold, 
       x->ld_cap = x->ld_cb.C_pad;
     }
     cb.C_pad = x->ld_cb.C_pad; cb.shadow_hi = x->ld_cb.shadow_hi; cb.shadow_lo = x->ld_cb.shadow_lo;
+    cb.shadow32 = x->ld_cb.shadow32;
     cb.tm_hi = x->ld_cb.tm_hi; cb.tm_lo = x->ld_cb.tm_lo;
     pcv_status s0 = write_shadow(x, cb, theta, x->d);
     if (s0 != PCV_OK) return s0;
@@ -1502,7 +1572,7 @@ pcv_status pcv_trajectory(pcv_ctx *x, const float *theta0, const float *r0, int3
                           float *r1, double *logp1, double *shat1) {
   if (!x) return PCV_E_INVALID_ARG;
   if (!theta0 || !r0 || !theta1 || !r1 || !logp1 || !shat1) return fail(x, PCV_E_INVALID_ARG, "null argument");
-  if (precision != (x->tc ? PCV_BF16 : x->tf32 ? PCV_TF32 : PCV_FP32_SIMT))
+  if (precision != x->opt.precision)
     return fail(x, PCV_E_UNSUPPORTED, "precision not available for this context");
   enter(x);
   if (!x->traj_cb.theta) {

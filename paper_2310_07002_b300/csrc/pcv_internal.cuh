@@ -213,6 +213,8 @@ struct TcArgs {
   float *ws;              // T x max_seg x (PN + kTcSlots) x 128
   unsigned int *tickets;  // T
   unsigned int *err;      // error flags (bit 0: wait time-out)
+  int tf32;               // TF32 operands (kind::tf32, 64-row chunks, X^T for the second GEMM)
+  float *shadow32;        // TF32 path: (theta - theta_ref) / 2 rounded to TF32 [C_pad x KP]
 };
 
 // launchers (k_grad_simt.cu)
@@ -243,6 +245,7 @@ struct BeginArgs {
   float *eps_iter;              // out (written by block 0): the step size of this iteration
   const float *r_given;         // optional start momenta instead of drawing (C x ld)
   __nv_bfloat16 *shadow_hi, *shadow_lo;
+  float *shadow32;              // TF32 form: (theta_p - theta_ref) / 2 rounded to TF32
   int ld_shadow;
   int shadow_d;                 // leading coordinates with a shadow (beta: p)
   const float *theta_ref;       // shadows hold (theta_p - theta_ref) / 2
@@ -360,6 +363,13 @@ __global__ void k_gather_rows(long long N, int p, int p_pad, const int *perm, co
 __global__ void k_x_bf16(long long N, int p, int p_pad, int KP, const float *X, const float *ysign,
                          __nv_bfloat16 *X16);
 __global__ void k_shadow_ones(int C_pad, int p, int KP, __nv_bfloat16 *hi);
+__global__ void k_x_tf32(long long N, int p, int p_pad, int KP, int N_pad, const float *X, const float *ysign,
+                         float *X32, float *XT32);
+__global__ void k_eta_ref32(int N, int N_pad, int p, int KP, const float *X32, const float *theta_ref,
+                            float *eta_half);
+__global__ void k_eta_fold32(int N_pad, int p, int KP, const float *eta_half, const float *y, float *X32);
+__global__ void k_shadow32(int C, int d, int ld, const float *theta, const float *theta_ref, float *s32, int ld_s);
+__global__ void k_shadow_ones32(int C_pad, int p, int KP, float *hi);
 // k_begin: a chain takes this many lanes (the power of two that covers its
 // ceil(d/4) coordinate quads, at most 32), so small models pack 32 / that
 // many chains per warp; 8 warps per block

@@ -86,3 +86,51 @@ def test_every_mma_group_length(torch, orc, p):
         ref_th, ref_r, _, _, _ = orc.trajectory(prob, k, np.float32(eps), w.leapfrog_steps, minv, a0[c], b0[c], g0)
         assert rel_vec(th1[c], ref_th) <= 2e-2 and rel_vec(r1[c], ref_r) <= 2e-2, (p, c)
     pc.close()
+
+
+PS_TF32 = [5, 13, 21, 29, 37, 45, 53, 61, 69, 77, 85, 93, 101, 109, 112]
+
+
+@pytest.mark.parametrize("p", PS_TF32)
+def test_every_tf32_mma_group_length(torch, orc, p):
+    # the TF32 form: K steps of 8, KS = ceil((p + 3) / 8) = 1 .. 15, 64-row
+    # chunks; log density and gradient of 300 positions and a trajectory of
+    # centred chains, at the TF32 tolerances (log density 1e-3, gradient
+    # 1e-2, trajectory 2e-2)
+    from paper_2310_07002_b300.pcv import PCV, TF32
+    assert -(-(p + 3) // 8) == PS_TF32.index(p) + 1
+    w = workload(p)
+    prob = orc.problem_from_workload(w)
+    scale = 0.3 if p <= 32 else 0.1
+    pc = PCV.from_workload(w, precision=TF32)
+    n = 300
+    tt = torch.tensor(W.random_theta(w.dim, n, scale=scale, seed=70 + p), dtype=torch.float32, device="cuda")
+    folds = np.arange(n) % (w.K + 1)
+    lp, g, _ = pc.log_density(tt, torch.tensor(folds, dtype=torch.int32, device="cuda"), TF32)
+    torch.cuda.synchronize()
+    lp, g = lp.cpu().numpy(), g.cpu().double().numpy()
+    th = tt.cpu().double().numpy()
+    for i in range(0, n, 3):
+        k = int(folds[i])
+        rl, rg, _ = orc.log_density(prob, -1 if k == w.K else k, th[i])
+        assert rel_scalar(lp[i], rl) <= 1e-3, (p, i, lp[i], rl)
+        assert rel_vec(g[i], rg) <= 1e-2, (p, i, rel_vec(g[i], rg))
+    pc.close()
+    eps = 0.01 if p <= 32 else 0.004
+    minv = np.ones(w.dim)
+    pc = PCV.from_workload(w, precision=TF32, step_size=eps, inv_mass_diag=minv)
+    gen = np.random.Generator(np.random.Philox(p + 1000))
+    th0 = w.truth["beta"][None, :] + (0.1 if p <= 32 else 0.03) * gen.standard_normal((w.n_chains, w.dim))
+    pc.set_positions(th0, step_size=eps)
+    r0 = gen.standard_normal((w.n_chains, w.dim))
+    t0 = torch.tensor(th0, dtype=torch.float32, device="cuda")
+    rr0 = torch.tensor(r0, dtype=torch.float32, device="cuda")
+    th1, r1, _, _ = pc.trajectory(t0, rr0, TF32)
+    th1, r1 = th1.cpu().double().numpy(), r1.cpu().double().numpy()
+    a0, b0 = t0.cpu().double().numpy(), rr0.cpu().double().numpy()
+    for c in range(0, w.n_chains, max(1, w.n_chains // 12)):
+        k = c // w.chains_per_fold
+        _, g0, _ = orc.log_density(prob, k, a0[c])
+        ref_th, ref_r, _, _, _ = orc.trajectory(prob, k, np.float32(eps), w.leapfrog_steps, minv, a0[c], b0[c], g0)
+        assert rel_vec(th1[c], ref_th) <= 2e-2 and rel_vec(r1[c], ref_r) <= 2e-2, (p, c)
+    pc.close()

@@ -1,4 +1,4 @@
-"""GPU parity of the TF32 rung (tensor cores through mma.sync m16n8k8: theta,
+"""GPU parity of the TF32 rung (tcgen05 kind::tf32 tensor cores: theta,
 X and the residual rounded to TF32, FP32 accumulation) against the FP64
 oracle, through the C ABI.  TF32 keeps 10 mantissa bits, so the tolerances
 are those of a reduced-precision form (stated and asserted here):
