@@ -104,14 +104,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   // compiler keeps shared-memory loads for y)
   uint8_t *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const int KA = ta.KP / AE;                       // 128-byte K atoms
-  const uint32_t th_bytes = (uint32_t)KA * kTM * 128;
-  const uint32_t xk_bytes = (uint32_t)KA * TN * 128;            // K-major X chunk
-  const uint32_t x_bytes = xk_bytes + (TF ? 2u * ta.PN * 128u : 0u);   // + X^T chunk (TF)
-  const int NS = ta.NS;
+  // theta in shared memory (the TF32 form keeps it in TMEM instead)
+  const uint32_t th_bytes = TF ? 0u : (uint32_t)KA * kTM * 128;
+  const uint32_t x_bytes = (uint32_t)KA * TN * 128;             // K-major X chunk
+  // TF32: the chunk's X^T (two 32-row column blocks of PN feature rows) in a
+  // ring of its own, so that an X slot is free again once the first GEMM is
+  // done with it while the X^T slot waits for the epilogue and second GEMM
+  const uint32_t xt_bytes = TF ? 2u * ta.PN * 128u : 0u;
+  const int NS = ta.NS, NT = TF ? ta.NT : 0;
   uint8_t *th_hi = sm;
   uint8_t *th_lo = th_hi + th_bytes;
   uint8_t *xs = th_lo + (ta.need_lo ? th_bytes : 0);
-  uint64_t *bars = reinterpret_cast<uint64_t *>(xs + (size_t)NS * x_bytes + 64);
+  uint8_t *xts = xs + (size_t)NS * x_bytes;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(xts + (size_t)NT * xt_bytes + 64);
   // barrier slots (up to kTcMaxStages X stages)
   uint64_t *x_full = bars, *x_empty = bars + kTcMaxStages;
   // r_part[4 b + h], h < 2: half h (64 rows) of R buffer b is in TMEM, so the
@@ -124,6 +129,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   volatile int *abort_flag = reinterpret_cast<volatile int *>(s_full + 19);
   volatile int *last_flag = reinterpret_cast<volatile int *>(s_full + 20);
   uint64_t *flush_bar = s_full + 21, *decide_bar = s_full + 22;   // epilogue-internal sync
+  uint64_t *xt_full = s_full + 24, *xt_empty = xt_full + kTcMaxStages;   // X^T ring (TF32)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long U = (long long)ta.T * ta.J;
@@ -133,18 +139,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) { mbar_init(smem_u32(&x_full[s]), 1); mbar_init(smem_u32(&x_empty[s]), 1); }
+    for (int s = 0; s < NT; ++s) { mbar_init(smem_u32(&xt_full[s]), 1); mbar_init(smem_u32(&xt_empty[s]), 1); }
     for (int s = 0; s < 2; ++s) {
       mbar_init(smem_u32(&s_full[s]), 1); mbar_init(smem_u32(&s_empty[s]), 4);
       for (int qq = 0; qq < 2; ++qq) mbar_init(smem_u32(&r_part[4 * s + qq]), 4);
       mbar_init(smem_u32(&r_empty[s]), 1);
     }
-    mbar_init(smem_u32(th_full), 1); mbar_init(smem_u32(th_empty), 1);
+    // th_full: the TMA load of theta (bf16), or the eight epilogue warps'
+    // TMEM stores of it (TF32)
+    mbar_init(smem_u32(th_full), TF ? 8 : 1); mbar_init(smem_u32(th_empty), 1);
     mbar_init(smem_u32(g_full), 1); mbar_init(smem_u32(g_empty), 4);
     mbar_init(smem_u32(flush_bar), 8); mbar_init(smem_u32(decide_bar), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) {   // TMEM: S[0] 0-127, S[1] 128-255, G 256-383, R[0] 384-447, R[1] 448-511
+  // TMEM, bf16: S[0] 0-127, S[1] 128-255, G 256-383, R[0] 384-447, R[1] 448-511;
+  // TF32: S[0] 0-63, S[1] 64-127, G 128-255, R[0] 256-319, R[1] 320-383,
+  // theta 384-511 (the first GEMM's A operand, K steps of 8 columns)
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_base_slot)),
                  "r"(512)
                  : "memory");
@@ -159,6 +171,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   // bf16x2, or 64 rows as TF32) after G
   const uint32_t tmem_G = tmem + 2 * TN;
   const uint32_t tmem_R = tmem_G + 128;
+  const uint32_t tmem_T = tmem_R + 128;            // TF32 only
 
   if (warp < 4) {
   // register split: warpgroup 0 (producers) gives registers up ...
@@ -173,7 +186,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int i = 0; i < nunits; ++i) {
         const long long u = u0 + i;
         const int t = (int)(u / ta.J), j = (int)(u - (long long)t * ta.J);
-        if (i == 0 || j == 0) {
+        if (!TF && (i == 0 || j == 0)) {
           if (!mbar_wait_fast(smem_u32(th_empty), (seg & 1) ^ 1, abort_flag, ta.err)) break;
           mbar_expect_tx(smem_u32(th_full), th_bytes * (ta.need_lo ? 2 : 1));
           for (int kb = 0; kb < KA; ++kb) {
@@ -190,12 +203,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         uint8_t *xb = xs + (size_t)st * x_bytes;
         for (int kb = 0; kb < KA; ++kb)
           tma_load_2d(smem_u32(xb + kb * TN * 128), &tm_x, kb * AE, j * TN, smem_u32(&x_full[st]));
-        if constexpr (TF) {
-          // X^T of the chunk: two 32-row column blocks of PN feature rows
-          for (int h = 0; h < 2; ++h)
-            tma_load_2d(smem_u32(xb + xk_bytes + h * ta.PN * 128), &tm_lo, j * TN + 32 * h, 0,
-                        smem_u32(&x_full[st]));
-        }
         last_round[st] = rnd;
       }
       // on abort: let copies already issued land before the CTA exits
@@ -232,7 +239,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           // K step ks: 32 bytes into 128-byte atom ks / 4 (16 bf16 or 8 TF32)
           const uint64_t off = (uint64_t)((((ks >> 2) * kTM * 128) + (ks & 3) * 32) >> 4);
           const uint64_t offx = (uint64_t)((((ks >> 2) * TN * 128) + (ks & 3) * 32) >> 4);
-          if constexpr (TF) tc_mma_tf32(dS, hd0 + off, xd0 + offx, id1, ks > 0 ? 1u : 0u);
+          if constexpr (TF) tc_mma_tf32_ta(dS, tmem_T + 8 * ks, xd0 + offx, id1, ks > 0 ? 1u : 0u);
           else tc_mma_bf16(dS, hd0 + off, xd0 + offx, id1, ks > 0 ? 1u : 0u);
         }
         if (!TF && ta.need_lo) {
@@ -244,6 +251,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           }
         }
         tc_commit(smem_u32(&s_full[sb]));
+        if constexpr (TF) tc_commit(smem_u32(&x_empty[st]));   // X slot read: free it
         if (last) { tc_commit(smem_u32(th_empty)); ++seg1; }
         if (++j == ta.J) j = 0;
         if (++st == NS) { st = 0; xph ^= 1; }
@@ -255,12 +263,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // of R as the epilogue produces it.
     if (lane == 0) {
       const uint32_t id2 = TF ? idesc_tf32(kTM, ta.PN) : idesc_bf16(kTM, ta.PN, true);
-      // bf16: X chunk as the MN-major B operand; TF: X^T chunk, K-major
-      const uint64_t xd_mn = TF ? sdesc_sw128(smem_u32(xs) + xk_bytes, 16, 1024)
+      // bf16: X chunk as the MN-major B operand; TF: X^T chunk, K-major, from
+      // its own ring
+      const uint64_t xd_mn = TF ? sdesc_sw128(smem_u32(xts), 16, 1024)
                                 : sdesc_sw128(smem_u32(xs), kTN * 128, 1024);
-      const uint64_t x_step = (uint64_t)(x_bytes >> 4);
+      const uint64_t x_step = (uint64_t)((TF ? xt_bytes : x_bytes) >> 4);
+      const int nring = TF ? NT : NS;
       int j = (int)(u0 % ta.J);
-      int seg2 = 0, st = 0;
+      int seg2 = 0, st = 0, tph = 0;
       for (int i = 0; i < nunits; ++i) {
         const bool first = (i == 0 || j == 0);
         const bool last = (i == nunits - 1 || j == ta.J - 1);
@@ -272,6 +282,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int qq = 0; qq < 2 && ok; ++qq) {
           ok = mbar_wait_fast(smem_u32(&r_part[4 * rb + qq]), (i >> 1) & 1, abort_flag, ta.err);
           if (ok && qq == 0 && first) ok = mbar_wait_fast(smem_u32(g_empty), (seg2 & 1) ^ 1, abort_flag, ta.err);
+          if (TF && ok && qq == 0) ok = mbar_wait_fast(smem_u32(&xt_full[st]), tph, abort_flag, ta.err);
           if (!ok) break;
           tc_fence_after();
 #pragma unroll
@@ -288,11 +299,35 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         if (!ok) break;
         tc_commit(smem_u32(&r_empty[rb]));
-        tc_commit(smem_u32(&x_empty[st]));
+        tc_commit(smem_u32(TF ? &xt_empty[st] : &x_empty[st]));
         if (last) { tc_commit(smem_u32(g_full)); ++seg2; }
         if (++j == ta.J) j = 0;
-        if (++st == NS) st = 0;
+        if (++st == nring) { st = 0; tph ^= 1; }
       }
+    }
+  } else if (warp == 3) {
+    // ---------------------------- TMA producer, X^T ------------------------
+    // (TF32 form only; idle otherwise)
+    if (TF && lane == 0) {
+      int last_round[kTcMaxStages];
+#pragma unroll
+      for (int s2 = 0; s2 < kTcMaxStages; ++s2) last_round[s2] = -1;
+      int j = (int)(u0 % ta.J);
+      const int nt = TF ? NT : 1;
+      for (int i = 0; i < nunits; ++i) {
+        const int st = i % nt, rnd = i / nt;
+        if (!mbar_wait_fast(smem_u32(&xt_empty[st]), (rnd & 1) ^ 1, abort_flag, ta.err)) break;
+        mbar_expect_tx(smem_u32(&xt_full[st]), xt_bytes);
+        uint8_t *xb = xts + (size_t)st * xt_bytes;
+        // X^T of the chunk: two 32-row column blocks of PN feature rows
+        for (int h = 0; h < 2; ++h)
+          tma_load_2d(smem_u32(xb + h * ta.PN * 128), &tm_lo, j * TN + 32 * h, 0, smem_u32(&xt_full[st]));
+        last_round[st] = rnd;
+        if (++j == ta.J) j = 0;
+      }
+      if (*abort_flag)
+        for (int s = 0; s < NT; ++s)
+          if (last_round[s] >= 0) mbar_wait_quiet(smem_u32(&xt_full[s]), last_round[s] & 1);
     }
   }
   } else {
@@ -310,8 +345,38 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int sb = eg, rb = eg;                     // this group's S and R buffers
     int nseg_done = 0;
     bool aborted = false;
+    // TF32 form: theta of chain tile tt as the first GEMM's A operand in
+    // TMEM, written by the epilogue warps from the shadow array (row m of
+    // the tile in TMEM lane m; group eg writes the K steps of its parity).
+    // Segment sgi's theta may be written once the first GEMMs of segment
+    // sgi - 1 have completed (th_empty); the first GEMM waits for all eight
+    // warps (th_full).  Tile rows up to the padded chain count are
+    // allocated, so the loads stay in bounds.
+    auto theta_to_tmem = [&](const int tt, const int sgi) -> bool {
+      if (!warp_wait(smem_u32(th_empty), (sgi & 1) ^ 1, abort_flag, ta.err)) return false;
+      tc_fence_after();
+      const float *row = ta.shadow32 + ((size_t)tt * kTM + m) * (size_t)ta.KP;
+#pragma unroll
+      for (int ks = eg; ks < KS; ks += 2) {
+        const float4 lo4 = __ldcg(reinterpret_cast<const float4 *>(row + 8 * ks));
+        const float4 hi4 = __ldcg(reinterpret_cast<const float4 *>(row + 8 * ks + 4));
+        uint32_t v[8] = {__float_as_uint(lo4.x), __float_as_uint(lo4.y), __float_as_uint(lo4.z),
+                         __float_as_uint(lo4.w), __float_as_uint(hi4.x), __float_as_uint(hi4.y),
+                         __float_as_uint(hi4.z), __float_as_uint(hi4.w)};
+        PCV_TMEM_ST8(tmem_T + 8 * ks + lane_off, v);
+        tmem_wait_st();
+        tmem_fence_regs(v);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(th_full));
+      return true;
+    };
     // walk the CTA's segments (maximal runs of units in one tile)
     int t = (int)(u0 / ta.J), j0 = (int)(u0 - (long long)t * ta.J);
+    if constexpr (TF) {
+      if (nunits > 0 && !theta_to_tmem(t, 0)) aborted = true;
+    }
     for (int ib = 0; ib < nunits && !aborted; ) {
       const int ie = min(nunits, ib + (ta.J - j0));   // segment [ib, ie)
       const int c = t * kTM + m;
@@ -564,6 +629,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         tmem_fence_regs(p3);
       }
       if (aborted) break;
+      // TF32: the next segment's theta (tile t + 1) goes to TMEM before this
+      // segment's finish, so that its first GEMMs need not wait for it
+      if constexpr (TF) {
+        if (ie < nunits && !theta_to_tmem(t + 1, nseg_done + 1)) break;
+      }
       // ---- segment end (both groups): the group that owns the segment's
       // last unit flushes this tile's G partial; both write their ll sums
       const int owner = (ie - 1) & 1;
@@ -810,17 +880,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-size_t tc_smem_bytes(int KP, int NS, int need_lo, int p, int tf32, int PN) {
+size_t tc_smem_bytes(int KP, int NS, int NT, int need_lo, int p, int tf32, int PN) {
   (void)p;
   size_t b;
-  if (tf32) {   // theta hi; per stage the 64-row X chunk and its X^T (2 x PN rows of 128 B)
+  if (tf32) {   // NS 64-row X chunks and NT X^T chunks (2 x PN rows of 128 B); theta is in TMEM
     const size_t KA = KP / 32;
-    b = KA * kTM * 128 + (size_t)NS * (KA * 64 * 128 + 2 * (size_t)PN * 128);
+    b = (size_t)NS * KA * 64 * 128 + (size_t)NT * 2 * PN * 128;
   } else {
     const size_t KA = KP / 64;
     b = KA * kTM * 128 * (need_lo ? 2 : 1) + (size_t)NS * KA * kTN * 128;
   }
-  b += 64 + (2 * kTcMaxStages + 23) * 8;   // barrier / flag slots
+  b += 64 + (4 * kTcMaxStages + 24) * 8;   // barrier / flag slots
   return b + 1024;                          // alignment slack
 }
 
@@ -914,7 +984,9 @@ static bool launch_ks(int ks, std::integer_sequence<int, K...>, bool gauss, bool
 
 cudaError_t launch_grad_tc(const CUtensorMap &tm_x, const CUtensorMap &tm_hi, const CUtensorMap &tm_lo,
                            const Problem &pb, const GradArgs &a, const TcArgs &ta, cudaStream_t st) {
-  const size_t smem = tc_smem_bytes(ta.KP, ta.NS, ta.need_lo, pb.p, ta.tf32, ta.PN);
+  const size_t smem = tc_smem_bytes(ta.KP, ta.NS, ta.NT, ta.need_lo, pb.p, ta.tf32, ta.PN);
+  if (ta.NS < 1 || ta.NS > kTcMaxStages || (ta.tf32 && (ta.NT < 1 || ta.NT > kTcMaxStages)))
+    return cudaErrorInvalidValue;
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   if (!g_tc_regs_ok) return cudaErrorInvalidConfiguration;   // tc_prepare not run, or the split does not fit
   if (pb.variant == MV_HIER) return cudaErrorInvalidValue;

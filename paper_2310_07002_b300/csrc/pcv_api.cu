@@ -23,7 +23,7 @@
 #include "pcv_internal.cuh"
 
 namespace pcv {
-size_t tc_smem_bytes(int KP, int NS, int need_lo, int p, int tf32, int PN);
+size_t tc_smem_bytes(int KP, int NS, int NT, int need_lo, int p, int tf32, int PN);
 int tc_max_stages();
 int tc_segments_per_tile(int T, int J, int n_cta);
 cudaError_t tc_prepare();
@@ -303,10 +303,18 @@ pcv_status alloc_shadows(pcv_ctx *x, ChainBufs &cb, int C) {
   return PCV_OK;
 }
 
+// X stages that fit (the TF32 form: with as many X^T stages)
 int tc_max_fit_stages(const pcv_ctx *x, int need_lo) {
   for (int ns = tc_max_stages(); ns > 2; --ns)
-    if (tc_smem_bytes(x->KP, ns, need_lo, x->p, x->tc32 ? 1 : 0, x->PN) <= 227 * 1024) return ns;
+    if (tc_smem_bytes(x->KP, ns, x->tc32 ? ns : 0, need_lo, x->p, x->tc32 ? 1 : 0, x->PN) <= 227 * 1024) return ns;
   return 2;
+}
+
+// TF32 form: the X^T stages beside ns X stages (as many as fit)
+int tc_xt_stages(const pcv_ctx *x, int ns) {
+  int nt = ns;
+  while (nt < tc_max_stages() && tc_smem_bytes(x->KP, ns, nt + 1, 0, x->p, 1, x->PN) <= 227 * 1024) ++nt;
+  return nt;
 }
 
 TcArgs tc_args(pcv_ctx *x, int C, bool need_ll) {
@@ -336,6 +344,7 @@ TcArgs tc_args(pcv_ctx *x, int C, bool need_ll) {
   t.err = &x->st->error;
   t.tf32 = x->tc32 ? 1 : 0;
   if (x->tc32) t.need_lo = 0;       // one TF32 part (centred)
+  t.NT = x->tc32 ? tc_xt_stages(x, t.NS) : 0;
   return t;
 }
 

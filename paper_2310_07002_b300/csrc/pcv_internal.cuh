@@ -207,6 +207,7 @@ struct TcArgs {
   int n_cta;              // grid size
   int max_seg;            // workspace segments per tile
   int NS;                 // X pipeline stages
+  int NT;                 // X^T pipeline stages (TF32 form)
   int need_lo;            // accumulate the theta lo part too (FP32-accurate eta)
   int accurate;           // FP32 epilogue with log densities (else the bf16x2 fast path)
   const float *theta_ref; // d: the shadows hold (theta - theta_ref) / 2
