@@ -136,6 +136,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const long long u0 = (long long)blockIdx.x * U / ta.n_cta;
   const long long u1 = (long long)(blockIdx.x + 1) * U / ta.n_cta;
   const int nunits = (int)(u1 - u0);
+  // Order of the CTA's units: a range that ends in a later tile than it
+  // starts in runs its last piece (chunks 0 .. of that tile) first, then the
+  // rest in order.  Every CTA's range is about U / n_cta units, so at any
+  // time all CTAs work on rows within J - U / n_cta chunks of one another
+  // and the X chunks in use stay resident in L2 (in plain order the CTAs
+  // start at chunks spread over all of X).  All roles walk this order; the
+  // ownership of tile segments and the finish do not depend on it.
+  const long long ls = (u1 - 1) / ta.J * ta.J;     // start of the last unit's tile
+  const int rot = (nunits > 0 && ls > u0) ? (int)(u1 - ls) : 0;
+  auto unit_of = [&](const int i) -> long long { return i < rot ? ls + i : u0 + (i - rot); };
+  // the chunk index j of unit i, walked incrementally by the single-thread
+  // issuers (no 64-bit division per unit): j of unit 0, and the step
+  const int j_u0 = (int)(u0 % ta.J);
+  const int j_first = rot > 0 ? 0 : j_u0;
+  auto j_step = [&](const int i, const int j) { return i + 1 == rot ? j_u0 : (j + 1 == ta.J ? 0 : j + 1); };
+  // segment boundaries in this order
+  auto seg_first = [&](const int i, const int j) { return i == 0 || i == rot || j == 0; };
+  auto seg_last = [&](const int i, const int j) { return i == nunits - 1 || i == rot - 1 || j == ta.J - 1; };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) { mbar_init(smem_u32(&x_full[s]), 1); mbar_init(smem_u32(&x_empty[s]), 1); }
@@ -183,10 +201,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       int last_round[kTcMaxStages];
 #pragma unroll
       for (int s2 = 0; s2 < kTcMaxStages; ++s2) last_round[s2] = -1;
-      for (int i = 0; i < nunits; ++i) {
-        const long long u = u0 + i;
-        const int t = (int)(u / ta.J), j = (int)(u - (long long)t * ta.J);
-        if (!TF && (i == 0 || j == 0)) {
+      for (int i = 0, j = j_first; i < nunits; j = j_step(i, j), ++i) {
+        if (!TF && seg_first(i, j)) {
+          const int t = (int)(unit_of(i) / ta.J);
           if (!mbar_wait_fast(smem_u32(th_empty), (seg & 1) ^ 1, abort_flag, ta.err)) break;
           mbar_expect_tx(smem_u32(th_full), th_bytes * (ta.need_lo ? 2 : 1));
           for (int kb = 0; kb < KA; ++kb) {
@@ -222,11 +239,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const uint64_t ld0 = sdesc_sw128(smem_u32(th_lo), 16, 1024);
       const uint64_t xd_k = sdesc_sw128(smem_u32(xs), 16, 1024);   // K-major view, stage 0
       const uint64_t x_step = (uint64_t)(x_bytes >> 4);
-      int j = (int)(u0 % ta.J);
       int seg1 = 0, st = 0, xph = 0;
-      for (int i = 0; i < nunits; ++i) {
-        const bool first = (i == 0 || j == 0);
-        const bool last = (i == nunits - 1 || j == ta.J - 1);
+      for (int i = 0, j = j_first; i < nunits; j = j_step(i, j), ++i) {
+        const bool first = seg_first(i, j);
+        const bool last = seg_last(i, j);
         if (first && !mbar_wait_fast(smem_u32(th_full), seg1 & 1, abort_flag, ta.err)) break;
         if (!mbar_wait_fast(smem_u32(&x_full[st]), xph, abort_flag, ta.err)) break;
         const int sb = i & 1;
@@ -253,7 +269,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         tc_commit(smem_u32(&s_full[sb]));
         if constexpr (TF) tc_commit(smem_u32(&x_empty[st]));   // X slot read: free it
         if (last) { tc_commit(smem_u32(th_empty)); ++seg1; }
-        if (++j == ta.J) j = 0;
         if (++st == NS) { st = 0; xph ^= 1; }
       }
     }
@@ -269,11 +284,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                                 : sdesc_sw128(smem_u32(xs), kTN * 128, 1024);
       const uint64_t x_step = (uint64_t)((TF ? xt_bytes : x_bytes) >> 4);
       const int nring = TF ? NT : NS;
-      int j = (int)(u0 % ta.J);
       int seg2 = 0, st = 0, tph = 0;
-      for (int i = 0; i < nunits; ++i) {
-        const bool first = (i == 0 || j == 0);
-        const bool last = (i == nunits - 1 || j == ta.J - 1);
+      for (int i = 0, j = j_first; i < nunits; j = j_step(i, j), ++i) {
+        const bool first = seg_first(i, j);
+        const bool last = seg_last(i, j);
         const int rb = i & 1;
         const uint32_t a0 = tmem_R + 64 * rb;       // K step ks: 8 columns (16 bf16) at a0 + 8 ks
         const uint64_t bd0 = xd_mn + (uint64_t)st * x_step;
@@ -301,7 +315,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         tc_commit(smem_u32(&r_empty[rb]));
         tc_commit(smem_u32(TF ? &xt_empty[st] : &x_empty[st]));
         if (last) { tc_commit(smem_u32(g_full)); ++seg2; }
-        if (++j == ta.J) j = 0;
         if (++st == nring) { st = 0; tph ^= 1; }
       }
     }
@@ -312,9 +325,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       int last_round[kTcMaxStages];
 #pragma unroll
       for (int s2 = 0; s2 < kTcMaxStages; ++s2) last_round[s2] = -1;
-      int j = (int)(u0 % ta.J);
       const int nt = TF ? NT : 1;
-      for (int i = 0; i < nunits; ++i) {
+      for (int i = 0, j = j_first; i < nunits; j = j_step(i, j), ++i) {
         const int st = i % nt, rnd = i / nt;
         if (!mbar_wait_fast(smem_u32(&xt_empty[st]), (rnd & 1) ^ 1, abort_flag, ta.err)) break;
         mbar_expect_tx(smem_u32(&xt_full[st]), xt_bytes);
@@ -323,7 +335,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int h = 0; h < 2; ++h)
           tma_load_2d(smem_u32(xb + h * ta.PN * 128), &tm_lo, j * TN + 32 * h, 0, smem_u32(&xt_full[st]));
         last_round[st] = rnd;
-        if (++j == ta.J) j = 0;
       }
       if (*abort_flag)
         for (int s = 0; s < NT; ++s)
@@ -373,12 +384,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       return true;
     };
     // walk the CTA's segments (maximal runs of units in one tile)
-    int t = (int)(u0 / ta.J), j0 = (int)(u0 - (long long)t * ta.J);
     if constexpr (TF) {
-      if (nunits > 0 && !theta_to_tmem(t, 0)) aborted = true;
+      if (nunits > 0 && !theta_to_tmem((int)(unit_of(0) / ta.J), 0)) aborted = true;
     }
     for (int ib = 0; ib < nunits && !aborted; ) {
-      const int ie = min(nunits, ib + (ta.J - j0));   // segment [ib, ie)
+      const long long ub = unit_of(ib);
+      const int t = (int)(ub / ta.J), j0 = (int)(ub - (long long)t * ta.J);
+      // segment [ib, ie): the rotated first piece, or up to the tile's end
+      const int ie = ib < rot ? rot : min(nunits, ib + (ta.J - j0));
       const int c = t * kTM + m;
       const bool valid = c < a.C;
       FoldDesc fd = {0, 0, 0, 0};
@@ -514,12 +527,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         };
         // the TF32 form: one element per column, the excluded rows zeroed
         auto pack32 = [&](const int qq, const float (&r)[32], uint32_t (&pk)[32]) {
-          const int n0 = j * TN + 32 * qq;
-          const bool edge = valid && n0 < fd.excl_hi && n0 + 32 > fd.excl_lo;
 #pragma unroll
-          for (int k = 0; k < 32; ++k) {
-            const int n = n0 + k;
-            pk[k] = (edge && n >= fd.excl_lo && n < fd.excl_hi) ? 0u : tf32_bits(r[k]);
+          for (int k = 0; k < 32; ++k) pk[k] = tf32_bits(r[k]);
+          const int n0 = j * TN + 32 * qq;
+          if (valid && n0 < fd.excl_hi && n0 + 32 > fd.excl_lo) {
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+              const int n = n0 + k;
+              if (n >= fd.excl_lo && n < fd.excl_hi) pk[k] = 0u;
+            }
           }
         };
         if constexpr (ACC || TF) {
@@ -629,10 +645,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         tmem_fence_regs(p3);
       }
       if (aborted) break;
-      // TF32: the next segment's theta (tile t + 1) goes to TMEM before this
+      // TF32: the next segment's theta goes to TMEM before this
       // segment's finish, so that its first GEMMs need not wait for it
       if constexpr (TF) {
-        if (ie < nunits && !theta_to_tmem(t + 1, nseg_done + 1)) break;
+        if (ie < nunits && !theta_to_tmem((int)(unit_of(ie) / ta.J), nseg_done + 1)) break;
       }
       // ---- segment end (both groups): the group that owns the segment's
       // last unit flushes this tile's G partial; both write their ll sums
@@ -859,10 +875,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           }
         }
       }
-      // next segment starts at chunk 0 of the next tile
       ib = ie;
-      ++t;
-      j0 = 0;
     }
     // back to the producers' count, so that all warps meet the teardown alike
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kTcRegsProducer));
