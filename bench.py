@@ -51,25 +51,33 @@ WORKLOADS = {
 
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), with the SHA-256 of
-# the kernel's source file at capture time: a figure whose source has changed
-# since is not reported (traffic: null).
+# the kernel's source files at capture time: a figure whose sources have
+# changed since is not reported (traffic: null).
+TC_SOURCES = ("k_grad_tc.cu", "tc_ptx.cuh")
 TRAFFIC = {
-    # kick-drift launch of the tcgen05 kernel (k_grad_tc<7, false>)
-    ("logistic_large", "bf16"): (36.90e6, "k_grad_tc.cu", "645c06cd15912a57"),
+    # kick-drift launch of the tcgen05 kernel (k_grad_tc<7, false, false>)
+    ("logistic_large", "bf16"): (44.31e6, TC_SOURCES, "572ac4fdc19b0b8d"),
+    # kick-drift launch of the TF32 tcgen05 kernel (k_grad_tc<13, false, false, true>)
+    ("logistic_large", "tf32"): (134.20e6, TC_SOURCES, "572ac4fdc19b0b8d"),
     # FP32 shared-memory-tiled kernel (k_grad_bigp<MV_LOGISTIC>)
-    ("logistic_large", "fp32"): (48.93e6, "k_grad_simt.cu", None),
+    ("logistic_large", "fp32"): (48.93e6, ("k_grad_simt.cu",), None),
 }
 
 
-def traffic_of(workload: str, precision: str):
+def sources_sha(files) -> str:
     import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2310_07002_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def traffic_of(workload: str, precision: str):
     ent = TRAFFIC.get((workload, precision))
-    if ent is None or ent[2] is None:
+    if ent is None or ent[0] is None or ent[2] is None:
         return None
-    path = os.path.join(ROOT, "paper_2310_07002_b300", "csrc", ent[1])
-    with open(path, "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()
-    return ent[0] if sha.startswith(ent[2]) else None
+    return ent[0] if sources_sha(ent[1]).startswith(ent[2]) else None
 
 
 def peaks():
@@ -244,9 +252,10 @@ def main():
                     help="whole trajectories in one launch: -1 autotuned (default), 0 never, w > 0 always "
                          "with w warps per chain where the problem allows (fixes the choice for profiler runs)")
     ap.add_argument("--profile-launches", action="store_true",
-                    help="for profiler captures: create the context, set positions "
-                         "(one gradient launch with log densities), then three "
-                         "kick-drift gradient launches; prints no JSON line")
+                    help="for profiler captures: create the context, set positions and "
+                         "autotune, then inside NVTX range pcv_prof one gradient launch "
+                         "with log densities and three kick-drift gradient launches; "
+                         "prints no JSON line")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -278,8 +287,16 @@ def main():
         if truth is not None:
             theta0[:, :len(truth)] = truth
         pc.set_positions(theta0, step_size=1e-3)
+        pc.time_leapfrog_kernel(1)          # autotuner (launch configuration of the timed runs)
+        torch.cuda.synchronize()
+        # the launches to profile, inside NVTX range pcv_prof: one gradient
+        # evaluation with log densities (set_positions), then kick-drift
+        # launches in the tuned configuration
+        torch.cuda.nvtx.range_push("pcv_prof")
+        pc.set_positions(theta0, step_size=1e-3)
         ms = pc.time_leapfrog_kernel(2)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         pc.close()
         print("profile launches done: %.3f ms per kick-drift launch" % ms, flush=True)
         return

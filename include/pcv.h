@@ -65,8 +65,9 @@ typedef enum {
  * accumulators are FP64 in every mode). */
 typedef enum {
     PCV_FP32_SIMT = 0,      /* FP32 CUDA-core kernels */
-    PCV_TF32 = 1,           /* tensor cores (mma.sync m16n8k8), TF32 in, FP32 accumulate;
-                               flat models with p <= 112 */
+    PCV_TF32 = 1,           /* tcgen05 tensor cores (kind::tf32), FP32 X and parameter
+                               shadows rounded to TF32 in, FP32 accumulate; flat models
+                               with p <= 112 */
     PCV_BF16 = 2            /* tcgen05 tensor cores, BF16 X and parameter shadows in,
                                FP32 accumulate; flat models (logistic, Gaussian linear,
                                AR) with p <= 128 */

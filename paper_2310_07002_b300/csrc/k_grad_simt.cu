@@ -606,291 +606,6 @@ __global__ void __launch_bounds__(256) k_grad_bigp(Problem pb, GradArgs a, int p
   }
 }
 
-// ---------------------------------------------------------------------------
-// TF32 rung (flat models, p <= 128): the two contractions on the tensor
-// cores through mma.sync.m16n8k8 with TF32 inputs and FP32 accumulation.
-// A CTA owns 64 chains and one of `splits` row ranges, in 64-row chunks:
-//   S = Theta_tile . X_chunk^T   (warp w: chains 16 (w % 4) .., rows 32 (w / 4) ..)
-//   R = mask .* dlogp/deta       (FP32 in registers, TF32 in shared memory)
-//   G += R . X_chunk             (warp w: chains 16 (w % 4) .., dim tiles w / 4, +2, ..)
-// Theta, X and R are rounded to TF32 (cvt.rna) once, when staged in shared
-// memory.  Fragment layouts of m16n8k8 (g = lane / 4, q = lane % 4):
-// A (16 x 8, row): (g, q), (g + 8, q), (g, q + 4), (g + 8, q + 4);
-// B (8 x 8, col): (q, g), (q + 4, g); C (16 x 8): (g, 2q), (g, 2q + 1),
-// (g + 8, 2q), (g + 8, 2q + 1).
-// ---------------------------------------------------------------------------
-constexpr int kT32C = 64, kT32R = 64, kT32Ldr = kT32R + 4;
-
-__device__ __forceinline__ uint32_t to_tf32(float v) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-  return r;
-}
-// 16-byte global -> shared copy that does not wait (cp.async); src_bytes 0
-// fills the destination with zeros and reads nothing
-__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
-  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int Pending>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(Pending) : "memory"); }
-
-__device__ __forceinline__ void mma_tf32(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-template <int MV>
-__global__ void __launch_bounds__(256) k_grad_tf32(Problem pb, GradArgs a, int pk) {
-  extern __shared__ __align__(16) uint32_t sm_t32[];
-  const int ldk = pk + 4;                           // = 4 (mod 8): conflict-free A/B fragment loads
-  uint32_t *th_s = sm_t32;                          // [64][ldk]  TF32
-  uint32_t *xs0 = th_s + kT32C * ldk;               // [2][64][ldk] X chunks: FP32 as copied, then TF32
-  uint32_t *rs = xs0 + 2 * kT32R * ldk;             // [64][68]   TF32 residual (chains x rows)
-  float *ys = reinterpret_cast<float *>(rs + kT32C * kT32Ldr);   // [64]
-  float *lls = ys + kT32R;                          // [3][64][8] partial sums
-  __shared__ double lld[2][kT32C];
-  __shared__ int is_last;
-  const int t = threadIdx.x, warp = t >> 5, lane = t & 31, g = lane >> 2, q = lane & 3;
-  const int tile = blockIdx.x / a.splits, split = blockIdx.x - tile * a.splits;
-  const int c0 = tile * kT32C, p = pb.p;
-  for (int i = t; i < kT32C * pk; i += 256) {
-    const int cl = i / pk, j = i - cl * pk;
-    const int c = c0 + cl;
-    th_s[cl * ldk + j] = to_tf32((c < a.C && j < p) ? a.theta[(size_t)c * a.ld_theta + j] : 0.0f);
-  }
-  const int mt = warp & 3, nh = warp >> 2;
-  // the two chains of this lane's accumulator rows
-  float logsig[2] = {0.0f, 0.0f}, inv_s2[2] = {1.0f, 1.0f};
-  FoldDesc fd[2];
-#pragma unroll
-  for (int u = 0; u < 2; ++u) {
-    const int c = c0 + 16 * mt + g + 8 * u;
-    const bool valid = c < a.C;
-    fd[u] = valid ? pb.folds[fold_of_chain(a, c)] : FoldDesc{0, 0, 0, 0};
-    if (MV == MV_GAUSS_KNOWN) {
-      logsig[u] = logf(pb.sigma_known);
-      inv_s2[u] = 1.0f / (pb.sigma_known * pb.sigma_known);
-    } else if (MV == MV_GAUSS_LOGSIG) {
-      logsig[u] = valid ? a.theta[(size_t)c * a.ld_theta + p] : 0.0f;
-      inv_s2[u] = expf(-2.0f * logsig[u]);
-    }
-  }
-  const int nk = pk / 8;                            // K steps of the first GEMM, dim tiles of the second
-  float acc2[7][4];
-#pragma unroll
-  for (int j = 0; j < 7; ++j)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) acc2[j][e] = 0.0f;
-  float ll_tr[2] = {0.0f, 0.0f}, ll_te[2] = {0.0f, 0.0f}, dls[2] = {0.0f, 0.0f};
-  const int r0 = (int)((long long)pb.N * split / a.splits);
-  const int r1 = (int)((long long)pb.N * (split + 1) / a.splits);
-  // X chunks are double-buffered: chunk c + 1 is copied (cp.async) while
-  // chunk c is computed; each thread rounds to TF32 the elements it copied
-  const int nq4 = pk / 4;                           // 16-byte groups per row
-  auto fetch_x = [&](int n0c, uint32_t *buf) {
-    const int nrc = min(kT32R, r1 - n0c);
-    for (int i = t; i < kT32R * nq4; i += 256) {
-      const int rr = i / nq4, j4 = 4 * (i - rr * nq4);
-      const bool ok = rr < nrc && j4 < pb.p_pad;    // beyond: zeros (rows, K padding)
-      cp_async16(buf + rr * ldk + j4, ok ? pb.X + (size_t)(n0c + rr) * pb.p_pad + j4 : pb.X, ok ? 16 : 0);
-    }
-    cp_async_commit();
-  };
-  if (r0 < r1) fetch_x(r0, xs0);
-  __syncthreads();
-  int cidx = 0;
-  for (int n0 = r0; n0 < r1; n0 += kT32R, ++cidx) {
-    const int nr = min(kT32R, r1 - n0);
-    uint32_t *xs = xs0 + (cidx & 1) * kT32R * ldk;
-    if (n0 + kT32R < r1) {
-      fetch_x(n0 + kT32R, xs0 + ((cidx + 1) & 1) * kT32R * ldk);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
-    for (int i = t; i < kT32R * nq4; i += 256) {
-      const int rr = i / nq4, j4 = 4 * (i - rr * nq4);
-      uint4 *q4 = reinterpret_cast<uint4 *>(xs + rr * ldk + j4);
-      uint4 v = *q4;
-      v.x = to_tf32(__uint_as_float(v.x)); v.y = to_tf32(__uint_as_float(v.y));
-      v.z = to_tf32(__uint_as_float(v.z)); v.w = to_tf32(__uint_as_float(v.w));
-      *q4 = v;
-    }
-    if (t < kT32R) ys[t] = t < nr ? pb.y[n0 + t] : 0.0f;
-    __syncthreads();
-    // ---- S for chains 16 mt .. 16 mt + 15, rows 32 nh .. 32 nh + 31
-    float acc1[4][4];
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc1[nt][e] = 0.0f;
-    const uint32_t *ta = th_s + (16 * mt + g) * ldk + q;
-    for (int ks = 0; ks < nk; ++ks) {
-      const int k0 = 8 * ks;
-      const uint32_t a0 = ta[k0], a1 = ta[8 * ldk + k0], a2 = ta[k0 + 4], a3 = ta[8 * ldk + k0 + 4];
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const uint32_t *xb = xs + (32 * nh + 8 * nt + g) * ldk + k0 + q;
-        mma_tf32(acc1[nt], a0, a1, a2, a3, xb[0], xb[4]);
-      }
-    }
-    // ---- masked residual dlogp/deta (and log likelihoods on evaluation steps)
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int u = e >> 1;                       // chain 16 mt + g + 8 u
-        const int rr = 32 * nh + 8 * nt + 2 * q + (e & 1), n = n0 + rr;
-        const float eta = acc1[nt][e], yv = ys[rr];
-        const bool in_rows = rr < nr;
-        const float tr = (in_rows && (n < fd[u].excl_lo || n >= fd[u].excl_hi)) ? 1.0f : 0.0f;
-        float dll, ll = 0.0f;
-        if (MV == MV_LOGISTIC) {
-          dll = yv - 1.0f / (1.0f + __expf(-eta));
-          if (a.need_ll) ll = yv * eta - softplusf(eta);
-        } else {
-          const float er = yv - eta;
-          dll = er * inv_s2[u];
-          if (a.need_ll) ll = -0.5f * kLog2Pi - logsig[u] - 0.5f * er * er * inv_s2[u];
-          if (MV == MV_GAUSS_LOGSIG) dls[u] = fmaf(tr, er * er * inv_s2[u] - 1.0f, dls[u]);
-        }
-        rs[(16 * mt + g + 8 * u) * kT32Ldr + rr] = to_tf32(dll * tr);
-        if (a.need_ll) {
-          const float te = (in_rows && n >= fd[u].test_lo && n < fd[u].test_hi) ? 1.0f : 0.0f;
-          ll_tr[u] = fmaf(tr, ll, ll_tr[u]);
-          ll_te[u] = fmaf(te, ll, ll_te[u]);
-        }
-      }
-    }
-    __syncthreads();
-    // ---- G[chains 16 mt .., dim tiles nh, nh + 2, ...] += R . X_chunk
-    const uint32_t *ra = rs + (16 * mt + g) * kT32Ldr + q;
-#pragma unroll
-    for (int ks = 0; ks < kT32R / 8; ++ks) {
-      const int k0 = 8 * ks;
-      const uint32_t a0 = ra[k0], a1 = ra[8 * kT32Ldr + k0], a2 = ra[k0 + 4], a3 = ra[8 * kT32Ldr + k0 + 4];
-      const uint32_t *xb = xs + (k0 + q) * ldk + g;
-#pragma unroll
-      for (int jj = 0; jj < 7; ++jj) {
-        const int j = nh + 2 * jj;
-        if (j < nk) mma_tf32(acc2[jj], a0, a1, a2, a3, xb[8 * j], xb[4 * ldk + 8 * j]);
-      }
-    }
-    __syncthreads();
-  }
-  // per-chain likelihood sums: slot nh * 4 + q of the chain, added in order
-#pragma unroll
-  for (int u = 0; u < 2; ++u) {
-    const int cl = 16 * mt + g + 8 * u, sl = nh * 4 + q;
-    lls[(0 * kT32C + cl) * 8 + sl] = ll_tr[u];
-    lls[(1 * kT32C + cl) * 8 + sl] = ll_te[u];
-    lls[(2 * kT32C + cl) * 8 + sl] = dls[u];
-  }
-  __syncthreads();
-  float sums[3] = {0.0f, 0.0f, 0.0f};
-  if (t < kT32C) {
-#pragma unroll
-    for (int qq = 0; qq < 3; ++qq)
-#pragma unroll
-      for (int v = 0; v < 8; ++v) sums[qq] += lls[(qq * kT32C + t) * 8 + v];
-  }
-  // partial of this CTA: [64 chains][ws_stride]: grads [0, pk), slot pk
-  // dlogsig, pk + 1 ll_tr, pk + 2 ll_te
-  float *mine = a.ws + ((size_t)tile * a.splits + split) * kT32C * a.ws_stride;
-#pragma unroll
-  for (int jj = 0; jj < 7; ++jj) {
-    const int j = nh + 2 * jj;
-    if (j < nk) {
-      const int dim = 8 * j + 2 * q;
-      mine[(16 * mt + g) * a.ws_stride + dim] = acc2[jj][0];
-      mine[(16 * mt + g) * a.ws_stride + dim + 1] = acc2[jj][1];
-      mine[(16 * mt + g + 8) * a.ws_stride + dim] = acc2[jj][2];
-      mine[(16 * mt + g + 8) * a.ws_stride + dim + 1] = acc2[jj][3];
-    }
-  }
-  if (t < kT32C) {
-    mine[t * a.ws_stride + pk] = sums[2];
-    mine[t * a.ws_stride + pk + 1] = sums[0];
-    mine[t * a.ws_stride + pk + 2] = sums[1];
-  }
-  __threadfence();
-  __syncthreads();
-  if (a.splits > 1) {
-    if (t == 0) {
-      const unsigned prev = atomicAdd(a.tickets + tile, 1u);
-      is_last = (prev == (unsigned)a.splits - 1);
-      if (is_last) a.tickets[tile] = 0u;
-    }
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-  }
-  // sum the splits' partials in split order (likelihood sums in FP64), then
-  // priors and the leapfrog update, one warp per chain
-  float *tot = reinterpret_cast<float *>(xs0);      // [64][pk + 4], reuses an X buffer
-  const int ts = pk + 4;
-  const float *base = a.ws + (size_t)tile * a.splits * kT32C * a.ws_stride;
-  for (int i = t; i < kT32C * (pk + 3); i += 256) {
-    const int cl = i / (pk + 3), j = i - cl * (pk + 3);
-    if (j > pk) {
-      double sacc = 0.0;
-      for (int s2 = 0; s2 < a.splits; ++s2) sacc += (double)__ldcg(base + ((size_t)s2 * kT32C + cl) * a.ws_stride + j);
-      lld[j - pk - 1][cl] = sacc;
-    } else {
-      float sacc = 0.0f;
-      for (int s2 = 0; s2 < a.splits; ++s2) sacc += __ldcg(base + ((size_t)s2 * kT32C + cl) * a.ws_stride + j);
-      tot[cl * ts + j] = sacc;
-    }
-  }
-  __syncthreads();
-  for (int cl = warp; cl < kT32C; cl += 8) {
-    const int c = c0 + cl;
-    if (c >= a.C) continue;
-    float *row = tot + cl * ts;
-    if (MV == MV_GAUSS_LOGSIG) {
-      const float d = row[pk];
-      __syncwarp();
-      if (lane == 0) row[p] = d;                    // d/dlog sigma at index p
-      __syncwarp();
-    }
-    finish_chain<MV>(pb, a, c, row, lld[0][cl], lld[1][cl], lane);
-  }
-}
-
-size_t tf32_smem_bytes(int pk) {
-  const size_t ldk = (size_t)pk + 4;
-  return sizeof(uint32_t) * ((kT32C + 2 * kT32R) * ldk + (size_t)kT32C * kT32Ldr + kT32R + 3 * kT32C * 8);
-}
-
-int tf32_k_round(int p) { return (p + 7) / 8 * 8; }
-
-template <int MV>
-static cudaError_t launch_tf32_mv(const Problem &pb, const GradArgs &a, cudaStream_t st) {
-  const int pk = tf32_k_round(pb.p);
-  const int tiles = (a.C + kT32C - 1) / kT32C;
-  const size_t sm = tf32_smem_bytes(pk);
-  cudaError_t e = cudaFuncSetAttribute(k_grad_tf32<MV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  k_grad_tf32<MV><<<tiles * a.splits, 256, sm, st>>>(pb, a, pk);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_grad_tf32(const Problem &pb, const GradArgs &a, cudaStream_t st) {
-  if (pb.p > 112) return cudaErrorInvalidValue;   // 14 dim tiles: 7 per warp
-  switch (pb.variant) {
-    case MV_GAUSS_KNOWN: return launch_tf32_mv<MV_GAUSS_KNOWN>(pb, a, st);
-    case MV_GAUSS_LOGSIG: return launch_tf32_mv<MV_GAUSS_LOGSIG>(pb, a, st);
-    case MV_LOGISTIC: return launch_tf32_mv<MV_LOGISTIC>(pb, a, st);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
 int simt_chain_tile(int p) { return simt_flat_pp(p) > 0 ? 32 : kBigTileC; }
 
 size_t bigp_smem_bytes(int pp) {

@@ -65,7 +65,6 @@ struct pcv_ctx {
   int64_t N = 0;
   int h = 0, Lf = 16, b = 50, M = 64, max_batches = 1024, n_fd_draws = 250;
   int chain_base = 0;             // Philox chain id of fold-chain 0 (first_fold * L)
-  bool tf32 = false;              // TF32 rung (mma.sync tensor cores)
   double traj_len = 0.0;          // effective trajectory length (0: no cap)
   float jitter = 0.0f;            // effective step-size jitter of the fold chains
   Problem pb{};
@@ -192,12 +191,11 @@ void free_all(pcv_ctx *x) {
   x->allocs.clear();
 }
 
-// chains per CTA tile and workspace row stride of the CUDA-core / TF32
-// gradient kernels (split-N partials)
-int chain_tile(const pcv_ctx *x) { return x->tf32 ? 64 : simt_chain_tile(x->p); }
+// chains per CTA tile and workspace row stride of the CUDA-core gradient
+// kernels (split-N partials)
+int chain_tile(const pcv_ctx *x) { return simt_chain_tile(x->p); }
 int ws_stride_of(const pcv_ctx *x) {
-  int s = std::max(x->d_pad, std::max(0, simt_flat_pp(x->p)));
-  if (x->tf32) s = std::max(s, tf32_k_round(x->p));
+  const int s = std::max(x->d_pad, std::max(0, simt_flat_pp(x->p)));
   return s + 4;
 }
 
@@ -411,8 +409,7 @@ pcv_status launch_grad(pcv_ctx *x, GradArgs a, const ChainBufs *cb = nullptr) {
   if (s != PCV_OK) return s;
   a.ws = x->ws;
   a.tickets = x->tickets;
-  if (x->tf32) CK(launch_grad_tf32(x->pb, a, x->stream));
-  else CK(launch_grad_simt(x->pb, a, x->stream));
+  CK(launch_grad_simt(x->pb, a, x->stream));
   return PCV_OK;
 }
 
@@ -943,7 +940,6 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
   // operands
   x->tc = opt->precision == PCV_BF16 || opt->precision == PCV_TF32;
   x->tc32 = opt->precision == PCV_TF32;
-  x->tf32 = false;
   if (x->tc32 && (model->kind == PCV_HIER_GAUSS || p > 112))
     return bail(PCV_E_UNSUPPORTED, "the TF32 path covers the flat models (logistic, Gaussian linear, AR) with p <= 112");
   if (x->tc && (model->kind == PCV_HIER_GAUSS || p > 128))

@@ -222,9 +222,6 @@ struct TcArgs {
 int simt_flat_pp(int p);
 size_t bigp_smem_bytes(int pp);
 int simt_chain_tile(int p);   // chains per CTA tile of the FP32 gradient kernels
-// TF32 rung (mma.sync m16n8k8): 64-chain tiles, p <= 112, dims padded to 8
-cudaError_t launch_grad_tf32(const Problem &pb, const GradArgs &a, cudaStream_t st);
-int tf32_k_round(int p);
 size_t hier_smem_bytes(int PP, int G, int splits);
 cudaError_t launch_grad_simt(const Problem &pb, const GradArgs &a, cudaStream_t st);
 
