@@ -98,6 +98,16 @@ typedef struct {
      * predictive; two contexts that differ only in this mask are the models
      * compared by pcv_compare. */
     const int32_t *active_covariates;
+    /* host, p flags, or NULL: a second model, the same one restricted to
+     * these covariates (a subset of active_covariates; PCV_E_INVALID_ARG
+     * otherwise), whose chains run in the same launches as model A's
+     * (Appendix B's parallel evaluation of models by their masks): folds
+     * [K, 2K) are model B's copies of folds [0, K) (pcv_num_folds reports
+     * 2K), chains [K L, 2 K L) its chains.  B takes A's step size and A's
+     * adapted inverse mass restricted to B's covariates, and its chains
+     * start from A's full-data draws with B's inactive coefficients at 0.
+     * pcv_compare_pair compares the two. first_fold must be 0. */
+    const int32_t *active_covariates_b;
 } pcv_model;
 
 /* Optional device allocator (the Python binding passes the torch caching
@@ -332,6 +342,15 @@ pcv_status pcv_scores_extra(pcv_ctx *ctx, double *hs_k, double *dss_k, double *h
  * give PCV_E_INVALID_ARG.
  */
 pcv_status pcv_compare(pcv_ctx *ctx_a, pcv_ctx *ctx_b, double *delta_k, double *mcse_k, double *out);
+
+/*
+ * The same comparison within one context that runs two models
+ * (pcv_model.active_covariates_b): model A's folds [0, K) against model B's
+ * [K, 2K); outputs as pcv_compare (delta_k, mcse_k: host, K each; out[4]).
+ * PCV_E_INVALID_ARG for a one-model context, PCV_E_BAD_STATE before
+ * pcv_sample.
+ */
+pcv_status pcv_compare_pair(pcv_ctx *ctx, double *delta_k, double *mcse_k, double *out);
 
 /*
  * R-hat_max benchmark (Section 4.2; the block-shuffle loop of Algorithm A2):

@@ -93,6 +93,8 @@ def _declare(L):
     L.orc_compare.restype = ct.c_int
     L.orc_pcv_set_tuning.argtypes = [ct.c_void_p, ct.c_double, ct.c_double]
     L.orc_pcv_set_tuning.restype = ct.c_int
+    L.orc_pcv_set_chain_base.argtypes = [ct.c_void_p, ct.c_int64]
+    L.orc_pcv_set_chain_base.restype = ct.c_int
     L.orc_pcv_fulldata.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_double]
     L.orc_pcv_fulldata.restype = ct.c_int
     L.orc_pcv_fulldata_accept.argtypes = [ct.c_void_p, _D, _D]
@@ -283,7 +285,7 @@ class OraclePCV:
                  eps: float = -1.0, minv: Optional[np.ndarray] = None, b: int = 50,
                  M: int = 64, max_batches: int = 4096, store_draws: bool = False,
                  n_threads: int = 0, init_scale: float = 1.0, traj_len: float = -1.0,
-                 jitter: float = -1.0):
+                 jitter: float = -1.0, chain_base: int = 0):
         self.prob = prob
         self.L = L
         self.K = prob.s.K
@@ -295,6 +297,8 @@ class OraclePCV:
                                       b, M, max_batches, int(store_draws), nt, init_scale)
         # trajectory-length cap and step-size jitter (< 0: the defaults)
         lib().orc_pcv_set_tuning(self.h, traj_len, jitter)
+        # Philox chain id of fold chain c = chain_base + c
+        assert lib().orc_pcv_set_chain_base(self.h, chain_base) == 0
 
     def __del__(self):
         if getattr(self, "h", None):

@@ -922,6 +922,7 @@ typedef struct {
     double *hs1, *hs2, *dsum, *douter;   /* C, C x T, C x T, C x T x T */
     double fd_tail_accept;    /* mean acceptance statistic since the last dual-averaging start */
     double fd_keep_accept;    /* mean acceptance statistic of the pool draws */
+    uint32_t chain_base;      /* Philox chain id of fold chain c: chain_base + c */
 } orc_pcv;
 
 orc_pcv *orc_pcv_create(const orc_problem *P, int32_t L, uint64_t seed, int32_t Lf, double eps,
@@ -1014,7 +1015,7 @@ static void extra_push(orc_pcv *S, int32_t c, int32_t k, uint32_t it, const doub
             double eta = 0.0;
             for (int32_t j = 0; j < P->p; ++j) eta += P->X[n * P->p + j] * theta[j];
             uint32_t w[4];
-            philox_at(S->seed, (uint32_t)(i / 4), (uint32_t)c, it, 5u, w);
+            philox_at(S->seed, (uint32_t)(i / 4), S->chain_base + (uint32_t)c, it, 5u, w);
             ytil[i] = u32_to_unit(w[i % 4]) < sigmoid(eta) ? 1.0 : 0.0;
         }
         for (int64_t i = 0; i < m; ++i) {
@@ -1026,7 +1027,7 @@ static void extra_push(orc_pcv *S, int32_t c, int32_t k, uint32_t it, const doub
     }
     const double sigma = (P->kind == ORC_GAUSS && P->sigma_known > 0) ? P->sigma_known : exp(theta[P->p]);
     const double s2 = sigma * sigma;
-    orc_normals(S->seed, (uint32_t)c, it, 5u, (int32_t)m, ytil);     /* stream 5: predictive draws */
+    orc_normals(S->seed, S->chain_base + (uint32_t)c, it, 5u, (int32_t)m, ytil);   /* stream 5: predictive draws */
     double xi1 = 0.0;
     for (int64_t i = 0; i < m; ++i) {
         const int64_t n = rows[i];
@@ -1136,6 +1137,15 @@ int orc_pcv_set_tuning(orc_pcv *S, double traj_len, double jitter)
 {
     S->traj_len = traj_len;
     S->jitter = jitter;
+    return 0;
+}
+/* The fold chains' Philox chain ids start at chain_base (default 0): with
+ * base K L the run replays the chains of a second model whose chains follow
+ * the K L chains of the first in one run (Appendix B's two-model runs). */
+int orc_pcv_set_chain_base(orc_pcv *S, int64_t chain_base)
+{
+    if (chain_base < 0 || chain_base > 0x7fffffff) return -1;
+    S->chain_base = (uint32_t)chain_base;
     return 0;
 }
 static double eff_traj_len(const orc_pcv *S) { return S->traj_len < 0 ? 1.5707963267948966 : S->traj_len; }
@@ -1365,7 +1375,7 @@ int orc_pcv_fold_warmup(orc_pcv *S, int32_t n_wu)
     const orc_problem *P = &S->P;
     const int32_t d = S->d;
     for (int32_t c = 0; c < S->C; ++c) {
-        uint32_t idx = orc_index(S->seed, (uint32_t)c, 0, ST_INIT, (uint32_t)S->n_pool);
+        uint32_t idx = orc_index(S->seed, S->chain_base + (uint32_t)c, 0, ST_INIT, (uint32_t)S->n_pool);
         memcpy(S->chains[c].theta, S->pool + (size_t)idx * d, sizeof(double) * (size_t)d);
     }
 #pragma omp parallel for schedule(dynamic, 1) num_threads(S->n_threads)
@@ -1376,7 +1386,7 @@ int orc_pcv_fold_warmup(orc_pcv *S, int32_t n_wu)
         for (int32_t i = 0; i < n_wu; ++i) {
             int acc, div;
             const uint32_t it = S->iter + (uint32_t)i;
-            hmc_transition(P, k, S->seed, (uint32_t)c, it, ST_MOM, ST_ACC, iter_eps(S, it),
+            hmc_transition(P, k, S->seed, S->chain_base + (uint32_t)c, it, ST_MOM, ST_ACC, iter_eps(S, it),
                            S->Lf, S->minv, &S->chains[c], work, &acc, &div);
         }
         free(work);
@@ -1426,7 +1436,7 @@ int orc_pcv_sample(orc_pcv *S, int32_t n_draws)
         for (int32_t i = 0; i < n_draws; ++i) {
             int acc, div;
             const uint32_t it = S->iter + (uint32_t)i;
-            hmc_transition(P, k, S->seed, (uint32_t)c, it, ST_MOM, ST_ACC, iter_eps(S, it),
+            hmc_transition(P, k, S->seed, S->chain_base + (uint32_t)c, it, ST_MOM, ST_ACC, iter_eps(S, it),
                            S->Lf, S->minv, &S->chains[c], work, &acc, &div);
             S->acc[c].divergences += div;
             S->acc[c].accepts += acc;

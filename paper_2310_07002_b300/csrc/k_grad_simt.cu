@@ -60,7 +60,7 @@ __device__ __forceinline__ void finish_chain(const Problem &pb, const GradArgs &
       const float rj = rr[j] + kick * g;
       rr[j] = rj;
       if (a.mode == MODE_KICK_DRIFT) {
-        const float tn = t + eps * a.minv[j] * rj;
+        const float tn = t + eps * minv_row(a.minv, c, a.minv_every, a.minv_ld)[j] * rj;
         th[j] = tn;
         if (a.shadow_hi) {
           const __nv_bfloat16 hi = __float2bfloat16_rn(tn);

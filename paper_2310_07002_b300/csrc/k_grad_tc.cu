@@ -736,7 +736,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               if (a.mode != MODE_NONE)
                 rv[u] = *reinterpret_cast<const float4 *>(a.r + (size_t)cc_[u] * a.ld_theta + jj_[u]);
               if (kd) {
-                mv[u] = *reinterpret_cast<const float4 *>(a.minv + jj_[u]);
+                mv[u] = *reinterpret_cast<const float4 *>(minv_row(a.minv, cc_[u], a.minv_every, a.minv_ld) + jj_[u]);
                 rf[u] = *reinterpret_cast<const float4 *>(ta.theta_ref + jj_[u]);
               }
             }
@@ -792,7 +792,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const float rj = rr[jj] + kick * g;
             rr[jj] = rj;
             if (kd) {
-              const float tn = tv + eps * a.minv[jj] * rj;
+              const float tn = tv + eps * minv_row(a.minv, cc, a.minv_every, a.minv_ld)[jj] * rj;
               th[jj] = tn;
               const float half = 0.5f * (tn - ta.theta_ref[jj]);   // shadows hold (theta - ref) / 2
               if constexpr (TF) {
@@ -834,7 +834,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               float *rr = a.r + (size_t)cc * a.ld_theta;
               const float rj = rr[pb.p] + kick * g;
               rr[pb.p] = rj;
-              if (kd) th[pb.p] = ls + eps * a.minv[pb.p] * rj;
+              if (kd) th[pb.p] = ls + eps * minv_row(a.minv, cc, a.minv_every, a.minv_ld)[pb.p] * rj;
             }
           }
         }

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256) k_begin(BeginArgs a) {
     for (int e = 0; e < 4; ++e) {
       const int j = 4 * q + e;
       if (j >= a.d) break;
-      const float mv = a.minv[j];
+      const float mv = minv_row(a.minv, c, a.minv_every, a.minv_ld)[j];
       // a coordinate with inverse mass 0 (masked covariate) is held: r = 0
       const float r0 = a.r_given ? a.r_given[(size_t)c * a.ld + j] : (mv > 0.0f ? z[e] / sqrtf(mv) : 0.0f);
       kin += (double)mv * (double)r0 * (double)r0;
@@ -158,9 +158,10 @@ __global__ void __launch_bounds__(kAccChains * 32) k_accept(AcceptArgs a) {
   const int c = cb0 + warp;
   if (c < a.C) {
     double kin = 0.0;
+    const float *mvr = minv_row(a.minv, c, a.minv_every, a.minv_ld);
     for (int j = lane; j < a.d; j += 32) {
       const double rj = a.r[(size_t)c * a.ld + j];
-      kin += (double)a.minv[j] * rj * rj;
+      kin += (double)mvr[j] * rj * rj;
     }
     kin = warp_sum_d(kin);
     const double H1 = -a.logp_p[c] + 0.5 * kin;

@@ -248,6 +248,7 @@ __device__ __forceinline__ void traj_team(const Problem &pb, const TrajArgs &t, 
   }
   if (!t.eval_only && c == 0 && writer && lane == 0 && t.eps_iter) *t.eps_iter = eps;
   const FoldDesc fd = pb.folds[t.fold_base + c / t.L];
+  const float *mvr = minv_row(t.minv, c, t.minv_every, t.minv_ld);   // this chain's model's inverse mass
   const float *th0 = t.theta + (size_t)c * t.ld;
 
   // position and momentum in registers (every lane holds all of them); for
@@ -279,7 +280,7 @@ __device__ __forceinline__ void traj_team(const Problem &pb, const TrajArgs &t, 
       const int k = jj & 3;
       const float zq = k == 0 ? z0 : k == 1 ? z1 : k == 2 ? z2 : z3;
       const float zj = __shfl_sync(0xffffffffu, zq, jj >> 2);
-      const float m = t.minv[jj];
+      const float m = mvr[jj];
       const float r0 = t.r_given ? t.r_given[(size_t)c * t.ld + jj] : (m > 0.0f ? zj / sqrtf(m) : 0.0f);
       if (lane == (jj & 31)) kterm = fmaf(m * r0, r0, kterm);
       rh = r0 + 0.5f * eps * g0[jj];
@@ -312,12 +313,12 @@ __device__ __forceinline__ void traj_team(const Problem &pb, const TrajArgs &t, 
       for (int j = 0; j < PP; ++j) {
         if (j < p) {
           rr[j] += kick * g[j];
-          if (!last) th[j] += eps * t.minv[j] * rr[j];
+          if (!last) th[j] += eps * mvr[j] * rr[j];
         }
       }
       if (LOGSIG) {
         rls += kick * gls;
-        if (!last) ls += eps * t.minv[p] * rls;
+        if (!last) ls += eps * mvr[p] * rls;
       }
     }
   }
@@ -359,8 +360,8 @@ __device__ __forceinline__ void traj_team(const Problem &pb, const TrajArgs &t, 
   float kt = 0.0f;
 #pragma unroll
   for (int j = 0; j < PP; ++j)
-    if (j < p && lane == (j & 31)) kt = fmaf(t.minv[j] * rr[j], rr[j], kt);
-  if (LOGSIG && lane == (p & 31)) kt = fmaf(t.minv[p] * rls, rls, kt);
+    if (j < p && lane == (j & 31)) kt = fmaf(mvr[j] * rr[j], rr[j], kt);
+  if (LOGSIG && lane == (p & 31)) kt = fmaf(mvr[p] * rls, rls, kt);
   const double H1 = -logp1 + 0.5 * warp_sum_d((double)kt);
   const double dH = H1 - H0;
   const bool finite = isfinite(H1) && isfinite(dH);

@@ -122,6 +122,14 @@ struct pcv_ctx {
   // covariate-selection mask (d_pad floats 1 / 0; nullptr: every covariate)
   float *active_d = nullptr;
   std::vector<float> active_h;
+  // two models in one context (pcv_model.active_covariates_b, Appendix B):
+  // folds [K_model, 2 K_model) are model B's copies of folds [0, K_model),
+  // chains [K_model L, 2 K_model L) its chains, and minv holds a second row
+  // (model A's inverse mass with B's inactive coefficients at 0)
+  bool pair = false;
+  int K_model = 0;
+  float *active_b_d = nullptr;
+  std::vector<float> active_b_h;
   double *cmp_out = nullptr;
   size_t cmp_n = 0;
   // R-hat_max benchmark scratch
@@ -197,6 +205,20 @@ int chain_tile(const pcv_ctx *x) { return simt_chain_tile(x->p); }
 int ws_stride_of(const pcv_ctx *x) {
   const int s = std::max(x->d_pad, std::max(0, simt_flat_pp(x->p)));
   return s + 4;
+}
+
+// chains per inverse-mass row (two models: one row per model; else one row)
+int minv_every_of(const pcv_ctx *x) { return x->pair ? x->K_model * x->L : 0; }
+
+// model B's inverse-mass row: model A's (row 0) with B's inactive
+// coefficients at 0 (B's covariates are a subset of A's)
+pcv_status sync_minv_b(pcv_ctx *x) {
+  if (!x->pair) return PCV_OK;
+  CK(cudaMemcpyAsync(x->minv + x->d_pad, x->minv, sizeof(float) * x->d_pad, cudaMemcpyDeviceToDevice, x->stream));
+  k_mask_positions<<<(unsigned)((x->d + 255) / 256), 256, 0, x->stream>>>(1, x->d, x->d_pad, x->active_b_d,
+                                                                          x->minv + x->d_pad);
+  CK(cudaGetLastError());
+  return PCV_OK;
 }
 
 int splits_cap(const pcv_ctx *x) {
@@ -384,6 +406,7 @@ GradArgs grad_args(pcv_ctx *x, const ChainBufs &cb, bool proposal) {
   a.r = cb.r;
   a.eps = &x->st->eps_iter;
   a.minv = x->minv;
+  a.minv_every = minv_every_of(x); a.minv_ld = x->d_pad;
   a.splits = splits_for(x, cb.C);
   a.ws = x->ws;
   a.ws_stride = ws_stride_of(x);
@@ -436,6 +459,7 @@ TrajArgs traj_args(pcv_ctx *x, ChainBufs &cb, bool fd, const float *r_given, flo
   t.eps_iter = &x->st->eps_iter;
   t.jitter = jitter;
   t.minv = x->minv;
+  t.minv_every = minv_every_of(x); t.minv_ld = x->d_pad;
   t.theta = cb.theta; t.grad = cb.grad; t.logp = cb.logp;
   t.r_given = r_given;
   t.theta_p = cb.theta_p; t.r = cb.r; t.grad_p = cb.grad_p;
@@ -466,6 +490,7 @@ pcv_status launch_proposal(pcv_ctx *x, ChainBufs &cb, bool fd, const float *r_gi
   ba.theta = cb.theta; ba.grad = cb.grad; ba.logp = cb.logp;
   ba.theta_p = cb.theta_p; ba.r = cb.r; ba.H0 = cb.H0;
   ba.eps = &x->st->eps; ba.minv = x->minv;
+  ba.minv_every = minv_every_of(x); ba.minv_ld = x->d_pad;
   ba.jitter = jitter;
   ba.eps_iter = &x->st->eps_iter;
   ba.chain_base = fd ? 0 : x->chain_base;
@@ -708,6 +733,7 @@ pcv_status launch_iteration(pcv_ctx *x, ChainBufs &cb, bool fd, bool accumulate)
   aa.theta_p = cb.theta_p; aa.r = cb.r; aa.grad_p = cb.grad_p;
   aa.logp_p = cb.logp_p; aa.shat_p = cb.shat_p; aa.H0 = cb.H0;
   aa.minv = x->minv;
+  aa.minv_every = minv_every_of(x); aa.minv_ld = x->d_pad;
   aa.accumulate = accumulate ? 1 : 0;
   aa.acc = x->acc;
   aa.accept_prob = cb.accept_prob;
@@ -1000,7 +1026,13 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
   }
   if (K < 1) return bail(PCV_E_INVALID_ARG, "no folds");
   x->K = K;
-  x->C = K * x->L;
+  x->K_model = K;
+  x->pair = model->active_covariates_b != nullptr;
+  if (x->pair) {
+    if (opt->first_fold != 0) return bail(PCV_E_UNSUPPORTED, "two models in one context: first_fold must be 0");
+    x->K = 2 * K;     // model B's folds follow model A's
+  }
+  x->C = x->K * x->L;
   x->chain_base = opt->first_fold * x->L;
   if (x->variant == MV_HIER)
     for (int64_t i = 0; i < N; ++i)
@@ -1041,6 +1073,11 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
     const int64_t elo = std::max<int64_t>(0, lo[k] - x->h), ehi = std::min<int64_t>(N, hi[k] + x->h);
     if (N - (ehi - elo) < 1) return bail(PCV_E_INVALID_ARG, "fold " + std::to_string(k) + " has no training rows");
     fds[k] = FoldDesc{(int)lo[k], (int)hi[k], (int)elo, (int)ehi};
+  }
+  if (x->pair) {   // model B's folds: the same rows; the full-data descriptor last
+    std::vector<FoldDesc> two(fds.begin(), fds.begin() + K);
+    two.insert(two.end(), fds.begin(), fds.end());
+    fds.swap(two);
   }
   // hierarchical segments: one contiguous row run per group
   std::vector<int> seg_off, seg_grp, grp_seg;
@@ -1086,11 +1123,11 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
     hperm[r] = (int)i;
   }
   if (!dalloc_n(x, &x->X, (size_t)N * x->p_pad) || !dalloc_n(x, &x->y, (size_t)N) ||
-      !dalloc_n(x, &x->folds, (size_t)K + 1) || !dalloc_n(x, &x->minv, (size_t)x->d_pad) ||
+      !dalloc_n(x, &x->folds, (size_t)x->K + 1) || !dalloc_n(x, &x->minv, (size_t)x->d_pad * (x->pair ? 2 : 1)) ||
       !dalloc_n(x, &x->st, 1) || !dalloc_n(x, &x->wmean, (size_t)x->d) || !dalloc_n(x, &x->wM2, (size_t)x->d) ||
       !dalloc_n(x, &x->pool, (size_t)x->n_fd_draws * kNumFdChains * x->d_pad) ||
-      !dalloc_n(x, &x->fold_out, (size_t)K * F_NFIELDS) || !dalloc_n(x, &x->tot_out, (size_t)T_NFIELDS) ||
-      !dalloc_n(x, &x->fin_scratch, (size_t)K * (4 * x->L + 2 * (x->M + 2))))
+      !dalloc_n(x, &x->fold_out, (size_t)x->K * F_NFIELDS) || !dalloc_n(x, &x->tot_out, (size_t)T_NFIELDS) ||
+      !dalloc_n(x, &x->fin_scratch, (size_t)x->K * (4 * x->L + 2 * (x->M + 2))))
     return bail(PCV_E_OOM, "device allocation failed");
   {
     float *xraw = nullptr;
@@ -1170,7 +1207,27 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
     if (!dalloc_n(x, &x->active_d, (size_t)x->d_pad)) return bail(PCV_E_OOM, "device allocation failed");
     cudaMemcpyAsync(x->active_d, x->active_h.data(), sizeof(float) * x->d_pad, cudaMemcpyHostToDevice, x->stream);
   }
+  if (x->pair) {
+    // model B's mask: a subset of model A's covariates (B nested in A), so
+    // that B's inverse mass is A's adapted one restricted to B's covariates
+    x->active_b_h.assign(x->d_pad, 1.0f);
+    for (int j = 0; j < p; ++j) {
+      const int32_t a = model->active_covariates_b[j];
+      if (a != 0 && a != 1) return bail(PCV_E_INVALID_ARG, "active_covariates_b must hold 0 or 1");
+      if (a && !(x->active_h.empty() || x->active_h[j] > 0))
+        return bail(PCV_E_INVALID_ARG, "active_covariates_b must select a subset of model A's covariates");
+      x->active_b_h[j] = (float)a;
+    }
+    if (!dalloc_n(x, &x->active_b_d, (size_t)x->d_pad)) return bail(PCV_E_OOM, "device allocation failed");
+    cudaMemcpyAsync(x->active_b_d, x->active_b_h.data(), sizeof(float) * x->d_pad, cudaMemcpyHostToDevice,
+                    x->stream);
+  }
   cudaMemcpyAsync(x->minv, hm.data(), hm.size() * sizeof(float), cudaMemcpyHostToDevice, x->stream);
+  if (x->pair) {
+    std::vector<float> hb(hm);
+    for (int j = 0; j < x->d_pad; ++j) hb[j] *= x->active_b_h[j];
+    cudaMemcpyAsync(x->minv + x->d_pad, hb.data(), hb.size() * sizeof(float), cudaMemcpyHostToDevice, x->stream);
+  }
   if (x->variant == MV_HIER) {
     if (!dalloc_n(x, &x->seg_off, seg_off.size()) || !dalloc_n(x, &x->seg_grp, seg_grp.size()) ||
         !dalloc_n(x, &x->grp_seg, grp_seg.size()))
@@ -1186,7 +1243,7 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
 
   Problem &pb = x->pb;
   pb.variant = x->variant; pb.N = (int)N; pb.p = p; pb.p_pad = x->p_pad; pb.d = x->d; pb.d_pad = x->d_pad;
-  pb.G = x->G; pb.K = K; pb.X = x->X; pb.y = x->y; pb.grp_off = x->seg_off; pb.folds = x->folds;
+  pb.G = x->G; pb.K = x->K; pb.X = x->X; pb.y = x->y; pb.grp_off = x->seg_off; pb.folds = x->folds;
   pb.seg_grp = x->seg_grp; pb.grp_seg = x->grp_seg;
   pb.beta_prec = (float)(1.0 / (model->beta_prior_sd * model->beta_prior_sd));
   pb.log_beta_sd = (float)std::log(model->beta_prior_sd);
@@ -1212,7 +1269,8 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
   }
   pcv_status s;
   if ((s = alloc_chains(x, x->fold_cb, x->C, x->L, 0)) != PCV_OK) return bail(s, x->err);
-  if ((s = alloc_chains(x, x->fd_cb, kNumFdChains, kNumFdChains, K)) != PCV_OK) return bail(s, x->err);
+  // full-data chains: the fold descriptor after the last fold (no rows excluded)
+  if ((s = alloc_chains(x, x->fd_cb, kNumFdChains, kNumFdChains, x->K)) != PCV_OK) return bail(s, x->err);
   if ((s = alloc_accum(x)) != PCV_OK) return bail(s, x->err);
   if (opt->extra_scores) {
     // Hyvarinen / Dawid-Sebastiani accumulators (Gaussian models whose rows
@@ -1284,13 +1342,23 @@ pcv_status pcv_warmup(pcv_ctx *x, int32_t n_fd, int32_t n_wu) {
   // tensor-core path: centre on the mean of the full-data draws
   s = set_reference(x, x->pool, x->n_fd_draws * kNumFdChains, x->d_pad);
   if (s != PCV_OK) return s;
-  // fold chains start from full-data draws (Algorithm 1)
+  // two models: B's inverse mass from A's adaptation
+  if ((s = sync_minv_b(x)) != PCV_OK) return s;
+  // fold chains start from full-data draws (Algorithm 1); model B's chains
+  // with B's inactive coefficients at 0
   {
     const long long T = (long long)x->C * x->d;
     k_init_from_pool<<<(unsigned)((T + 255) / 256), 256, 0, x->stream>>>(
         x->C, x->d, x->d_pad, x->opt.seed, x->pool, x->n_fd_draws * kNumFdChains, x->fold_cb.theta,
         x->chain_base);
     CK(cudaGetLastError());
+    if (x->pair) {
+      const int cb = x->K_model * x->L;
+      const long long Tm = (long long)cb * x->d;
+      k_mask_positions<<<(unsigned)((Tm + 255) / 256), 256, 0, x->stream>>>(
+          cb, x->d, x->d_pad, x->active_b_d, x->fold_cb.theta + (size_t)cb * x->d_pad);
+      CK(cudaGetLastError());
+    }
   }
   s = refresh(x, x->fold_cb);
   if (s != PCV_OK) return s;
@@ -1398,7 +1466,10 @@ pcv_status pcv_set_positions(pcv_ctx *x, const double *theta, double step_size, 
     for (int j = 0; j < x->d; ++j) {
       const double v = theta[(size_t)c * x->d + j];
       if (!std::isfinite(v)) return fail(x, PCV_E_NUMERIC, "non-finite position");
-      h[(size_t)c * x->d_pad + j] = x->active_d ? (float)v * x->active_h[j] : (float)v;   // masked: held at 0
+      // masked coefficients (the chain's model's mask) are held at 0
+      const bool in_b = x->pair && c >= x->K_model * x->L;
+      const float m = in_b ? x->active_b_h[j] : x->active_d ? x->active_h[j] : 1.0f;
+      h[(size_t)c * x->d_pad + j] = (float)v * m;
     }
   CK(cudaMemcpyAsync(x->fold_cb.theta, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, x->stream));
   {
@@ -1418,6 +1489,8 @@ pcv_status pcv_set_positions(pcv_ctx *x, const double *theta, double step_size, 
       hm[j] = (float)inv_mass[j] * (x->active_d ? x->active_h[j] : 1.0f);
     }
     CK(cudaMemcpyAsync(x->minv, hm.data(), hm.size() * sizeof(float), cudaMemcpyHostToDevice, x->stream));
+    pcv_status sb = sync_minv_b(x);
+    if (sb != PCV_OK) return sb;
   }
   pcv_status s = refresh(x, x->fold_cb);
   if (s != PCV_OK) return s;
@@ -1721,7 +1794,7 @@ std::vector<Seg> ckpt_segments(pcv_ctx *x) {
   std::vector<Seg> v;
   Accum &A = x->acc;
   v.push_back({x->st, sizeof(IterState)});
-  v.push_back({x->minv, sizeof(float) * x->d_pad});
+  v.push_back({x->minv, sizeof(float) * x->d_pad * (x->pair ? 2 : 1)});
   v.push_back({x->fold_cb.theta, sizeof(float) * C * x->d_pad});
   v.push_back({x->fold_cb.grad, sizeof(float) * C * x->d_pad});
   v.push_back({x->fold_cb.logp, sizeof(double) * C});
@@ -1895,6 +1968,32 @@ pcv_status pcv_compare(pcv_ctx *a, pcv_ctx *b, double *delta_k, double *mcse_k, 
   std::memcpy(mcse_k, h.data() + K, sizeof(double) * K);
   std::memcpy(out, h.data() + 2 * K, sizeof(double) * 4);
   leave(a);
+  return PCV_OK;
+}
+
+pcv_status pcv_compare_pair(pcv_ctx *x, double *delta_k, double *mcse_k, double *out) {
+  if (!x) return PCV_E_INVALID_ARG;
+  if (!delta_k || !mcse_k || !out) return fail(x, PCV_E_INVALID_ARG, "null argument");
+  if (!x->pair) return fail(x, PCV_E_INVALID_ARG, "the context holds one model (no active_covariates_b)");
+  if (x->state != ST_SAMPLED) return fail(x, PCV_E_BAD_STATE, "pcv_compare_pair before pcv_sample");
+  enter(x);
+  pcv_status s = finalize(x);
+  if (s != PCV_OK) return s;
+  const int K = x->K_model;
+  if ((size_t)(2 * K + 4) > x->cmp_n) {
+    if (!dalloc_n(x, &x->cmp_out, (size_t)(2 * K + 4))) return fail(x, PCV_E_OOM, "allocation failed");
+    x->cmp_n = (size_t)(2 * K + 4);
+  }
+  // model A's folds [0, K), model B's [K, 2 K): the fold outputs are fold-major
+  k_compare<<<1, 256, 0, x->stream>>>(x->fold_out, x->fold_out + (size_t)K * F_NFIELDS, K, x->cmp_out);
+  CK(cudaGetLastError());
+  std::vector<double> h((size_t)(2 * K + 4));
+  CK(cudaMemcpyAsync(h.data(), x->cmp_out, h.size() * sizeof(double), cudaMemcpyDeviceToHost, x->stream));
+  CK(cudaStreamSynchronize(x->stream));
+  std::memcpy(delta_k, h.data(), sizeof(double) * K);
+  std::memcpy(mcse_k, h.data() + K, sizeof(double) * K);
+  std::memcpy(out, h.data() + 2 * K, sizeof(double) * 4);
+  leave(x);
   return PCV_OK;
 }
 

@@ -58,6 +58,13 @@ enum { MODE_NONE = 0, MODE_KICK_DRIFT = 1, MODE_LAST_KICK = 2 };
 
 // Arguments of one gradient evaluation (optionally fused with a leapfrog
 // update) for a batch of chain positions.
+// Two models in one context (covariate masks M_A, M_B; Appendix B): chains
+// [0, K L) are model A's, [K L, 2 K L) model B's, and each model has its own
+// row of the inverse mass (B's is A's with B's inactive coefficients at 0).
+__host__ __device__ inline const float *minv_row(const float *minv, int c, int every, int ld) {
+  return every > 0 ? minv + (size_t)(c / every) * ld : minv;
+}
+
 struct GradArgs {
   int C;                  // positions
   int L;                  // chains per fold (fold = fold_base + c / L) if fold_of == nullptr
@@ -73,7 +80,8 @@ struct GradArgs {
   int mode;               // MODE_NONE, MODE_KICK_DRIFT, MODE_LAST_KICK
   float *r;               // C x ld_theta momenta (updated by the modes)
   const float *eps;       // device scalar step size
-  const float *minv;      // inverse mass diagonal (d_pad)
+  const float *minv;      // inverse mass diagonal (d_pad), one row per model
+  int minv_every, minv_ld;   // chains per row and row stride (minv_every 0: one row)
   // split-N cross-CTA combine
   int splits;             // row splits per chain tile
   float *ws;              // workspace: tiles x splits x 32 x ws_stride floats
@@ -237,7 +245,8 @@ struct BeginArgs {
   const double *logp;
   float *theta_p, *r;           // proposal position and momentum (out)
   double *H0;                   // out
-  const float *eps, *minv;      // nominal step size, inverse mass
+  const float *eps, *minv;      // nominal step size, inverse mass (one row per model)
+  int minv_every, minv_ld;      // chains per inverse-mass row, row stride (0: one row)
   float jitter;                 // eps_iter = eps (1 + jitter (2u - 1)), u from stream ST_JIT
   int chain_base;               // Philox chain id = chain_base + c (global fold-chain id)
   float *eps_iter;              // out (written by block 0): the step size of this iteration
@@ -263,6 +272,7 @@ struct TrajArgs {
   float *eps_iter;              // out (chain 0): this iteration's step size
   float jitter;
   const float *minv;
+  int minv_every, minv_ld;      // chains per inverse-mass row, row stride (0: one row)
   const float *theta, *grad;    // current state
   const double *logp;
   const float *r_given;         // optional start momenta (C x ld)
@@ -306,6 +316,7 @@ struct AcceptArgs {
   const float *theta_p, *r, *grad_p;
   const double *logp_p, *shat_p, *H0;
   const float *minv;
+  int minv_every, minv_ld;         // chains per inverse-mass row, row stride (0: one row)
   int accumulate;                  // 1: sampling phase
   Accum acc;
   double *accept_prob;             // per chain, or null

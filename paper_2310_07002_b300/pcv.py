@@ -37,7 +37,8 @@ class Model(ct.Structure):
     _fields_ = [("kind", ct.c_int32), ("beta_prior_sd", ct.c_double),
                 ("sigma_known", ct.c_double), ("sigma_prior_sd", ct.c_double),
                 ("tau_prior_sd", ct.c_double), ("group", ct.c_void_p),
-                ("n_groups", ct.c_int32), ("active_covariates", ct.c_void_p)]
+                ("n_groups", ct.c_int32), ("active_covariates", ct.c_void_p),
+                ("active_covariates_b", ct.c_void_p)]
 
 
 ALLOC_FN = ct.CFUNCTYPE(ct.c_void_p, ct.c_size_t, ct.c_void_p)
@@ -92,6 +93,7 @@ def load():
         "pcv_tuning_info": (i32, [vp, ct.c_char_p, i32]),
         "pcv_rhat_shuffle": (i32, [vp, i32, i32, vp, vp]),
         "pcv_compare": (i32, [vp, vp, vp, vp, vp]),
+        "pcv_compare_pair": (i32, [vp, vp, vp, vp]),
         "pcv_scores_extra": (i32, [vp, vp, vp, vp, vp]),
         "pcv_checkpoint_size": (i32, [vp, ct.POINTER(i64)]),
         "pcv_checkpoint_save": (i32, [vp, vp, i64]),
@@ -130,7 +132,7 @@ def exported_symbols():
             "pcv_get_draws", "pcv_accept_rate", "pcv_last_sample_ms",
             "pcv_time_leapfrog_kernel", "pcv_log_density_noalloc", "pcv_tuning_info",
             "pcv_checkpoint_size", "pcv_checkpoint_save", "pcv_checkpoint_load",
-            "pcv_rhat_shuffle", "pcv_compare", "pcv_scores_extra", "pcv_setup_ms",
+            "pcv_rhat_shuffle", "pcv_compare", "pcv_compare_pair", "pcv_scores_extra", "pcv_setup_ms",
             "pcv_get_pool", "pcv_adapt_trace"]
 
 
@@ -185,7 +187,7 @@ class PCV:
                  use_graphs: bool = True, torch_allocator: bool = True,
                  trajectory_length: float = -1.0, step_jitter: float = -1.0,
                  autotune: bool = True, active=None, extra_scores: int = 0,
-                 first_fold: int = 0, fused_trajectory: int = -1):
+                 first_fold: int = 0, fused_trajectory: int = -1, active_b=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("PCV needs a CUDA device (sm_103a); none is available")
@@ -198,8 +200,11 @@ class PCV:
         N, p = X.shape
         self.N, self.p, self.L = N, p, chains_per_fold
         self._active = None if active is None else np.ascontiguousarray(active, dtype=np.int32)
+        # a second model in the same launches (a subset of the covariates):
+        # folds [K, 2K) and chains [K L, 2 K L) are its
+        self._active_b = None if active_b is None else np.ascontiguousarray(active_b, dtype=np.int32)
         m = Model(kind, beta_prior_sd, sigma_known, sigma_prior_sd, tau_prior_sd,
-                  _ptr(self._group), n_groups, _ptr(self._active))
+                  _ptr(self._group), n_groups, _ptr(self._active), _ptr(self._active_b))
         o = Options()
         L.pcv_default_options(ct.byref(o))
         o.seed = seed
@@ -345,6 +350,17 @@ class PCV:
         mk = np.empty(self.K)
         out = np.empty(4)
         self._check(self._L.pcv_compare(self.h, other.h, _ptr(dk), _ptr(mk), _ptr(out)), "pcv_compare")
+        return {"delta_k": dk, "mcse_k": mk, "delta": out[0], "se": out[1], "mcse": out[2],
+                "prob": out[3]}
+
+    def compare_pair(self):
+        """Model A (folds [0, K/2)) against model B (folds [K/2, K)) of a
+        context created with active_b: the same outputs as compare()."""
+        K = self.K // 2
+        dk = np.empty(K)
+        mk = np.empty(K)
+        out = np.empty(4)
+        self._check(self._L.pcv_compare_pair(self.h, _ptr(dk), _ptr(mk), _ptr(out)), "pcv_compare_pair")
         return {"delta_k": dk, "mcse_k": mk, "delta": out[0], "se": out[1], "mcse": out[2],
                 "prob": out[3]}
 

@@ -61,3 +61,28 @@ def test_pairwise_comparison(orc):
     # swapping the models negates the difference and complements the probability
     r = orc.compare(fb["elpd"], fb["mcse"], fa["elpd"], fa["mcse"])
     assert abs(r["delta"] + c["delta"]) < 1e-12 and abs(r["prob"] + c["prob"] - 1.0) < 1e-12
+
+
+def test_chain_base_replays_the_chains_of_a_longer_run(orc):
+    # one fold, so that chain ids and folds do not interact: a run of L0
+    # chains with chain_base = L0 is chains L0 .. 2 L0 - 1 of a run of 2 L0
+    # chains (the same Philox ids), bit for bit, from the pool start index
+    # on (Appendix B's two-model runs replay model B's chains this way)
+    w = W.gauss_blocks()
+    fold = np.where(np.arange(w.N) < 20, 0, -1).astype(np.int32)
+    w1 = dataclasses.replace(w, fold=fold, K=1)
+    prob = orc.problem_from_workload(w1)
+    L0 = 3
+    long = orc.OraclePCV(prob, 2 * L0, w.seed, w.leapfrog_steps, eps=0.05, b=5)
+    short = orc.OraclePCV(prob, L0, w.seed, w.leapfrog_steps, eps=0.05, b=5, chain_base=L0)
+    for r in (long, short):
+        r.fulldata(0, 40)
+        r.fold_warmup(0)
+    np.testing.assert_array_equal(short.state()["theta"], long.state()["theta"][L0:])
+    for r in (long, short):
+        r.sample(10)
+    a, b = long.state(), short.state()
+    np.testing.assert_array_equal(b["theta"], a["theta"][L0:])
+    np.testing.assert_array_equal(b["shat"], a["shat"][L0:])
+    # and base 0 is not base L0: the first chains of the long run differ
+    assert not np.array_equal(b["theta"], a["theta"][:L0])
