@@ -30,6 +30,9 @@ WORKLOADS = {
     # comparison measures arithmetic only
     "logistic_loo_bf16x": lambda: W.logistic_loo(bf16=True),
     "hier_logo": lambda: W.hier_logo(),
+    # config 3 with one pure-noise covariate appended (index 10; true
+    # coefficient 0): with and without it the models are close
+    "hier_logo_noise": lambda: W.hier_logo(noise_p=1),
     "ar2_hvblock": lambda: W.ar2_hvblock(),
     # lagged design rounded to bf16 values for both precisions (arithmetic only)
     "ar2_hvblock_bf16x": lambda: W.ar2_hvblock(bf16=True),
@@ -97,6 +100,46 @@ def run(w, precision: str, draws: int, fd_warmup: int, fold_warmup: int, seed: i
     return out, sc, dg
 
 
+def pair_progress(w, precision: str, draws: int, fd_warmup: int, fold_warmup: int, seed: int,
+                  drop: str, n_reports: int):
+    """Models A (all covariates) and B (without `drop`) in one context: both
+    models' chains in every launch (Appendix B's masks); after each of
+    n_reports equal parts of the draws, the comparison (eq. sel-cv,
+    norm-approx, mc-var) and the largest fold R-hat of each model."""
+    import torch
+    from . import pcv as P
+    act = np.ones(w.p, np.int32)
+    act[[int(v) for v in drop.split(",")]] = 0
+    t0 = time.perf_counter()
+    pc = P.PCV.from_workload(w, precision=P.PRECISIONS[precision], seed=seed, active_b=act)
+    pc.warmup(fd_warmup, fold_warmup)
+    torch.cuda.synchronize()
+    warm_s = time.perf_counter() - t0
+    K = pc.K // 2
+    step = max(w.batch_size, draws // n_reports // w.batch_size * w.batch_size)
+    rows, done, sample_s = [], 0, 0.0
+    while done < draws:
+        n = min(step, draws - done)
+        t1 = time.perf_counter()
+        pc.sample(n)
+        torch.cuda.synchronize()
+        sample_s += time.perf_counter() - t1
+        done += n
+        c = pc.compare_pair()
+        dg = pc.diagnostics()
+        rows.append({"draws": done, "delta": c["delta"], "se": c["se"], "mcse": c["mcse"],
+                     "prob_a_better": c["prob"], "rhat_max_a": float(np.max(dg["rhat"][:K])),
+                     "rhat_max_b": float(np.max(dg["rhat"][K:]))})
+    sc = pc.scores()
+    out = {"workload": w.name, "N": w.N, "p": w.p, "K": K, "L": w.chains_per_fold, "dropped": drop,
+           "chains_per_launch": pc.C, "precision": precision, "seed": seed, "draws": draws,
+           "fd_warmup": fd_warmup, "fold_warmup": fold_warmup,
+           "elpd_a": float(np.sum(sc["elpd"][:K])), "elpd_b": float(np.sum(sc["elpd"][K:])),
+           "warmup_s": warm_s, "sample_s": sample_s, "progress": rows}
+    pc.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="logistic_large", choices=sorted(WORKLOADS))
@@ -109,6 +152,11 @@ def main():
                     help="draws of the comparison run (default: the same)")
     ap.add_argument("--compare-fold-warmup", type=int, default=None)
     ap.add_argument("--seed", type=int, default=None)
+    ap.add_argument("--pair-drop", default=None,
+                    help="comma-separated covariate indices: run model B (without them) in the same "
+                         "launches as model A, one context, and report the comparison as sampling "
+                         "proceeds (the progressive estimate of Fig. 1)")
+    ap.add_argument("--progress", type=int, default=10, help="reports over the draws (--pair-drop)")
     ap.add_argument("--drop-covariates", default=None,
                     help="comma-separated covariate indices: also run model B without them "
                          "(Appendix B's selection mask) and report the pairwise comparison")
@@ -120,6 +168,10 @@ def main():
     fdw = args.fd_warmup or w.n_fulldata_warmup
     fow = args.fold_warmup or w.n_fold_warmup
     seed = w.seed if args.seed is None else args.seed
+    if args.pair_drop is not None:
+        print(json.dumps(pair_progress(w, args.precision, draws, fdw, fow, seed, args.pair_drop, args.progress)),
+              flush=True)
+        return
     sel = args.drop_covariates is not None
     if sel:
         a, sca, dga, pa = run(w, args.precision, draws, fdw, fow, seed, keep=True)

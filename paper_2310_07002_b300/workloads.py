@@ -150,14 +150,16 @@ def logistic_loo(N: int = 2000, p: int = 20, L: int = 8, seed: int = 1002,
 
 
 def hier_logo(G: int = 100, p: int = 10, L: int = 16, mean_extra: float = 30.0,
-              seed: int = 1003) -> Workload:
+              seed: int = 1003, noise_p: int = 0) -> Workload:
     """Varying-intercept Gaussian model, non-centred alpha_g = tau * z_g,
     group sizes 5 + Poisson(30), leave-one-group-out.  True tau, sigma, beta,
     z drawn from the priors (tau, sigma ~ half-N(0,1), beta ~ N(0, I)).
     4000 draws: with data this informative the non-centred (tau, z) posterior
     is a ridge that a diagonal mass crosses slowly (autocorrelation time ~30
     iterations), and R-hat < 1.01 in every fold needs ~100 effective draws
-    per chain."""
+    per chain.  noise_p > 0 appends that many N(0, 1) columns with true
+    coefficient 0, drawn after y (the rest of the data is unchanged): a
+    model with them and one without are close (a model-selection case)."""
     g = _rng(seed)
     sizes = 5 + g.poisson(mean_extra, G)
     group = np.repeat(np.arange(G, dtype=np.int32), sizes)
@@ -168,6 +170,9 @@ def hier_logo(G: int = 100, p: int = 10, L: int = 16, mean_extra: float = 30.0,
     sigma = abs(g.standard_normal())
     z = g.standard_normal(G)
     y = X @ beta + tau * z[group] + sigma * g.standard_normal(N)
+    if noise_p > 0:
+        X = np.hstack([X, g.standard_normal((N, noise_p))])
+        beta = np.concatenate([beta, np.zeros(noise_p)])
     X, y = _fp32(X), _fp32(y)
     return Workload("hier_logo", HIER_GAUSS, X, y, group.copy(), G, L,
                     beta_prior_sd=1.0, sigma_prior_sd=1.0, tau_prior_sd=1.0,
