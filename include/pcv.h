@@ -353,6 +353,14 @@ pcv_status pcv_compare(pcv_ctx *ctx_a, pcv_ctx *ctx_b, double *delta_k, double *
 pcv_status pcv_compare_pair(pcv_ctx *ctx, double *delta_k, double *mcse_k, double *out);
 
 /*
+ * Kernels the library's iterations (warm-up and sampling) have issued since
+ * pcv_create: each iteration graph's kernel nodes, counted at capture, times
+ * its replays (no paper counterpart; for benchmark records).  *n out.
+ * PCV_E_UNSUPPORTED when iterations ran outside CUDA graphs (use_graphs 0).
+ */
+pcv_status pcv_kernel_launches(pcv_ctx *ctx, int64_t *n);
+
+/*
  * R-hat_max benchmark (Section 4.2; the block-shuffle loop of Algorithm A2):
  * each chain's draws so far are cut into n_blocks contiguous blocks of whole
  * batches (block d holds batches [d a / D, (d+1) a / D), a batches); each of

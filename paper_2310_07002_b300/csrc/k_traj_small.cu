@@ -403,7 +403,6 @@ __device__ __forceinline__ void traj_team(const Problem &pb, const TrajArgs &t, 
 template <int PP, int MV, bool XB16>
 __global__ void __launch_bounds__(kTrajWarps * 32, PP <= 12 ? 2 : 1) k_traj_small(Problem pb, TrajArgs t) {
   extern __shared__ __align__(16) uint8_t traj_smem[];
-  constexpr bool LOGSIG = MV == MV_GAUSS_LOGSIG;
   // rows: staged into shared memory (compact, PP elements per row) when the
   // host sized it for them
   Rows<PP, XB16> R{pb.X, t.X16, pb.y, XB16 ? PP : pb.p_pad};

@@ -91,6 +91,11 @@ struct pcv_ctx {
   std::vector<double> h_fold, h_tot;
   // graphs
   cudaGraphExec_t g_sample_b = nullptr, g_fold_1 = nullptr, g_fd_1 = nullptr;
+  // kernels issued by iterations: kernel nodes of each instantiated graph,
+  // and the running count (exact while every iteration ran from a graph)
+  std::map<cudaGraphExec_t, long long> graph_kernels;
+  long long kernels_issued = 0;
+  bool kernels_exact = true;
   int fd_n_adapt = 0;
   // tensor-core path
   bool tc = false;
@@ -777,6 +782,7 @@ pcv_status run_iterations(pcv_ctx *x, ChainBufs &cb, bool fd, bool accumulate, l
                           cudaGraphExec_t *cache, int per_graph) {
   if (count <= 0) return PCV_OK;
   if (!x->opt.use_graphs) {
+    x->kernels_exact = false;          // launches outside a graph are not counted
     for (long long i = 0; i < count; ++i) {
       pcv_status s = launch_iteration(x, cb, fd, accumulate);
       if (s != PCV_OK) return s;
@@ -795,13 +801,32 @@ pcv_status run_iterations(pcv_ctx *x, ChainBufs &cb, bool fd, bool accumulate, l
     cudaError_t e = cudaStreamEndCapture(x->stream, &g);
     if (s != PCV_OK) return s;
     if (e != cudaSuccess) return fail_cuda(x, "cudaStreamEndCapture", e);
+    // the graph's kernel nodes: the kernels each replay issues
+    long long nk = 0;
+    {
+      size_t nn = 0;
+      if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+          for (size_t k = 0; k < nn; ++k) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nodes[k], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
+          }
+      }
+    }
     e = cudaGraphInstantiate(cache, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail_cuda(x, "cudaGraphInstantiate", e);
+    x->graph_kernels[*cache] = nk;
     x->capture_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
   }
   long long full = count / per_graph, rest = count - full * per_graph;
   for (long long i = 0; i < full; ++i) CK(cudaGraphLaunch(*cache, x->stream));
+  {
+    const auto it = x->graph_kernels.find(*cache);
+    if (it == x->graph_kernels.end() || (rest > 0 && it->second % per_graph != 0)) x->kernels_exact = false;
+    else x->kernels_issued += full * it->second + rest * (it->second / per_graph);
+  }
   for (long long i = 0; i < rest; ++i) {
     pcv_status s = launch_iteration(x, cb, fd, accumulate);
     if (s != PCV_OK) return s;
@@ -1968,6 +1993,13 @@ pcv_status pcv_compare(pcv_ctx *a, pcv_ctx *b, double *delta_k, double *mcse_k, 
   std::memcpy(mcse_k, h.data() + K, sizeof(double) * K);
   std::memcpy(out, h.data() + 2 * K, sizeof(double) * 4);
   leave(a);
+  return PCV_OK;
+}
+
+pcv_status pcv_kernel_launches(pcv_ctx *x, int64_t *n) {
+  if (!x || !n) return fail(x, PCV_E_INVALID_ARG, "null argument");
+  if (!x->kernels_exact) return fail(x, PCV_E_UNSUPPORTED, "iterations ran outside CUDA graphs (use_graphs = 0)");
+  *n = x->kernels_issued;
   return PCV_OK;
 }
 

@@ -94,6 +94,7 @@ def load():
         "pcv_rhat_shuffle": (i32, [vp, i32, i32, vp, vp]),
         "pcv_compare": (i32, [vp, vp, vp, vp, vp]),
         "pcv_compare_pair": (i32, [vp, vp, vp, vp]),
+        "pcv_kernel_launches": (i32, [vp, vp]),
         "pcv_scores_extra": (i32, [vp, vp, vp, vp, vp]),
         "pcv_checkpoint_size": (i32, [vp, ct.POINTER(i64)]),
         "pcv_checkpoint_save": (i32, [vp, vp, i64]),
@@ -132,7 +133,7 @@ def exported_symbols():
             "pcv_get_draws", "pcv_accept_rate", "pcv_last_sample_ms",
             "pcv_time_leapfrog_kernel", "pcv_log_density_noalloc", "pcv_tuning_info",
             "pcv_checkpoint_size", "pcv_checkpoint_save", "pcv_checkpoint_load",
-            "pcv_rhat_shuffle", "pcv_compare", "pcv_compare_pair", "pcv_scores_extra", "pcv_setup_ms",
+            "pcv_rhat_shuffle", "pcv_compare", "pcv_compare_pair", "pcv_kernel_launches", "pcv_scores_extra", "pcv_setup_ms",
             "pcv_get_pool", "pcv_adapt_trace"]
 
 
@@ -352,6 +353,12 @@ class PCV:
         self._check(self._L.pcv_compare(self.h, other.h, _ptr(dk), _ptr(mk), _ptr(out)), "pcv_compare")
         return {"delta_k": dk, "mcse_k": mk, "delta": out[0], "se": out[1], "mcse": out[2],
                 "prob": out[3]}
+
+    def kernel_launches(self) -> int:
+        """Kernels issued by the iterations so far (graph kernel nodes x replays)."""
+        n = ct.c_int64()
+        self._check(self._L.pcv_kernel_launches(self.h, ct.byref(n)), "pcv_kernel_launches")
+        return n.value
 
     def compare_pair(self):
         """Model A (folds [0, K/2)) against model B (folds [K/2, K)) of a

@@ -147,3 +147,19 @@ def test_autotuner_times_the_fused_trajectory(torch, orc):
     pc.sample(100)
     assert np.all(np.isfinite(pc.scores()["elpd"]))
     pc.close()
+
+
+@pytest.mark.parametrize("fused", [0, 1])
+def test_kernel_launch_count(torch, fused):
+    # the library's count of kernels issued by its iterations: one launch
+    # per iteration on the fused path (trajectory, accept, accumulators),
+    # k_begin + L_f gradient launches + k_accept on the separate one
+    from paper_2310_07002_b300.pcv import PCV
+    w = W.gauss_blocks()
+    pc = PCV.from_workload(w, batch_size=10, fused_trajectory=fused)
+    pc.warmup(20, 10)
+    n0 = pc.kernel_launches()
+    pc.sample(30)
+    n = pc.kernel_launches() - n0
+    pc.close()
+    assert n == 30 * (1 if fused else w.leapfrog_steps + 2), n
