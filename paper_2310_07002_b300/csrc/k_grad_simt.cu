@@ -222,18 +222,6 @@ __global__ void __launch_bounds__(kWarps * 32) k_grad_flat(Problem pb, GradArgs 
 // (ws_stride = d_pad + 4; slot d_pad / d_pad+1 = ll_tr / ll_te); z slots are
 // written only for the groups the CTA owns.  The finishing CTA sums the
 // shared slots over splits and takes each z slot from its owner split.
-// ---------------------------------------------------------------------------
-// log N(e | 0, s^2 I + t^2 1 1') of a group of m rows with residuals e
-// (intercept integrated out), from S1 = sum e and S2 = sum e^2:
-//   det = s^(2(m-1)) (s^2 + m t^2),
-//   e' inv e = (S2 - t^2 S1^2 / (s^2 + m t^2)) / s^2
-__device__ __forceinline__ double new_group_log_pred(float S1, float S2, int m, float logsig, float logtau) {
-  const double s2 = exp(2.0 * (double)logsig), t2 = exp(2.0 * (double)logtau);
-  const double den = s2 + (double)m * t2;
-  const double q = ((double)S2 - t2 * (double)S1 * (double)S1 / den) / s2;
-  return -0.5 * (double)m * kLog2PiD - 0.5 * ((double)(m - 1) * log(s2) + log(den)) - 0.5 * q;
-}
-
 template <int PP>
 __global__ void __launch_bounds__(kWarps * 32) k_grad_hier(Problem pb, GradArgs a) {
   constexpr int S = PP + 4;        // beta grads, dlogtau, dlogsig, ll_tr, ll_te

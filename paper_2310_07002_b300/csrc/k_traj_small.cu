@@ -229,6 +229,32 @@ __device__ __forceinline__ void evaluate(const Problem &pb, const Rows<PP, XB16>
   }
 }
 
+// Accept mode, after the Metropolis test (the positions and gradients are
+// written by the caller): the chain's log densities on acceptance, its
+// acceptance statistic, and the draw's held-out value into the online
+// accumulators (as k_accept).  One warp.
+__device__ __forceinline__ void accept_tail(const TrajArgs &t, int c, int lane, bool acc, bool div, bool finite,
+                                            double dH, double logp1, double ll_te) {
+  const double s_draw = acc ? ll_te : t.shat_w[c];
+  if (lane == 0) {
+    if (acc) {
+      t.logp_w[c] = logp1;
+      t.shat_w[c] = ll_te;
+    }
+    if (t.accept_prob) t.accept_prob[c] = finite ? (dH <= 0.0 ? 1.0 : exp(-dH)) : 0.0;
+  }
+  if (t.accumulate) {
+    const long long n_before = t.st->n_draws;
+    accum_lags(t.acc, c, acov_x(t.acc, c, s_draw, n_before), n_before, lane);
+    if (lane == 0) {
+      t.acc.div[c] += div ? 1 : 0;
+      t.acc.acc[c] += acc ? 1 : 0;
+      accum_scalar(t.acc, c, s_draw, n_before);
+      if (t.acc.draws && n_before < t.acc.draw_cap) t.acc.draws[(size_t)c * t.acc.draw_cap + n_before] = s_draw;
+    }
+  }
+}
+
 // One chain's trajectory (and, in accept mode, its Metropolis test and
 // accumulators), carried by its team of warps.
 template <int PP, int MV, bool XB16>
@@ -380,22 +406,28 @@ __device__ __forceinline__ void traj_team(const Problem &pb, const TrajArgs &t, 
       if (j < p && lane == (j & 31)) { thw[j] = th[j]; gw[j] = g[j]; }
     if (LOGSIG && lane == (p & 31)) { thw[p] = ls; gw[p] = gls; }
   }
-  const double s_draw = acc ? ll_te : t.shat_w[c];
-  if (lane == 0) {
-    if (acc) {
-      t.logp_w[c] = logp1;
-      t.shat_w[c] = ll_te;
-    }
-    if (t.accept_prob) t.accept_prob[c] = finite ? (dH <= 0.0 ? 1.0 : exp(-dH)) : 0.0;
+  accept_tail(t, c, lane, acc, div, finite, dH, logp1, ll_te);
+}
+
+// Accept mode, at the end of the kernel (every thread of the CTA): once all
+// teams of this CTA are done, the last CTA advances the iteration counters
+// (every CTA has read them by now).
+__device__ __forceinline__ void advance_counters(const TrajArgs &t) {
+  __shared__ int is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(&t.st->ticket, 1u);
+    is_last = prev == gridDim.x - 1;
   }
-  if (t.accumulate) {
-    const long long n_before = t.st->n_draws;
-    accum_lags(t.acc, c, acov_x(t.acc, c, s_draw, n_before), n_before, lane);
-    if (lane == 0) {
-      t.acc.div[c] += div ? 1 : 0;
-      t.acc.acc[c] += acc ? 1 : 0;
-      accum_scalar(t.acc, c, s_draw, n_before);
-      if (t.acc.draws && n_before < t.acc.draw_cap) t.acc.draws[(size_t)c * t.acc.draw_cap + n_before] = s_draw;
+  __syncthreads();
+  if (is_last && threadIdx.x == 0) {
+    __threadfence();
+    t.st->ticket = 0u;
+    if (t.fd) t.st->fd_iter += 1u;
+    else {
+      t.st->iter += 1u;
+      if (t.accumulate) t.st->n_draws += 1;
     }
   }
 }
@@ -446,26 +478,312 @@ __global__ void __launch_bounds__(kTrajWarps * 32, PP <= 12 ? 2 : 1) k_traj_smal
   // a team past the last chain does nothing, but (accept mode) still meets
   // the CTA barrier at the end
   if (c < t.C) traj_team<PP, MV, XB16>(pb, t, R, tm, c);
-  if (!t.accept) return;
-  // all teams of this CTA are done; the last CTA advances the counters
-  // (every CTA has read them by now)
-  __shared__ int is_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned prev = atomicAdd(&t.st->ticket, 1u);
-    is_last = prev == gridDim.x - 1;
+  if (t.accept) advance_counters(t);
+}
+
+// ---------------------------------------------------------------------------
+// The hierarchical model in one launch per iteration (varying intercepts,
+// non-centred alpha_g = tau z_g; theta = [beta (p), z (G), log tau,
+// log sigma]): one warp per chain.  beta, log tau and log sigma live in
+// every lane's registers (every lane applies the same update to them); z,
+// its momentum and its gradient live in the chain's slice of shared memory.
+// Rows are sorted by group, so lane l owns the row segments l, l + 32, ...
+// (one group each): the sums for d/dz_g need no atomics, and a group's z is
+// read, kicked and drifted by its own lane only (no barrier between steps).
+// The gradient and the log densities are those of k_grad_hier with
+// finish_chain<MV_HIER>: a training row adds e x / sigma^2 to beta's
+// gradient, e / sigma^2 to its segment's sum seg_g (d/dz_g = tau seg_g,
+// d/dlog tau = sum_g seg_g tau z_g) and e^2 / sigma^2 - 1 to d/dlog sigma;
+// a group held out by the fold is scored by the group-level predictive with
+// its intercept integrated out.
+// ---------------------------------------------------------------------------
+template <int PP, bool LL>
+__device__ __forceinline__ void eval_hier(const Problem &pb, const Rows<PP, false> &R, const FoldDesc &fd,
+                                          int lane, const float (&bt)[PP], float lt, float ls, const float *zs,
+                                          float *gz, float (&g)[PP], float &glt, float &gls, double &ll_tr,
+                                          double &ll_te) {
+  const int p = pb.p, G = pb.G;
+  const float tau = expf(lt), inv_s2 = expf(-2.0f * ls);
+  float acc[PP];
+#pragma unroll
+  for (int j = 0; j < PP; ++j) acc[j] = 0.0f;
+  float dls = 0.0f, dlt = 0.0f, llt = 0.0f;
+  double lte = 0.0;
+  for (int gg = lane; gg < G; gg += 32) {
+    const int gid = __ldg(pb.seg_grp + gg);
+    const float z = zs[gid], off = tau * z;
+    const int n0 = __ldg(pb.grp_off + gg), n1 = __ldg(pb.grp_off + gg + 1);
+    const bool test_seg = LL && n1 > n0 && n0 >= fd.test_lo && n1 <= fd.test_hi;
+    float seg = 0.0f, s1 = 0.0f, s2 = 0.0f;
+    auto row = [&](const float (&x)[PP], float yv, int n) {
+      float eta = off;
+#pragma unroll
+      for (int j = 0; j < PP; ++j) eta = fmaf(bt[j], x[j], eta);
+      const float e = yv - eta;
+      const float tr = (n < fd.excl_lo || n >= fd.excl_hi) ? 1.0f : 0.0f;
+      const float wv = e * inv_s2 * tr;
+#pragma unroll
+      for (int j = 0; j < PP; ++j) acc[j] = fmaf(wv, x[j], acc[j]);
+      seg += wv;
+      dls = fmaf(tr, e * e * inv_s2 - 1.0f, dls);
+      if (LL) {
+        llt = fmaf(tr, -0.5f * kLog2Pi - ls - 0.5f * e * e * inv_s2, llt);
+        if (test_seg) {
+          const float e0 = e + off;
+          s1 += e0;
+          s2 = fmaf(e0, e0, s2);
+        }
+      }
+    };
+    // several rows per pass, their loads issued before any arithmetic
+    constexpr int U = PP <= 8 ? 4 : PP <= 16 ? 3 : 2;
+    int n = n0;
+    for (; n + U <= n1; n += U) {
+      float x[U][PP], yv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        R.load(n + u, x[u]);
+        yv[u] = R.y[n + u];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) row(x[u], yv[u], n + u);
+    }
+    for (; n < n1; ++n) {
+      float x[PP];
+      R.load(n, x);
+      row(x, R.y[n], n);
+    }
+    if (test_seg) lte += new_group_log_pred(s1, s2, n1 - n0, ls, lt);
+    gz[gid] = tau * seg - z;                        // the likelihood's, then z_g ~ N(0, 1)
+    dlt = fmaf(seg, off, dlt);
   }
-  __syncthreads();
-  if (is_last && threadIdx.x == 0) {
-    __threadfence();
-    t.st->ticket = 0u;
-    if (t.fd) t.st->fd_iter += 1u;
-    else {
-      t.st->iter += 1u;
-      if (t.accumulate) t.st->n_draws += 1;
+#pragma unroll
+  for (int j = 0; j < PP; ++j) g[j] = j < p ? warp_sum(acc[j]) - bt[j] * pb.beta_prec : 0.0f;
+  dls = warp_sum(dls);
+  dlt = warp_sum(dlt);
+  glt = dlt - __expf(2.0f * lt) * pb.tau_prec + 1.0f;   // tau ~ half-N, with the log-Jacobian
+  gls = dls - __expf(2.0f * ls) * pb.sigma_prec + 1.0f; // sigma ~ half-N, with the log-Jacobian
+  if (LL) {
+    ll_tr = warp_sum_d((double)llt);
+    ll_te = warp_sum_d(lte);
+  }
+}
+
+// One chain's trajectory of the hierarchical model (and, in accept mode,
+// its Metropolis test and accumulators); zsh: the chain's shared-memory
+// slice [z (G) | momentum (G) | gradient (G) | normals (d_pad)].
+template <int PP>
+__device__ __forceinline__ void traj_hier(const Problem &pb, const TrajArgs &t, const Rows<PP, false> &R, int c,
+                                          int lane, float *zsh) {
+  const int p = pb.p, G = pb.G, d = pb.d;
+  const int jt = p + G, js = p + G + 1;            // log tau, log sigma
+  float *zs = zsh, *rz = zsh + G, *gz = rz + G, *nrm = gz + G;
+  const unsigned it = *t.iter;
+  float eps = *t.eps;
+  if (t.jitter > 0.0f) {
+    const uint4 w = philox_at(t.seed, 0u, 0u, it, ST_JIT);
+    eps = (float)((double)eps * (1.0 + (double)t.jitter * (2.0 * unit_from_word(w.x) - 1.0)));
+  }
+  if (!t.eval_only && c == 0 && lane == 0 && t.eps_iter) *t.eps_iter = eps;
+  const FoldDesc fd = pb.folds[t.fold_base + c / t.L];
+  const float *mvr = minv_row(t.minv, c, t.minv_every, t.minv_ld);
+  const float *th0 = t.theta + (size_t)c * t.ld;
+  float bt[PP], rb[PP], g[PP];
+#pragma unroll
+  for (int j = 0; j < PP; ++j) { bt[j] = j < p ? th0[j] : 0.0f; rb[j] = 0.0f; }
+  float lt = th0[jt], ls = th0[js], rlt = 0.0f, rls = 0.0f, glt = 0.0f, gls = 0.0f;
+  for (int gg = lane; gg < G; gg += 32) {          // each lane its own groups' z
+    const int gid = __ldg(pb.seg_grp + gg);
+    zs[gid] = th0[p + gid];
+  }
+  double ll_tr = 0.0, ll_te = 0.0, H0 = 0.0;
+  if (t.eval_only) {
+    eval_hier<PP, true>(pb, R, fd, lane, bt, lt, ls, zs, gz, g, glt, gls, ll_tr, ll_te);
+  } else {
+    // momentum: the normals of coordinate quad q (Philox block q, as
+    // k_begin) drawn by lane q mod 32 into shared memory, read by the
+    // coordinate's lane; kinetic energy in FP64, first half kick and drift
+    if (!t.r_given) {
+      for (int q = lane; q < (d + 3) / 4; q += 32) {
+        const uint4 w = philox_at(t.seed, (uint32_t)q, (uint32_t)(t.chain_base + c), it, t.stream);
+        const float2 a0 = box_muller(w.x, w.y), a1 = box_muller(w.z, w.w);
+        nrm[4 * q] = a0.x; nrm[4 * q + 1] = a0.y; nrm[4 * q + 2] = a1.x; nrm[4 * q + 3] = a1.y;
+      }
+      __syncwarp();
+    }
+    const float *g0 = t.grad + (size_t)c * t.ld;
+    auto start = [&](int j, float v, float &tn, float &rh) -> float {
+      const float m = mvr[j];
+      const float r0 = t.r_given ? t.r_given[(size_t)c * t.ld + j] : (m > 0.0f ? nrm[j] / sqrtf(m) : 0.0f);
+      rh = r0 + 0.5f * eps * g0[j];
+      tn = v + eps * m * rh;
+      return m * r0 * r0;
+    };
+    float kterm = 0.0f;     // this lane's kinetic-energy terms
+#pragma unroll
+    for (int j = 0; j < PP; ++j)
+      if (j < p) {
+        float tn, rh;
+        const float k = start(j, bt[j], tn, rh);
+        bt[j] = tn;
+        rb[j] = rh;
+        if (lane == (j & 31)) kterm += k;
+      }
+    {
+      float tn, rh;
+      const float k = start(jt, lt, tn, rh);
+      lt = tn;
+      rlt = rh;
+      if (lane == (jt & 31)) kterm += k;
+    }
+    {
+      float tn, rh;
+      const float k = start(js, ls, tn, rh);
+      ls = tn;
+      rls = rh;
+      if (lane == (js & 31)) kterm += k;
+    }
+    for (int gg = lane; gg < G; gg += 32) {
+      const int gid = __ldg(pb.seg_grp + gg);
+      float tn, rh;
+      kterm += start(p + gid, zs[gid], tn, rh);
+      zs[gid] = tn;
+      rz[gid] = rh;
+    }
+    H0 = -t.logp[c] + 0.5 * warp_sum_d((double)kterm);
+    if (!t.accept && lane == 0) t.H0[c] = H0;
+    for (int s = 1; s <= t.Lf; ++s) {
+      const bool last = s == t.Lf;
+      if (last) eval_hier<PP, true>(pb, R, fd, lane, bt, lt, ls, zs, gz, g, glt, gls, ll_tr, ll_te);
+      else eval_hier<PP, false>(pb, R, fd, lane, bt, lt, ls, zs, gz, g, glt, gls, ll_tr, ll_te);
+      const float kick = last ? 0.5f * eps : eps;
+#pragma unroll
+      for (int j = 0; j < PP; ++j)
+        if (j < p) {
+          rb[j] += kick * g[j];
+          if (!last) bt[j] += eps * mvr[j] * rb[j];
+        }
+      rlt += kick * glt;
+      rls += kick * gls;
+      if (!last) {
+        lt += eps * mvr[jt] * rlt;
+        ls += eps * mvr[js] * rls;
+      }
+      for (int gg = lane; gg < G; gg += 32) {
+        const int gid = __ldg(pb.seg_grp + gg);
+        rz[gid] += kick * gz[gid];
+        if (!last) zs[gid] += eps * mvr[p + gid] * rz[gid];
+      }
     }
   }
+  // log prior (finish_chain<MV_HIER>'s terms): this lane's coordinates in
+  // FP32, summed across lanes in FP64
+  float lpt = 0.0f;
+#pragma unroll
+  for (int j = 0; j < PP; ++j)
+    if (j < p && lane == (j & 31)) lpt += -0.5f * kLog2Pi - pb.log_beta_sd - 0.5f * bt[j] * bt[j] * pb.beta_prec;
+  for (int gg = lane; gg < G; gg += 32) {
+    const float z = zs[__ldg(pb.seg_grp + gg)];
+    lpt += -0.5f * kLog2Pi - 0.5f * z * z;
+  }
+  if (lane == (jt & 31))
+    lpt += (float)kLog2D - 0.5f * kLog2Pi - pb.log_tau_sd - 0.5f * __expf(2.0f * lt) * pb.tau_prec + lt;
+  if (lane == (js & 31))
+    lpt += (float)kLog2D - 0.5f * kLog2Pi - pb.log_sigma_sd - 0.5f * __expf(2.0f * ls) * pb.sigma_prec + ls;
+  const double logp1 = ll_tr + warp_sum_d((double)lpt);
+  // every coordinate of a state out: beta, log tau, log sigma by lane j mod
+  // 32, each z by its group's lane
+  auto put = [&](float *th_o, float *r_o, float *g_o) {
+    float *tho = th_o ? th_o + (size_t)c * t.ld : nullptr, *ro = r_o ? r_o + (size_t)c * t.ld : nullptr;
+    float *go = g_o + (size_t)c * t.ld;
+#pragma unroll
+    for (int j = 0; j < PP; ++j)
+      if (j < p && lane == (j & 31)) {
+        if (tho) tho[j] = bt[j];
+        if (ro) ro[j] = rb[j];
+        go[j] = g[j];
+      }
+    if (lane == (jt & 31)) {
+      if (tho) tho[jt] = lt;
+      if (ro) ro[jt] = rlt;
+      go[jt] = glt;
+    }
+    if (lane == (js & 31)) {
+      if (tho) tho[js] = ls;
+      if (ro) ro[js] = rls;
+      go[js] = gls;
+    }
+    for (int gg = lane; gg < G; gg += 32) {
+      const int gid = __ldg(pb.seg_grp + gg);
+      if (tho) tho[p + gid] = zs[gid];
+      if (ro) ro[p + gid] = rz[gid];
+      go[p + gid] = gz[gid];
+    }
+  };
+  if (!t.accept) {
+    if (t.eval_only) put(nullptr, nullptr, t.grad_p);
+    else put(t.theta_p, t.r, t.grad_p);
+    if (lane == 0) {
+      t.logp_p[c] = logp1;
+      t.shat_p[c] = ll_te;
+    }
+    return;
+  }
+  // accept mode: the Metropolis test in FP64 (as k_accept)
+  float kt = 0.0f;
+#pragma unroll
+  for (int j = 0; j < PP; ++j)
+    if (j < p && lane == (j & 31)) kt = fmaf(mvr[j] * rb[j], rb[j], kt);
+  if (lane == (jt & 31)) kt = fmaf(mvr[jt] * rlt, rlt, kt);
+  if (lane == (js & 31)) kt = fmaf(mvr[js] * rls, rls, kt);
+  for (int gg = lane; gg < G; gg += 32) {
+    const int gid = __ldg(pb.seg_grp + gg);
+    kt = fmaf(mvr[p + gid] * rz[gid], rz[gid], kt);
+  }
+  const double H1 = -logp1 + 0.5 * warp_sum_d((double)kt);
+  const double dH = H1 - H0;
+  const bool finite = isfinite(H1) && isfinite(dH);
+  double lu = 0.0;
+  if (lane == 0) {
+    const uint4 w = philox_at(t.seed, 0u, (uint32_t)(t.chain_base + c), it, t.acc_stream);
+    lu = log(unit_from_word(w.x));
+  }
+  lu = __shfl_sync(0xffffffffu, lu, 0);
+  const bool acc = finite && (lu < -dH);
+  const bool div = !finite || dH > 1000.0;
+  if (acc) put(t.theta_w, nullptr, t.grad_w);
+  accept_tail(t, c, lane, acc, div, finite, dH, logp1, ll_te);
+}
+
+// Every chain reads every row at every step, so the CTA first copies X (PP
+// columns per row) and y into shared memory when they fit beside the
+// chains' slices (t.smem_rows; t.part_offset: bytes of the staged rows);
+// the warps of a CTA (blockDim.x / 32, up to hier_warps_max(PP): 16 where
+// the registers of a wider row would not fit) are its chains.
+constexpr int hier_warps_max(int PP) { return PP <= 12 ? 16 : 8; }
+
+template <int PP>
+__global__ void __launch_bounds__(hier_warps_max(PP) * 32) k_traj_hier(Problem pb, TrajArgs t) {
+  extern __shared__ __align__(16) uint8_t hier_smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  Rows<PP, false> R{pb.X, nullptr, pb.y, pb.p_pad};
+  if (t.smem_rows) {
+    float *xs = reinterpret_cast<float *>(hier_smem);
+    for (int i = threadIdx.x; i < pb.N * PP; i += blockDim.x) {
+      const int n = i / PP, q = i - n * PP;
+      xs[i] = __ldg(pb.X + (size_t)n * pb.p_pad + q);
+    }
+    float *ys = xs + (size_t)pb.N * PP;
+    for (int i = threadIdx.x; i < pb.N; i += blockDim.x) ys[i] = __ldg(pb.y + i);
+    __syncthreads();
+    R.X = xs;
+    R.y = ys;
+    R.stride = PP;
+  }
+  float *zsh = reinterpret_cast<float *>(hier_smem + t.part_offset) + (size_t)warp * (3 * pb.G + pb.d_pad);
+  const int c = blockIdx.x * nw + warp;
+  if (c < t.C) traj_hier<PP>(pb, t, R, c, lane, zsh);
+  if (t.accept) advance_counters(t);
 }
 
 // which register width PP serves p (p <= 32)
@@ -481,9 +799,22 @@ static int traj_pp(int p) {
   return -1;
 }
 
-bool traj_small_supported(const Problem &pb) {
-  return pb.variant != MV_HIER && traj_pp(pb.p) > 0 && pb.p_pad >= traj_pp(pb.p) && pb.p_pad % 4 == 0;
+// shared memory of the hierarchical kernel per chain: z, its momentum and
+// gradient (G each) and the normals (d_pad)
+static size_t traj_hier_slice(const Problem &pb) {
+  return (3 * (size_t)pb.G + (size_t)pb.d_pad) * sizeof(float);
 }
+static size_t traj_hier_smem(const Problem &pb) { return (size_t)kTrajWarps * traj_hier_slice(pb); }
+constexpr size_t kHierSmemMax = 227 * 1024 - 1024;   // opt-in shared memory per CTA, less the static part
+
+bool traj_small_supported(const Problem &pb) {
+  const bool rows = traj_pp(pb.p) > 0 && pb.p_pad >= traj_pp(pb.p) && pb.p_pad % 4 == 0;
+  if (pb.variant == MV_HIER) return rows && traj_hier_smem(pb) <= kTrajSmemMax;
+  return rows;
+}
+
+// the hierarchical kernel runs one warp per chain
+int traj_max_wpc(const Problem &pb) { return pb.variant == MV_HIER ? 1 : 8; }
 
 int traj_small_row_width(int p) { return traj_pp(p); }
 
@@ -522,6 +853,30 @@ static cudaError_t launch_one(const Problem &pb, TrajArgs t, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int PP>
+static cudaError_t launch_hier(const Problem &pb, TrajArgs t, cudaStream_t st) {
+  static bool attr_set = false;
+  if (t.wpc != 1 || t.X16) return cudaErrorInvalidValue;
+  // warps (chains) per CTA: enough for one wave over the 148 SMs, at most 16
+  int nw = (int)std::min<long long>(hier_warps_max(PP), std::max<long long>(1, ((long long)t.C + 147) / 148));
+  const size_t rows = ((size_t)pb.N * PP * sizeof(float) + (size_t)pb.N * sizeof(float) + 15) / 16 * 16;
+  const size_t slice = traj_hier_slice(pb);
+  t.smem_rows = rows + (size_t)nw * slice <= kHierSmemMax ? 1 : 0;
+  if (!t.smem_rows) nw = kTrajWarps;          // rows from global memory: 8 chains per CTA
+  t.part_offset = t.smem_rows ? (int)rows : 0;
+  const size_t smem = (size_t)t.part_offset + (size_t)nw * slice;
+  if (smem > kHierSmemMax) return cudaErrorInvalidValue;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_traj_hier<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kHierSmemMax);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int grid = (t.C + nw - 1) / nw;
+  k_traj_hier<PP><<<grid, nw * 32, smem, st>>>(pb, t);
+  return cudaGetLastError();
+}
+
 template <int MV, bool XB16>
 static cudaError_t launch_mv(const Problem &pb, const TrajArgs &t, cudaStream_t st) {
   switch (traj_pp(pb.p)) {
@@ -544,6 +899,18 @@ cudaError_t launch_traj_small(const Problem &pb, const TrajArgs &t, cudaStream_t
     case MV_GAUSS_KNOWN: return b16 ? launch_mv<MV_GAUSS_KNOWN, true>(pb, t, st) : launch_mv<MV_GAUSS_KNOWN, false>(pb, t, st);
     case MV_GAUSS_LOGSIG: return b16 ? launch_mv<MV_GAUSS_LOGSIG, true>(pb, t, st) : launch_mv<MV_GAUSS_LOGSIG, false>(pb, t, st);
     case MV_LOGISTIC: return b16 ? launch_mv<MV_LOGISTIC, true>(pb, t, st) : launch_mv<MV_LOGISTIC, false>(pb, t, st);
+    case MV_HIER:
+      switch (traj_pp(pb.p)) {
+        case 2: return launch_hier<2>(pb, t, st);
+        case 4: return launch_hier<4>(pb, t, st);
+        case 6: return launch_hier<6>(pb, t, st);
+        case 8: return launch_hier<8>(pb, t, st);
+        case 12: return launch_hier<12>(pb, t, st);
+        case 16: return launch_hier<16>(pb, t, st);
+        case 24: return launch_hier<24>(pb, t, st);
+        case 32: return launch_hier<32>(pb, t, st);
+        default: return cudaErrorInvalidValue;
+      }
     default: return cudaErrorInvalidValue;
   }
 }

@@ -446,10 +446,11 @@ pcv_status launch_grad(pcv_ctx *x, GradArgs a, const ChainBufs *cb = nullptr) {
 // a chain count, small problems (rows x register width <= 32 Ki) take it.
 int fused_for(const pcv_ctx *x, int C) {
   if (!x->traj_ok) return 0;
-  if (x->opt.fused_trajectory > 0) return x->opt.fused_trajectory;
+  const int wmax = traj_max_wpc(x->pb);           // the hierarchical kernel: one warp per chain
+  if (x->opt.fused_trajectory > 0) return std::min(x->opt.fused_trajectory, wmax);
   auto it = x->tuned_fused.find(C);
   if (it != x->tuned_fused.end()) return it->second;
-  return x->N * (int64_t)traj_small_row_width(x->p) <= 32768 ? traj_default_wpc(C) : 0;
+  return x->N * (int64_t)traj_small_row_width(x->p) <= 32768 ? std::min(traj_default_wpc(C), wmax) : 0;
 }
 
 TrajArgs traj_args(pcv_ctx *x, ChainBufs &cb, bool fd, const float *r_given, float jitter, int wpc) {
@@ -538,6 +539,7 @@ pcv_status tune_fused(pcv_ctx *x, ChainBufs &cb) {
   int best = 0;
   std::string log = "trajectory for " + std::to_string(C) + " chains:";
   for (int f : cand) {
+    if (f > traj_max_wpc(x->pb)) continue;
     float ms = 0.0f;
     pcv_status s = launch_proposal(x, cb, fd, nullptr, 0.0f, f);
     if (s == PCV_OK) s = cudaEventRecord(e0, x->stream) == cudaSuccess ? PCV_OK : PCV_E_CUDA;

@@ -195,6 +195,18 @@ constexpr float kLog2Pi = 1.8378770664093453f;
 constexpr double kLog2PiD = 1.8378770664093454835606594728112;
 constexpr double kLog2D = 0.69314718055994530942;
 
+// The hierarchical model's held-out group (leave-one-group-out):
+// log N(e | 0, s^2 I + t^2 1 1') of a group of m rows with residuals e
+// (intercept integrated out), from S1 = sum e and S2 = sum e^2:
+//   det = s^(2(m-1)) (s^2 + m t^2),
+//   e' inv e = (S2 - t^2 S1^2 / (s^2 + m t^2)) / s^2
+__device__ __forceinline__ double new_group_log_pred(float S1, float S2, int m, float logsig, float logtau) {
+  const double s2 = exp(2.0 * (double)logsig), t2 = exp(2.0 * (double)logtau);
+  const double den = s2 + (double)m * t2;
+  const double q = ((double)S2 - t2 * (double)S1 * (double)S1 / den) / s2;
+  return -0.5 * (double)m * kLog2PiD - 0.5 * ((double)(m - 1) * log(s2) + log(den)) - 0.5 * q;
+}
+
 // tensor-core path (k_grad_tc.cu)
 // workspace rows per tile segment beyond the PN gradient rows: per
 // warpgroup the training and test softplus sums, each as an FP32 hi + lo pair
@@ -299,6 +311,7 @@ struct TrajArgs {
   double *logp_w, *shat_w;
 };
 int traj_default_wpc(int C);
+int traj_max_wpc(const Problem &pb);
 bool traj_small_supported(const Problem &pb);
 int traj_small_row_width(int p);
 cudaError_t launch_traj_small(const Problem &pb, const TrajArgs &t, cudaStream_t st);

@@ -49,14 +49,19 @@ def cases():
         # log sigma sampled at p = 32 (the widest register tile)
         "gauss_p32": dataclasses.replace(W.gauss_blocks(N=203, p=32, K=15, L=5, bf16=True),
                                          sigma_known=-1.0, sigma_prior_sd=1.0),
+        # hierarchical, leave-one-group-out: 37 groups (segments l, l + 32
+        # for lanes 0 .. 4), 74 chains (9 full CTAs of 8 warps + 2)
+        "hier": W.hier_logo(G=37, p=6, L=2),
     }
 
 
 @pytest.mark.parametrize("wpc", [1, 8])
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
-@pytest.mark.parametrize("name", ["gauss", "logistic", "ar2", "gauss_p32"])
+@pytest.mark.parametrize("name", ["gauss", "logistic", "ar2", "gauss_p32", "hier"])
 def test_fused_trajectory_and_evaluation(torch, orc, name, precision, wpc):
     from paper_2310_07002_b300.pcv import PCV, PRECISIONS
+    if name == "hier" and precision == "bf16":
+        pytest.skip("the hierarchical model has the FP32 form only")
     P = PRECISIONS[precision]
     w = cases()[name]
     prob = orc.problem_from_workload(w)
@@ -163,3 +168,49 @@ def test_kernel_launch_count(torch, fused):
     n = pc.kernel_launches() - n0
     pc.close()
     assert n == 30 * (1 if fused else w.leapfrog_steps + 2), n
+
+
+def test_fused_hierarchical_follows_oracle_paths(torch, orc):
+    # one warp per chain (z in shared memory, lanes owning whole groups):
+    # 20 iterations on the same Philox streams as the oracle
+    from paper_2310_07002_b300.pcv import PCV
+    w = W.hier_logo(G=37, p=6, L=2)
+    prob = orc.problem_from_workload(w)
+    th0 = np.zeros((w.n_chains, w.dim))
+    th0[:, :w.p] = w.truth["beta"]
+    th0 += 0.05 * W.random_theta(w.dim, w.n_chains, scale=1.0, seed=17)
+    th0 = th0.astype(np.float32).astype(np.float64)
+    pc = PCV.from_workload(w, step_size=0.02, batch_size=10, acov_max_lag=5, fused_trajectory=1)
+    pc.set_positions(th0, step_size=0.02)
+    pc.sample(20)
+    th_gpu, _, sh_gpu = pc.positions()
+    pc.close()
+    run = orc.OraclePCV(prob, w.chains_per_fold, w.seed, w.leapfrog_steps, eps=0.02, b=10, M=5)
+    run.set_state(th0, eps=0.02)
+    run.sample(20)
+    st = run.state()
+    err = rel_vec(th_gpu, st["theta"])
+    assert np.mean(err < 1e-3) >= 0.9, np.sort(err)[-10:]
+    ok = err < 1e-3
+    assert rel_scalar(sh_gpu[ok], st["shat"][ok]).max() < 1e-3
+
+
+def test_fused_hierarchical_one_launch_per_iteration(torch):
+    # config 3's model runs each iteration as one launch, and the fused and
+    # separate paths follow the same chains
+    from paper_2310_07002_b300.pcv import PCV
+    w = W.hier_logo(G=37, p=6, L=2)
+    th0 = np.zeros((w.n_chains, w.dim))
+    th0[:, :w.p] = w.truth["beta"]
+    th0 += 0.05 * W.random_theta(w.dim, w.n_chains, scale=1.0, seed=19)
+    out = {}
+    for f in (0, 1):
+        pc = PCV.from_workload(w, step_size=0.02, batch_size=10, fused_trajectory=f)
+        pc.set_positions(th0, step_size=0.02)
+        n0 = pc.kernel_launches()
+        pc.sample(20)
+        assert pc.kernel_launches() - n0 == 20 * (1 if f else w.leapfrog_steps + 2)
+        out[f] = pc.positions()[0]
+        pc.close()
+    err = rel_vec(out[1], out[0])
+    assert np.mean(err < 1e-4) >= 0.9, np.sort(err)[-5:]
