@@ -9,7 +9,10 @@
 //   Appendix B), each followed by its kick and drift, the last one by the
 //   final half kick and the log densities log pi_k(theta') and
 //   s_k(theta') = sum over the fold's test rows of log p(y_n | theta').
-// The accept kernel then runs unchanged.
+// In accept mode the same warp then takes the Metropolis decision and updates
+// the chain's FP64 accumulators (what k_accept does), so an iteration is one
+// launch; otherwise k_accept runs after it.  The hierarchical model has a
+// kernel of its own below (k_traj_hier: z lives in shared memory).
 //
 // Layout: lanes stride over rows; each lane keeps the whole position and
 // momentum in registers, the gradient sums are reduced with warp shuffles
