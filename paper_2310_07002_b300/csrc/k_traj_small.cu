@@ -766,7 +766,7 @@ __device__ __forceinline__ void traj_hier(const Problem &pb, const TrajArgs &t, 
 constexpr int hier_warps_max(int PP) { return PP <= 12 ? 16 : 8; }
 
 template <int PP>
-__global__ void __launch_bounds__(hier_warps_max(PP) * 32) k_traj_hier(Problem pb, TrajArgs t) {
+__global__ void __launch_bounds__(hier_warps_max(PP) * 32, 1) k_traj_hier(Problem pb, TrajArgs t) {
   extern __shared__ __align__(16) uint8_t hier_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   Rows<PP, false> R{pb.X, nullptr, pb.y, pb.p_pad};
