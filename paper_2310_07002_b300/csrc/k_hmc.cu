@@ -370,9 +370,10 @@ __global__ void k_finalize(Accum A, int K, int L, long long n, double *out, doub
   double *mean = scratch + (size_t)k * (4 * L + 2 * (A.M + 2));
   double *M2 = mean + 2 * L;
   double *rho = M2 + 2 * L;
-  // f_k by log-sum-exp of the per-chain U_x (A2 final step)
+  // f_k by log-sum-exp of the per-chain U_x (A2 final step); a chain keeps
+  // U_x as the sum of exp(s - em) on its shift em
   double lse = -INFINITY;
-  for (int l = 0; l < L; ++l) lse = log_add_exp(lse, A.Ux[c0 + l]);
+  for (int l = 0; l < L; ++l) lse = log_add_exp(lse, A.em[c0 + l] + log(A.Ux[c0 + l]));
   const double Ln = (double)L * (double)n;
   o[F_ELPD] = lse - log(Ln);
   // pooled log-shifted Welford of exp(s) (sample variance s^2)

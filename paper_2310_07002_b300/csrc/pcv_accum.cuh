@@ -34,19 +34,21 @@ __device__ __forceinline__ void lshift_push(double &shift, double &mean, double 
   M2 += delta * (v - mean);
 }
 
-// push draw s of chain c; n_before draws already accumulated (same for all
-// chains).  Called by a full warp.  The recursions are independent, so each
-// runs on its own lane (the same operations in the same order as a serial
-// update): lane 0 U_x, lane 1 U_x2, lane 2 the batch LSE Z_x and, when the
-// batch closes, the log-shifted Welford of batch means, lane 3 the
-// log-shifted Welford of exp(s), lane 4 the Welford sums of s, the batch
-// Welford state and the autocovariance centring; then all lanes add their
-// lags.
 // The accumulators of one draw are split by the shape of their work: the
-// scalar ones (log-sum-exp, log-shifted Welford, Welford, batch means) are
-// FP64 transcendental chains, run one thread per chain so that a warp
-// instruction serves 32 chains (B300's FP64 units are narrow); the lag sums
-// of the autocovariance are a warp per chain, lanes over lags.
+// scalar ones (the log-sum-exps, the log-shifted Welford of exp(s), Welford
+// of s, batch means) are FP64 chains, run one thread per chain so that a warp
+// instruction serves 32 chains (B300's FP64 pipe is narrow: a warp
+// instruction of it takes ~32 cycles of an SM); the lag sums of the
+// autocovariance are a warp per chain, lanes over lags.
+//
+// The log-sum-exps of Algorithm A2 (U_x, U_x^2 and the batch's Z_x) share the
+// shift of the log-shifted Welford of exp(s): m = em, the chain's running
+// maximum of s.  They are kept as plain FP64 sums of exp(s - m),
+// exp(2 (s - m)) and (within the batch) exp(s - m), rescaled when m moves,
+// so that a draw costs one FP64 exp (v = exp(s - m), or the rescale factor
+// exp(m_old - s) when s is the new maximum and v = 1) instead of one exp and
+// one log1p per log-sum-exp; U_x = m + log(sum) is formed in the finalize and
+// Z_x at the batch's close.
 
 // x_t = s_t - c0 (c0: the chain's first draw), the autocovariance variable
 __device__ __forceinline__ double acov_x(const Accum &A, int c, double s, long long n_before) {
@@ -58,25 +60,39 @@ __device__ __forceinline__ void accum_scalar(const Accum &A, int c, double s, lo
   const long long n = n_before + 1;
   const int b = A.b;
   const int in_batch = (int)(n_before % b) + 1;
-  A.Ux[c] = log_add_exp(A.Ux[c], s);
-  A.Ux2[c] = log_add_exp(A.Ux2[c], 2.0 * s);
-  const double zx = log_add_exp(in_batch == 1 ? -INFINITY : A.Zx[c], s);
-  A.Zx[c] = zx;
+  const double rn = 1.0 / (double)n;
+  // the shared shift m (running maximum of s) and v = exp(s - m)
+  double m = A.em[c], sc = 1.0, v;
+  if (s > m) {
+    sc = m == -INFINITY ? 0.0 : exp(m - s);
+    m = s;
+    v = 1.0;
+  } else {
+    v = s == -INFINITY ? 0.0 : exp(s - m);   // (m = s = -inf: no mass yet)
+  }
+  A.em[c] = m;
+  A.Ux[c] = A.Ux[c] * sc + v;                        // sum exp(s - m)
+  A.Ux2[c] = A.Ux2[c] * (sc * sc) + v * v;           // sum exp(2 (s - m))
+  const double zs = (in_batch == 1 ? 0.0 : A.Zx[c] * sc) + v;   // this batch's sum exp(s - m)
+  A.Zx[c] = zs;
   if (in_batch == b) {                       // the batch closes (A2 batch loop end)
     const long long na = n / b;
-    const double z = zx - log((double)b);    // log of the batch mean, eq. bmean
+    const double z = m + log(zs / (double)b);   // log of the batch mean, eq. bmean
     double vm = A.vm[c], vmean = A.vmean[c], vM2 = A.vM2[c];
     lshift_push(vm, vmean, vM2, na, z);
     A.vm[c] = vm; A.vmean[c] = vmean; A.vM2[c] = vM2;
   }
   {
-    double em = A.em[c], emean = A.emean[c], eM2 = A.eM2[c];
-    lshift_push(em, emean, eM2, n, s);
-    A.em[c] = em; A.emean[c] = emean; A.eM2[c] = eM2;
+    // log-shifted Welford of exp(s) on the shift m (as lshift_push, with v shared)
+    double emean = A.emean[c] * sc, eM2 = A.eM2[c] * (sc * sc);
+    const double delta = v - emean;
+    emean += delta * rn;
+    eM2 += delta * (v - emean);
+    A.emean[c] = emean; A.eM2[c] = eM2;
   }
   double wm = A.wmean[c], wM2 = A.wM2[c];
   double dl = s - wm;
-  wm += dl / (double)n;
+  wm += dl * rn;
   wM2 += dl * (s - wm);
   A.wmean[c] = wm; A.wM2[c] = wM2;
   double bm = in_batch == 1 ? 0.0 : A.bmean_cur[c], b2 = in_batch == 1 ? 0.0 : A.bM2_cur[c];

@@ -864,9 +864,10 @@ pcv_status alloc_accum(pcv_ctx *x) {
   A.draws = nullptr;
   if (A.draw_cap > 0) ok = ok && dalloc_n(x, &A.draws, C * A.draw_cap);
   if (!ok) return fail(x, PCV_E_OOM, "accumulator allocation failed");
-  // -inf initialisation of the log-space fields (A2 "initial entries -inf")
+  // the shifts start at -inf (A2 "initial entries -inf"); the shifted sums
+  // U_x, U_x^2, Z_x and the Welford states start at 0 (allocations are zeroed)
   std::vector<double> ninf(C, -INFINITY);
-  for (double *p : {A.Ux, A.Ux2, A.Zx, A.em, A.vm})
+  for (double *p : {A.em, A.vm})
     CK(cudaMemcpyAsync(p, ninf.data(), C * sizeof(double), cudaMemcpyHostToDevice, x->stream));
   CK(cudaStreamSynchronize(x->stream));
   return PCV_OK;
@@ -1854,7 +1855,7 @@ std::vector<Seg> ckpt_segments(pcv_ctx *x) {
 CkptHeader ckpt_header(pcv_ctx *x) {
   CkptHeader h{};
   std::memcpy(h.magic, kCkptMagic, 8);
-  h.version = 2;
+  h.version = 3;
   h.precision = x->opt.precision; h.variant = x->variant; h.p = x->p; h.d = x->d; h.d_pad = x->d_pad;
   h.K = x->K; h.L = x->L; h.C = x->C; h.M = x->M; h.max_batches = x->max_batches; h.b = x->b;
   h.draw_cap = x->acc.draw_cap; h.Lf = x->Lf; h.N_pad = x->N_pad; h.N = x->N; h.seed = x->opt.seed;
@@ -1910,7 +1911,7 @@ pcv_status pcv_checkpoint_load(pcv_ctx *x, const void *buf, int64_t bytes) {
   CkptHeader h;
   std::memcpy(&h, buf, sizeof(h));
   const CkptHeader mine = ckpt_header(x);
-  if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 2)
+  if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 3)
     return fail(x, PCV_E_INVALID_ARG, "not a PCV checkpoint");
   if (h.precision != mine.precision || h.variant != mine.variant || h.p != mine.p || h.d != mine.d ||
       h.K != mine.K || h.L != mine.L || h.C != mine.C || h.M != mine.M || h.max_batches != mine.max_batches ||

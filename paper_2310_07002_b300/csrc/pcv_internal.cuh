@@ -98,8 +98,8 @@ struct Accum {
   int M;                  // autocovariance lag cap (0 = off)
   int max_batches;
   int b;                  // batch size
-  double *Ux, *Ux2, *Zx;  // log-sum-exp of s, of 2 s, and of s in the current batch
-  double *em, *emean, *eM2;   // log-shifted Welford of exp(s) over draws
+  double *Ux, *Ux2, *Zx;  // sums of exp(s - em), exp(2 (s - em)), and exp(s - em) in the current batch
+  double *em, *emean, *eM2;   // log-shifted Welford of exp(s) over draws (em: the running max of s)
   double *vm, *vmean, *vM2;   // log-shifted Welford of batch means
   double *wmean, *wM2;        // Welford of s over draws
   double *bmean_cur, *bM2_cur;// Welford of s in the current batch
