@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(256) k_begin(BeginArgs a) {
   const float eps = eps_s;
   const float *th = a.theta + (size_t)c * a.ld;
   const float *g = a.grad + (size_t)c * a.ld;
-  double kin = 0.0;
+  F2 kin = {0.0f, 0.0f};                    // kinetic energy r' M^-1 r, as an FP32 pair
   for (int q = sl; valid && 4 * q < a.d; q += gsz) {
     float z[4];
     if (a.r_given) {
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256) k_begin(BeginArgs a) {
       const float mv = minv_row(a.minv, c, a.minv_every, a.minv_ld)[j];
       // a coordinate with inverse mass 0 (masked covariate) is held: r = 0
       const float r0 = a.r_given ? a.r_given[(size_t)c * a.ld + j] : (mv > 0.0f ? z[e] / sqrtf(mv) : 0.0f);
-      kin += (double)mv * (double)r0 * (double)r0;
+      f2_add_mr2(kin, mv, r0);
       const float rh = r0 + 0.5f * eps * g[j];
       const float tn = th[j] + eps * mv * rh;
       a.r[(size_t)c * a.ld + j] = rh;
@@ -81,10 +81,9 @@ __global__ void __launch_bounds__(256) k_begin(BeginArgs a) {
       }
     }
   }
-  // sum over the chain's lanes: the xor tree of warp_sum_d restricted to
-  // the group (lanes outside it hold 0, so the sum is the same bit for bit)
-  for (int off = gsz >> 1; off > 0; off >>= 1) kin += __shfl_xor_sync(0xffffffffu, kin, off);
-  if (valid && sl == 0) a.H0[c] = -a.logp[c] + 0.5 * kin;
+  // sum over the chain's lanes (xor tree within the group), then FP64
+  const double K0 = f2_group_sum(kin, gsz);
+  if (valid && sl == 0) a.H0[c] = -a.logp[c] + 0.5 * K0;
 }
 
 // standard normals for (iteration, stream) into out[C x ld] (scaled)
@@ -157,13 +156,10 @@ __global__ void __launch_bounds__(kAccChains * 32) k_accept(AcceptArgs a) {
   // restore-or-keep, the held-out value of the draw and its lag sums
   const int c = cb0 + warp;
   if (c < a.C) {
-    double kin = 0.0;
+    F2 k2 = {0.0f, 0.0f};                  // kinetic energy as an FP32 pair, then FP64
     const float *mvr = minv_row(a.minv, c, a.minv_every, a.minv_ld);
-    for (int j = lane; j < a.d; j += 32) {
-      const double rj = a.r[(size_t)c * a.ld + j];
-      kin += (double)mvr[j] * rj * rj;
-    }
-    kin = warp_sum_d(kin);
+    for (int j = lane; j < a.d; j += 32) f2_add_mr2(k2, mvr[j], a.r[(size_t)c * a.ld + j]);
+    const double kin = f2_group_sum(k2, 32);
     const double H1 = -a.logp_p[c] + 0.5 * kin;
     const double dH = H1 - a.H0[c];
     const bool finite = isfinite(H1) && isfinite(dH);

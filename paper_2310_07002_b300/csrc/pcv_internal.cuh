@@ -182,6 +182,42 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+// A sum of FP32 products carried as an unevaluated pair hi + lo of floats
+// with error-free transformations: Knuth's TwoSum for each addition and the
+// FMA TwoProduct for each product (the Dot2 scheme of Ogita, Rump and Oishi,
+// "Accurate sum and dot product", SIAM J. Sci. Comput. 2005).  The pair holds
+// the sum to about twice FP32's precision (~2^-48 relative for the positive
+// kinetic-energy terms) without FP64 arithmetic, whose pipe on this part
+// takes ~32 cycles of an SM per warp instruction; it becomes one double at
+// the end (hi + lo).
+struct F2 {
+  float hi, lo;
+};
+// (the _rn intrinsics keep the compiler from contracting a product and a
+// sum into one FMA, which would break the exact error terms)
+__device__ __forceinline__ void f2_add(F2 &s, float x) {
+  const float t = __fadd_rn(s.hi, x);
+  const float z = __fsub_rn(t, s.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, z)), __fsub_rn(x, z)));
+  s.hi = t;
+}
+// s += m r^2: m r = p1 + p2 exactly, p1 r = q1 + q2 exactly, p2 r rounded
+__device__ __forceinline__ void f2_add_mr2(F2 &s, float m, float r) {
+  const float p1 = __fmul_rn(m, r), p2 = __fmaf_rn(m, r, -p1);
+  const float q1 = __fmul_rn(p1, r), q2 = __fmaf_rn(p1, r, -q1);
+  f2_add(s, q1);
+  s.lo = __fadd_rn(s.lo, __fmaf_rn(p2, r, q2));
+}
+// the pair summed over the lanes of an aligned group of gsz lanes (xor tree)
+__device__ __forceinline__ double f2_group_sum(F2 s, int gsz) {
+  for (int o = gsz >> 1; o > 0; o >>= 1) {
+    const float h = __shfl_xor_sync(0xffffffffu, s.hi, o), l = __shfl_xor_sync(0xffffffffu, s.lo, o);
+    f2_add(s, h);
+    s.lo = __fadd_rn(s.lo, l);
+  }
+  return (double)s.hi + (double)s.lo;
+}
+
 __device__ __forceinline__ int fold_of_chain(const GradArgs &a, int c) {
   return a.fold_of ? a.fold_of[c] : a.fold_base + c / a.L;
 }
