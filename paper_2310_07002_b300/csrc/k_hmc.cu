@@ -128,72 +128,86 @@ __global__ void k_shadow(int C, int d, int ld, const float *theta, const float *
 }
 
 // ---------------------------------------------------------------------------
-// k_accept: 32 chains per block; per chain one warp for the vector work
-// (kinetic energy, the accept copies, the lag sums) and one lane of warp 0
-// for the scalar FP64 work (log u, the accumulators); the last block
-// advances the counters
+// k_accept: 32 chains per block.  B300's FP64 pipe takes ~32 cycles of an SM
+// per warp instruction, so the FP64 work runs one lane per chain (a warp
+// instruction serves 32 chains) and the vector work a warp per chain:
+//   A) a warp per chain: the kinetic energy of the proposal as an FP32 pair
+//      (error-free sums, no FP64);
+//   B) one lane per chain (warp 0): log u, H1, dH, the Metropolis test in
+//      FP64, the kept log density and held-out value, the scalar
+//      accumulators;
+//   C) a warp per chain: the accept copies and the lag sums;
+// the last block advances the counters.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kAccChains * 32) k_accept(AcceptArgs a) {
-  __shared__ double logu_s[kAccChains], s_s[kAccChains], dH_s[kAccChains];
-  __shared__ int flag_s[kAccChains];         // bit 0 accepted, 1 divergent, 2 finite
+  __shared__ float khi_s[kAccChains], klo_s[kAccChains];
+  __shared__ double s_s[kAccChains];
+  __shared__ int flag_s[kAccChains];         // 1: accepted
   __shared__ int is_last;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cb0 = blockIdx.x * kAccChains;
   const unsigned it = a.fd ? a.st->fd_iter : a.st->iter;
   const long long n_before = a.st->n_draws;
-  // 1) the accept uniforms, one lane per chain
-  if (warp == 0) {
-    const int c = cb0 + lane;
-    double lu = 0.0;
+  // A) kinetic energy r' M^-1 r of the proposal
+  {
+    const int c = cb0 + warp;
     if (c < a.C) {
-      const uint4 w = philox_at(a.seed, 0u, (uint32_t)(a.chain_base + c), it, a.stream);
-      lu = log(unit_from_word(w.x));
+      F2 k2 = {0.0f, 0.0f};
+      const float *mvr = minv_row(a.minv, c, a.minv_every, a.minv_ld);
+      for (int j = lane; j < a.d; j += 32) f2_add_mr2(k2, mvr[j], a.r[(size_t)c * a.ld + j]);
+      for (int o = 16; o > 0; o >>= 1) {
+        const float h = __shfl_xor_sync(0xffffffffu, k2.hi, o), l = __shfl_xor_sync(0xffffffffu, k2.lo, o);
+        f2_add(k2, h);
+        k2.lo = __fadd_rn(k2.lo, l);
+      }
+      if (lane == 0) { khi_s[warp] = k2.hi; klo_s[warp] = k2.lo; }
     }
-    logu_s[lane] = lu;
   }
   __syncthreads();
-  // 2) one warp per chain: FP64 Hamiltonian difference, Metropolis test,
-  // restore-or-keep, the held-out value of the draw and its lag sums
-  const int c = cb0 + warp;
-  if (c < a.C) {
-    F2 k2 = {0.0f, 0.0f};                  // kinetic energy as an FP32 pair, then FP64
-    const float *mvr = minv_row(a.minv, c, a.minv_every, a.minv_ld);
-    for (int j = lane; j < a.d; j += 32) f2_add_mr2(k2, mvr[j], a.r[(size_t)c * a.ld + j]);
-    const double kin = f2_group_sum(k2, 32);
+  // B) one lane per chain: FP64 Hamiltonian difference, Metropolis test with
+  // the uniform of stream a.stream, the kept state's log density and
+  // held-out value, the scalar accumulators
+  if (warp == 0 && cb0 + lane < a.C) {
+    const int c = cb0 + lane;
+    const uint4 w = philox_at(a.seed, 0u, (uint32_t)(a.chain_base + c), it, a.stream);
+    const double lu = log(unit_from_word(w.x));
+    const double kin = (double)khi_s[lane] + (double)klo_s[lane];
     const double H1 = -a.logp_p[c] + 0.5 * kin;
     const double dH = H1 - a.H0[c];
     const bool finite = isfinite(H1) && isfinite(dH);
-    const bool acc = finite && (logu_s[warp] < -dH);
+    const bool acc = finite && (lu < -dH);
     const bool div = !finite || dH > 1000.0;
+    double s;
     if (acc) {
-      for (int j = lane; j < a.d; j += 32) {
-        a.theta[(size_t)c * a.ld + j] = a.theta_p[(size_t)c * a.ld + j];
-        a.grad[(size_t)c * a.ld + j] = a.grad_p[(size_t)c * a.ld + j];
-      }
+      s = a.shat_p[c];
+      a.logp[c] = a.logp_p[c];
+      a.shat[c] = s;
+    } else {
+      s = a.shat[c];
     }
-    const double s = acc ? a.shat_p[c] : a.shat[c];
-    if (lane == 0) {
-      if (acc) {
-        a.logp[c] = a.logp_p[c];
-        a.shat[c] = a.shat_p[c];
-      }
-      flag_s[warp] = (acc ? 1 : 0) | (div ? 2 : 0) | (finite ? 4 : 0);
-      dH_s[warp] = dH;
-      s_s[warp] = s;
+    flag_s[lane] = acc ? 1 : 0;
+    s_s[lane] = s;
+    if (a.accept_prob) a.accept_prob[c] = finite ? (dH <= 0.0 ? 1.0 : exp(-dH)) : 0.0;
+    if (a.accumulate) {
+      a.acc.div[c] += div ? 1 : 0;
+      a.acc.acc[c] += acc ? 1 : 0;
+      accum_scalar(a.acc, c, s, n_before);
+      if (a.acc.draws && n_before < a.acc.draw_cap) a.acc.draws[(size_t)c * a.acc.draw_cap + n_before] = s;
     }
-    if (a.accumulate) accum_lags(a.acc, c, acov_x(a.acc, c, s, n_before), n_before, lane);
   }
   __syncthreads();
-  // 3) one lane per chain: acceptance probability, counters, accumulators
-  if (warp == 0 && cb0 + lane < a.C) {
-    const int cc = cb0 + lane;
-    const int f = flag_s[lane];
-    if (a.accept_prob) a.accept_prob[cc] = (f & 4) ? (dH_s[lane] <= 0.0 ? 1.0 : exp(-dH_s[lane])) : 0.0;
-    if (a.accumulate) {
-      a.acc.div[cc] += (f & 2) ? 1 : 0;
-      a.acc.acc[cc] += (f & 1) ? 1 : 0;
-      accum_scalar(a.acc, cc, s_s[lane], n_before);
-      if (a.acc.draws && n_before < a.acc.draw_cap) a.acc.draws[(size_t)cc * a.acc.draw_cap + n_before] = s_s[lane];
+  // C) a warp per chain: restore-or-keep (theta and gradient of the proposal
+  // when accepted) and the lag sums of the held-out value
+  {
+    const int c = cb0 + warp;
+    if (c < a.C) {
+      if (flag_s[warp] & 1) {
+        for (int j = lane; j < a.d; j += 32) {
+          a.theta[(size_t)c * a.ld + j] = a.theta_p[(size_t)c * a.ld + j];
+          a.grad[(size_t)c * a.ld + j] = a.grad_p[(size_t)c * a.ld + j];
+        }
+      }
+      if (a.accumulate) accum_lags(a.acc, c, acov_x(a.acc, c, s_s[warp], n_before), n_before, lane);
     }
   }
   __threadfence();
