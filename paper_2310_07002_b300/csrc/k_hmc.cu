@@ -137,9 +137,11 @@ __global__ void k_shadow(int C, int d, int ld, const float *theta, const float *
 //      FP64, the kept log density and held-out value, the scalar
 //      accumulators;
 //   C) a warp per chain: the accept copies and the lag sums;
-// the last block advances the counters.
+// the last block advances the counters.  A block has kAccWarps warps, each
+// taking kAccChains / kAccWarps chains in A and C, so that several blocks
+// (several phase-B warps) share an SM and hide the FP64 latency.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kAccChains * 32) k_accept(AcceptArgs a) {
+__global__ void __launch_bounds__(kAccWarps * 32) k_accept(AcceptArgs a) {
   __shared__ float khi_s[kAccChains], klo_s[kAccChains];
   __shared__ double s_s[kAccChains];
   __shared__ int flag_s[kAccChains];         // 1: accepted
@@ -149,8 +151,8 @@ __global__ void __launch_bounds__(kAccChains * 32) k_accept(AcceptArgs a) {
   const unsigned it = a.fd ? a.st->fd_iter : a.st->iter;
   const long long n_before = a.st->n_draws;
   // A) kinetic energy r' M^-1 r of the proposal
-  {
-    const int c = cb0 + warp;
+  for (int wc = warp; wc < kAccChains; wc += kAccWarps) {
+    const int c = cb0 + wc;
     if (c < a.C) {
       F2 k2 = {0.0f, 0.0f};
       const float *mvr = minv_row(a.minv, c, a.minv_every, a.minv_ld);
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(kAccChains * 32) k_accept(AcceptArgs a) {
         f2_add(k2, h);
         k2.lo = __fadd_rn(k2.lo, l);
       }
-      if (lane == 0) { khi_s[warp] = k2.hi; klo_s[warp] = k2.lo; }
+      if (lane == 0) { khi_s[wc] = k2.hi; klo_s[wc] = k2.lo; }
     }
   }
   __syncthreads();
@@ -198,16 +200,16 @@ __global__ void __launch_bounds__(kAccChains * 32) k_accept(AcceptArgs a) {
   __syncthreads();
   // C) a warp per chain: restore-or-keep (theta and gradient of the proposal
   // when accepted) and the lag sums of the held-out value
-  {
-    const int c = cb0 + warp;
+  for (int wc = warp; wc < kAccChains; wc += kAccWarps) {
+    const int c = cb0 + wc;
     if (c < a.C) {
-      if (flag_s[warp] & 1) {
+      if (flag_s[wc] & 1) {
         for (int j = lane; j < a.d; j += 32) {
           a.theta[(size_t)c * a.ld + j] = a.theta_p[(size_t)c * a.ld + j];
           a.grad[(size_t)c * a.ld + j] = a.grad_p[(size_t)c * a.ld + j];
         }
       }
-      if (a.accumulate) accum_lags(a.acc, c, acov_x(a.acc, c, s_s[warp], n_before), n_before, lane);
+      if (a.accumulate) accum_lags(a.acc, c, acov_x(a.acc, c, s_s[wc], n_before), n_before, lane);
     }
   }
   __threadfence();

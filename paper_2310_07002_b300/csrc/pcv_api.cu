@@ -744,7 +744,7 @@ pcv_status launch_iteration(pcv_ctx *x, ChainBufs &cb, bool fd, bool accumulate)
   aa.accumulate = accumulate ? 1 : 0;
   aa.acc = x->acc;
   aa.accept_prob = cb.accept_prob;
-  k_accept<<<(cb.C + kAccChains - 1) / kAccChains, kAccChains * 32, 0, x->stream>>>(aa);
+  k_accept<<<(cb.C + kAccChains - 1) / kAccChains, kAccWarps * 32, 0, x->stream>>>(aa);
   CK(cudaGetLastError());
   if (accumulate && x->extra.flags) {
     k_extra_push<<<(cb.C + 7) / 8, 256, sizeof(double) * 8 * x->extra.T, x->stream>>>(

@@ -442,6 +442,7 @@ inline int begin_blocks(int C, int d) {
   return (C + per_block - 1) / per_block;
 }
 constexpr int kAccChains = 32;   // chains per block of the accept / accumulate kernels
+constexpr int kAccWarps = 8;     // warps per block of the accept kernel (each takes 4 chains' vector work)
 __global__ void k_accept(AcceptArgs a);
 __global__ void k_accumulate_given(Accum A, const double *s, int n, long long n0);
 __global__ void k_fd_adapt(FdAdaptArgs a);
