@@ -232,30 +232,56 @@ __device__ __forceinline__ void evaluate(const Problem &pb, const Rows<PP, XB16>
   }
 }
 
-// Accept mode, after the Metropolis test (the positions and gradients are
-// written by the caller): the chain's log densities on acceptance, its
-// acceptance statistic, and the draw's held-out value into the online
-// accumulators (as k_accept).  One warp.
-__device__ __forceinline__ void accept_tail(const TrajArgs &t, int c, int lane, bool acc, bool div, bool finite,
-                                            double dH, double logp1, double ll_te) {
-  const double s_draw = acc ? ll_te : t.shat_w[c];
-  if (lane == 0) {
+// Accept mode: the Metropolis tests and scalar accumulators of the CTA's
+// chains, one lane per chain in the CTA's first warp (as k_accept's phase
+// B): an FP64 warp instruction, ~32 cycles of an SM on this part, then
+// serves every chain of the CTA instead of one.  Every warp of the CTA calls
+// it exactly once (it holds two CTA barriers); slot is the chain's place in
+// the CTA (its lane 0 reports dH, finiteness and the proposal's log
+// densities), -1 for a warp with nothing to report.  Returns whether the
+// chain was accepted and, in s_draw, the draw's held-out value; on
+// acceptance the chain's log densities are the proposal's.
+constexpr int kBatchMax = 16;   // chains per CTA at most (k_traj_hier: 16 warps)
+
+__device__ __forceinline__ bool accept_batch(const TrajArgs &t, int slot, int lane, int c0, int nch, double dH,
+                                             bool finite, double logp1, double ll_te, double &s_draw) {
+  __shared__ double b_dh[kBatchMax], b_lp[kBatchMax], b_te[kBatchMax], b_s[kBatchMax];
+  __shared__ int b_fl[kBatchMax];
+  if (slot >= 0 && lane == 0) {
+    b_dh[slot] = dH;
+    b_lp[slot] = logp1;
+    b_te[slot] = ll_te;
+    b_fl[slot] = finite ? 1 : 0;
+  }
+  __syncthreads();
+  if (threadIdx.x < nch) {
+    const int l = threadIdx.x, cc = c0 + l;
+    const uint4 w = philox_at(t.seed, 0u, (uint32_t)(t.chain_base + cc), *t.iter, t.acc_stream);
+    const double lu = log(unit_from_word(w.x));
+    const double d = b_dh[l];
+    const bool fin = b_fl[l] != 0;
+    const bool acc = fin && (lu < -d);
+    const bool div = !fin || d > 1000.0;
+    const double sd = acc ? b_te[l] : t.shat_w[cc];
     if (acc) {
-      t.logp_w[c] = logp1;
-      t.shat_w[c] = ll_te;
+      t.logp_w[cc] = b_lp[l];
+      t.shat_w[cc] = b_te[l];
     }
-    if (t.accept_prob) t.accept_prob[c] = finite ? (dH <= 0.0 ? 1.0 : exp(-dH)) : 0.0;
-  }
-  if (t.accumulate) {
-    const long long n_before = t.st->n_draws;
-    accum_lags(t.acc, c, acov_x(t.acc, c, s_draw, n_before), n_before, lane);
-    if (lane == 0) {
-      t.acc.div[c] += div ? 1 : 0;
-      t.acc.acc[c] += acc ? 1 : 0;
-      accum_scalar(t.acc, c, s_draw, n_before);
-      if (t.acc.draws && n_before < t.acc.draw_cap) t.acc.draws[(size_t)c * t.acc.draw_cap + n_before] = s_draw;
+    if (t.accept_prob) t.accept_prob[cc] = fin ? (d <= 0.0 ? 1.0 : exp(-d)) : 0.0;
+    if (t.accumulate) {
+      const long long n_before = t.st->n_draws;
+      t.acc.div[cc] += div ? 1 : 0;
+      t.acc.acc[cc] += acc ? 1 : 0;
+      accum_scalar(t.acc, cc, sd, n_before);
+      if (t.acc.draws && n_before < t.acc.draw_cap) t.acc.draws[(size_t)cc * t.acc.draw_cap + n_before] = sd;
     }
+    b_fl[l] = acc ? 1 : 0;
+    b_s[l] = sd;
   }
+  __syncthreads();
+  if (slot < 0) return false;
+  s_draw = b_s[slot];
+  return b_fl[slot] != 0;
 }
 
 // One chain's trajectory (and, in accept mode, its Metropolis test and
@@ -351,7 +377,12 @@ __device__ __forceinline__ void traj_team(const Problem &pb, const TrajArgs &t, 
       }
     }
   }
-  if (!writer) return;
+  const int cpc = kTrajWarps / t.wpc, c0 = blockIdx.x * cpc, nch = min(cpc, t.C - c0);
+  if (!writer) {
+    double sd;
+    if (t.accept) accept_batch(t, -1, lane, c0, nch, 0.0, false, 0.0, 0.0, sd);
+    return;
+  }
   // log prior: this lane's coordinates in FP32, summed across lanes in FP64
   float lpt = 0.0f;
 #pragma unroll
@@ -394,14 +425,8 @@ __device__ __forceinline__ void traj_team(const Problem &pb, const TrajArgs &t, 
   const double H1 = -logp1 + 0.5 * warp_sum_d((double)kt);
   const double dH = H1 - H0;
   const bool finite = isfinite(H1) && isfinite(dH);
-  double lu = 0.0;
-  if (lane == 0) {
-    const uint4 w = philox_at(t.seed, 0u, (uint32_t)(t.chain_base + c), it, t.acc_stream);
-    lu = log(unit_from_word(w.x));
-  }
-  lu = __shfl_sync(0xffffffffu, lu, 0);
-  const bool acc = finite && (lu < -dH);
-  const bool div = !finite || dH > 1000.0;
+  double s_draw = 0.0;
+  const bool acc = accept_batch(t, tm.warp / t.wpc, lane, c0, nch, dH, finite, logp1, ll_te, s_draw);
   float *thw = t.theta_w + (size_t)c * t.ld, *gw = t.grad_w + (size_t)c * t.ld;
   if (acc) {
 #pragma unroll
@@ -409,7 +434,10 @@ __device__ __forceinline__ void traj_team(const Problem &pb, const TrajArgs &t, 
       if (j < p && lane == (j & 31)) { thw[j] = th[j]; gw[j] = g[j]; }
     if (LOGSIG && lane == (p & 31)) { thw[p] = ls; gw[p] = gls; }
   }
-  accept_tail(t, c, lane, acc, div, finite, dH, logp1, ll_te);
+  if (t.accumulate) {
+    const long long n_before = t.st->n_draws;
+    accum_lags(t.acc, c, acov_x(t.acc, c, s_draw, n_before), n_before, lane);
+  }
 }
 
 // Accept mode, at the end of the kernel (every thread of the CTA): once all
@@ -479,8 +507,14 @@ __global__ void __launch_bounds__(kTrajWarps * 32, PP <= 12 ? 2 : 1) k_traj_smal
   tm.parity = 0;
   const int c = blockIdx.x * (kTrajWarps / t.wpc) + warp / t.wpc;
   // a team past the last chain does nothing, but (accept mode) still meets
-  // the CTA barrier at the end
-  if (c < t.C) traj_team<PP, MV, XB16>(pb, t, R, tm, c);
+  // the CTA barriers of the batched accept and of the counter advance
+  if (c < t.C) {
+    traj_team<PP, MV, XB16>(pb, t, R, tm, c);
+  } else if (t.accept) {
+    const int cpc = kTrajWarps / t.wpc, c0 = blockIdx.x * cpc;
+    double sd;
+    accept_batch(t, -1, lane, c0, min(cpc, t.C - c0), 0.0, false, 0.0, 0.0, sd);
+  }
   if (t.accept) advance_counters(t);
 }
 
@@ -746,16 +780,14 @@ __device__ __forceinline__ void traj_hier(const Problem &pb, const TrajArgs &t, 
   const double H1 = -logp1 + 0.5 * warp_sum_d((double)kt);
   const double dH = H1 - H0;
   const bool finite = isfinite(H1) && isfinite(dH);
-  double lu = 0.0;
-  if (lane == 0) {
-    const uint4 w = philox_at(t.seed, 0u, (uint32_t)(t.chain_base + c), it, t.acc_stream);
-    lu = log(unit_from_word(w.x));
-  }
-  lu = __shfl_sync(0xffffffffu, lu, 0);
-  const bool acc = finite && (lu < -dH);
-  const bool div = !finite || dH > 1000.0;
+  const int nw = blockDim.x >> 5, c0 = blockIdx.x * nw;
+  double s_draw = 0.0;
+  const bool acc = accept_batch(t, c - c0, lane, c0, min(nw, t.C - c0), dH, finite, logp1, ll_te, s_draw);
   if (acc) put(t.theta_w, nullptr, t.grad_w);
-  accept_tail(t, c, lane, acc, div, finite, dH, logp1, ll_te);
+  if (t.accumulate) {
+    const long long n_before = t.st->n_draws;
+    accum_lags(t.acc, c, acov_x(t.acc, c, s_draw, n_before), n_before, lane);
+  }
 }
 
 // Every chain reads every row at every step, so the CTA first copies X (PP
@@ -785,7 +817,12 @@ __global__ void __launch_bounds__(hier_warps_max(PP) * 32, 1) k_traj_hier(Proble
   }
   float *zsh = reinterpret_cast<float *>(hier_smem + t.part_offset) + (size_t)warp * (3 * pb.G + pb.d_pad);
   const int c = blockIdx.x * nw + warp;
-  if (c < t.C) traj_hier<PP>(pb, t, R, c, lane, zsh);
+  if (c < t.C) {
+    traj_hier<PP>(pb, t, R, c, lane, zsh);
+  } else if (t.accept) {   // no chain: still meets the batched accept's barriers
+    double sd;
+    accept_batch(t, -1, lane, blockIdx.x * nw, min(nw, t.C - (int)blockIdx.x * nw), 0.0, false, 0.0, 0.0, sd);
+  }
   if (t.accept) advance_counters(t);
 }
 
