@@ -175,6 +175,13 @@ typedef struct {
      * takes it, with teams that fill the GPU); 0 never; 1, 2, 4 or 8: always
      * where the problem allows it, with that many warps per chain. */
     int32_t fused_trajectory;
+    /* Tensor-core BF16 form, where each 128-chain tile has a CTA of its own
+     * (the autotuner's grid for short tiles, e.g. leave-one-out on a few
+     * thousand rows): 0 (default) runs the L_f - 1 kick-drift steps of a
+     * trajectory in one launch, each CTA carrying its tile from step to step
+     * (lock-step HMC, Section 3.3: a tile depends on no other tile); 1 runs
+     * one launch per step. Both give the same bits. */
+    int32_t tc_steps_per_launch;
 } pcv_options;
 
 /* Fill *opt with the defaults listed above (seed 0, L_f 16, adapted step). */

@@ -92,7 +92,10 @@ constexpr int kTcMaxStages = 8; // X pipeline stages (as many as fit in shared m
 // through tm_lo, which the TF form does not otherwise use) so that both
 // GEMMs take K-major operands; the residual goes to TMEM as TF32, one
 // element per column.
-template <int KS, bool ACC, bool GAUSS, bool TF = false>
+// MS: several kick-drift steps in one launch (BF16, one CTA per tile,
+// ta.steps of them); a separate instantiation so that the one-step kernel's
+// code is not touched by it
+template <int KS, bool ACC, bool GAUSS, bool TF = false, bool MS = false>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_grad_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_hi,
               const __grid_constant__ CUtensorMap tm_lo, Problem pb, GradArgs a, TcArgs ta) {
@@ -129,13 +132,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   volatile int *abort_flag = reinterpret_cast<volatile int *>(s_full + 19);
   volatile int *last_flag = reinterpret_cast<volatile int *>(s_full + 20);
   uint64_t *flush_bar = s_full + 21, *decide_bar = s_full + 22;   // epilogue-internal sync
+  // several steps per launch: the finish of a step is done (its theta,
+  // momentum and shadows written), so the next step may load theta
+  uint64_t *th_ready = s_full + 23;
   uint64_t *xt_full = s_full + 24, *xt_empty = xt_full + kTcMaxStages;   // X^T ring (TF32)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long U = (long long)ta.T * ta.J;
   const long long u0 = (long long)blockIdx.x * U / ta.n_cta;
   const long long u1 = (long long)(blockIdx.x + 1) * U / ta.n_cta;
-  const int nunits = (int)(u1 - u0);
+  // MS (kick-drift, one CTA per tile): the CTA carries its tile
+  // through that many leapfrog steps, its J units once per step
+  const int per = (int)(u1 - u0);
+  const int nunits = MS ? per * ta.steps : per;
   // Order of the CTA's units: a range that ends in a later tile than it
   // starts in runs its last piece (chunks 0 .. of that tile) first, then the
   // rest in order.  Every CTA's range is about U / n_cta units, so at any
@@ -145,7 +154,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   // ownership of tile segments and the finish do not depend on it.
   const long long ls = (u1 - 1) / ta.J * ta.J;     // start of the last unit's tile
   const int rot = (nunits > 0 && ls > u0) ? (int)(u1 - ls) : 0;
-  auto unit_of = [&](const int i) -> long long { return i < rot ? ls + i : u0 + (i - rot); };
+  auto unit_of = [&](const int i) -> long long { return i < rot ? ls + i : u0 + (MS ? (i - rot) % per : i - rot); };
   // the chunk index j of unit i, walked incrementally by the single-thread
   // issuers (no 64-bit division per unit): j of unit 0, and the step
   const int j_u0 = (int)(u0 % ta.J);
@@ -168,6 +177,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     mbar_init(smem_u32(th_full), TF ? 8 : 1); mbar_init(smem_u32(th_empty), 1);
     mbar_init(smem_u32(g_full), 1); mbar_init(smem_u32(g_empty), 4);
     mbar_init(smem_u32(flush_bar), 8); mbar_init(smem_u32(decide_bar), 1);
+    if (MS) mbar_init(smem_u32(th_ready), 8);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -205,6 +215,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (!TF && seg_first(i, j)) {
           const int t = (int)(unit_of(i) / ta.J);
           if (!mbar_wait_fast(smem_u32(th_empty), (seg & 1) ^ 1, abort_flag, ta.err)) break;
+          // the next step of the same tile: its theta comes from the last
+          // step's finish
+          if (MS && seg > 0 && !mbar_wait_fast(smem_u32(th_ready), (seg - 1) & 1, abort_flag, ta.err)) break;
           mbar_expect_tx(smem_u32(th_full), th_bytes * (ta.need_lo ? 2 : 1));
           for (int kb = 0; kb < KA; ++kb) {
             tma_load_2d(smem_u32(th_hi + kb * kTM * 128), &tm_hi, kb * AE, t * kTM, smem_u32(th_full));
@@ -875,6 +888,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           }
         }
       }
+      // several steps per launch: every epilogue thread's finish writes
+      // (theta, momentum, gradient, shadows) precede the next step, both
+      // the producer's TMA load of the new shadow (async proxy: hence the
+      // proxy fence) and the epilogue's own reads of theta
+      if constexpr (MS) {
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(th_ready));
+        if (!warp_wait(smem_u32(th_ready), fl & 1, abort_flag, ta.err)) break;
+      }
       ib = ie;
     }
     // back to the producers' count, so that all warps meet the teardown alike
@@ -923,10 +946,15 @@ int tc_segments_per_tile(int T, int J, int n_cta) {
 template <int KS, bool TF>
 static cudaError_t set_smem_attr() {
   const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t r[4] = {cudaFuncSetAttribute(k_grad_tc<KS, false, false, TF>, at, 227 * 1024),
+  cudaError_t r[6] = {cudaFuncSetAttribute(k_grad_tc<KS, false, false, TF>, at, 227 * 1024),
                       cudaFuncSetAttribute(k_grad_tc<KS, true, false, TF>, at, 227 * 1024),
                       cudaFuncSetAttribute(k_grad_tc<KS, false, true, TF>, at, 227 * 1024),
-                      cudaFuncSetAttribute(k_grad_tc<KS, true, true, TF>, at, 227 * 1024)};
+                      cudaFuncSetAttribute(k_grad_tc<KS, true, true, TF>, at, 227 * 1024),
+                      cudaSuccess, cudaSuccess};
+  if constexpr (!TF) {   // the several-steps kick-drift kernels
+    r[4] = cudaFuncSetAttribute(k_grad_tc<KS, false, false, false, true>, at, 227 * 1024);
+    r[5] = cudaFuncSetAttribute(k_grad_tc<KS, false, true, false, true>, at, 227 * 1024);
+  }
   for (cudaError_t x : r)
     if (x != cudaSuccess) return x;
   return cudaSuccess;
@@ -940,12 +968,18 @@ static bool g_tc_regs_ok = false;
 template <int KS, bool TF>
 static bool regs_fit() {
   const long need = 128L * kTcRegsProducer + 256L * kTcRegsEpilogue;
-  cudaFuncAttributes fa[4];
+  cudaFuncAttributes fa[6];
   if (cudaFuncGetAttributes(&fa[0], k_grad_tc<KS, false, false, TF>) != cudaSuccess ||
       cudaFuncGetAttributes(&fa[1], k_grad_tc<KS, true, false, TF>) != cudaSuccess ||
       cudaFuncGetAttributes(&fa[2], k_grad_tc<KS, false, true, TF>) != cudaSuccess ||
       cudaFuncGetAttributes(&fa[3], k_grad_tc<KS, true, true, TF>) != cudaSuccess)
     return false;
+  fa[4] = fa[5] = fa[0];
+  if constexpr (!TF) {
+    if (cudaFuncGetAttributes(&fa[4], k_grad_tc<KS, false, false, false, true>) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa[5], k_grad_tc<KS, false, true, false, true>) != cudaSuccess)
+      return false;
+  }
   for (const cudaFuncAttributes &f : fa)
     if ((long)f.numRegs * kTcThreads < need) return false;
   return true;
@@ -976,6 +1010,13 @@ template <int K, bool TF>
 static void launch_k(bool gauss, bool accurate, const CUtensorMap &tm_x, const CUtensorMap &tm_hi,
                      const CUtensorMap &tm_lo, const Problem &pb, const GradArgs &a, const TcArgs &ta, size_t smem,
                      cudaStream_t st) {
+  if constexpr (!TF) {
+    if (ta.steps > 1) {   // several kick-drift steps (the caller checked the form and the grid)
+      if (gauss) k_grad_tc<K, false, true, false, true><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta);
+      else k_grad_tc<K, false, false, false, true><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta);
+      return;
+    }
+  }
   if (gauss) {
     if (accurate) k_grad_tc<K, true, true, TF><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta);
     else k_grad_tc<K, false, true, TF><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta);
@@ -1004,6 +1045,9 @@ cudaError_t launch_grad_tc(const CUtensorMap &tm_x, const CUtensorMap &tm_hi, co
   if (!g_tc_regs_ok) return cudaErrorInvalidConfiguration;   // tc_prepare not run, or the split does not fit
   if (pb.variant == MV_HIER) return cudaErrorInvalidValue;
   if (ta.tf32 && ta.need_lo) return cudaErrorInvalidValue;    // the TF32 form has no lo part
+  // several steps per launch: BF16 kick-drift steps, one CTA per tile
+  if (ta.steps > 1 && (ta.tf32 || ta.n_cta != ta.T || a.mode != MODE_KICK_DRIFT || a.need_ll))
+    return cudaErrorInvalidValue;
   const bool gauss = pb.variant == MV_GAUSS_KNOWN || pb.variant == MV_GAUSS_LOGSIG;
   const bool ok = ta.tf32 ? launch_ks<true>(ta.KS, std::make_integer_sequence<int, 15>{}, gauss, ta.accurate != 0,
                                            tm_x, tm_hi, tm_lo, pb, a, ta, smem, st)

@@ -422,13 +422,14 @@ GradArgs grad_args(pcv_ctx *x, const ChainBufs &cb, bool proposal) {
   return a;
 }
 
-pcv_status launch_grad(pcv_ctx *x, GradArgs a, const ChainBufs *cb = nullptr) {
+pcv_status launch_grad(pcv_ctx *x, GradArgs a, const ChainBufs *cb = nullptr, int steps = 1) {
   if (x->tc) {
     if (!cb) return fail(x, PCV_E_UNSUPPORTED, "internal: tensor-core launch without a chain set");
     pcv_status s = ensure_ws_tc(x, a.C);
     if (s != PCV_OK) return s;
     TcArgs t = tc_args(x, a.C, a.need_ll != 0);
     t.shadow32 = cb->shadow32;
+    t.steps = steps;
     // TF32 form: the X^T map goes where the bf16 form's lo shadow map goes
     CK(launch_grad_tc(x->tm_x, cb->tm_hi, x->tc32 ? x->tm_xt : cb->tm_lo, x->pb, a, t, x->stream));
     return PCV_OK;
@@ -439,6 +440,14 @@ pcv_status launch_grad(pcv_ctx *x, GradArgs a, const ChainBufs *cb = nullptr) {
   a.tickets = x->tickets;
   CK(launch_grad_simt(x->pb, a, x->stream));
   return PCV_OK;
+}
+
+// Kick-drift steps per tensor-core launch for a chain set: all L_f - 1 of
+// them where each 128-chain tile has a CTA of its own (BF16 form), else one.
+int tc_steps_per_launch(pcv_ctx *x, int C) {
+  if (!x->tc || x->tc32 || x->opt.tc_steps_per_launch == 1 || x->Lf < 3) return 1;
+  const TcArgs t = tc_args(x, C, false);
+  return t.n_cta == t.T ? x->Lf - 1 : 1;
 }
 
 // Whole trajectories in one launch: warps per chain (1, 2, 4, 8), or 0 for
@@ -510,11 +519,18 @@ pcv_status launch_proposal(pcv_ctx *x, ChainBufs &cb, bool fd, const float *r_gi
   k_begin<<<begin_blocks(cb.C, x->d), 256, 0, x->stream>>>(ba);
   CK(cudaGetLastError());
   GradArgs ga = grad_args(x, cb, true);
-  for (int s = 1; s <= x->Lf; ++s) {
-    ga.mode = s < x->Lf ? MODE_KICK_DRIFT : MODE_LAST_KICK;
-    ga.need_ll = s == x->Lf;
-    pcv_status st = launch_grad(x, ga, &cb);
+  // the kick-drift steps: one launch each, or all in one launch where each
+  // tile has a CTA of its own (BF16 form); then the last step with the log
+  // densities
+  const int per_launch = tc_steps_per_launch(x, cb.C);
+  for (int s = 1; s <= x->Lf;) {
+    const bool last = s == x->Lf;
+    const int k = last ? 1 : std::min(per_launch, x->Lf - s);
+    ga.mode = last ? MODE_LAST_KICK : MODE_KICK_DRIFT;
+    ga.need_ll = last;
+    pcv_status st = launch_grad(x, ga, &cb, k);
     if (st != PCV_OK) return st;
+    s += k;
   }
   return PCV_OK;
 }
@@ -944,6 +960,7 @@ void pcv_default_options(pcv_options *o) {
   o->extra_scores = 0;
   o->first_fold = 0;
   o->fused_trajectory = -1;
+  o->tc_steps_per_launch = 0;
 }
 
 pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
@@ -962,7 +979,8 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
       opt->acov_max_lag < 0 || opt->max_batches < 1 || opt->n_fulldata_draws < 1 ||
       !(opt->step_jitter < 1.0) || !std::isfinite(opt->trajectory_length) || opt->first_fold < 0 ||
       (opt->fused_trajectory != -1 && opt->fused_trajectory != 0 && opt->fused_trajectory != 1 &&
-       opt->fused_trajectory != 2 && opt->fused_trajectory != 4 && opt->fused_trajectory != 8))
+       opt->fused_trajectory != 2 && opt->fused_trajectory != 4 && opt->fused_trajectory != 8) ||
+      (opt->tc_steps_per_launch != 0 && opt->tc_steps_per_launch != 1))
     return invalid("an option is out of range");
   if (model->kind < PCV_GAUSS_LINEAR || model->kind > PCV_AR_GAUSS) return invalid("unknown model kind");
   if (!(model->beta_prior_sd > 0)) return invalid("beta_prior_sd must be > 0");
