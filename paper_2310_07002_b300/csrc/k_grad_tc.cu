@@ -211,29 +211,44 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       int last_round[kTcMaxStages];
 #pragma unroll
       for (int s2 = 0; s2 < kTcMaxStages; ++s2) last_round[s2] = -1;
-      for (int i = 0, j = j_first; i < nunits; j = j_step(i, j), ++i) {
-        if (!TF && seg_first(i, j)) {
-          const int t = (int)(unit_of(i) / ta.J);
-          if (!mbar_wait_fast(smem_u32(th_empty), (seg & 1) ^ 1, abort_flag, ta.err)) break;
-          // the next step of the same tile: its theta comes from the last
-          // step's finish
-          if (MS && seg > 0 && !mbar_wait_fast(smem_u32(th_ready), (seg - 1) & 1, abort_flag, ta.err)) break;
-          mbar_expect_tx(smem_u32(th_full), th_bytes * (ta.need_lo ? 2 : 1));
-          for (int kb = 0; kb < KA; ++kb) {
-            tma_load_2d(smem_u32(th_hi + kb * kTM * 128), &tm_hi, kb * AE, t * kTM, smem_u32(th_full));
-            if (!TF && ta.need_lo)
-              tma_load_2d(smem_u32(th_lo + kb * kTM * 128), &tm_lo, kb * AE, t * kTM, smem_u32(th_full));
-          }
-          th_issued = seg;
-          ++seg;
+      // theta of the segment starting at unit i (the chain tile's shadow)
+      auto load_theta = [&](const int i) -> bool {
+        const int t = (int)(unit_of(i) / ta.J);
+        if (!mbar_wait_fast(smem_u32(th_empty), (seg & 1) ^ 1, abort_flag, ta.err)) return false;
+        // the next step of the same tile: its theta comes from the last
+        // step's finish
+        if (MS && seg > 0 && !mbar_wait_fast(smem_u32(th_ready), (seg - 1) & 1, abort_flag, ta.err)) return false;
+        mbar_expect_tx(smem_u32(th_full), th_bytes * (ta.need_lo ? 2 : 1));
+        for (int kb = 0; kb < KA; ++kb) {
+          tma_load_2d(smem_u32(th_hi + kb * kTM * 128), &tm_hi, kb * AE, t * kTM, smem_u32(th_full));
+          if (!TF && ta.need_lo)
+            tma_load_2d(smem_u32(th_lo + kb * kTM * 128), &tm_lo, kb * AE, t * kTM, smem_u32(th_full));
         }
+        th_issued = seg;
+        ++seg;
+        return true;
+      };
+      // the X chunk of unit i (chunk j) into its ring slot
+      auto load_x = [&](const int i, const int j) -> bool {
         const int st = i % NS, rnd = i / NS;
-        if (!mbar_wait_fast(smem_u32(&x_empty[st]), (rnd & 1) ^ 1, abort_flag, ta.err)) break;
+        if (!mbar_wait_fast(smem_u32(&x_empty[st]), (rnd & 1) ^ 1, abort_flag, ta.err)) return false;
         mbar_expect_tx(smem_u32(&x_full[st]), x_bytes);
         uint8_t *xb = xs + (size_t)st * x_bytes;
         for (int kb = 0; kb < KA; ++kb)
           tma_load_2d(smem_u32(xb + kb * TN * 128), &tm_x, kb * AE, j * TN, smem_u32(&x_full[st]));
         last_round[st] = rnd;
+        return true;
+      };
+      for (int i = 0, j = j_first; i < nunits; j = j_step(i, j), ++i) {
+        const bool sf = !TF && seg_first(i, j);
+        if (MS && sf && seg > 0) {
+          // the next step's first chunk does not depend on the last step's
+          // finish: load it before waiting for the new theta
+          if (!load_x(i, j) || !load_theta(i)) break;
+          continue;
+        }
+        if (sf && !load_theta(i)) break;
+        if (!load_x(i, j)) break;
       }
       // on abort: let copies already issued land before the CTA exits
       if (*abort_flag) {
@@ -699,10 +714,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (!warp_wait(smem_u32(flush_bar), fl & 1, abort_flag, ta.err)) break;
       const int nseg = owner_cta((long long)t * ta.J + ta.J - 1, U, ta.n_cta) - b0 + 1;
       if (et == 0) {
-        __threadfence();
-        const unsigned prev = atomicAdd(ta.tickets + t, 1u);
-        *last_flag = (prev == (unsigned)nseg - 1);
-        if (prev == (unsigned)nseg - 1) ta.tickets[t] = 0u;
+        if constexpr (MS) {
+          *last_flag = 1;                           // the CTA is the tile's only owner
+        } else {
+          __threadfence();
+          const unsigned prev = atomicAdd(ta.tickets + t, 1u);
+          *last_flag = (prev == (unsigned)nseg - 1);
+          if (prev == (unsigned)nseg - 1) ta.tickets[t] = 0u;
+        }
         mbar_arrive(smem_u32(decide_bar));
       }
       if (!warp_wait(smem_u32(decide_bar), fl & 1, abort_flag, ta.err)) break;
