@@ -208,7 +208,7 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
-def time_steps(P, w, prec, K, Wu, seed, barrier, flush, nvtx=True, fused=-1):
+def time_steps(P, w, prec, K, Wu, seed, barrier, flush, nvtx=True, fused=-1, tc_grid=0):
     """Create a context for workload w at precision prec, run Wu untimed
     warm-up iterations, then time K sampling iterations (one step each) with
     CUDA events on the library's launch stream, L2 flushed before each step.
@@ -221,7 +221,7 @@ def time_steps(P, w, prec, K, Wu, seed, barrier, flush, nvtx=True, fused=-1):
     import time
     import torch
     common = dict(seed=seed, batch_size=1, max_batches=K + 64, acov_max_lag=64,
-                  precision=prec, init_scale=0.1, fused_trajectory=fused)
+                  precision=prec, init_scale=0.1, fused_trajectory=fused, tc_grid=tc_grid)
     pc = P.PCV.from_workload(w, **common)
     pc.warmup(100, Wu)                                   # untimed warm-up iterations
     stream = pc.stream
@@ -259,6 +259,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-form", action="store_true",
                     help="skip timing the plain FP32 form beside a BF16/TF32 run")
+    ap.add_argument("--tc-grid", type=int, default=0, choices=[0, 1, 2],
+                    help="tensor-core grid: 0 autotuned, 1 one CTA per SM (tiles split), 2 one CTA per tile "
+                         "(fixes the choice for profiler runs)")
     ap.add_argument("--fused-trajectory", type=int, default=-1, choices=[-1, 0, 1, 2, 4, 8],
                     help="whole trajectories in one launch: -1 autotuned (default), 0 never, w > 0 always "
                          "with w warps per chain where the problem allows (fixes the choice for profiler runs)")
@@ -292,7 +295,7 @@ def main():
 
     prec = P.PRECISIONS[args.precision]
     if args.profile_launches:
-        pc = P.PCV.from_workload(w, precision=prec)
+        pc = P.PCV.from_workload(w, precision=prec, tc_grid=args.tc_grid)
         theta0 = np.zeros((pc.C, w.dim))
         truth = w.truth.get("beta", w.truth.get("phi"))
         if truth is not None:
@@ -325,7 +328,7 @@ def main():
 
     clocks = ClockSampler(local)
     total_ms, C, k_ms, k_ms_hot, launches = time_steps(P, w, prec, K, Wu, seed, barrier, flush,
-                                                       fused=args.fused_trajectory)
+                                                       fused=args.fused_trajectory, tc_grid=args.tc_grid)
     clk = clocks.stop()
     if dist is not None:
         t = torch.tensor([total_ms], device="cuda")

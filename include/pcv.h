@@ -182,6 +182,11 @@ typedef struct {
      * (lock-step HMC, Section 3.3: a tile depends on no other tile); 1 runs
      * one launch per step. Both give the same bits. */
     int32_t tc_steps_per_launch;
+    /* Tensor-core grid: 0 (default) the autotuner's choice per chain count;
+     * 1 one CTA per SM with the chain tiles split across CTAs (stream-K);
+     * 2 one CTA per 128-chain tile. Fixing it makes profiler runs (where
+     * the autotuner's timings are distorted) take the grid of a live run. */
+    int32_t tc_grid;
 } pcv_options;
 
 /* Fill *opt with the defaults listed above (seed 0, L_f 16, adapted step). */

@@ -352,6 +352,8 @@ TcArgs tc_args(pcv_ctx *x, int C, bool need_ll) {
   // across CTAs: better for short tiles, worse when tiles are long)
   auto itn = x->tuned_ncta.find(C);
   if (itn != x->tuned_ncta.end()) t.n_cta = (int)std::min<long long>(itn->second, U);
+  if (x->opt.tc_grid == 1) t.n_cta = (int)std::min<long long>(x->n_sm, U);   // fixed by the caller
+  else if (x->opt.tc_grid == 2) t.n_cta = t.T;
   t.max_seg = tc_segments_per_tile(t.T, t.J, t.n_cta);
   // theta hi + lo where log densities are needed or no centring reference
   // is set yet; the kick-drift launches of centred chains use hi only
@@ -633,7 +635,7 @@ pcv_status tune(pcv_ctx *x, ChainBufs &cb) {
   if (x->tc) x->tuned_ns[std::make_pair(C, need_lo)] = best;
   else x->tuned_splits[C] = best;
   x->tune_log.push_back(log + " -> " + std::to_string(best));
-  if (x->tc && x->tuned_ncta.count(C) == 0) {
+  if (x->tc && x->opt.tc_grid == 0 && x->tuned_ncta.count(C) == 0) {
     // grid: one CTA per SM (tiles split across CTAs, stream-K) or, when
     // there are fewer tiles than SMs, one CTA per tile
     const int T = (C + 127) / 128;
@@ -961,6 +963,7 @@ void pcv_default_options(pcv_options *o) {
   o->first_fold = 0;
   o->fused_trajectory = -1;
   o->tc_steps_per_launch = 0;
+  o->tc_grid = 0;
 }
 
 pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
@@ -980,7 +983,7 @@ pcv_status pcv_create(const pcv_model *model, const float *X, const float *y,
       !(opt->step_jitter < 1.0) || !std::isfinite(opt->trajectory_length) || opt->first_fold < 0 ||
       (opt->fused_trajectory != -1 && opt->fused_trajectory != 0 && opt->fused_trajectory != 1 &&
        opt->fused_trajectory != 2 && opt->fused_trajectory != 4 && opt->fused_trajectory != 8) ||
-      (opt->tc_steps_per_launch != 0 && opt->tc_steps_per_launch != 1))
+      (opt->tc_steps_per_launch != 0 && opt->tc_steps_per_launch != 1) || opt->tc_grid < 0 || opt->tc_grid > 2)
     return invalid("an option is out of range");
   if (model->kind < PCV_GAUSS_LINEAR || model->kind > PCV_AR_GAUSS) return invalid("unknown model kind");
   if (!(model->beta_prior_sd > 0)) return invalid("beta_prior_sd must be > 0");

@@ -58,7 +58,8 @@ class Options(ct.Structure):
                 ("step_jitter", ct.c_double), ("autotune", ct.c_int32),
                 ("extra_scores", ct.c_int32), ("first_fold", ct.c_int32),
                 ("fused_trajectory", ct.c_int32),
-                ("tc_steps_per_launch", ct.c_int32)]
+                ("tc_steps_per_launch", ct.c_int32),
+                ("tc_grid", ct.c_int32)]
 
 
 _lib = None
@@ -190,7 +191,7 @@ class PCV:
                  trajectory_length: float = -1.0, step_jitter: float = -1.0,
                  autotune: bool = True, active=None, extra_scores: int = 0,
                  first_fold: int = 0, fused_trajectory: int = -1, active_b=None,
-                 tc_steps_per_launch: int = 0):
+                 tc_steps_per_launch: int = 0, tc_grid: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("PCV needs a CUDA device (sm_103a); none is available")
@@ -235,6 +236,7 @@ class PCV:
         o.first_fold = first_fold
         o.fused_trajectory = fused_trajectory
         o.tc_steps_per_launch = tc_steps_per_launch
+        o.tc_grid = tc_grid
         self._alloc = None
         if torch_allocator:
             self._alloc = _TorchAllocator(torch.cuda.current_device())
