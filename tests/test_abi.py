@@ -57,6 +57,7 @@ def test_default_options_host_only(libpcv):
     assert o.leapfrog_steps == 16 and o.batch_size == 50 and o.step_size < 0
     assert o.acov_max_lag == 64 and o.use_graphs == 1 and o.max_batches == 1024
     assert o.trajectory_length == -1.0 and o.step_jitter == -1.0     # defaults: auto
+    assert o.fused_trajectory == -1 and o.tc_steps_per_launch == 0 and o.tc_grid == 0
 
 
 def test_create_rejects_bad_arguments_before_any_cuda_call(libpcv):
@@ -90,6 +91,14 @@ def test_create_rejects_bad_arguments_before_any_cuda_call(libpcv):
     assert not h.value
     assert L.pcv_num_folds(None) == -1
     assert L.pcv_last_error(None) == b"an option is out of range"
+    # the launch-shape options take only their listed values
+    for field, bad in [("fused_trajectory", 3), ("tc_steps_per_launch", 2), ("tc_steps_per_launch", -1),
+                       ("tc_grid", 3), ("tc_grid", -1)]:
+        L.pcv_default_options(ct.byref(o))
+        setattr(o, field, bad)
+        assert L.pcv_create(ct.byref(m), X.ctypes.data, y.ctypes.data, f.ctypes.data, 10, 2, 4,
+                            ct.byref(o), ct.byref(h)) == E_INVALID_ARG, (field, bad)
+        assert L.pcv_last_error(None) == b"an option is out of range"
     # a model kind the library does not know
     L.pcv_default_options(ct.byref(o))
     m.kind = 99
