@@ -175,7 +175,7 @@ typedef struct {
      * takes it, with teams that fill the GPU); 0 never; 1, 2, 4 or 8: always
      * where the problem allows it, with that many warps per chain. */
     int32_t fused_trajectory;
-    /* Tensor-core BF16 form, where each 128-chain tile has a CTA of its own
+    /* Tensor-core forms (BF16, TF32), where each 128-chain tile has a CTA of its own
      * (the autotuner's grid for short tiles, e.g. leave-one-out on a few
      * thousand rows): 0 (default) runs the L_f - 1 kick-drift steps of a
      * trajectory in one launch, each CTA carrying its tile from step to step

@@ -675,7 +675,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (aborted) break;
       // TF32: the next segment's theta goes to TMEM before this
       // segment's finish, so that its first GEMMs need not wait for it
-      if constexpr (TF) {
+      // (several steps per launch: the next segment is this tile's next
+      // step, whose theta comes from this finish, so it goes after it)
+      if constexpr (TF && !MS) {
         if (ie < nunits && !theta_to_tmem((int)(unit_of(ie) / ta.J), nseg_done + 1)) break;
       }
       // ---- segment end (both groups): the group that owns the segment's
@@ -916,6 +918,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(th_ready));
         if (!warp_wait(smem_u32(th_ready), fl & 1, abort_flag, ta.err)) break;
+        // TF32: the new theta into TMEM for the next step's first GEMMs
+        if constexpr (TF) {
+          if (ie < nunits && !theta_to_tmem((int)(unit_of(ie) / ta.J), nseg_done)) break;
+        }
       }
       ib = ie;
     }
@@ -970,10 +976,9 @@ static cudaError_t set_smem_attr() {
                       cudaFuncSetAttribute(k_grad_tc<KS, false, true, TF>, at, 227 * 1024),
                       cudaFuncSetAttribute(k_grad_tc<KS, true, true, TF>, at, 227 * 1024),
                       cudaSuccess, cudaSuccess};
-  if constexpr (!TF) {   // the several-steps kick-drift kernels
-    r[4] = cudaFuncSetAttribute(k_grad_tc<KS, false, false, false, true>, at, 227 * 1024);
-    r[5] = cudaFuncSetAttribute(k_grad_tc<KS, false, true, false, true>, at, 227 * 1024);
-  }
+  // the several-steps kick-drift kernels
+  r[4] = cudaFuncSetAttribute(k_grad_tc<KS, false, false, TF, true>, at, 227 * 1024);
+  r[5] = cudaFuncSetAttribute(k_grad_tc<KS, false, true, TF, true>, at, 227 * 1024);
   for (cudaError_t x : r)
     if (x != cudaSuccess) return x;
   return cudaSuccess;
@@ -993,12 +998,9 @@ static bool regs_fit() {
       cudaFuncGetAttributes(&fa[2], k_grad_tc<KS, false, true, TF>) != cudaSuccess ||
       cudaFuncGetAttributes(&fa[3], k_grad_tc<KS, true, true, TF>) != cudaSuccess)
     return false;
-  fa[4] = fa[5] = fa[0];
-  if constexpr (!TF) {
-    if (cudaFuncGetAttributes(&fa[4], k_grad_tc<KS, false, false, false, true>) != cudaSuccess ||
-        cudaFuncGetAttributes(&fa[5], k_grad_tc<KS, false, true, false, true>) != cudaSuccess)
-      return false;
-  }
+  if (cudaFuncGetAttributes(&fa[4], k_grad_tc<KS, false, false, TF, true>) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa[5], k_grad_tc<KS, false, true, TF, true>) != cudaSuccess)
+    return false;
   for (const cudaFuncAttributes &f : fa)
     if ((long)f.numRegs * kTcThreads < need) return false;
   return true;
@@ -1029,12 +1031,10 @@ template <int K, bool TF>
 static void launch_k(bool gauss, bool accurate, const CUtensorMap &tm_x, const CUtensorMap &tm_hi,
                      const CUtensorMap &tm_lo, const Problem &pb, const GradArgs &a, const TcArgs &ta, size_t smem,
                      cudaStream_t st) {
-  if constexpr (!TF) {
-    if (ta.steps > 1) {   // several kick-drift steps (the caller checked the form and the grid)
-      if (gauss) k_grad_tc<K, false, true, false, true><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta);
-      else k_grad_tc<K, false, false, false, true><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta);
-      return;
-    }
+  if (ta.steps > 1) {   // several kick-drift steps (the caller checked the grid)
+    if (gauss) k_grad_tc<K, false, true, TF, true><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta);
+    else k_grad_tc<K, false, false, TF, true><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta);
+    return;
   }
   if (gauss) {
     if (accurate) k_grad_tc<K, true, true, TF><<<ta.n_cta, kTcThreads, smem, st>>>(tm_x, tm_hi, tm_lo, pb, a, ta);
@@ -1064,8 +1064,8 @@ cudaError_t launch_grad_tc(const CUtensorMap &tm_x, const CUtensorMap &tm_hi, co
   if (!g_tc_regs_ok) return cudaErrorInvalidConfiguration;   // tc_prepare not run, or the split does not fit
   if (pb.variant == MV_HIER) return cudaErrorInvalidValue;
   if (ta.tf32 && ta.need_lo) return cudaErrorInvalidValue;    // the TF32 form has no lo part
-  // several steps per launch: BF16 kick-drift steps, one CTA per tile
-  if (ta.steps > 1 && (ta.tf32 || ta.n_cta != ta.T || a.mode != MODE_KICK_DRIFT || a.need_ll))
+  // several steps per launch: kick-drift steps, one CTA per tile
+  if (ta.steps > 1 && (ta.n_cta != ta.T || a.mode != MODE_KICK_DRIFT || a.need_ll))
     return cudaErrorInvalidValue;
   const bool gauss = pb.variant == MV_GAUSS_KNOWN || pb.variant == MV_GAUSS_LOGSIG;
   const bool ok = ta.tf32 ? launch_ks<true>(ta.KS, std::make_integer_sequence<int, 15>{}, gauss, ta.accurate != 0,

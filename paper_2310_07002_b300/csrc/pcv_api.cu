@@ -445,9 +445,9 @@ pcv_status launch_grad(pcv_ctx *x, GradArgs a, const ChainBufs *cb = nullptr, in
 }
 
 // Kick-drift steps per tensor-core launch for a chain set: all L_f - 1 of
-// them where each 128-chain tile has a CTA of its own (BF16 form), else one.
+// them where each 128-chain tile has a CTA of its own, else one.
 int tc_steps_per_launch(pcv_ctx *x, int C) {
-  if (!x->tc || x->tc32 || x->opt.tc_steps_per_launch == 1 || x->Lf < 3) return 1;
+  if (!x->tc || x->opt.tc_steps_per_launch == 1 || x->Lf < 3) return 1;
   const TcArgs t = tc_args(x, C, false);
   return t.n_cta == t.T ? x->Lf - 1 : 1;
 }

@@ -272,7 +272,7 @@ struct TcArgs {
   unsigned int *err;      // error flags (bit 0: wait time-out)
   int tf32;               // TF32 operands (kind::tf32, 64-row chunks, X^T for the second GEMM)
   float *shadow32;        // TF32 path: (theta - theta_ref) / 2 rounded to TF32 [C_pad x KP]
-  int steps;              // kick-drift steps in this launch (> 1: BF16, one CTA per tile)
+  int steps;              // kick-drift steps in this launch (> 1: one CTA per tile)
 };
 
 // launchers (k_grad_simt.cu)

@@ -1,16 +1,16 @@
-"""Several leapfrog steps per tensor-core launch (BF16 form, one CTA per
-128-chain tile; lock-step HMC of Section 3.3: a tile depends on no other
-tile, so its CTA can carry it from step to step): the L_f - 1 kick-drift
-steps of a trajectory in one launch give the same bits as one launch per
-step, and the iteration is then 4 launches (begin, kick-drift steps, last
-step with the log densities, accept) instead of L_f + 2.
+"""Several leapfrog steps per tensor-core launch (BF16 and TF32 forms, one
+CTA per 128-chain tile; lock-step HMC of Section 3.3: a tile depends on no
+other tile, so its CTA can carry it from step to step): the L_f - 1
+kick-drift steps of a trajectory in one launch give the same bits as one
+launch per step on the same grid, and the iteration is then 4 launches
+(begin, kick-drift steps, last step with the log densities, accept)
+instead of L_f + 2.
 
-* tiles of one 128-row chunk (N <= 128: one CTA per tile whatever the
-  autotuner chooses), logistic and AR(2) with log sigma sampled (its
-  coordinate is finished by other epilogue threads than those that read it
-  at the next step);
-* config 2 itself (2000 rows: 16 chunks per tile), where the autotuner
-  gives each of the 125 tiles a CTA of its own.
+* short tiles, logistic and AR(2) with log sigma sampled (its coordinate is
+  finished by other epilogue threads than those that read it at the next
+  step);
+* config 2 itself (2000 rows: 16 BF16 or 32 TF32 chunks per tile).
+The grid is fixed to one CTA per tile (tc_grid = 2) for both runs.
 """
 import numpy as np
 import pytest
@@ -38,10 +38,10 @@ def cases():
     }
 
 
-def run(w, eps, n, per_launch):
-    from paper_2310_07002_b300.pcv import PCV, BF16
-    pc = PCV.from_workload(w, precision=BF16, fused_trajectory=0, tc_steps_per_launch=per_launch,
-                           step_size=eps, batch_size=n // 2, acov_max_lag=4)
+def run(w, eps, n, per_launch, precision):
+    from paper_2310_07002_b300.pcv import PCV, PRECISIONS
+    pc = PCV.from_workload(w, precision=PRECISIONS[precision], fused_trajectory=0, tc_grid=2,
+                           tc_steps_per_launch=per_launch, step_size=eps, batch_size=n // 2, acov_max_lag=4)
     truth = np.zeros(w.dim)
     tv = w.truth.get("beta", w.truth.get("phi"))
     truth[:len(tv)] = tv
@@ -56,11 +56,12 @@ def run(w, eps, n, per_launch):
     return th, lp, sh, acc, launches
 
 
+@pytest.mark.parametrize("precision", ["bf16", "tf32"])
 @pytest.mark.parametrize("name", ["logistic_one_chunk", "ar2_one_chunk", "logistic_loo_config2"])
-def test_steps_per_launch_same_bits(torch, name):
+def test_steps_per_launch_same_bits(torch, name, precision):
     w, eps, n = cases()[name]
-    one = run(w, eps, n, 1)
-    many = run(w, eps, n, 0)
+    one = run(w, eps, n, 1, precision)
+    many = run(w, eps, n, 0, precision)
     for a, b in zip(one[:3], many[:3]):
         assert np.array_equal(a, b), np.abs(a - b).max()
     assert np.array_equal(np.asarray(one[3]), np.asarray(many[3]))
