@@ -547,9 +547,9 @@ __device__ __forceinline__ void eval_hier(const Problem &pb, const Rows<PP, fals
   float dls = 0.0f, dlt = 0.0f, llt = 0.0f;
   double lte = 0.0;
   for (int gg = lane; gg < G; gg += 32) {
-    const int gid = __ldg(pb.seg_grp + gg);
+    const int gid = pb.seg_grp[gg];
     const float z = zs[gid], off = tau * z;
-    const int n0 = __ldg(pb.grp_off + gg), n1 = __ldg(pb.grp_off + gg + 1);
+    const int n0 = pb.grp_off[gg], n1 = pb.grp_off[gg + 1];
     const bool test_seg = LL && n1 > n0 && n0 >= fd.test_lo && n1 <= fd.test_hi;
     float seg = 0.0f, s1 = 0.0f, s2 = 0.0f;
     auto row = [&](const float (&x)[PP], float yv, int n) {
@@ -630,7 +630,7 @@ __device__ __forceinline__ void traj_hier(const Problem &pb, const TrajArgs &t, 
   for (int j = 0; j < PP; ++j) { bt[j] = j < p ? th0[j] : 0.0f; rb[j] = 0.0f; }
   float lt = th0[jt], ls = th0[js], rlt = 0.0f, rls = 0.0f, glt = 0.0f, gls = 0.0f;
   for (int gg = lane; gg < G; gg += 32) {          // each lane its own groups' z
-    const int gid = __ldg(pb.seg_grp + gg);
+    const int gid = pb.seg_grp[gg];
     zs[gid] = th0[p + gid];
   }
   double ll_tr = 0.0, ll_te = 0.0, H0 = 0.0;
@@ -681,7 +681,7 @@ __device__ __forceinline__ void traj_hier(const Problem &pb, const TrajArgs &t, 
       if (lane == (js & 31)) kterm += k;
     }
     for (int gg = lane; gg < G; gg += 32) {
-      const int gid = __ldg(pb.seg_grp + gg);
+      const int gid = pb.seg_grp[gg];
       float tn, rh;
       kterm += start(p + gid, zs[gid], tn, rh);
       zs[gid] = tn;
@@ -707,7 +707,7 @@ __device__ __forceinline__ void traj_hier(const Problem &pb, const TrajArgs &t, 
         ls += eps * mvr[js] * rls;
       }
       for (int gg = lane; gg < G; gg += 32) {
-        const int gid = __ldg(pb.seg_grp + gg);
+        const int gid = pb.seg_grp[gg];
         rz[gid] += kick * gz[gid];
         if (!last) zs[gid] += eps * mvr[p + gid] * rz[gid];
       }
@@ -720,7 +720,7 @@ __device__ __forceinline__ void traj_hier(const Problem &pb, const TrajArgs &t, 
   for (int j = 0; j < PP; ++j)
     if (j < p && lane == (j & 31)) lpt += -0.5f * kLog2Pi - pb.log_beta_sd - 0.5f * bt[j] * bt[j] * pb.beta_prec;
   for (int gg = lane; gg < G; gg += 32) {
-    const float z = zs[__ldg(pb.seg_grp + gg)];
+    const float z = zs[pb.seg_grp[gg]];
     lpt += -0.5f * kLog2Pi - 0.5f * z * z;
   }
   if (lane == (jt & 31))
@@ -751,7 +751,7 @@ __device__ __forceinline__ void traj_hier(const Problem &pb, const TrajArgs &t, 
       go[js] = gls;
     }
     for (int gg = lane; gg < G; gg += 32) {
-      const int gid = __ldg(pb.seg_grp + gg);
+      const int gid = pb.seg_grp[gg];
       if (tho) tho[p + gid] = zs[gid];
       if (ro) ro[p + gid] = rz[gid];
       go[p + gid] = gz[gid];
@@ -774,7 +774,7 @@ __device__ __forceinline__ void traj_hier(const Problem &pb, const TrajArgs &t, 
   if (lane == (jt & 31)) kt = fmaf(mvr[jt] * rlt, rlt, kt);
   if (lane == (js & 31)) kt = fmaf(mvr[js] * rls, rls, kt);
   for (int gg = lane; gg < G; gg += 32) {
-    const int gid = __ldg(pb.seg_grp + gg);
+    const int gid = pb.seg_grp[gg];
     kt = fmaf(mvr[p + gid] * rz[gid], rz[gid], kt);
   }
   const double H1 = -logp1 + 0.5 * warp_sum_d((double)kt);
@@ -791,8 +791,9 @@ __device__ __forceinline__ void traj_hier(const Problem &pb, const TrajArgs &t, 
 }
 
 // Every chain reads every row at every step, so the CTA first copies X (PP
-// columns per row) and y into shared memory when they fit beside the
-// chains' slices (t.smem_rows; t.part_offset: bytes of the staged rows);
+// columns per row), y and the group tables (segment offsets and groups)
+// into shared memory when they fit beside the chains' slices (t.smem_rows;
+// t.part_offset: bytes of the staged rows);
 // the warps of a CTA (blockDim.x / 32, up to hier_warps_max(PP): 16 where
 // the registers of a wider row would not fit) are its chains.
 constexpr int hier_warps_max(int PP) { return PP <= 12 ? 16 : 8; }
@@ -802,6 +803,7 @@ __global__ void __launch_bounds__(hier_warps_max(PP) * 32, 1) k_traj_hier(Proble
   extern __shared__ __align__(16) uint8_t hier_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   Rows<PP, false> R{pb.X, nullptr, pb.y, pb.p_pad};
+  Problem pl = pb;
   if (t.smem_rows) {
     float *xs = reinterpret_cast<float *>(hier_smem);
     for (int i = threadIdx.x; i < pb.N * PP; i += blockDim.x) {
@@ -810,15 +812,21 @@ __global__ void __launch_bounds__(hier_warps_max(PP) * 32, 1) k_traj_hier(Proble
     }
     float *ys = xs + (size_t)pb.N * PP;
     for (int i = threadIdx.x; i < pb.N; i += blockDim.x) ys[i] = __ldg(pb.y + i);
+    // the group tables too: each segment's row loop waits on them
+    int *go = reinterpret_cast<int *>(ys + pb.N), *sg = go + pb.G + 1;
+    for (int i = threadIdx.x; i <= pb.G; i += blockDim.x) go[i] = __ldg(pb.grp_off + i);
+    for (int i = threadIdx.x; i < pb.G; i += blockDim.x) sg[i] = __ldg(pb.seg_grp + i);
     __syncthreads();
     R.X = xs;
     R.y = ys;
     R.stride = PP;
+    pl.grp_off = go;
+    pl.seg_grp = sg;
   }
   float *zsh = reinterpret_cast<float *>(hier_smem + t.part_offset) + (size_t)warp * (3 * pb.G + pb.d_pad);
   const int c = blockIdx.x * nw + warp;
   if (c < t.C) {
-    traj_hier<PP>(pb, t, R, c, lane, zsh);
+    traj_hier<PP>(pl, t, R, c, lane, zsh);
   } else if (t.accept) {   // no chain: still meets the batched accept's barriers
     double sd;
     accept_batch(t, -1, lane, blockIdx.x * nw, min(nw, t.C - (int)blockIdx.x * nw), 0.0, false, 0.0, 0.0, sd);
@@ -899,7 +907,8 @@ static cudaError_t launch_hier(const Problem &pb, TrajArgs t, cudaStream_t st) {
   if (t.wpc != 1 || t.X16) return cudaErrorInvalidValue;
   // warps (chains) per CTA: enough for one wave over the 148 SMs, at most 16
   int nw = (int)std::min<long long>(hier_warps_max(PP), std::max<long long>(1, ((long long)t.C + 147) / 148));
-  const size_t rows = ((size_t)pb.N * PP * sizeof(float) + (size_t)pb.N * sizeof(float) + 15) / 16 * 16;
+  const size_t rows = ((size_t)pb.N * PP * sizeof(float) + (size_t)pb.N * sizeof(float) +
+                       (2 * (size_t)pb.G + 1) * sizeof(int) + 15) / 16 * 16;
   const size_t slice = traj_hier_slice(pb);
   t.smem_rows = rows + (size_t)nw * slice <= kHierSmemMax ? 1 : 0;
   if (!t.smem_rows) nw = kTrajWarps;          // rows from global memory: 8 chains per CTA
