@@ -45,11 +45,14 @@ def bf16_workload(p):
 
 # p = 14: the three eta_ref columns spill into a second K step (KS = 2);
 # p = 128: KS = 9, K padded to 192 (three 64-column TMA atoms)
+# grid 0: the autotuner's (here the split grid for 300 positions); 2: one
+# CTA per 128-chain tile
+@pytest.mark.parametrize("grid", [0, 2])
 @pytest.mark.parametrize("p", [14, 20, 100, 128])
-def test_bf16_log_density_and_gradient(torch, orc, p):
+def test_bf16_log_density_and_gradient(torch, orc, p, grid):
     from paper_2310_07002_b300.pcv import PCV, BF16
     w = bf16_workload(p)
-    pc = PCV.from_workload(w, precision=BF16)
+    pc = PCV.from_workload(w, precision=BF16, tc_grid=grid)
     prob = orc.problem_from_workload(w)
     n = 300                                       # 128 + 128 + 44 positions
     scale = 0.3 if p <= 32 else 0.1
@@ -102,13 +105,17 @@ def test_bf16_gradient_where_the_model_predicts_well(torch, orc):
     pc.close()
 
 
+# grid 2: one CTA per tile, so the kick-drift steps of the trajectory run in
+# one launch
+@pytest.mark.parametrize("grid", [0, 2])
 @pytest.mark.parametrize("p", [20, 100, 128])
-def test_bf16_trajectory(torch, orc, p):
+def test_bf16_trajectory(torch, orc, p, grid):
     from paper_2310_07002_b300.pcv import PCV, BF16
     w = bf16_workload(p)
     eps = 0.01 if p <= 32 else 0.004
     minv = np.ones(w.dim)
-    pc = PCV.from_workload(w, precision=BF16, step_size=eps, inv_mass_diag=minv, fused_trajectory=0)
+    pc = PCV.from_workload(w, precision=BF16, step_size=eps, inv_mass_diag=minv, fused_trajectory=0,
+                           tc_grid=grid)
     prob = orc.problem_from_workload(w)
     g = np.random.Generator(np.random.Philox(6))
     th0 = (0.2 if p <= 32 else 0.05) * g.standard_normal((w.n_chains, w.dim))
