@@ -70,13 +70,16 @@ def test_tf32_log_density_and_gradient(torch, orc, name):
     pc.close()
 
 
+# grid 2: one CTA per tile, so the kick-drift steps of the trajectory run in
+# one launch (theta reaches TMEM after each step's finish)
+@pytest.mark.parametrize("grid", [0, 2])
 @pytest.mark.parametrize("name", ["logistic_p100", "gauss_p40"])
-def test_tf32_trajectory(torch, orc, name):
+def test_tf32_trajectory(torch, orc, name, grid):
     from paper_2310_07002_b300.pcv import PCV, TF32
     w = workloads()[name]
     eps = 0.004 if name == "logistic_p100" else 0.002
     minv = np.linspace(0.5, 1.5, w.dim)
-    pc = PCV.from_workload(w, precision=TF32, step_size=eps, inv_mass_diag=minv)
+    pc = PCV.from_workload(w, precision=TF32, step_size=eps, inv_mass_diag=minv, tc_grid=grid)
     prob = orc.problem_from_workload(w)
     g = np.random.Generator(np.random.Philox(7))
     t0 = torch.tensor(0.05 * g.standard_normal((w.n_chains, w.dim)), dtype=torch.float32, device="cuda")
