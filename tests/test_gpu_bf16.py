@@ -207,13 +207,17 @@ def test_bf16_gaussian_log_density_and_gradient(torch, orc, name):
     pc.close()
 
 
+# grid 2: one CTA per tile, the kick-drift steps in one launch (log sigma is
+# finished by other epilogue threads than those reading it at the next step)
+@pytest.mark.parametrize("grid", [0, 2])
 @pytest.mark.parametrize("name", ["gauss", "gauss_logsig_p40", "ar2"])
-def test_bf16_gaussian_trajectory(torch, orc, name):
+def test_bf16_gaussian_trajectory(torch, orc, name, grid):
     from paper_2310_07002_b300.pcv import PCV, BF16
     w = gauss_bf16_workloads()[name]
     eps = {"gauss": 0.01, "gauss_logsig_p40": 0.002, "ar2": 0.005}[name]
     minv = np.ones(w.dim)
-    pc = PCV.from_workload(w, precision=BF16, step_size=eps, inv_mass_diag=minv, fused_trajectory=0)
+    pc = PCV.from_workload(w, precision=BF16, step_size=eps, inv_mass_diag=minv, fused_trajectory=0,
+                           tc_grid=grid)
     prob = orc.problem_from_workload(w)
     g = np.random.Generator(np.random.Philox(7))
     th0 = 0.2 * g.standard_normal((w.n_chains, w.dim))
